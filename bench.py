@@ -1,0 +1,357 @@
+#!/usr/bin/env python3
+"""Benchmark: UOT Sinkhorn sweeps/s (and kernel-sum matvecs/s) at n = m = 2^20,
+d = 3 on the Gaussian-mixture workload, through the uotk C ABI.
+
+A step is one complete unbalanced Sinkhorn solve of the workload (200 sweeps of
+Alg. 2 with the NFFT fast summation by default; --method direct runs Alg. 1's
+exact form): plan, binning, every sweep (two kernel summations and two FP64 dual
+updates each) and the dual value.  `value` = sweeps processed by all ranks /
+max-over-ranks time.  Inputs are resident in HBM; L2 is flushed between steps.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--method nfft|direct]
+  python bench.py --impl reference ...   # the FP64 CPU oracle on this host's cores
+
+Under torchrun each rank runs an independent replica (the path has no exchange
+step: "replicas only"); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "kernel-sum matvecs/s and UOT Sinkhorn sweeps/s at n=m=2^20,d=3 (direct vs NFFT, rel err)"
+UNIT = "sweeps/s"
+L2_FLUSH_BYTES = 512 << 20   # > 129 MB L2
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="uotk", choices=["uotk", "reference"])
+    p.add_argument("--method", default="nfft", choices=["nfft", "direct"])
+    p.add_argument("--sweeps", type=int, default=0, help="sweeps per solve (0: the workload's)")
+    p.add_argument("--n", type=int, default=1 << 20)
+    p.add_argument("--no-extras", action="store_true", help="skip direct/oracle side measurements")
+    p.add_argument("--cpu-seconds", type=float, default=12.0)
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")),
+            int(os.environ.get("LOCAL_RANK", "0")))
+
+
+class ClockSampler:
+    """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                mhz.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        mhz.sort()
+        med = mhz[len(mhz) // 2] if mhz else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(mhz)}
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def cpu_oracle_rate(W, seconds, rank0=True):
+    """FP64 oracle kernel-sum pairs/s on this host: all sources onto a sample of
+    targets sized for about `seconds` of CPU work."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    Y = W.y.astype(np.float64)
+    B = W.b.astype(np.float64)
+    X = W.x.astype(np.float64)
+    t = 64
+    while True:
+        t0 = time.perf_counter()
+        oracle.ksum(Y, B, X[:t], W.eps)
+        dt = time.perf_counter() - t0
+        if dt > 0.5 or t >= W.n:
+            break
+        t = min(W.n, t * 4)
+    rate = t * W.m / dt
+    want = int(min(W.n, max(t, rate * seconds / W.m)))
+    t0 = time.perf_counter()
+    oracle.ksum(Y, B, X[:want], W.eps)
+    dt = time.perf_counter() - t0
+    return want * W.m / dt, want, dt, oracle.num_threads()
+
+
+def reference_arm(args, W, rank, world):
+    """The base contract's reference arm is the FP64 oracle (timed as it stands)."""
+    if rank != 0:
+        return
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    Y, B, X = W.y.astype(np.float64), W.b.astype(np.float64), W.x.astype(np.float64)
+    # size one step to ~2 s of host work
+    t0 = time.perf_counter()
+    oracle.ksum(Y, B, X[:128], W.eps)
+    per_target = (time.perf_counter() - t0) / 128
+    tgt = int(max(64, min(W.n, 2.0 / per_target)))
+    for _ in range(args.warmup):
+        oracle.ksum(Y, B, X[:tgt], W.eps)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.ksum(Y, B, X[:tgt], W.eps)
+    dt = (time.perf_counter() - t0) / args.steps
+    pairs_per_s = tgt * W.m / dt
+    sweeps_per_s = pairs_per_s / (2.0 * W.n * W.m)
+    sample = (f"per step: FP64 kernel sum of all {W.m} sources onto {tgt} targets "
+              f"(one half-sweep restricted to {tgt} rows); sweeps/s extrapolated as "
+              f"pairs/s / (2 n m)")
+    line = {"impl": "reference", "metric": METRIC, "value": sweeps_per_s, "unit": UNIT,
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dt * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"gmm3 n=m={W.n} d=3 eps={W.eps} rho={W.rho}",
+                       "sweeps_per_solve": W.sweeps},
+            "cpu_baseline": {"value": sweeps_per_s, "unit": UNIT, "cores": oracle.num_threads(),
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": sweeps_per_s, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_env()
+    from paper_2306_13618_gb300 import inputs
+    W = inputs.gmm3(seed=2000, n=args.n, m=args.n)
+    if args.sweeps:
+        W.sweeps = args.sweeps
+    elif args.method == "direct":
+        W.sweeps = 2  # 200 exact sweeps at 2^20 would take ~100 s; see matvecs
+    if args.impl == "reference":
+        return reference_arm(args, W, rank, world)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2306_13618_gb300 import build as B
+    from paper_2306_13618_gb300 import uotk
+    B.build()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dev = torch.device("cuda", local)
+    ctx = uotk.default_context(local)
+    x, y = torch.from_numpy(W.x).to(dev), torch.from_numpy(W.y).to(dev)
+    a, b = torch.from_numpy(W.a).to(dev), torch.from_numpy(W.b).to(dev)
+    beta = torch.empty(W.n, device=dev, dtype=torch.float64)
+    gamma = torch.empty(W.m, device=dev, dtype=torch.float64)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
+    nfft_kw = {} if args.method == "direct" else {}
+
+    def step():
+        return uotk.uot_sinkhorn(x, a, y, b, W.eps, W.rho, max_sweeps=W.sweeps,
+                                 method=args.method, ctx=ctx, beta=beta, gamma=gamma, **nfft_kw)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ctx.profile_reset()
+    ctx.set_profiling(True)
+    launches0 = ctx.launch_count()
+    times = []
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = step()
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    t_wall = time.perf_counter() - t_wall
+    launches = ctx.launch_count() - launches0
+    prof = ctx.profile()
+    ctx.set_profiling(False)
+    clk = clocks.stop()
+    ms = sum(times) / len(times)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    value = world * W.sweeps / (ms / 1e3)
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
+    # --- roofline of the dominant kernel (stage with the largest device time) ---
+    peaks, peak_kind = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    stages = {k: v for k, v in prof.items()}
+    dom = max(stages.items(), key=lambda kv: kv[1][1]) if stages else ("none", (0, 0.0))
+    dom_name, (dom_launches, dom_ms) = dom
+    per_launch_s = dom_ms / 1e3 / max(dom_launches, 1)
+    clk_mhz = peaks.get("sm_max_mhz", 2070.0)
+    roof = {"kernel": dom_name, "launches": dom_launches,
+            "share": dom_ms / max(sum(v[1] for v in stages.values()), 1e-12)}
+    if dom_name == "direct":
+        pairs = float(W.n) * W.m
+        peak = 16.0 * sms * clk_mhz * 1e6 / 1e9  # MUFU ex2 per clock per SM x SMs x clock
+        roof.update({"bound": "alu", "achieved": pairs / per_launch_s / 1e9, "peak": peak,
+                     "unit": "Gexp2/s", "peak_source": f"16 ex2/clk/SM x {sms} SMs x {clk_mhz:.0f} MHz"})
+    else:
+        roof.update({"bound": "alu", "achieved": None, "peak": None, "unit": None})
+    if roof.get("achieved") and roof.get("peak"):
+        roof["frac"] = roof["achieved"] / roof["peak"]
+    roof["traffic"] = None
+
+    # --- end to end through the C ABI from pinned host buffers ---
+    hx, hy = torch.from_numpy(W.x).pin_memory(), torch.from_numpy(W.y).pin_memory()
+    ha, hb = torch.from_numpy(W.a).pin_memory(), torch.from_numpy(W.b).pin_memory()
+    hbeta = torch.empty(W.n, dtype=torch.float64).pin_memory()
+    hgamma = torch.empty(W.m, dtype=torch.float64).pin_memory()
+    e2e_steps = min(args.steps, 2)
+    e2e_times = []
+    for _ in range(e2e_steps):
+        flush.zero_()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        x.copy_(hx, non_blocking=True); y.copy_(hy, non_blocking=True)
+        a.copy_(ha, non_blocking=True); b.copy_(hb, non_blocking=True)
+        step()
+        hbeta.copy_(beta, non_blocking=True); hgamma.copy_(gamma, non_blocking=True)
+        e1.record(stream)
+        e1.synchronize()
+        e2e_times.append(e0.elapsed_time(e1))
+    e2e_ms = sum(e2e_times) / len(e2e_times)
+    h2d = sum(t.numel() * t.element_size() for t in (hx, hy, ha, hb))
+    d2h = sum(t.numel() * t.element_size() for t in (hbeta, hgamma))
+
+    extras = {}
+    if not args.no_extras:
+        import oracle
+        idx = inputs.subsample_rows(inputs.rng(11), 256, W.n)
+        X, Y, Bw = W.x.astype(np.float64), W.y.astype(np.float64), W.b.astype(np.float64)
+        ref = oracle.ksum(Y, Bw, X[idx], W.eps)
+        scale = Bw.sum()
+        for meth in ("nfft", "direct"):
+            try:
+                out = uotk.kernel_sum(y, b, x, W.eps, method=meth, ctx=ctx)
+                torch.cuda.synchronize()
+                reps = 3 if meth == "nfft" else 1
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(reps):
+                    out = uotk.kernel_sum(y, b, x, W.eps, method=meth, ctx=ctx)
+                e1.record(stream)
+                e1.synchronize()
+                t_ms = e0.elapsed_time(e1) / reps
+                o = out.cpu().numpy()[idx].astype(np.float64)
+                extras[meth] = {"matvecs_per_s": 1e3 / t_ms, "ms_per_matvec": t_ms,
+                                "rel_err_max": float(np.max(np.abs(o - ref) / ref)),
+                                "err_vs_sum_w": float(np.max(np.abs(o - ref)) / scale)}
+            except uotk.UotkError as e:
+                extras[meth] = {"error": str(e)}
+    if "nfft" in extras and "direct" in extras and "ms_per_matvec" in extras.get("direct", {}) \
+            and "ms_per_matvec" in extras.get("nfft", {}):
+        extras["nfft_speedup_vs_direct"] = extras["direct"]["ms_per_matvec"] / extras["nfft"]["ms_per_matvec"]
+
+    rate, tgt, dt, cores = cpu_oracle_rate(W, args.cpu_seconds)
+    cpu = {"value": rate / (2.0 * W.n * W.m), "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"FP64 kernel sum of all {W.m} sources onto {tgt} targets ({dt:.1f} s); "
+                     f"sweeps/s extrapolated as pairs/s / (2 n m)"}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"gmm3: n=m={W.n}, d=3, 5-component Gaussian mixture, eps={W.eps}, "
+                               f"rho={W.rho}", "method": args.method,
+                   "sweeps_per_solve": W.sweeps, "step": "one full unbalanced Sinkhorn solve",
+                   "l2": "flushed (512 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof, "peaks": peak_kind,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * W.sweeps / (e2e_ms / 1e3), "unit": UNIT,
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": launches, "clocks": clk,
+        "stages_ms_per_step": {k: v[1] / args.steps for k, v in stages.items()},
+        "sum_forms": extras, "wall_s_timed": t_wall,
+    }
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * uotk.h -- C ABI of the GB300 (sm_103a) kernel-summation library for entropic
+ * unbalanced optimal transport and maximum mean discrepancies
+ * (Lakshmanan & Pichler, arXiv 2306.13618).
+ *
+ * General conventions, valid for every entry point below:
+ *  - Array arguments named as device arrays are DEVICE pointers owned by the
+ *    caller.  The library never frees them and never keeps them past the call.
+ *    Point clouds are row-major FP32 (point i occupies p[i*d .. i*d+d-1]).
+ *    Every device pointer must be 4-byte aligned (8 for FP64 arrays).
+ *  - `stream` is a cudaStream_t (passed as void*); all device work is enqueued
+ *    on it.  Calls that return host scalars synchronise that stream.
+ *  - Scratch memory is owned by the context (uotk_ctx) and grows on demand; a
+ *    context serves one host thread at a time and one device.
+ *  - Every call returns a uotk_status and never aborts, traps or prints.  On
+ *    error, uotk_last_error(ctx) gives a message.  Arguments are validated on
+ *    the host before any launch; data-dependent checks (negative or non-finite
+ *    weights, non-finite coordinates) run on the device and are reported by
+ *    the same call, which then synchronises its stream.
+ *  - Notation: eps is the kernel width of K(x,y) = exp(-||x-y||^2/eps), the
+ *    paper's Gibbs kernel k = exp(-lambda d^2) with lambda = 1/eps (Alg. 1,
+ *    Def. def:526); rho (eta in the paper) is the KL marginal penalty.
+ */
+#ifndef UOTK_H
+#define UOTK_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct uotk_ctx uotk_ctx;
+
+typedef enum {
+  UOTK_OK = 0,
+  UOTK_ERR_INVALID = 1,        /* bad argument (null pointer, size, parameter range) */
+  UOTK_ERR_NOMEM = 2,          /* device or pinned allocation failed */
+  UOTK_ERR_CUDA = 3,           /* a CUDA runtime call failed */
+  UOTK_ERR_UNSUPPORTED = 4,    /* valid request the library does not implement (e.g. NFFT with d > 3) */
+  UOTK_ERR_NONFINITE = 5,      /* NaN/Inf in inputs, or a non-finite dual/result */
+  UOTK_ERR_NOT_CONVERGED = 6,  /* tol > 0 and max_sweeps reached; outputs are valid */
+  UOTK_ERR_TIMEOUT = 7,        /* a bounded device-side wait gave up */
+  UOTK_ERR_INTERNAL = 8
+} uotk_status;
+
+typedef enum { UOTK_DIRECT = 0, UOTK_NFFT = 1 } uotk_method;
+
+/* Reference measure of the entropy term.
+ * PRODUCT : (1/lambda) D(pi || mu (x) nu), the paper's Eq. (W4); the update is
+ *           beta_i = -q log sum_j k_ij nu_j e^{lambda gamma_j}  (Eq. Sinkhorn_uot_iteration).
+ * COUNTING: the counting reference, whose scaling update reads
+ *           u = (a / (K v))^{rho/(rho+eps)},  u = e^{lambda beta}, v = e^{lambda gamma}.
+ * q = rho/(1 + rho*lambda) in both. */
+typedef enum { UOTK_REF_PRODUCT = 0, UOTK_REF_COUNTING = 1 } uotk_ref;
+
+/* Options of one kernel summation.  A NULL pointer means all defaults. */
+typedef struct {
+  int32_t method;      /* uotk_method; default UOTK_DIRECT */
+  int32_t grid;        /* NFFT: oversampled grid size n per dimension, power of two in [16, 256]; 0 = 128 */
+  int32_t bandwidth;   /* NFFT: bandwidth N, even, 4 <= N <= grid; 0 = grid/2 (oversampling sigma = 2) */
+  int32_t cutoff;      /* NFFT: window cut-off m in [2, 8]; 0 = smallest of 6, 7, 8 meeting target_err */
+  double period;       /* NFFT: torus period h; 0 = chosen from the data and eps */
+  double target_err;   /* NFFT: accuracy goal, max error relative to sum|w|; 0 = 1e-6 */
+} uotk_sum_opts;
+
+/* Parameters of an NFFT fast summation as chosen by uotk_nfft_plan (Sec. 4).
+ * Torus coordinates u = (p - center) * inv_h + 1/2, reduced mod 1; grid node l
+ * sits at u = l/grid.  Grids are grid^3 FP32 arrays laid out [z][y][x] (x
+ * fastest), d < 3 being embedded with the missing coordinates at the centre. */
+typedef struct {
+  int32_t d;           /* dimension of the points, 1..3 */
+  int32_t grid;        /* oversampled grid n */
+  int32_t bandwidth;   /* N: Fourier coefficients b_k kept for k in {-N/2..N/2-1}^3 */
+  int32_t cutoff;      /* window cut-off m: each point touches (2m)^3 grid nodes */
+  float center[3];     /* c */
+  float inv_h;         /* 1/h as the FP32 value every kernel uses */
+  double h;            /* torus period */
+  double eps;          /* kernel width the plan was made for */
+} uotk_nfft_plan_info;
+
+/* ---- context ---------------------------------------------------------------- */
+
+/* Create a context on CUDA device `device` (makes it current).  *out receives the
+ * context; release it with uotk_destroy. */
+uotk_status uotk_create(uotk_ctx** out, int device);
+void uotk_destroy(uotk_ctx* ctx);
+/* Message of the last error on this context ("" if none); owned by the context. */
+const char* uotk_last_error(const uotk_ctx* ctx);
+const char* uotk_status_string(int status);
+/* Number of device kernels this context has launched so far (instrumentation). */
+int64_t uotk_launch_count(const uotk_ctx* ctx);
+
+/* Per-stage device timing (instrumentation; the paper reports wall time only).
+ * With profiling enabled, every kernel launch of the library is bracketed by
+ * CUDA events on its stream, grouped by stage name ("direct", "spread",
+ * "fft", "gather", "update", ...).  uotk_profile_read synchronises the device,
+ * writes up to `max` stages (names as a ';'-separated list into names[cap],
+ * launches into counts[], summed milliseconds into ms[]) and returns the
+ * number of stages; uotk_profile_reset clears the totals. */
+uotk_status uotk_set_profiling(uotk_ctx* ctx, int enable);
+int uotk_profile_read(uotk_ctx* ctx, char* names, int cap, int64_t* counts, double* ms, int max);
+void uotk_profile_reset(uotk_ctx* ctx);
+
+/* ---- the kernel summation (Eq. fast_sum; the matrix-vector product of Alg. 1/2) --
+ * out[j] = sum_i w[i] * exp(-||src_i - tgt_j||^2 / eps),  j = 0..m-1.
+ *   src: device FP32 [n*d]; w: device FP32 [n], every w[i] >= 0 and finite;
+ *   tgt: device FP32 [m*d]; out: device FP32 [m] (written, never read).
+ *   d >= 1 (direct form: d <= 128; NFFT: d <= 3).  n >= 0, m >= 0 (n = 0 gives
+ *   zeros).  eps > 0.  opts->method selects the exact direct O(nm) form or the
+ *   NFFT fast summation of Eq. (1724) (spread, FFT, multiply by b_k/phihat^2,
+ *   inverse FFT, gather).  Negative/non-finite weights or non-finite
+ *   coordinates return UOTK_ERR_INVALID / UOTK_ERR_NONFINITE. */
+uotk_status uotk_kernel_sum(uotk_ctx* ctx, void* stream, int d,
+                            const float* src, int64_t n, const float* w,
+                            const float* tgt, int64_t m, float* out,
+                            double eps, const uotk_sum_opts* opts);
+
+/* ---- entropic UOT by Sinkhorn's algorithm (Alg. 1 direct, Alg. 2 NFFT) -------------
+ * Solves Eq. (W4) (r = 2, lambda = 1/eps, eta1 = rho1, eta2 = rho2) through
+ * its dual, Eq. (dual_euot), by the alternating updates of
+ * Eq. (Sinkhorn_uot_iteration): one sweep = the beta half-step followed by the
+ * gamma half-step, each one kernel summation plus an FP64 update.
+ *   x: device FP32 [n*d], a (mu): device FP32 [n] > 0; y: device FP32 [m*d],
+ *   b (nu): device FP32 [m] > 0.  beta: device FP64 [n] (output),
+ *   gamma: device FP64 [m] (input gamma^0 if flags & UOTK_WARM_START, else
+ *   gamma^0 = 0; output gamma^S).
+ *   Runs max_sweeps sweeps; if tol > 0 it stops early once
+ *   max(||lambda (beta^s - beta^{s-1})||_inf, ||lambda (gamma^s - gamma^{s-1})||_inf) < tol,
+ *   tested every 10 sweeps, and returns UOTK_ERR_NOT_CONVERGED (outputs valid)
+ *   if that never happens.
+ *   sweeps_done (host, may be NULL) receives the sweeps run; value (host, may be
+ *   NULL) receives D(beta, gamma) of Eq. (dual_euot) at the final duals (for
+ *   ref = COUNTING the coupling term has no reference-mass constant).
+ *   Synchronises `stream` before returning. */
+#define UOTK_WARM_START 1u
+uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d,
+                              const float* x, int64_t n, const float* a,
+                              const float* y, int64_t m, const float* b,
+                              double eps, double rho1, double rho2,
+                              int max_sweeps, double tol, int ref, unsigned flags,
+                              double* beta, double* gamma, int* sweeps_done,
+                              double* value, const uotk_sum_opts* opts);
+
+/* ---- unbalanced Sinkhorn divergence, Eq. (586) ---------------------------------------
+ * sd = UOT(mu,nu) - UOT(mu,mu)/2 - UOT(nu,nu)/2 + (mu(X) - nu(X))^2 * eps/2,
+ * each UOT value being D(beta, gamma) after max_sweeps sweeps (or tol, as
+ * above) from gamma^0 = 0, product reference, rho1 = rho2 = rho.
+ *   sd (host) receives the divergence; parts (host double[3], may be NULL)
+ *   receives the three UOT values.  Synchronises `stream`. */
+uotk_status uotk_sinkhorn_divergence(uotk_ctx* ctx, void* stream, int d,
+                                     const float* x, int64_t n, const float* a,
+                                     const float* y, int64_t m, const float* b,
+                                     double eps, double rho, int max_sweeps, double tol,
+                                     double* sd, double* parts, const uotk_sum_opts* opts);
+
+/* ---- MMD^2, Eq. (1205), Gaussian kernel k(x,y) = exp(-||x-y||^2/ell^2) (Table tab:0) --
+ * mmd2 = sum_ij a_i a_j k(x_i,x_j) - 2 sum_ij a_i b_j k(x_i,y_j) + sum_ij b_i b_j k(y_i,y_j),
+ * three kernel summations (eps = ell^2) and FP64 dot products.
+ *   a, b >= 0.  mmd2 (host) receives the value; parts (host double[3], may be
+ *   NULL) receives the three double sums.  Synchronises `stream`. */
+uotk_status uotk_mmd2(uotk_ctx* ctx, void* stream, int d,
+                      const float* x, int64_t n, const float* a,
+                      const float* y, int64_t m, const float* b,
+                      double ell, double* mmd2, double* parts, const uotk_sum_opts* opts);
+
+/* ---- NFFT stages (Sec. 4), exposed for inspection and testing ---------------------
+ * uotk_nfft_plan: choose centre, period h, grid, bandwidth and cut-off for
+ *   summing from src to tgt with kernel width eps (opts as for
+ *   uotk_kernel_sum; method ignored).  Reads the point clouds on the device
+ *   (bounding box) and synchronises `stream`.  d in 1..3.
+ * uotk_nfft_cells: grid cell of every point, cells = device int32 [n*3]
+ *   (x, y, z per point), by the FP32 rule
+ *   cell = floor(((p - c) * inv_h + 0.5f) * grid) mod grid, one IEEE rounding
+ *   per operation.
+ * uotk_nfft_spread: adjoint-NFFT step 1, g_l = sum_i w_i prod_t phi(u_it - l_t/n)
+ *   into grid (device FP32 [grid^3], overwritten).
+ * uotk_nfft_convolve: grid_out = IFFT( scale_k * FFT(grid_in) ), with
+ *   scale_k = b_k / prod_t (n phihat(k_t))^2 on {-N/2..N/2-1}^3 and 0 elsewhere;
+ *   forward and inverse FFT unnormalised.  grid_in and grid_out may alias.
+ * uotk_nfft_gather: out_j = sum_l grid_l prod_t phi(u_jt - l_t/n), out = device FP32 [m]. */
+uotk_status uotk_nfft_plan(uotk_ctx* ctx, void* stream, int d,
+                           const float* src, int64_t n, const float* tgt, int64_t m,
+                           double eps, const uotk_sum_opts* opts, uotk_nfft_plan_info* plan);
+uotk_status uotk_nfft_cells(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                            const float* pts, int64_t n, int32_t* cells);
+uotk_status uotk_nfft_spread(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                             const float* pts, int64_t n, const float* w, float* grid);
+uotk_status uotk_nfft_convolve(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                               const float* grid_in, float* grid_out);
+uotk_status uotk_nfft_gather(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                             const float* grid, const float* pts, int64_t m, float* out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* UOTK_H */

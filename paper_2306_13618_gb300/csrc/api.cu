@@ -1,0 +1,406 @@
+// Exported C ABI (include/uotk.h): context management, host-side argument
+// validation, and dispatch to the operations.
+#include <math.h>
+#include <stdarg.h>
+#include <stdlib.h>
+
+#include <new>
+
+#include "engine.cuh"
+
+namespace uotk {
+
+uotk_status op_kernel_sum(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
+                          const float*, int64_t, float*, double, const uotk_sum_opts*);
+uotk_status op_uot_sinkhorn(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
+                            const float*, int64_t, const float*, double, double, double, int,
+                            double, int, unsigned, double*, double*, int*, double*,
+                            const uotk_sum_opts*);
+uotk_status op_sinkhorn_divergence(uotk_ctx*, cudaStream_t, int, const float*, int64_t,
+                                   const float*, const float*, int64_t, const float*, double,
+                                   double, int, double, double*, double*, const uotk_sum_opts*);
+uotk_status op_mmd2(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
+                    const float*, int64_t, const float*, double, double*, double*,
+                    const uotk_sum_opts*);
+uotk_status op_nfft_plan(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
+                         int64_t, double, const uotk_sum_opts*, uotk_nfft_plan_info*);
+uotk_status op_nfft_cells(uotk_ctx*, cudaStream_t, const uotk_nfft_plan_info*, const float*,
+                          int64_t, int32_t*);
+uotk_status op_nfft_spread(uotk_ctx*, cudaStream_t, const uotk_nfft_plan_info*, const float*,
+                           int64_t, const float*, float*);
+uotk_status op_nfft_convolve(uotk_ctx*, cudaStream_t, const uotk_nfft_plan_info*, const float*,
+                             float*);
+uotk_status op_nfft_gather(uotk_ctx*, cudaStream_t, const uotk_nfft_plan_info*, const float*,
+                           const float*, int64_t, float*);
+
+uotk_status set_error(uotk_ctx* ctx, uotk_status st, const char* fmt, ...) {
+  if (ctx) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(ctx->err, sizeof(ctx->err), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+uotk_status ws_reserve(uotk_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->ws_cap) return UOTK_OK;
+  size_t want = bytes + bytes / 8 + (1 << 20);
+  if (ctx->ws) {
+    UOTK_CUDA(ctx, cudaDeviceSynchronize());
+    cudaFree(ctx->ws);
+    ctx->ws = nullptr;
+    ctx->ws_cap = 0;
+  }
+  if (cudaMalloc(&ctx->ws, want) != cudaSuccess) {
+    cudaGetLastError();
+    ctx->ws = nullptr;
+    return set_error(ctx, UOTK_ERR_NOMEM, "workspace allocation of %zu bytes failed", want);
+  }
+  ctx->ws_cap = want;
+  return UOTK_OK;
+}
+
+static void prof_fold(uotk_ctx* ctx) {
+  uotk_prof& P = ctx->prof;
+  if (!P.pending) return;
+  cudaEventSynchronize(P.ev[2 * (P.pending - 1) + 1]);
+  for (int i = 0; i < P.pending; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, P.ev[2 * i], P.ev[2 * i + 1]) == cudaSuccess) {
+      P.ms[P.stage_of[i]] += ms;
+      P.counts[P.stage_of[i]]++;
+    }
+  }
+  cudaGetLastError();
+  P.pending = 0;
+}
+
+int prof_begin(uotk_ctx* ctx, cudaStream_t s, const char* name) {
+  uotk_prof& P = ctx->prof;
+  if (!P.created) return -1;
+  if (P.pending == UOTK_PROF_POOL) prof_fold(ctx);
+  int st = -1;
+  for (int i = 0; i < P.nstages; ++i)
+    if (!strncmp(P.names[i], name, sizeof(P.names[i]) - 1)) { st = i; break; }
+  if (st < 0) {
+    if (P.nstages == UOTK_PROF_STAGES) return -1;
+    st = P.nstages++;
+    strncpy(P.names[st], name, sizeof(P.names[st]) - 1);
+  }
+  const int slot = P.pending;
+  P.stage_of[slot] = st;
+  cudaEventRecord(P.ev[2 * slot], s);
+  return slot;
+}
+
+void prof_end(uotk_ctx* ctx, cudaStream_t s, int slot) {
+  uotk_prof& P = ctx->prof;
+  cudaEventRecord(P.ev[2 * slot + 1], s);
+  P.pending = slot + 1;
+}
+
+}  // namespace uotk
+
+using namespace uotk;
+
+namespace {
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+uotk_status check_cloud(uotk_ctx* ctx, const char* what, const float* p, int64_t n, int d) {
+  if (n < 0) return set_error(ctx, UOTK_ERR_INVALID, "%s: negative size %lld", what, (long long)n);
+  if (n > 0 && !p) return set_error(ctx, UOTK_ERR_INVALID, "%s: null pointer", what);
+  if (p && !aligned(p, 4)) return set_error(ctx, UOTK_ERR_INVALID, "%s: not 4-byte aligned", what);
+  if (n > (int64_t(1) << 31) - (int64_t(1) << 20))
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED, "%s: %lld points exceed the supported 2^31 - 2^20",
+                     what, (long long)n);
+  (void)d;
+  return UOTK_OK;
+}
+
+uotk_status check_common(uotk_ctx* ctx, int d, const uotk_sum_opts* opts) {
+  if (d < 1) return set_error(ctx, UOTK_ERR_INVALID, "dimension d = %d < 1", d);
+  const int method = opts ? opts->method : UOTK_DIRECT;
+  if (method != UOTK_DIRECT && method != UOTK_NFFT)
+    return set_error(ctx, UOTK_ERR_INVALID, "unknown method %d", method);
+  if (method == UOTK_DIRECT && d > 128)
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED, "direct form: d = %d > 128", d);
+  if (method == UOTK_NFFT) {
+    if (d > 3)
+      return set_error(ctx, UOTK_ERR_UNSUPPORTED,
+                       "NFFT fast summation is limited to d <= 3 (grid grows like N^d), got d = %d", d);
+    const int g = opts->grid ? opts->grid : 128;
+    if (g < 16 || g > 256 || (g & (g - 1)))
+      return set_error(ctx, UOTK_ERR_INVALID, "NFFT grid %d not a power of two in [16, 256]", g);
+    const int N = opts->bandwidth ? opts->bandwidth : g / 2;
+    if (N < 4 || N > g || (N & 1))
+      return set_error(ctx, UOTK_ERR_INVALID, "NFFT bandwidth %d not even in [4, grid]", N);
+    if (opts->cutoff && (opts->cutoff < 2 || opts->cutoff > 8))
+      return set_error(ctx, UOTK_ERR_INVALID, "NFFT cut-off %d outside [2, 8]", opts->cutoff);
+    if (!(opts->period >= 0.0) || !(opts->target_err >= 0.0))
+      return set_error(ctx, UOTK_ERR_INVALID, "NFFT period/target_err must be >= 0");
+  }
+  return UOTK_OK;
+}
+
+uotk_status enter(uotk_ctx* ctx) {
+  if (!ctx) return UOTK_ERR_INVALID;
+  ctx->err[0] = 0;
+  UOTK_CUDA(ctx, cudaSetDevice(ctx->device));
+  return UOTK_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+uotk_status uotk_create(uotk_ctx** out, int device) {
+  if (!out) return UOTK_ERR_INVALID;
+  *out = nullptr;
+  uotk_ctx* ctx = new (std::nothrow) uotk_ctx();
+  if (!ctx) return UOTK_ERR_NOMEM;
+  ctx->device = device;
+  int count = 0;
+  if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+    cudaGetLastError();
+    delete ctx;
+    return UOTK_ERR_CUDA;
+  }
+  if (cudaSetDevice(device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&ctx->max_smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin,
+                             device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return UOTK_ERR_CUDA;
+  }
+  if (cudaMallocHost(reinterpret_cast<void**>(&ctx->host), 64 * sizeof(double)) != cudaSuccess ||
+      cudaMalloc(reinterpret_cast<void**>(&ctx->dflags), NUM_FLAGS * sizeof(long long)) !=
+          cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->host) cudaFreeHost(ctx->host);
+    delete ctx;
+    return UOTK_ERR_NOMEM;
+  }
+  cudaMemset(ctx->dflags, 0, NUM_FLAGS * sizeof(long long));
+  cudaDeviceSynchronize();
+  *out = ctx;
+  return UOTK_OK;
+}
+
+void uotk_destroy(uotk_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->ws) cudaFree(ctx->ws);
+  if (ctx->dflags) cudaFree(ctx->dflags);
+  if (ctx->host) cudaFreeHost(ctx->host);
+  if (ctx->prof.created)
+    for (int i = 0; i < 2 * UOTK_PROF_POOL; ++i) cudaEventDestroy(ctx->prof.ev[i]);
+  delete ctx;
+}
+
+const char* uotk_last_error(const uotk_ctx* ctx) { return ctx ? ctx->err : "null context"; }
+
+const char* uotk_status_string(int st) {
+  switch (st) {
+    case UOTK_OK: return "ok";
+    case UOTK_ERR_INVALID: return "invalid argument";
+    case UOTK_ERR_NOMEM: return "out of memory";
+    case UOTK_ERR_CUDA: return "CUDA error";
+    case UOTK_ERR_UNSUPPORTED: return "unsupported";
+    case UOTK_ERR_NONFINITE: return "non-finite value";
+    case UOTK_ERR_NOT_CONVERGED: return "not converged";
+    case UOTK_ERR_TIMEOUT: return "device wait timed out";
+    case UOTK_ERR_INTERNAL: return "internal error";
+    default: return "unknown status";
+  }
+}
+
+int64_t uotk_launch_count(const uotk_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+uotk_status uotk_set_profiling(uotk_ctx* ctx, int enable) {
+  UOTK_TRY(enter(ctx));
+  uotk_prof& P = ctx->prof;
+  if (enable && !P.created) {
+    for (int i = 0; i < 2 * UOTK_PROF_POOL; ++i)
+      UOTK_CUDA(ctx, cudaEventCreate(&P.ev[i]));
+    P.created = true;
+  }
+  if (!enable) prof_fold(ctx);
+  P.on = enable != 0;
+  return UOTK_OK;
+}
+
+int uotk_profile_read(uotk_ctx* ctx, char* names, int cap, int64_t* counts, double* ms, int max) {
+  if (!ctx) return 0;
+  cudaSetDevice(ctx->device);
+  prof_fold(ctx);
+  uotk_prof& P = ctx->prof;
+  int k = P.nstages < max ? P.nstages : max;
+  if (names && cap > 0) {
+    names[0] = 0;
+    int used = 0;
+    for (int i = 0; i < k; ++i) {
+      int w = snprintf(names + used, cap - used, i ? ";%s" : "%s", P.names[i]);
+      if (w < 0 || used + w >= cap) break;
+      used += w;
+    }
+  }
+  for (int i = 0; i < k; ++i) {
+    if (counts) counts[i] = P.counts[i];
+    if (ms) ms[i] = P.ms[i];
+  }
+  return k;
+}
+
+void uotk_profile_reset(uotk_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  prof_fold(ctx);
+  for (int i = 0; i < UOTK_PROF_STAGES; ++i) { ctx->prof.counts[i] = 0; ctx->prof.ms[i] = 0; }
+}
+
+uotk_status uotk_kernel_sum(uotk_ctx* ctx, void* stream, int d, const float* src, int64_t n,
+                            const float* w, const float* tgt, int64_t m, float* out, double eps,
+                            const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_cloud(ctx, "src", src, n, d));
+  UOTK_TRY(check_cloud(ctx, "w", w, n, 1));
+  UOTK_TRY(check_cloud(ctx, "tgt", tgt, m, d));
+  UOTK_TRY(check_cloud(ctx, "out", out, m, 1));
+  if (!(eps > 0.0) || !isfinite(eps))
+    return set_error(ctx, UOTK_ERR_INVALID, "eps must be finite and > 0, got %g", eps);
+  if (m == 0) return UOTK_OK;
+  return op_kernel_sum(ctx, (cudaStream_t)stream, d, src, n, w, tgt, m, out, eps, opts);
+}
+
+uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
+                              const float* a, const float* y, int64_t m, const float* b,
+                              double eps, double rho1, double rho2, int max_sweeps, double tol,
+                              int ref, unsigned flags, double* beta, double* gamma,
+                              int* sweeps_done, double* value, const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_cloud(ctx, "x", x, n, d));
+  UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
+  UOTK_TRY(check_cloud(ctx, "y", y, m, d));
+  UOTK_TRY(check_cloud(ctx, "b", b, m, 1));
+  if (n < 1 || m < 1)
+    return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn needs n >= 1 and m >= 1");
+  if (!beta || !gamma || !aligned(beta, 8) || !aligned(gamma, 8))
+    return set_error(ctx, UOTK_ERR_INVALID, "beta/gamma must be 8-byte aligned device arrays");
+  if (!(eps > 0.0) || !isfinite(eps) || !(rho1 > 0.0) || !(rho2 > 0.0) || !isfinite(rho1) ||
+      !isfinite(rho2))
+    return set_error(ctx, UOTK_ERR_INVALID, "eps, rho1, rho2 must be finite and > 0");
+  if (max_sweeps < 1) return set_error(ctx, UOTK_ERR_INVALID, "max_sweeps must be >= 1");
+  if (ref != UOTK_REF_PRODUCT && ref != UOTK_REF_COUNTING)
+    return set_error(ctx, UOTK_ERR_INVALID, "unknown reference measure %d", ref);
+  if (!(tol >= 0.0) && !(tol <= 0.0)) return set_error(ctx, UOTK_ERR_INVALID, "tol is NaN");
+  return op_uot_sinkhorn(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2,
+                         max_sweeps, tol, ref, flags, beta, gamma, sweeps_done, value, opts);
+}
+
+uotk_status uotk_sinkhorn_divergence(uotk_ctx* ctx, void* stream, int d, const float* x,
+                                     int64_t n, const float* a, const float* y, int64_t m,
+                                     const float* b, double eps, double rho, int max_sweeps,
+                                     double tol, double* sd, double* parts,
+                                     const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_cloud(ctx, "x", x, n, d));
+  UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
+  UOTK_TRY(check_cloud(ctx, "y", y, m, d));
+  UOTK_TRY(check_cloud(ctx, "b", b, m, 1));
+  if (n < 1 || m < 1)
+    return set_error(ctx, UOTK_ERR_INVALID, "sinkhorn_divergence needs n >= 1 and m >= 1");
+  if (!sd) return set_error(ctx, UOTK_ERR_INVALID, "sd is null");
+  if (!(eps > 0.0) || !isfinite(eps) || !(rho > 0.0) || !isfinite(rho))
+    return set_error(ctx, UOTK_ERR_INVALID, "eps and rho must be finite and > 0");
+  if (max_sweeps < 1) return set_error(ctx, UOTK_ERR_INVALID, "max_sweeps must be >= 1");
+  return op_sinkhorn_divergence(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho,
+                                max_sweeps, tol, sd, parts, opts);
+}
+
+uotk_status uotk_mmd2(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
+                      const float* a, const float* y, int64_t m, const float* b, double ell,
+                      double* mmd2, double* parts, const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_cloud(ctx, "x", x, n, d));
+  UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
+  UOTK_TRY(check_cloud(ctx, "y", y, m, d));
+  UOTK_TRY(check_cloud(ctx, "b", b, m, 1));
+  if (n < 1 || m < 1) return set_error(ctx, UOTK_ERR_INVALID, "mmd2 needs n >= 1 and m >= 1");
+  if (!mmd2) return set_error(ctx, UOTK_ERR_INVALID, "mmd2 is null");
+  if (!(ell > 0.0) || !isfinite(ell))
+    return set_error(ctx, UOTK_ERR_INVALID, "ell must be finite and > 0");
+  return op_mmd2(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, ell, mmd2, parts, opts);
+}
+
+uotk_status uotk_nfft_plan(uotk_ctx* ctx, void* stream, int d, const float* src, int64_t n,
+                           const float* tgt, int64_t m, double eps, const uotk_sum_opts* opts,
+                           uotk_nfft_plan_info* plan) {
+  UOTK_TRY(enter(ctx));
+  uotk_sum_opts o = opts ? *opts : uotk_sum_opts{};
+  o.method = UOTK_NFFT;
+  UOTK_TRY(check_common(ctx, d, &o));
+  UOTK_TRY(check_cloud(ctx, "src", src, n, d));
+  UOTK_TRY(check_cloud(ctx, "tgt", tgt, m, d));
+  if (!plan) return set_error(ctx, UOTK_ERR_INVALID, "plan is null");
+  if (!(eps > 0.0) || !isfinite(eps))
+    return set_error(ctx, UOTK_ERR_INVALID, "eps must be finite and > 0");
+  return op_nfft_plan(ctx, (cudaStream_t)stream, d, src, n, tgt, m, eps, &o, plan);
+}
+
+static uotk_status check_plan(uotk_ctx* ctx, const uotk_nfft_plan_info* p) {
+  if (!p) return set_error(ctx, UOTK_ERR_INVALID, "plan is null");
+  if (p->d < 1 || p->d > 3 || p->grid < 16 || p->grid > 256 || (p->grid & (p->grid - 1)) ||
+      p->bandwidth < 4 || p->bandwidth > p->grid || (p->bandwidth & 1) || p->cutoff < 2 ||
+      p->cutoff > 8 || 2 * p->cutoff > p->grid || !(p->h > 0.0) || !(p->inv_h > 0.f) ||
+      !(p->eps > 0.0))
+    return set_error(ctx, UOTK_ERR_INVALID, "inconsistent NFFT plan");
+  return UOTK_OK;
+}
+
+uotk_status uotk_nfft_cells(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                            const float* pts, int64_t n, int32_t* cells) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_plan(ctx, plan));
+  UOTK_TRY(check_cloud(ctx, "pts", pts, n, plan->d));
+  if (n > 0 && !cells) return set_error(ctx, UOTK_ERR_INVALID, "cells is null");
+  return op_nfft_cells(ctx, (cudaStream_t)stream, plan, pts, n, cells);
+}
+
+uotk_status uotk_nfft_spread(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                             const float* pts, int64_t n, const float* w, float* grid) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_plan(ctx, plan));
+  UOTK_TRY(check_cloud(ctx, "pts", pts, n, plan->d));
+  UOTK_TRY(check_cloud(ctx, "w", w, n, 1));
+  if (!grid || !aligned(grid, 16)) return set_error(ctx, UOTK_ERR_INVALID, "grid null or unaligned");
+  return op_nfft_spread(ctx, (cudaStream_t)stream, plan, pts, n, w, grid);
+}
+
+uotk_status uotk_nfft_convolve(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                               const float* grid_in, float* grid_out) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_plan(ctx, plan));
+  if (!grid_in || !grid_out || !aligned(grid_in, 16) || !aligned(grid_out, 16))
+    return set_error(ctx, UOTK_ERR_INVALID, "grid null or unaligned");
+  return op_nfft_convolve(ctx, (cudaStream_t)stream, plan, grid_in, grid_out);
+}
+
+uotk_status uotk_nfft_gather(uotk_ctx* ctx, void* stream, const uotk_nfft_plan_info* plan,
+                             const float* grid, const float* pts, int64_t m, float* out) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_plan(ctx, plan));
+  UOTK_TRY(check_cloud(ctx, "pts", pts, m, plan->d));
+  UOTK_TRY(check_cloud(ctx, "out", out, m, 1));
+  if (!grid || !aligned(grid, 16)) return set_error(ctx, UOTK_ERR_INVALID, "grid null or unaligned");
+  return op_nfft_gather(ctx, (cudaStream_t)stream, plan, grid, pts, m, out);
+}
+
+}  // extern "C"

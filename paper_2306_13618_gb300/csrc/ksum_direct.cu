@@ -1,0 +1,390 @@
+// Exact direct kernel summation, the matrix-vector product of Alg. 1 without
+// ever forming the Gibbs matrix k_ij = exp(-||x_i - y_j||^2/eps):
+//
+//   out_j = sum_i w_i * 2^{-c ||s_i - t_j||^2},   c = log2(e)/eps.
+//
+// Design (d <= 3): sources packed as float4 (x, y, z, w); each CTA keeps
+// DIRECT_THREADS*R targets in registers and streams source tiles of
+// DIRECT_TILE float4 through shared memory with 1-D bulk copies (TMA,
+// cp.async.bulk) completing on mbarriers.  Every thread reads a source with one
+// broadcast shared load and evaluates R pairs: 3 FADD + 1 FMUL + 2 FFMA for the
+// squared distance in unscaled coordinates (x - y is exact to half an ulp of
+// the difference), 1 FMUL by -c, one MUFU ex2, 1 FFMA into the accumulator.
+// FP32 partial sums over 32 sources are folded into a Neumaier-compensated
+// (hi, lo) pair.  Sources are split across blockIdx.y when there are too few
+// target blocks to fill the GPU; split partials are added in FP64 in a fixed
+// order, so the result is deterministic.
+#include "uotk_internal.cuh"
+
+namespace uotk {
+
+namespace {
+
+constexpr int STAGES = 3;
+constexpr int GEN_TILE = 64;  // sources per tile on the general-d path
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+// One 1-D bulk copy global -> shared that completes `bytes` on `bar`.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+               "r"(bytes)
+               : "memory");
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+// Bounded wait for phase `parity` of `bar`: gives up after ~2^31 clocks (~1 s).
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+  const unsigned a = smem_addr(bar);
+  const long long t0 = clock64();
+  while (true) {
+    unsigned done;
+    asm volatile(
+        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
+        : "=r"(done)
+        : "r"(a), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > (1LL << 31)) return false;
+  }
+}
+
+__device__ __forceinline__ void neumaier(float& hi, float& lo, float v) {
+  const float t = hi + v;
+  lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
+  hi = t;
+}
+
+template <int D, int R>
+__global__ void __launch_bounds__(DIRECT_THREADS)
+    k_direct_small(const float4* __restrict__ src, long long tiles, int tiles_per_split,
+                   const float4* __restrict__ tgt, long long m, float neg_c,
+                   float* __restrict__ out, long long* __restrict__ flags) {
+  __shared__ __align__(128) float4 sm[STAGES][DIRECT_TILE];
+  __shared__ __align__(8) unsigned long long bar[STAGES];
+  const int tid = threadIdx.x;
+  const long long tb = (long long)blockIdx.x * (DIRECT_THREADS * R) + tid;
+
+  float tx[R], ty[R], tz[R], hi[R], lo[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long j = tb + (long long)r * DIRECT_THREADS;
+    const float4 p = j < m ? tgt[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    tx[r] = p.x; ty[r] = p.y; tz[r] = p.z;
+    hi[r] = 0.f; lo[r] = 0.f;
+  }
+
+  const long long t_begin = (long long)blockIdx.y * tiles_per_split;
+  const long long t_end = min(t_begin + (long long)tiles_per_split, tiles);
+  const int count = t_end > t_begin ? (int)(t_end - t_begin) : 0;
+  constexpr unsigned BYTES = DIRECT_TILE * sizeof(float4);
+
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < STAGES && s < count; ++s)
+      bulk_load(sm[s], src + (t_begin + s) * DIRECT_TILE, BYTES, &bar[s]);
+  }
+
+  for (int k = 0; k < count; ++k) {
+    const int s = k % STAGES;
+    const bool ok = mbar_wait(&bar[s], (unsigned)(k / STAGES) & 1u);
+    if (__syncthreads_or(!ok)) {
+      // A copy never completed: record it, wait (bounded) for the copies this
+      // CTA still has in flight so none lands after exit, and leave.
+      if (tid == 0) {
+        flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        for (int q = k; q < count && q < k + STAGES; ++q)
+          mbar_wait(&bar[q % STAGES], (unsigned)(q / STAGES) & 1u);
+      }
+      return;
+    }
+    const float4* T = sm[s];
+#pragma unroll 1
+    for (int j0 = 0; j0 < DIRECT_TILE; j0 += 32) {
+      float acc[R];
+#pragma unroll
+      for (int r = 0; r < R; ++r) acc[r] = 0.f;
+#pragma unroll 8
+      for (int j = j0; j < j0 + 32; ++j) {
+        const float4 q = T[j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float dx = tx[r] - q.x;
+          float r2 = dx * dx;
+          if (D > 1) { const float dy = ty[r] - q.y; r2 = fmaf(dy, dy, r2); }
+          if (D > 2) { const float dz = tz[r] - q.z; r2 = fmaf(dz, dz, r2); }
+          acc[r] = fmaf(q.w, ex2_approx(r2 * neg_c), acc[r]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r) neumaier(hi[r], lo[r], acc[r]);
+    }
+    __syncthreads();
+    if (tid == 0 && k + STAGES < count)
+      bulk_load(sm[s], src + (t_begin + k + STAGES) * DIRECT_TILE, BYTES, &bar[s]);
+  }
+
+  float* o = out + (long long)blockIdx.y * m;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long j = tb + (long long)r * DIRECT_THREADS;
+    if (j < m) o[j] = hi[r] + lo[r];
+  }
+}
+
+// General dimension: packed points of dp floats (coordinates, zeros, weight last).
+template <int DMAX>
+__global__ void __launch_bounds__(DIRECT_THREADS)
+    k_direct_general(const float* __restrict__ src, long long tiles, int tiles_per_split,
+                     const float* __restrict__ tgt, long long m, int d, int dp, float neg_c,
+                     float* __restrict__ out) {
+  extern __shared__ float gs[];  // [GEN_TILE][dp]
+  const int tid = threadIdx.x;
+  const long long j = (long long)blockIdx.x * DIRECT_THREADS + tid;
+  float tc[DMAX];
+#pragma unroll
+  for (int t = 0; t < DMAX; ++t) tc[t] = (j < m && t < d) ? tgt[j * dp + t] : 0.f;
+  const long long t_begin = (long long)blockIdx.y * tiles_per_split;
+  const long long t_end = min(t_begin + (long long)tiles_per_split, tiles);
+  float hi = 0.f, lo = 0.f;
+  for (long long tile = t_begin; tile < t_end; ++tile) {
+    __syncthreads();
+    const float* g = src + tile * GEN_TILE * dp;
+    for (int q = tid; q < GEN_TILE * dp; q += DIRECT_THREADS) gs[q] = g[q];
+    __syncthreads();
+    for (int i0 = 0; i0 < GEN_TILE; i0 += 32) {
+      float acc = 0.f;
+      for (int i = i0; i < i0 + 32; ++i) {
+        const float* p = gs + i * dp;
+        float r2 = 0.f;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t)
+          if (t < d) { const float u = tc[t] - p[t]; r2 = fmaf(u, u, r2); }
+        acc = fmaf(p[dp - 1], ex2_approx(r2 * neg_c), acc);
+      }
+      neumaier(hi, lo, acc);
+    }
+  }
+  if (j < m) out[(long long)blockIdx.y * m + j] = hi + lo;
+}
+
+__global__ void k_reduce_splits(const float* __restrict__ part, int splits, long long m,
+                                float* __restrict__ out) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < m;
+       j += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += (double)part[(long long)k * m + j];
+    out[j] = (float)s;
+  }
+}
+
+__device__ __forceinline__ void count_flags(long long* flags, bool neg, bool nonfinite) {
+  const unsigned bn = __ballot_sync(0xffffffffu, neg);
+  const unsigned bf = __ballot_sync(0xffffffffu, nonfinite);
+  if ((threadIdx.x & 31) == 0) {
+    if (bn) flag_add(&flags[FLAG_NEG_WEIGHT], (long long)__popc(bn));
+    if (bf) flag_add(&flags[FLAG_NONFINITE], (long long)__popc(bf));
+  }
+}
+
+// Sources: float4 (x, y, z, w) for d <= 3, or dp floats; rows >= n are zero.
+__global__ void k_pack(const float* __restrict__ pts, const float* __restrict__ w, long long n,
+                       long long n_pad, int d, int dp, int small, void* __restrict__ packed,
+                       long long* __restrict__ flags) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  // every lane of a warp runs the same number of iterations (for the ballots)
+  const long long iters = (n_pad + stride - 1) / stride;
+  for (long long it = 0; it < iters; ++it) {
+    const long long i = start + it * stride;
+    bool neg = false, bad = false;
+    if (i < n_pad) {
+      if (small) {
+        float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (i < n) {
+          p.x = pts[i * d];
+          if (d > 1) p.y = pts[i * d + 1];
+          if (d > 2) p.z = pts[i * d + 2];
+          p.w = w ? w[i] : 0.f;
+          bad = !isfinite(p.x) || !isfinite(p.y) || !isfinite(p.z) || !isfinite(p.w);
+          neg = p.w < 0.f;
+        }
+        reinterpret_cast<float4*>(packed)[i] = p;
+      } else {
+        float* o = reinterpret_cast<float*>(packed) + i * dp;
+        for (int t = 0; t < dp; ++t) {
+          float v = 0.f;
+          if (i < n) {
+            if (t < d) v = pts[i * d + t];
+            else if (t == dp - 1 && w) v = w[i];
+            bad |= !isfinite(v);
+          }
+          o[t] = v;
+        }
+        if (i < n && w) neg = w[i] < 0.f;
+      }
+    }
+    count_flags(flags, neg, bad);
+  }
+}
+
+__global__ void k_set_weights(void* __restrict__ packed, long long n, int small, int dp,
+                              const float* __restrict__ base, const double* __restrict__ pot,
+                              double lam, const long long* __restrict__ shift_slot) {
+  const double shift = ordered_to_dbl(*shift_slot);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    double v = exp(lam * pot[i] - shift);
+    if (base) v *= (double)base[i];
+    if (small) reinterpret_cast<float4*>(packed)[i].w = (float)v;
+    else reinterpret_cast<float*>(packed)[i * dp + dp - 1] = (float)v;
+  }
+}
+
+}  // namespace
+
+int grid_for(const uotk_ctx* ctx, int64_t work, int threads, int per_sm) {
+  const int64_t want = (work + threads - 1) / threads;
+  const int64_t cap = (int64_t)ctx->num_sms * per_sm;
+  return (int)(want < 1 ? 1 : (want < cap ? want : cap));
+}
+
+DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m) {
+  DirectLayout L;
+  L.d = d;
+  L.n = n;
+  L.m = m;
+  const bool small = d <= 3;
+  const int tile = small ? DIRECT_TILE : GEN_TILE;
+  L.reg_targets = (small && m >= 4 * DIRECT_THREADS * (int64_t)ctx->num_sms) ? 4 : 1;
+  L.blocks_x = (int)((m + (int64_t)DIRECT_THREADS * L.reg_targets - 1) /
+                     ((int64_t)DIRECT_THREADS * L.reg_targets));
+  if (L.blocks_x < 1) L.blocks_x = 1;
+  L.tiles = (n + tile - 1) / tile;
+  const int64_t want = 32LL * ctx->num_sms;  // ~8 waves of 4 resident CTAs per SM
+  int64_t splits = (want + L.blocks_x - 1) / L.blocks_x;
+  int64_t max_splits = L.tiles / 2 > 0 ? L.tiles / 2 : 1;
+  if (splits > max_splits) splits = max_splits;
+  if (splits > 65535) splits = 65535;
+  if (splits < 1) splits = 1;
+  L.tiles_per_split = (int)((L.tiles + splits - 1) / splits);
+  if (L.tiles_per_split < 1) L.tiles_per_split = 1;
+  L.splits = (int)((L.tiles + L.tiles_per_split - 1) / L.tiles_per_split);
+  if (L.splits < 1) L.splits = 1;
+  L.dp = small ? 4 : ((d + 1 + 3) / 4) * 4;
+  const int64_t n_pad = L.tiles * tile;
+  L.src_bytes = (size_t)n_pad * L.dp * sizeof(float);
+  L.tgt_bytes = (size_t)(m > 0 ? m : 1) * L.dp * sizeof(float);
+  L.part_bytes = L.splits > 1 ? (size_t)L.splits * m * sizeof(float) : 0;
+  return L;
+}
+
+void direct_carve(Carver& cv, const DirectLayout& L, DirectBufs& b) {
+  b.src = cv.take<char>(L.src_bytes > 0 ? L.src_bytes : 16);
+  b.tgt = cv.take<char>(L.tgt_bytes);
+  b.part = L.part_bytes ? cv.take<float>(L.part_bytes / sizeof(float)) : nullptr;
+}
+
+uotk_status direct_pack_sources(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                                const float* pts, const float* w, void* packed) {
+  const int tile = L.d <= 3 ? DIRECT_TILE : GEN_TILE;
+  const int64_t n_pad = L.tiles * tile;
+  if (n_pad == 0) return UOTK_OK;
+  UOTK_PROF(ctx, s, "pack");
+  k_pack<<<grid_for(ctx, n_pad, 256), 256, 0, s>>>(pts, w, L.n, n_pad, L.d, L.dp, L.d <= 3,
+                                                   packed, ctx->dflags);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+uotk_status direct_pack_targets(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                                const float* pts, void* packed) {
+  if (L.m == 0) return UOTK_OK;
+  UOTK_PROF(ctx, s, "pack");
+  k_pack<<<grid_for(ctx, L.m, 256), 256, 0, s>>>(pts, nullptr, L.m, L.m, L.d, L.dp, L.d <= 3,
+                                                 packed, ctx->dflags);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+uotk_status direct_set_weights(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                               void* packed, const float* base, const double* pot, double lam,
+                               const long long* shift_slot) {
+  if (L.n == 0) return UOTK_OK;
+  UOTK_PROF(ctx, s, "weights");
+  k_set_weights<<<grid_for(ctx, L.n, 256), 256, 0, s>>>(packed, L.n, L.d <= 3, L.dp, base, pot,
+                                                        lam, shift_slot);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, const DirectBufs& b,
+                       double eps, float* out) {
+  if (L.m == 0) return UOTK_OK;
+  if (L.n == 0) {
+    UOTK_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(float) * L.m, s));
+    return UOTK_OK;
+  }
+  const float neg_c = (float)(-1.4426950408889634 / eps);
+  float* dst = L.splits > 1 ? b.part : out;
+  const dim3 grid(L.blocks_x, L.splits);
+  {
+  UOTK_PROF(ctx, s, "direct");
+  if (L.d <= 3) {
+    const float4* src = reinterpret_cast<const float4*>(b.src);
+    const float4* tgt = reinterpret_cast<const float4*>(b.tgt);
+#define UOTK_DIRECT_CASE(DD, RR)                                                          \
+  if (L.d == DD && L.reg_targets == RR)                                                   \
+    k_direct_small<DD, RR><<<grid, DIRECT_THREADS, 0, s>>>(src, L.tiles, L.tiles_per_split, \
+                                                           tgt, L.m, neg_c, dst, ctx->dflags);
+    UOTK_DIRECT_CASE(1, 1) UOTK_DIRECT_CASE(1, 4) UOTK_DIRECT_CASE(2, 1)
+    UOTK_DIRECT_CASE(2, 4) UOTK_DIRECT_CASE(3, 1) UOTK_DIRECT_CASE(3, 4)
+#undef UOTK_DIRECT_CASE
+  } else {
+    const float* src = reinterpret_cast<const float*>(b.src);
+    const float* tgt = reinterpret_cast<const float*>(b.tgt);
+    const size_t smem = (size_t)GEN_TILE * L.dp * sizeof(float);
+    if (L.d <= 8)
+      k_direct_general<8><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
+                                                             L.m, L.d, L.dp, neg_c, dst);
+    else if (L.d <= 16)
+      k_direct_general<16><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
+                                                              L.m, L.d, L.dp, neg_c, dst);
+    else if (L.d <= 32)
+      k_direct_general<32><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
+                                                              L.m, L.d, L.dp, neg_c, dst);
+    else if (L.d <= 64)
+      k_direct_general<64><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
+                                                              L.m, L.d, L.dp, neg_c, dst);
+    else
+      k_direct_general<128><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split,
+                                                               tgt, L.m, L.d, L.dp, neg_c, dst);
+  }
+  }
+  UOTK_LAUNCHED(ctx);
+  if (L.splits > 1) {
+    UOTK_PROF(ctx, s, "split_reduce");
+    k_reduce_splits<<<grid_for(ctx, L.m, 256), 256, 0, s>>>(b.part, L.splits, L.m, out);
+    UOTK_LAUNCHED(ctx);
+  }
+  return UOTK_OK;
+}
+
+}  // namespace uotk

@@ -1,0 +1,567 @@
+// Sinkhorn's algorithm for entropic UOT (Alg. 1 / Alg. 2), the dual value of
+// Eq. (dual_euot), MMD^2 (Eq. 1205) and the unbalanced Sinkhorn divergence
+// (Eq. 586), on top of a summation engine (direct or NFFT).
+//
+// Half-step (beta side; the gamma side exchanges the roles):
+//   w_j    = nu_j * exp(lambda*gamma_j - M_gamma)        (product reference)
+//   t_i    = sum_j exp(-||x_i - y_j||^2/eps) w_j          (FP32 kernel sum)
+//   beta_i = -q (log t_i + M_gamma)                       (FP64)
+//   beta_i =  q (log mu_i - log t_i - M_gamma)            (counting reference)
+// with q = eta/(1 + eta*lambda) and M_gamma = max_j lambda*gamma_j, a global
+// shift that keeps the FP32 weights in range and is added back after the log.
+// Shifts are maxima taken with integer atomics on an order-preserving encoding,
+// so every result is independent of scheduling.
+#include <math.h>
+#include <stdarg.h>
+
+#include <memory>
+
+#include "engine.cuh"
+
+namespace uotk {
+
+namespace {
+
+constexpr int RED_THREADS = 256;
+constexpr int RED_BLOCKS_PER_SM = 2;
+
+// ---------------------------------------------------------------------------
+// Direct engine.
+// ---------------------------------------------------------------------------
+struct DirectEngine : Engine {
+  uotk_ctx* ctx = nullptr;
+  int d = 0;
+  int64_t n = 0, m = 0;
+  const float* a = nullptr;
+  const float* b = nullptr;
+  double eps = 1.0;
+  DirectLayout Lyx, Lxy, Lxx, Lyy;  // src -> tgt
+  void* Px = nullptr;  // X packed as sources (weights a), also read as targets
+  void* Py = nullptr;
+  float* part = nullptr;
+
+  static void layouts(uotk_ctx* ctx, const EngineSpec& sp, DirectLayout& yx, DirectLayout& xy,
+                      DirectLayout& xx, DirectLayout& yy) {
+    yx = direct_layout(ctx, sp.d, sp.m, sp.n);
+    xy = direct_layout(ctx, sp.d, sp.n, sp.m);
+    xx = direct_layout(ctx, sp.d, sp.n, sp.n);
+    yy = direct_layout(ctx, sp.d, sp.m, sp.m);
+  }
+  static void carve(uotk_ctx* ctx, const EngineSpec& sp, Carver& cv, DirectEngine* e) {
+    DirectLayout yx, xy, xx, yy;
+    layouts(ctx, sp, yx, xy, xx, yy);
+    size_t part = yx.part_bytes;
+    for (size_t p : {xy.part_bytes, xx.part_bytes, yy.part_bytes}) part = p > part ? p : part;
+    // X is packed once as a source of xy/xx (n_pad rows >= n, also valid as targets).
+    size_t bx = xy.src_bytes > yx.tgt_bytes ? xy.src_bytes : yx.tgt_bytes;
+    size_t by = yx.src_bytes > xy.tgt_bytes ? yx.src_bytes : xy.tgt_bytes;
+    void* px = cv.take<char>(bx > 0 ? bx : 16);
+    void* py = cv.take<char>(by > 0 ? by : 16);
+    float* pp = part ? cv.take<float>(part / sizeof(float)) : nullptr;
+    if (e) {
+      e->Lyx = yx; e->Lxy = xy; e->Lxx = xx; e->Lyy = yy;
+      e->Px = px; e->Py = py; e->part = pp;
+    }
+  }
+
+  uotk_status half(cudaStream_t s, int side, const float* base, const double* pot, double lam,
+                   const long long* shift_slot, float* out) override {
+    const DirectLayout& L = side == 0 ? Lyx : Lxy;
+    void* src = side == 0 ? Py : Px;
+    void* tgt = side == 0 ? Px : Py;
+    UOTK_TRY(direct_set_weights(ctx, s, L, src, base, pot, lam, shift_slot));
+    DirectBufs bufs{src, tgt, part};
+    return direct_run(ctx, s, L, bufs, eps, out);
+  }
+  uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
+    (void)w;  // the packed sources carry the caller's weights
+    const DirectLayout& L = src == 0 ? (tgt == 0 ? Lxx : Lxy) : (tgt == 0 ? Lyx : Lyy);
+    DirectBufs bufs{src == 0 ? Px : Py, tgt == 0 ? Px : Py, part};
+    return direct_run(ctx, s, L, bufs, eps, out);
+  }
+  const float* weights(int side) const override { return side == 0 ? a : b; }
+  uotk_status to_caller(cudaStream_t s, int side, const double* in, double* out) override {
+    if (in != out)
+      UOTK_CUDA(ctx, cudaMemcpyAsync(out, in, sizeof(double) * (side == 0 ? n : m),
+                                     cudaMemcpyDeviceToDevice, s));
+    return UOTK_OK;
+  }
+  uotk_status to_caller_f32(cudaStream_t s, int side, const float* in, float* out) override {
+    if (in != out)
+      UOTK_CUDA(ctx, cudaMemcpyAsync(out, in, sizeof(float) * (side == 0 ? n : m),
+                                     cudaMemcpyDeviceToDevice, s));
+    return UOTK_OK;
+  }
+  uotk_status from_caller(cudaStream_t s, int side, const double* in, double* out) override {
+    return to_caller(s, side, in, out);
+  }
+  bool identity_order() const override { return true; }
+};
+
+// ---------------------------------------------------------------------------
+// Kernels of the dual updates and reductions.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double block_max(double v, double* sh) {
+  v = warp_max(v);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) {
+    v = lane < (int)(blockDim.x >> 5) ? sh[lane] : -INFINITY;
+    v = warp_max(v);
+  }
+  __syncthreads();
+  return v;
+}
+
+// pot_i <- dual update from t_i; max of lam*pot -> *max_out; optional max |lam*change|.
+__global__ void k_dual_update(const float* __restrict__ t, const float* __restrict__ base,
+                              long long count, double q, double lam, int ref,
+                              long long* __restrict__ flags, int shift_in, int max_out,
+                              int reset_slot, int delta_out, int reset_delta,
+                              double* __restrict__ pot) {
+  __shared__ double sh[32];
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    flags[reset_slot] = ORDERED_NEG_INF;
+    if (reset_delta >= 0) flags[reset_delta] = ORDERED_NEG_INF;
+  }
+  const double shift = ordered_to_dbl(flags[shift_in]);
+  double mx = -INFINITY, dl = 0.0;
+  long long bad = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double lt = log((double)t[i]) + shift;
+    const double v = ref == 0 ? -q * lt : q * (log((double)base[i]) - lt);
+    if (delta_out >= 0) dl = fmax(dl, fabs(lam * (v - pot[i])));
+    pot[i] = v;
+    if (isfinite(v)) mx = fmax(mx, lam * v);
+    else bad++;
+  }
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0) atomicMax(&flags[max_out], dbl_to_ordered(mx));
+  if (delta_out >= 0) {
+    dl = block_max(dl, sh);
+    if (threadIdx.x == 0) atomicMax(&flags[delta_out], dbl_to_ordered(dl));
+  }
+  if (bad) flag_add(&flags[FLAG_NONFINITE_DUAL], bad);
+}
+
+__global__ void k_max_pot(const double* __restrict__ pot, long long count, double lam,
+                          long long* __restrict__ slot) {
+  __shared__ double sh[32];
+  double mx = -INFINITY;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x)
+    mx = fmax(mx, lam * pot[i]);
+  mx = block_max(mx, sh);
+  if (threadIdx.x == 0) atomicMax(slot, dbl_to_ordered(mx));
+}
+
+__global__ void k_flags_reset(long long* flags) {
+  const int i = threadIdx.x;
+  if (i < NUM_FLAGS)
+    flags[i] = (i >= FLAG_MAX_G0 && i <= FLAG_DELTA1) ? ORDERED_NEG_INF : 0LL;
+}
+
+// Block partial sums of up to 5 FP64 terms; term k over [0, len_k):
+//   kind 0: sum base_i * exp(-pot_i / eta)
+//   kind 1: sum base_i
+//   kind 2: sum base_i * t_i                     (t FP32)
+//   kind 3: sum (base_i or 1) * exp(lam*pot_i + shift) * t_i
+struct SumTerm {
+  int kind;
+  long long len;
+  const float* base;
+  const double* pot;
+  const float* t;
+  double eta, lam;
+  int shift_slot;
+};
+struct SumTerms {
+  SumTerm k[5];
+  int count;
+};
+
+__global__ void k_sum_partials(SumTerms terms, const long long* __restrict__ flags,
+                               double* __restrict__ part) {
+  __shared__ double sh[32];
+  for (int q = 0; q < terms.count; ++q) {
+    const SumTerm T = terms.k[q];
+    const double shift = T.kind == 3 ? ordered_to_dbl(flags[T.shift_slot]) : 0.0;
+    double acc = 0.0;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T.len;
+         i += (long long)gridDim.x * blockDim.x) {
+      const double bi = T.base ? (double)T.base[i] : 1.0;
+      double v;
+      if (T.kind == 0) v = bi * exp(-T.pot[i] / T.eta);
+      else if (T.kind == 1) v = bi;
+      else if (T.kind == 2) v = bi * (double)T.t[i];
+      else v = bi * exp(T.lam * T.pot[i] + shift) * (double)T.t[i];
+      acc += v;
+    }
+    acc = warp_sum(acc);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) sh[w] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int i = 0; i < (int)(blockDim.x >> 5); ++i) s += sh[i];
+      part[q * gridDim.x + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_sum_final(const double* __restrict__ part, int blocks, int count,
+                            double* __restrict__ out) {
+  // one warp per term, fixed order
+  const int q = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (q >= count) return;
+  double s = 0.0;
+  for (int i = lane; i < blocks; i += 32) s += part[q * blocks + i];
+  s = warp_sum(s);
+  if (lane == 0) out[q] = s;
+}
+
+struct Reducer {
+  double* part = nullptr;  // [5][blocks]
+  double* out = nullptr;   // [5]
+  int blocks = 0;
+};
+
+uotk_status run_sums(uotk_ctx* ctx, cudaStream_t s, const Reducer& R, const SumTerms& T,
+                     double* host_out) {
+  {
+    UOTK_PROF(ctx, s, "reduce");
+    k_sum_partials<<<R.blocks, RED_THREADS, 0, s>>>(T, ctx->dflags, R.part);
+  }
+  UOTK_LAUNCHED(ctx);
+  {
+    UOTK_PROF(ctx, s, "reduce");
+    k_sum_final<<<1, 32 * 5, 0, s>>>(R.part, R.blocks, T.count, R.out);
+  }
+  UOTK_LAUNCHED(ctx);
+  UOTK_CUDA(ctx, cudaMemcpyAsync(host_out, R.out, sizeof(double) * T.count,
+                                 cudaMemcpyDeviceToHost, s));
+  return UOTK_OK;
+}
+
+void carve_reducer(uotk_ctx* ctx, Carver& cv, Reducer& R) {
+  R.blocks = ctx->num_sms * RED_BLOCKS_PER_SM;
+  R.part = cv.take<double>((size_t)5 * R.blocks);
+  R.out = cv.take<double>(5);
+}
+
+// Internal-order work arrays of one solve.
+struct SolveBufs {
+  double* beta = nullptr;   // internal order (aliases caller's when identity order)
+  double* gamma = nullptr;
+  float* tx = nullptr;
+  float* ty = nullptr;
+};
+
+void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& B) {
+  B.tx = cv.take<float>(n > 0 ? n : 1);
+  B.ty = cv.take<float>(m > 0 ? m : 1);
+  if (need_copies) {
+    B.beta = cv.take<double>(n > 0 ? n : 1);
+    B.gamma = cv.take<double>(m > 0 ? m : 1);
+  }
+}
+
+struct SolveResult {
+  int sweeps = 0;
+  double value = 0.0;
+  bool converged = false;
+};
+
+// Alg. 1 / Alg. 2 for up to max_sweeps sweeps on an engine, then D(beta, gamma).
+uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m, double eps,
+                  double eta1, double eta2, int max_sweeps, double tol, int ref, bool warm,
+                  const SolveBufs& B, const Reducer& R, SolveResult* res) {
+  const double lam = 1.0 / eps;
+  const double q1 = eta1 / (1.0 + eta1 * lam), q2 = eta2 / (1.0 + eta2 * lam);
+  const float* a = E->weights(0);
+  const float* b = E->weights(1);
+  long long* F = ctx->dflags;
+  if (!warm) UOTK_CUDA(ctx, cudaMemsetAsync(B.gamma, 0, sizeof(double) * m, s));
+  k_max_pot<<<grid_for(ctx, m, 256, 2), 256, 0, s>>>(B.gamma, m, lam, F + FLAG_MAX_G0);
+  UOTK_LAUNCHED(ctx);
+  const bool track = tol > 0.0;
+  const int gu = grid_for(ctx, n > m ? n : m, 256, 4);
+  int done = 0;
+  bool converged = false;
+  for (int sw = 0; sw < max_sweeps; ++sw) {
+    const int cur = sw & 1, nxt = cur ^ 1;
+    // beta half-step: sum over Y into X
+    UOTK_TRY(E->half(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.tx));
+    {
+    UOTK_PROF(ctx, s, "dual_update");
+    k_dual_update<<<gu, 256, 0, s>>>(B.tx, a, n, q1, lam, ref, F, FLAG_MAX_G0 + cur,
+                                     FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt,
+                                     track ? FLAG_DELTA0 + cur : -1,
+                                     track ? FLAG_DELTA0 + nxt : -1, B.beta);
+    }
+    UOTK_LAUNCHED(ctx);
+    // gamma half-step: sum over X into Y
+    UOTK_TRY(E->half(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ty));
+    {
+    UOTK_PROF(ctx, s, "dual_update");
+    k_dual_update<<<gu, 256, 0, s>>>(B.ty, b, m, q2, lam, ref, F, FLAG_MAX_B0 + cur,
+                                     FLAG_MAX_G0 + nxt, FLAG_MAX_B0 + nxt,
+                                     track ? FLAG_DELTA0 + cur : -1, -1, B.gamma);
+    }
+    UOTK_LAUNCHED(ctx);
+    done = sw + 1;
+    if (track && (done % 10 == 0 || done == max_sweeps)) {
+      UOTK_CUDA(ctx, cudaMemcpyAsync(ctx->host, F + FLAG_DELTA0 + cur, sizeof(long long),
+                                     cudaMemcpyDeviceToHost, s));
+      UOTK_CUDA(ctx, cudaStreamSynchronize(s));
+      long long enc;
+      memcpy(&enc, ctx->host, sizeof(long long));
+      if (ordered_to_dbl(enc) < tol) {
+        converged = true;
+        break;
+      }
+    }
+  }
+  // Dual value, Eq. (dual_euot), at the final duals.  The last gamma half-step
+  // left t_y = sum_i k_ij mu_i e^{lambda beta_i - M_beta}, so the coupling sum is
+  // sum_j nu_j e^{lambda gamma_j + M_beta} t_y,j.
+  const int last = (done - 1) & 1;
+  SumTerms T{};
+  T.count = 5;
+  T.k[0] = SumTerm{0, n, a, B.beta, nullptr, eta1, lam, 0};
+  T.k[1] = SumTerm{0, m, b, B.gamma, nullptr, eta2, lam, 0};
+  T.k[2] = SumTerm{1, n, a, nullptr, nullptr, 1.0, lam, 0};
+  T.k[3] = SumTerm{1, m, b, nullptr, nullptr, 1.0, lam, 0};
+  T.k[4] = SumTerm{3, m, ref == 0 ? b : nullptr, B.gamma, B.ty, 1.0, lam, FLAG_MAX_B0 + last};
+  UOTK_TRY(run_sums(ctx, s, R, T, ctx->host + 8));
+  UOTK_TRY(flags_check(ctx, s, "uot_sinkhorn"));
+  const double* h = ctx->host + 8;
+  double coupling = h[4];
+  if (ref == 0) coupling -= h[2] * h[3];
+  res->value = -eta1 * h[0] - eta2 * h[1] + eta1 * h[2] + eta2 * h[3] - coupling / lam;
+  res->sweeps = done;
+  res->converged = converged;
+  return UOTK_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Engine construction.
+// ---------------------------------------------------------------------------
+size_t engine_bytes(uotk_ctx* ctx, const EngineSpec& sp) {
+  if (sp.method == UOTK_NFFT) return nfft_engine_bytes(ctx, sp);
+  Carver cv(nullptr);
+  DirectEngine::carve(ctx, sp, cv, nullptr);
+  return cv.off;
+}
+
+uotk_status engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, Carver& cv,
+                          Engine** out) {
+  if (sp.method == UOTK_NFFT) return nfft_engine_create(ctx, s, sp, cv, out);
+  std::unique_ptr<DirectEngine> e(new DirectEngine());
+  e->ctx = ctx; e->d = sp.d; e->n = sp.n; e->m = sp.m; e->a = sp.a; e->b = sp.b;
+  e->eps = sp.eps;
+  DirectEngine::carve(ctx, sp, cv, e.get());
+  UOTK_TRY(direct_pack_sources(ctx, s, e->Lxy, sp.x, sp.a, e->Px));
+  UOTK_TRY(direct_pack_sources(ctx, s, e->Lyx, sp.y, sp.b, e->Py));
+  *out = e.release();
+  return UOTK_OK;
+}
+
+uotk_status flags_reset(uotk_ctx* ctx, cudaStream_t s) {
+  k_flags_reset<<<1, 32, 0, s>>>(ctx->dflags);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+uotk_status flags_check(uotk_ctx* ctx, cudaStream_t s, const char* what) {
+  long long* h = reinterpret_cast<long long*>(ctx->host + 32);
+  UOTK_CUDA(ctx, cudaMemcpyAsync(h, ctx->dflags, sizeof(long long) * NUM_FLAGS,
+                                 cudaMemcpyDeviceToHost, s));
+  UOTK_CUDA(ctx, cudaStreamSynchronize(s));
+  if (h[FLAG_NONFINITE])
+    return set_error(ctx, UOTK_ERR_NONFINITE, "%s: %lld non-finite input values", what,
+                     h[FLAG_NONFINITE]);
+  if (h[FLAG_NEG_WEIGHT])
+    return set_error(ctx, UOTK_ERR_INVALID, "%s: %lld negative weights", what, h[FLAG_NEG_WEIGHT]);
+  if (h[FLAG_TIMEOUT])
+    return set_error(ctx, UOTK_ERR_TIMEOUT, "%s: a device-side wait timed out", what);
+  if (h[FLAG_INTERNAL])
+    return set_error(ctx, UOTK_ERR_INTERNAL, "%s: internal bound check failed (%lld)", what,
+                     h[FLAG_INTERNAL]);
+  if (h[FLAG_NONFINITE_DUAL])
+    return set_error(ctx, UOTK_ERR_NONFINITE,
+                     "%s: %lld non-finite dual values (a kernel sum underflowed: eps too small "
+                     "for the spread of the points?)", what, h[FLAG_NONFINITE_DUAL]);
+  return UOTK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Public operations (called from api.cu after validation).
+// ---------------------------------------------------------------------------
+uotk_status op_kernel_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* src, int64_t n,
+                          const float* w, const float* tgt, int64_t m, float* out, double eps,
+                          const uotk_sum_opts* opts) {
+  // X = targets (no weights), Y = sources.
+  EngineSpec sp{opts ? opts->method : UOTK_DIRECT, d, tgt, m, nullptr, src, n, w, eps, opts};
+  Carver size(nullptr);
+  const size_t eb = engine_bytes(ctx, sp);
+  size.off = eb;
+  float* tmp_off = size.take<float>(m > 0 ? m : 1);
+  (void)tmp_off;
+  UOTK_TRY(ws_reserve(ctx, size.off));
+  UOTK_TRY(flags_reset(ctx, s));
+  Carver cv(ctx->ws);
+  Engine* raw = nullptr;
+  UOTK_TRY(engine_create(ctx, s, sp, cv, &raw));
+  std::unique_ptr<Engine> E(raw);
+  cv.off = eb;
+  float* tmp = cv.take<float>(m > 0 ? m : 1);
+  if (E->identity_order()) {
+    UOTK_TRY(E->plain(s, 1, 0, w, out));
+  } else {
+    UOTK_TRY(E->plain(s, 1, 0, w, tmp));
+    UOTK_TRY(E->to_caller_f32(s, 0, tmp, out));
+  }
+  return flags_check(ctx, s, "kernel_sum");
+}
+
+uotk_status op_uot_sinkhorn(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
+                            const float* a, const float* y, int64_t m, const float* b, double eps,
+                            double rho1, double rho2, int max_sweeps, double tol, int ref,
+                            unsigned flags, double* beta, double* gamma, int* sweeps_done,
+                            double* value, const uotk_sum_opts* opts) {
+  EngineSpec sp{opts ? opts->method : UOTK_DIRECT, d, x, n, a, y, m, b, eps, opts};
+  const bool copies = sp.method == UOTK_NFFT;
+  Carver size(nullptr);
+  size.off = engine_bytes(ctx, sp);
+  SolveBufs B;
+  Reducer R;
+  carve_solve(size, n, m, copies, B);
+  carve_reducer(ctx, size, R);
+  UOTK_TRY(ws_reserve(ctx, size.off));
+  UOTK_TRY(flags_reset(ctx, s));
+  Carver cv(ctx->ws);
+  Engine* raw = nullptr;
+  UOTK_TRY(engine_create(ctx, s, sp, cv, &raw));
+  std::unique_ptr<Engine> E(raw);
+  cv.off = engine_bytes(ctx, sp);
+  carve_solve(cv, n, m, copies, B);
+  carve_reducer(ctx, cv, R);
+  if (!copies) { B.beta = beta; B.gamma = gamma; }
+  const bool warm = (flags & UOTK_WARM_START) != 0;
+  if (copies && warm) UOTK_TRY(E->from_caller(s, 1, gamma, B.gamma));
+  SolveResult res;
+  UOTK_TRY(solve(ctx, s, E.get(), n, m, eps, rho1, rho2, max_sweeps, tol, ref, warm, B, R, &res));
+  if (copies) {
+    UOTK_TRY(E->to_caller(s, 0, B.beta, beta));
+    UOTK_TRY(E->to_caller(s, 1, B.gamma, gamma));
+    UOTK_CUDA(ctx, cudaStreamSynchronize(s));
+  }
+  if (sweeps_done) *sweeps_done = res.sweeps;
+  if (value) *value = res.value;
+  if (tol > 0.0 && !res.converged)
+    return set_error(ctx, UOTK_ERR_NOT_CONVERGED, "uot_sinkhorn: tol %g not reached in %d sweeps",
+                     tol, max_sweeps);
+  return UOTK_OK;
+}
+
+uotk_status op_sinkhorn_divergence(uotk_ctx* ctx, cudaStream_t s, int d, const float* x,
+                                   int64_t n, const float* a, const float* y, int64_t m,
+                                   const float* b, double eps, double rho, int max_sweeps,
+                                   double tol, double* sd, double* parts,
+                                   const uotk_sum_opts* opts) {
+  const int method = opts ? opts->method : UOTK_DIRECT;
+  const EngineSpec specs[3] = {
+      {method, d, x, n, a, y, m, b, eps, opts},
+      {method, d, x, n, a, x, n, a, eps, opts},
+      {method, d, y, m, b, y, m, b, eps, opts}};
+  const bool copies = method == UOTK_NFFT;
+  size_t need = 0;
+  for (const EngineSpec& sp : specs) {
+    Carver c(nullptr);
+    c.off = engine_bytes(ctx, sp);
+    SolveBufs B;
+    Reducer R;
+    carve_solve(c, sp.n, sp.m, true, B);
+    carve_reducer(ctx, c, R);
+    need = c.off > need ? c.off : need;
+  }
+  UOTK_TRY(ws_reserve(ctx, need));
+  double v[3];
+  double masses[2] = {0, 0};
+  bool all_converged = true;
+  for (int k = 0; k < 3; ++k) {
+    const EngineSpec& sp = specs[k];
+    UOTK_TRY(flags_reset(ctx, s));
+    Carver cv(ctx->ws);
+    Engine* raw = nullptr;
+    UOTK_TRY(engine_create(ctx, s, sp, cv, &raw));
+    std::unique_ptr<Engine> E(raw);
+    cv.off = engine_bytes(ctx, sp);
+    SolveBufs B;
+    Reducer R;
+    carve_solve(cv, sp.n, sp.m, true, B);
+    carve_reducer(ctx, cv, R);
+    (void)copies;
+    SolveResult res;
+    UOTK_TRY(solve(ctx, s, E.get(), sp.n, sp.m, eps, rho, rho, max_sweeps, tol, 0, false, B, R,
+                   &res));
+    all_converged = all_converged && res.converged;
+    v[k] = res.value;
+    if (k == 0) {
+      masses[0] = ctx->host[8 + 2];
+      masses[1] = ctx->host[8 + 3];
+    }
+  }
+  const double dm = masses[0] - masses[1];
+  *sd = v[0] - 0.5 * v[1] - 0.5 * v[2] + 0.5 * eps * dm * dm;
+  if (parts) { parts[0] = v[0]; parts[1] = v[1]; parts[2] = v[2]; }
+  if (tol > 0.0 && !all_converged)
+    return set_error(ctx, UOTK_ERR_NOT_CONVERGED, "sinkhorn_divergence: tol %g not reached", tol);
+  return UOTK_OK;
+}
+
+uotk_status op_mmd2(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
+                    const float* a, const float* y, int64_t m, const float* b, double ell,
+                    double* mmd2, double* parts, const uotk_sum_opts* opts) {
+  EngineSpec sp{opts ? opts->method : UOTK_DIRECT, d, x, n, a, y, m, b, ell * ell, opts};
+  Carver size(nullptr);
+  size.off = engine_bytes(ctx, sp);
+  size.take<float>(2 * (n > 0 ? n : 1) + (m > 0 ? m : 1));
+  Reducer R;
+  carve_reducer(ctx, size, R);
+  UOTK_TRY(ws_reserve(ctx, size.off));
+  UOTK_TRY(flags_reset(ctx, s));
+  Carver cv(ctx->ws);
+  Engine* raw = nullptr;
+  UOTK_TRY(engine_create(ctx, s, sp, cv, &raw));
+  std::unique_ptr<Engine> E(raw);
+  cv.off = engine_bytes(ctx, sp);
+  float* t1 = cv.take<float>(2 * (n > 0 ? n : 1) + (m > 0 ? m : 1));
+  float* t2 = t1 + (n > 0 ? n : 1);
+  float* t3 = t2 + (n > 0 ? n : 1);
+  carve_reducer(ctx, cv, R);
+  const float* ai = E->weights(0);
+  const float* bi = E->weights(1);
+  UOTK_TRY(E->plain(s, 0, 0, ai, t1));  // (K_xx a)_i
+  UOTK_TRY(E->plain(s, 1, 0, bi, t2));  // (K_xy b)_i
+  UOTK_TRY(E->plain(s, 1, 1, bi, t3));  // (K_yy b)_j
+  SumTerms T{};
+  T.count = 3;
+  T.k[0] = SumTerm{2, n, ai, nullptr, t1, 1.0, 1.0, 0};
+  T.k[1] = SumTerm{2, n, ai, nullptr, t2, 1.0, 1.0, 0};
+  T.k[2] = SumTerm{2, m, bi, nullptr, t3, 1.0, 1.0, 0};
+  UOTK_TRY(run_sums(ctx, s, R, T, ctx->host + 16));
+  UOTK_TRY(flags_check(ctx, s, "mmd2"));
+  const double* h = ctx->host + 16;
+  *mmd2 = h[0] - 2.0 * h[1] + h[2];
+  if (parts) { parts[0] = h[0]; parts[1] = h[1]; parts[2] = h[2]; }
+  return UOTK_OK;
+}
+
+}  // namespace uotk

@@ -1,0 +1,205 @@
+// Internal declarations of the uotk CUDA library (sm_103a).  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "../../include/uotk.h"
+
+// ---------------------------------------------------------------------------
+// Context: device, workspace arena, pinned host staging, error text.
+// ---------------------------------------------------------------------------
+constexpr int UOTK_PROF_POOL = 1024;   // event pairs in flight before a fold
+constexpr int UOTK_PROF_STAGES = 32;
+struct uotk_prof {
+  bool on = false;
+  int nstages = 0;
+  char names[UOTK_PROF_STAGES][24] = {};
+  long long counts[UOTK_PROF_STAGES] = {};
+  double ms[UOTK_PROF_STAGES] = {};
+  cudaEvent_t ev[2 * UOTK_PROF_POOL] = {};
+  int stage_of[UOTK_PROF_POOL] = {};
+  int pending = 0;
+  bool created = false;
+};
+
+struct uotk_ctx {
+  int device = 0;
+  int num_sms = 0;
+  int max_smem_optin = 0;
+  char err[512] = {0};
+  // Device workspace: one allocation, carved per call.
+  char* ws = nullptr;
+  size_t ws_cap = 0;
+  // Pinned host staging for scalars read back at the end of a call.
+  double* host = nullptr;   // 64 doubles
+  // Device flags/counters (int64 slots), zeroed per call where used.
+  long long* dflags = nullptr;  // 16 slots
+  int64_t launches = 0;
+  uotk_prof prof;
+};
+
+namespace uotk {
+
+// Flag slots in ctx->dflags.
+enum FlagSlot {
+  FLAG_NEG_WEIGHT = 0,     // count of negative weights
+  FLAG_NONFINITE = 1,      // count of non-finite weights/coordinates
+  FLAG_TIMEOUT = 2,        // a bounded device wait gave up
+  FLAG_INTERNAL = 3,       // an internal bound check failed
+  FLAG_MAX_G0 = 4,         // ordered-int64 maxima of lambda*gamma (two parities)
+  FLAG_MAX_G1 = 5,
+  FLAG_MAX_B0 = 6,         // ordered-int64 maxima of lambda*beta (two parities)
+  FLAG_MAX_B1 = 7,
+  FLAG_DELTA0 = 8,         // max |lambda * change| over a sweep (two parities)
+  FLAG_DELTA1 = 9,
+  FLAG_NONFINITE_DUAL = 10,  // count of non-finite dual values produced
+  NUM_FLAGS = 16
+};
+
+uotk_status set_error(uotk_ctx* ctx, uotk_status st, const char* fmt, ...);
+
+// Grow the workspace to `bytes` (synchronises the device when it reallocates).
+uotk_status ws_reserve(uotk_ctx* ctx, size_t bytes);
+
+// Sub-allocation from the workspace.  Usage: first pass computes the size with
+// a null base; second pass hands out pointers.
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(char* b) : base(b) {}
+  template <class T>
+  T* take(size_t count) {
+    off = (off + 255) & ~size_t(255);
+    T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+#define UOTK_CUDA(ctx, call)                                                    \
+  do {                                                                          \
+    cudaError_t e_ = (call);                                                    \
+    if (e_ != cudaSuccess)                                                      \
+      return uotk::set_error((ctx), UOTK_ERR_CUDA, "%s failed: %s (%s:%d)",     \
+                             #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+  } while (0)
+
+#define UOTK_LAUNCHED(ctx)                                                      \
+  do {                                                                          \
+    cudaError_t e_ = cudaGetLastError();                                        \
+    if (e_ != cudaSuccess)                                                      \
+      return uotk::set_error((ctx), UOTK_ERR_CUDA, "kernel launch failed: %s (%s:%d)", \
+                             cudaGetErrorString(e_), __FILE__, __LINE__);       \
+    (ctx)->launches++;                                                          \
+  } while (0)
+
+// Per-stage CUDA-event timing of the launch that follows in the same scope.
+int prof_begin(uotk_ctx* ctx, cudaStream_t s, const char* name);
+void prof_end(uotk_ctx* ctx, cudaStream_t s, int slot);
+struct ProfScope {
+  uotk_ctx* ctx;
+  cudaStream_t s;
+  int slot;
+  ProfScope(uotk_ctx* c, cudaStream_t st, const char* name)
+      : ctx(c), s(st), slot(c->prof.on ? prof_begin(c, st, name) : -1) {}
+  ~ProfScope() {
+    if (slot >= 0) prof_end(ctx, s, slot);
+  }
+};
+#define UOTK_PROF(ctx, s, name) uotk::ProfScope uotk_prof_scope_((ctx), (s), (name))
+
+#define UOTK_TRY(expr)                 \
+  do {                                 \
+    uotk_status s_ = (expr);           \
+    if (s_ != UOTK_OK) return s_;      \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Device helpers.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Order-preserving map of doubles onto signed 64-bit integers, so that the
+// maximum of doubles can be taken with integer atomicMax (deterministic).
+__device__ __host__ __forceinline__ long long dbl_to_ordered(double v) {
+  long long b;
+  memcpy(&b, &v, 8);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __host__ __forceinline__ double ordered_to_dbl(long long b) {
+  long long r = b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+  double v;
+  memcpy(&v, &r, 8);
+  return v;
+}
+static const long long ORDERED_NEG_INF = (long long)0x800fffffffffffffULL;  // encodes -inf
+
+__device__ __forceinline__ void flag_add(long long* p, long long v) {
+  atomicAdd(reinterpret_cast<unsigned long long*>(p), static_cast<unsigned long long>(v));
+}
+
+template <class T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// Direct kernel summation (ksum_direct.cu).
+// ---------------------------------------------------------------------------
+struct DirectLayout {
+  int d = 0;
+  int64_t n = 0, m = 0;
+  int reg_targets = 1;   // targets per thread
+  int blocks_x = 0;      // target blocks
+  int splits = 1;        // source splits (partial sums reduced in FP64)
+  int64_t tiles = 0;     // source tiles of TILE points
+  int tiles_per_split = 0;
+  int dp = 4;            // floats per packed point (general-d path)
+  size_t src_bytes = 0, tgt_bytes = 0, part_bytes = 0;
+};
+constexpr int DIRECT_TILE = 256;
+constexpr int DIRECT_THREADS = 256;
+
+DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m);
+
+// Buffers of one direct summation.
+struct DirectBufs {
+  void* src = nullptr;    // packed sources (float4 for d<=3, float[dp] otherwise)
+  void* tgt = nullptr;    // packed targets
+  float* part = nullptr;  // [splits][m] partial sums (splits > 1)
+};
+void direct_carve(Carver& cv, const DirectLayout& L, DirectBufs& b);
+
+// Pack raw row-major FP32 points (sources with weights / targets without).
+// Weight validation counters go to ctx->dflags.
+uotk_status direct_pack_sources(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                                const float* pts, const float* w, void* packed);
+uotk_status direct_pack_targets(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                                const float* pts, void* packed);
+// Rewrite only the weights of packed sources: w_i = base_i * exp(lam*pot_i - shift),
+// shift read from the ordered-int64 slot *shift_slot (base may be NULL for 1).
+uotk_status direct_set_weights(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                               void* packed, const float* base, const double* pot,
+                               double lam, const long long* shift_slot);
+// out[j] = sum_i w_i exp(-||s_i - t_j||^2 / eps) from packed buffers.
+uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                       const DirectBufs& b, double eps, float* out);
+
+int grid_for(const uotk_ctx* ctx, int64_t work, int threads, int per_sm = 8);
+
+}  // namespace uotk

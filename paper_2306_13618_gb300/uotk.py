@@ -1,0 +1,317 @@
+"""Thin ctypes binding of the uotk C ABI (include/uotk.h).
+
+Argument marshalling only: every step of every operation runs in the CUDA
+library ``_lib/libuotk.so``.  Tensors are torch CUDA tensors (PyTorch provides
+device memory and the current stream); nothing here computes.  If the library
+is missing, ``lib()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libuotk.so")
+
+UOTK_OK = 0
+UOTK_ERR_NOT_CONVERGED = 6
+DIRECT, NFFT = 0, 1
+REF_PRODUCT, REF_COUNTING = 0, 1
+WARM_START = 1
+
+_lib = None
+_lock = threading.Lock()
+
+
+class UotkError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"uotk status {status}: {message}")
+        self.status = status
+
+
+class SumOpts(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("bandwidth", ctypes.c_int32), ("cutoff", ctypes.c_int32),
+                ("period", ctypes.c_double), ("target_err", ctypes.c_double)]
+
+
+class NfftPlan(ctypes.Structure):
+    _fields_ = [("d", ctypes.c_int32), ("grid", ctypes.c_int32),
+                ("bandwidth", ctypes.c_int32), ("cutoff", ctypes.c_int32),
+                ("center", ctypes.c_float * 3), ("inv_h", ctypes.c_float),
+                ("h", ctypes.c_double), ("eps", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"d": self.d, "grid": self.grid, "bandwidth": self.bandwidth,
+                "cutoff": self.cutoff, "center": list(self.center), "inv_h": self.inv_h,
+                "h": self.h, "eps": self.eps}
+
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+_D = ctypes.c_double
+
+
+def lib():
+    """Load the CUDA library; raise if it was not built (no fallback)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"uotk CUDA library not built: {LIB_PATH} missing "
+                               "(run __graft_entry__.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        L.uotk_create.argtypes = [ctypes.POINTER(_P), ctypes.c_int]
+        L.uotk_destroy.argtypes = [_P]
+        L.uotk_last_error.argtypes = [_P]
+        L.uotk_last_error.restype = ctypes.c_char_p
+        L.uotk_status_string.restype = ctypes.c_char_p
+        L.uotk_launch_count.argtypes = [_P]
+        L.uotk_launch_count.restype = _I64
+        L.uotk_set_profiling.argtypes = [_P, ctypes.c_int]
+        L.uotk_set_profiling.restype = ctypes.c_int
+        L.uotk_profile_read.argtypes = [_P, ctypes.c_char_p, ctypes.c_int,
+                                        ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.c_int]
+        L.uotk_profile_read.restype = ctypes.c_int
+        L.uotk_profile_reset.argtypes = [_P]
+        opts = ctypes.POINTER(SumOpts)
+        plan = ctypes.POINTER(NfftPlan)
+        L.uotk_kernel_sum.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, opts]
+        L.uotk_uot_sinkhorn.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, _D,
+                                        _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_uint, _P, _P,
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D), opts]
+        L.uotk_sinkhorn_divergence.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
+                                               _D, _D, ctypes.c_int, _D, ctypes.POINTER(_D),
+                                               ctypes.POINTER(_D), opts]
+        L.uotk_mmd2.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
+                                ctypes.POINTER(_D), ctypes.POINTER(_D), opts]
+        L.uotk_nfft_plan.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _I64, _D, opts, plan]
+        L.uotk_nfft_cells.argtypes = [_P, _P, plan, _P, _I64, _P]
+        L.uotk_nfft_spread.argtypes = [_P, _P, plan, _P, _I64, _P, _P]
+        L.uotk_nfft_convolve.argtypes = [_P, _P, plan, _P, _P]
+        L.uotk_nfft_gather.argtypes = [_P, _P, plan, _P, _P, _I64, _P]
+        for name in ("uotk_create", "uotk_kernel_sum", "uotk_uot_sinkhorn",
+                     "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_nfft_plan",
+                     "uotk_nfft_cells", "uotk_nfft_spread", "uotk_nfft_convolve",
+                     "uotk_nfft_gather"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+        return L
+
+
+class Context:
+    """One uotk_ctx (device workspace, flags) on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.device = device
+        h = _P()
+        st = lib().uotk_create(ctypes.byref(h), int(device))
+        if st != UOTK_OK:
+            raise UotkError(st, f"uotk_create(device={device}) failed")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().uotk_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        return int(lib().uotk_launch_count(self.handle))
+
+    def set_profiling(self, on: bool):
+        self.check(lib().uotk_set_profiling(self.handle, int(bool(on))))
+
+    def profile(self) -> dict:
+        """{stage: (launches, total device ms)} since the last reset."""
+        names = ctypes.create_string_buffer(4096)
+        counts = (_I64 * 32)()
+        ms = (_D * 32)()
+        k = lib().uotk_profile_read(self.handle, names, 4096, counts, ms, 32)
+        labels = names.value.decode().split(";") if k else []
+        return {labels[i]: (int(counts[i]), float(ms[i])) for i in range(k)}
+
+    def profile_reset(self):
+        lib().uotk_profile_reset(self.handle)
+
+    def check(self, st, ok=(UOTK_OK,)):
+        if st not in ok:
+            msg = lib().uotk_last_error(self.handle).decode()
+            raise UotkError(st, msg)
+        return st
+
+
+_contexts = {}
+
+
+def default_context(device=None) -> Context:
+    dev = torch.cuda.current_device() if device is None else int(device)
+    if dev not in _contexts:
+        _contexts[dev] = Context(dev)
+    return _contexts[dev]
+
+
+def _stream():
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _f32(t, name, ndim=None):
+    if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float32):
+        raise TypeError(f"{name} must be a CUDA float32 tensor")
+    if ndim is not None and t.dim() != ndim:
+        raise ValueError(f"{name} must have {ndim} dimensions")
+    return t.contiguous()
+
+
+def _pts(t, name):
+    t = _f32(t, name)
+    if t.dim() == 1:
+        t = t.reshape(-1, 1)
+    if t.dim() != 2:
+        raise ValueError(f"{name} must be (n, d)")
+    return t
+
+
+def _opts(method="direct", grid=0, bandwidth=0, cutoff=0, period=0.0, target_err=0.0):
+    m = {"direct": DIRECT, "nfft": NFFT}.get(method, method)
+    return SumOpts(int(m), int(grid), int(bandwidth), int(cutoff), float(period), float(target_err))
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr() if t is not None else 0)
+
+
+def kernel_sum(src, w, tgt, eps, method="direct", out=None, ctx=None, **nfft):
+    """out_j = sum_i w_i exp(-||src_i - tgt_j||^2/eps) (uotk_kernel_sum)."""
+    src, tgt, w = _pts(src, "src"), _pts(tgt, "tgt"), _f32(w, "w").reshape(-1)
+    ctx = ctx or default_context()
+    if out is None:
+        out = torch.empty(tgt.shape[0], device=tgt.device, dtype=torch.float32)
+    o = _opts(method, **nfft)
+    ctx.check(lib().uotk_kernel_sum(ctx.handle, _stream(), src.shape[1], _ptr(src), src.shape[0],
+                                    _ptr(w), _ptr(tgt), tgt.shape[0], _ptr(out), float(eps),
+                                    ctypes.byref(o)))
+    return out
+
+
+def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref="product",
+                 gamma0=None, method="direct", ctx=None, beta=None, gamma=None, **nfft):
+    """KL-penalised entropic UOT by Sinkhorn (uotk_uot_sinkhorn).
+
+    Returns (beta, gamma, sweeps_done, value, converged)."""
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    rho2 = rho1 if rho2 is None else rho2
+    ctx = ctx or default_context()
+    dev = x.device
+    beta = torch.empty(x.shape[0], device=dev, dtype=torch.float64) if beta is None else beta
+    flags = 0
+    if gamma0 is not None:
+        gamma = gamma0.to(device=dev, dtype=torch.float64).contiguous().clone()
+        flags |= WARM_START
+    elif gamma is None:
+        gamma = torch.empty(y.shape[0], device=dev, dtype=torch.float64)
+    refc = {"product": REF_PRODUCT, "counting": REF_COUNTING}.get(ref, ref)
+    sweeps = ctypes.c_int(0)
+    value = _D(0.0)
+    o = _opts(method, **nfft)
+    st = ctx.check(lib().uotk_uot_sinkhorn(
+        ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0], _ptr(a), _ptr(y), y.shape[0],
+        _ptr(b), float(eps), float(rho1), float(rho2), int(max_sweeps), float(tol), int(refc),
+        flags, _ptr(beta), _ptr(gamma), ctypes.byref(sweeps), ctypes.byref(value),
+        ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
+    return beta, gamma, sweeps.value, value.value, st == UOTK_OK
+
+
+def sinkhorn_divergence(x, a, y, b, eps, rho, max_sweeps=100, tol=0.0, method="direct",
+                        ctx=None, **nfft):
+    """Unbalanced Sinkhorn divergence of Eq. (586); returns (sd, [UOT_xy, UOT_xx, UOT_yy])."""
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    ctx = ctx or default_context()
+    sd = _D(0.0)
+    parts = (_D * 3)()
+    o = _opts(method, **nfft)
+    ctx.check(lib().uotk_sinkhorn_divergence(
+        ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0], _ptr(a), _ptr(y), y.shape[0],
+        _ptr(b), float(eps), float(rho), int(max_sweeps), float(tol), ctypes.byref(sd), parts,
+        ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
+    return sd.value, list(parts)
+
+
+def mmd2(x, a, y, b, ell, method="direct", ctx=None, **nfft):
+    """MMD^2 of Eq. (1205), Gaussian kernel exp(-d^2/ell^2); returns (value, [A, B, C])."""
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    ctx = ctx or default_context()
+    v = _D(0.0)
+    parts = (_D * 3)()
+    o = _opts(method, **nfft)
+    ctx.check(lib().uotk_mmd2(ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0], _ptr(a),
+                              _ptr(y), y.shape[0], _ptr(b), float(ell), ctypes.byref(v), parts,
+                              ctypes.byref(o)))
+    return v.value, list(parts)
+
+
+def nfft_plan(src, tgt, eps, ctx=None, **nfft):
+    src, tgt = _pts(src, "src"), _pts(tgt, "tgt")
+    ctx = ctx or default_context()
+    p = NfftPlan()
+    o = _opts("nfft", **nfft)
+    ctx.check(lib().uotk_nfft_plan(ctx.handle, _stream(), src.shape[1], _ptr(src), src.shape[0],
+                                   _ptr(tgt), tgt.shape[0], float(eps), ctypes.byref(o),
+                                   ctypes.byref(p)))
+    return p
+
+
+def nfft_cells(plan, pts, ctx=None):
+    pts = _pts(pts, "pts")
+    ctx = ctx or default_context()
+    cells = torch.empty((pts.shape[0], 3), device=pts.device, dtype=torch.int32)
+    ctx.check(lib().uotk_nfft_cells(ctx.handle, _stream(), ctypes.byref(plan), _ptr(pts),
+                                    pts.shape[0], _ptr(cells)))
+    return cells
+
+
+def nfft_spread(plan, pts, w, ctx=None):
+    pts, w = _pts(pts, "pts"), _f32(w, "w").reshape(-1)
+    ctx = ctx or default_context()
+    g = plan.grid
+    grid = torch.empty((g, g, g), device=pts.device, dtype=torch.float32)
+    ctx.check(lib().uotk_nfft_spread(ctx.handle, _stream(), ctypes.byref(plan), _ptr(pts),
+                                     pts.shape[0], _ptr(w), _ptr(grid)))
+    return grid
+
+
+def nfft_convolve(plan, grid_in, grid_out=None, ctx=None):
+    grid_in = _f32(grid_in, "grid_in")
+    ctx = ctx or default_context()
+    grid_out = torch.empty_like(grid_in) if grid_out is None else grid_out
+    ctx.check(lib().uotk_nfft_convolve(ctx.handle, _stream(), ctypes.byref(plan), _ptr(grid_in),
+                                       _ptr(grid_out)))
+    return grid_out
+
+
+def nfft_gather(plan, grid, pts, ctx=None):
+    grid, pts = _f32(grid, "grid"), _pts(pts, "pts")
+    ctx = ctx or default_context()
+    out = torch.empty(pts.shape[0], device=pts.device, dtype=torch.float32)
+    ctx.check(lib().uotk_nfft_gather(ctx.handle, _stream(), ctypes.byref(plan), _ptr(grid),
+                                     _ptr(pts), pts.shape[0], _ptr(out)))
+    return out
+
+
+EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_string",
+            "uotk_launch_count", "uotk_set_profiling", "uotk_profile_read", "uotk_profile_reset",
+            "uotk_kernel_sum", "uotk_uot_sinkhorn",
+            "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_nfft_plan", "uotk_nfft_cells",
+            "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]

@@ -1,0 +1,190 @@
+"""GPU parity of the direct (exact O(nm)) form against the FP64 oracle, through
+the C ABI.  Tolerances derived from FP32 arithmetic (see the derivation in the
+design notes): every kernel-sum term is positive, so the relative error of an
+output is bounded by the relative error of its terms -- ex2.approx (~2 ulp),
+the FP32 squared distance (a few ulp of the exponent) and the FP32 partial sums
+of 32 terms -- about 4e-7; we test at 2e-6 per output (5e-6 for d >= 8, whose
+squared distance carries d roundings).  Sinkhorn duals after a fixed number of
+sweeps are compared with the paper's residual (Table Tab:Accuracy_analysis2):
+||beta - beta*||/||beta*|| + ||gamma - gamma*||/||gamma*|| <= 1e-6."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_13618_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def uotk():
+    from paper_2306_13618_gb300 import build, uotk
+    build.build()
+    return uotk
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def rel_err(got, ref):
+    got, ref = np.asarray(got, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300))
+
+
+@pytest.mark.parametrize("d", [1, 2, 3, 5, 8, 64])
+@pytest.mark.parametrize("n,m", [(3001, 1777), (257, 2049), (1, 5)])
+def test_kernel_sum_parity(uotk, d, n, m):
+    g = inputs.rng(100 + d)
+    src = g.uniform(-0.3, 0.3, (n, d)).astype(np.float32)
+    tgt = g.uniform(-0.3, 0.3, (m, d)).astype(np.float32)
+    w = g.uniform(0.1, 2.0, n).astype(np.float32)
+    eps = 0.05 * d
+    got = uotk.kernel_sum(dev(src), dev(w), dev(tgt), eps).cpu().numpy()
+    ref = oracle.ksum(f64(src), f64(w), f64(tgt), eps)
+    assert rel_err(got, ref) <= (2e-6 if d <= 3 else 5e-6)
+
+
+def test_kernel_sum_large_sampled(uotk):
+    """n = m = 2^20, d = 3 Gaussian mixture (the scale workload): 512 sampled
+    outputs against the oracle over all 2^20 sources."""
+    W = inputs.gmm3(seed=2000)
+    out = uotk.kernel_sum(dev(W.y), dev(W.b), dev(W.x), W.eps).cpu().numpy()
+    idx = inputs.subsample_rows(inputs.rng(5), 512, W.n)
+    ref = oracle.ksum(f64(W.y), f64(W.b), f64(W.x[idx]), W.eps)
+    assert rel_err(out[idx], ref) <= 2e-6
+
+
+def test_kernel_sum_edge_cases(uotk):
+    g = inputs.rng(7)
+    tgt = g.uniform(-0.3, 0.3, (100, 3)).astype(np.float32)
+    # no sources -> zeros
+    out = uotk.kernel_sum(dev(np.zeros((0, 3), np.float32)), dev(np.zeros(0, np.float32)),
+                          dev(tgt), 0.1).cpu().numpy()
+    assert np.all(out == 0)
+    # no targets -> empty
+    out = uotk.kernel_sum(dev(tgt), dev(np.ones(100, np.float32)),
+                          dev(np.zeros((0, 3), np.float32)), 0.1)
+    assert out.numel() == 0
+    # coincident points: every term is w exactly
+    src = np.repeat(tgt[:1], 1000, axis=0)
+    w = np.full(1000, 0.5, np.float32)
+    out = uotk.kernel_sum(dev(src), dev(w), dev(src[:7]), 0.1).cpu().numpy()
+    assert np.allclose(out, 500.0, rtol=1e-6)
+    # zero weights and far outliers contribute exactly zero
+    src2 = np.concatenate([tgt, tgt + 100.0]).astype(np.float32)
+    w2 = np.concatenate([np.zeros(100), np.ones(100)]).astype(np.float32)
+    out = uotk.kernel_sum(dev(src2), dev(w2), dev(tgt), 0.1).cpu().numpy()
+    assert np.all(out == 0)
+
+
+def test_kernel_sum_rejects_bad_weights(uotk):
+    g = inputs.rng(8)
+    p = dev(g.uniform(-0.3, 0.3, (64, 3)).astype(np.float32))
+    w = np.ones(64, np.float32)
+    w[5] = -1.0
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.kernel_sum(p, dev(w), p, 0.1)
+    assert e.value.status == 1
+    w[5] = np.nan
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.kernel_sum(p, dev(w), p, 0.1)
+    assert e.value.status == 5
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.kernel_sum(p, dev(np.ones(64, np.float32)), p, -1.0)
+    assert e.value.status == 1
+    q = dev(g.uniform(-0.3, 0.3, (64, 4)).astype(np.float32))
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.kernel_sum(q, dev(np.ones(64, np.float32)), q, 0.1, method="nfft")
+    assert e.value.status == 4
+
+
+def residual(b, g, rb, rg):
+    return (np.linalg.norm(b - rb) / np.linalg.norm(rb)
+            + np.linalg.norm(g - rg) / np.linalg.norm(rg))
+
+
+@pytest.mark.parametrize("ref", ["product", "counting"])
+def test_sinkhorn_uniform_box(uotk, ref):
+    """n = m = 2000, d = 2, eps = 0.05, rho = 1, 100 sweeps: duals and D(beta, gamma)."""
+    W = inputs.uniform_box()
+    r = 0 if ref == "product" else 1
+    beta, gamma, sweeps, value, _ = uotk.uot_sinkhorn(
+        dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho, max_sweeps=W.sweeps, ref=ref)
+    X, Y, A, B = f64(W.x), f64(W.y), f64(W.a), f64(W.b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=W.sweeps, ref=r)
+    assert sweeps == W.sweeps
+    res = residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg)
+    assert res <= 1e-6, res
+    v = oracle.dual_value(X, A, Y, B, W.eps, W.rho, W.rho, rb, rg, ref=r)
+    assert abs(value - v) <= 1e-6 * abs(v), (value, v)
+
+
+def test_sinkhorn_ragged_unequal_penalties_warm_start(uotk):
+    g = inputs.rng(9)
+    n, m, d = 1537, 999, 3
+    x = g.uniform(-0.3, 0.3, (n, d)).astype(np.float32)
+    y = g.uniform(-0.2, 0.35, (m, d)).astype(np.float32)
+    a = g.uniform(0.5, 1.5, n).astype(np.float32) / n
+    b = g.uniform(0.5, 1.5, m).astype(np.float32) * 1.7 / m
+    g0 = g.uniform(-0.05, 0.05, m)
+    beta, gamma, _, value, _ = uotk.uot_sinkhorn(dev(x), dev(a), dev(y), dev(b), 0.04, 0.7, 2.5,
+                                                 max_sweeps=37, gamma0=torch.from_numpy(g0))
+    rb, rg = oracle.uot_sinkhorn(f64(x), f64(a), f64(y), f64(b), 0.04, 0.7, 2.5, sweeps=37,
+                                 gamma0=g0)
+    assert residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg) <= 1e-6
+    v = oracle.dual_value(f64(x), f64(a), f64(y), f64(b), 0.04, 0.7, 2.5, rb, rg)
+    assert abs(value - v) <= 1e-6 * abs(v)
+
+
+def test_sinkhorn_constant_cost_closed_form(uotk):
+    """All x_i equal, all y_j equal: converged duals equal the closed form of Eq. (561)."""
+    n, m, lam, eta = 300, 200, 20.0, 1.0
+    x = np.tile(np.float32([0.1, -0.05]), (n, 1))
+    y = np.tile(np.float32([-0.1, 0.15]), (m, 1))
+    a = np.full(n, 1.0 / n, np.float32)
+    b = np.full(m, 1.3 / m, np.float32)
+    D = float(np.sum((f64(x[0]) - f64(y[0])) ** 2))
+    m1, m2 = f64(a).sum(), f64(b).sum()
+    den = 2 * eta + 1 / lam
+    c = np.exp(-D / den) * (m1 * m2) ** (-eta / den)
+    beta, gamma, sweeps, _, conv = uotk.uot_sinkhorn(dev(x), dev(a), dev(y), dev(b), 1 / lam, eta,
+                                                     max_sweeps=2000, tol=1e-12)
+    assert conv and sweeps < 2000
+    assert np.allclose(beta.cpu().numpy(), -eta * np.log(c * m2), atol=2e-7, rtol=0)
+    assert np.allclose(gamma.cpu().numpy(), -eta * np.log(c * m1), atol=2e-7, rtol=0)
+
+
+def test_sinkhorn_not_converged_status(uotk):
+    W = inputs.uniform_box(n=300, m=200)
+    _, _, sweeps, _, conv = uotk.uot_sinkhorn(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps,
+                                              W.rho, max_sweeps=20, tol=1e-14)
+    assert sweeps == 20 and not conv
+
+
+def test_mmd2_uniform_box(uotk):
+    W = inputs.uniform_box()
+    v, parts = uotk.mmd2(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.ell)
+    rv, rp = oracle.mmd2(f64(W.x), f64(W.a), f64(W.y), f64(W.b), W.ell, return_parts=True)
+    assert np.allclose(parts, rp, rtol=1e-6, atol=0)
+    # the FP32 sums' relative error is amplified by (A + 2B + C)/MMD^2
+    kappa = (rp[0] + 2 * rp[1] + rp[2]) / rv
+    assert abs(v - rv) <= 1e-6 * kappa * abs(rv), (v, rv, kappa)
+    z, _ = uotk.mmd2(dev(W.x), dev(W.a), dev(W.x), dev(W.a), W.ell)
+    assert abs(z) <= 1e-6 * rp[0]
+
+
+def test_sinkhorn_divergence_uniform_box(uotk):
+    W = inputs.uniform_box(n=800, m=700)
+    sd, parts = uotk.sinkhorn_divergence(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho,
+                                         max_sweeps=W.sweeps)
+    rsd, rparts = oracle.sinkhorn_divergence(f64(W.x), f64(W.a), f64(W.y), f64(W.b), W.eps, W.rho,
+                                             sweeps=W.sweeps, return_parts=True)
+    assert np.allclose(parts, rparts, rtol=1e-6, atol=0)
+    kappa = sum(abs(p) for p in rparts) / abs(rsd)
+    assert abs(sd - rsd) <= 1e-6 * kappa * abs(rsd), (sd, rsd, kappa)
