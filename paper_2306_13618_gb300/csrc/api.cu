@@ -175,7 +175,7 @@ uotk_status uotk_create(uotk_ctx** out, int device) {
     delete ctx;
     return UOTK_ERR_CUDA;
   }
-  if (cudaMallocHost(reinterpret_cast<void**>(&ctx->host), 64 * sizeof(double)) != cudaSuccess ||
+  if (cudaMallocHost(reinterpret_cast<void**>(&ctx->host), 128 * sizeof(double)) != cudaSuccess ||
       cudaMalloc(reinterpret_cast<void**>(&ctx->dflags), NUM_FLAGS * sizeof(long long)) !=
           cudaSuccess) {
     cudaGetLastError();

@@ -1,0 +1,94 @@
+// NFFT fast summation (Sec. 4, Eq. 1724) for the Gaussian kernel: shared
+// declarations of the plan, the binned point sets and the stage kernels.
+//
+// Torus coordinates (Eq. boundaries, translated by 1/2): u = (p - c)/h + 1/2,
+// grid node l at u = l/n.  In grid units t = u*n the point sits in cell
+// floor(t) with fraction delta = t - floor(t), and the window touches the 2m
+// nodes floor(t) - m + 1 + k, k = 0..2m-1, at distance v = delta + m - 1 - k.
+// Grids are n^3 FP32, layout [z][y][x]; d < 3 is embedded in 3-D with the
+// missing coordinates at the centre (their 1-D kernel factor is the constant 1).
+#pragma once
+
+#include "engine.cuh"
+
+namespace uotk {
+
+constexpr int NFFT_TILE = 16;          // grid cells per tile edge (binning granularity)
+constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
+constexpr int NFFT_MAX_M = 8;
+
+struct NfftParams {
+  int d = 3;
+  int n = 128;         // oversampled grid
+  int N = 64;          // bandwidth
+  int m = 6;           // window cut-off
+  float c[3] = {0, 0, 0};
+  float inv_h = 1.f;
+  double h = 1.0;
+  double eps = 1.0;
+  float b = 0.f;       // Kaiser-Bessel shape pi (2 - 1/sigma)
+  int tiles1 = 8;      // tiles per dimension = n / NFFT_TILE
+  int E = 27;          // smem block edge = NFFT_TILE + 2m - 1
+};
+
+// Host: choose h, m; fill params (bounding box given).
+uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const float hi[3], double eps,
+                             const uotk_sum_opts* opts, NfftParams* P);
+// Host: 1-D factors g(k) of scale_k = prod_t g_t(k_t), k in {-N/2..N/2-1}
+// (FP64 -> FP32 table of 3*N floats, one row per dimension).
+void nfft_scale_table(const NfftParams& P, float* host_table /* 3*N */);
+
+// A point set binned by tile: sorted cells/fractions, window weights, permutation.
+struct NfftPoints {
+  int64_t n = 0;
+  int4* cell = nullptr;      // sorted: (cx | cy<<10 | cz<<20, frac x, y, z as float bits)
+  float* win = nullptr;      // sorted: [n][3][2m] window weights
+  int* perm = nullptr;       // sorted position -> caller index
+  int* tile_start = nullptr; // [tiles+1] start of each tile in sorted order
+  int* unit_tile = nullptr;  // [max_units] tile of each work unit
+  int* unit_begin = nullptr; // [max_units] first sorted point of the unit
+  int* unit_count = nullptr; // [max_units]
+  int* num_units = nullptr;  // [1] device count
+  int* tile_unit_start = nullptr;  // [tiles+1] first unit of each tile
+  int max_units = 0;
+  int* scratch = nullptr;    // [tiles] counters
+};
+size_t nfft_points_bytes(const NfftParams& P, int64_t n);
+void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S);
+// Bin, sort and precompute windows for caller-order points (n x d FP32).
+uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                              const float* pts, int64_t n, NfftPoints& S);
+
+// Work buffers of one summation.
+struct NfftWork {
+  float* part = nullptr;   // [max_units(src)][E^3] spread blocks
+  float* grid = nullptr;   // [n^3] real grid
+  float2* cgrid = nullptr; // [n^3] complex work grid
+  float* scale = nullptr;  // [3*N] device table
+};
+size_t nfft_work_bytes(const NfftParams& P, int max_src_units);
+void nfft_work_carve(Carver& cv, const NfftParams& P, int max_src_units, NfftWork& W);
+
+// Weights of the spread: w_i = base_i * exp(lam*pot_i - shift) (sorted order),
+// or plain w_i when pot == NULL (base required).
+struct SpreadWeights {
+  const float* base = nullptr;
+  const double* pot = nullptr;
+  double lam = 0.0;
+  const long long* shift_slot = nullptr;
+};
+
+uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
+                        const SpreadWeights& w, NfftWork& W, float* grid_out);
+uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W,
+                          const float* grid_in, float* grid_out);
+uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
+                        const float* grid, float* out_sorted);
+
+// Bounding box of point clouds on the device -> host (synchronises).
+uotk_status nfft_bbox(uotk_ctx* ctx, cudaStream_t s, int d, const float* a, int64_t na,
+                      const float* b, int64_t nb, float lo[3], float hi[3]);
+
+int nfft_max_units(const NfftParams& P, int64_t n);
+
+}  // namespace uotk

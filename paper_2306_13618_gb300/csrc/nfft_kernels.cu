@@ -1,0 +1,373 @@
+// NFFT stage kernels (Sec. 4, Eq. 1724): spread (adjoint NFFT step 1), the
+// grid convolution (FFT, multiply by b_k and the double deconvolution,
+// inverse FFT) and gather (NFFT final step).
+//
+// Spread.  Points are sorted by tile (16^3 cells).  A work unit is (tile, up to
+// NFFT_UNIT_POINTS points); its CTA accumulates the windows of its points into
+// an E^3 shared-memory block (E = 16 + 2m - 1, the tile plus the window halo)
+// and writes the block out whole.  A fold kernel then adds, for every grid
+// node, the blocks that cover it in unit order -- a fixed order, so the grid
+// does not depend on scheduling between units.
+// Gather.  The CTA of a unit stages the E^3 block of the grid around its tile
+// in shared memory; a warp evaluates one target: lanes split the (2m)^2 (y, x)
+// pairs of the footprint, loop over the 2m z-planes, and reduce by shuffles.
+// FFT.  Radix-2 decimation-in-time on lines of n <= 256 complex values in
+// shared memory (bit-reversed load, log2 n butterfly stages), 16 lines per CTA,
+// lines adjacent in memory so every load and store is coalesced; passes along
+// x, y, z.  The z pass multiplies by scale_k (zero outside I_N^3) between its
+// forward and inverse transforms.
+#include <math.h>
+
+#include "nfft.cuh"
+
+namespace uotk {
+
+namespace {
+
+constexpr int FFT_LINES = 16;
+constexpr int FFT_THREADS = 256;
+
+// ---------------------------------------------------------------- spread ----
+__global__ void __launch_bounds__(384)
+    k_spread(const int4* __restrict__ cell, const float* __restrict__ win,
+             const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
+             const int* __restrict__ unit_count, const int* __restrict__ num_units, int m,
+             int tiles1, int E, const float* __restrict__ base, const double* __restrict__ pot,
+             double lam, const long long* __restrict__ shift_slot, float* __restrict__ part) {
+  extern __shared__ float blk[];  // [E][E][E]
+  const int u = blockIdx.x;
+  if (u >= *num_units) return;
+  const int E3 = E * E * E;
+  for (int i = threadIdx.x; i < E3; i += blockDim.x) blk[i] = 0.f;
+  const int tile = unit_tile[u];
+  const int tx0 = (tile % tiles1) * NFFT_TILE;
+  const int ty0 = ((tile / tiles1) % tiles1) * NFFT_TILE;
+  const int tz0 = (tile / (tiles1 * tiles1)) * NFFT_TILE;
+  const int w2 = 2 * m, w22 = w2 * w2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  // (ky, kx) pairs of this lane: c = lane + 32 it
+  int off[8];
+  int nit = 0;
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int c = lane + 32 * it;
+    off[it] = c < w22 ? (c / w2) * E + (c % w2) : -1;
+    if (c < w22) nit = it + 1;
+  }
+  const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
+  __syncthreads();
+  const int b0 = unit_begin[u], cnt = unit_count[u];
+  for (int p = warp; p < cnt; p += nwarps) {
+    const int q = b0 + p;
+    const int4 c = cell[q];
+    const int bx = (c.x & 1023) - tx0, by = ((c.x >> 10) & 1023) - ty0, bz = (c.x >> 20) - tz0;
+    double wd = base ? (double)base[q] : 1.0;
+    if (pot) wd *= exp(lam * pot[q] - shift);
+    const float w = (float)wd;
+    const float* wq = win + (size_t)q * 3 * w2;
+    float pxy[8];
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      const int cc = lane + 32 * it;
+      pxy[it] = it < nit && cc < w22 ? wq[cc % w2] * wq[w2 + cc / w2] : 0.f;
+    }
+    float* dst = blk + (bz * E + by) * E + bx;
+    for (int kz = 0; kz < w2; ++kz) {
+      const float wz = w * wq[2 * w2 + kz];
+      float* plane = dst + kz * E * E;
+#pragma unroll
+      for (int it = 0; it < 8; ++it)
+        if (it < nit && off[it] >= 0) atomicAdd(plane + off[it], wz * pxy[it]);
+    }
+  }
+  __syncthreads();
+  float* out = part + (size_t)u * E3;
+  for (int i = threadIdx.x; i < E3; i += blockDim.x) out[i] = blk[i];
+}
+
+// Grid node g (per dimension) is covered by block (tile t, local l) when
+// l = g - t*16 + m - 1 (mod n) + r n lies in [0, E).
+__device__ __forceinline__ int covers(int g, int n, int tiles1, int m, int E, int* tl, int* ll) {
+  int k = 0;
+  for (int t = 0; t < tiles1 && k < 8; ++t) {
+    int l = g - t * NFFT_TILE + m - 1;
+    l %= n;
+    if (l < 0) l += n;
+    for (; l < E && k < 8; l += n) { tl[k] = t; ll[k] = l; ++k; }
+  }
+  return k;
+}
+
+__global__ void k_fold(const float* __restrict__ part, const int* __restrict__ tile_unit_start,
+                       int n, int tiles1, int m, int E, float* __restrict__ grid) {
+  const long long total = (long long)n * n * n;
+  const long long E2 = (long long)E * E, E3 = E2 * E;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int gx = (int)(i % n), gy = (int)((i / n) % n), gz = (int)(i / ((long long)n * n));
+    int txl[8], lxl[8], tyl[8], lyl[8], tzl[8], lzl[8];
+    const int nx = covers(gx, n, tiles1, m, E, txl, lxl);
+    const int ny = covers(gy, n, tiles1, m, E, tyl, lyl);
+    const int nz = covers(gz, n, tiles1, m, E, tzl, lzl);
+    float acc = 0.f;
+    for (int a = 0; a < nz; ++a)
+      for (int b = 0; b < ny; ++b)
+        for (int c = 0; c < nx; ++c) {
+          const int tile = (tzl[a] * tiles1 + tyl[b]) * tiles1 + txl[c];
+          const long long loc = ((long long)lzl[a] * E + lyl[b]) * E + lxl[c];
+          for (int u = tile_unit_start[tile]; u < tile_unit_start[tile + 1]; ++u)
+            acc += part[(long long)u * E3 + loc];
+        }
+    grid[i] = acc;
+  }
+}
+
+// ------------------------------------------------------------------ FFT ----
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// In-place radix-2 DIT on FFT_LINES lines of length n held in bit-reversed
+// order in `buf` ([line][n]); tw[j] = exp(-2 pi i j / n), j < n/2; dir = +1
+// uses the conjugate twiddles (inverse, unnormalised).
+__device__ void fft_lines_smem(float2* buf, const float2* tw, int n, int logn, int dir) {
+  const int half_total = FFT_LINES * (n >> 1);
+  for (int s = 1; s <= logn; ++s) {
+    const int half = 1 << (s - 1);
+    const int tstep = n >> s;
+    for (int b = threadIdx.x; b < half_total; b += blockDim.x) {
+      const int line = b / (n >> 1);
+      const int j = b - line * (n >> 1);
+      const int grp = j >> (s - 1);
+      const int pos = j & (half - 1);
+      const int i0 = line * n + grp * 2 * half + pos;
+      const int i1 = i0 + half;
+      float2 w = tw[pos * tstep];
+      if (dir > 0) w.y = -w.y;
+      const float2 t = cmul(w, buf[i1]);
+      const float2 a = buf[i0];
+      buf[i0] = make_float2(a.x + t.x, a.y + t.y);
+      buf[i1] = make_float2(a.x - t.x, a.y - t.y);
+    }
+    __syncthreads();
+  }
+}
+
+__device__ __forceinline__ void load_twiddles(float2* tw, int n) {
+  for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
+    float sn, cs;
+    sincospif(-2.0f * (float)j / (float)n, &sn, &cs);
+    tw[j] = make_float2(cs, sn);
+  }
+}
+
+// Line geometry: axis 0 = x (lines are rows), 1 = y, 2 = z.  Line L, element e.
+__device__ __forceinline__ long long line_addr(int axis, int n, long long L, int e) {
+  const long long n2 = (long long)n * n;
+  if (axis == 0) return L * n + e;
+  if (axis == 1) return (L / n) * n2 + (long long)e * n + (L % n);
+  return (long long)e * n2 + L;
+}
+
+// One FFT pass along `axis`.  mode 0: real in -> complex out (forward);
+// mode 1: complex -> complex; mode 2: complex in -> real part out (inverse);
+// mode 3: z pass: forward, multiply by scale_k on I_N^3, inverse.
+__global__ void __launch_bounds__(FFT_THREADS)
+    k_fft_pass(const float* __restrict__ rin, const float2* __restrict__ cin,
+               float* __restrict__ rout, float2* __restrict__ cout, int n, int logn, int axis,
+               int mode, int dir, const float* __restrict__ scale, int N) {
+  extern __shared__ float2 sh[];
+  float2* tw = sh;
+  float2* buf = sh + n / 2;
+  load_twiddles(tw, n);
+  const long long L0 = (long long)blockIdx.x * FFT_LINES;
+  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
+    // consecutive threads take consecutive lines for y/z passes (coalesced),
+    // consecutive elements for x passes
+    int line, e;
+    if (axis == 0) { line = i / n; e = i - line * n; }
+    else { e = i / FFT_LINES; line = i - e * FFT_LINES; }
+    const long long a = line_addr(axis, n, L0 + line, e);
+    const float2 v = mode == 0 ? make_float2(rin[a], 0.f) : cin[a];
+    buf[line * n + (__brev(e) >> (32 - logn))] = v;
+  }
+  __syncthreads();
+  fft_lines_smem(buf, tw, n, logn, mode == 3 ? -1 : dir);
+  if (mode == 3) {
+    // multiply by scale_k: line L = y*n + x carries (kx, ky); element = kz
+    for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
+      const int line = i / n, e = i - line * n;
+      const long long L = L0 + line;
+      const int x = (int)(L % n), y = (int)(L / n);
+      const int kx = x < n / 2 ? x : x - n, ky = y < n / 2 ? y : y - n, kz = e < n / 2 ? e : e - n;
+      float f = 0.f;
+      if (kx >= -N / 2 && kx < N / 2 && ky >= -N / 2 && ky < N / 2 && kz >= -N / 2 && kz < N / 2)
+        f = scale[kx + N / 2] * scale[N + ky + N / 2] * scale[2 * N + kz + N / 2];
+      const float2 v = buf[i];
+      buf[i] = make_float2(v.x * f, v.y * f);
+    }
+    __syncthreads();
+    // bit-reverse in place for the inverse transform
+    for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
+      const int line = i / n, e = i - line * n;
+      const int r = __brev(e) >> (32 - logn);
+      if (r > e) {
+        const float2 t = buf[line * n + e];
+        buf[line * n + e] = buf[line * n + r];
+        buf[line * n + r] = t;
+      }
+    }
+    __syncthreads();
+    fft_lines_smem(buf, tw, n, logn, +1);
+  }
+  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
+    int line, e;
+    if (axis == 0) { line = i / n; e = i - line * n; }
+    else { e = i / FFT_LINES; line = i - e * FFT_LINES; }
+    const long long a = line_addr(axis, n, L0 + line, e);
+    const float2 v = buf[line * n + e];
+    if (mode == 2) rout[a] = v.x;
+    else cout[a] = v;
+  }
+}
+
+// ---------------------------------------------------------------- gather ----
+__global__ void __launch_bounds__(384)
+    k_gather(const int4* __restrict__ cell, const float* __restrict__ win,
+             const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
+             const int* __restrict__ unit_count, const int* __restrict__ num_units, int m, int n,
+             int tiles1, int E, const float* __restrict__ grid, float* __restrict__ out) {
+  extern __shared__ float blk[];
+  const int u = blockIdx.x;
+  if (u >= *num_units) return;
+  const int tile = unit_tile[u];
+  const int tx0 = (tile % tiles1) * NFFT_TILE;
+  const int ty0 = ((tile / tiles1) % tiles1) * NFFT_TILE;
+  const int tz0 = (tile / (tiles1 * tiles1)) * NFFT_TILE;
+  const int E2 = E * E, E3 = E2 * E;
+  for (int i = threadIdx.x; i < E3; i += blockDim.x) {
+    const int lz = i / E2, ly = (i / E) % E, lx = i % E;
+    int gz = (tz0 - m + 1 + lz) % n, gy = (ty0 - m + 1 + ly) % n, gx = (tx0 - m + 1 + lx) % n;
+    gz += gz < 0 ? n : 0; gy += gy < 0 ? n : 0; gx += gx < 0 ? n : 0;
+    blk[i] = grid[((long long)gz * n + gy) * n + gx];
+  }
+  __syncthreads();
+  const int w2 = 2 * m, w22 = w2 * w2;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  int off[8];
+  int nit = 0;
+#pragma unroll
+  for (int it = 0; it < 8; ++it) {
+    const int c = lane + 32 * it;
+    off[it] = c < w22 ? (c / w2) * E + (c % w2) : -1;
+    if (c < w22) nit = it + 1;
+  }
+  const int b0 = unit_begin[u], cnt = unit_count[u];
+  for (int p = warp; p < cnt; p += nwarps) {
+    const int q = b0 + p;
+    const int4 c = cell[q];
+    const int bx = (c.x & 1023) - tx0, by = ((c.x >> 10) & 1023) - ty0, bz = (c.x >> 20) - tz0;
+    const float* wq = win + (size_t)q * 3 * w2;
+    const float* src = blk + (bz * E + by) * E + bx;
+    float acc = 0.f;
+#pragma unroll
+    for (int it = 0; it < 8; ++it) {
+      if (it < nit && off[it] >= 0) {
+        const int cc = lane + 32 * it;
+        const float pxy = wq[cc % w2] * wq[w2 + cc / w2];
+        float col = 0.f;
+        for (int kz = 0; kz < w2; ++kz) col = fmaf(wq[2 * w2 + kz], src[kz * E2 + off[it]], col);
+        acc = fmaf(pxy, col, acc);
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) out[q] = acc;
+  }
+}
+
+int spread_threads(int m) { return 32 * (m <= 6 ? 12 : 12); }
+
+}  // namespace
+
+uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
+                        const SpreadWeights& w, NfftWork& W, float* grid_out) {
+  const size_t smem = (size_t)P.E * P.E * P.E * sizeof(float);
+  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  if (S.n > 0) {
+    UOTK_PROF(ctx, s, "spread");
+    k_spread<<<S.max_units, spread_threads(P.m), smem, s>>>(
+        S.cell, S.win, S.unit_tile, S.unit_begin, S.unit_count, S.num_units, P.m, P.tiles1, P.E,
+        w.base, w.pot, w.lam, w.shift_slot, W.part);
+    UOTK_LAUNCHED(ctx);
+  }
+  {
+    UOTK_PROF(ctx, s, "fold");
+    const long long total = (long long)P.n * P.n * P.n;
+    if (S.n > 0) {
+      k_fold<<<grid_for(ctx, total, 256, 8), 256, 0, s>>>(W.part, S.tile_unit_start, P.n, P.tiles1,
+                                                          P.m, P.E, grid_out);
+      UOTK_LAUNCHED(ctx);
+    } else {
+      UOTK_CUDA(ctx, cudaMemsetAsync(grid_out, 0, sizeof(float) * total, s));
+    }
+  }
+  return UOTK_OK;
+}
+
+uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W,
+                          const float* grid_in, float* grid_out) {
+  const int n = P.n;
+  int logn = 0;
+  while ((1 << logn) < n) ++logn;
+  const int blocks = n * n / FFT_LINES;
+  const size_t smem = sizeof(float2) * (n / 2 + FFT_LINES * n);
+  UOTK_PROF(ctx, s, "fft");
+  // forward x (real -> complex), forward y, z (forward, scale, inverse), inverse y, inverse x
+  k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(grid_in, nullptr, nullptr, W.cgrid, n, logn, 0, 0,
+                                               -1, nullptr, P.N);
+  UOTK_LAUNCHED(ctx);
+  k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 1, 1,
+                                               -1, nullptr, P.N);
+  UOTK_LAUNCHED(ctx);
+  k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 2, 3,
+                                               -1, W.scale, P.N);
+  UOTK_LAUNCHED(ctx);
+  k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 1, 1,
+                                               +1, nullptr, P.N);
+  UOTK_LAUNCHED(ctx);
+  k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, grid_out, nullptr, n, logn, 0, 2,
+                                               +1, nullptr, P.N);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
+                        const float* grid, float* out_sorted) {
+  if (S.n == 0) return UOTK_OK;
+  const size_t smem = (size_t)P.E * P.E * P.E * sizeof(float);
+  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  UOTK_PROF(ctx, s, "gather");
+  k_gather<<<S.max_units, 384, smem, s>>>(S.cell, S.win, S.unit_tile, S.unit_begin, S.unit_count,
+                                          S.num_units, P.m, P.n, P.tiles1, P.E, grid, out_sorted);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+size_t nfft_work_bytes(const NfftParams& P, int max_src_units) {
+  Carver cv(nullptr);
+  NfftWork W;
+  nfft_work_carve(cv, P, max_src_units, W);
+  return cv.off;
+}
+
+void nfft_work_carve(Carver& cv, const NfftParams& P, int max_src_units, NfftWork& W) {
+  const size_t n3 = (size_t)P.n * P.n * P.n;
+  W.part = cv.take<float>((size_t)(max_src_units > 0 ? max_src_units : 1) * P.E * P.E * P.E);
+  W.grid = cv.take<float>(n3);
+  W.cgrid = cv.take<float2>(n3);
+  W.scale = cv.take<float>(3 * P.N);
+}
+
+}  // namespace uotk

@@ -1,0 +1,382 @@
+// NFFT plan and point preprocessing (Sec. 4): torus scaling, the Kaiser-Bessel
+// window and its Fourier coefficients, the Gaussian's Fourier coefficients
+// b_k, binning of the points by grid tile, and the per-point window weights.
+#include <math.h>
+
+#include "nfft.cuh"
+
+namespace uotk {
+
+namespace {
+
+// I_0(x) = sum_j ((x/2)^j / j!)^2, summed in FP64 until the terms vanish.
+double bessel_i0(double x) {
+  const double q = 0.25 * x * x;
+  double term = 1.0, sum = 1.0;
+  for (int j = 1; j < 500; ++j) {
+    term *= q / ((double)j * (double)j);
+    sum += term;
+    if (term < 1e-18 * sum) break;
+  }
+  return sum;
+}
+
+// Upper bound of the Kaiser-Bessel window error for cut-off m and oversampling
+// sigma (the standard bound of the NFFT literature), relative to sum |w|.
+double kb_error_bound(int m, double sigma) {
+  const double r = sqrt(1.0 - 1.0 / sigma);
+  return 4.0 * M_PI * (sqrt((double)m) + m) * sqrt(r) * exp(-2.0 * M_PI * m * r);
+}
+
+__global__ void k_bbox(const float* __restrict__ p, long long n, int d, long long* __restrict__ slots) {
+  float mx[3] = {-INFINITY, -INFINITY, -INFINITY}, mn[3] = {INFINITY, INFINITY, INFINITY};
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    for (int t = 0; t < d; ++t) {
+      const float v = p[i * d + t];
+      mx[t] = fmaxf(mx[t], v);
+      mn[t] = fminf(mn[t], v);
+    }
+  for (int t = 0; t < d; ++t) {
+    double a = mx[t], b = -(double)mn[t];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a = fmax(a, __shfl_xor_sync(0xffffffffu, a, o));
+      b = fmax(b, __shfl_xor_sync(0xffffffffu, b, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+      atomicMax(&slots[t], dbl_to_ordered(a));
+      atomicMax(&slots[3 + t], dbl_to_ordered(b));
+    }
+  }
+}
+
+__global__ void k_bbox_reset(long long* slots) {
+  if (threadIdx.x < 6) slots[threadIdx.x] = ORDERED_NEG_INF;
+}
+
+struct CellRule {
+  float c[3];
+  float inv_h;
+  int n, d;
+};
+
+// Cell and fraction of one point by the FP32 rule of the header, one IEEE
+// rounding per operation (no contraction).
+__device__ __forceinline__ void cell_of(const float* __restrict__ p, const CellRule& R, int cell[3],
+                                        float frac[3]) {
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const float x = t < R.d ? p[t] : R.c[t];
+    float v = __fsub_rn(x, R.c[t]);
+    v = __fmul_rn(v, R.inv_h);
+    v = __fadd_rn(v, 0.5f);
+    v = __fmul_rn(v, (float)R.n);
+    const float fl = floorf(v);
+    frac[t] = __fsub_rn(v, fl);
+    int ci = (int)fl % R.n;
+    cell[t] = ci < 0 ? ci + R.n : ci;
+  }
+}
+
+__global__ void k_cells(const float* __restrict__ pts, long long n, CellRule R,
+                        int* __restrict__ out) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    float f[3];
+    cell_of(pts + i * R.d, R, c, f);
+    out[3 * i] = c[0];
+    out[3 * i + 1] = c[1];
+    out[3 * i + 2] = c[2];
+  }
+}
+
+__global__ void k_bin_count(const float* __restrict__ pts, long long n, CellRule R, int tiles1,
+                            int4* __restrict__ tmp_cell, int* __restrict__ tmp_tile,
+                            int* __restrict__ count) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    float f[3];
+    cell_of(pts + i * R.d, R, c, f);
+    const int tile = ((c[2] / NFFT_TILE) * tiles1 + c[1] / NFFT_TILE) * tiles1 + c[0] / NFFT_TILE;
+    tmp_tile[i] = tile;
+    tmp_cell[i] = make_int4(c[0] | (c[1] << 10) | (c[2] << 20), __float_as_int(f[0]),
+                            __float_as_int(f[1]), __float_as_int(f[2]));
+    atomicAdd(&count[tile], 1);
+  }
+}
+
+// Single block: exclusive scans of points and of work units per tile.
+__global__ void k_bin_scan(int* __restrict__ count, int tiles, int unit_pts,
+                           int* __restrict__ tile_start, int* __restrict__ tile_unit_start,
+                           int* __restrict__ num_units) {
+  __shared__ int sp[1024], su[1024];
+  __shared__ int carry_p, carry_u;
+  if (threadIdx.x == 0) { carry_p = 0; carry_u = 0; }
+  __syncthreads();
+  for (int base = 0; base < tiles; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int c = i < tiles ? count[i] : 0;
+    sp[threadIdx.x] = c;
+    su[threadIdx.x] = (c + unit_pts - 1) / unit_pts;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int a = threadIdx.x >= o ? sp[threadIdx.x - o] : 0;
+      const int b = threadIdx.x >= o ? su[threadIdx.x - o] : 0;
+      __syncthreads();
+      sp[threadIdx.x] += a;
+      su[threadIdx.x] += b;
+      __syncthreads();
+    }
+    if (i < tiles) {
+      tile_start[i] = carry_p + sp[threadIdx.x] - c;
+      tile_unit_start[i] = carry_u + su[threadIdx.x] - (c + unit_pts - 1) / unit_pts;
+      count[i] = 0;  // reused as the scatter cursor
+    }
+    __syncthreads();
+    if (threadIdx.x == 1023) { carry_p += sp[1023]; carry_u += su[1023]; }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    tile_start[tiles] = carry_p;
+    tile_unit_start[tiles] = carry_u;
+    *num_units = carry_u;
+  }
+}
+
+__global__ void k_bin_scatter(const int4* __restrict__ tmp_cell, const int* __restrict__ tmp_tile,
+                              long long n, const int* __restrict__ tile_start,
+                              int* __restrict__ cursor, int4* __restrict__ cell,
+                              int* __restrict__ perm) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int t = tmp_tile[i];
+    const int pos = tile_start[t] + atomicAdd(&cursor[t], 1);
+    cell[pos] = tmp_cell[i];
+    perm[pos] = (int)i;
+  }
+}
+
+__global__ void k_make_units(const int* __restrict__ tile_start,
+                             const int* __restrict__ tile_unit_start, int tiles, int unit_pts,
+                             int* __restrict__ unit_tile, int* __restrict__ unit_begin,
+                             int* __restrict__ unit_count) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+    const int b = tile_start[t], e = tile_start[t + 1];
+    int u = tile_unit_start[t];
+    for (int p = b; p < e; p += unit_pts, ++u) {
+      unit_tile[u] = t;
+      unit_begin[u] = p;
+      unit_count[u] = min(unit_pts, e - p);
+    }
+  }
+}
+
+// Normalised Kaiser-Bessel window at distance v (grid units, |v| < m):
+// phi(v)/phi(0) = (m/s) e^{b(s-m)} (1 - e^{-2bs}) / (1 - e^{-2bm}),  s = sqrt(m^2 - v^2).
+__device__ __forceinline__ float kb_window(float v, int m, float b) {
+  const float mf = (float)m;
+  const float s2 = fmaxf(mf * mf - v * v, 0.f);
+  const float s = sqrtf(s2);
+  const float den = -expm1f(-2.f * b * mf);
+  if (s < 1e-4f) return mf * 2.f * b * expf(-b * mf) / den;
+  return mf * expf(b * (s - mf)) * (-expm1f(-2.f * b * s)) / (s * den);
+}
+
+__global__ void k_windows(const int4* __restrict__ cell, long long n, int m, float b,
+                          int d, float* __restrict__ win) {
+  const int w2 = 2 * m;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * 3 * w2;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / (3 * w2);
+    const int r = (int)(i - q * 3 * w2);
+    const int t = r / w2, k = r - t * w2;
+    const int4 c = cell[q];
+    const float f = __int_as_float(t == 0 ? c.y : (t == 1 ? c.z : c.w));
+    const float v = f + (float)(m - 1 - k);
+    win[i] = kb_window(v, m, b);
+  }
+}
+
+}  // namespace
+
+int nfft_max_units(const NfftParams& P, int64_t n) {
+  const int64_t tiles = (int64_t)P.tiles1 * P.tiles1 * P.tiles1;
+  return (int)((n + NFFT_UNIT_POINTS - 1) / NFFT_UNIT_POINTS + (n < tiles ? n : tiles));
+}
+
+uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const float hi[3],
+                             double eps, const uotk_sum_opts* opts, NfftParams* P) {
+  P->d = d;
+  P->n = (opts && opts->grid) ? opts->grid : 128;
+  P->N = (opts && opts->bandwidth) ? opts->bandwidth : P->n / 2;
+  P->eps = eps;
+  const double sigma = (double)P->n / P->N;
+  P->b = (float)(M_PI * (2.0 - 1.0 / sigma));
+  double L = 0.0;
+  for (int t = 0; t < 3; ++t) {
+    if (t < d) {
+      P->c[t] = (float)(0.5 * ((double)lo[t] + (double)hi[t]));
+      L = fmax(L, (double)hi[t] - (double)lo[t]);
+    } else {
+      P->c[t] = 0.f;
+    }
+  }
+  if (!isfinite(L)) return set_error(ctx, UOTK_ERR_NONFINITE, "NFFT plan: non-finite coordinates");
+  const double target = (opts && opts->target_err > 0) ? opts->target_err : 1e-6;
+  if (opts && opts->period > 0) {
+    P->h = opts->period;
+  } else {
+    // Balance the periodisation error exp(-(h-L)^2/eps) against the Fourier
+    // truncation error exp(-pi^2 eps N^2 / (4 h^2)): h (h - L) = pi eps N / 2.
+    P->h = 0.5 * (L + sqrt(L * L + 2.0 * M_PI * eps * P->N));
+    const double e1 = (P->h - L) * (P->h - L) / eps;
+    if (exp(-e1) > 0.1 * target)
+      return set_error(ctx, UOTK_ERR_UNSUPPORTED,
+                       "NFFT: bandwidth %d too small for eps %g over a point spread of %g "
+                       "(estimated error %.1e > target %.1e); raise grid/bandwidth", P->N, eps, L,
+                       exp(-e1), target);
+  }
+  // the kernels scale by the FP32 value inv_h; h is its exact reciprocal, so the
+  // Fourier coefficients b_k describe the scaling actually applied
+  P->inv_h = (float)(1.0 / P->h);
+  P->h = 1.0 / (double)P->inv_h;
+  if (opts && opts->cutoff) {
+    P->m = opts->cutoff;
+  } else {
+    P->m = 8;
+    for (int m = 6; m <= 8; ++m)
+      if (kb_error_bound(m, sigma) <= target) { P->m = m; break; }
+  }
+  if (2 * P->m > P->n) return set_error(ctx, UOTK_ERR_INVALID, "NFFT: 2m > grid");
+  P->tiles1 = P->n / NFFT_TILE;
+  P->E = NFFT_TILE + 2 * P->m - 1;
+  return UOTK_OK;
+}
+
+void nfft_scale_table(const NfftParams& P, float* table) {
+  // scale_k = b_k / prod_t (n phihat_s(k_t))^2 is separable: row t holds
+  // g_t(k) = sqrt(pi eps)/h exp(-pi^2 eps k^2/h^2) / (n phihat_s(k))^2 for a real
+  // dimension, and [k == 0] / (n phihat_s(0))^2 for an embedded one (constant 1).
+  // n phihat_s(k) = I_0(m sqrt(b^2 - (2 pi k/n)^2)) * pi m / sinh(b m).
+  const double b = M_PI * (2.0 - (double)P.N / P.n);
+  const double m = P.m;
+  const double sh = sinh(b * m);
+  for (int t = 0; t < 3; ++t)
+    for (int i = 0; i < P.N; ++i) {
+      const double k = i - P.N / 2;
+      const double arg = b * b - pow(2.0 * M_PI * k / P.n, 2);
+      const double nph = bessel_i0(m * sqrt(arg > 0 ? arg : 0.0)) * M_PI * m / sh;
+      double g;
+      if (t < P.d)
+        g = sqrt(M_PI * P.eps) / P.h * exp(-M_PI * M_PI * P.eps * k * k / (P.h * P.h)) / (nph * nph);
+      else
+        g = (i == P.N / 2) ? 1.0 / (nph * nph) : 0.0;
+      table[t * P.N + i] = (float)g;
+    }
+}
+
+uotk_status nfft_bbox(uotk_ctx* ctx, cudaStream_t s, int d, const float* a, int64_t na,
+                      const float* b, int64_t nb, float lo[3], float hi[3]) {
+  long long* slots = ctx->dflags + FLAG_BBOX;
+  k_bbox_reset<<<1, 32, 0, s>>>(slots);
+  UOTK_LAUNCHED(ctx);
+  if (na > 0) {
+    k_bbox<<<grid_for(ctx, na, 256, 4), 256, 0, s>>>(a, na, d, slots);
+    UOTK_LAUNCHED(ctx);
+  }
+  if (nb > 0) {
+    k_bbox<<<grid_for(ctx, nb, 256, 4), 256, 0, s>>>(b, nb, d, slots);
+    UOTK_LAUNCHED(ctx);
+  }
+  long long* h = reinterpret_cast<long long*>(ctx->host + 96);
+  UOTK_CUDA(ctx, cudaMemcpyAsync(h, slots, 6 * sizeof(long long), cudaMemcpyDeviceToHost, s));
+  UOTK_CUDA(ctx, cudaStreamSynchronize(s));
+  for (int t = 0; t < 3; ++t) {
+    if (t < d) {
+      hi[t] = (float)ordered_to_dbl(h[t]);
+      lo[t] = (float)(-ordered_to_dbl(h[3 + t]));
+    } else {
+      hi[t] = lo[t] = 0.f;
+    }
+  }
+  return UOTK_OK;
+}
+
+size_t nfft_points_bytes(const NfftParams& P, int64_t n) {
+  Carver cv(nullptr);
+  NfftPoints S;
+  nfft_points_carve(cv, P, n, S);
+  return cv.off;
+}
+
+void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S) {
+  const int tiles = P.tiles1 * P.tiles1 * P.tiles1;
+  const int64_t nn = n > 0 ? n : 1;
+  S.n = n;
+  S.max_units = nfft_max_units(P, n);
+  S.cell = cv.take<int4>(nn);
+  S.win = cv.take<float>((size_t)nn * 3 * 2 * P.m);
+  S.perm = cv.take<int>(nn);
+  S.tile_start = cv.take<int>(tiles + 1);
+  S.tile_unit_start = cv.take<int>(tiles + 1);
+  S.unit_tile = cv.take<int>(S.max_units + 1);
+  S.unit_begin = cv.take<int>(S.max_units + 1);
+  S.unit_count = cv.take<int>(S.max_units + 1);
+  S.num_units = cv.take<int>(1);
+  S.scratch = cv.take<int>(tiles);
+  // temporaries of the build (caller order)
+  cv.take<int4>(nn);
+  cv.take<int>(nn);
+}
+
+uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                              const float* pts, int64_t n, NfftPoints& S) {
+  const int tiles = P.tiles1 * P.tiles1 * P.tiles1;
+  // the temporaries sit right after `scratch` (see nfft_points_carve)
+  Carver cv(reinterpret_cast<char*>(S.scratch));
+  cv.take<int>(tiles);
+  int4* tmp_cell = cv.take<int4>(n > 0 ? n : 1);
+  int* tmp_tile = cv.take<int>(n > 0 ? n : 1);
+  CellRule R{{P.c[0], P.c[1], P.c[2]}, P.inv_h, P.n, P.d};
+  UOTK_CUDA(ctx, cudaMemsetAsync(S.scratch, 0, sizeof(int) * tiles, s));
+  {
+    UOTK_PROF(ctx, s, "bin");
+    if (n > 0) {
+      k_bin_count<<<grid_for(ctx, n, 256), 256, 0, s>>>(pts, n, R, P.tiles1, tmp_cell, tmp_tile,
+                                                         S.scratch);
+      UOTK_LAUNCHED(ctx);
+    }
+    k_bin_scan<<<1, 1024, 0, s>>>(S.scratch, tiles, NFFT_UNIT_POINTS, S.tile_start,
+                                  S.tile_unit_start, S.num_units);
+    UOTK_LAUNCHED(ctx);
+    if (n > 0) {
+      k_bin_scatter<<<grid_for(ctx, n, 256), 256, 0, s>>>(tmp_cell, tmp_tile, n, S.tile_start,
+                                                           S.scratch, S.cell, S.perm);
+      UOTK_LAUNCHED(ctx);
+    }
+    k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.tile_unit_start, tiles,
+                                                          NFFT_UNIT_POINTS, S.unit_tile,
+                                                          S.unit_begin, S.unit_count);
+    UOTK_LAUNCHED(ctx);
+  }
+  if (n > 0) {
+    UOTK_PROF(ctx, s, "window");
+    k_windows<<<grid_for(ctx, n * 3 * 2 * P.m, 256), 256, 0, s>>>(S.cell, n, P.m, P.b, P.d, S.win);
+    UOTK_LAUNCHED(ctx);
+  }
+  return UOTK_OK;
+}
+
+uotk_status op_nfft_cells(uotk_ctx* ctx, cudaStream_t s, const uotk_nfft_plan_info* plan,
+                          const float* pts, int64_t n, int32_t* cells) {
+  if (n == 0) return UOTK_OK;
+  CellRule R{{plan->center[0], plan->center[1], plan->center[2]}, plan->inv_h, plan->grid, plan->d};
+  k_cells<<<grid_for(ctx, n, 256), 256, 0, s>>>(pts, n, R, cells);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+}  // namespace uotk

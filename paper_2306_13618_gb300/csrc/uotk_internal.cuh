@@ -34,9 +34,9 @@ struct uotk_ctx {
   char* ws = nullptr;
   size_t ws_cap = 0;
   // Pinned host staging for scalars read back at the end of a call.
-  double* host = nullptr;   // 64 doubles
+  double* host = nullptr;   // 128 doubles
   // Device flags/counters (int64 slots), zeroed per call where used.
-  long long* dflags = nullptr;  // 16 slots
+  long long* dflags = nullptr;  // NUM_FLAGS slots
   int64_t launches = 0;
   uotk_prof prof;
 };
@@ -56,7 +56,8 @@ enum FlagSlot {
   FLAG_DELTA0 = 8,         // max |lambda * change| over a sweep (two parities)
   FLAG_DELTA1 = 9,
   FLAG_NONFINITE_DUAL = 10,  // count of non-finite dual values produced
-  NUM_FLAGS = 16
+  FLAG_BBOX = 16,          // 6 slots: max x,y,z and max of -x,-y,-z (ordered encodings)
+  NUM_FLAGS = 32
 };
 
 uotk_status set_error(uotk_ctx* ctx, uotk_status st, const char* fmt, ...);
