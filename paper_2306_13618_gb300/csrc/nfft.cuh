@@ -13,7 +13,7 @@
 
 namespace uotk {
 
-constexpr int NFFT_TILE = 16;          // grid cells per tile edge (binning granularity)
+constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit granularity)
 constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
 constexpr int NFFT_MAX_M = 8;
 
@@ -27,8 +27,8 @@ struct NfftParams {
   double h = 1.0;
   double eps = 1.0;
   float b = 0.f;       // Kaiser-Bessel shape pi (2 - 1/sigma)
-  int tiles1 = 8;      // tiles per dimension = n / NFFT_TILE
-  int E = 27;          // smem block edge = NFFT_TILE + 2m - 1
+  int tiles1 = 16;     // tiles per dimension = n / NFFT_TILE
+  int E = 19;          // smem block edge = NFFT_TILE + 2m - 1
 };
 
 // Host: choose h, m; fill params (bounding box given).
@@ -38,7 +38,8 @@ uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const floa
 // (FP64 -> FP32 table of 3*N floats, one row per dimension).
 void nfft_scale_table(const NfftParams& P, float* host_table /* 3*N */);
 
-// A point set binned by tile: sorted cells/fractions, window weights, permutation.
+// A point set sorted by grid cell, cells ordered tile by tile (tile-major,
+// then z, y, x inside the tile): points of one cell are contiguous.
 struct NfftPoints {
   int64_t n = 0;
   int4* cell = nullptr;      // sorted: (cx | cy<<10 | cz<<20, frac x, y, z as float bits)
@@ -52,6 +53,9 @@ struct NfftPoints {
   int* tile_unit_start = nullptr;  // [tiles+1] first unit of each tile
   int max_units = 0;
   int* scratch = nullptr;    // [tiles] counters
+  int* cell_count = nullptr; // [n^3] histogram, then scatter cursor
+  int* cell_start = nullptr; // [n^3 + 1] exclusive scan
+  int* block_sums = nullptr; // scan partials
 };
 size_t nfft_points_bytes(const NfftParams& P, int64_t n);
 void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S);

@@ -28,67 +28,111 @@ constexpr int FFT_LINES = 16;
 constexpr int FFT_THREADS = 256;
 
 // ---------------------------------------------------------------- spread ----
-__global__ void __launch_bounds__(384)
+constexpr int CH = 64;  // points staged in shared memory per chunk
+
+// M floats of a window row from shared memory (8-byte vector loads when M is even).
+template <int M>
+__device__ __forceinline__ void load_row(const float* p, float* r) {
+  if (M % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < M; j += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(p + j);
+      r[j] = v.x;
+      r[j + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < M; ++j) r[j] = p[j];
+  }
+}
+
+// One CTA per work unit.  Thread (row r = (kz, ky), half) owns the M nodes
+// kx in [half*M, half*M + M) of footprint row (kz, ky).  The points of one grid
+// cell share the footprint: their rank-1 window products are accumulated in
+// registers, then added to the block once; a barrier separates the additions of
+// consecutive cells, so no two threads ever update a node at the same time.
+template <int M>
+__global__ void __launch_bounds__(8 * M * M)
     k_spread(const int4* __restrict__ cell, const float* __restrict__ win,
              const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
-             const int* __restrict__ unit_count, const int* __restrict__ num_units, int m,
-             int tiles1, int E, const float* __restrict__ base, const double* __restrict__ pot,
-             double lam, const long long* __restrict__ shift_slot, float* __restrict__ part) {
-  extern __shared__ float blk[];  // [E][E][E]
+             const int* __restrict__ unit_count, const int* __restrict__ num_units, int tiles1,
+             const float* __restrict__ base, const double* __restrict__ pot, double lam,
+             const long long* __restrict__ shift_slot, float* __restrict__ part) {
+  constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E3 = E * E * E, WIN = 3 * W2;
+  constexpr int NT = 8 * M * M;
+  extern __shared__ float smem[];
+  float* blk = smem;
+  float* swin = blk + E3 + (E3 & 1);  // 8-byte aligned
+  float* sw = swin + CH * WIN;
+  int* skey = reinterpret_cast<int*>(sw + CH);
   const int u = blockIdx.x;
   if (u >= *num_units) return;
-  const int E3 = E * E * E;
-  for (int i = threadIdx.x; i < E3; i += blockDim.x) blk[i] = 0.f;
+  for (int i = threadIdx.x; i < E3; i += NT) blk[i] = 0.f;
   const int tile = unit_tile[u];
   const int tx0 = (tile % tiles1) * NFFT_TILE;
   const int ty0 = ((tile / tiles1) % tiles1) * NFFT_TILE;
   const int tz0 = (tile / (tiles1 * tiles1)) * NFFT_TILE;
-  const int w2 = 2 * m, w22 = w2 * w2;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  // (ky, kx) pairs of this lane: c = lane + 32 it
-  int off[8];
-  int nit = 0;
-#pragma unroll
-  for (int it = 0; it < 8; ++it) {
-    const int c = lane + 32 * it;
-    off[it] = c < w22 ? (c / w2) * E + (c % w2) : -1;
-    if (c < w22) nit = it + 1;
-  }
+  const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
+  const int kz = r / W2, ky = r - kz * W2, kx0 = half * M;
   const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
-  __syncthreads();
   const int b0 = unit_begin[u], cnt = unit_count[u];
-  for (int p = warp; p < cnt; p += nwarps) {
-    const int q = b0 + p;
-    const int4 c = cell[q];
-    const int bx = (c.x & 1023) - tx0, by = ((c.x >> 10) & 1023) - ty0, bz = (c.x >> 20) - tz0;
-    double wd = base ? (double)base[q] : 1.0;
-    if (pot) wd *= exp(lam * pot[q] - shift);
-    const float w = (float)wd;
-    const float* wq = win + (size_t)q * 3 * w2;
-    float pxy[8];
-#pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      const int cc = lane + 32 * it;
-      pxy[it] = it < nit && cc < w22 ? wq[cc % w2] * wq[w2 + cc / w2] : 0.f;
+  for (int c0 = 0; c0 < cnt; c0 += CH) {
+    const int cn = min(CH, cnt - c0);
+    __syncthreads();
+    const float* gw = win + (size_t)(b0 + c0) * WIN;
+    for (int i = threadIdx.x; i < cn * WIN; i += NT) swin[i] = gw[i];
+    for (int i = threadIdx.x; i < cn; i += NT) {
+      const int q = b0 + c0 + i;
+      double wd = base ? (double)base[q] : 1.0;
+      if (pot) wd *= exp(lam * pot[q] - shift);
+      sw[i] = (float)wd;
+      skey[i] = cell[q].x;
     }
-    float* dst = blk + (bz * E + by) * E + bx;
-    for (int kz = 0; kz < w2; ++kz) {
-      const float wz = w * wq[2 * w2 + kz];
-      float* plane = dst + kz * E * E;
+    __syncthreads();
+    int p = 0;
+    while (p < cn) {
+      const int key = skey[p];
+      float acc[M];
 #pragma unroll
-      for (int it = 0; it < 8; ++it)
-        if (it < nit && off[it] >= 0) atomicAdd(plane + off[it], wz * pxy[it]);
+      for (int j = 0; j < M; ++j) acc[j] = 0.f;
+      int q = p;
+      for (; q < cn && skey[q] == key; ++q) {
+        const float* wq = swin + q * WIN;
+        const float a = sw[q] * wq[2 * W2 + kz] * wq[W2 + ky];
+        float fx[M];
+        load_row<M>(wq + kx0, fx);
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[j] = fmaf(a, fx[j], acc[j]);
+      }
+      const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+      float* dst = blk + ((bz + kz) * E + by + ky) * E + bx + kx0;
+#pragma unroll
+      for (int j = 0; j < M; ++j) dst[j] += acc[j];
+      __syncthreads();
+      p = q;
     }
   }
   __syncthreads();
   float* out = part + (size_t)u * E3;
-  for (int i = threadIdx.x; i < E3; i += blockDim.x) out[i] = blk[i];
+  for (int i = threadIdx.x; i < E3; i += NT) out[i] = blk[i];
 }
 
-// Grid node g (per dimension) is covered by block (tile t, local l) when
-// l = g - t*16 + m - 1 (mod n) + r n lies in [0, E).
+// Grid node g (per dimension) is covered by the block of tile t at local index
+// l = g - t*T + m - 1 (mod n), when l lies in [0, E).  General form (aliases
+// when E > n) and the direct form for n >= 2E.
 __device__ __forceinline__ int covers(int g, int n, int tiles1, int m, int E, int* tl, int* ll) {
   int k = 0;
+  if (n >= 2 * E) {
+    const int top = (g + m - 1) >= 0 ? (g + m - 1) / NFFT_TILE : -1;
+    for (int t = top; k < 8; --t) {
+      const int l = g + m - 1 - t * NFFT_TILE;
+      if (l >= E) break;
+      tl[k] = ((t % tiles1) + tiles1) % tiles1;
+      ll[k] = l;
+      ++k;
+    }
+    return k;
+  }
   for (int t = 0; t < tiles1 && k < 8; ++t) {
     int l = g - t * NFFT_TILE + m - 1;
     l %= n;
@@ -232,74 +276,141 @@ __global__ void __launch_bounds__(FFT_THREADS)
 }
 
 // ---------------------------------------------------------------- gather ----
-__global__ void __launch_bounds__(384)
+// One CTA per work unit: the E^3 block of the grid around the tile is staged
+// in shared memory, then each warp evaluates one target at a time.
+template <int M>
+__global__ void __launch_bounds__(256)
     k_gather(const int4* __restrict__ cell, const float* __restrict__ win,
              const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
-             const int* __restrict__ unit_count, const int* __restrict__ num_units, int m, int n,
-             int tiles1, int E, const float* __restrict__ grid, float* __restrict__ out) {
-  extern __shared__ float blk[];
+             const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
+             int tiles1, const float* __restrict__ grid, float* __restrict__ out) {
+  constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E2 = E * E, E3 = E2 * E, WIN = 3 * W2;
+  constexpr int NIT = (W2 * W2 + 31) / 32;
+  extern __shared__ float smem[];
+  float* blk = smem;
+  float* swin = blk + E3 + (E3 & 1);
+  int* skey = reinterpret_cast<int*>(swin + CH * WIN);
   const int u = blockIdx.x;
   if (u >= *num_units) return;
   const int tile = unit_tile[u];
   const int tx0 = (tile % tiles1) * NFFT_TILE;
   const int ty0 = ((tile / tiles1) % tiles1) * NFFT_TILE;
   const int tz0 = (tile / (tiles1 * tiles1)) * NFFT_TILE;
-  const int E2 = E * E, E3 = E2 * E;
   for (int i = threadIdx.x; i < E3; i += blockDim.x) {
     const int lz = i / E2, ly = (i / E) % E, lx = i % E;
-    int gz = (tz0 - m + 1 + lz) % n, gy = (ty0 - m + 1 + ly) % n, gx = (tx0 - m + 1 + lx) % n;
-    gz += gz < 0 ? n : 0; gy += gy < 0 ? n : 0; gx += gx < 0 ? n : 0;
+    int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
+    gz += gz < 0 ? n : 0;
+    gy += gy < 0 ? n : 0;
+    gx += gx < 0 ? n : 0;
     blk[i] = grid[((long long)gz * n + gy) * n + gx];
   }
-  __syncthreads();
-  const int w2 = 2 * m, w22 = w2 * w2;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-  int off[8];
-  int nit = 0;
+  int off[NIT], kxs[NIT], kys[NIT];
 #pragma unroll
-  for (int it = 0; it < 8; ++it) {
+  for (int it = 0; it < NIT; ++it) {
     const int c = lane + 32 * it;
-    off[it] = c < w22 ? (c / w2) * E + (c % w2) : -1;
-    if (c < w22) nit = it + 1;
+    kxs[it] = c % W2;
+    kys[it] = c / W2;
+    off[it] = c < W2 * W2 ? kys[it] * E + kxs[it] : -1;
   }
   const int b0 = unit_begin[u], cnt = unit_count[u];
-  for (int p = warp; p < cnt; p += nwarps) {
-    const int q = b0 + p;
-    const int4 c = cell[q];
-    const int bx = (c.x & 1023) - tx0, by = ((c.x >> 10) & 1023) - ty0, bz = (c.x >> 20) - tz0;
-    const float* wq = win + (size_t)q * 3 * w2;
-    const float* src = blk + (bz * E + by) * E + bx;
-    float acc = 0.f;
+  for (int c0 = 0; c0 < cnt; c0 += CH) {
+    const int cn = min(CH, cnt - c0);
+    __syncthreads();
+    const float* gw = win + (size_t)(b0 + c0) * WIN;
+    for (int i = threadIdx.x; i < cn * WIN; i += blockDim.x) swin[i] = gw[i];
+    for (int i = threadIdx.x; i < cn; i += blockDim.x) skey[i] = cell[b0 + c0 + i].x;
+    __syncthreads();
+    for (int p = warp; p < cn; p += nwarps) {
+      const int key = skey[p];
+      const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+      const float* wq = swin + p * WIN;
+      float fz[W2];
 #pragma unroll
-    for (int it = 0; it < 8; ++it) {
-      if (it < nit && off[it] >= 0) {
-        const int cc = lane + 32 * it;
-        const float pxy = wq[cc % w2] * wq[w2 + cc / w2];
-        float col = 0.f;
-        for (int kz = 0; kz < w2; ++kz) col = fmaf(wq[2 * w2 + kz], src[kz * E2 + off[it]], col);
-        acc = fmaf(pxy, col, acc);
+      for (int k = 0; k < W2; ++k) fz[k] = wq[2 * W2 + k];
+      const float* src = blk + (bz * E + by) * E + bx;
+      float acc = 0.f;
+#pragma unroll
+      for (int it = 0; it < NIT; ++it) {
+        if (off[it] >= 0) {
+          const float pxy = wq[kxs[it]] * wq[W2 + kys[it]];
+          const float* col = src + off[it];
+          float s = 0.f;
+#pragma unroll
+          for (int k = 0; k < W2; ++k) s = fmaf(fz[k], col[k * E2], s);
+          acc = fmaf(pxy, s, acc);
+        }
       }
+      acc = warp_sum(acc);
+      if (lane == 0) out[b0 + c0 + p] = acc;
     }
-    acc = warp_sum(acc);
-    if (lane == 0) out[q] = acc;
   }
 }
 
-int spread_threads(int m) { return 32 * (m <= 6 ? 12 : 12); }
+template <int M>
+size_t spread_smem() {
+  constexpr int E = NFFT_TILE + 2 * M - 1, E3 = E * E * E;
+  return sizeof(float) * (E3 + 1 + CH * 6 * M + 2 * CH);
+}
+
+template <int M>
+uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                          const NfftPoints& S, const SpreadWeights& w, float* part) {
+  const size_t smem = spread_smem<M>();
+  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_spread<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  k_spread<M><<<S.max_units, 8 * M * M, smem, s>>>(S.cell, S.win, S.unit_tile, S.unit_begin,
+                                                   S.unit_count, S.num_units, P.tiles1, w.base,
+                                                   w.pot, w.lam, w.shift_slot, part);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+template <int M>
+uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                          const NfftPoints& S, const float* grid, float* out) {
+  const size_t smem = spread_smem<M>();
+  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_gather<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem));
+  k_gather<M><<<S.max_units, 256, smem, s>>>(S.cell, S.win, S.unit_tile, S.unit_begin,
+                                             S.unit_count, S.num_units, P.n, P.tiles1, grid, out);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
 
 }  // namespace
 
+#define UOTK_M_SWITCH(m, CALL)                 \
+  switch (m) {                                 \
+    case 2: return CALL(2);                    \
+    case 3: return CALL(3);                    \
+    case 4: return CALL(4);                    \
+    case 5: return CALL(5);                    \
+    case 6: return CALL(6);                    \
+    case 7: return CALL(7);                    \
+    case 8: return CALL(8);                    \
+    default: return set_error(ctx, UOTK_ERR_INVALID, "cut-off %d outside [2, 8]", m); \
+  }
+
+static uotk_status spread_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                                const NfftPoints& S, const SpreadWeights& w, float* part) {
+#define UOTK_SPREAD_CALL(M) launch_spread<M>(ctx, s, P, S, w, part)
+  UOTK_M_SWITCH(P.m, UOTK_SPREAD_CALL)
+#undef UOTK_SPREAD_CALL
+}
+
+static uotk_status gather_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                                const NfftPoints& S, const float* grid, float* out) {
+#define UOTK_GATHER_CALL(M) launch_gather<M>(ctx, s, P, S, grid, out)
+  UOTK_M_SWITCH(P.m, UOTK_GATHER_CALL)
+#undef UOTK_GATHER_CALL
+}
+
 uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
                         const SpreadWeights& w, NfftWork& W, float* grid_out) {
-  const size_t smem = (size_t)P.E * P.E * P.E * sizeof(float);
-  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_spread, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
   if (S.n > 0) {
     UOTK_PROF(ctx, s, "spread");
-    k_spread<<<S.max_units, spread_threads(P.m), smem, s>>>(
-        S.cell, S.win, S.unit_tile, S.unit_begin, S.unit_count, S.num_units, P.m, P.tiles1, P.E,
-        w.base, w.pot, w.lam, w.shift_slot, W.part);
-    UOTK_LAUNCHED(ctx);
+    UOTK_TRY(spread_units(ctx, s, P, S, w, W.part));
   }
   {
     UOTK_PROF(ctx, s, "fold");
@@ -345,14 +456,8 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
 uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
                         const float* grid, float* out_sorted) {
   if (S.n == 0) return UOTK_OK;
-  const size_t smem = (size_t)P.E * P.E * P.E * sizeof(float);
-  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_gather, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
   UOTK_PROF(ctx, s, "gather");
-  k_gather<<<S.max_units, 384, smem, s>>>(S.cell, S.win, S.unit_tile, S.unit_begin, S.unit_count,
-                                          S.num_units, P.m, P.n, P.tiles1, P.E, grid, out_sorted);
-  UOTK_LAUNCHED(ctx);
-  return UOTK_OK;
+  return gather_units(ctx, s, P, S, grid, out_sorted);
 }
 
 size_t nfft_work_bytes(const NfftParams& P, int max_src_units) {

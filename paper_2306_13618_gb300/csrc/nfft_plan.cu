@@ -92,20 +92,102 @@ __global__ void k_cells(const float* __restrict__ pts, long long n, CellRule R,
   }
 }
 
+// Cell key: tile-major, then z, y, x inside the tile, so that the points of a
+// tile, and inside it the points of a cell, are contiguous after sorting.
+__device__ __forceinline__ int cell_key(const int c[3], int tiles1) {
+  const int tile = ((c[2] / NFFT_TILE) * tiles1 + c[1] / NFFT_TILE) * tiles1 + c[0] / NFFT_TILE;
+  const int local = ((c[2] % NFFT_TILE) * NFFT_TILE + c[1] % NFFT_TILE) * NFFT_TILE + c[0] % NFFT_TILE;
+  return tile * (NFFT_TILE * NFFT_TILE * NFFT_TILE) + local;
+}
+
 __global__ void k_bin_count(const float* __restrict__ pts, long long n, CellRule R, int tiles1,
-                            int4* __restrict__ tmp_cell, int* __restrict__ tmp_tile,
+                            int4* __restrict__ tmp_cell, int* __restrict__ tmp_key,
                             int* __restrict__ count) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     int c[3];
     float f[3];
     cell_of(pts + i * R.d, R, c, f);
-    const int tile = ((c[2] / NFFT_TILE) * tiles1 + c[1] / NFFT_TILE) * tiles1 + c[0] / NFFT_TILE;
-    tmp_tile[i] = tile;
+    const int key = cell_key(c, tiles1);
+    tmp_key[i] = key;
     tmp_cell[i] = make_int4(c[0] | (c[1] << 10) | (c[2] << 20), __float_as_int(f[0]),
                             __float_as_int(f[1]), __float_as_int(f[2]));
-    atomicAdd(&count[tile], 1);
+    atomicAdd(&count[key], 1);
   }
+}
+
+// Exclusive scan of the n^3 cell counts: blocks of 2048 (two per thread),
+// block sums scanned by one block, then added back.  Counts are zeroed as they
+// are read (they become the scatter cursors).
+constexpr int SCAN_BLOCK = 2048;
+
+__global__ void __launch_bounds__(1024) k_scan_local(int* __restrict__ count, long long total,
+                                                     int* __restrict__ start,
+                                                     int* __restrict__ block_sums) {
+  __shared__ int sh[SCAN_BLOCK];
+  const long long base = (long long)blockIdx.x * SCAN_BLOCK;
+  for (int k = threadIdx.x; k < SCAN_BLOCK; k += blockDim.x) {
+    const long long i = base + k;
+    int v = 0;
+    if (i < total) { v = count[i]; count[i] = 0; }
+    sh[k] = v;
+  }
+  __syncthreads();
+  // Hillis-Steele inclusive scan over 2048 entries (each thread owns two)
+  for (int o = 1; o < SCAN_BLOCK; o <<= 1) {
+    int a0 = 0, a1 = 0;
+    const int k0 = threadIdx.x, k1 = threadIdx.x + 1024;
+    if (k0 >= o) a0 = sh[k0 - o];
+    if (k1 >= o) a1 = sh[k1 - o];
+    __syncthreads();
+    sh[k0] += a0;
+    sh[k1] += a1;
+    __syncthreads();
+  }
+  for (int k = threadIdx.x; k < SCAN_BLOCK; k += blockDim.x) {
+    const long long i = base + k;
+    if (i < total) start[i] = k ? sh[k - 1] : 0;
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = sh[SCAN_BLOCK - 1];
+}
+
+__global__ void __launch_bounds__(1024) k_scan_top(int* __restrict__ block_sums, int nb) {
+  __shared__ int sh[1024];
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < nb ? block_sums[i] : 0;
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int o = 1; o < 1024; o <<= 1) {
+      const int a = threadIdx.x >= o ? sh[threadIdx.x - o] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += a;
+      __syncthreads();
+    }
+    if (i < nb) block_sums[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) block_sums[nb] = carry;
+}
+
+__global__ void k_scan_add(int* __restrict__ start, long long total,
+                           const int* __restrict__ block_sums, int nb) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x)
+    start[i] += block_sums[i / SCAN_BLOCK];
+  if (blockIdx.x == 0 && threadIdx.x == 0) start[total] = block_sums[nb];
+}
+
+__global__ void k_tile_counts(const int* __restrict__ cell_start, int tiles,
+                              int* __restrict__ count) {
+  constexpr int T3 = NFFT_TILE * NFFT_TILE * NFFT_TILE;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x)
+    count[t] = cell_start[(long long)(t + 1) * T3] - cell_start[(long long)t * T3];
 }
 
 // Single block: exclusive scans of points and of work units per tile.
@@ -146,14 +228,14 @@ __global__ void k_bin_scan(int* __restrict__ count, int tiles, int unit_pts,
   }
 }
 
-__global__ void k_bin_scatter(const int4* __restrict__ tmp_cell, const int* __restrict__ tmp_tile,
-                              long long n, const int* __restrict__ tile_start,
+__global__ void k_bin_scatter(const int4* __restrict__ tmp_cell, const int* __restrict__ tmp_key,
+                              long long n, const int* __restrict__ cell_start,
                               int* __restrict__ cursor, int4* __restrict__ cell,
                               int* __restrict__ perm) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    const int t = tmp_tile[i];
-    const int pos = tile_start[t] + atomicAdd(&cursor[t], 1);
+    const int k = tmp_key[i];
+    const int pos = cell_start[k] + atomicAdd(&cursor[k], 1);
     cell[pos] = tmp_cell[i];
     perm[pos] = (int)i;
   }
@@ -327,6 +409,10 @@ void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S
   S.unit_count = cv.take<int>(S.max_units + 1);
   S.num_units = cv.take<int>(1);
   S.scratch = cv.take<int>(tiles);
+  const long long n3 = (long long)P.n * P.n * P.n;
+  S.cell_count = cv.take<int>(n3);
+  S.cell_start = cv.take<int>(n3 + 1);
+  S.block_sums = cv.take<int>(n3 / 2048 + 2);
   // temporaries of the build (caller order)
   cv.take<int4>(nn);
   cv.take<int>(nn);
@@ -335,26 +421,36 @@ void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S
 uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                               const float* pts, int64_t n, NfftPoints& S) {
   const int tiles = P.tiles1 * P.tiles1 * P.tiles1;
-  // the temporaries sit right after `scratch` (see nfft_points_carve)
-  Carver cv(reinterpret_cast<char*>(S.scratch));
-  cv.take<int>(tiles);
+  const long long n3 = (long long)P.n * P.n * P.n;
+  const int nb = (int)((n3 + SCAN_BLOCK - 1) / SCAN_BLOCK);
+  // the temporaries sit right after `block_sums` (see nfft_points_carve)
+  Carver cv(reinterpret_cast<char*>(S.block_sums));
+  cv.take<int>(n3 / 2048 + 2);
   int4* tmp_cell = cv.take<int4>(n > 0 ? n : 1);
-  int* tmp_tile = cv.take<int>(n > 0 ? n : 1);
+  int* tmp_key = cv.take<int>(n > 0 ? n : 1);
   CellRule R{{P.c[0], P.c[1], P.c[2]}, P.inv_h, P.n, P.d};
-  UOTK_CUDA(ctx, cudaMemsetAsync(S.scratch, 0, sizeof(int) * tiles, s));
   {
     UOTK_PROF(ctx, s, "bin");
+    UOTK_CUDA(ctx, cudaMemsetAsync(S.cell_count, 0, sizeof(int) * n3, s));
     if (n > 0) {
-      k_bin_count<<<grid_for(ctx, n, 256), 256, 0, s>>>(pts, n, R, P.tiles1, tmp_cell, tmp_tile,
-                                                         S.scratch);
+      k_bin_count<<<grid_for(ctx, n, 256), 256, 0, s>>>(pts, n, R, P.tiles1, tmp_cell, tmp_key,
+                                                         S.cell_count);
       UOTK_LAUNCHED(ctx);
     }
+    k_scan_local<<<nb, 1024, 0, s>>>(S.cell_count, n3, S.cell_start, S.block_sums);
+    UOTK_LAUNCHED(ctx);
+    k_scan_top<<<1, 1024, 0, s>>>(S.block_sums, nb);
+    UOTK_LAUNCHED(ctx);
+    k_scan_add<<<grid_for(ctx, n3, 256), 256, 0, s>>>(S.cell_start, n3, S.block_sums, nb);
+    UOTK_LAUNCHED(ctx);
+    k_tile_counts<<<grid_for(ctx, tiles, 256), 256, 0, s>>>(S.cell_start, tiles, S.scratch);
+    UOTK_LAUNCHED(ctx);
     k_bin_scan<<<1, 1024, 0, s>>>(S.scratch, tiles, NFFT_UNIT_POINTS, S.tile_start,
                                   S.tile_unit_start, S.num_units);
     UOTK_LAUNCHED(ctx);
     if (n > 0) {
-      k_bin_scatter<<<grid_for(ctx, n, 256), 256, 0, s>>>(tmp_cell, tmp_tile, n, S.tile_start,
-                                                           S.scratch, S.cell, S.perm);
+      k_bin_scatter<<<grid_for(ctx, n, 256), 256, 0, s>>>(tmp_cell, tmp_key, n, S.cell_start,
+                                                           S.cell_count, S.cell, S.perm);
       UOTK_LAUNCHED(ctx);
     }
     k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.tile_unit_start, tiles,

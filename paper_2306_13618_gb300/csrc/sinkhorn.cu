@@ -422,9 +422,9 @@ uotk_status op_kernel_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* src
   cv.off = eb;
   float* tmp = cv.take<float>(m > 0 ? m : 1);
   if (E->identity_order()) {
-    UOTK_TRY(E->plain(s, 1, 0, w, out));
+    UOTK_TRY(E->plain(s, 1, 0, E->weights(1), out));
   } else {
-    UOTK_TRY(E->plain(s, 1, 0, w, tmp));
+    UOTK_TRY(E->plain(s, 1, 0, E->weights(1), tmp));
     UOTK_TRY(E->to_caller_f32(s, 0, tmp, out));
   }
   return flags_check(ctx, s, "kernel_sum");
