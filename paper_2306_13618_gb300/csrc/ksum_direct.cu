@@ -251,10 +251,10 @@ __global__ void k_set_weights(void* __restrict__ packed, long long n, int small,
   const double shift = ordered_to_dbl(*shift_slot);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    double v = exp(lam * pot[i] - shift);
-    if (base) v *= (double)base[i];
-    if (small) reinterpret_cast<float4*>(packed)[i].w = (float)v;
-    else reinterpret_cast<float*>(packed)[i * dp + dp - 1] = (float)v;
+    float v = exp_shifted(lam * pot[i] - shift);
+    if (base) v *= base[i];
+    if (small) reinterpret_cast<float4*>(packed)[i].w = v;
+    else reinterpret_cast<float*>(packed)[i * dp + dp - 1] = v;
   }
 }
 

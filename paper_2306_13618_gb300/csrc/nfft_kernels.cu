@@ -83,9 +83,8 @@ __global__ void __launch_bounds__(8 * M * M)
     for (int i = threadIdx.x; i < cn * WIN; i += NT) swin[i] = gw[i];
     for (int i = threadIdx.x; i < cn; i += NT) {
       const int q = b0 + c0 + i;
-      double wd = base ? (double)base[q] : 1.0;
-      if (pot) wd *= exp(lam * pot[q] - shift);
-      sw[i] = (float)wd;
+      const float bq = base ? base[q] : 1.f;
+      sw[i] = pot ? bq * exp_shifted(lam * pot[q] - shift) : bq;
       skey[i] = cell[q].x;
     }
     __syncthreads();
@@ -164,6 +163,43 @@ __global__ void k_fold(const float* __restrict__ part, const int* __restrict__ t
         }
     grid[i] = acc;
   }
+}
+
+// Fold for grids of at least 3 tiles per dimension: one CTA per output tile
+// (T^3 threads, one node each).  The blocks that can cover the tile are those
+// of the 27 neighbouring tiles (E - m + 1 <= 2T and T + m - 1 < 2T for T = 8,
+// m <= 8); each node adds the covering block values unit by unit, neighbours
+// in a fixed order.
+__global__ void __launch_bounds__(NFFT_TILE * NFFT_TILE * NFFT_TILE)
+    k_fold_tiles(const float* __restrict__ part, const int* __restrict__ tile_unit_start, int n,
+                 int tiles1, int m, int E, float* __restrict__ grid) {
+  const int t = blockIdx.x;
+  const int tx = t % tiles1, ty = (t / tiles1) % tiles1, tz = t / (tiles1 * tiles1);
+  const int lx = threadIdx.x % NFFT_TILE, ly = (threadIdx.x / NFFT_TILE) % NFFT_TILE,
+            lz = threadIdx.x / (NFFT_TILE * NFFT_TILE);
+  const long long E3 = (long long)E * E * E;
+  float acc = 0.f;
+  for (int dz = -1; dz <= 1; ++dz) {
+    const int bz = lz - dz * NFFT_TILE + m - 1;
+    if (bz < 0 || bz >= E) continue;
+    const int nz = (tz + dz + tiles1) % tiles1;
+    for (int dy = -1; dy <= 1; ++dy) {
+      const int by = ly - dy * NFFT_TILE + m - 1;
+      if (by < 0 || by >= E) continue;
+      const int ny = (ty + dy + tiles1) % tiles1;
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int bx = lx - dx * NFFT_TILE + m - 1;
+        if (bx < 0 || bx >= E) continue;
+        const int nx = (tx + dx + tiles1) % tiles1;
+        const int nt = (nz * tiles1 + ny) * tiles1 + nx;
+        const long long loc = ((long long)bz * E + by) * E + bx;
+        for (int u = tile_unit_start[nt]; u < tile_unit_start[nt + 1]; ++u)
+          acc += part[(long long)u * E3 + loc];
+      }
+    }
+  }
+  const int gx = tx * NFFT_TILE + lx, gy = ty * NFFT_TILE + ly, gz = tz * NFFT_TILE + lz;
+  grid[((long long)gz * n + gy) * n + gx] = acc;
 }
 
 // ------------------------------------------------------------------ FFT ----
@@ -286,6 +322,9 @@ __global__ void __launch_bounds__(256)
              int tiles1, const float* __restrict__ grid, float* __restrict__ out) {
   constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E2 = E * E, E3 = E2 * E, WIN = 3 * W2;
   constexpr int NIT = (W2 * W2 + 31) / 32;
+  // Footprint values of the current cell kept in registers while a warp's
+  // consecutive targets share that cell (targets are sorted by cell).
+  constexpr bool CACHE = NIT * W2 <= 64;
   extern __shared__ float smem[];
   float* blk = smem;
   float* swin = blk + E3 + (E3 & 1);
@@ -313,6 +352,8 @@ __global__ void __launch_bounds__(256)
     kys[it] = c / W2;
     off[it] = c < W2 * W2 ? kys[it] * E + kxs[it] : -1;
   }
+  float hc[CACHE ? NIT * W2 : 1];
+  int cached = -1;
   const int b0 = unit_begin[u], cnt = unit_count[u];
   for (int c0 = 0; c0 < cnt; c0 += CH) {
     const int cn = min(CH, cnt - c0);
@@ -325,20 +366,39 @@ __global__ void __launch_bounds__(256)
       const int key = skey[p];
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
       const float* wq = swin + p * WIN;
+      const float* src = blk + (bz * E + by) * E + bx;
       float fz[W2];
 #pragma unroll
       for (int k = 0; k < W2; ++k) fz[k] = wq[2 * W2 + k];
-      const float* src = blk + (bz * E + by) * E + bx;
       float acc = 0.f;
+      if (CACHE) {
+        if (key != cached) {
 #pragma unroll
-      for (int it = 0; it < NIT; ++it) {
-        if (off[it] >= 0) {
-          const float pxy = wq[kxs[it]] * wq[W2 + kys[it]];
-          const float* col = src + off[it];
+          for (int it = 0; it < NIT; ++it)
+#pragma unroll
+            for (int k = 0; k < W2; ++k)
+              hc[CACHE ? it * W2 + k : 0] = off[it] >= 0 ? src[k * E2 + off[it]] : 0.f;
+          cached = key;
+        }
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) {
           float s = 0.f;
 #pragma unroll
-          for (int k = 0; k < W2; ++k) s = fmaf(fz[k], col[k * E2], s);
+          for (int k = 0; k < W2; ++k) s = fmaf(fz[k], hc[CACHE ? it * W2 + k : 0], s);
+          const float pxy = off[it] >= 0 ? wq[kxs[it]] * wq[W2 + kys[it]] : 0.f;
           acc = fmaf(pxy, s, acc);
+        }
+      } else {
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+          if (off[it] >= 0) {
+            const float pxy = wq[kxs[it]] * wq[W2 + kys[it]];
+            const float* col = src + off[it];
+            float s = 0.f;
+#pragma unroll
+            for (int k = 0; k < W2; ++k) s = fmaf(fz[k], col[k * E2], s);
+            acc = fmaf(pxy, s, acc);
+          }
         }
       }
       acc = warp_sum(acc);
@@ -415,7 +475,11 @@ uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
   {
     UOTK_PROF(ctx, s, "fold");
     const long long total = (long long)P.n * P.n * P.n;
-    if (S.n > 0) {
+    if (S.n > 0 && P.tiles1 >= 3) {
+      k_fold_tiles<<<P.tiles1 * P.tiles1 * P.tiles1, NFFT_TILE * NFFT_TILE * NFFT_TILE, 0, s>>>(
+          W.part, S.tile_unit_start, P.n, P.tiles1, P.m, P.E, grid_out);
+      UOTK_LAUNCHED(ctx);
+    } else if (S.n > 0) {
       k_fold<<<grid_for(ctx, total, 256, 8), 256, 0, s>>>(W.part, S.tile_unit_start, P.n, P.tiles1,
                                                           P.m, P.E, grid_out);
       UOTK_LAUNCHED(ctx);

@@ -130,8 +130,9 @@ __global__ void k_dual_update(const float* __restrict__ t, const float* __restri
   long long bad = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
-    const double lt = log((double)t[i]) + shift;
-    const double v = ref == 0 ? -q * lt : q * (log((double)base[i]) - lt);
+    const float ti = t[i];
+    const double lt = (ti > 0.f && isfinite(ti) ? log_f32(ti) : log((double)ti)) + shift;
+    const double v = ref == 0 ? -q * lt : q * (log_f32(base[i]) - lt);
     if (delta_out >= 0) dl = fmax(dl, fabs(lam * (v - pot[i])));
     pot[i] = v;
     if (isfinite(v)) mx = fmax(mx, lam * v);

@@ -127,6 +127,26 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// exp(a) for an FP64 argument, returned in FP32: a = k ln2 + r with integer k
+// and |r| <= ln2/2 taken in FP64, expf(r) in FP32, scaled by 2^k.  The result
+// has FP32 relative accuracy whatever |a| (converting a itself to FP32 would
+// cost |a| ulps).  Underflows to 0 below 2^-149.
+__device__ __forceinline__ float exp_shifted(double a) {
+  const double k = rint(a * 1.4426950408889634);
+  if (k < -160.0) return 0.f;
+  const double r = fma(-k, 0.6931471805599453, a);
+  const double r2 = fma(-k, 2.3190468138462996e-17, r);
+  return ldexpf(expf((float)r2), (int)k);
+}
+
+// log(t) of a positive FP32 value in FP64: t = f 2^e with f in [0.5, 1),
+// log f in FP32 (absolute error < 1e-7), e ln2 in FP64.
+__device__ __forceinline__ double log_f32(float t) {
+  int e;
+  const float f = frexpf(t, &e);
+  return (double)logf(f) + (double)e * 0.6931471805599453;
+}
+
 // Order-preserving map of doubles onto signed 64-bit integers, so that the
 // maximum of doubles can be taken with integer atomicMax (deterministic).
 __device__ __host__ __forceinline__ long long dbl_to_ordered(double v) {
