@@ -23,44 +23,6 @@ namespace {
 constexpr int STAGES = 3;
 constexpr int GEN_TILE = 64;  // sources per tile on the general-d path
 
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-  return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-// One 1-D bulk copy global -> shared that completes `bytes` on `bar`.
-__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
-                                          unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-               "r"(bytes)
-               : "memory");
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_addr(dst)),
-      "l"(src), "r"(bytes), "r"(smem_addr(bar))
-      : "memory");
-}
-// Bounded wait for phase `parity` of `bar`: gives up after ~2^31 clocks (~1 s).
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
-  const unsigned a = smem_addr(bar);
-  const long long t0 = clock64();
-  while (true) {
-    unsigned done;
-    asm volatile(
-        "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; selp.u32 %0, 1, 0, p; }"
-        : "=r"(done)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (done) return true;
-    if (clock64() - t0 > (1LL << 31)) return false;
-  }
-}
-
 __device__ __forceinline__ void neumaier(float& hi, float& lo, float v) {
   const float t = hi + v;
   lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
@@ -99,7 +61,7 @@ __global__ void __launch_bounds__(DIRECT_THREADS)
   __syncthreads();
   if (tid == 0) {
     for (int s = 0; s < STAGES && s < count; ++s)
-      bulk_load(sm[s], src + (t_begin + s) * DIRECT_TILE, BYTES, &bar[s]);
+      { mbar_expect(&bar[s], BYTES); bulk_copy(sm[s], src + (t_begin + s) * DIRECT_TILE, BYTES, &bar[s]); }
   }
 
   for (int k = 0; k < count; ++k) {
@@ -138,7 +100,7 @@ __global__ void __launch_bounds__(DIRECT_THREADS)
     }
     __syncthreads();
     if (tid == 0 && k + STAGES < count)
-      bulk_load(sm[s], src + (t_begin + k + STAGES) * DIRECT_TILE, BYTES, &bar[s]);
+      { mbar_expect(&bar[s], BYTES); bulk_copy(sm[s], src + (t_begin + k + STAGES) * DIRECT_TILE, BYTES, &bar[s]); }
   }
 
   float* o = out + (long long)blockIdx.y * m;

@@ -120,10 +120,9 @@ struct NfftEngine : Engine {
     NfftWork W;
     nfft_points_carve(cv, P, n, X);
     nfft_points_carve(cv, P, m, Y);
-    const int mu = X.max_units > Y.max_units ? X.max_units : Y.max_units;
-    nfft_work_carve(cv, P, mu, W);
-    float* as = cv.take<float>(n > 0 ? n : 1);
-    float* bs = cv.take<float>(m > 0 ? m : 1);
+    nfft_work_carve(cv, P, n > m ? n : m, W);
+    float* as = cv.take<float>((n > 0 ? n : 1) + 4);
+    float* bs = cv.take<float>((m > 0 ? m : 1) + 4);
     if (e) { e->X = X; e->Y = Y; e->W = W; e->as = as; e->bs = bs; }
   }
 
@@ -170,10 +169,8 @@ struct NfftEngine : Engine {
 uotk_status sorted_weights(uotk_ctx* ctx, cudaStream_t s, const NfftPoints& S, const float* w,
                            float* out) {
   if (S.n == 0) return UOTK_OK;
-  if (!w) {
-    UOTK_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(float) * S.n, s));
-    return UOTK_OK;
-  }
+  UOTK_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(float) * (S.n + 4), s));
+  if (!w) return UOTK_OK;
   k_gather_f32<<<grid_for(ctx, S.n, 256), 256, 0, s>>>(S.perm, w, S.n, out);
   UOTK_LAUNCHED(ctx);
   k_check_weights<<<grid_for(ctx, S.n, 256, 2), 256, 0, s>>>(out, S.n, ctx->dflags);
@@ -241,14 +238,14 @@ uotk_status op_nfft_spread(uotk_ctx* ctx, cudaStream_t s, const uotk_nfft_plan_i
   NfftPoints S;
   NfftWork W;
   nfft_points_carve(size, P, n, S);
-  nfft_work_carve(size, P, S.max_units, W);
-  size.take<float>(n > 0 ? n : 1);
+  nfft_work_carve(size, P, n, W);
+  size.take<float>((n > 0 ? n : 1) + 4);
   UOTK_TRY(ws_reserve(ctx, size.off));
   UOTK_TRY(flags_reset(ctx, s));
   Carver cv(ctx->ws);
   nfft_points_carve(cv, P, n, S);
-  nfft_work_carve(cv, P, S.max_units, W);
-  float* ws = cv.take<float>(n > 0 ? n : 1);
+  nfft_work_carve(cv, P, n, W);
+  float* ws = cv.take<float>((n > 0 ? n : 1) + 4);
   UOTK_TRY(check_points(ctx, s, pts, n * P.d));
   UOTK_TRY(nfft_points_build(ctx, s, P, pts, n, S));
   UOTK_TRY(sorted_weights(ctx, s, S, w, ws));

@@ -16,6 +16,10 @@ namespace uotk {
 constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit granularity)
 constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
 constexpr int NFFT_MAX_M = 8;
+constexpr int NFFT_CHUNK = 64;          // points per bulk-copied staging chunk
+// Floats per point of the window table: 3 x 2m weights, padded to 16 bytes
+// so that every chunk of the table is a legal bulk-copy source.
+__host__ __device__ constexpr int nfft_win_stride(int m) { return (6 * m + 3) & ~3; }
 
 struct NfftParams {
   int d = 3;
@@ -43,7 +47,8 @@ void nfft_scale_table(const NfftParams& P, float* host_table /* 3*N */);
 struct NfftPoints {
   int64_t n = 0;
   int4* cell = nullptr;      // sorted: (cx | cy<<10 | cz<<20, frac x, y, z as float bits)
-  float* win = nullptr;      // sorted: [n][3][2m] window weights
+  float* win = nullptr;      // sorted: [n][nfft_win_stride(m)] window weights (x, y, z rows)
+  int* ckey = nullptr;       // sorted: packed cell (cx | cy<<10 | cz<<20), n + 4 entries
   int* perm = nullptr;       // sorted position -> caller index
   int* tile_start = nullptr; // [tiles+1] start of each tile in sorted order
   int* unit_tile = nullptr;  // [max_units] tile of each work unit
@@ -65,16 +70,16 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
 
 // Work buffers of one summation.
 struct NfftWork {
-  float* part = nullptr;   // [max_units(src)][E^3] spread blocks
+  float* wts = nullptr;    // [max points + 4] spread weights (sorted order)
   float* grid = nullptr;   // [n^3] real grid
   float2* cgrid = nullptr; // [n^3] complex work grid
   float* scale = nullptr;  // [3*N] device table
 };
-size_t nfft_work_bytes(const NfftParams& P, int max_src_units);
-void nfft_work_carve(Carver& cv, const NfftParams& P, int max_src_units, NfftWork& W);
+size_t nfft_work_bytes(const NfftParams& P, int64_t max_points);
+void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWork& W);
 
 // Weights of the spread: w_i = base_i * exp(lam*pot_i - shift) (sorted order),
-// or plain w_i when pot == NULL (base required).
+// or plain w_i = base_i when pot == NULL (base then needs n + 4 entries).
 struct SpreadWeights {
   const float* base = nullptr;
   const double* pot = nullptr;

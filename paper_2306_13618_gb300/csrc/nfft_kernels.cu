@@ -2,20 +2,22 @@
 // grid convolution (FFT, multiply by b_k and the double deconvolution,
 // inverse FFT) and gather (NFFT final step).
 //
-// Spread.  Points are sorted by tile (16^3 cells).  A work unit is (tile, up to
-// NFFT_UNIT_POINTS points); its CTA accumulates the windows of its points into
-// an E^3 shared-memory block (E = 16 + 2m - 1, the tile plus the window halo)
-// and writes the block out whole.  A fold kernel then adds, for every grid
-// node, the blocks that cover it in unit order -- a fixed order, so the grid
-// does not depend on scheduling between units.
-// Gather.  The CTA of a unit stages the E^3 block of the grid around its tile
-// in shared memory; a warp evaluates one target: lanes split the (2m)^2 (y, x)
-// pairs of the footprint, loop over the 2m z-planes, and reduce by shuffles.
-// FFT.  Radix-2 decimation-in-time on lines of n <= 256 complex values in
-// shared memory (bit-reversed load, log2 n butterfly stages), 16 lines per CTA,
-// lines adjacent in memory so every load and store is coalesced; passes along
-// x, y, z.  The z pass multiplies by scale_k (zero outside I_N^3) between its
-// forward and inverse transforms.
+// Work units.  Points are sorted by grid cell, cells tile by tile (8^3 cells
+// per tile).  A unit is (tile, up to NFFT_UNIT_POINTS points); its CTA owns the
+// E^3 block of grid nodes the tile's windows reach (E = 8 + 2m - 1).  Chunks
+// of NFFT_CHUNK points -- window table rows, packed cells, weights -- are
+// staged in shared memory by double-buffered 1-D bulk copies (TMA) completing
+// on mbarriers, so the copy of chunk k+1 overlaps the arithmetic of chunk k.
+// Spread.  Thread (row (kz, ky), half) owns the m nodes kx in [half m, half m
+// + m) of footprint row (kz, ky).  The points of one cell share the footprint:
+// their rank-1 window products w phi_z phi_y phi_x accumulate in registers and
+// are added to the shared block once per cell, a barrier separating the
+// additions of consecutive cells (no shared-memory atomics).  The finished
+// block is added into the grid with global reductions, skipping zeros.
+// Gather.  The CTA stages the E^3 grid block around its tile; each warp
+// evaluates one target at a time: lanes split the (2m)^2 (y, x) pairs of the
+// footprint, each lane contracting its z-columns with phi_z; consecutive
+// targets of one cell reuse the footprint held in registers.
 #include <math.h>
 
 #include "nfft.cuh"
@@ -24,13 +26,60 @@ namespace uotk {
 
 namespace {
 
-constexpr int FFT_LINES = 16;
-constexpr int FFT_THREADS = 256;
+constexpr int CH = NFFT_CHUNK;
+constexpr int STAGES = 2;
 
-// ---------------------------------------------------------------- spread ----
-constexpr int CH = 64;  // points staged in shared memory per chunk
+template <int M>
+struct Geo {
+  static constexpr int W2 = 2 * M;
+  static constexpr int E = NFFT_TILE + 2 * M - 1;
+  static constexpr int E2 = E * E;
+  static constexpr int E3 = E2 * E;
+  static constexpr int E3P = (E3 + 3) & ~3;           // block floats, 16-byte multiple
+  static constexpr int WS = nfft_win_stride(M);      // floats per window-table row
+  static constexpr int STAGE_F = CH * WS + 2 * (CH + 4);  // floats per staging buffer
+};
 
-// M floats of a window row from shared memory (8-byte vector loads when M is even).
+// Issue the bulk copies of chunk `k` of a unit into staging buffer `st`:
+// the window rows (16-byte aligned by construction), and the packed cells and
+// weights from the 16-byte-aligned element at or below the chunk start, whose
+// offset `off` (0..3) the consumer adds back.
+template <int M>
+__device__ __forceinline__ void stage_chunk(float* st, unsigned long long* bar, const float* win,
+                                            const int* ckey, const float* wts, int q0, int cn) {
+  using G = Geo<M>;
+  const int off = q0 & 3;
+  const unsigned wbytes = (unsigned)(cn * G::WS * 4);
+  const unsigned kbytes = (unsigned)(((cn + off + 3) & ~3) * 4);
+  mbar_expect(bar, wbytes + (wts ? 2 * kbytes : kbytes));
+  bulk_copy(st, win + (size_t)q0 * G::WS, wbytes, bar);
+  bulk_copy(st + CH * G::WS, ckey + (q0 - off), kbytes, bar);
+  if (wts) bulk_copy(st + CH * G::WS + CH + 4, wts + (q0 - off), kbytes, bar);
+}
+
+// Bounded wait for a staging buffer; on time-out every thread learns it, the
+// copies still in flight are waited for (bounded) and the CTA leaves.
+__device__ __forceinline__ bool stage_ready(unsigned long long* bars, int k, int nchunks,
+                                            long long* flags) {
+  const bool ok = mbar_wait(&bars[k % STAGES], (unsigned)(k / STAGES) & 1u);
+  if (__syncthreads_or(!ok)) {
+    if (threadIdx.x == 0) {
+      flag_add(&flags[FLAG_TIMEOUT], 1LL);
+      for (int q = k; q < nchunks && q < k + STAGES; ++q)
+        mbar_wait(&bars[q % STAGES], (unsigned)(q / STAGES) & 1u);
+    }
+    return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void tile_origin(int tile, int tiles1, int& x, int& y, int& z) {
+  x = (tile % tiles1) * NFFT_TILE;
+  y = ((tile / tiles1) % tiles1) * NFFT_TILE;
+  z = (tile / (tiles1 * tiles1)) * NFFT_TILE;
+}
+
+// M floats of a window row from shared memory (8-byte loads when M is even).
 template <int M>
 __device__ __forceinline__ void load_row(const float* p, float* r) {
   if (M % 2 == 0) {
@@ -46,48 +95,43 @@ __device__ __forceinline__ void load_row(const float* p, float* r) {
   }
 }
 
-// One CTA per work unit.  Thread (row r = (kz, ky), half) owns the M nodes
-// kx in [half*M, half*M + M) of footprint row (kz, ky).  The points of one grid
-// cell share the footprint: their rank-1 window products are accumulated in
-// registers, then added to the block once; a barrier separates the additions of
-// consecutive cells, so no two threads ever update a node at the same time.
+// ---------------------------------------------------------------- spread ----
 template <int M>
 __global__ void __launch_bounds__(8 * M * M)
-    k_spread(const int4* __restrict__ cell, const float* __restrict__ win,
-             const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
-             const int* __restrict__ unit_count, const int* __restrict__ num_units, int tiles1,
-             const float* __restrict__ base, const double* __restrict__ pot, double lam,
-             const long long* __restrict__ shift_slot, float* __restrict__ part) {
-  constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E3 = E * E * E, WIN = 3 * W2;
-  constexpr int NT = 8 * M * M;
-  extern __shared__ float smem[];
+    k_spread(const float* __restrict__ win, const int* __restrict__ ckey,
+             const float* __restrict__ wts, const int* __restrict__ unit_tile,
+             const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
+             const int* __restrict__ num_units, int n, int tiles1, float* __restrict__ grid,
+             long long* __restrict__ flags) {
+  using G = Geo<M>;
+  constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M;
+  extern __shared__ __align__(16) float smem[];
+  __shared__ __align__(8) unsigned long long bars[STAGES];
   float* blk = smem;
-  float* swin = blk + E3 + (E3 & 1);  // 8-byte aligned
-  float* sw = swin + CH * WIN;
-  int* skey = reinterpret_cast<int*>(sw + CH);
+  float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
   if (u >= *num_units) return;
+  const int b0 = unit_begin[u], cnt = unit_count[u];
+  const int nchunks = (cnt + CH - 1) / CH;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+    for (int k = 0; k < STAGES && k < nchunks; ++k)
+      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, wts, b0 + k * CH,
+                     min(CH, cnt - k * CH));
+  }
   for (int i = threadIdx.x; i < E3; i += NT) blk[i] = 0.f;
-  const int tile = unit_tile[u];
-  const int tx0 = (tile % tiles1) * NFFT_TILE;
-  const int ty0 = ((tile / tiles1) % tiles1) * NFFT_TILE;
-  const int tz0 = (tile / (tiles1 * tiles1)) * NFFT_TILE;
+  __syncthreads();  // barriers initialised and block zeroed before anyone waits or adds
+  int tx0, ty0, tz0;
+  tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
   const int kz = r / W2, ky = r - kz * W2, kx0 = half * M;
-  const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
-  const int b0 = unit_begin[u], cnt = unit_count[u];
-  for (int c0 = 0; c0 < cnt; c0 += CH) {
-    const int cn = min(CH, cnt - c0);
-    __syncthreads();
-    const float* gw = win + (size_t)(b0 + c0) * WIN;
-    for (int i = threadIdx.x; i < cn * WIN; i += NT) swin[i] = gw[i];
-    for (int i = threadIdx.x; i < cn; i += NT) {
-      const int q = b0 + c0 + i;
-      const float bq = base ? base[q] : 1.f;
-      sw[i] = pot ? bq * exp_shifted(lam * pot[q] - shift) : bq;
-      skey[i] = cell[q].x;
-    }
-    __syncthreads();
+  for (int k = 0; k < nchunks; ++k) {
+    if (!stage_ready(bars, k, nchunks, flags)) return;
+    const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), off = q0 & 3;
+    const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
+    const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + off;
+    const float* swt = sw + CH * WS + CH + 4 + off;
     int p = 0;
     while (p < cn) {
       const int key = skey[p];
@@ -96,8 +140,8 @@ __global__ void __launch_bounds__(8 * M * M)
       for (int j = 0; j < M; ++j) acc[j] = 0.f;
       int q = p;
       for (; q < cn && skey[q] == key; ++q) {
-        const float* wq = swin + q * WIN;
-        const float a = sw[q] * wq[2 * W2 + kz] * wq[W2 + ky];
+        const float* wq = sw + q * WS;
+        const float a = swt[q] * wq[2 * W2 + kz] * wq[W2 + ky];
         float fx[M];
         load_row<M>(wq + kx0, fx);
 #pragma unroll
@@ -110,124 +154,68 @@ __global__ void __launch_bounds__(8 * M * M)
       __syncthreads();
       p = q;
     }
+    if (threadIdx.x == 0 && k + STAGES < nchunks)
+      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, wts,
+                     b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
   }
   __syncthreads();
-  float* out = part + (size_t)u * E3;
-  for (int i = threadIdx.x; i < E3; i += NT) out[i] = blk[i];
-}
-
-// Grid node g (per dimension) is covered by the block of tile t at local index
-// l = g - t*T + m - 1 (mod n), when l lies in [0, E).  General form (aliases
-// when E > n) and the direct form for n >= 2E.
-__device__ __forceinline__ int covers(int g, int n, int tiles1, int m, int E, int* tl, int* ll) {
-  int k = 0;
-  if (n >= 2 * E) {
-    const int top = (g + m - 1) >= 0 ? (g + m - 1) / NFFT_TILE : -1;
-    for (int t = top; k < 8; --t) {
-      const int l = g + m - 1 - t * NFFT_TILE;
-      if (l >= E) break;
-      tl[k] = ((t % tiles1) + tiles1) % tiles1;
-      ll[k] = l;
-      ++k;
-    }
-    return k;
-  }
-  for (int t = 0; t < tiles1 && k < 8; ++t) {
-    int l = g - t * NFFT_TILE + m - 1;
-    l %= n;
-    if (l < 0) l += n;
-    for (; l < E && k < 8; l += n) { tl[k] = t; ll[k] = l; ++k; }
-  }
-  return k;
-}
-
-__global__ void k_fold(const float* __restrict__ part, const int* __restrict__ tile_unit_start,
-                       int n, int tiles1, int m, int E, float* __restrict__ grid) {
-  const long long total = (long long)n * n * n;
-  const long long E2 = (long long)E * E, E3 = E2 * E;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int gx = (int)(i % n), gy = (int)((i / n) % n), gz = (int)(i / ((long long)n * n));
-    int txl[8], lxl[8], tyl[8], lyl[8], tzl[8], lzl[8];
-    const int nx = covers(gx, n, tiles1, m, E, txl, lxl);
-    const int ny = covers(gy, n, tiles1, m, E, tyl, lyl);
-    const int nz = covers(gz, n, tiles1, m, E, tzl, lzl);
-    float acc = 0.f;
-    for (int a = 0; a < nz; ++a)
-      for (int b = 0; b < ny; ++b)
-        for (int c = 0; c < nx; ++c) {
-          const int tile = (tzl[a] * tiles1 + tyl[b]) * tiles1 + txl[c];
-          const long long loc = ((long long)lzl[a] * E + lyl[b]) * E + lxl[c];
-          for (int u = tile_unit_start[tile]; u < tile_unit_start[tile + 1]; ++u)
-            acc += part[(long long)u * E3 + loc];
-        }
-    grid[i] = acc;
+  for (int i = threadIdx.x; i < E3; i += NT) {
+    const float v = blk[i];
+    if (v == 0.f) continue;
+    const int lz = i / G::E2, ly = (i / E) % E, lx = i % E;
+    int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
+    gz += gz < 0 ? n : 0;
+    gy += gy < 0 ? n : 0;
+    gx += gx < 0 ? n : 0;
+    atomicAdd(&grid[((long long)gz * n + gy) * n + gx], v);
   }
 }
 
-// Fold for grids of at least 3 tiles per dimension: one CTA per output tile
-// (T^3 threads, one node each).  The blocks that can cover the tile are those
-// of the 27 neighbouring tiles (E - m + 1 <= 2T and T + m - 1 < 2T for T = 8,
-// m <= 8); each node adds the covering block values unit by unit, neighbours
-// in a fixed order.
-__global__ void __launch_bounds__(NFFT_TILE * NFFT_TILE * NFFT_TILE)
-    k_fold_tiles(const float* __restrict__ part, const int* __restrict__ tile_unit_start, int n,
-                 int tiles1, int m, int E, float* __restrict__ grid) {
-  const int t = blockIdx.x;
-  const int tx = t % tiles1, ty = (t / tiles1) % tiles1, tz = t / (tiles1 * tiles1);
-  const int lx = threadIdx.x % NFFT_TILE, ly = (threadIdx.x / NFFT_TILE) % NFFT_TILE,
-            lz = threadIdx.x / (NFFT_TILE * NFFT_TILE);
-  const long long E3 = (long long)E * E * E;
-  float acc = 0.f;
-  for (int dz = -1; dz <= 1; ++dz) {
-    const int bz = lz - dz * NFFT_TILE + m - 1;
-    if (bz < 0 || bz >= E) continue;
-    const int nz = (tz + dz + tiles1) % tiles1;
-    for (int dy = -1; dy <= 1; ++dy) {
-      const int by = ly - dy * NFFT_TILE + m - 1;
-      if (by < 0 || by >= E) continue;
-      const int ny = (ty + dy + tiles1) % tiles1;
-      for (int dx = -1; dx <= 1; ++dx) {
-        const int bx = lx - dx * NFFT_TILE + m - 1;
-        if (bx < 0 || bx >= E) continue;
-        const int nx = (tx + dx + tiles1) % tiles1;
-        const int nt = (nz * tiles1 + ny) * tiles1 + nx;
-        const long long loc = ((long long)bz * E + by) * E + bx;
-        for (int u = tile_unit_start[nt]; u < tile_unit_start[nt + 1]; ++u)
-          acc += part[(long long)u * E3 + loc];
-      }
-    }
-  }
-  const int gx = tx * NFFT_TILE + lx, gy = ty * NFFT_TILE + ly, gz = tz * NFFT_TILE + lz;
-  grid[((long long)gz * n + gy) * n + gx] = acc;
+// Spread weights in sorted order: w_q = base_q exp(lam pot_q - shift).
+__global__ void k_point_weights(const float* __restrict__ base, const double* __restrict__ pot,
+                                double lam, const long long* __restrict__ shift_slot, long long n,
+                                float* __restrict__ out) {
+  const double shift = ordered_to_dbl(*shift_slot);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n + 4;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = i < n ? (base ? base[i] : 1.f) * exp_shifted(lam * pot[i] - shift) : 0.f;
 }
 
 // ------------------------------------------------------------------ FFT ----
+// Radix-2 decimation in time on lines held in shared memory in bit-reversed
+// order: line l, element e at buf[l * lstride + e * estride].  tw[j] =
+// exp(-2 pi i j/n), j < n/2; dir = +1 takes the conjugate twiddles (inverse,
+// unnormalised).  Called by all threads of the CTA; ends with a barrier.
+constexpr int FFT_LINES = 16;
+constexpr int FFT_THREADS = 256;
+constexpr int SLAB_THREADS = 512;
+constexpr int SLAB_ROWS = 16;
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
-// In-place radix-2 DIT on FFT_LINES lines of length n held in bit-reversed
-// order in `buf` ([line][n]); tw[j] = exp(-2 pi i j / n), j < n/2; dir = +1
-// uses the conjugate twiddles (inverse, unnormalised).
-__device__ void fft_lines_smem(float2* buf, const float2* tw, int n, int logn, int dir) {
-  const int half_total = FFT_LINES * (n >> 1);
-  for (int s = 1; s <= logn; ++s) {
-    const int half = 1 << (s - 1);
-    const int tstep = n >> s;
-    for (int b = threadIdx.x; b < half_total; b += blockDim.x) {
-      const int line = b / (n >> 1);
-      const int j = b - line * (n >> 1);
-      const int grp = j >> (s - 1);
+__device__ void fft_smem(float2* buf, int lines, int lstride, int estride, const float2* tw, int n,
+                         int logn, int dir) {
+  const int hn = n >> 1;
+  const int total = lines * hn;
+  for (int st = 1; st <= logn; ++st) {
+    const int half = 1 << (st - 1);
+    const int tstep = n >> st;
+    for (int b = threadIdx.x; b < total; b += blockDim.x) {
+      const int line = b / hn;
+      const int j = b - line * hn;
+      const int grp = j >> (st - 1);
       const int pos = j & (half - 1);
-      const int i0 = line * n + grp * 2 * half + pos;
-      const int i1 = i0 + half;
+      const int e0 = grp * 2 * half + pos;
+      float2* p0 = buf + line * lstride + e0 * estride;
+      float2* p1 = p0 + half * estride;
       float2 w = tw[pos * tstep];
       if (dir > 0) w.y = -w.y;
-      const float2 t = cmul(w, buf[i1]);
-      const float2 a = buf[i0];
-      buf[i0] = make_float2(a.x + t.x, a.y + t.y);
-      buf[i1] = make_float2(a.x - t.x, a.y - t.y);
+      const float2 t = cmul(w, *p1);
+      const float2 a = *p0;
+      *p0 = make_float2(a.x + t.x, a.y + t.y);
+      *p1 = make_float2(a.x - t.x, a.y - t.y);
     }
     __syncthreads();
   }
@@ -241,7 +229,124 @@ __device__ __forceinline__ void load_twiddles(float2* tw, int n) {
   }
 }
 
-// Line geometry: axis 0 = x (lines are rows), 1 = y, 2 = z.  Line L, element e.
+__device__ __forceinline__ int bitrev(int e, int logn) { return (int)(__brev((unsigned)e) >> (32 - logn)); }
+// FFT index of the k' th kept frequency, k = k' - N/2 in I_N.
+__device__ __forceinline__ int kept_index(int kp, int N, int n) {
+  const int k = kp - N / 2;
+  return k < 0 ? k + n : k;
+}
+
+// Forward transform of one z-slab: x then y, both pruned to I_N.
+// in: real grid [z][y][x];  out: A[z][ky'][kx'] complex, n x N x N.
+__global__ void __launch_bounds__(SLAB_THREADS)
+    k_fft_slab_fwd(const float* __restrict__ g, float2* __restrict__ A, int n, int logn, int N) {
+  extern __shared__ __align__(16) float2 fsh[];
+  float2* tw = fsh;
+  float2* col = fsh + n / 2;            // [n (y, bit-reversed)][N (kx')]
+  float2* rows = col + (size_t)n * N;   // [SLAB_ROWS][n]
+  load_twiddles(tw, n);
+  const int z = blockIdx.x;
+  const float* gz = g + (size_t)z * n * n;
+  for (int r0 = 0; r0 < n; r0 += SLAB_ROWS) {
+    for (int i = threadIdx.x; i < SLAB_ROWS * n; i += blockDim.x) {
+      const int r = i / n, x = i - r * n;
+      rows[r * n + bitrev(x, logn)] = make_float2(gz[(size_t)(r0 + r) * n + x], 0.f);
+    }
+    __syncthreads();
+    fft_smem(rows, SLAB_ROWS, n, 1, tw, n, logn, -1);
+    for (int i = threadIdx.x; i < SLAB_ROWS * N; i += blockDim.x) {
+      const int r = i / N, kp = i - r * N;
+      col[bitrev(r0 + r, logn) * N + kp] = rows[r * n + kept_index(kp, N, n)];
+    }
+    __syncthreads();
+  }
+  fft_smem(col, N, 1, N, tw, n, logn, -1);
+  float2* Az = A + (size_t)z * N * N;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int kyp = i / N, kxp = i - kyp * N;
+    Az[i] = col[kept_index(kyp, N, n) * N + kxp];
+  }
+}
+
+// z lines: forward FFT, keep I_N and multiply by scale_k, inverse FFT.
+// In place on A[z][ky'][kx'] (n x N x N); FFT_LINES adjacent kx' per CTA.
+__global__ void __launch_bounds__(FFT_THREADS)
+    k_fft_zlines(float2* __restrict__ A, int n, int logn, int N, const float* __restrict__ scale) {
+  extern __shared__ __align__(16) float2 fsh[];
+  float2* tw = fsh;
+  float2* a = fsh + n / 2;                // [FFT_LINES][n]
+  float2* b = a + FFT_LINES * n;          // [FFT_LINES][n]
+  load_twiddles(tw, n);
+  const int line0 = blockIdx.x * FFT_LINES;  // line = ky' * N + kx'
+  const size_t zs = (size_t)N * N;
+  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
+    const int z = i / FFT_LINES, l = i - z * FFT_LINES;
+    a[l * n + bitrev(z, logn)] = A[(size_t)z * zs + line0 + l];
+  }
+  __syncthreads();
+  fft_smem(a, FFT_LINES, n, 1, tw, n, logn, -1);
+  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
+    const int l = i / n, e = i - l * n;
+    const int line = line0 + l;
+    const int kyp = line / N, kxp = line - kyp * N;
+    const int kz = e < n / 2 ? e : e - n;
+    float2 v = make_float2(0.f, 0.f);
+    if (kz >= -N / 2 && kz < N / 2) {
+      const float f = scale[kxp] * scale[N + kyp] * scale[2 * N + kz + N / 2];
+      const float2 u = a[l * n + e];
+      v = make_float2(u.x * f, u.y * f);
+    }
+    b[l * n + bitrev(e, logn)] = v;
+  }
+  __syncthreads();
+  fft_smem(b, FFT_LINES, n, 1, tw, n, logn, +1);
+  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
+    const int z = i / FFT_LINES, l = i - z * FFT_LINES;
+    A[(size_t)z * zs + line0 + l] = b[l * n + z];
+  }
+}
+
+// Inverse transform of one z-slab: y then x from the I_N^2 coefficients,
+// real part out.  in: A[z][ky'][kx'];  out: real grid [z][y][x].
+__global__ void __launch_bounds__(SLAB_THREADS)
+    k_fft_slab_inv(const float2* __restrict__ A, float* __restrict__ g, int n, int logn, int N) {
+  extern __shared__ __align__(16) float2 fsh[];
+  float2* tw = fsh;
+  float2* col = fsh + n / 2;
+  float2* rows = col + (size_t)n * N;
+  load_twiddles(tw, n);
+  const int z = blockIdx.x;
+  const float2* Az = A + (size_t)z * N * N;
+  for (int i = threadIdx.x; i < n * N; i += blockDim.x) col[i] = make_float2(0.f, 0.f);
+  __syncthreads();
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
+    const int kyp = i / N, kxp = i - kyp * N;
+    col[bitrev(kept_index(kyp, N, n), logn) * N + kxp] = Az[i];
+  }
+  __syncthreads();
+  fft_smem(col, N, 1, N, tw, n, logn, +1);
+  float* gz = g + (size_t)z * n * n;
+  for (int r0 = 0; r0 < n; r0 += SLAB_ROWS) {
+    for (int i = threadIdx.x; i < SLAB_ROWS * n; i += blockDim.x) rows[i] = make_float2(0.f, 0.f);
+    __syncthreads();
+    for (int i = threadIdx.x; i < SLAB_ROWS * N; i += blockDim.x) {
+      const int r = i / N, kp = i - r * N;
+      rows[r * n + bitrev(kept_index(kp, N, n), logn)] = col[(r0 + r) * N + kp];
+    }
+    __syncthreads();
+    fft_smem(rows, SLAB_ROWS, n, 1, tw, n, logn, +1);
+    for (int i = threadIdx.x; i < SLAB_ROWS * n; i += blockDim.x) {
+      const int r = i / n, x = i - r * n;
+      gz[(size_t)(r0 + r) * n + x] = rows[i].x;
+    }
+    __syncthreads();
+  }
+}
+
+// Unpruned passes for large grids (n > 128): one FFT pass along `axis` on
+// FFT_LINES lines adjacent in memory.  mode 0: real in -> complex out;
+// mode 1: complex -> complex; mode 2: complex in -> real part out; mode 3:
+// z pass: forward, multiply by scale_k on I_N^3, inverse.
 __device__ __forceinline__ long long line_addr(int axis, int n, long long L, int e) {
   const long long n2 = (long long)n * n;
   if (axis == 0) return L * n + e;
@@ -249,32 +354,26 @@ __device__ __forceinline__ long long line_addr(int axis, int n, long long L, int
   return (long long)e * n2 + L;
 }
 
-// One FFT pass along `axis`.  mode 0: real in -> complex out (forward);
-// mode 1: complex -> complex; mode 2: complex in -> real part out (inverse);
-// mode 3: z pass: forward, multiply by scale_k on I_N^3, inverse.
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_pass(const float* __restrict__ rin, const float2* __restrict__ cin,
                float* __restrict__ rout, float2* __restrict__ cout, int n, int logn, int axis,
                int mode, int dir, const float* __restrict__ scale, int N) {
-  extern __shared__ float2 sh[];
-  float2* tw = sh;
-  float2* buf = sh + n / 2;
+  extern __shared__ __align__(16) float2 fsh[];
+  float2* tw = fsh;
+  float2* buf = fsh + n / 2;
   load_twiddles(tw, n);
   const long long L0 = (long long)blockIdx.x * FFT_LINES;
   for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
-    // consecutive threads take consecutive lines for y/z passes (coalesced),
-    // consecutive elements for x passes
     int line, e;
     if (axis == 0) { line = i / n; e = i - line * n; }
     else { e = i / FFT_LINES; line = i - e * FFT_LINES; }
-    const long long a = line_addr(axis, n, L0 + line, e);
-    const float2 v = mode == 0 ? make_float2(rin[a], 0.f) : cin[a];
-    buf[line * n + (__brev(e) >> (32 - logn))] = v;
+    const long long ad = line_addr(axis, n, L0 + line, e);
+    const float2 v = mode == 0 ? make_float2(rin[ad], 0.f) : cin[ad];
+    buf[line * n + bitrev(e, logn)] = v;
   }
   __syncthreads();
-  fft_lines_smem(buf, tw, n, logn, mode == 3 ? -1 : dir);
+  fft_smem(buf, FFT_LINES, n, 1, tw, n, logn, mode == 3 ? -1 : dir);
   if (mode == 3) {
-    // multiply by scale_k: line L = y*n + x carries (kx, ky); element = kz
     for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
       const int line = i / n, e = i - line * n;
       const long long L = L0 + line;
@@ -287,10 +386,9 @@ __global__ void __launch_bounds__(FFT_THREADS)
       buf[i] = make_float2(v.x * f, v.y * f);
     }
     __syncthreads();
-    // bit-reverse in place for the inverse transform
     for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
       const int line = i / n, e = i - line * n;
-      const int r = __brev(e) >> (32 - logn);
+      const int r = bitrev(e, logn);
       if (r > e) {
         const float2 t = buf[line * n + e];
         buf[line * n + e] = buf[line * n + r];
@@ -298,43 +396,50 @@ __global__ void __launch_bounds__(FFT_THREADS)
       }
     }
     __syncthreads();
-    fft_lines_smem(buf, tw, n, logn, +1);
+    fft_smem(buf, FFT_LINES, n, 1, tw, n, logn, +1);
   }
   for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
     int line, e;
     if (axis == 0) { line = i / n; e = i - line * n; }
     else { e = i / FFT_LINES; line = i - e * FFT_LINES; }
-    const long long a = line_addr(axis, n, L0 + line, e);
+    const long long ad = line_addr(axis, n, L0 + line, e);
     const float2 v = buf[line * n + e];
-    if (mode == 2) rout[a] = v.x;
-    else cout[a] = v;
+    if (mode == 2) rout[ad] = v.x;
+    else cout[ad] = v;
   }
 }
 
 // ---------------------------------------------------------------- gather ----
-// One CTA per work unit: the E^3 block of the grid around the tile is staged
-// in shared memory, then each warp evaluates one target at a time.
 template <int M>
 __global__ void __launch_bounds__(256)
-    k_gather(const int4* __restrict__ cell, const float* __restrict__ win,
+    k_gather(const float* __restrict__ win, const int* __restrict__ ckey,
              const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
              const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
-             int tiles1, const float* __restrict__ grid, float* __restrict__ out) {
-  constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E2 = E * E, E3 = E2 * E, WIN = 3 * W2;
+             int tiles1, const float* __restrict__ grid, float* __restrict__ out,
+             long long* __restrict__ flags) {
+  using G = Geo<M>;
+  constexpr int W2 = G::W2, E = G::E, E2 = G::E2, E3 = G::E3, WS = G::WS;
   constexpr int NIT = (W2 * W2 + 31) / 32;
-  // Footprint values of the current cell kept in registers while a warp's
-  // consecutive targets share that cell (targets are sorted by cell).
+  // Footprint of the current cell kept in registers while a warp's consecutive
+  // targets share that cell.
   constexpr bool CACHE = NIT * W2 <= 64;
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) float smem[];
+  __shared__ __align__(8) unsigned long long bars[STAGES];
   float* blk = smem;
-  float* swin = blk + E3 + (E3 & 1);
-  int* skey = reinterpret_cast<int*>(swin + CH * WIN);
+  float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
   if (u >= *num_units) return;
-  const int tile = unit_tile[u];
-  const int tx0 = (tile % tiles1) * NFFT_TILE;
-  const int ty0 = ((tile / tiles1) % tiles1) * NFFT_TILE;
-  const int tz0 = (tile / (tiles1 * tiles1)) * NFFT_TILE;
+  const int b0 = unit_begin[u], cnt = unit_count[u];
+  const int nchunks = (cnt + CH - 1) / CH;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    mbar_fence_init();
+    for (int k = 0; k < STAGES && k < nchunks; ++k)
+      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * CH,
+                     min(CH, cnt - k * CH));
+  }
+  int tx0, ty0, tz0;
+  tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   for (int i = threadIdx.x; i < E3; i += blockDim.x) {
     const int lz = i / E2, ly = (i / E) % E, lx = i % E;
     int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
@@ -343,6 +448,7 @@ __global__ void __launch_bounds__(256)
     gx += gx < 0 ? n : 0;
     blk[i] = grid[((long long)gz * n + gy) * n + gx];
   }
+  __syncthreads();  // barriers initialised and block staged before anyone waits or reads
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   int off[NIT], kxs[NIT], kys[NIT];
 #pragma unroll
@@ -354,37 +460,34 @@ __global__ void __launch_bounds__(256)
   }
   float hc[CACHE ? NIT * W2 : 1];
   int cached = -1;
-  const int b0 = unit_begin[u], cnt = unit_count[u];
-  for (int c0 = 0; c0 < cnt; c0 += CH) {
-    const int cn = min(CH, cnt - c0);
-    __syncthreads();
-    const float* gw = win + (size_t)(b0 + c0) * WIN;
-    for (int i = threadIdx.x; i < cn * WIN; i += blockDim.x) swin[i] = gw[i];
-    for (int i = threadIdx.x; i < cn; i += blockDim.x) skey[i] = cell[b0 + c0 + i].x;
-    __syncthreads();
+  for (int k = 0; k < nchunks; ++k) {
+    if (!stage_ready(bars, k, nchunks, flags)) return;
+    const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), koff = q0 & 3;
+    const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
+    const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + koff;
     for (int p = warp; p < cn; p += nwarps) {
       const int key = skey[p];
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-      const float* wq = swin + p * WIN;
+      const float* wq = sw + p * WS;
       const float* src = blk + (bz * E + by) * E + bx;
       float fz[W2];
 #pragma unroll
-      for (int k = 0; k < W2; ++k) fz[k] = wq[2 * W2 + k];
+      for (int kk = 0; kk < W2; ++kk) fz[kk] = wq[2 * W2 + kk];
       float acc = 0.f;
       if (CACHE) {
         if (key != cached) {
 #pragma unroll
           for (int it = 0; it < NIT; ++it)
 #pragma unroll
-            for (int k = 0; k < W2; ++k)
-              hc[CACHE ? it * W2 + k : 0] = off[it] >= 0 ? src[k * E2 + off[it]] : 0.f;
+            for (int kk = 0; kk < W2; ++kk)
+              hc[CACHE ? it * W2 + kk : 0] = off[it] >= 0 ? src[kk * E2 + off[it]] : 0.f;
           cached = key;
         }
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
           float s = 0.f;
 #pragma unroll
-          for (int k = 0; k < W2; ++k) s = fmaf(fz[k], hc[CACHE ? it * W2 + k : 0], s);
+          for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], hc[CACHE ? it * W2 + kk : 0], s);
           const float pxy = off[it] >= 0 ? wq[kxs[it]] * wq[W2 + kys[it]] : 0.f;
           acc = fmaf(pxy, s, acc);
         }
@@ -396,32 +499,36 @@ __global__ void __launch_bounds__(256)
             const float* col = src + off[it];
             float s = 0.f;
 #pragma unroll
-            for (int k = 0; k < W2; ++k) s = fmaf(fz[k], col[k * E2], s);
+            for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], col[kk * E2], s);
             acc = fmaf(pxy, s, acc);
           }
         }
       }
       acc = warp_sum(acc);
-      if (lane == 0) out[b0 + c0 + p] = acc;
+      if (lane == 0) out[q0 + p] = acc;
     }
+    __syncthreads();
+    if (threadIdx.x == 0 && k + STAGES < nchunks)
+      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, nullptr,
+                     b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
   }
 }
 
 template <int M>
-size_t spread_smem() {
-  constexpr int E = NFFT_TILE + 2 * M - 1, E3 = E * E * E;
-  return sizeof(float) * (E3 + 1 + CH * 6 * M + 2 * CH);
+size_t unit_smem() {
+  using G = Geo<M>;
+  return sizeof(float) * (G::E3P + STAGES * G::STAGE_F);
 }
 
 template <int M>
 uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
-                          const NfftPoints& S, const SpreadWeights& w, float* part) {
-  const size_t smem = spread_smem<M>();
+                          const NfftPoints& S, const float* wts, float* grid) {
+  const size_t smem = unit_smem<M>();
   UOTK_CUDA(ctx, cudaFuncSetAttribute(k_spread<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-  k_spread<M><<<S.max_units, 8 * M * M, smem, s>>>(S.cell, S.win, S.unit_tile, S.unit_begin,
-                                                   S.unit_count, S.num_units, P.tiles1, w.base,
-                                                   w.pot, w.lam, w.shift_slot, part);
+  k_spread<M><<<S.max_units, 8 * M * M, smem, s>>>(S.win, S.ckey, wts, S.unit_tile, S.unit_begin,
+                                                   S.unit_count, S.num_units, P.n, P.tiles1, grid,
+                                                   ctx->dflags);
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -429,11 +536,12 @@ uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
 template <int M>
 uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* grid, float* out) {
-  const size_t smem = spread_smem<M>();
+  const size_t smem = unit_smem<M>();
   UOTK_CUDA(ctx, cudaFuncSetAttribute(k_gather<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)smem));
-  k_gather<M><<<S.max_units, 256, smem, s>>>(S.cell, S.win, S.unit_tile, S.unit_begin,
-                                             S.unit_count, S.num_units, P.n, P.tiles1, grid, out);
+  k_gather<M><<<S.max_units, 256, smem, s>>>(S.win, S.ckey, S.unit_tile, S.unit_begin,
+                                             S.unit_count, S.num_units, P.n, P.tiles1, grid, out,
+                                             ctx->dflags);
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -453,8 +561,8 @@ uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
   }
 
 static uotk_status spread_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
-                                const NfftPoints& S, const SpreadWeights& w, float* part) {
-#define UOTK_SPREAD_CALL(M) launch_spread<M>(ctx, s, P, S, w, part)
+                                const NfftPoints& S, const float* wts, float* grid) {
+#define UOTK_SPREAD_CALL(M) launch_spread<M>(ctx, s, P, S, wts, grid)
   UOTK_M_SWITCH(P.m, UOTK_SPREAD_CALL)
 #undef UOTK_SPREAD_CALL
 }
@@ -468,51 +576,60 @@ static uotk_status gather_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams&
 
 uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
                         const SpreadWeights& w, NfftWork& W, float* grid_out) {
-  if (S.n > 0) {
-    UOTK_PROF(ctx, s, "spread");
-    UOTK_TRY(spread_units(ctx, s, P, S, w, W.part));
+  const long long total = (long long)P.n * P.n * P.n;
+  UOTK_CUDA(ctx, cudaMemsetAsync(grid_out, 0, sizeof(float) * total, s));
+  if (S.n == 0) return UOTK_OK;
+  const float* wts = w.base;
+  if (w.pot) {
+    UOTK_PROF(ctx, s, "weights");
+    k_point_weights<<<grid_for(ctx, S.n + 4, 256, 4), 256, 0, s>>>(w.base, w.pot, w.lam,
+                                                                   w.shift_slot, S.n, W.wts);
+    UOTK_LAUNCHED(ctx);
+    wts = W.wts;
   }
-  {
-    UOTK_PROF(ctx, s, "fold");
-    const long long total = (long long)P.n * P.n * P.n;
-    if (S.n > 0 && P.tiles1 >= 3) {
-      k_fold_tiles<<<P.tiles1 * P.tiles1 * P.tiles1, NFFT_TILE * NFFT_TILE * NFFT_TILE, 0, s>>>(
-          W.part, S.tile_unit_start, P.n, P.tiles1, P.m, P.E, grid_out);
-      UOTK_LAUNCHED(ctx);
-    } else if (S.n > 0) {
-      k_fold<<<grid_for(ctx, total, 256, 8), 256, 0, s>>>(W.part, S.tile_unit_start, P.n, P.tiles1,
-                                                          P.m, P.E, grid_out);
-      UOTK_LAUNCHED(ctx);
-    } else {
-      UOTK_CUDA(ctx, cudaMemsetAsync(grid_out, 0, sizeof(float) * total, s));
-    }
-  }
-  return UOTK_OK;
+  UOTK_PROF(ctx, s, "spread");
+  return spread_units(ctx, s, P, S, wts, grid_out);
 }
 
 uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W,
                           const float* grid_in, float* grid_out) {
-  const int n = P.n;
+  const int n = P.n, N = P.N;
   int logn = 0;
   while ((1 << logn) < n) ++logn;
+  UOTK_PROF(ctx, s, "fft");
+  const size_t slab_smem = sizeof(float2) * (n / 2 + (size_t)n * N + SLAB_ROWS * n);
+  if (n <= 128 && (N * N) % FFT_LINES == 0 && slab_smem <= (size_t)ctx->max_smem_optin) {
+    // pruned: forward x+y per slab, z lines with the scale, inverse y+x per slab
+    UOTK_CUDA(ctx, cudaFuncSetAttribute(k_fft_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)slab_smem));
+    UOTK_CUDA(ctx, cudaFuncSetAttribute(k_fft_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)slab_smem));
+    k_fft_slab_fwd<<<n, SLAB_THREADS, slab_smem, s>>>(grid_in, W.cgrid, n, logn, N);
+    UOTK_LAUNCHED(ctx);
+    const size_t zsmem = sizeof(float2) * (n / 2 + 2 * FFT_LINES * n);
+    k_fft_zlines<<<N * N / FFT_LINES, FFT_THREADS, zsmem, s>>>(W.cgrid, n, logn, N, W.scale);
+    UOTK_LAUNCHED(ctx);
+    k_fft_slab_inv<<<n, SLAB_THREADS, slab_smem, s>>>(W.cgrid, grid_out, n, logn, N);
+    UOTK_LAUNCHED(ctx);
+    return UOTK_OK;
+  }
   const int blocks = n * n / FFT_LINES;
   const size_t smem = sizeof(float2) * (n / 2 + FFT_LINES * n);
-  UOTK_PROF(ctx, s, "fft");
   // forward x (real -> complex), forward y, z (forward, scale, inverse), inverse y, inverse x
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(grid_in, nullptr, nullptr, W.cgrid, n, logn, 0, 0,
-                                               -1, nullptr, P.N);
+                                               -1, nullptr, N);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 1, 1,
-                                               -1, nullptr, P.N);
+                                               -1, nullptr, N);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 2, 3,
-                                               -1, W.scale, P.N);
+                                               -1, W.scale, N);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 1, 1,
-                                               +1, nullptr, P.N);
+                                               +1, nullptr, N);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, grid_out, nullptr, n, logn, 0, 2,
-                                               +1, nullptr, P.N);
+                                               +1, nullptr, N);
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -524,16 +641,16 @@ uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
   return gather_units(ctx, s, P, S, grid, out_sorted);
 }
 
-size_t nfft_work_bytes(const NfftParams& P, int max_src_units) {
+size_t nfft_work_bytes(const NfftParams& P, int64_t max_points) {
   Carver cv(nullptr);
   NfftWork W;
-  nfft_work_carve(cv, P, max_src_units, W);
+  nfft_work_carve(cv, P, max_points, W);
   return cv.off;
 }
 
-void nfft_work_carve(Carver& cv, const NfftParams& P, int max_src_units, NfftWork& W) {
+void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWork& W) {
   const size_t n3 = (size_t)P.n * P.n * P.n;
-  W.part = cv.take<float>((size_t)(max_src_units > 0 ? max_src_units : 1) * P.E * P.E * P.E);
+  W.wts = cv.take<float>((size_t)(max_points > 0 ? max_points : 1) + 4);
   W.grid = cv.take<float>(n3);
   W.cgrid = cv.take<float2>(n3);
   W.scale = cv.take<float>(3 * P.N);

@@ -231,12 +231,14 @@ __global__ void k_bin_scan(int* __restrict__ count, int tiles, int unit_pts,
 __global__ void k_bin_scatter(const int4* __restrict__ tmp_cell, const int* __restrict__ tmp_key,
                               long long n, const int* __restrict__ cell_start,
                               int* __restrict__ cursor, int4* __restrict__ cell,
-                              int* __restrict__ perm) {
+                              int* __restrict__ ckey, int* __restrict__ perm) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
     const int k = tmp_key[i];
     const int pos = cell_start[k] + atomicAdd(&cursor[k], 1);
-    cell[pos] = tmp_cell[i];
+    const int4 c = tmp_cell[i];
+    cell[pos] = c;
+    ckey[pos] = c.x;
     perm[pos] = (int)i;
   }
 }
@@ -269,11 +271,12 @@ __device__ __forceinline__ float kb_window(float v, int m, float b) {
 
 __global__ void k_windows(const int4* __restrict__ cell, long long n, int m, float b,
                           int d, float* __restrict__ win) {
-  const int w2 = 2 * m;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * 3 * w2;
+  const int w2 = 2 * m, ws = nfft_win_stride(m);
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * ws;
        i += (long long)gridDim.x * blockDim.x) {
-    const long long q = i / (3 * w2);
-    const int r = (int)(i - q * 3 * w2);
+    const long long q = i / ws;
+    const int r = (int)(i - q * ws);
+    if (r >= 3 * w2) { win[i] = 0.f; continue; }
     const int t = r / w2, k = r - t * w2;
     const int4 c = cell[q];
     const float f = __int_as_float(t == 0 ? c.y : (t == 1 ? c.z : c.w));
@@ -400,7 +403,8 @@ void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S
   S.n = n;
   S.max_units = nfft_max_units(P, n);
   S.cell = cv.take<int4>(nn);
-  S.win = cv.take<float>((size_t)nn * 3 * 2 * P.m);
+  S.ckey = cv.take<int>(nn + 4);
+  S.win = cv.take<float>((size_t)nn * nfft_win_stride(P.m));
   S.perm = cv.take<int>(nn);
   S.tile_start = cv.take<int>(tiles + 1);
   S.tile_unit_start = cv.take<int>(tiles + 1);
@@ -450,7 +454,7 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
     UOTK_LAUNCHED(ctx);
     if (n > 0) {
       k_bin_scatter<<<grid_for(ctx, n, 256), 256, 0, s>>>(tmp_cell, tmp_key, n, S.cell_start,
-                                                           S.cell_count, S.cell, S.perm);
+                                                           S.cell_count, S.cell, S.ckey, S.perm);
       UOTK_LAUNCHED(ctx);
     }
     k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.tile_unit_start, tiles,
@@ -460,7 +464,8 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
   }
   if (n > 0) {
     UOTK_PROF(ctx, s, "window");
-    k_windows<<<grid_for(ctx, n * 3 * 2 * P.m, 256), 256, 0, s>>>(S.cell, n, P.m, P.b, P.d, S.win);
+    k_windows<<<grid_for(ctx, n * nfft_win_stride(P.m), 256), 256, 0, s>>>(S.cell, n, P.m, P.b,
+                                                                         P.d, S.win);
     UOTK_LAUNCHED(ctx);
   }
   return UOTK_OK;
