@@ -188,8 +188,6 @@ __global__ void k_point_weights(const float* __restrict__ base, const double* __
 // unnormalised).  Called by all threads of the CTA; ends with a barrier.
 constexpr int FFT_LINES = 16;
 constexpr int FFT_THREADS = 256;
-constexpr int SLAB_THREADS = 512;
-constexpr int SLAB_ROWS = 16;
 
 __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
   return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
@@ -230,117 +228,230 @@ __device__ __forceinline__ void load_twiddles(float2* tw, int n) {
 }
 
 __device__ __forceinline__ int bitrev(int e, int logn) { return (int)(__brev((unsigned)e) >> (32 - logn)); }
-// FFT index of the k' th kept frequency, k = k' - N/2 in I_N.
-__device__ __forceinline__ int kept_index(int kp, int N, int n) {
-  const int k = kp - N / 2;
-  return k < 0 ? k + n : k;
+// ---- warp FFT: n = 32 R points, R complex values per lane -----------------
+// Lane L holds v[j] = x[32 j + L].  With m = 32 j + L and k = k1 + R k2,
+//   X[k] = sum_L W_32^{L k2} [ W_n^{L k1} sum_j x[32 j + L] W_R^{j k1} ],
+// so each lane first takes an R-point DFT over its registers, multiplies by
+// W_n^{L k1}, and the warp then takes 32-point DFTs across lanes by radix-2
+// decimation in frequency with shuffles (spans 16, 8, 4, 2, 1).  On return
+// lane L, register k1 holds X[k1 + R bitrev5(L)].  tw[j] = W_n^j = exp(-2 pi i j/n)
+// for j < n; dir = +1 conjugates every twiddle (unnormalised inverse).
+template <int R>
+__device__ __forceinline__ void warp_fft(float2 (&v)[R], const float2* tw, int dir) {
+  constexpr int n = 32 * R;
+  const int L = threadIdx.x & 31;
+  const float sg = dir > 0 ? -1.f : 1.f;
+  float2 y[R];
+#pragma unroll
+  for (int k1 = 0; k1 < R; ++k1) {
+    float2 acc = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      float2 w = tw[(32 * j * k1) % n];
+      w.y *= sg;
+      acc.x += v[j].x * w.x - v[j].y * w.y;
+      acc.y += v[j].x * w.y + v[j].y * w.x;
+    }
+    y[k1] = acc;
+  }
+#pragma unroll
+  for (int k1 = 1; k1 < R; ++k1) {
+    float2 w = tw[(L * k1) % n];
+    w.y *= sg;
+    y[k1] = cmul(y[k1], w);
+  }
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    float2 w = tw[((L & (s - 1)) * (16 / s)) * R];
+    w.y *= sg;
+    const bool upper = (L & s) != 0;
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+      float2 o;
+      o.x = __shfl_xor_sync(0xffffffffu, y[k1].x, s);
+      o.y = __shfl_xor_sync(0xffffffffu, y[k1].y, s);
+      if (!upper) y[k1] = make_float2(y[k1].x + o.x, y[k1].y + o.y);
+      else y[k1] = cmul(make_float2(o.x - y[k1].x, o.y - y[k1].y), w);
+    }
+  }
+#pragma unroll
+  for (int k1 = 0; k1 < R; ++k1) v[k1] = y[k1];
 }
 
-// Forward transform of one z-slab: x then y, both pruned to I_N.
-// in: real grid [z][y][x];  out: A[z][ky'][kx'] complex, n x N x N.
-__global__ void __launch_bounds__(SLAB_THREADS)
-    k_fft_slab_fwd(const float* __restrict__ g, float2* __restrict__ A, int n, int logn, int N) {
-  extern __shared__ __align__(16) float2 fsh[];
-  float2* tw = fsh;
-  float2* col = fsh + n / 2;            // [n (y, bit-reversed)][N (kx')]
-  float2* rows = col + (size_t)n * N;   // [SLAB_ROWS][n]
-  load_twiddles(tw, n);
-  const int z = blockIdx.x;
-  const float* gz = g + (size_t)z * n * n;
-  for (int r0 = 0; r0 < n; r0 += SLAB_ROWS) {
-    for (int i = threadIdx.x; i < SLAB_ROWS * n; i += blockDim.x) {
-      const int r = i / n, x = i - r * n;
-      rows[r * n + bitrev(x, logn)] = make_float2(gz[(size_t)(r0 + r) * n + x], 0.f);
-    }
-    __syncthreads();
-    fft_smem(rows, SLAB_ROWS, n, 1, tw, n, logn, -1);
-    for (int i = threadIdx.x; i < SLAB_ROWS * N; i += blockDim.x) {
-      const int r = i / N, kp = i - r * N;
-      col[bitrev(r0 + r, logn) * N + kp] = rows[r * n + kept_index(kp, N, n)];
-    }
-    __syncthreads();
-  }
-  fft_smem(col, N, 1, N, tw, n, logn, -1);
-  float2* Az = A + (size_t)z * N * N;
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    const int kyp = i / N, kxp = i - kyp * N;
-    Az[i] = col[kept_index(kyp, N, n) * N + kxp];
-  }
-}
-
-// z lines: forward FFT, keep I_N and multiply by scale_k, inverse FFT.
-// In place on A[z][ky'][kx'] (n x N x N); FFT_LINES adjacent kx' per CTA.
-__global__ void __launch_bounds__(FFT_THREADS)
-    k_fft_zlines(float2* __restrict__ A, int n, int logn, int N, const float* __restrict__ scale) {
-  extern __shared__ __align__(16) float2 fsh[];
-  float2* tw = fsh;
-  float2* a = fsh + n / 2;                // [FFT_LINES][n]
-  float2* b = a + FFT_LINES * n;          // [FFT_LINES][n]
-  load_twiddles(tw, n);
-  const int line0 = blockIdx.x * FFT_LINES;  // line = ky' * N + kx'
-  const size_t zs = (size_t)N * N;
-  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
-    const int z = i / FFT_LINES, l = i - z * FFT_LINES;
-    a[l * n + bitrev(z, logn)] = A[(size_t)z * zs + line0 + l];
-  }
-  __syncthreads();
-  fft_smem(a, FFT_LINES, n, 1, tw, n, logn, -1);
-  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
-    const int l = i / n, e = i - l * n;
-    const int line = line0 + l;
-    const int kyp = line / N, kxp = line - kyp * N;
-    const int kz = e < n / 2 ? e : e - n;
-    float2 v = make_float2(0.f, 0.f);
-    if (kz >= -N / 2 && kz < N / 2) {
-      const float f = scale[kxp] * scale[N + kyp] * scale[2 * N + kz + N / 2];
-      const float2 u = a[l * n + e];
-      v = make_float2(u.x * f, u.y * f);
-    }
-    b[l * n + bitrev(e, logn)] = v;
-  }
-  __syncthreads();
-  fft_smem(b, FFT_LINES, n, 1, tw, n, logn, +1);
-  for (int i = threadIdx.x; i < FFT_LINES * n; i += blockDim.x) {
-    const int z = i / FFT_LINES, l = i - z * FFT_LINES;
-    A[(size_t)z * zs + line0 + l] = b[l * n + z];
+__device__ __forceinline__ void full_twiddles(float2* tw, int n) {
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float sn, cs;
+    sincospif(-2.0f * (float)j / (float)n, &sn, &cs);
+    tw[j] = make_float2(cs, sn);
   }
 }
 
-// Inverse transform of one z-slab: y then x from the I_N^2 coefficients,
-// real part out.  in: A[z][ky'][kx'];  out: real grid [z][y][x].
-__global__ void __launch_bounds__(SLAB_THREADS)
-    k_fft_slab_inv(const float2* __restrict__ A, float* __restrict__ g, int n, int logn, int N) {
-  extern __shared__ __align__(16) float2 fsh[];
-  float2* tw = fsh;
-  float2* col = fsh + n / 2;
-  float2* rows = col + (size_t)n * N;
-  load_twiddles(tw, n);
-  const int z = blockIdx.x;
-  const float2* Az = A + (size_t)z * N * N;
-  for (int i = threadIdx.x; i < n * N; i += blockDim.x) col[i] = make_float2(0.f, 0.f);
+// Position k' in I_N (k' = k + N/2) of FFT index f, or -1 if f is not kept.
+__device__ __forceinline__ int kept_pos(int f, int N, int n) {
+  if (f < N / 2) return f + N / 2;
+  if (f >= n - N / 2) return f - n + N / 2;
+  return -1;
+}
+
+constexpr int WF_WARPS = 8;
+constexpr int WF_LINES = 16;   // adjacent lines per CTA in the strided passes
+constexpr int WF_PITCH = WF_LINES + 1;
+
+// Pass 1: forward x, real grid [z][y][x] -> A1[z][y][kx'] (n x n x N), one row per warp.
+template <int R>
+__global__ void __launch_bounds__(32 * WF_WARPS)
+    k_wfft_x_fwd(const float* __restrict__ g, float2* __restrict__ A1, int N) {
+  constexpr int n = 32 * R;
+  __shared__ float2 tw[n];
+  __shared__ float2 rowbuf[WF_WARPS][n];
+  full_twiddles(tw, n);
   __syncthreads();
-  for (int i = threadIdx.x; i < N * N; i += blockDim.x) {
-    const int kyp = i / N, kxp = i - kyp * N;
-    col[bitrev(kept_index(kyp, N, n), logn) * N + kxp] = Az[i];
+  const int L = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r = (long long)blockIdx.x * WF_WARPS + w;
+  float2 v[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) v[j] = make_float2(g[r * n + 32 * j + L], 0.f);
+  warp_fft<R>(v, tw, -1);
+  const int br = (int)(__brev((unsigned)L) >> 27);
+#pragma unroll
+  for (int k1 = 0; k1 < R; ++k1) {
+    const int kp = kept_pos(k1 + R * br, N, n);
+    if (kp >= 0) rowbuf[w][kp] = v[k1];
+  }
+  __syncwarp();
+  for (int i = L; i < N; i += 32) A1[r * N + i] = rowbuf[w][i];
+}
+
+// Pass 5: inverse x, A4[z][y][kx'] -> real grid [z][y][x], one row per warp.
+template <int R>
+__global__ void __launch_bounds__(32 * WF_WARPS)
+    k_wfft_x_inv(const float2* __restrict__ A4, float* __restrict__ g, int N) {
+  constexpr int n = 32 * R;
+  __shared__ float2 tw[n];
+  __shared__ float rowbuf[WF_WARPS][n];
+  full_twiddles(tw, n);
+  __syncthreads();
+  const int L = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long r = (long long)blockIdx.x * WF_WARPS + w;
+  float2 v[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    const int kp = kept_pos(32 * j + L, N, n);
+    v[j] = kp >= 0 ? A4[r * N + kp] : make_float2(0.f, 0.f);
+  }
+  warp_fft<R>(v, tw, +1);
+  const int br = (int)(__brev((unsigned)L) >> 27);
+#pragma unroll
+  for (int k1 = 0; k1 < R; ++k1) rowbuf[w][k1 + R * br] = v[k1].x;
+  __syncwarp();
+  for (int i = L; i < n; i += 32) g[r * n + i] = rowbuf[w][i];
+}
+
+// Passes 2 and 4 (y) and 3 (z): lines at a stride, WF_LINES adjacent lines per
+// CTA staged through shared memory so global accesses stay coalesced.
+//   mode 0 (y forward):  in A1[z][y][kx']  (n rows)  -> out A2[z][ky'][kx'] (N rows)
+//   mode 1 (y inverse):  in A2[z][ky'][kx'] (N rows) -> out A4[z][y][kx']   (n rows)
+//   mode 2 (z, scaled):  in/out A2 lines along z at fixed (ky', kx')
+// Row e of a line group starts at base + e * rstride; the group's lines are
+// the WF_LINES consecutive complex values there.
+template <int R>
+__global__ void __launch_bounds__(32 * WF_WARPS)
+    k_wfft_lines(const float2* __restrict__ in, float2* __restrict__ out, int N, int mode,
+                 const float* __restrict__ scale) {
+  constexpr int n = 32 * R;
+  extern __shared__ __align__(16) float2 wsh[];
+  float2* tw = wsh;
+  float2* tin = wsh + n;               // [n][WF_PITCH]
+  float2* tout = tin + n * WF_PITCH;   // [n][WF_PITCH]
+  full_twiddles(tw, n);
+  const int groups = N / WF_LINES;
+  const int gi = blockIdx.x % groups;
+  const long long outer = blockIdx.x / groups;   // z (modes 0, 1) or ky' (mode 2)
+  const int kx0 = gi * WF_LINES;
+  const int rows_in = mode == 1 ? N : n, rows_out = mode == 0 ? N : n;
+  long long in_base, in_stride, out_base, out_stride;
+  if (mode == 2) {
+    in_base = out_base = outer * N + kx0;
+    in_stride = out_stride = (long long)N * N;
+  } else {
+    in_base = outer * rows_in * (long long)N + kx0;
+    out_base = outer * rows_out * (long long)N + kx0;
+    in_stride = out_stride = N;
+  }
+  for (int i = threadIdx.x; i < rows_in * WF_LINES; i += blockDim.x) {
+    const int e = i / WF_LINES, l = i - e * WF_LINES;
+    tin[e * WF_PITCH + l] = in[in_base + e * in_stride + l];
   }
   __syncthreads();
-  fft_smem(col, N, 1, N, tw, n, logn, +1);
-  float* gz = g + (size_t)z * n * n;
-  for (int r0 = 0; r0 < n; r0 += SLAB_ROWS) {
-    for (int i = threadIdx.x; i < SLAB_ROWS * n; i += blockDim.x) rows[i] = make_float2(0.f, 0.f);
-    __syncthreads();
-    for (int i = threadIdx.x; i < SLAB_ROWS * N; i += blockDim.x) {
-      const int r = i / N, kp = i - r * N;
-      rows[r * n + bitrev(kept_index(kp, N, n), logn)] = col[(r0 + r) * N + kp];
+  const int L = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int br = (int)(__brev((unsigned)L) >> 27);
+  for (int l = w; l < WF_LINES; l += WF_WARPS) {
+    float2 v[R];
+    if (mode == 1) {
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int kp = kept_pos(32 * j + L, N, n);
+        v[j] = kp >= 0 ? tin[kp * WF_PITCH + l] : make_float2(0.f, 0.f);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[j] = tin[(32 * j + L) * WF_PITCH + l];
     }
-    __syncthreads();
-    fft_smem(rows, SLAB_ROWS, n, 1, tw, n, logn, +1);
-    for (int i = threadIdx.x; i < SLAB_ROWS * n; i += blockDim.x) {
-      const int r = i / n, x = i - r * n;
-      gz[(size_t)(r0 + r) * n + x] = rows[i].x;
+    warp_fft<R>(v, tw, mode == 1 ? +1 : -1);
+    if (mode == 2) {
+      // keep I_N, multiply by scale_k, back to natural frequency order, inverse
+      const int kyp = (int)outer, kxp = kx0 + l;
+      const float fxy = scale[kxp] * scale[N + kyp];
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) {
+        const int f = k1 + R * br;
+        const int kp = kept_pos(f, N, n);
+        const float fz = kp >= 0 ? fxy * scale[2 * N + kp] : 0.f;
+        tout[f * WF_PITCH + l] = make_float2(v[k1].x * fz, v[k1].y * fz);
+      }
+      __syncwarp();
+#pragma unroll
+      for (int j = 0; j < R; ++j) v[j] = tout[(32 * j + L) * WF_PITCH + l];
+      __syncwarp();
+      warp_fft<R>(v, tw, +1);
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) tout[(k1 + R * br) * WF_PITCH + l] = v[k1];
+    } else if (mode == 0) {
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) {
+        const int kp = kept_pos(k1 + R * br, N, n);
+        if (kp >= 0) tout[kp * WF_PITCH + l] = v[k1];
+      }
+    } else {
+#pragma unroll
+      for (int k1 = 0; k1 < R; ++k1) tout[(k1 + R * br) * WF_PITCH + l] = v[k1];
     }
-    __syncthreads();
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < rows_out * WF_LINES; i += blockDim.x) {
+    const int e = i / WF_LINES, l = i - e * WF_LINES;
+    out[out_base + e * out_stride + l] = tout[e * WF_PITCH + l];
+  }
+}
+
+template <int R>
+uotk_status wfft_convolve(uotk_ctx* ctx, cudaStream_t s, int N, const float* scale,
+                          const float* grid_in, float2* A1, float2* A2, float* grid_out) {
+  constexpr int n = 32 * R;
+  const size_t lsmem = sizeof(float2) * (n + 2 * n * WF_PITCH);
+  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_wfft_lines<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)lsmem));
+  k_wfft_x_fwd<R><<<n * n / WF_WARPS, 32 * WF_WARPS, 0, s>>>(grid_in, A1, N);
+  UOTK_LAUNCHED(ctx);
+  k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A1, A2, N, 0, scale);
+  UOTK_LAUNCHED(ctx);
+  k_wfft_lines<R><<<N * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A2, A2, N, 2, scale);
+  UOTK_LAUNCHED(ctx);
+  k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A2, A1, N, 1, scale);
+  UOTK_LAUNCHED(ctx);
+  k_wfft_x_inv<R><<<n * n / WF_WARPS, 32 * WF_WARPS, 0, s>>>(A1, grid_out, N);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
 }
 
 // Unpruned passes for large grids (n > 128): one FFT pass along `axis` on
@@ -597,21 +708,17 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
   int logn = 0;
   while ((1 << logn) < n) ++logn;
   UOTK_PROF(ctx, s, "fft");
-  const size_t slab_smem = sizeof(float2) * (n / 2 + (size_t)n * N + SLAB_ROWS * n);
-  if (n <= 128 && (N * N) % FFT_LINES == 0 && slab_smem <= (size_t)ctx->max_smem_optin) {
-    // pruned: forward x+y per slab, z lines with the scale, inverse y+x per slab
-    UOTK_CUDA(ctx, cudaFuncSetAttribute(k_fft_slab_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)slab_smem));
-    UOTK_CUDA(ctx, cudaFuncSetAttribute(k_fft_slab_inv, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)slab_smem));
-    k_fft_slab_fwd<<<n, SLAB_THREADS, slab_smem, s>>>(grid_in, W.cgrid, n, logn, N);
-    UOTK_LAUNCHED(ctx);
-    const size_t zsmem = sizeof(float2) * (n / 2 + 2 * FFT_LINES * n);
-    k_fft_zlines<<<N * N / FFT_LINES, FFT_THREADS, zsmem, s>>>(W.cgrid, n, logn, N, W.scale);
-    UOTK_LAUNCHED(ctx);
-    k_fft_slab_inv<<<n, SLAB_THREADS, slab_smem, s>>>(W.cgrid, grid_out, n, logn, N);
-    UOTK_LAUNCHED(ctx);
-    return UOTK_OK;
+  if (n >= 32 && N % WF_LINES == 0) {
+    // pruned warp-FFT passes: A1 = n x n x N, A2 = n x N x N complex inside cgrid
+    float2* A1 = W.cgrid;
+    float2* A2 = W.cgrid + (size_t)n * n * N;
+    switch (n) {
+      case 32: return wfft_convolve<1>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
+      case 64: return wfft_convolve<2>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
+      case 128: return wfft_convolve<4>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
+      case 256: return wfft_convolve<8>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
+      default: break;
+    }
   }
   const int blocks = n * n / FFT_LINES;
   const size_t smem = sizeof(float2) * (n / 2 + FFT_LINES * n);
@@ -652,7 +759,10 @@ void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWo
   const size_t n3 = (size_t)P.n * P.n * P.n;
   W.wts = cv.take<float>((size_t)(max_points > 0 ? max_points : 1) + 4);
   W.grid = cv.take<float>(n3);
-  W.cgrid = cv.take<float2>(n3);
+  // complex work grid: n^3 for the unpruned passes, n^2 N + n N^2 for the
+  // pruned ones (A1 and A2)
+  const size_t pr = (size_t)P.n * P.n * P.N + (size_t)P.n * P.N * P.N;
+  W.cgrid = cv.take<float2>(pr > n3 ? pr : n3);
   W.scale = cv.take<float>(3 * P.N);
 }
 
