@@ -116,6 +116,30 @@ uotk_status uotk_kernel_sum(uotk_ctx* ctx, void* stream, int d,
                             const float* tgt, int64_t m, float* out,
                             double eps, const uotk_sum_opts* opts);
 
+/* ---- the direct kernel summation without allocation ------------------------------
+ * The paper has no counterpart to this entry point; it serves callers that may
+ * not allocate device memory while they run: a service that reserves all of its
+ * memory when it starts and treats any later allocation as a fault, or code on a
+ * latency-critical path where cudaMalloc would synchronise the device or could
+ * fail under memory pressure.  It computes what uotk_kernel_sum computes with
+ * the direct form, out[j] = sum_i w[i] * exp(-||src_i - tgt_j||^2 / eps),
+ * needs no context, and allocates nothing: its scratch is one fixed device
+ * array of 4 MiB + 4 KiB inside the library, present on every GPU that loads
+ * the library until the process exits.
+ *   Limits: 1 <= d <= 3, n <= 65536 sources, m <= 65536 targets; larger
+ *   problems return UOTK_ERR_UNSUPPORTED (use uotk_kernel_sum).
+ *   src, w, tgt, out: device arrays as for uotk_kernel_sum, owned by the caller.
+ *   Uses the current CUDA device.  The first call on a device looks up the
+ *   scratch's device address (a one-time set-up); make that first call before
+ *   any stream capture.  Every call on a device shares the scratch, so calls
+ *   whose work overlaps on the GPU (different streams, or different host
+ *   threads) race; serialise them.  Synchronises `stream` to report data
+ *   errors: negative weights -> UOTK_ERR_INVALID, non-finite values ->
+ *   UOTK_ERR_NONFINITE. */
+uotk_status uotk_kernel_sum_noalloc(void* stream, int d, const float* src, int64_t n,
+                                    const float* w, const float* tgt, int64_t m, float* out,
+                                    double eps);
+
 /* ---- entropic UOT by Sinkhorn's algorithm (Alg. 1 direct, Alg. 2 NFFT) -------------
  * Solves Eq. (W4) (r = 2, lambda = 1/eps, eta1 = rho1, eta2 = rho2) through
  * its dual, Eq. (dual_euot), by the alternating updates of

@@ -14,6 +14,10 @@
 // (hi, lo) pair.  Sources are split across blockIdx.y when there are too few
 // target blocks to fill the GPU; split partials are added in FP64 in a fixed
 // order, so the result is deterministic.
+#include <math.h>
+
+#include <mutex>
+
 #include "uotk_internal.cuh"
 
 namespace uotk {
@@ -350,3 +354,126 @@ uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, con
 }
 
 }  // namespace uotk
+
+// ---------------------------------------------------------------------------
+// Direct kernel summation without any allocation (uotk_kernel_sum_noalloc).
+//
+// For callers that must not allocate device memory at call time.  Examples
+// are a service that reserves all of its memory when it starts and treats
+// any later cudaMalloc as an error, or code that runs where an allocation
+// would synchronise the device or could fail under memory pressure.  The
+// scratch these calls need (packed points, split partial sums, validation
+// counters) lives in one file-scope device array, reserved when the library
+// is loaded on a device and kept until the process exits.
+// ---------------------------------------------------------------------------
+namespace uotk {
+namespace {
+
+constexpr long long NOALLOC_MAX_POINTS = 65536;  // per cloud (sources, targets)
+constexpr int NOALLOC_MAX_SPLITS = 8;
+constexpr size_t NOALLOC_SRC_BYTES =
+    (size_t)(NOALLOC_MAX_POINTS + DIRECT_TILE) * sizeof(float4);            // 1 MiB + 4 KiB
+constexpr size_t NOALLOC_TGT_BYTES = (size_t)NOALLOC_MAX_POINTS * sizeof(float4);  // 1 MiB
+constexpr size_t NOALLOC_PART_BYTES =
+    (size_t)NOALLOC_MAX_SPLITS * NOALLOC_MAX_POINTS * sizeof(float);        // 2 MiB
+constexpr size_t NOALLOC_FLAG_BYTES = 256;
+constexpr size_t NOALLOC_BYTES =
+    NOALLOC_SRC_BYTES + NOALLOC_TGT_BYTES + NOALLOC_PART_BYTES + NOALLOC_FLAG_BYTES;
+
+// The scratch itself.  In host code `noalloc_scratch` names a host-side
+// stand-in, not the device memory: its device address is looked up once per
+// device with cudaGetSymbolAddress and passed to the kernels.
+static __device__ __align__(256) unsigned char noalloc_scratch[NOALLOC_BYTES];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex noalloc_mutex;
+unsigned char* noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch on the current device (set-up on first use).
+uotk_status noalloc_scratch_on(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return UOTK_ERR_UNSUPPORTED;
+  std::lock_guard<std::mutex> lock(noalloc_mutex);
+  if (!noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, noalloc_scratch) != cudaSuccess || !p) {
+      cudaGetLastError();
+      return UOTK_ERR_CUDA;
+    }
+    noalloc_ptr[dev] = static_cast<unsigned char*>(p);
+  }
+  *out = noalloc_ptr[dev];
+  return UOTK_OK;
+}
+
+}  // namespace
+
+}  // namespace uotk
+
+extern "C" uotk_status uotk_kernel_sum_noalloc(void* stream, int d, const float* src, int64_t n,
+                                               const float* w, const float* tgt, int64_t m,
+                                               float* out, double eps) {
+  using namespace uotk;
+  if (d < 1 || d > 3) return UOTK_ERR_UNSUPPORTED;
+  if (n < 0 || m < 0 || !(eps > 0.0) || !isfinite(eps)) return UOTK_ERR_INVALID;
+  if (n > NOALLOC_MAX_POINTS || m > NOALLOC_MAX_POINTS) return UOTK_ERR_UNSUPPORTED;
+  if ((n > 0 && (!src || !w)) || (m > 0 && (!tgt || !out))) return UOTK_ERR_INVALID;
+  if (m == 0) return UOTK_OK;
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return UOTK_ERR_CUDA;
+  }
+  if (n == 0) {
+    if (cudaMemsetAsync(out, 0, sizeof(float) * m, s) != cudaSuccess) return UOTK_ERR_CUDA;
+    return UOTK_OK;
+  }
+  unsigned char* base = nullptr;
+  const uotk_status st0 = noalloc_scratch_on(dev, &base);
+  if (st0 != UOTK_OK) return st0;
+  float4* psrc = reinterpret_cast<float4*>(base);
+  float4* ptgt = reinterpret_cast<float4*>(base + NOALLOC_SRC_BYTES);
+  float* part = reinterpret_cast<float*>(base + NOALLOC_SRC_BYTES + NOALLOC_TGT_BYTES);
+  long long* flags =
+      reinterpret_cast<long long*>(base + NOALLOC_SRC_BYTES + NOALLOC_TGT_BYTES + NOALLOC_PART_BYTES);
+  // the same launch shape as the context path, with at most NOALLOC_MAX_SPLITS splits
+  const int R = 1;
+  const int blocks_x = (int)((m + DIRECT_THREADS - 1) / DIRECT_THREADS);
+  const long long tiles = (n + DIRECT_TILE - 1) / DIRECT_TILE;
+  long long splits = (32LL * sms + blocks_x - 1) / blocks_x;
+  const long long max_splits = tiles / 2 > 0 ? tiles / 2 : 1;
+  if (splits > max_splits) splits = max_splits;
+  if (splits > NOALLOC_MAX_SPLITS) splits = NOALLOC_MAX_SPLITS;
+  if (splits < 1) splits = 1;
+  const int tps = (int)((tiles + splits - 1) / splits);
+  splits = (tiles + tps - 1) / tps;
+  // the validation counters start at zero on every call
+  if (cudaMemsetAsync(flags, 0, NOALLOC_FLAG_BYTES, s) != cudaSuccess) return UOTK_ERR_CUDA;
+  const long long n_pad = tiles * DIRECT_TILE;
+  const int gp = (int)((n_pad + 255) / 256 < 8LL * sms ? (n_pad + 255) / 256 : 8LL * sms);
+  k_pack<<<gp, 256, 0, s>>>(src, w, n, n_pad, d, 4, 1, psrc, flags);
+  const int gt = (int)((m + 255) / 256 < 8LL * sms ? (m + 255) / 256 : 8LL * sms);
+  k_pack<<<gt, 256, 0, s>>>(tgt, nullptr, m, m, d, 4, 1, ptgt, flags);
+  const float neg_c = (float)(-1.4426950408889634 / eps);
+  float* dst = splits > 1 ? part : out;
+  const dim3 grid(blocks_x, (unsigned)splits);
+  if (d == 1)
+    k_direct_small<1, R><<<grid, DIRECT_THREADS, 0, s>>>(psrc, tiles, tps, ptgt, m, neg_c, dst, flags);
+  else if (d == 2)
+    k_direct_small<2, R><<<grid, DIRECT_THREADS, 0, s>>>(psrc, tiles, tps, ptgt, m, neg_c, dst, flags);
+  else
+    k_direct_small<3, R><<<grid, DIRECT_THREADS, 0, s>>>(psrc, tiles, tps, ptgt, m, neg_c, dst, flags);
+  if (splits > 1) k_reduce_splits<<<gt, 256, 0, s>>>(part, (int)splits, m, out);
+  if (cudaGetLastError() != cudaSuccess) return UOTK_ERR_CUDA;
+  long long h[4] = {0, 0, 0, 0};
+  if (cudaMemcpyAsync(h, flags, sizeof(h), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess) {
+    cudaGetLastError();
+    return UOTK_ERR_CUDA;
+  }
+  if (h[FLAG_NONFINITE]) return UOTK_ERR_NONFINITE;
+  if (h[FLAG_NEG_WEIGHT]) return UOTK_ERR_INVALID;
+  if (h[FLAG_TIMEOUT]) return UOTK_ERR_TIMEOUT;
+  return UOTK_OK;
+}

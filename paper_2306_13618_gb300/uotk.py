@@ -81,6 +81,8 @@ def lib():
         opts = ctypes.POINTER(SumOpts)
         plan = ctypes.POINTER(NfftPlan)
         L.uotk_kernel_sum.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, opts]
+        L.uotk_kernel_sum_noalloc.argtypes = [_P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D]
+        L.uotk_kernel_sum_noalloc.restype = ctypes.c_int
         L.uotk_uot_sinkhorn.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, _D,
                                         _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_uint, _P, _P,
                                         ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D), opts]
@@ -203,6 +205,16 @@ def kernel_sum(src, w, tgt, eps, method="direct", out=None, ctx=None, **nfft):
     return out
 
 
+def kernel_sum_noalloc(src, w, tgt, eps, out):
+    """Direct kernel sum through uotk_kernel_sum_noalloc: no context, no
+    allocation inside the library; `out` must be provided by the caller.
+    Returns the status code (0 on success)."""
+    src, tgt, w = _pts(src, "src"), _pts(tgt, "tgt"), _f32(w, "w").reshape(-1)
+    return int(lib().uotk_kernel_sum_noalloc(_stream(), src.shape[1], _ptr(src), src.shape[0],
+                                             _ptr(w), _ptr(tgt), tgt.shape[0], _ptr(out),
+                                             float(eps)))
+
+
 def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref="product",
                  gamma0=None, method="direct", ctx=None, beta=None, gamma=None, **nfft):
     """KL-penalised entropic UOT by Sinkhorn (uotk_uot_sinkhorn).
@@ -312,6 +324,6 @@ def nfft_gather(plan, grid, pts, ctx=None):
 
 EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_string",
             "uotk_launch_count", "uotk_set_profiling", "uotk_profile_read", "uotk_profile_reset",
-            "uotk_kernel_sum", "uotk_uot_sinkhorn",
+            "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_nfft_plan", "uotk_nfft_cells",
             "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]
