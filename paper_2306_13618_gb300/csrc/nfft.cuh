@@ -17,9 +17,22 @@ constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit gr
 constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
 constexpr int NFFT_MAX_M = 8;
 constexpr int NFFT_CHUNK = 64;          // points per bulk-copied staging chunk
-// Floats per point of the window table: 3 x 2m weights, padded to 16 bytes
-// so that every chunk of the table is a legal bulk-copy source.
-__host__ __device__ constexpr int nfft_win_stride(int m) { return (6 * m + 3) & ~3; }
+// Window table row of one point (floats): phi_x split in two halves of m
+// values, then phi_y (2m), then phi_z (2m); every block padded to a 16-byte
+// multiple, so that every chunk of the table is a legal bulk-copy source and
+// each half of phi_x and all of phi_z are 16-byte vector loads.
+__host__ __device__ constexpr int nfft_win_half(int m) { return (m + 3) & ~3; }
+__host__ __device__ constexpr int nfft_win_yoff(int m) { return 2 * nfft_win_half(m); }
+__host__ __device__ constexpr int nfft_win_zoff(int m) {
+  return 2 * nfft_win_half(m) + ((2 * m + 3) & ~3);
+}
+__host__ __device__ constexpr int nfft_win_stride(int m) {
+  return nfft_win_zoff(m) + ((2 * m + 3) & ~3);
+}
+// Offset in the row of phi_x[kx], kx in [0, 2m).
+__host__ __device__ constexpr int nfft_win_xoff(int m, int kx) {
+  return kx < m ? kx : nfft_win_half(m) + kx - m;
+}
 
 struct NfftParams {
   int d = 3;
@@ -47,7 +60,7 @@ void nfft_scale_table(const NfftParams& P, float* host_table /* 3*N */);
 struct NfftPoints {
   int64_t n = 0;
   int4* cell = nullptr;      // sorted: (cx | cy<<10 | cz<<20, frac x, y, z as float bits)
-  float* win = nullptr;      // sorted: [n][nfft_win_stride(m)] window weights (x, y, z rows)
+  float* win = nullptr;      // sorted: [n][nfft_win_stride(m)] window rows (layout above)
   int* ckey = nullptr;       // sorted: packed cell (cx | cy<<10 | cz<<20), n + 4 entries
   int* perm = nullptr;       // sorted position -> caller index
   int* tile_start = nullptr; // [tiles+1] start of each tile in sorted order

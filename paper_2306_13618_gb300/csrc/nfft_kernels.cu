@@ -79,20 +79,22 @@ __device__ __forceinline__ void tile_origin(int tile, int tiles1, int& x, int& y
   z = (tile / (tiles1 * tiles1)) * NFFT_TILE;
 }
 
-// M floats of a window row from shared memory (8-byte loads when M is even).
-template <int M>
-__device__ __forceinline__ void load_row(const float* p, float* r) {
-  if (M % 2 == 0) {
+// K consecutive floats from 16-byte-aligned shared memory: 16-byte loads, then
+// an 8-byte and a 4-byte load for the remainder.
+template <int K>
+__device__ __forceinline__ void load_vec(const float* p, float* r) {
+  int j = 0;
 #pragma unroll
-    for (int j = 0; j < M; j += 2) {
-      const float2 v = *reinterpret_cast<const float2*>(p + j);
-      r[j] = v.x;
-      r[j + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < M; ++j) r[j] = p[j];
+  for (; j + 4 <= K; j += 4) {
+    const float4 v = *reinterpret_cast<const float4*>(p + j);
+    r[j] = v.x; r[j + 1] = v.y; r[j + 2] = v.z; r[j + 3] = v.w;
   }
+  if (K - j >= 2) {
+    const float2 v = *reinterpret_cast<const float2*>(p + j);
+    r[j] = v.x; r[j + 1] = v.y;
+    j += 2;
+  }
+  if (K - j == 1) r[j] = p[j];
 }
 
 // ---------------------------------------------------------------- spread ----
@@ -105,8 +107,11 @@ __global__ void __launch_bounds__(8 * M * M)
              long long* __restrict__ flags) {
   using G = Geo<M>;
   constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M;
+  constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
+  __shared__ int gstart[CH + 1];
+  __shared__ int ngroups;
   float* blk = smem;
   float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
@@ -125,34 +130,64 @@ __global__ void __launch_bounds__(8 * M * M)
   int tx0, ty0, tz0;
   tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
-  const int kz = r / W2, ky = r - kz * W2, kx0 = half * M;
+  const int kz = r / W2, ky = r - kz * W2;
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
     const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), off = q0 & 3;
-    const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
+    float* sw = stage0 + (k % STAGES) * G::STAGE_F;
     const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + off;
     const float* swt = sw + CH * WS + CH + 4 + off;
-    int p = 0;
-    while (p < cn) {
-      const int key = skey[p];
+    // Fold each point's weight into its phi_z row, and list where each cell's
+    // run of points starts (points are sorted by cell).
+    for (int i = threadIdx.x; i < cn * W2; i += NT) {
+      const int q = i / W2;
+      sw[q * WS + ZO + (i - q * W2)] *= swt[q];
+    }
+    if (threadIdx.x < 32) {
+      int base = 0;
+      for (int h = 0; h < CH; h += 32) {
+        const int q = h + lane;
+        const bool f = q < cn && (q == 0 || skey[q] != skey[q - 1]);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (f) gstart[base + __popc(bal & ((1u << lane) - 1u))] = q;
+        base += __popc(bal);
+      }
+      if (lane == 0) { ngroups = base; gstart[base] = cn; }
+    }
+    __syncthreads();
+    const int ng = ngroups;
+    for (int g = 0; g < ng; ++g) {
+      const int p0 = gstart[g], p1 = gstart[g + 1];
+      const int key = skey[p0];
       float acc[M];
 #pragma unroll
       for (int j = 0; j < M; ++j) acc[j] = 0.f;
-      int q = p;
-      for (; q < cn && skey[q] == key; ++q) {
-        const float* wq = sw + q * WS;
-        const float a = swt[q] * wq[2 * W2 + kz] * wq[W2 + ky];
-        float fx[M];
-        load_row<M>(wq + kx0, fx);
+      int q = p0;
+      for (; q + 1 < p1; q += 2) {
+        const float* w0 = sw + q * WS;
+        const float* w1 = w0 + WS;
+        const float a0 = w0[ZO + kz] * w0[YO + ky];
+        const float a1 = w1[ZO + kz] * w1[YO + ky];
+        float f0[M], f1[M];
+        load_vec<M>(w0 + half * HP, f0);
+        load_vec<M>(w1 + half * HP, f1);
 #pragma unroll
-        for (int j = 0; j < M; ++j) acc[j] = fmaf(a, fx[j], acc[j]);
+        for (int j = 0; j < M; ++j) acc[j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[j]));
+      }
+      if (q < p1) {
+        const float* w0 = sw + q * WS;
+        const float a0 = w0[ZO + kz] * w0[YO + ky];
+        float f0[M];
+        load_vec<M>(w0 + half * HP, f0);
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[j] = fmaf(a0, f0[j], acc[j]);
       }
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-      float* dst = blk + ((bz + kz) * E + by + ky) * E + bx + kx0;
+      float* dst = blk + ((bz + kz) * E + by + ky) * E + bx + half * M;
 #pragma unroll
       for (int j = 0; j < M; ++j) dst[j] += acc[j];
       __syncthreads();
-      p = q;
     }
     if (threadIdx.x == 0 && k + STAGES < nchunks)
       stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, wts,
@@ -530,6 +565,7 @@ __global__ void __launch_bounds__(256)
              long long* __restrict__ flags) {
   using G = Geo<M>;
   constexpr int W2 = G::W2, E = G::E, E2 = G::E2, E3 = G::E3, WS = G::WS;
+  constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   constexpr int NIT = (W2 * W2 + 31) / 32;
   // Footprint of the current cell kept in registers while a warp's consecutive
   // targets share that cell.
@@ -565,9 +601,10 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
   for (int it = 0; it < NIT; ++it) {
     const int c = lane + 32 * it;
-    kxs[it] = c % W2;
-    kys[it] = c / W2;
-    off[it] = c < W2 * W2 ? kys[it] * E + kxs[it] : -1;
+    const int kx = c % W2, ky = c / W2;
+    kxs[it] = nfft_win_xoff(M, kx);  // offset of phi_x[kx] in the window row
+    kys[it] = YO + ky;               // offset of phi_y[ky]
+    off[it] = c < W2 * W2 ? ky * E + kx : -1;
   }
   float hc[CACHE ? NIT * W2 : 1];
   int cached = -1;
@@ -582,8 +619,7 @@ __global__ void __launch_bounds__(256)
       const float* wq = sw + p * WS;
       const float* src = blk + (bz * E + by) * E + bx;
       float fz[W2];
-#pragma unroll
-      for (int kk = 0; kk < W2; ++kk) fz[kk] = wq[2 * W2 + kk];
+      load_vec<W2>(wq + ZO, fz);
       float acc = 0.f;
       if (CACHE) {
         if (key != cached) {
@@ -599,14 +635,14 @@ __global__ void __launch_bounds__(256)
           float s = 0.f;
 #pragma unroll
           for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], hc[CACHE ? it * W2 + kk : 0], s);
-          const float pxy = off[it] >= 0 ? wq[kxs[it]] * wq[W2 + kys[it]] : 0.f;
+          const float pxy = off[it] >= 0 ? wq[kxs[it]] * wq[kys[it]] : 0.f;
           acc = fmaf(pxy, s, acc);
         }
       } else {
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
           if (off[it] >= 0) {
-            const float pxy = wq[kxs[it]] * wq[W2 + kys[it]];
+            const float pxy = wq[kxs[it]] * wq[kys[it]];
             const float* col = src + off[it];
             float s = 0.f;
 #pragma unroll
