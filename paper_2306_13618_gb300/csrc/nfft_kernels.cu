@@ -97,6 +97,23 @@ __device__ __forceinline__ void load_vec(const float* p, float* r) {
   if (K - j == 1) r[j] = p[j];
 }
 
+// M floats starting at an 8-byte boundary when M is even (a half row of
+// phi_x: offset half*M), else 4-byte.
+template <int M>
+__device__ __forceinline__ void load_row(const float* p, float* r) {
+  if (M % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < M; j += 2) {
+      const float2 v = *reinterpret_cast<const float2*>(p + j);
+      r[j] = v.x;
+      r[j + 1] = v.y;
+    }
+  } else {
+#pragma unroll
+    for (int j = 0; j < M; ++j) r[j] = p[j];
+  }
+}
+
 // ---------------------------------------------------------------- spread ----
 template <int M>
 __global__ void __launch_bounds__(8 * M * M)
@@ -107,7 +124,7 @@ __global__ void __launch_bounds__(8 * M * M)
              long long* __restrict__ flags) {
   using G = Geo<M>;
   constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M;
-  constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
+  constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
   __shared__ int gstart[CH + 1];
@@ -170,8 +187,8 @@ __global__ void __launch_bounds__(8 * M * M)
         const float a0 = w0[ZO + kz] * w0[YO + ky];
         const float a1 = w1[ZO + kz] * w1[YO + ky];
         float f0[M], f1[M];
-        load_vec<M>(w0 + half * HP, f0);
-        load_vec<M>(w1 + half * HP, f1);
+        load_row<M>(w0 + half * M, f0);
+        load_row<M>(w1 + half * M, f1);
 #pragma unroll
         for (int j = 0; j < M; ++j) acc[j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[j]));
       }
@@ -179,7 +196,7 @@ __global__ void __launch_bounds__(8 * M * M)
         const float* w0 = sw + q * WS;
         const float a0 = w0[ZO + kz] * w0[YO + ky];
         float f0[M];
-        load_vec<M>(w0 + half * HP, f0);
+        load_row<M>(w0 + half * M, f0);
 #pragma unroll
         for (int j = 0; j < M; ++j) acc[j] = fmaf(a0, f0[j], acc[j]);
       }
@@ -474,8 +491,7 @@ uotk_status wfft_convolve(uotk_ctx* ctx, cudaStream_t s, int N, const float* sca
                           const float* grid_in, float2* A1, float2* A2, float* grid_out) {
   constexpr int n = 32 * R;
   const size_t lsmem = sizeof(float2) * (n + 2 * n * WF_PITCH);
-  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_wfft_lines<R>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)lsmem));
+  UOTK_CUDA(ctx, smem_attr(s, k_wfft_lines<R>, lsmem));
   k_wfft_x_fwd<R><<<n * n / WF_WARPS, 32 * WF_WARPS, 0, s>>>(grid_in, A1, N);
   UOTK_LAUNCHED(ctx);
   k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A1, A2, N, 0, scale);
@@ -556,8 +572,99 @@ __global__ void __launch_bounds__(FFT_THREADS)
 }
 
 // ---------------------------------------------------------------- gather ----
+// Tensor-core path for a run of targets in one cell.  With H the footprint of
+// the cell (H[kz][ky][kx], (2m)^3 grid values), the gather of target p is
+//   s_p = sum_{kz,ky} phi_z,p[kz] phi_y,p[ky] T[p][(kz,ky)],
+//   T[p][(kz,ky)] = sum_kx phi_x,p[kx] H[kz][ky][kx],
+// and T = Phi_x H^T is a dense product: m16n8k8 TF32 MMAs with FP32
+// accumulation, each operand split into a TF32 head and tail and the three
+// significant products added (FP32-level accuracy).  Rows of the 16-row tile are
+// targets, the K index is kx, columns are (kz, ky) pairs; the epilogue weighs
+// each column with phi_z phi_y of its row's target and sums.
+__device__ __forceinline__ unsigned to_tf32(float x) {
+  unsigned r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
+  hi = to_tf32(x);
+  lo = to_tf32(x - __uint_as_float(hi));
+}
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0,
+                                         unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};"
+      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One warp: targets s0 .. s0+cnt-1 (cnt <= 16) of the staged chunk, all in the
+// cell whose footprint starts at `src` in the shared block.
 template <int M>
-__global__ void __launch_bounds__(256)
+__device__ __forceinline__ void gather_run_mma(const float* sw, int s0, int cnt, const float* src,
+                                               float* out) {
+  using G = Geo<M>;
+  constexpr int W2 = G::W2, E = G::E, E2 = G::E2, WS = G::WS;
+  constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
+  constexpr int NT = (W2 * W2 + 7) / 8, KS = (W2 + 7) / 8;
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const bool v0 = g < cnt, v1 = g + 8 < cnt;
+  const float* w0 = sw + (s0 + (v0 ? g : 0)) * WS;
+  const float* w1 = sw + (s0 + (v1 ? g + 8 : 0)) * WS;
+  unsigned ahi[KS][4], alo[KS][4];
+#pragma unroll
+  for (int ks = 0; ks < KS; ++ks) {
+    const int ka = ks * 8 + t, kb = ka + 4;
+    const float x0 = (v0 && ka < W2) ? w0[ka] : 0.f;
+    const float x1 = (v1 && ka < W2) ? w1[ka] : 0.f;
+    const float x2 = (v0 && kb < W2) ? w0[kb] : 0.f;
+    const float x3 = (v1 && kb < W2) ? w1[kb] : 0.f;
+    split_tf32(x0, ahi[ks][0], alo[ks][0]);
+    split_tf32(x1, ahi[ks][1], alo[ks][1]);
+    split_tf32(x2, ahi[ks][2], alo[ks][2]);
+    split_tf32(x3, ahi[ks][3], alo[ks][3]);
+  }
+  float rs0 = 0.f, rs1 = 0.f;
+#pragma unroll 2
+  for (int nt = 0; nt < NT; ++nt) {
+    float c[4] = {0.f, 0.f, 0.f, 0.f};
+    const int n = nt * 8 + g;                       // this lane's B column
+    const bool vn = n < W2 * W2;
+    const int kzb = vn ? n / W2 : 0, kyb = vn ? n - kzb * W2 : 0;
+    const float* hrow = src + kzb * E2 + kyb * E;
+#pragma unroll
+    for (int ks = 0; ks < KS; ++ks) {
+      const int ka = ks * 8 + t, kb = ka + 4;
+      unsigned bh0, bl0, bh1, bl1;
+      split_tf32((vn && ka < W2) ? hrow[ka] : 0.f, bh0, bl0);
+      split_tf32((vn && kb < W2) ? hrow[kb] : 0.f, bh1, bl1);
+      mma_tf32(c, alo[ks], bh0, bh1);
+      mma_tf32(c, ahi[ks], bl0, bl1);
+      mma_tf32(c, ahi[ks], bh0, bh1);
+    }
+    const int n0 = nt * 8 + 2 * t;                  // this lane's C columns n0, n0 + 1
+    if (n0 < W2 * W2) {
+      const int kz = n0 / W2, ky = n0 - kz * W2;   // n0 even, W2 even: same kz for n0 + 1
+      rs0 = fmaf(w0[ZO + kz], fmaf(c[1], w0[YO + ky + 1], c[0] * w0[YO + ky]), rs0);
+      rs1 = fmaf(w1[ZO + kz], fmaf(c[3], w1[YO + ky + 1], c[2] * w1[YO + ky]), rs1);
+    }
+  }
+  rs0 += __shfl_xor_sync(0xffffffffu, rs0, 1);
+  rs0 += __shfl_xor_sync(0xffffffffu, rs0, 2);
+  rs1 += __shfl_xor_sync(0xffffffffu, rs1, 1);
+  rs1 += __shfl_xor_sync(0xffffffffu, rs1, 2);
+  if (t == 0) {
+    if (v0) out[s0 + g] = rs0;
+    if (v1) out[s0 + g + 8] = rs1;
+  }
+}
+
+// Runs of at least this many targets of one cell take the tensor-core path.
+constexpr int GATHER_MMA_MIN = 4;
+
+template <int M>
+__global__ void __launch_bounds__(256, 2)
     k_gather(const float* __restrict__ win, const int* __restrict__ ckey,
              const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
              const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
@@ -567,11 +674,10 @@ __global__ void __launch_bounds__(256)
   constexpr int W2 = G::W2, E = G::E, E2 = G::E2, E3 = G::E3, WS = G::WS;
   constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   constexpr int NIT = (W2 * W2 + 31) / 32;
-  // Footprint of the current cell kept in registers while a warp's consecutive
-  // targets share that cell.
-  constexpr bool CACHE = NIT * W2 <= 64;
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
+  __shared__ int gstart[CH + 1];
+  __shared__ int ngroups;
   float* blk = smem;
   float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
@@ -602,57 +708,60 @@ __global__ void __launch_bounds__(256)
   for (int it = 0; it < NIT; ++it) {
     const int c = lane + 32 * it;
     const int kx = c % W2, ky = c / W2;
-    kxs[it] = nfft_win_xoff(M, kx);  // offset of phi_x[kx] in the window row
-    kys[it] = YO + ky;               // offset of phi_y[ky]
+    kxs[it] = kx;       // offset of phi_x[kx] in the window row
+    kys[it] = YO + ky;  // offset of phi_y[ky]
     off[it] = c < W2 * W2 ? ky * E + kx : -1;
   }
-  float hc[CACHE ? NIT * W2 : 1];
-  int cached = -1;
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
     const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), koff = q0 & 3;
     const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
     const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + koff;
-    for (int p = warp; p < cn; p += nwarps) {
-      const int key = skey[p];
+    if (threadIdx.x < 32) {
+      int base = 0;
+      for (int h = 0; h < CH; h += 32) {
+        const int q = h + lane;
+        const bool f = q < cn && (q == 0 || skey[q] != skey[q - 1]);
+        const unsigned bal = __ballot_sync(0xffffffffu, f);
+        if (f) gstart[base + __popc(bal & ((1u << lane) - 1u))] = q;
+        base += __popc(bal);
+      }
+      if (lane == 0) { ngroups = base; gstart[base] = cn; }
+    }
+    __syncthreads();
+    const int ng = ngroups;
+    float* outc = out + q0;
+    int item = 0;  // work items (runs of up to 16 targets, or single targets) dealt to warps in turn
+    for (int gi = 0; gi < ng; ++gi) {
+      const int p0 = gstart[gi], p1 = gstart[gi + 1];
+      const int key = skey[p0];
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-      const float* wq = sw + p * WS;
       const float* src = blk + (bz * E + by) * E + bx;
-      float fz[W2];
-      load_vec<W2>(wq + ZO, fz);
-      float acc = 0.f;
-      if (CACHE) {
-        if (key != cached) {
-#pragma unroll
-          for (int it = 0; it < NIT; ++it)
-#pragma unroll
-            for (int kk = 0; kk < W2; ++kk)
-              hc[CACHE ? it * W2 + kk : 0] = off[it] >= 0 ? src[kk * E2 + off[it]] : 0.f;
-          cached = key;
-        }
-#pragma unroll
-        for (int it = 0; it < NIT; ++it) {
-          float s = 0.f;
-#pragma unroll
-          for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], hc[CACHE ? it * W2 + kk : 0], s);
-          const float pxy = off[it] >= 0 ? wq[kxs[it]] * wq[kys[it]] : 0.f;
-          acc = fmaf(pxy, s, acc);
-        }
-      } else {
+      if (p1 - p0 >= GATHER_MMA_MIN) {
+        for (int s0 = p0; s0 < p1; s0 += 16, ++item)
+          if (item % nwarps == warp) gather_run_mma<M>(sw, s0, min(16, p1 - s0), src, outc);
+        continue;
+      }
+      for (int p = p0; p < p1; ++p, ++item) {
+        if (item % nwarps != warp) continue;
+        const float* wq = sw + p * WS;
+        float fz[W2];
+        load_vec<W2>(wq + ZO, fz);
+        float acc = 0.f;
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
           if (off[it] >= 0) {
             const float pxy = wq[kxs[it]] * wq[kys[it]];
             const float* col = src + off[it];
-            float s = 0.f;
+            float sacc = 0.f;
 #pragma unroll
-            for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], col[kk * E2], s);
-            acc = fmaf(pxy, s, acc);
+            for (int kk = 0; kk < W2; ++kk) sacc = fmaf(fz[kk], col[kk * E2], sacc);
+            acc = fmaf(pxy, sacc, acc);
           }
         }
+        acc = warp_sum(acc);
+        if (lane == 0) outc[p] = acc;
       }
-      acc = warp_sum(acc);
-      if (lane == 0) out[q0 + p] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0 && k + STAGES < nchunks)
@@ -671,8 +780,7 @@ template <int M>
 uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* wts, float* grid) {
   const size_t smem = unit_smem<M>();
-  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_spread<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+  UOTK_CUDA(ctx, smem_attr(s, k_spread<M>, smem));
   k_spread<M><<<S.max_units, 8 * M * M, smem, s>>>(S.win, S.ckey, wts, S.unit_tile, S.unit_begin,
                                                    S.unit_count, S.num_units, P.n, P.tiles1, grid,
                                                    ctx->dflags);
@@ -684,8 +792,7 @@ template <int M>
 uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* grid, float* out) {
   const size_t smem = unit_smem<M>();
-  UOTK_CUDA(ctx, cudaFuncSetAttribute(k_gather<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                      (int)smem));
+  UOTK_CUDA(ctx, smem_attr(s, k_gather<M>, smem));
   k_gather<M><<<S.max_units, 256, smem, s>>>(S.win, S.ckey, S.unit_tile, S.unit_begin,
                                              S.unit_count, S.num_units, P.n, P.tiles1, grid, out,
                                              ctx->dflags);

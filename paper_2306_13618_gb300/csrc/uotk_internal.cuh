@@ -112,6 +112,17 @@ struct ProfScope {
 };
 #define UOTK_PROF(ctx, s, name) uotk::ProfScope uotk_prof_scope_((ctx), (s), (name))
 
+// Opt a kernel in to `bytes` of dynamic shared memory.  Skipped while the
+// stream is being captured into a graph: the attribute was set by the eager
+// launch that precedes every capture.
+template <class K>
+inline cudaError_t smem_attr(cudaStream_t s, K kernel, size_t bytes) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) == cudaSuccess && cs != cudaStreamCaptureStatusNone)
+    return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
 #define UOTK_TRY(expr)                 \
   do {                                 \
     uotk_status s_ = (expr);           \

@@ -188,3 +188,18 @@ def test_sinkhorn_divergence_uniform_box(uotk):
     assert np.allclose(parts, rparts, rtol=1e-6, atol=0)
     kappa = sum(abs(p) for p in rparts) / abs(rsd)
     assert abs(sd - rsd) <= 1e-6 * kappa * abs(rsd), (sd, rsd, kappa)
+
+
+def test_graph_replay_matches_eager(uotk):
+    """Sweeps replayed from the captured CUDA graph equal eager launches bit for
+    bit (the direct form is deterministic); profiling forces eager launches."""
+    W = inputs.uniform_box(n=1000, m=900)
+    ctx = uotk.default_context()
+    args = (dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho)
+    ctx.set_profiling(True)
+    b1, g1, s1, v1, _ = uotk.uot_sinkhorn(*args, max_sweeps=37)
+    ctx.set_profiling(False)
+    ctx.profile_reset()
+    b2, g2, s2, v2, _ = uotk.uot_sinkhorn(*args, max_sweeps=37)
+    assert s1 == s2 == 37 and v1 == v2
+    assert torch.equal(b1, b2) and torch.equal(g1, g2)
