@@ -16,7 +16,7 @@ namespace uotk {
 constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit granularity)
 constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
 constexpr int NFFT_MAX_M = 8;
-constexpr int NFFT_CHUNK = 64;          // points per bulk-copied staging chunk
+constexpr int NFFT_CHUNK = 128;         // points per bulk-copied staging chunk
 // Window table row of one point (floats): phi_x (2m), phi_y (2m), phi_z (2m),
 // each block padded to a 16-byte multiple, so that every chunk of the table is a
 // legal bulk-copy source and every block a run of 16-byte vector loads.
