@@ -155,10 +155,15 @@ __device__ __forceinline__ void spread_run_mma(const float* sw, int p0, int p1, 
   const bool vr0 = r0 < W2 * W2, vr1 = r1 < W2 * W2;
   const int kz0 = vr0 ? r0 / W2 : 0, ky0 = vr0 ? r0 - kz0 * W2 : 0;
   const int kz1 = vr1 ? r1 / W2 : 0, ky1 = vr1 ? r1 - kz1 * W2 : 0;
-  float c[NTL][4];
+  // Separate accumulators for the three split products and for even / odd
+  // k-steps: twelve independent MMA chains instead of one.
+  float c[NTL][6][4];
 #pragma unroll
-  for (int nt = 0; nt < NTL; ++nt) c[nt][0] = c[nt][1] = c[nt][2] = c[nt][3] = 0.f;
-  for (int q = p0; q < p1; q += 8) {
+  for (int nt = 0; nt < NTL; ++nt)
+#pragma unroll
+    for (int j = 0; j < 6; ++j) c[nt][j][0] = c[nt][j][1] = c[nt][j][2] = c[nt][j][3] = 0.f;
+  int par = 0;
+  for (int q = p0; q < p1; q += 8, par ^= 3) {
     const int qa = q + t, qb = q + t + 4;
     const bool va = qa < p1, vb = qb < p1;
     const float* wa = sw + (va ? qa : p0) * WS;
@@ -175,26 +180,41 @@ __device__ __forceinline__ void spread_run_mma(const float* sw, int p0, int p1, 
       split_tf32((va && kx < W2) ? wa[kx] : 0.f, bh[nt][0], bl[nt][0]);
       split_tf32((vb && kx < W2) ? wb[kx] : 0.f, bh[nt][1], bl[nt][1]);
     }
+    if (par == 0) {
 #pragma unroll
-    for (int nt = 0; nt < NTL; ++nt) mma_tf32(c[nt], alo, bh[nt][0], bh[nt][1]);
+      for (int nt = 0; nt < NTL; ++nt) {
+        mma_tf32(c[nt][0], alo, bh[nt][0], bh[nt][1]);
+        mma_tf32(c[nt][1], ahi, bl[nt][0], bl[nt][1]);
+        mma_tf32(c[nt][2], ahi, bh[nt][0], bh[nt][1]);
+      }
+    } else {
 #pragma unroll
-    for (int nt = 0; nt < NTL; ++nt) mma_tf32(c[nt], ahi, bl[nt][0], bl[nt][1]);
-#pragma unroll
-    for (int nt = 0; nt < NTL; ++nt) mma_tf32(c[nt], ahi, bh[nt][0], bh[nt][1]);
+      for (int nt = 0; nt < NTL; ++nt) {
+        mma_tf32(c[nt][3], alo, bh[nt][0], bh[nt][1]);
+        mma_tf32(c[nt][4], ahi, bl[nt][0], bl[nt][1]);
+        mma_tf32(c[nt][5], ahi, bh[nt][0], bh[nt][1]);
+      }
+    }
   }
+#pragma unroll
+  for (int nt = 0; nt < NTL; ++nt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+      c[nt][0][e] = ((c[nt][0][e] + c[nt][1][e]) + (c[nt][3][e] + c[nt][4][e])) +
+                    (c[nt][2][e] + c[nt][5][e]);
 #pragma unroll
   for (int nt = 0; nt < NTL; ++nt) {
     const int kx = nt * 8 + 2 * t;  // columns kx, kx + 1 (W2 even: both valid or neither)
     if (kx < W2) {
       if (vr0) {
         float* d = dst + (kz0 * E + ky0) * E + kx;
-        d[0] += c[nt][0];
-        d[1] += c[nt][1];
+        d[0] += c[nt][0][0];
+        d[1] += c[nt][0][1];
       }
       if (vr1) {
         float* d = dst + (kz1 * E + ky1) * E + kx;
-        d[0] += c[nt][2];
-        d[1] += c[nt][3];
+        d[0] += c[nt][0][2];
+        d[1] += c[nt][0][3];
       }
     }
   }
@@ -694,7 +714,11 @@ __device__ __forceinline__ void gather_run_mma(const float* sw, int s0, int cnt,
   float rs0 = 0.f, rs1 = 0.f;
   // two n-tiles at a time: independent accumulators overlap the MMA latencies
   for (int nt = 0; nt < NT; nt += 2) {
-    float c[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+    float c[2][3][4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) c[h][j][0] = c[h][j][1] = c[h][j][2] = c[h][j][3] = 0.f;
     unsigned bh[2][KS][2], bl[2][KS][2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
@@ -712,19 +736,23 @@ __device__ __forceinline__ void gather_run_mma(const float* sw, int s0, int cnt,
 #pragma unroll
     for (int ks = 0; ks < KS; ++ks) {
 #pragma unroll
-      for (int h = 0; h < 2; ++h) mma_tf32(c[h], alo[ks], bh[h][ks][0], bh[h][ks][1]);
+      for (int h = 0; h < 2; ++h) mma_tf32(c[h][0], alo[ks], bh[h][ks][0], bh[h][ks][1]);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) mma_tf32(c[h], ahi[ks], bl[h][ks][0], bl[h][ks][1]);
+      for (int h = 0; h < 2; ++h) mma_tf32(c[h][1], ahi[ks], bl[h][ks][0], bl[h][ks][1]);
 #pragma unroll
-      for (int h = 0; h < 2; ++h) mma_tf32(c[h], ahi[ks], bh[h][ks][0], bh[h][ks][1]);
+      for (int h = 0; h < 2; ++h) mma_tf32(c[h][2], ahi[ks], bh[h][ks][0], bh[h][ks][1]);
     }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) c[h][0][e] = (c[h][0][e] + c[h][1][e]) + c[h][2][e];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int n0 = (nt + h) * 8 + 2 * t;          // this lane's C columns n0, n0 + 1
       if (n0 < W2 * W2) {
         const int kz = n0 / W2, ky = n0 - kz * W2; // n0 even, W2 even: same kz for n0 + 1
-        rs0 = fmaf(w0[ZO + kz], fmaf(c[h][1], w0[YO + ky + 1], c[h][0] * w0[YO + ky]), rs0);
-        rs1 = fmaf(w1[ZO + kz], fmaf(c[h][3], w1[YO + ky + 1], c[h][2] * w1[YO + ky]), rs1);
+        rs0 = fmaf(w0[ZO + kz], fmaf(c[h][0][1], w0[YO + ky + 1], c[h][0][0] * w0[YO + ky]), rs0);
+        rs1 = fmaf(w1[ZO + kz], fmaf(c[h][0][3], w1[YO + ky + 1], c[h][0][2] * w1[YO + ky]), rs1);
       }
     }
   }
