@@ -16,14 +16,23 @@ namespace uotk {
 constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit granularity)
 constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
 constexpr int NFFT_MAX_M = 8;
-constexpr int NFFT_CHUNK = 128;         // points per bulk-copied staging chunk
-// Window table row of one point (floats): phi_x (2m), phi_y (2m), phi_z (2m),
-// each block padded to a 16-byte multiple, so that every chunk of the table is a
-// legal bulk-copy source and every block a run of 16-byte vector loads.
-__host__ __device__ constexpr int nfft_win_blk(int m) { return (2 * m + 3) & ~3; }
-__host__ __device__ constexpr int nfft_win_yoff(int m) { return nfft_win_blk(m); }
-__host__ __device__ constexpr int nfft_win_zoff(int m) { return 2 * nfft_win_blk(m); }
-__host__ __device__ constexpr int nfft_win_stride(int m) { return 3 * nfft_win_blk(m); }
+constexpr int NFFT_CHUNK = 64;          // points per bulk-copied staging chunk
+// Window table row of one point (floats): phi_x split in two halves of m
+// values, then phi_y (2m), then phi_z (2m); every block padded to a 16-byte
+// multiple, so that every chunk of the table is a legal bulk-copy source and
+// each half of phi_x and all of phi_z are 16-byte vector loads.
+__host__ __device__ constexpr int nfft_win_half(int m) { return (m + 3) & ~3; }
+__host__ __device__ constexpr int nfft_win_yoff(int m) { return 2 * nfft_win_half(m); }
+__host__ __device__ constexpr int nfft_win_zoff(int m) {
+  return 2 * nfft_win_half(m) + ((2 * m + 3) & ~3);
+}
+__host__ __device__ constexpr int nfft_win_stride(int m) {
+  return nfft_win_zoff(m) + ((2 * m + 3) & ~3);
+}
+// Offset in the row of phi_x[kx], kx in [0, 2m).
+__host__ __device__ constexpr int nfft_win_xoff(int m, int kx) {
+  return kx < m ? kx : nfft_win_half(m) + kx - m;
+}
 
 struct NfftParams {
   int d = 3;

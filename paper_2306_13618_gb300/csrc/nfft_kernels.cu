@@ -26,11 +26,10 @@ namespace uotk {
 
 namespace {
 
+constexpr int CH = NFFT_CHUNK;
 constexpr int STAGES = 2;
-constexpr int SPREAD_CHUNK = 64;         // spread: more CTAs per SM
-constexpr int GATHER_CHUNK = NFFT_CHUNK; // gather: enough 16-target runs per chunk for every warp
 
-template <int M, int CH>
+template <int M>
 struct Geo {
   static constexpr int W2 = 2 * M;
   static constexpr int E = NFFT_TILE + 2 * M - 1;
@@ -45,10 +44,10 @@ struct Geo {
 // the window rows (16-byte aligned by construction), and the packed cells and
 // weights from the 16-byte-aligned element at or below the chunk start, whose
 // offset `off` (0..3) the consumer adds back.
-template <int M, int CH>
+template <int M>
 __device__ __forceinline__ void stage_chunk(float* st, unsigned long long* bar, const float* win,
                                             const int* ckey, const float* wts, int q0, int cn) {
-  using G = Geo<M, CH>;
+  using G = Geo<M>;
   const int off = q0 & 3;
   const unsigned wbytes = (unsigned)(cn * G::WS * 4);
   const unsigned kbytes = (unsigned)(((cn + off + 3) & ~3) * 4);
@@ -98,143 +97,17 @@ __device__ __forceinline__ void load_vec(const float* p, float* r) {
   if (K - j == 1) r[j] = p[j];
 }
 
-// M floats starting at an 8-byte boundary when M is even (a half row of
-// phi_x: offset half*M), else 4-byte.
-template <int M>
-__device__ __forceinline__ void load_row(const float* p, float* r) {
-  if (M % 2 == 0) {
-#pragma unroll
-    for (int j = 0; j < M; j += 2) {
-      const float2 v = *reinterpret_cast<const float2*>(p + j);
-      r[j] = v.x;
-      r[j + 1] = v.y;
-    }
-  } else {
-#pragma unroll
-    for (int j = 0; j < M; ++j) r[j] = p[j];
-  }
-}
-
-__device__ __forceinline__ unsigned to_tf32(float x) {
-  unsigned r;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
-  return r;
-}
-__device__ __forceinline__ void split_tf32(float x, unsigned& hi, unsigned& lo) {
-  hi = to_tf32(x);
-  lo = to_tf32(x - __uint_as_float(hi));
-}
-__device__ __forceinline__ void mma_tf32(float (&c)[4], const unsigned (&a)[4], unsigned b0,
-                                         unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
-}
-
 // ---------------------------------------------------------------- spread ----
-// Threads of a spread CTA: 8 m^2 (rounded up to whole warps).
 template <int M>
-constexpr int spread_threads() { return 32 * ((8 * M * M + 31) / 32); }
-
-// Tensor-core path for a run of sources in one cell (weights folded into phi_z):
-//   C[(kz,ky)][kx] = sum_p (w_p phi_z,p[kz] phi_y,p[ky]) phi_x,p[kx]
-// is the product of A ((kz,ky) rows x points) and B (points x kx), taken with
-// m16n8k8 TF32 MMAs in three split products (FP32-level accuracy).  Warp w
-// owns the 16 rows 16w .. 16w+15 of (kz, ky); K runs over the points in steps
-// of 8; the result is added to the footprint at `dst` in the shared block.
-template <int M, int CHK>
-__device__ __forceinline__ void spread_run_mma(const float* sw, int p0, int p1, float* dst) {
-  using G = Geo<M, CHK>;
-  constexpr int W2 = G::W2, E = G::E, WS = G::WS;
-  constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
-  constexpr int NTL = (W2 + 7) / 8;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3, warp = threadIdx.x >> 5;
-  const int r0 = 16 * warp + g, r1 = r0 + 8;
-  const bool vr0 = r0 < W2 * W2, vr1 = r1 < W2 * W2;
-  const int kz0 = vr0 ? r0 / W2 : 0, ky0 = vr0 ? r0 - kz0 * W2 : 0;
-  const int kz1 = vr1 ? r1 / W2 : 0, ky1 = vr1 ? r1 - kz1 * W2 : 0;
-  // Separate accumulators for the three split products and for even / odd
-  // k-steps: twelve independent MMA chains instead of one.
-  float c[NTL][6][4];
-#pragma unroll
-  for (int nt = 0; nt < NTL; ++nt)
-#pragma unroll
-    for (int j = 0; j < 6; ++j) c[nt][j][0] = c[nt][j][1] = c[nt][j][2] = c[nt][j][3] = 0.f;
-  int par = 0;
-  for (int q = p0; q < p1; q += 8, par ^= 3) {
-    const int qa = q + t, qb = q + t + 4;
-    const bool va = qa < p1, vb = qb < p1;
-    const float* wa = sw + (va ? qa : p0) * WS;
-    const float* wb = sw + (vb ? qb : p0) * WS;
-    unsigned ahi[4], alo[4];
-    split_tf32((va && vr0) ? wa[ZO + kz0] * wa[YO + ky0] : 0.f, ahi[0], alo[0]);
-    split_tf32((va && vr1) ? wa[ZO + kz1] * wa[YO + ky1] : 0.f, ahi[1], alo[1]);
-    split_tf32((vb && vr0) ? wb[ZO + kz0] * wb[YO + ky0] : 0.f, ahi[2], alo[2]);
-    split_tf32((vb && vr1) ? wb[ZO + kz1] * wb[YO + ky1] : 0.f, ahi[3], alo[3]);
-    unsigned bh[NTL][2], bl[NTL][2];
-#pragma unroll
-    for (int nt = 0; nt < NTL; ++nt) {
-      const int kx = nt * 8 + g;
-      split_tf32((va && kx < W2) ? wa[kx] : 0.f, bh[nt][0], bl[nt][0]);
-      split_tf32((vb && kx < W2) ? wb[kx] : 0.f, bh[nt][1], bl[nt][1]);
-    }
-    if (par == 0) {
-#pragma unroll
-      for (int nt = 0; nt < NTL; ++nt) {
-        mma_tf32(c[nt][0], alo, bh[nt][0], bh[nt][1]);
-        mma_tf32(c[nt][1], ahi, bl[nt][0], bl[nt][1]);
-        mma_tf32(c[nt][2], ahi, bh[nt][0], bh[nt][1]);
-      }
-    } else {
-#pragma unroll
-      for (int nt = 0; nt < NTL; ++nt) {
-        mma_tf32(c[nt][3], alo, bh[nt][0], bh[nt][1]);
-        mma_tf32(c[nt][4], ahi, bl[nt][0], bl[nt][1]);
-        mma_tf32(c[nt][5], ahi, bh[nt][0], bh[nt][1]);
-      }
-    }
-  }
-#pragma unroll
-  for (int nt = 0; nt < NTL; ++nt)
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      c[nt][0][e] = ((c[nt][0][e] + c[nt][1][e]) + (c[nt][3][e] + c[nt][4][e])) +
-                    (c[nt][2][e] + c[nt][5][e]);
-#pragma unroll
-  for (int nt = 0; nt < NTL; ++nt) {
-    const int kx = nt * 8 + 2 * t;  // columns kx, kx + 1 (W2 even: both valid or neither)
-    if (kx < W2) {
-      if (vr0) {
-        float* d = dst + (kz0 * E + ky0) * E + kx;
-        d[0] += c[nt][0][0];
-        d[1] += c[nt][0][1];
-      }
-      if (vr1) {
-        float* d = dst + (kz1 * E + ky1) * E + kx;
-        d[0] += c[nt][0][2];
-        d[1] += c[nt][0][3];
-      }
-    }
-  }
-}
-
-// Runs of at least this many sources of one cell take the tensor-core path.
-constexpr int SPREAD_MMA_MIN = 4;
-
-template <int M>
-__global__ void __launch_bounds__(spread_threads<M>())
+__global__ void __launch_bounds__(8 * M * M)
     k_spread(const float* __restrict__ win, const int* __restrict__ ckey,
              const float* __restrict__ wts, const int* __restrict__ unit_tile,
              const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
              const int* __restrict__ num_units, int n, int tiles1, float* __restrict__ grid,
              long long* __restrict__ flags) {
-  constexpr int CH = SPREAD_CHUNK;
-  using G = Geo<M, CH>;
-  constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = spread_threads<M>();
-  constexpr int MT = (W2 * W2 + 15) / 16;  // 16-row tiles of (kz, ky) for the tensor-core path
-  constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
+  using G = Geo<M>;
+  constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M;
+  constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
   __shared__ int gstart[CH + 1];
@@ -249,17 +122,16 @@ __global__ void __launch_bounds__(spread_threads<M>())
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
-      stage_chunk<M, CH>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, wts, b0 + k * CH,
-                         min(CH, cnt - k * CH));
+      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, wts, b0 + k * CH,
+                     min(CH, cnt - k * CH));
   }
   for (int i = threadIdx.x; i < E3; i += NT) blk[i] = 0.f;
   __syncthreads();  // barriers initialised and block zeroed before anyone waits or adds
   int tx0, ty0, tz0;
   tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
-  const bool active = threadIdx.x < 8 * M * M;  // owns footprint row r, half `half`
-  const int kz = active ? r / W2 : 0, ky = active ? r - kz * W2 : 0;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int kz = r / W2, ky = r - kz * W2;
+  const int lane = threadIdx.x & 31;
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
     const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), off = q0 & 3;
@@ -288,31 +160,38 @@ __global__ void __launch_bounds__(spread_threads<M>())
     for (int g = 0; g < ng; ++g) {
       const int p0 = gstart[g], p1 = gstart[g + 1];
       const int key = skey[p0];
-      const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-      float* fp = blk + (bz * E + by) * E + bx;  // footprint origin of this cell
-      if (p1 - p0 >= SPREAD_MMA_MIN) {
-        if (warp < MT) spread_run_mma<M, CH>(sw, p0, p1, fp);
-      } else if (active) {
-        float acc[M];
+      float acc[M];
 #pragma unroll
-        for (int j = 0; j < M; ++j) acc[j] = 0.f;
-        for (int q = p0; q < p1; ++q) {
-          const float* w0 = sw + q * WS;
-          const float a0 = w0[ZO + kz] * w0[YO + ky];
-          float f0[M];
-          load_row<M>(w0 + half * M, f0);
+      for (int j = 0; j < M; ++j) acc[j] = 0.f;
+      int q = p0;
+      for (; q + 1 < p1; q += 2) {
+        const float* w0 = sw + q * WS;
+        const float* w1 = w0 + WS;
+        const float a0 = w0[ZO + kz] * w0[YO + ky];
+        const float a1 = w1[ZO + kz] * w1[YO + ky];
+        float f0[M], f1[M];
+        load_vec<M>(w0 + half * HP, f0);
+        load_vec<M>(w1 + half * HP, f1);
 #pragma unroll
-          for (int j = 0; j < M; ++j) acc[j] = fmaf(a0, f0[j], acc[j]);
-        }
-        float* dst = fp + (kz * E + ky) * E + half * M;
-#pragma unroll
-        for (int j = 0; j < M; ++j) dst[j] += acc[j];
+        for (int j = 0; j < M; ++j) acc[j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[j]));
       }
+      if (q < p1) {
+        const float* w0 = sw + q * WS;
+        const float a0 = w0[ZO + kz] * w0[YO + ky];
+        float f0[M];
+        load_vec<M>(w0 + half * HP, f0);
+#pragma unroll
+        for (int j = 0; j < M; ++j) acc[j] = fmaf(a0, f0[j], acc[j]);
+      }
+      const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+      float* dst = blk + ((bz + kz) * E + by + ky) * E + bx + half * M;
+#pragma unroll
+      for (int j = 0; j < M; ++j) dst[j] += acc[j];
       __syncthreads();
     }
     if (threadIdx.x == 0 && k + STAGES < nchunks)
-      stage_chunk<M, CH>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, wts,
-                         b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
+      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, wts,
+                     b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
   }
   __syncthreads();
   for (int i = threadIdx.x; i < E3; i += NT) {
@@ -676,115 +555,22 @@ __global__ void __launch_bounds__(FFT_THREADS)
 }
 
 // ---------------------------------------------------------------- gather ----
-// Tensor-core path for a run of targets in one cell.  With H the footprint of
-// the cell (H[kz][ky][kx], (2m)^3 grid values), the gather of target p is
-//   s_p = sum_{kz,ky} phi_z,p[kz] phi_y,p[ky] T[p][(kz,ky)],
-//   T[p][(kz,ky)] = sum_kx phi_x,p[kx] H[kz][ky][kx],
-// and T = Phi_x H^T is a dense product: m16n8k8 TF32 MMAs with FP32
-// accumulation, each operand split into a TF32 head and tail and the three
-// significant products added (FP32-level accuracy).  Rows of the 16-row tile are
-// targets, the K index is kx, columns are (kz, ky) pairs; the epilogue weighs
-// each column with phi_z phi_y of its row's target and sums.
-// One warp: targets s0 .. s0+cnt-1 (cnt <= 16) of the staged chunk, all in the
-// cell whose footprint starts at `src` in the shared block.
 template <int M>
-__device__ __forceinline__ void gather_run_mma(const float* sw, int s0, int cnt, const float* src,
-                                               float* out) {
-  using G = Geo<M, GATHER_CHUNK>;
-  constexpr int W2 = G::W2, E = G::E, E2 = G::E2, WS = G::WS;
-  constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
-  constexpr int NT = (W2 * W2 + 7) / 8, KS = (W2 + 7) / 8;
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const bool v0 = g < cnt, v1 = g + 8 < cnt;
-  const float* w0 = sw + (s0 + (v0 ? g : 0)) * WS;
-  const float* w1 = sw + (s0 + (v1 ? g + 8 : 0)) * WS;
-  unsigned ahi[KS][4], alo[KS][4];
-#pragma unroll
-  for (int ks = 0; ks < KS; ++ks) {
-    const int ka = ks * 8 + t, kb = ka + 4;
-    const float x0 = (v0 && ka < W2) ? w0[ka] : 0.f;
-    const float x1 = (v1 && ka < W2) ? w1[ka] : 0.f;
-    const float x2 = (v0 && kb < W2) ? w0[kb] : 0.f;
-    const float x3 = (v1 && kb < W2) ? w1[kb] : 0.f;
-    split_tf32(x0, ahi[ks][0], alo[ks][0]);
-    split_tf32(x1, ahi[ks][1], alo[ks][1]);
-    split_tf32(x2, ahi[ks][2], alo[ks][2]);
-    split_tf32(x3, ahi[ks][3], alo[ks][3]);
-  }
-  float rs0 = 0.f, rs1 = 0.f;
-  // two n-tiles at a time: independent accumulators overlap the MMA latencies
-  for (int nt = 0; nt < NT; nt += 2) {
-    float c[2][3][4];
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) c[h][j][0] = c[h][j][1] = c[h][j][2] = c[h][j][3] = 0.f;
-    unsigned bh[2][KS][2], bl[2][KS][2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int n = (nt + h) * 8 + g;               // this lane's B column
-      const bool vn = n < W2 * W2;
-      const int kzb = vn ? n / W2 : 0, kyb = vn ? n - kzb * W2 : 0;
-      const float* hrow = src + kzb * E2 + kyb * E;
-#pragma unroll
-      for (int ks = 0; ks < KS; ++ks) {
-        const int ka = ks * 8 + t, kb = ka + 4;
-        split_tf32((vn && ka < W2) ? hrow[ka] : 0.f, bh[h][ks][0], bl[h][ks][0]);
-        split_tf32((vn && kb < W2) ? hrow[kb] : 0.f, bh[h][ks][1], bl[h][ks][1]);
-      }
-    }
-#pragma unroll
-    for (int ks = 0; ks < KS; ++ks) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) mma_tf32(c[h][0], alo[ks], bh[h][ks][0], bh[h][ks][1]);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) mma_tf32(c[h][1], ahi[ks], bl[h][ks][0], bl[h][ks][1]);
-#pragma unroll
-      for (int h = 0; h < 2; ++h) mma_tf32(c[h][2], ahi[ks], bh[h][ks][0], bh[h][ks][1]);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) c[h][0][e] = (c[h][0][e] + c[h][1][e]) + c[h][2][e];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int n0 = (nt + h) * 8 + 2 * t;          // this lane's C columns n0, n0 + 1
-      if (n0 < W2 * W2) {
-        const int kz = n0 / W2, ky = n0 - kz * W2; // n0 even, W2 even: same kz for n0 + 1
-        rs0 = fmaf(w0[ZO + kz], fmaf(c[h][0][1], w0[YO + ky + 1], c[h][0][0] * w0[YO + ky]), rs0);
-        rs1 = fmaf(w1[ZO + kz], fmaf(c[h][0][3], w1[YO + ky + 1], c[h][0][2] * w1[YO + ky]), rs1);
-      }
-    }
-  }
-  rs0 += __shfl_xor_sync(0xffffffffu, rs0, 1);
-  rs0 += __shfl_xor_sync(0xffffffffu, rs0, 2);
-  rs1 += __shfl_xor_sync(0xffffffffu, rs1, 1);
-  rs1 += __shfl_xor_sync(0xffffffffu, rs1, 2);
-  if (t == 0) {
-    if (v0) out[s0 + g] = rs0;
-    if (v1) out[s0 + g + 8] = rs1;
-  }
-}
-
-// Runs of at least this many targets of one cell take the tensor-core path.
-constexpr int GATHER_MMA_MIN = 4;
-
-template <int M>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256)
     k_gather(const float* __restrict__ win, const int* __restrict__ ckey,
              const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
              const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
              int tiles1, const float* __restrict__ grid, float* __restrict__ out,
              long long* __restrict__ flags) {
-  constexpr int CH = GATHER_CHUNK;
-  using G = Geo<M, CH>;
+  using G = Geo<M>;
   constexpr int W2 = G::W2, E = G::E, E2 = G::E2, E3 = G::E3, WS = G::WS;
   constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   constexpr int NIT = (W2 * W2 + 31) / 32;
+  // Footprint of the current cell kept in registers while a warp's consecutive
+  // targets share that cell.
+  constexpr bool CACHE = NIT * W2 <= 64;
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
-  __shared__ int gstart[CH + 1];
-  __shared__ int ngroups;
   float* blk = smem;
   float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
@@ -795,8 +581,8 @@ __global__ void __launch_bounds__(256, 2)
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
-      stage_chunk<M, CH>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * CH,
-                         min(CH, cnt - k * CH));
+      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * CH,
+                     min(CH, cnt - k * CH));
   }
   int tx0, ty0, tz0;
   tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
@@ -815,80 +601,77 @@ __global__ void __launch_bounds__(256, 2)
   for (int it = 0; it < NIT; ++it) {
     const int c = lane + 32 * it;
     const int kx = c % W2, ky = c / W2;
-    kxs[it] = kx;       // offset of phi_x[kx] in the window row
-    kys[it] = YO + ky;  // offset of phi_y[ky]
+    kxs[it] = nfft_win_xoff(M, kx);  // offset of phi_x[kx] in the window row
+    kys[it] = YO + ky;               // offset of phi_y[ky]
     off[it] = c < W2 * W2 ? ky * E + kx : -1;
   }
+  float hc[CACHE ? NIT * W2 : 1];
+  int cached = -1;
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
     const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), koff = q0 & 3;
     const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
     const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + koff;
-    if (threadIdx.x < 32) {
-      int base = 0;
-      for (int h = 0; h < CH; h += 32) {
-        const int q = h + lane;
-        const bool f = q < cn && (q == 0 || skey[q] != skey[q - 1]);
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (f) gstart[base + __popc(bal & ((1u << lane) - 1u))] = q;
-        base += __popc(bal);
-      }
-      if (lane == 0) { ngroups = base; gstart[base] = cn; }
-    }
-    __syncthreads();
-    const int ng = ngroups;
-    float* outc = out + q0;
-    int item = 0;  // work items (runs of up to 16 targets, or single targets) dealt to warps in turn
-    for (int gi = 0; gi < ng; ++gi) {
-      const int p0 = gstart[gi], p1 = gstart[gi + 1];
-      const int key = skey[p0];
+    for (int p = warp; p < cn; p += nwarps) {
+      const int key = skey[p];
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+      const float* wq = sw + p * WS;
       const float* src = blk + (bz * E + by) * E + bx;
-      if (p1 - p0 >= GATHER_MMA_MIN) {
-        for (int s0 = p0; s0 < p1; s0 += 16, ++item)
-          if (item % nwarps == warp) gather_run_mma<M>(sw, s0, min(16, p1 - s0), src, outc);
-        continue;
-      }
-      for (int p = p0; p < p1; ++p, ++item) {
-        if (item % nwarps != warp) continue;
-        const float* wq = sw + p * WS;
-        float fz[W2];
-        load_vec<W2>(wq + ZO, fz);
-        float acc = 0.f;
+      float fz[W2];
+      load_vec<W2>(wq + ZO, fz);
+      float acc = 0.f;
+      if (CACHE) {
+        if (key != cached) {
+#pragma unroll
+          for (int it = 0; it < NIT; ++it)
+#pragma unroll
+            for (int kk = 0; kk < W2; ++kk)
+              hc[CACHE ? it * W2 + kk : 0] = off[it] >= 0 ? src[kk * E2 + off[it]] : 0.f;
+          cached = key;
+        }
+#pragma unroll
+        for (int it = 0; it < NIT; ++it) {
+          float s = 0.f;
+#pragma unroll
+          for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], hc[CACHE ? it * W2 + kk : 0], s);
+          const float pxy = off[it] >= 0 ? wq[kxs[it]] * wq[kys[it]] : 0.f;
+          acc = fmaf(pxy, s, acc);
+        }
+      } else {
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
           if (off[it] >= 0) {
             const float pxy = wq[kxs[it]] * wq[kys[it]];
             const float* col = src + off[it];
-            float sacc = 0.f;
+            float s = 0.f;
 #pragma unroll
-            for (int kk = 0; kk < W2; ++kk) sacc = fmaf(fz[kk], col[kk * E2], sacc);
-            acc = fmaf(pxy, sacc, acc);
+            for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], col[kk * E2], s);
+            acc = fmaf(pxy, s, acc);
           }
         }
-        acc = warp_sum(acc);
-        if (lane == 0) outc[p] = acc;
       }
+      acc = warp_sum(acc);
+      if (lane == 0) out[q0 + p] = acc;
     }
     __syncthreads();
     if (threadIdx.x == 0 && k + STAGES < nchunks)
-      stage_chunk<M, CH>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey,
-                         nullptr, b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
+      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, nullptr,
+                     b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
   }
 }
 
-template <int M, int CH>
+template <int M>
 size_t unit_smem() {
-  using G = Geo<M, CH>;
+  using G = Geo<M>;
   return sizeof(float) * (G::E3P + STAGES * G::STAGE_F);
 }
 
 template <int M>
 uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* wts, float* grid) {
-  const size_t smem = unit_smem<M, SPREAD_CHUNK>();
+  const size_t smem = unit_smem<M>();
   UOTK_CUDA(ctx, smem_attr(s, k_spread<M>, smem));
-  k_spread<M><<<S.max_units, spread_threads<M>(), smem, s>>>(S.win, S.ckey, wts, S.unit_tile, S.unit_begin,
+  k_spread<M><<<S.max_units, 8 * M * M, smem, s>>>(S.win, S.ckey, wts, S.unit_tile, S.unit_begin,
                                                    S.unit_count, S.num_units, P.n, P.tiles1, grid,
                                                    ctx->dflags);
   UOTK_LAUNCHED(ctx);
@@ -898,7 +681,7 @@ uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
 template <int M>
 uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* grid, float* out) {
-  const size_t smem = unit_smem<M, GATHER_CHUNK>();
+  const size_t smem = unit_smem<M>();
   UOTK_CUDA(ctx, smem_attr(s, k_gather<M>, smem));
   k_gather<M><<<S.max_units, 256, smem, s>>>(S.win, S.ckey, S.unit_tile, S.unit_begin,
                                              S.unit_count, S.num_units, P.n, P.tiles1, grid, out,

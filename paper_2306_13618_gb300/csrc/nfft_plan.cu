@@ -271,14 +271,15 @@ __device__ __forceinline__ float kb_window(float v, int m, float b) {
 
 __global__ void k_windows(const int4* __restrict__ cell, long long n, int m, float b,
                           int d, float* __restrict__ win) {
-  const int w2 = 2 * m, ws = nfft_win_stride(m);
+  const int w2 = 2 * m, ws = nfft_win_stride(m), hp = nfft_win_half(m);
   const int yo = nfft_win_yoff(m), zo = nfft_win_zoff(m);
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * ws;
        i += (long long)gridDim.x * blockDim.x) {
     const long long q = i / ws;
     const int r = (int)(i - q * ws);
     int t, k;
-    if (r < w2) { t = 0; k = r; }
+    if (r < m) { t = 0; k = r; }
+    else if (r >= hp && r < hp + m) { t = 0; k = r - hp + m; }
     else if (r >= yo && r < yo + w2) { t = 1; k = r - yo; }
     else if (r >= zo && r < zo + w2) { t = 2; k = r - zo; }
     else { win[i] = 0.f; continue; }
