@@ -160,6 +160,24 @@ def stage_rooflines(prof, W, sms, peaks, plan):
     return out
 
 
+def recorded_traffic(stage):
+    """DRAM bytes per launch of `stage` from the committed ncu capture
+    (profiles/ncu_traffic.json), or None when the kernel source has changed since
+    the capture (its SHA-256 no longer matches) or no capture exists."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+            rec = json.load(f)
+        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()
+    except (OSError, ValueError, KeyError):
+        return None
+    if sha != rec.get("source_sha256"):
+        return None
+    k = rec.get("kernels", {}).get(stage)
+    return k.get("bytes_per_launch") if k else None
+
+
 def cpu_oracle_rate(W, seconds, rank0=True):
     """FP64 oracle kernel-sum pairs/s on this host: all sources onto a sample of
     targets sized for about `seconds` of CPU work."""
@@ -307,7 +325,7 @@ def main():
     roofs = stage_rooflines(prof, W, sms, peaks, plan)
     dom = max(roofs.values(), key=lambda r: r["ms_total"]) if roofs else {}
     roof = {k: v for k, v in dom.items() if k != "ms_total"}
-    roof["traffic"] = None
+    roof["traffic"] = recorded_traffic(roof.get("kernel"))
 
     # --- end to end through the C ABI from pinned host buffers ---
     hx, hy = torch.from_numpy(W.x).pin_memory(), torch.from_numpy(W.y).pin_memory()
