@@ -188,6 +188,47 @@ uotk_status uotk_mmd2(uotk_ctx* ctx, void* stream, int d,
                       const float* y, int64_t m, const float* b,
                       double ell, double* mmd2, double* parts, const uotk_sum_opts* opts);
 
+/* ---- gradients (an extension: the paper differentiates neither quantity) ----------
+ * Both operations return the value and its partial derivatives with respect to
+ * the weights a, b and the support points x, y, as device FP64 arrays in the
+ * caller's order: grad_a [n], grad_x [n*d] (row-major like x), grad_b [m],
+ * grad_y [m*d].  Any gradient pointer may be NULL (not computed; a NULL
+ * point gradient also skips its 2d extra kernel summations per problem).
+ * Arguments otherwise as for the value operations; the method in opts
+ * (direct or NFFT) is used for every kernel summation.  Synchronises `stream`.
+ *
+ * uotk_mmd2_grad: exact derivatives of Eq. (1205) with the Gaussian kernel of
+ *   Table tab:0 (eps = ell^2):
+ *   d/da_i = 2 sum_j a_j k(x_i,x_j) - 2 sum_j b_j k(x_i,y_j),
+ *   d/dx_i = -(4 a_i/eps) [ sum_j a_j (x_i-x_j) k(x_i,x_j) - sum_j b_j (x_i-y_j) k(x_i,y_j) ],
+ *   and symmetrically for b, y.  Each (x_i - y_j)-weighted sum is formed as
+ *   x'_i t_i - s_i from two kernel summations over shifted coordinates
+ *   (origin x_0), so its absolute error is that of the sums times the
+ *   diameter of the clouds.
+ * uotk_sinkhorn_divergence_grad: derivative of Eq. (586) through the envelope
+ *   theorem: each UOT value is the maximum over (beta, gamma) of D of
+ *   Eq. (dual_euot), so its derivative is the partial derivative of D at the
+ *   duals, evaluated at the duals after max_sweeps sweeps (or tol):
+ *   d/da_i = -rho e^{-beta_i/rho} + rho - eps (e^{beta_i/eps} T_i - b(X)),
+ *   d/dx_i = 2 a_i e^{beta_i/eps} sum_j b_j e^{gamma_j/eps} (x_i - y_j) k_ij,
+ *   T_i = sum_j k_ij b_j e^{gamma_j/eps}, the symmetric problems counted
+ *   through both roles, plus +-eps (a(X) - b(X)) on the weights.  Exact at
+ *   the fixed point of Alg. 1; after finitely many sweeps it differs from the
+ *   derivative of the returned value by the dual residual.
+ *   sd, parts as for uotk_sinkhorn_divergence. */
+uotk_status uotk_mmd2_grad(uotk_ctx* ctx, void* stream, int d,
+                           const float* x, int64_t n, const float* a,
+                           const float* y, int64_t m, const float* b,
+                           double ell, double* mmd2, double* grad_a, double* grad_x,
+                           double* grad_b, double* grad_y, const uotk_sum_opts* opts);
+uotk_status uotk_sinkhorn_divergence_grad(uotk_ctx* ctx, void* stream, int d,
+                                          const float* x, int64_t n, const float* a,
+                                          const float* y, int64_t m, const float* b,
+                                          double eps, double rho, int max_sweeps, double tol,
+                                          double* sd, double* parts, double* grad_a,
+                                          double* grad_x, double* grad_b, double* grad_y,
+                                          const uotk_sum_opts* opts);
+
 /* ---- NFFT stages (Sec. 4), exposed for inspection and testing ---------------------
  * uotk_nfft_plan: choose centre, period h, grid, bandwidth and cut-off for
  *   summing from src to tgt with kernel width eps (opts as for

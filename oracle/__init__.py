@@ -71,6 +71,17 @@ def _load():
     lib.orc_sinkhorn_divergence.restype = ctypes.c_double
     lib.orc_balanced_sinkhorn.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
                                           ctypes.c_double, ctypes.c_int, _D, _D]
+    lib.orc_mmd2_grad.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D, ctypes.c_double,
+                                  _D, _D, _D, _D]
+    lib.orc_mmd2_grad_rows.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
+                                       ctypes.c_double, ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int64), _I64, _D, _D]
+    lib.orc_dual_grad.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D, ctypes.c_double,
+                                  ctypes.c_double, ctypes.c_double, _D, _D, _D, _D, _D, _D]
+    lib.orc_sinkhorn_divergence_grad.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
+                                                 ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                                 _D, _D, _D, _D]
+    lib.orc_sinkhorn_divergence_grad.restype = ctypes.c_double
     lib.orc_num_threads.restype = ctypes.c_int
     lib.orc_set_num_threads.argtypes = [ctypes.c_int]
     _lib = lib
@@ -178,3 +189,52 @@ def balanced_sinkhorn(x, P, y, Q, eps, iters):
     _load().orc_balanced_sinkhorn(x.shape[1], _p(x), x.shape[0], _p(P), _p(y), y.shape[0],
                                   _p(Q), 1.0 / eps, int(iters), _p(f), _p(g))
     return f, g
+
+
+def _grad_bufs(x, y):
+    n, d = x.shape
+    m = y.shape[0]
+    return np.empty(n), np.empty((n, d)), np.empty(m), np.empty((m, d))
+
+
+def mmd2_grad(x, mu, y, nu, ell):
+    """Derivatives of MMD^2 (Eq. 1205) in (mu, x, nu, y): returns (gmu, gx, gnu, gy)."""
+    x, y, mu, nu = _pts(x), _pts(y), _vec(mu), _vec(nu)
+    ga, gx, gb, gy = _grad_bufs(x, y)
+    _load().orc_mmd2_grad(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0], _p(nu),
+                          float(ell), _p(ga), _p(gx), _p(gb), _p(gy))
+    return ga, gx, gb, gy
+
+
+def mmd2_grad_rows(x, mu, y, nu, ell, side, rows):
+    """mmd2_grad at selected rows of one side (0: mu/x, 1: nu/y): returns (gw, gp)."""
+    x, y, mu, nu = _pts(x), _pts(y), _vec(mu), _vec(nu)
+    rows = np.ascontiguousarray(np.asarray(rows, dtype=np.int64))
+    gw, gp = np.empty(rows.size), np.empty((rows.size, x.shape[1]))
+    _load().orc_mmd2_grad_rows(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0],
+                               _p(nu), float(ell), int(side),
+                               rows.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), rows.size,
+                               _p(gw), _p(gp))
+    return gw, gp
+
+
+def dual_grad(x, mu, y, nu, eps, eta1, eta2, beta, gamma):
+    """Partial derivatives of D(beta, gamma) (Eq. dual_euot, product reference) in
+    (mu, x, nu, y) at fixed duals: returns (gmu, gx, gnu, gy)."""
+    x, y, mu, nu, beta, gamma = _pts(x), _pts(y), _vec(mu), _vec(nu), _vec(beta), _vec(gamma)
+    ga, gx, gb, gy = _grad_bufs(x, y)
+    _load().orc_dual_grad(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0], _p(nu),
+                          1.0 / eps, float(eta1), float(eta2), _p(beta), _p(gamma),
+                          _p(ga), _p(gx), _p(gb), _p(gy))
+    return ga, gx, gb, gy
+
+
+def sinkhorn_divergence_grad(x, mu, y, nu, eps, eta, sweeps=100):
+    """Sinkhorn divergence (Eq. 586) and its envelope-theorem gradient at the
+    duals after `sweeps` sweeps: returns (sd, gmu, gx, gnu, gy)."""
+    x, y, mu, nu = _pts(x), _pts(y), _vec(mu), _vec(nu)
+    ga, gx, gb, gy = _grad_bufs(x, y)
+    v = _load().orc_sinkhorn_divergence_grad(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y),
+                                             y.shape[0], _p(nu), 1.0 / eps, float(eta),
+                                             int(sweeps), _p(ga), _p(gx), _p(gb), _p(gy))
+    return v, ga, gx, gb, gy

@@ -304,3 +304,154 @@ void orc_balanced_sinkhorn(int d, const double* x, int64_t n, const double* P,
     }
   }
 }
+
+/* ---------------------------- gradients ------------------------------------
+ * Partial derivatives of the quantities above with respect to the weights and
+ * the support points, written directly from the definitions with
+ *   d/du k(u, v) = -(2/eps) (u - v) k(u, v),  k(u, v) = exp(-||u - v||^2/eps),
+ * every pairwise difference (u - v) formed explicitly.  Points are row-major
+ * (gx[i*d + c] = d/dx_ic). */
+
+/* Derivatives of MMD^2 (Eq. 1205), eps = ell^2:
+ *   d/dmu_i = 2 sum_j mu_j k(x_i,x_j) - 2 sum_j nu_j k(x_i,y_j)
+ *   d/dx_i  = 2 mu_i sum_j mu_j d/dx_i k(x_i,x_j) - 2 mu_i sum_j nu_j d/dx_i k(x_i,y_j)
+ * (each pair of the symmetric double sum counted from both ends), and the same
+ * for (nu, y) with the roles exchanged. */
+static void mmd2_grad_side(int d, const double* x, int64_t n, const double* mu,
+                           const double* y, int64_t m, const double* nu, double eps,
+                           const int64_t* rows, int64_t nrows, double* gw, double* gp) {
+#pragma omp parallel for schedule(static)
+  for (int64_t r = 0; r < nrows; ++r) {
+    const int64_t i = rows ? rows[r] : r;
+    nsum t = {0, 0};
+    nsum* g = (nsum*)calloc((size_t)d, sizeof(nsum));
+    for (int64_t j = 0; j < n; ++j) {
+      double k = exp(-sqdist(d, x + i * d, x + j * d) / eps);
+      nsum_add(&t, 2.0 * mu[j] * k);
+      for (int c = 0; c < d; ++c)
+        nsum_add(&g[c], 2.0 * mu[i] * mu[j] * (-2.0 / eps) * (x[i * d + c] - x[j * d + c]) * k);
+    }
+    for (int64_t j = 0; j < m; ++j) {
+      double k = exp(-sqdist(d, x + i * d, y + j * d) / eps);
+      nsum_add(&t, -2.0 * nu[j] * k);
+      for (int c = 0; c < d; ++c)
+        nsum_add(&g[c], -2.0 * mu[i] * nu[j] * (-2.0 / eps) * (x[i * d + c] - y[j * d + c]) * k);
+    }
+    if (gw) gw[r] = nsum_get(&t);
+    if (gp)
+      for (int c = 0; c < d; ++c) gp[r * d + c] = nsum_get(&g[c]);
+    free(g);
+  }
+}
+
+void orc_mmd2_grad(int d, const double* x, int64_t n, const double* mu,
+                   const double* y, int64_t m, const double* nu, double ell,
+                   double* gmu, double* gx, double* gnu, double* gy) {
+  const double eps = ell * ell;
+  mmd2_grad_side(d, x, n, mu, y, m, nu, eps, NULL, n, gmu, gx);
+  mmd2_grad_side(d, y, m, nu, x, n, mu, eps, NULL, m, gnu, gy);
+}
+
+/* The same derivatives at selected rows only: side 0 gives d/dmu and d/dx at
+ * the points x[rows[r]], side 1 d/dnu and d/dy at y[rows[r]]; output row r. */
+void orc_mmd2_grad_rows(int d, const double* x, int64_t n, const double* mu,
+                        const double* y, int64_t m, const double* nu, double ell, int side,
+                        const int64_t* rows, int64_t nrows, double* gw, double* gp) {
+  const double eps = ell * ell;
+  if (side == 0) mmd2_grad_side(d, x, n, mu, y, m, nu, eps, rows, nrows, gw, gp);
+  else mmd2_grad_side(d, y, m, nu, x, n, mu, eps, rows, nrows, gw, gp);
+}
+
+/* Partial derivatives of D(beta, gamma) of Eq. (dual_euot) (product
+ * reference) in mu, x, nu, y at FIXED duals:
+ *   dD/dmu_i = -eta1 e^{-beta_i/eta1} + eta1
+ *              - (1/lambda) (sum_j e^{lambda beta_i} k_ij e^{lambda gamma_j} nu_j - sum_j nu_j)
+ *   dD/dx_i  = -(1/lambda) sum_j mu_i nu_j e^{lambda (beta_i + gamma_j)} d/dx_i k_ij
+ * with lambda = 1/eps in k, and the same for nu, y with eta2. */
+static void dual_grad_side(int d, const double* x, int64_t n, const double* mu,
+                           const double* y, int64_t m, const double* nu, double lambda,
+                           double eta, const double* beta, const double* gamma,
+                           double* gw, double* gp) {
+  nsum sn = {0, 0};
+  for (int64_t j = 0; j < m; ++j) nsum_add(&sn, nu[j]);
+  const double mass = nsum_get(&sn);
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n; ++i) {
+    nsum t = {0, 0};
+    nsum* g = (nsum*)calloc((size_t)d, sizeof(nsum));
+    for (int64_t j = 0; j < m; ++j) {
+      double k = exp(-lambda * sqdist(d, x + i * d, y + j * d));
+      double e = exp(lambda * (beta[i] + gamma[j]));
+      nsum_add(&t, e * k * nu[j]);
+      for (int c = 0; c < d; ++c) {
+        double dk = -2.0 * lambda * (x[i * d + c] - y[j * d + c]) * k;
+        nsum_add(&g[c], -(1.0 / lambda) * mu[i] * nu[j] * e * dk);
+      }
+    }
+    if (gw) gw[i] = -eta * exp(-beta[i] / eta) + eta - (nsum_get(&t) - mass) / lambda;
+    if (gp)
+      for (int c = 0; c < d; ++c) gp[i * d + c] = nsum_get(&g[c]);
+    free(g);
+  }
+}
+
+void orc_dual_grad(int d, const double* x, int64_t n, const double* mu,
+                   const double* y, int64_t m, const double* nu, double lambda,
+                   double eta1, double eta2, const double* beta, const double* gamma,
+                   double* gmu, double* gx, double* gnu, double* gy) {
+  dual_grad_side(d, x, n, mu, y, m, nu, lambda, eta1, beta, gamma, gmu, gx);
+  dual_grad_side(d, y, m, nu, x, n, mu, lambda, eta2, gamma, beta, gnu, gy);
+}
+
+/* Gradient of the Sinkhorn divergence of Eq. (586) by the envelope theorem:
+ * each UOT value is max D(beta, gamma), so its derivative is the partial
+ * derivative of D at the maximising duals, here the duals after `sweeps`
+ * sweeps of Alg. 1 from gamma^0 = 0.  In UOT(mu, mu) and UOT(nu, nu) the
+ * measure fills both arguments and both partial derivatives count.  The
+ * mass term adds (mu(X) - nu(X))/lambda to d/dmu and subtracts it from d/dnu.
+ * Returns the divergence (as orc_sinkhorn_divergence). */
+double orc_sinkhorn_divergence_grad(int d, const double* x, int64_t n, const double* mu,
+                                    const double* y, int64_t m, const double* nu,
+                                    double lambda, double eta, int sweeps,
+                                    double* gmu, double* gx, double* gnu, double* gy) {
+  int64_t nmax = n > m ? n : m;
+  size_t sz = (size_t)(nmax > 0 ? nmax : 1);
+  double* b = (double*)malloc(sizeof(double) * sz);
+  double* g = (double*)malloc(sizeof(double) * sz);
+  double* w1 = (double*)malloc(sizeof(double) * sz);
+  double* w2 = (double*)malloc(sizeof(double) * sz);
+  double* p1 = (double*)malloc(sizeof(double) * sz * (size_t)d);
+  double* p2 = (double*)malloc(sizeof(double) * sz * (size_t)d);
+  double v[3];
+  /* UOT(mu, nu) */
+  memset(g, 0, sizeof(double) * (size_t)m);
+  orc_uot_sinkhorn(d, x, n, mu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g);
+  v[0] = orc_dual_value(d, x, n, mu, y, m, nu, lambda, eta, eta, b, g, 0);
+  orc_dual_grad(d, x, n, mu, y, m, nu, lambda, eta, eta, b, g, gmu, gx, gnu, gy);
+  /* UOT(mu, mu) */
+  memset(g, 0, sizeof(double) * (size_t)n);
+  orc_uot_sinkhorn(d, x, n, mu, x, n, mu, lambda, eta, eta, sweeps, 0, 0, b, g);
+  v[1] = orc_dual_value(d, x, n, mu, x, n, mu, lambda, eta, eta, b, g, 0);
+  orc_dual_grad(d, x, n, mu, x, n, mu, lambda, eta, eta, b, g, w1, p1, w2, p2);
+  for (int64_t i = 0; i < n; ++i) {
+    gmu[i] -= 0.5 * (w1[i] + w2[i]);
+    for (int c = 0; c < d; ++c) gx[i * d + c] -= 0.5 * (p1[i * d + c] + p2[i * d + c]);
+  }
+  /* UOT(nu, nu) */
+  memset(g, 0, sizeof(double) * (size_t)m);
+  orc_uot_sinkhorn(d, y, m, nu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g);
+  v[2] = orc_dual_value(d, y, m, nu, y, m, nu, lambda, eta, eta, b, g, 0);
+  orc_dual_grad(d, y, m, nu, y, m, nu, lambda, eta, eta, b, g, w1, p1, w2, p2);
+  for (int64_t j = 0; j < m; ++j) {
+    gnu[j] -= 0.5 * (w1[j] + w2[j]);
+    for (int c = 0; c < d; ++c) gy[j * d + c] -= 0.5 * (p1[j * d + c] + p2[j * d + c]);
+  }
+  free(b); free(g); free(w1); free(w2); free(p1); free(p2);
+  nsum sm = {0, 0}, sn = {0, 0};
+  for (int64_t i = 0; i < n; ++i) nsum_add(&sm, mu[i]);
+  for (int64_t j = 0; j < m; ++j) nsum_add(&sn, nu[j]);
+  double dm = nsum_get(&sm) - nsum_get(&sn);
+  for (int64_t i = 0; i < n; ++i) gmu[i] += dm / lambda;
+  for (int64_t j = 0; j < m; ++j) gnu[j] -= dm / lambda;
+  return v[0] - 0.5 * v[1] - 0.5 * v[2] + dm * dm / (2.0 * lambda);
+}

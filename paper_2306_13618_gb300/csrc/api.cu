@@ -22,6 +22,13 @@ uotk_status op_sinkhorn_divergence(uotk_ctx*, cudaStream_t, int, const float*, i
 uotk_status op_mmd2(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
                     const float*, int64_t, const float*, double, double*, double*,
                     const uotk_sum_opts*);
+uotk_status op_mmd2_grad(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
+                         const float*, int64_t, const float*, double, double*, double*, double*,
+                         double*, double*, const uotk_sum_opts*);
+uotk_status op_sinkhorn_divergence_grad(uotk_ctx*, cudaStream_t, int, const float*, int64_t,
+                                        const float*, const float*, int64_t, const float*,
+                                        double, double, int, double, double*, double*, double*,
+                                        double*, double*, double*, const uotk_sum_opts*);
 uotk_status op_nfft_plan(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
                          int64_t, double, const uotk_sum_opts*, uotk_nfft_plan_info*);
 uotk_status op_nfft_cells(uotk_ctx*, cudaStream_t, const uotk_nfft_plan_info*, const float*,
@@ -338,6 +345,61 @@ uotk_status uotk_mmd2(uotk_ctx* ctx, void* stream, int d, const float* x, int64_
   if (!(ell > 0.0) || !isfinite(ell))
     return set_error(ctx, UOTK_ERR_INVALID, "ell must be finite and > 0");
   return op_mmd2(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, ell, mmd2, parts, opts);
+}
+
+static uotk_status check_grad_outputs(uotk_ctx* ctx, int d, int64_t n, int64_t m, double* ga,
+                                      double* gx, double* gb, double* gy) {
+  (void)d;
+  (void)n;
+  (void)m;
+  const double* p[4] = {ga, gx, gb, gy};
+  const char* name[4] = {"grad_a", "grad_x", "grad_b", "grad_y"};
+  for (int k = 0; k < 4; ++k)
+    if (p[k] && !aligned(p[k], 8))
+      return set_error(ctx, UOTK_ERR_INVALID, "%s: not 8-byte aligned", name[k]);
+  return UOTK_OK;
+}
+
+uotk_status uotk_mmd2_grad(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
+                           const float* a, const float* y, int64_t m, const float* b, double ell,
+                           double* mmd2, double* grad_a, double* grad_x, double* grad_b,
+                           double* grad_y, const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_cloud(ctx, "x", x, n, d));
+  UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
+  UOTK_TRY(check_cloud(ctx, "y", y, m, d));
+  UOTK_TRY(check_cloud(ctx, "b", b, m, 1));
+  if (n < 1 || m < 1) return set_error(ctx, UOTK_ERR_INVALID, "mmd2_grad needs n >= 1 and m >= 1");
+  UOTK_TRY(check_grad_outputs(ctx, d, n, m, grad_a, grad_x, grad_b, grad_y));
+  if (!(ell > 0.0) || !isfinite(ell))
+    return set_error(ctx, UOTK_ERR_INVALID, "ell must be finite and > 0");
+  return op_mmd2_grad(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, ell, mmd2, grad_a, grad_x,
+                      grad_b, grad_y, opts);
+}
+
+uotk_status uotk_sinkhorn_divergence_grad(uotk_ctx* ctx, void* stream, int d, const float* x,
+                                          int64_t n, const float* a, const float* y, int64_t m,
+                                          const float* b, double eps, double rho, int max_sweeps,
+                                          double tol, double* sd, double* parts, double* grad_a,
+                                          double* grad_x, double* grad_b, double* grad_y,
+                                          const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_cloud(ctx, "x", x, n, d));
+  UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
+  UOTK_TRY(check_cloud(ctx, "y", y, m, d));
+  UOTK_TRY(check_cloud(ctx, "b", b, m, 1));
+  if (n < 1 || m < 1)
+    return set_error(ctx, UOTK_ERR_INVALID, "sinkhorn_divergence_grad needs n >= 1 and m >= 1");
+  UOTK_TRY(check_grad_outputs(ctx, d, n, m, grad_a, grad_x, grad_b, grad_y));
+  if (!(eps > 0.0) || !isfinite(eps) || !(rho > 0.0) || !isfinite(rho))
+    return set_error(ctx, UOTK_ERR_INVALID, "eps and rho must be finite and > 0");
+  if (max_sweeps < 1) return set_error(ctx, UOTK_ERR_INVALID, "max_sweeps must be >= 1");
+  if (!(tol >= 0.0) && !(tol <= 0.0)) return set_error(ctx, UOTK_ERR_INVALID, "tol is NaN");
+  return op_sinkhorn_divergence_grad(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho,
+                                     max_sweeps, tol, sd, parts, grad_a, grad_x, grad_b, grad_y,
+                                     opts);
 }
 
 uotk_status uotk_nfft_plan(uotk_ctx* ctx, void* stream, int d, const float* src, int64_t n,

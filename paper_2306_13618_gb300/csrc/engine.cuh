@@ -17,9 +17,12 @@ struct Engine {
   // All arrays are in internal order.
   virtual uotk_status half(cudaStream_t s, int side, const float* base, const double* pot,
                            double lam, const long long* shift_slot, float* out) = 0;
-  // Plain kernel sum with given internal-order weights (for MMD^2): t = K(src -> tgt) w.
+  // Plain kernel sum with given internal-order weights w >= 0 of the source side
+  // (w = weights(src) for the caller's weights): t = K(src -> tgt) w.
   // src/tgt: 0 = X, 1 = Y.
   virtual uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) = 0;
+  // Internal position -> caller index of `side` (NULL: identity).
+  virtual const int* perm(int side) const = 0;
   // Internal-order copies of the caller's weights (may alias the inputs).
   virtual const float* weights(int side) const = 0;
   // Scatter an internal-order FP64 array of `side` back to caller order.

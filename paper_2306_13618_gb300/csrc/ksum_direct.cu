@@ -214,10 +214,10 @@ __global__ void k_pack(const float* __restrict__ pts, const float* __restrict__ 
 __global__ void k_set_weights(void* __restrict__ packed, long long n, int small, int dp,
                               const float* __restrict__ base, const double* __restrict__ pot,
                               double lam, const long long* __restrict__ shift_slot) {
-  const double shift = ordered_to_dbl(*shift_slot);
+  const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x) {
-    float v = exp_shifted(lam * pot[i] - shift);
+    float v = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
     if (base) v *= base[i];
     if (small) reinterpret_cast<float4*>(packed)[i].w = v;
     else reinterpret_cast<float*>(packed)[i * dp + dp - 1] = v;

@@ -142,6 +142,7 @@ struct NfftEngine : Engine {
     return nfft_gather(ctx, s, P, tgt == 0 ? X : Y, W.grid, out);
   }
   const float* weights(int side) const override { return side == 0 ? as : bs; }
+  const int* perm(int side) const override { return side == 0 ? X.perm : Y.perm; }
   uotk_status to_caller(cudaStream_t s, int side, const double* in, double* out) override {
     const NfftPoints& S = side == 0 ? X : Y;
     if (S.n == 0) return UOTK_OK;

@@ -16,7 +16,7 @@
 
 #include <memory>
 
-#include "engine.cuh"
+#include "solver.cuh"
 
 namespace uotk {
 
@@ -74,11 +74,14 @@ struct DirectEngine : Engine {
     return direct_run(ctx, s, L, bufs, eps, out);
   }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
-    (void)w;  // the packed sources carry the caller's weights
     const DirectLayout& L = src == 0 ? (tgt == 0 ? Lxx : Lxy) : (tgt == 0 ? Lyx : Lyy);
-    DirectBufs bufs{src == 0 ? Px : Py, tgt == 0 ? Px : Py, part};
+    void* P = src == 0 ? Px : Py;
+    // the packed sources carry their current weights; rewrite them from w
+    UOTK_TRY(direct_set_weights(ctx, s, L, P, w, nullptr, 0.0, nullptr));
+    DirectBufs bufs{P, tgt == 0 ? Px : Py, part};
     return direct_run(ctx, s, L, bufs, eps, out);
   }
+  const int* perm(int) const override { return nullptr; }
   const float* weights(int side) const override { return side == 0 ? a : b; }
   uotk_status to_caller(cudaStream_t s, int side, const double* in, double* out) override {
     if (in != out)
@@ -164,25 +167,6 @@ __global__ void k_flags_reset(long long* flags) {
     flags[i] = (i >= FLAG_MAX_G0 && i <= FLAG_DELTA1) ? ORDERED_NEG_INF : 0LL;
 }
 
-// Block partial sums of up to 5 FP64 terms; term k over [0, len_k):
-//   kind 0: sum base_i * exp(-pot_i / eta)
-//   kind 1: sum base_i
-//   kind 2: sum base_i * t_i                     (t FP32)
-//   kind 3: sum (base_i or 1) * exp(lam*pot_i + shift) * t_i
-struct SumTerm {
-  int kind;
-  long long len;
-  const float* base;
-  const double* pot;
-  const float* t;
-  double eta, lam;
-  int shift_slot;
-};
-struct SumTerms {
-  SumTerm k[5];
-  int count;
-};
-
 __global__ void k_sum_partials(SumTerms terms, const long long* __restrict__ flags,
                                double* __restrict__ part) {
   __shared__ double sh[32];
@@ -224,11 +208,7 @@ __global__ void k_sum_final(const double* __restrict__ part, int blocks, int cou
   if (lane == 0) out[q] = s;
 }
 
-struct Reducer {
-  double* part = nullptr;  // [5][blocks]
-  double* out = nullptr;   // [5]
-  int blocks = 0;
-};
+}  // namespace
 
 uotk_status run_sums(uotk_ctx* ctx, cudaStream_t s, const Reducer& R, const SumTerms& T,
                      double* host_out) {
@@ -253,14 +233,6 @@ void carve_reducer(uotk_ctx* ctx, Carver& cv, Reducer& R) {
   R.out = cv.take<double>(5);
 }
 
-// Internal-order work arrays of one solve.
-struct SolveBufs {
-  double* beta = nullptr;   // internal order (aliases caller's when identity order)
-  double* gamma = nullptr;
-  float* tx = nullptr;
-  float* ty = nullptr;
-};
-
 void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& B) {
   B.tx = cv.take<float>(n > 0 ? n : 1);
   B.ty = cv.take<float>(m > 0 ? m : 1);
@@ -269,12 +241,6 @@ void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& 
     B.gamma = cv.take<double>(m > 0 ? m : 1);
   }
 }
-
-struct SolveResult {
-  int sweeps = 0;
-  double value = 0.0;
-  bool converged = false;
-};
 
 // Alg. 1 / Alg. 2 for up to max_sweeps sweeps on an engine, then D(beta, gamma).
 uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m, double eps,
@@ -400,7 +366,6 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
   return UOTK_OK;
 }
 
-}  // namespace
 
 // ---------------------------------------------------------------------------
 // Engine construction.

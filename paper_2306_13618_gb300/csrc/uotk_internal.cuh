@@ -57,6 +57,8 @@ enum FlagSlot {
   FLAG_DELTA1 = 9,
   FLAG_NONFINITE_DUAL = 10,  // count of non-finite dual values produced
   FLAG_BBOX = 16,          // 6 slots: max x,y,z and max of -x,-y,-z (ordered encodings)
+  FLAG_GRAD_SX = 22,       // shifts of the weights used by the gradient sums (ordered)
+  FLAG_GRAD_SY = 23,
   NUM_FLAGS = 32
 };
 
@@ -266,7 +268,8 @@ uotk_status direct_pack_sources(uotk_ctx* ctx, cudaStream_t s, const DirectLayou
 uotk_status direct_pack_targets(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
                                 const float* pts, void* packed);
 // Rewrite only the weights of packed sources: w_i = base_i * exp(lam*pot_i - shift),
-// shift read from the ordered-int64 slot *shift_slot (base may be NULL for 1).
+// shift read from the ordered-int64 slot *shift_slot (base may be NULL for 1);
+// with pot == NULL, w_i = base_i.
 uotk_status direct_set_weights(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
                                void* packed, const float* base, const double* pot,
                                double lam, const long long* shift_slot);

@@ -91,13 +91,20 @@ def lib():
                                                ctypes.POINTER(_D), opts]
         L.uotk_mmd2.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                 ctypes.POINTER(_D), ctypes.POINTER(_D), opts]
+        L.uotk_mmd2_grad.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
+                                     ctypes.POINTER(_D), _P, _P, _P, _P, opts]
+        L.uotk_sinkhorn_divergence_grad.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64,
+                                                    _P, _D, _D, ctypes.c_int, _D,
+                                                    ctypes.POINTER(_D), ctypes.POINTER(_D), _P,
+                                                    _P, _P, _P, opts]
         L.uotk_nfft_plan.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _I64, _D, opts, plan]
         L.uotk_nfft_cells.argtypes = [_P, _P, plan, _P, _I64, _P]
         L.uotk_nfft_spread.argtypes = [_P, _P, plan, _P, _I64, _P, _P]
         L.uotk_nfft_convolve.argtypes = [_P, _P, plan, _P, _P]
         L.uotk_nfft_gather.argtypes = [_P, _P, plan, _P, _P, _I64, _P]
         for name in ("uotk_create", "uotk_kernel_sum", "uotk_uot_sinkhorn",
-                     "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_nfft_plan",
+                     "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
+                     "uotk_sinkhorn_divergence_grad", "uotk_nfft_plan",
                      "uotk_nfft_cells", "uotk_nfft_spread", "uotk_nfft_convolve",
                      "uotk_nfft_gather"):
             getattr(L, name).restype = ctypes.c_int
@@ -274,6 +281,97 @@ def mmd2(x, a, y, b, ell, method="direct", ctx=None, **nfft):
     return v.value, list(parts)
 
 
+def _grad_outputs(x, y, need):
+    """FP64 device gradient buffers (a, x, b, y); None where not needed."""
+    n, d = x.shape
+    m = y.shape[0]
+    shapes = ((n,), (n, d), (m,), (m, d))
+    return [torch.empty(sh, device=x.device, dtype=torch.float64) if k else None
+            for sh, k in zip(shapes, need)]
+
+
+def mmd2_grad(x, a, y, b, ell, method="direct", need=(True, True, True, True), ctx=None,
+              **nfft):
+    """MMD^2 (Eq. 1205) and its gradients (uotk_mmd2_grad).
+
+    Returns (value, grad_a, grad_x, grad_b, grad_y): FP64 device tensors in the
+    caller's order, None where `need` is False."""
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    ctx = ctx or default_context()
+    g = _grad_outputs(x, y, need)
+    v = _D(0.0)
+    o = _opts(method, **nfft)
+    ctx.check(lib().uotk_mmd2_grad(ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0],
+                                   _ptr(a), _ptr(y), y.shape[0], _ptr(b), float(ell),
+                                   ctypes.byref(v), *[_ptr(t) for t in g], ctypes.byref(o)))
+    return (v.value, *g)
+
+
+def sinkhorn_divergence_grad(x, a, y, b, eps, rho, max_sweeps=100, tol=0.0, method="direct",
+                             need=(True, True, True, True), ctx=None, **nfft):
+    """Sinkhorn divergence (Eq. 586) and its envelope-theorem gradients
+    (uotk_sinkhorn_divergence_grad).
+
+    Returns (sd, parts, grad_a, grad_x, grad_b, grad_y), gradients as FP64
+    device tensors in the caller's order, None where `need` is False."""
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    ctx = ctx or default_context()
+    g = _grad_outputs(x, y, need)
+    sd = _D(0.0)
+    parts = (_D * 3)()
+    o = _opts(method, **nfft)
+    ctx.check(lib().uotk_sinkhorn_divergence_grad(
+        ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0], _ptr(a), _ptr(y), y.shape[0],
+        _ptr(b), float(eps), float(rho), int(max_sweeps), float(tol), ctypes.byref(sd), parts,
+        *[_ptr(t) for t in g], ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
+    return (sd.value, list(parts), *g)
+
+
+class _LossFn(torch.autograd.Function):
+    """Scalar loss with gradients from one library call in forward; backward
+    scales the stored gradients by the incoming grad_output."""
+
+    @staticmethod
+    def forward(ctx_, call, x, a, y, b):
+        nig = ctx_.needs_input_grad  # (call, x, a, y, b)
+        value, *grads = call(x, a, y, b, (nig[2], nig[1], nig[4], nig[3]))
+        ctx_.save_for_backward(*[g if g is not None else torch.empty(0) for g in grads])
+        ctx_.has = [g is not None for g in grads]
+        ctx_.dtypes = (a.dtype, x.dtype, b.dtype, y.dtype)
+        ctx_.shapes = (a.shape, x.shape, b.shape, y.shape)
+        return torch.tensor(value, dtype=torch.float64, device=x.device)
+
+    @staticmethod
+    def backward(ctx_, gout):
+        out = []
+        for g, has, dt, sh in zip(ctx_.saved_tensors, ctx_.has, ctx_.dtypes, ctx_.shapes):
+            out.append((gout * g).to(dt).reshape(sh) if has else None)
+        ga, gx, gb, gy = out
+        return None, gx, ga, gy, gb
+
+
+def mmd2_loss(x, a, y, b, ell, method="direct", ctx=None, **nfft):
+    """MMD^2 as a differentiable scalar (FP64 0-dim tensor) in x, a, y, b."""
+    def call(x_, a_, y_, b_, need):
+        return mmd2_grad(x_.detach(), a_.detach(), y_.detach(), b_.detach(), ell, method,
+                         need, ctx, **nfft)
+    return _LossFn.apply(call, x, a, y, b)
+
+
+def sinkhorn_divergence_loss(x, a, y, b, eps, rho, max_sweeps=100, tol=0.0, method="direct",
+                             ctx=None, **nfft):
+    """Sinkhorn divergence as a differentiable scalar (FP64 0-dim tensor); the
+    gradient is the envelope-theorem gradient at the final duals."""
+    def call(x_, a_, y_, b_, need):
+        sd, _, *g = sinkhorn_divergence_grad(x_.detach(), a_.detach(), y_.detach(),
+                                             b_.detach(), eps, rho, max_sweeps, tol, method,
+                                             need, ctx, **nfft)
+        return (sd, *g)
+    return _LossFn.apply(call, x, a, y, b)
+
+
 def nfft_plan(src, tgt, eps, ctx=None, **nfft):
     src, tgt = _pts(src, "src"), _pts(tgt, "tgt")
     ctx = ctx or default_context()
@@ -325,5 +423,6 @@ def nfft_gather(plan, grid, pts, ctx=None):
 EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_string",
             "uotk_launch_count", "uotk_set_profiling", "uotk_profile_read", "uotk_profile_reset",
             "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
-            "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_nfft_plan", "uotk_nfft_cells",
+            "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
+            "uotk_sinkhorn_divergence_grad", "uotk_nfft_plan", "uotk_nfft_cells",
             "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]
