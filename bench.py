@@ -242,6 +242,57 @@ def reference_arm(args, W, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def gradient_extras(uotk, ctx, stream, W, x, a, y, b, method):
+    """Gradient throughput on the same clouds: MMD^2 and Sinkhorn divergence with
+    all four gradients, against their value-only calls; sampled rows of the MMD^2
+    point gradient checked against the FP64 oracle."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2306_13618_gb300 import inputs
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            out = fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / reps, out
+
+    res = {"method": method}
+    reps = 3 if method == "nfft" else 1
+    try:
+        t_val, _ = timed(lambda: uotk.mmd2(x, a, y, b, W.ell, method=method, ctx=ctx), reps)
+        t_grad, g = timed(lambda: uotk.mmd2_grad(x, a, y, b, W.ell, method=method, ctx=ctx),
+                          reps)
+        rows = inputs.subsample_rows(inputs.rng(12), 16, W.n)
+        rw, rp = oracle.mmd2_grad_rows(W.x.astype(np.float64), W.a.astype(np.float64),
+                                       W.y.astype(np.float64), W.b.astype(np.float64), W.ell,
+                                       0, rows)
+        gx = g[2].cpu().numpy()[rows]
+        res["mmd2"] = {"ms_value": t_val, "ms_value_and_grads": t_grad,
+                       "grad_points_per_s": (W.n + W.m) / (t_grad / 1e3),
+                       "grad_x_sampled_err_rel_max": float(np.max(np.abs(gx - rp)) /
+                                                           np.max(np.abs(rp)))}
+        sweeps = W.sweeps
+        t_val, _ = timed(lambda: uotk.sinkhorn_divergence(x, a, y, b, W.eps, W.rho,
+                                                          max_sweeps=sweeps, method=method,
+                                                          ctx=ctx))
+        t_grad, _ = timed(lambda: uotk.sinkhorn_divergence_grad(x, a, y, b, W.eps, W.rho,
+                                                                max_sweeps=sweeps,
+                                                                method=method, ctx=ctx))
+        res["sinkhorn_divergence"] = {"sweeps": sweeps, "ms_value": t_val,
+                                      "ms_value_and_grads": t_grad,
+                                      "grad_points_per_s": (W.n + W.m) / (t_grad / 1e3)}
+    except uotk.UotkError as e:
+        res["error"] = str(e)
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -374,6 +425,7 @@ def main():
                                 "err_vs_sum_w": float(np.max(np.abs(o - ref)) / scale)}
             except uotk.UotkError as e:
                 extras[meth] = {"error": str(e)}
+        extras["gradients"] = gradient_extras(uotk, ctx, stream, W, x, a, y, b, args.method)
     if "nfft" in extras and "direct" in extras and "ms_per_matvec" in extras.get("direct", {}) \
             and "ms_per_matvec" in extras.get("nfft", {}):
         extras["nfft_speedup_vs_direct"] = extras["direct"]["ms_per_matvec"] / extras["nfft"]["ms_per_matvec"]

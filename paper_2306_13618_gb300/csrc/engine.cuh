@@ -17,8 +17,9 @@ struct Engine {
   // All arrays are in internal order.
   virtual uotk_status half(cudaStream_t s, int side, const float* base, const double* pot,
                            double lam, const long long* shift_slot, float* out) = 0;
-  // Plain kernel sum with given internal-order weights w >= 0 of the source side
-  // (w = weights(src) for the caller's weights): t = K(src -> tgt) w.
+  // Plain kernel sum with given internal-order weights w of the source side
+  // (w = weights(src) for the caller's weights; any sign, n + 4 entries with
+  // the last 4 zero): t = K(src -> tgt) w.
   // src/tgt: 0 = X, 1 = Y.
   virtual uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) = 0;
   // Internal position -> caller index of `side` (NULL: identity).

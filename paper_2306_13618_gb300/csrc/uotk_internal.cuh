@@ -57,8 +57,6 @@ enum FlagSlot {
   FLAG_DELTA1 = 9,
   FLAG_NONFINITE_DUAL = 10,  // count of non-finite dual values produced
   FLAG_BBOX = 16,          // 6 slots: max x,y,z and max of -x,-y,-z (ordered encodings)
-  FLAG_GRAD_SX = 22,       // shifts of the weights used by the gradient sums (ordered)
-  FLAG_GRAD_SY = 23,
   NUM_FLAGS = 32
 };
 

@@ -16,7 +16,10 @@ with the size of the cancelling terms, not with the result:
     half-step, so lambda*|beta - beta*| <= delta (1 + eta*lambda); the bound
     adds that to the sums' delta.
 Each test computes the scale of the cancelling terms from oracle quantities
-and checks |g - g*| <= tol * scale elementwise."""
+and checks |g - g*| <= tol * scale elementwise.  These bounds are worst
+cases (measured errors sit at 1-7% of them for the direct sums and far lower
+for the duals), so every test also holds the normwise relative error
+||g - g*|| / ||g*|| to a bar about ten times the measured value (NORM_*)."""
 import numpy as np
 import pytest
 
@@ -28,6 +31,12 @@ pytestmark = pytest.mark.gpu
 
 DELTA = 2e-6
 E_NFFT = 1e-5
+NORM_DIRECT = 1e-5     # measured <= 1.3e-6 (MMD^2), 3e-7 (divergence)
+NORM_NFFT = 5e-5       # measured <= 1.5e-6 (MMD^2), 4.7e-6 (divergence)
+
+
+def normwise(got, ref):
+    return np.linalg.norm(host(got) - ref) / np.linalg.norm(ref)
 
 
 @pytest.fixture(scope="module")
@@ -95,10 +104,11 @@ def test_mmd2_grad_direct(uotk, d, n, m):
     for got, ref, s, name in zip((ga, gx, gb, gy), (ra, rx, rb, ry), sc, "axby"):
         err = np.abs(host(got) - ref)
         assert np.all(err <= 2 * s), (name, np.max(err / s))
+        assert normwise(got, ref) <= NORM_DIRECT, (name, normwise(got, ref))
 
 
 def test_mmd2_grad_nfft(uotk):
-    W = inputs.gmm3(seed=2004, n=3000, m=2500)
+    W = inputs.gmm3(seed=2004, n=4096, m=4096)
     x, a, y, b, ell = W.x, W.a, W.y, W.b, W.ell
     v, ga, gx, gb, gy = uotk.mmd2_grad(dev(x), dev(a), dev(y), dev(b), ell, method="nfft")
     ra, rx, rb, ry = oracle.mmd2_grad(f64(x), f64(a), f64(y), f64(b), ell)
@@ -110,6 +120,7 @@ def test_mmd2_grad_nfft(uotk):
     for got, ref, s, name in zip((ga, gx, gb, gy), (ra, rx, rb, ry), sc, "axby"):
         err = np.abs(host(got) - ref)
         assert np.all(err <= 2 * s), (name, np.max(err / s))
+        assert normwise(got, ref) <= NORM_NFFT, (name, normwise(got, ref))
 
 
 def test_mmd2_grad_large_sampled(uotk):
@@ -175,10 +186,11 @@ def test_sinkhorn_divergence_grad_direct(uotk, d, n, m):
         s = s if s.ndim == np.ndim(ref) else s[:, None]
         err = np.abs(host(got) - ref)
         assert np.all(err <= 2 * tol * s), (name, np.max(err / s) / tol)
+        assert normwise(got, ref) <= NORM_DIRECT, (name, normwise(got, ref))
 
 
 def test_sinkhorn_divergence_grad_nfft(uotk):
-    W = inputs.gmm3(seed=2005, n=1500, m=1200)
+    W = inputs.gmm3(seed=2005, n=4096, m=4096)
     x, a, y, b = W.x, W.a, W.y, W.b
     eps, rho, S = W.eps, W.rho, 30
     sd, parts, ga, gx, gb, gy = uotk.sinkhorn_divergence_grad(dev(x), dev(a), dev(y), dev(b),
@@ -186,12 +198,11 @@ def test_sinkhorn_divergence_grad_nfft(uotk):
                                                              method="nfft")
     rsd, ra, rx, rb, ry = oracle.sinkhorn_divergence_grad(f64(x), f64(a), f64(y), f64(b), eps,
                                                           rho, S)
-    # NFFT sums: absolute error E ||w||_1 relative to the row scale; measured
-    # in the same normwise way as the Sinkhorn NFFT parity test (1e-4).
+    # NFFT sums: absolute error E ||w||_1; the duals carry it as in the
+    # Sinkhorn NFFT parity test, whose normwise bar this follows.
+    assert abs(sd - rsd) <= 1e-4 * sum(abs(p) for p in parts)
     for got, ref, name in zip((ga, gx, gb, gy), (ra, rx, rb, ry), "axby"):
-        g = host(got)
-        rel = np.linalg.norm(g - ref) / np.linalg.norm(ref)
-        assert rel <= 1e-3, (name, rel)
+        assert normwise(got, ref) <= NORM_NFFT, (name, normwise(got, ref))
 
 
 def test_grad_selective_outputs_and_autograd(uotk):
