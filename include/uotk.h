@@ -44,7 +44,24 @@ typedef enum {
   UOTK_ERR_INTERNAL = 8
 } uotk_status;
 
-typedef enum { UOTK_DIRECT = 0, UOTK_NFFT = 1 } uotk_method;
+/* Form of every kernel summation of a call (never switched silently):
+ * DIRECT      : the exact O(nm) sum of Alg. 1 in FP32 (any d <= 128).
+ * NFFT        : the fast summation of Sec. 4 / Alg. 2 (d <= 3).
+ * DIRECT_BF16 : the exact O(nm) sum with the cross term x.y of
+ *               ||x-y||^2 = |x|^2 + |y|^2 - 2 x.y on the tensor cores from
+ *               BF16-rounded centred points (FP32 accumulation, norms and
+ *               exponentials in FP32); about 3 significant digits per term.
+ * DIRECT_BF16X3: the same with each centred coordinate split into BF16 hi + lo
+ *               and x.y = hi.hi + hi.lo + lo.hi (three tensor-core products),
+ *               near FP32 accuracy.
+ * The two tensor-core forms take d <= 128; they pay off for d >~ 16, where the
+ * FP32 form spends d FMAs per pair on the distance. */
+typedef enum {
+  UOTK_DIRECT = 0,
+  UOTK_NFFT = 1,
+  UOTK_DIRECT_BF16 = 2,
+  UOTK_DIRECT_BF16X3 = 3
+} uotk_method;
 
 /* Reference measure of the entropy term.
  * PRODUCT : (1/lambda) D(pi || mu (x) nu), the paper's Eq. (W4); the update is

@@ -129,9 +129,10 @@ uotk_status check_cloud(uotk_ctx* ctx, const char* what, const float* p, int64_t
 uotk_status check_common(uotk_ctx* ctx, int d, const uotk_sum_opts* opts) {
   if (d < 1) return set_error(ctx, UOTK_ERR_INVALID, "dimension d = %d < 1", d);
   const int method = opts ? opts->method : UOTK_DIRECT;
-  if (method != UOTK_DIRECT && method != UOTK_NFFT)
+  if (method != UOTK_DIRECT && method != UOTK_NFFT && method != UOTK_DIRECT_BF16 &&
+      method != UOTK_DIRECT_BF16X3)
     return set_error(ctx, UOTK_ERR_INVALID, "unknown method %d", method);
-  if (method == UOTK_DIRECT && d > 128)
+  if (method != UOTK_NFFT && d > 128)
     return set_error(ctx, UOTK_ERR_UNSUPPORTED, "direct form: d = %d > 128", d);
   if (method == UOTK_NFFT) {
     if (d > 3)

@@ -53,6 +53,11 @@ size_t engine_bytes(uotk_ctx* ctx, const EngineSpec& sp);
 uotk_status engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, Carver& cv,
                           Engine** out);
 
+// Tensor-core direct engine (ksum_tc.cu): methods UOTK_DIRECT_BF16, UOTK_DIRECT_BF16X3.
+size_t tc_engine_bytes(uotk_ctx* ctx, const EngineSpec& sp);
+uotk_status tc_engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, Carver& cv,
+                             Engine** out);
+
 // NFFT engine (nfft.cu).
 size_t nfft_engine_bytes(uotk_ctx* ctx, const EngineSpec& sp);
 uotk_status nfft_engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, Carver& cv,

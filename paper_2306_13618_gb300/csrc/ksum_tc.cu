@@ -1,0 +1,707 @@
+// Direct kernel summation with the cross term on the 5th-generation tensor
+// cores (tcgen05):
+//
+//   out_i = sum_j w_j 2^{-c ||x_i - y_j||^2},   c = log2(e)/eps,
+//   ||x_i - y_j||^2 = |x_i|^2 + |y_j|^2 - 2 x_i . y_j,
+//
+// the exact matrix-vector product of Alg. 1 for high-dimensional clouds.  For
+// d >= ~16 the squared distance, not the exponential, dominates the FP32 form
+// (d FMAs per pair); here S = X Y^T is a dense contraction and runs on
+// tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulators in tensor memory),
+// while the norms, the exponential and the weighted row sums stay in FP32 on
+// the CUDA cores, fused behind the MMA.
+//
+// Precision.  Points are centred on the middle of the joint bounding box and
+// rounded to BF16 as v = hi + lo (both BF16, lo the rounded remainder).
+//   * BF16 form: S = hi_x . hi_y, one product (about 3 significant digits).
+//   * BF16x3 form: S = hi.hi + hi.lo + lo.hi, three products accumulated in
+//     FP32, the cross term to about 2^-17 relative (near FP32).
+// The norms |x|^2, |y|^2 are FP32 from the FP32 centred coordinates.
+//
+// Layout.  Each cloud is packed once into tiles of 128 points; a tile holds,
+// per 64-coordinate chunk, a block of hi and a block of lo values, each block
+// 128 rows x 128 bytes in the 128-byte-swizzled K-major layout the MMA reads
+// (16-byte chunk g of row r stored at chunk g ^ (r mod 8)).  Blocks are
+// 16 KB, contiguous, and move global -> shared with 1-D bulk copies.
+//
+// CTA (384 threads, one per SM, all 512 tensor-memory columns):
+//   warp 0, one lane: producer -- the CTA's 128-target tile once, then source
+//     tiles through a ring of shared-memory stages (mbarrier transaction counts);
+//   warp 1: allocates tensor memory; one lane issues the MMAs of each source
+//     tile into one of 4 accumulator stages of 128 columns, and commits them to
+//     the stage's barriers;
+//   warps 4-11: two epilogue warpgroups taking alternate source tiles; thread
+//     (warp, lane) owns target row 32 (warp mod 4) + lane, reads its 128
+//     accumulator columns with tcgen05.ld, and adds w_j 2^{2c S + b_j + a_i}
+//     (b_j = -c |y_j|^2, a_i = -c |x_i|^2) into a compensated FP32 pair.
+// Every wait is bounded; a timeout raises the context's TIMEOUT flag, and the
+// CTA drains its copies and MMAs before it frees tensor memory and exits.
+#include <cuda_bf16.h>
+#include <math.h>
+
+#include <memory>
+
+#include "engine.cuh"
+
+namespace uotk {
+
+namespace {
+
+constexpr int TC_ROWS = 128;                 // targets per CTA (MMA M) = sources per tile (MMA N)
+constexpr int TC_BLOCK = TC_ROWS * 128;      // bytes of one 128 x 64 BF16 block
+constexpr int TC_ACC = 4;                    // accumulator stages (4 x 128 columns)
+constexpr int TC_THREADS = 384;
+constexpr int TC_MISC = 2048;                // barriers, flags, hand-over buffer
+constexpr int TC_MIN_SMEM = 120 * 1024;      // forces one CTA per SM
+
+__host__ __device__ constexpr int tc_ka(bool split, int dc) { return split ? 2 * dc : dc; }
+__host__ __device__ constexpr int tc_stages(bool split, int dc) {
+  return (200 * 1024 - tc_ka(split, dc) * TC_BLOCK) / (tc_ka(split, dc) * TC_BLOCK) > 4
+             ? 4
+             : (200 * 1024 - tc_ka(split, dc) * TC_BLOCK) / (tc_ka(split, dc) * TC_BLOCK);
+}
+__host__ __device__ constexpr size_t tc_smem_bytes(bool split, int dc) {
+  return (size_t)tc_ka(split, dc) * TC_BLOCK * (1 + tc_stages(split, dc)) + TC_MISC + 1024;
+}
+
+// ---- tcgen05 helpers (inline PTX) ----
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), start address advanced within the
+// swizzle atom for each K step of 16 elements.
+__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr) {
+  unsigned long long d = (unsigned long long)((saddr & 0x3FFFFu) >> 4);
+  d |= 1ull << 16;                 // leading byte offset (unused for swizzled K-major)
+  d |= (1024ull >> 4) << 32;       // stride byte offset
+  d |= 1ull << 46;                 // descriptor version
+  d |= 2ull << 61;                 // 128-byte swizzle
+  return d;
+}
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = N = 128.
+__host__ __device__ constexpr unsigned tc_idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_ROWS >> 3) << 17) |
+         ((unsigned)(TC_ROWS >> 4) << 24);
+}
+__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long ad,
+                                       unsigned long long bd, unsigned acc) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(ad), "l"(bd), "r"(tc_idesc()), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// tcgen05.ld is asynchronous: its registers are valid only after
+// tcgen05.wait::ld.  tc_wait16 names them as in/out operands, so no use of them
+// can be scheduled before the wait.
+__device__ __forceinline__ void tc_ld16(unsigned taddr, unsigned (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
+      "%11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+}
+__device__ __forceinline__ void tc_wait16(unsigned (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tc_neumaier(float& hi, float& lo, float v) {
+  const float t = hi + v;
+  lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
+  hi = t;
+}
+
+// Weighted exponential sum of 16 accumulator columns of one row.
+__device__ __forceinline__ float tc_chunk(const unsigned (&v)[16], const float4* __restrict__ bw,
+                                          float two_c, float aa) {
+  float s0 = 0.f, s1 = 0.f;
+#pragma unroll
+  for (int j = 0; j < 16; j += 2) {
+    const float4 q = __ldg(bw + (j >> 1));  // {b_j, w_j, b_j+1, w_j+1}, same for the whole warp
+    s0 = fmaf(q.y, ex2_approx(fmaf(__uint_as_float(v[j]), two_c, q.x) + aa), s0);
+    s1 = fmaf(q.w, ex2_approx(fmaf(__uint_as_float(v[j + 1]), two_c, q.z) + aa), s1);
+  }
+  return s0 + s1;
+}
+
+// One CTA: 128 targets (blockIdx.x) against the source tiles of split
+// blockIdx.y.  tiles: [tile][2*DC blocks][16 KB], block 2c = hi, 2c+1 = lo of
+// coordinate chunk c.  bw: per source {-c |y|^2, w}, zero past the last source.
+// out: [splits][m] (split partial sums) or [m].
+template <bool SPLIT, int DC>
+__global__ void __launch_bounds__(TC_THREADS, 1)
+    k_direct_tc(const unsigned char* __restrict__ src_tiles, const float2* __restrict__ src_bw,
+                long long src_tiles_total, int tiles_per_split,
+                const unsigned char* __restrict__ tgt_tiles, const float* __restrict__ tgt_n2,
+                long long m, float two_c, float neg_c, float* __restrict__ out,
+                long long* __restrict__ flags) {
+  constexpr int KBT = 2 * DC;               // blocks per tile in global memory
+  constexpr int KA = tc_ka(SPLIT, DC);      // blocks per tile in shared memory
+  constexpr int S = tc_stages(SPLIT, DC);   // source-tile stages
+  constexpr unsigned STAGE_BYTES = (unsigned)KA * TC_BLOCK;
+  static_assert(S >= 2, "at least two source stages");
+
+  extern __shared__ unsigned char tc_raw[];
+  const unsigned raw = smem_addr(tc_raw);
+  unsigned char* sA = tc_raw + ((1024u - (raw & 1023u)) & 1023u);
+  unsigned char* sB = sA + STAGE_BYTES;
+  unsigned char* misc = sB + (size_t)S * STAGE_BYTES;
+  unsigned long long* a_full = reinterpret_cast<unsigned long long*>(misc);
+  unsigned long long* b_full = a_full + 1;
+  unsigned long long* b_empty = b_full + S;
+  unsigned long long* t_full = b_empty + S;
+  unsigned long long* t_empty = t_full + TC_ACC;
+  unsigned long long* done = t_empty + TC_ACC;
+  unsigned* tmem_slot = reinterpret_cast<unsigned*>(misc + 256);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 260);
+  float* hand = reinterpret_cast<float*>(misc + 512);  // [2][128] partial sums of warpgroup 1
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long t_begin = (long long)blockIdx.y * tiles_per_split;
+  const long long t_end = min(t_begin + (long long)tiles_per_split, src_tiles_total);
+  const int count = t_end > t_begin ? (int)(t_end - t_begin) : 0;
+
+  if (threadIdx.x == 0) {
+    mbar_init(a_full, 1);
+    for (int s = 0; s < S; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
+    for (int a = 0; a < TC_ACC; ++a) { mbar_init(&t_full[a], 1); mbar_init(&t_empty[a], 128); }
+    mbar_init(done, 1);
+    *abort_flag = 0;
+    mbar_fence_init();
+  }
+  if (warp == 1) {
+    __syncwarp();
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
+                     smem_addr(tmem_slot))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const unsigned tmem = *tmem_slot;
+  float hi = 0.f, lo = 0.f;  // epilogue: compensated row sum
+
+  if (warp == 0 && lane == 0) {
+    // ---- producer ----
+    int fills[S];
+#pragma unroll
+    for (int s = 0; s < S; ++s) fills[s] = 0;
+    mbar_expect(a_full, STAGE_BYTES);
+    for (int b = 0; b < KA; ++b) {
+      const int kb = SPLIT ? b : 2 * b;
+      bulk_copy(sA + (size_t)b * TC_BLOCK,
+                tgt_tiles + ((size_t)blockIdx.x * KBT + kb) * TC_BLOCK, TC_BLOCK, a_full);
+    }
+    for (int k = 0; k < count; ++k) {
+      const int s = k % S, u = k / S;
+      if (u > 0 && !mbar_wait(&b_empty[s], (unsigned)(u - 1) & 1u)) {
+        *abort_flag = 1;
+        flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        break;
+      }
+      if (*abort_flag) break;
+      mbar_expect(&b_full[s], STAGE_BYTES);
+      const size_t tile = (size_t)(t_begin + k);
+      for (int b = 0; b < KA; ++b) {
+        const int kb = SPLIT ? b : 2 * b;
+        bulk_copy(sB + (size_t)s * STAGE_BYTES + (size_t)b * TC_BLOCK,
+                  src_tiles + (tile * KBT + kb) * TC_BLOCK, TC_BLOCK, &b_full[s]);
+      }
+      fills[s]++;
+    }
+    // Drain: every copy this thread started has landed before the CTA exits.
+    mbar_wait(a_full, 0u);
+#pragma unroll
+    for (int s = 0; s < S; ++s)
+      if (fills[s]) mbar_wait(&b_full[s], (unsigned)(fills[s] - 1) & 1u);
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    int issued = 0;
+    bool ok = mbar_wait(a_full, 0u);
+    if (!ok) { *abort_flag = 1; flag_add(&flags[FLAG_TIMEOUT], 1LL); }
+    const unsigned a0 = smem_addr(sA);
+    for (int k = 0; ok && k < count; ++k) {
+      const int s = k % S, a = k % TC_ACC;
+      const int us = k / S, ua = k / TC_ACC;
+      if (!mbar_wait(&b_full[s], (unsigned)us & 1u) ||
+          (ua > 0 && !mbar_wait(&t_empty[a], (unsigned)(ua - 1) & 1u))) {
+        *abort_flag = 1;
+        flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        break;
+      }
+      if (*abort_flag) break;
+      tc_fence_after();
+      const unsigned d_tmem = tmem + (unsigned)(a * TC_ROWS);
+      const unsigned b0 = smem_addr(sB + (size_t)s * STAGE_BYTES);
+      unsigned q = 0;
+#pragma unroll
+      for (int c = 0; c < DC; ++c) {
+#pragma unroll
+        for (int p = 0; p < (SPLIT ? 3 : 1); ++p) {
+          // products hi.hi, hi.lo, lo.hi (blocks 2c = hi, 2c + 1 = lo)
+          const int ba = SPLIT ? 2 * c + (p == 2 ? 1 : 0) : c;
+          const int bb = SPLIT ? 2 * c + (p == 1 ? 1 : 0) : c;
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks, ++q)
+            tc_mma(d_tmem, tc_desc(a0 + (unsigned)(ba * TC_BLOCK + ks * 32)),
+                   tc_desc(b0 + (unsigned)(bb * TC_BLOCK + ks * 32)), q > 0 ? 1u : 0u);
+        }
+      }
+      tc_commit(&b_empty[s]);
+      tc_commit(&t_full[a]);
+      issued++;
+    }
+    // Drain: no MMA may still be running when tensor memory is freed.
+    if (issued) {
+      tc_commit(done);
+      mbar_wait(done, 0u);
+    }
+  } else if (warp >= 4) {
+    // ---- epilogue ----
+    const int g = (warp - 4) >> 2;  // warpgroup: source tiles k = g, g + 2, ...
+    const int quad = warp & 3;      // tensor-memory lanes 32 quad .. 32 quad + 31
+    const int row = quad * 32 + lane;
+    const long long i = (long long)blockIdx.x * TC_ROWS + row;
+    const float aa = i < m ? neg_c * tgt_n2[i] : 0.f;
+    for (int k = g; k < count; k += 2) {
+      const int a = k % TC_ACC, ua = k / TC_ACC;
+      bool ok = mbar_wait(&t_full[a], (unsigned)ua & 1u);
+      ok = __all_sync(0xffffffffu, ok) && !__any_sync(0xffffffffu, *abort_flag != 0);
+      if (!ok) {
+        if (lane == 0) {
+          *abort_flag = 1;
+          flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        }
+        break;
+      }
+      tc_fence_after();
+      const float4* bw = reinterpret_cast<const float4*>(src_bw + (t_begin + k) * TC_ROWS);
+      const unsigned tb = tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(a * TC_ROWS);
+      // columns in chunks of 16, the load of the next chunk in flight while
+      // the current one is summed
+      unsigned v0[16], v1[16];
+      tc_ld16(tb, v0);
+      tc_wait16(v0);
+#pragma unroll
+      for (int c0 = 0; c0 < TC_ROWS; c0 += 32) {
+        tc_ld16(tb + (unsigned)(c0 + 16), v1);
+        tc_neumaier(hi, lo, tc_chunk(v0, bw + (c0 >> 1), two_c, aa));
+        tc_wait16(v1);
+        if (c0 + 32 < TC_ROWS) tc_ld16(tb + (unsigned)(c0 + 32), v0);
+        tc_neumaier(hi, lo, tc_chunk(v1, bw + ((c0 + 16) >> 1), two_c, aa));
+        if (c0 + 32 < TC_ROWS) tc_wait16(v0);
+      }
+      tc_fence_before();
+      mbar_arrive(&t_empty[a]);
+    }
+    if (g == 1) {
+      hand[row] = hi;
+      hand[TC_ROWS + row] = lo;
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp >= 4 && warp < 8) {
+    // warpgroup 0 adds warpgroup 1's pair for the same row and writes the sum
+    const int row = (warp & 3) * 32 + lane;
+    const long long i = (long long)blockIdx.x * TC_ROWS + row;
+    tc_neumaier(hi, lo, hand[row]);
+    tc_neumaier(hi, lo, hand[TC_ROWS + row]);
+    if (i < m) out[(long long)blockIdx.y * m + i] = hi + lo;
+  }
+  if (warp == 1) {
+    __syncwarp();
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+  }
+}
+
+// ---- packing ----
+// Per-dimension maximum of v and of -v over a cloud (ordered encodings in
+// slots[0..d) and slots[d..2d)).  The grid stride is a multiple of d, so each
+// thread stays on one coordinate.
+__global__ void k_tc_minmax(const float* __restrict__ p, long long count, int d,
+                            long long* __restrict__ slots) {
+  __shared__ long long smx[128], smn[128];
+  for (int c = threadIdx.x; c < d; c += blockDim.x) { smx[c] = ORDERED_NEG_INF; smn[c] = ORDERED_NEG_INF; }
+  __syncthreads();
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long first = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (first < count) {
+    double mx = -INFINITY, mn = -INFINITY;
+    for (long long q = first; q < count; q += stride) {
+      const double v = (double)p[q];
+      mx = fmax(mx, v);
+      mn = fmax(mn, -v);
+    }
+    atomicMax(&smx[first % d], dbl_to_ordered(mx));
+    atomicMax(&smn[first % d], dbl_to_ordered(mn));
+  }
+  __syncthreads();
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    if (smx[c] != ORDERED_NEG_INF) atomicMax(&slots[c], smx[c]);
+    if (smn[c] != ORDERED_NEG_INF) atomicMax(&slots[d + c], smn[c]);
+  }
+}
+
+__global__ void k_tc_center(const long long* __restrict__ slots, int d, float* __restrict__ center) {
+  for (int c = threadIdx.x; c < d; c += blockDim.x) {
+    const double hi = ordered_to_dbl(slots[c]), lo = -ordered_to_dbl(slots[d + c]);
+    center[c] = isfinite(hi) && isfinite(lo) ? (float)(0.5 * (hi + lo)) : 0.f;
+  }
+}
+
+__global__ void k_tc_fill_slots(long long* slots, int count) {
+  for (int c = threadIdx.x; c < count; c += blockDim.x) slots[c] = ORDERED_NEG_INF;
+}
+
+// BF16 hi/lo blocks of the centred coordinates: one thread per (point, 8
+// coordinates).  Points i >= n are zero rows.
+__global__ void k_tc_pack(const float* __restrict__ pts, long long n, long long n_pad, int d,
+                          int dc, const float* __restrict__ center,
+                          unsigned char* __restrict__ tiles) {
+  const long long units = n_pad * 8 * dc;
+  for (long long u = blockIdx.x * (long long)blockDim.x + threadIdx.x; u < units;
+       u += (long long)gridDim.x * blockDim.x) {
+    const long long i = u / (8 * dc);
+    const int q = (int)(u % (8 * dc));
+    const int c = q >> 3, g = q & 7;
+    unsigned hw[4], lw[4];
+#pragma unroll
+    for (int e = 0; e < 8; e += 2) {
+      float v[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int t = 64 * c + 8 * g + e + h;
+        v[h] = (i < n && t < d) ? __fsub_rn(pts[i * d + t], center[t]) : 0.f;
+      }
+      const __nv_bfloat16 h0 = __float2bfloat16_rn(v[0]), h1 = __float2bfloat16_rn(v[1]);
+      const __nv_bfloat16 l0 = __float2bfloat16_rn(__fsub_rn(v[0], __bfloat162float(h0)));
+      const __nv_bfloat16 l1 = __float2bfloat16_rn(__fsub_rn(v[1], __bfloat162float(h1)));
+      hw[e >> 1] = (unsigned)__bfloat16_as_ushort(h0) | ((unsigned)__bfloat16_as_ushort(h1) << 16);
+      lw[e >> 1] = (unsigned)__bfloat16_as_ushort(l0) | ((unsigned)__bfloat16_as_ushort(l1) << 16);
+    }
+    const long long tile = i / TC_ROWS;
+    const int r = (int)(i % TC_ROWS);
+    const size_t off = (size_t)(r >> 3) * 1024 + (size_t)(r & 7) * 128 + (size_t)((g ^ (r & 7)) * 16);
+    unsigned char* hb = tiles + ((size_t)tile * 2 * dc + 2 * c) * TC_BLOCK + off;
+    *reinterpret_cast<uint4*>(hb) = make_uint4(hw[0], hw[1], hw[2], hw[3]);
+    *reinterpret_cast<uint4*>(hb + TC_BLOCK) = make_uint4(lw[0], lw[1], lw[2], lw[3]);
+  }
+}
+
+// Squared norms of the centred FP32 points (0 past n), the per-source pairs
+// {-c |p|^2, w} (w = 0 past n), and validation counters of the weights.
+__global__ void k_tc_norms(const float* __restrict__ pts, const float* __restrict__ w, long long n,
+                           long long n_pad, int d, const float* __restrict__ center, float neg_c,
+                           float* __restrict__ n2, float2* __restrict__ bw,
+                           long long* __restrict__ flags) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long iters = (n_pad + stride - 1) / stride;
+  for (long long it = 0; it < iters; ++it) {
+    const long long i = start + it * stride;
+    bool neg = false, bad = false;
+    if (i < n_pad) {
+      double s = 0.0;
+      float wi = 0.f;
+      if (i < n) {
+        for (int t = 0; t < d; ++t) {
+          const float v = __fsub_rn(pts[i * d + t], center[t]);
+          bad |= !isfinite(pts[i * d + t]);
+          s = fma((double)v, (double)v, s);
+        }
+        if (w) {
+          wi = w[i];
+          neg = wi < 0.f;
+          bad |= !isfinite(wi);
+        }
+      }
+      n2[i] = (float)s;
+      bw[i] = make_float2(neg_c * (float)s, wi);
+    }
+    const unsigned bn = __ballot_sync(0xffffffffu, neg);
+    const unsigned bf = __ballot_sync(0xffffffffu, bad);
+    if ((threadIdx.x & 31) == 0) {
+      if (bn) flag_add(&flags[FLAG_NEG_WEIGHT], (long long)__popc(bn));
+      if (bf) flag_add(&flags[FLAG_NONFINITE], (long long)__popc(bf));
+    }
+  }
+}
+
+// w_j = base_j * exp(lam*pot_j - shift) (pot NULL: base_j; base NULL: 1).
+__global__ void k_tc_set_weights(float2* __restrict__ bw, long long n, const float* __restrict__ base,
+                                 const double* __restrict__ pot, double lam,
+                                 const long long* __restrict__ shift_slot) {
+  const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    float v = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
+    if (base) v *= base[i];
+    bw[i].y = v;
+  }
+}
+
+__global__ void k_tc_reduce(const float* __restrict__ part, int splits, long long m,
+                            float* __restrict__ out) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < m;
+       j += (long long)gridDim.x * blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < splits; ++k) s += (double)part[(long long)k * m + j];
+    out[j] = (float)s;
+  }
+}
+
+// A packed cloud: tiles, squared norms, source pairs.
+struct TcCloud {
+  int64_t n = 0, tiles = 0;
+  unsigned char* tile_data = nullptr;  // [tiles][2 dc][16 KB]
+  float* n2 = nullptr;                 // [tiles * 128]
+  float2* bw = nullptr;                // [tiles * 128]
+};
+
+int64_t tc_tiles(int64_t n) { return (n + TC_ROWS - 1) / TC_ROWS; }
+
+void tc_carve_cloud(Carver& cv, int dc, int64_t n, TcCloud& C) {
+  C.n = n;
+  C.tiles = tc_tiles(n);
+  const int64_t t = C.tiles > 0 ? C.tiles : 1;
+  C.tile_data = cv.take<unsigned char>((size_t)t * 2 * dc * TC_BLOCK);
+  C.n2 = cv.take<float>((size_t)t * TC_ROWS);
+  C.bw = cv.take<float2>((size_t)t * TC_ROWS);
+}
+
+// Source splits for a (sources -> targets) pair: enough CTAs for about two
+// per SM when the targets alone give fewer.
+struct TcSplit {
+  int splits = 1;
+  int tiles_per_split = 0;
+};
+TcSplit tc_split(const uotk_ctx* ctx, int64_t src_tiles, int64_t tgt_tiles) {
+  TcSplit L;
+  if (src_tiles == 0 || tgt_tiles == 0) return L;
+  int64_t want = (2 * (int64_t)ctx->num_sms + tgt_tiles - 1) / tgt_tiles;
+  want = want < 1 ? 1 : (want > src_tiles ? src_tiles : want);
+  want = want > 64 ? 64 : want;
+  L.tiles_per_split = (int)((src_tiles + want - 1) / want);
+  L.splits = (int)((src_tiles + L.tiles_per_split - 1) / L.tiles_per_split);
+  return L;
+}
+
+template <bool SPLIT, int DC>
+uotk_status tc_launch(uotk_ctx* ctx, cudaStream_t s, const TcCloud& src, const TcCloud& tgt,
+                      const TcSplit& L, double eps, float* dst) {
+  constexpr size_t smem0 = tc_smem_bytes(SPLIT, DC);
+  constexpr size_t smem = smem0 > (size_t)TC_MIN_SMEM ? smem0 : (size_t)TC_MIN_SMEM;
+  UOTK_CUDA(ctx, smem_attr(s, k_direct_tc<SPLIT, DC>, smem));
+  const double c = 1.4426950408889634 / eps;
+  const dim3 grid((unsigned)tgt.tiles, (unsigned)L.splits);
+  k_direct_tc<SPLIT, DC><<<grid, TC_THREADS, smem, s>>>(
+      src.tile_data, src.bw, src.tiles, L.tiles_per_split, tgt.tile_data, tgt.n2, tgt.n,
+      (float)(2.0 * c), (float)(-c), dst, ctx->dflags);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+// out[i] = sum_j w_j exp(-||tgt_i - src_j||^2/eps), w in src.bw.
+uotk_status tc_run(uotk_ctx* ctx, cudaStream_t s, bool split, int dc, const TcCloud& src,
+                   const TcCloud& tgt, double eps, float* part, float* out) {
+  if (tgt.n == 0) return UOTK_OK;
+  if (src.n == 0) {
+    UOTK_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(float) * tgt.n, s));
+    return UOTK_OK;
+  }
+  const TcSplit L = tc_split(ctx, src.tiles, tgt.tiles);
+  float* dst = L.splits > 1 ? part : out;
+  {
+    UOTK_PROF(ctx, s, "direct_tc");
+    uotk_status st;
+    if (split)
+      st = dc == 1 ? tc_launch<true, 1>(ctx, s, src, tgt, L, eps, dst)
+                   : tc_launch<true, 2>(ctx, s, src, tgt, L, eps, dst);
+    else
+      st = dc == 1 ? tc_launch<false, 1>(ctx, s, src, tgt, L, eps, dst)
+                   : tc_launch<false, 2>(ctx, s, src, tgt, L, eps, dst);
+    UOTK_TRY(st);
+  }
+  if (L.splits > 1) {
+    UOTK_PROF(ctx, s, "split_reduce");
+    k_tc_reduce<<<grid_for(ctx, tgt.n, 256), 256, 0, s>>>(part, L.splits, tgt.n, out);
+    UOTK_LAUNCHED(ctx);
+  }
+  return UOTK_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Engine: both clouds packed once; every half-step rewrites the source weights
+// and runs the tensor-core summation.
+// ---------------------------------------------------------------------------
+struct TcEngine : Engine {
+  uotk_ctx* ctx = nullptr;
+  int d = 0, dc = 1;
+  bool split = true;
+  int64_t n = 0, m = 0;
+  const float* a = nullptr;
+  const float* b = nullptr;
+  double eps = 1.0;
+  TcCloud X, Y;
+  float* part = nullptr;
+  float* center = nullptr;
+  long long* slots = nullptr;
+
+  static void carve(const uotk_ctx* ctx, const EngineSpec& sp, Carver& cv, TcEngine* e) {
+    const int dc = (sp.d + 63) / 64;
+    TcCloud X, Y;
+    tc_carve_cloud(cv, dc, sp.n, X);
+    tc_carve_cloud(cv, dc, sp.m, Y);
+    size_t part = 1;
+    const int64_t pairs[4][2] = {{Y.tiles, X.tiles}, {X.tiles, Y.tiles}, {X.tiles, X.tiles},
+                                 {Y.tiles, Y.tiles}};
+    const int64_t tgt_n[4] = {sp.n, sp.m, sp.n, sp.m};
+    for (int k = 0; k < 4; ++k) {
+      const TcSplit L = tc_split(ctx, pairs[k][0], pairs[k][1]);
+      if (L.splits > 1) {
+        const size_t need = (size_t)L.splits * (size_t)tgt_n[k];
+        part = need > part ? need : part;
+      }
+    }
+    float* pp = cv.take<float>(part);
+    float* ctr = cv.take<float>(128);
+    long long* sl = cv.take<long long>(256);
+    if (e) {
+      e->dc = dc;
+      e->X = X;
+      e->Y = Y;
+      e->part = pp;
+      e->center = ctr;
+      e->slots = sl;
+    }
+  }
+
+  uotk_status set_weights(cudaStream_t s, TcCloud& C, const float* base, const double* pot,
+                          double lam, const long long* shift_slot) {
+    if (C.n == 0) return UOTK_OK;
+    UOTK_PROF(ctx, s, "weights");
+    k_tc_set_weights<<<grid_for(ctx, C.n, 256, 4), 256, 0, s>>>(C.bw, C.n, base, pot, lam,
+                                                                 shift_slot);
+    UOTK_LAUNCHED(ctx);
+    return UOTK_OK;
+  }
+
+  uotk_status half(cudaStream_t s, int side, const float* base, const double* pot, double lam,
+                   const long long* shift_slot, float* out) override {
+    TcCloud& src = side == 0 ? Y : X;
+    const TcCloud& tgt = side == 0 ? X : Y;
+    UOTK_TRY(set_weights(s, src, base, pot, lam, shift_slot));
+    return tc_run(ctx, s, split, dc, src, tgt, eps, part, out);
+  }
+  uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
+    TcCloud& S = src == 0 ? X : Y;
+    UOTK_TRY(set_weights(s, S, w, nullptr, 0.0, nullptr));
+    return tc_run(ctx, s, split, dc, S, tgt == 0 ? X : Y, eps, part, out);
+  }
+  const int* perm(int) const override { return nullptr; }
+  const float* weights(int side) const override { return side == 0 ? a : b; }
+  uotk_status to_caller(cudaStream_t s, int side, const double* in, double* out) override {
+    if (in != out)
+      UOTK_CUDA(ctx, cudaMemcpyAsync(out, in, sizeof(double) * (side == 0 ? n : m),
+                                     cudaMemcpyDeviceToDevice, s));
+    return UOTK_OK;
+  }
+  uotk_status to_caller_f32(cudaStream_t s, int side, const float* in, float* out) override {
+    if (in != out)
+      UOTK_CUDA(ctx, cudaMemcpyAsync(out, in, sizeof(float) * (side == 0 ? n : m),
+                                     cudaMemcpyDeviceToDevice, s));
+    return UOTK_OK;
+  }
+  uotk_status from_caller(cudaStream_t s, int side, const double* in, double* out) override {
+    return to_caller(s, side, in, out);
+  }
+  bool identity_order() const override { return true; }
+};
+
+int gcd_int(int a, int b) { return b == 0 ? a : gcd_int(b, a % b); }
+
+uotk_status tc_minmax(uotk_ctx* ctx, cudaStream_t s, const float* p, int64_t n, int d,
+                      long long* slots) {
+  if (n == 0) return UOTK_OK;
+  const long long count = (long long)n * d;
+  const int step = d / gcd_int(d, 256);  // blocks per multiple of d threads
+  int blocks = grid_for(ctx, count, 256, 2);
+  blocks = ((blocks + step - 1) / step) * step;
+  k_tc_minmax<<<blocks, 256, 0, s>>>(p, count, d, slots);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+uotk_status tc_pack(uotk_ctx* ctx, cudaStream_t s, const float* pts, const float* w, int d,
+                    int dc, const float* center, double eps, TcCloud& C) {
+  if (C.tiles == 0) return UOTK_OK;
+  const long long n_pad = C.tiles * TC_ROWS;
+  k_tc_pack<<<grid_for(ctx, n_pad * 8 * dc, 256, 4), 256, 0, s>>>(pts, C.n, n_pad, d, dc, center,
+                                                                   C.tile_data);
+  UOTK_LAUNCHED(ctx);
+  k_tc_norms<<<grid_for(ctx, n_pad, 256, 4), 256, 0, s>>>(
+      pts, w, C.n, n_pad, d, center, (float)(-1.4426950408889634 / eps), C.n2, C.bw, ctx->dflags);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
+}
+
+}  // namespace
+
+size_t tc_engine_bytes(uotk_ctx* ctx, const EngineSpec& sp) {
+  Carver cv(nullptr);
+  TcEngine::carve(ctx, sp, cv, nullptr);
+  return cv.off;
+}
+
+uotk_status tc_engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, Carver& cv,
+                             Engine** out) {
+  std::unique_ptr<TcEngine> e(new TcEngine());
+  e->ctx = ctx;
+  e->d = sp.d;
+  e->n = sp.n;
+  e->m = sp.m;
+  e->a = sp.a;
+  e->b = sp.b;
+  e->eps = sp.eps;
+  e->split = sp.method == UOTK_DIRECT_BF16X3;
+  TcEngine::carve(ctx, sp, cv, e.get());
+  {
+    UOTK_PROF(ctx, s, "pack");
+    k_tc_fill_slots<<<1, 256, 0, s>>>(e->slots, 2 * sp.d);
+    UOTK_LAUNCHED(ctx);
+    UOTK_TRY(tc_minmax(ctx, s, sp.x, sp.n, sp.d, e->slots));
+    UOTK_TRY(tc_minmax(ctx, s, sp.y, sp.m, sp.d, e->slots));
+    k_tc_center<<<1, 128, 0, s>>>(e->slots, sp.d, e->center);
+    UOTK_LAUNCHED(ctx);
+    UOTK_TRY(tc_pack(ctx, s, sp.x, sp.a, sp.d, e->dc, e->center, sp.eps, e->X));
+    UOTK_TRY(tc_pack(ctx, s, sp.y, sp.b, sp.d, e->dc, e->center, sp.eps, e->Y));
+  }
+  *out = e.release();
+  return UOTK_OK;
+}
+
+}  // namespace uotk

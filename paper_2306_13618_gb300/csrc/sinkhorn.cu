@@ -372,6 +372,8 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
 // ---------------------------------------------------------------------------
 size_t engine_bytes(uotk_ctx* ctx, const EngineSpec& sp) {
   if (sp.method == UOTK_NFFT) return nfft_engine_bytes(ctx, sp);
+  if (sp.method == UOTK_DIRECT_BF16 || sp.method == UOTK_DIRECT_BF16X3)
+    return tc_engine_bytes(ctx, sp);
   Carver cv(nullptr);
   DirectEngine::carve(ctx, sp, cv, nullptr);
   return cv.off;
@@ -380,6 +382,8 @@ size_t engine_bytes(uotk_ctx* ctx, const EngineSpec& sp) {
 uotk_status engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, Carver& cv,
                           Engine** out) {
   if (sp.method == UOTK_NFFT) return nfft_engine_create(ctx, s, sp, cv, out);
+  if (sp.method == UOTK_DIRECT_BF16 || sp.method == UOTK_DIRECT_BF16X3)
+    return tc_engine_create(ctx, s, sp, cv, out);
   std::unique_ptr<DirectEngine> e(new DirectEngine());
   e->ctx = ctx; e->d = sp.d; e->n = sp.n; e->m = sp.m; e->a = sp.a; e->b = sp.b;
   e->eps = sp.eps;

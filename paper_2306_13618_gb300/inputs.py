@@ -16,6 +16,10 @@ Workloads (shapes and distributions of the measured configurations):
   [-0.2, 0.2]^3, standard deviation 0.03), source and target independent draws
   of the same mixture; weights lognormal(0, 0.5) normalised to masses 1.0 and
   0.8; eps = 0.02, rho = 0.5, 200 sweeps.
+* ``gauss64`` -- n = m = 262144 points in d = 64: source N(0, I/64), target
+  an independent draw of N(0.1 e_1, I/64) (the same cloud shifted by 0.1 along
+  the first axis); uniform weights with masses 1.0 and 1.2; eps = 1, rho = 2.
+  The high-dimensional case of the direct form.
 * ``paper_uniform`` -- the paper's own synthetic measures (Sec. 5.1.1): points and
   weights i.i.d. uniform on [0, 1] (unnormalised).
 """
@@ -85,6 +89,17 @@ def gmm3(seed: int = 2000, n: int = 1 << 20, m: int = 1 << 20, d: int = 3,
     b = _normalise(g.lognormal(0.0, 0.5, m), 0.8)
     return Workload("gmm3", x, a, y, b, eps=0.02, rho=0.5, sweeps=200, ell=0.2,
                     extra={"means": means})
+
+
+def gauss64(seed: int = 3000, n: int = 262144, m: int = 262144, d: int = 64) -> Workload:
+    g = rng(seed)
+    x = (g.standard_normal((n, d)) / 8.0).astype(np.float32)
+    shift = np.zeros(d)
+    shift[0] = 0.1
+    y = (g.standard_normal((m, d)) / 8.0 + shift).astype(np.float32)
+    a = np.full(n, 1.0 / n, dtype=np.float32)
+    b = np.full(m, 1.2 / m, dtype=np.float32)
+    return Workload("gauss64", x, a, y, b, eps=1.0, rho=2.0, sweeps=100, ell=1.0)
 
 
 def paper_uniform(seed: int = 3000, n: int = 1000, d: int = 3, eps: float = 0.05,

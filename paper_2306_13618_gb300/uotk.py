@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libuotk.so")
 
 UOTK_OK = 0
 UOTK_ERR_NOT_CONVERGED = 6
-DIRECT, NFFT = 0, 1
+DIRECT, NFFT, DIRECT_BF16, DIRECT_BF16X3 = 0, 1, 2, 3
 REF_PRODUCT, REF_COUNTING = 0, 1
 WARM_START = 1
 
@@ -191,7 +191,8 @@ def _pts(t, name):
 
 
 def _opts(method="direct", grid=0, bandwidth=0, cutoff=0, period=0.0, target_err=0.0):
-    m = {"direct": DIRECT, "nfft": NFFT}.get(method, method)
+    m = {"direct": DIRECT, "nfft": NFFT, "direct_bf16": DIRECT_BF16,
+         "direct_bf16x3": DIRECT_BF16X3}.get(method, method)
     return SumOpts(int(m), int(grid), int(bandwidth), int(cutoff), float(period), float(target_err))
 
 

@@ -1,0 +1,143 @@
+"""GPU parity of the tensor-core direct forms (UOTK_DIRECT_BF16, UOTK_DIRECT_BF16X3)
+against the FP64 oracle, through the C ABI.
+
+Error model.  The library forms ||x - y||^2 = |x|^2 + |y|^2 - 2 x.y from points
+centred on the middle of the joint bounding box, with R = max |p - o| the
+largest centred norm.  An error e in x.y changes a term exp(-||x-y||^2/eps)
+by the factor exp(2 e / eps), so every (positive) term, and therefore every
+sum of positive terms, has relative error about 2 e / eps, plus the FP32
+error of the FP32 form:
+  * BF16: each factor is rounded to 8 significant bits, e <= 2^-8 R^2
+    (two roundings of 2^-9), bound 2^-7 R^2 / eps;
+  * BF16x3: v = hi + lo leaves 2^-18 |v|, and the dropped lo.lo term is
+    2^-18 |x||y|, so e <= 3 * 2^-18 R^2 and the bound is 6 * 2^-18 R^2 / eps,
+    plus the FP32 accumulation of 3d products (2^-22 R^2) and the FP32
+    exponent arithmetic (a few 2^-24 c R^2).
+Each test computes R from the data and checks max relative error <= 2 x bound
++ 2e-6 (the FP32 sum bar)."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_13618_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def uotk():
+    from paper_2306_13618_gb300 import build, uotk
+    build.build()
+    return uotk
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def rel_err(got, ref):
+    got, ref = f64(got), f64(ref)
+    return np.max(np.abs(got - ref) / np.maximum(np.abs(ref), 1e-300))
+
+
+def radius(*clouds):
+    lo = np.min([np.min(f64(c), 0) for c in clouds], 0)
+    hi = np.max([np.max(f64(c), 0) for c in clouds], 0)
+    o = (f64(lo.astype(np.float32)) + f64(hi.astype(np.float32))) / 2
+    return max(np.max(np.linalg.norm(f64(c) - o, axis=1)) for c in clouds)
+
+
+def bound(method, R, eps):
+    per = 2.0 ** -7 if method == "direct_bf16" else 6 * 2.0 ** -18 + 2.0 ** -21
+    return 2 * per * R * R / eps + 2e-6
+
+
+@pytest.mark.parametrize("method", ["direct_bf16x3", "direct_bf16"])
+@pytest.mark.parametrize("d,n,m", [(64, 1000, 777), (3, 300, 129), (17, 128, 128),
+                                   (100, 513, 250), (128, 129, 1), (1, 1, 300)])
+def test_kernel_sum_tc_parity(uotk, method, d, n, m):
+    g = inputs.rng(400 + d)
+    src = (g.standard_normal((n, d)) / np.sqrt(d)).astype(np.float32)
+    tgt = (g.standard_normal((m, d)) / np.sqrt(d) + 0.05).astype(np.float32)
+    w = g.uniform(0.1, 2.0, n).astype(np.float32)
+    eps = 0.5
+    got = uotk.kernel_sum(dev(src), dev(w), dev(tgt), eps, method=method).cpu().numpy()
+    ref = oracle.ksum(f64(src), f64(w), f64(tgt), eps)
+    err = rel_err(got, ref)
+    assert err <= bound(method, radius(src, tgt), eps), (err, bound(method, radius(src, tgt), eps))
+
+
+def test_kernel_sum_tc_edges(uotk):
+    g = inputs.rng(450)
+    tgt = (g.standard_normal((200, 64)) / 8).astype(np.float32)
+    for method in ("direct_bf16x3", "direct_bf16"):
+        # zero weights contribute exactly zero; far outliers underflow to zero
+        src = np.concatenate([tgt, tgt + 50.0]).astype(np.float32)
+        w = np.concatenate([np.zeros(200), np.ones(200)]).astype(np.float32)
+        out = uotk.kernel_sum(dev(src), dev(w), dev(tgt), 1.0, method=method).cpu().numpy()
+        assert np.all(out == 0), method
+        # no sources -> zeros
+        out = uotk.kernel_sum(dev(np.zeros((0, 64), np.float32)), dev(np.zeros(0, np.float32)),
+                              dev(tgt), 1.0, method=method).cpu().numpy()
+        assert np.all(out == 0)
+    # negative weight rejected, d > 128 unsupported
+    w = np.ones(200, np.float32)
+    w[3] = -1
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.kernel_sum(dev(tgt), dev(w), dev(tgt), 1.0, method="direct_bf16x3")
+    assert e.value.status == 1
+    big = np.zeros((10, 129), np.float32)
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.kernel_sum(dev(big), dev(np.ones(10, np.float32)), dev(big), 1.0,
+                        method="direct_bf16")
+    assert e.value.status == 4
+
+
+def test_kernel_sum_tc_large_sampled(uotk):
+    """n = m = 262144, d = 64 (the high-dimensional workload): 256 sampled
+    targets against the oracle over all sources, both precisions."""
+    W = inputs.gauss64()
+    idx = inputs.subsample_rows(inputs.rng(7), 256, W.m)
+    ref = oracle.ksum(f64(W.x), f64(W.a), f64(W.y[idx]), W.eps)
+    R = radius(W.x, W.y)
+    for method in ("direct_bf16x3", "direct_bf16"):
+        out = uotk.kernel_sum(dev(W.x), dev(W.a), dev(W.y), W.eps, method=method).cpu().numpy()
+        err = rel_err(out[idx], ref)
+        assert err <= bound(method, R, W.eps), (method, err, bound(method, R, W.eps))
+
+
+def residual(b, g, rb, rg):
+    return (np.linalg.norm(b - rb) / np.linalg.norm(rb)
+            + np.linalg.norm(g - rg) / np.linalg.norm(rg))
+
+
+def test_sinkhorn_tc_vs_oracle(uotk):
+    """Alg. 1 with the BF16x3 cross term on a 1024 + 1024 subsample of the
+    high-dimensional workload, 100 sweeps, against the FP64 oracle."""
+    W = inputs.gauss64(seed=3001, n=1024, m=1024)
+    X, Y, A, B = f64(W.x), f64(W.y), f64(W.a), f64(W.b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=W.sweeps)
+    beta, gamma, sweeps, value, _ = uotk.uot_sinkhorn(dev(W.x), dev(W.a), dev(W.y), dev(W.b),
+                                                      W.eps, W.rho, max_sweeps=W.sweeps,
+                                                      method="direct_bf16x3")
+    # per-sum relative error delta moves the duals by about q*delta per
+    # half-step, accumulated over the contraction: residual ~ delta (1 + eta lambda)
+    delta = bound("direct_bf16x3", radius(W.x, W.y), W.eps)
+    res = residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg)
+    assert res <= delta * (1 + W.rho / W.eps), (res, delta)
+    v = oracle.dual_value(X, A, Y, B, W.eps, W.rho, W.rho, rb, rg)
+    assert abs(value - v) <= delta * abs(v) * (1 + W.rho / W.eps)
+
+
+def test_mmd2_tc(uotk):
+    W = inputs.gauss64(seed=3002, n=1500, m=1300)
+    rv, rp = oracle.mmd2(f64(W.x), f64(W.a), f64(W.y), f64(W.b), W.ell, return_parts=True)
+    delta = bound("direct_bf16x3", radius(W.x, W.y), W.ell ** 2)
+    v, parts = uotk.mmd2(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.ell, method="direct_bf16x3")
+    assert np.allclose(parts, rp, rtol=delta, atol=0)
+    assert abs(v - rv) <= delta * (rp[0] + 2 * rp[1] + rp[2])
