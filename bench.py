@@ -114,13 +114,15 @@ def load_peaks():
         return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
-def stage_rooflines(prof, W, sms, peaks, plan):
+def stage_rooflines(prof, W, sms, peaks, plan, rates):
     """Achieved vs peak for each profiled stage (per launch, CUDA-event times).
 
+    rates = (ex2, ffma): operations per clock per SM measured on this GPU by
+    uotk_measure_unit_rates.
     direct : MUFU ex2 bound, one ex2 per (source, target) pair;
-             peak = 16 ex2/clk/SM x SMs x max SM clock.
+             peak = measured ex2/clk/SM x SMs x max SM clock.
     spread, gather : FP32 FMA-pipe bound, one FMA per footprint node per point,
-             (2m)^3 nodes; peak = 128 FMA/clk/SM x SMs x max SM clock.
+             (2m)^3 nodes; peak = measured FMA/clk/SM x SMs x max SM clock.
     fft    : HBM bound, algorithmic bytes = read + write of the n^3 FP32 grid.
     dual_update : HBM bound, 24 bytes per element (t, base, old and new dual).
     """
@@ -134,16 +136,18 @@ def stage_rooflines(prof, W, sms, peaks, plan):
         t = ms / 1e3 / launches
         r = {"kernel": name, "launches": launches, "share": ms / total, "ms_total": ms,
              "us_per_launch": t * 1e6}
-        if name == "direct":
+        ex2, ffma = rates
+        if name in ("direct", "direct_tc"):
             r.update(bound="alu", unit="Gexp2/s", achieved=W.n * W.m / t / 1e9,
-                     peak=16.0 * sms * clk / 1e9,
-                     peak_source=f"16 ex2/clk/SM x {sms} SMs x {clk/1e6:.0f} MHz")
+                     peak=ex2 * sms * clk / 1e9,
+                     peak_source=f"{ex2:.1f} ex2/clk/SM (measured) x {sms} SMs x "
+                                 f"{clk/1e6:.0f} MHz")
         elif name in ("spread", "gather") and plan:
             nodes = (2 * plan["cutoff"]) ** 3
             r.update(bound="alu", unit="GFMA/s", achieved=W.n * nodes / t / 1e9,
-                     peak=128.0 * sms * clk / 1e9,
-                     peak_source=f"128 FP32 FMA/clk/SM x {sms} SMs x {clk/1e6:.0f} MHz; "
-                                 f"{nodes} FMAs per point (m = {plan['cutoff']})")
+                     peak=ffma * sms * clk / 1e9,
+                     peak_source=f"{ffma:.1f} FP32 FMA/clk/SM (measured) x {sms} SMs x "
+                                 f"{clk/1e6:.0f} MHz; {nodes} FMAs per point (m = {plan['cutoff']})")
         elif name == "fft" and plan:
             byts = 2 * 4 * plan["grid"] ** 3
             r.update(bound="hbm", unit="GB/s", achieved=byts / t / 1e9, peak=hbm,
@@ -293,6 +297,58 @@ def gradient_extras(uotk, ctx, stream, W, x, a, y, b, method):
     return res
 
 
+def high_dim_extras(uotk, ctx, stream, rates, sms, peaks):
+    """The direct form in d = 64 (gauss64 workload, n = m = 262144): FP32 against
+    the tensor-core forms (BF16 cross term, three-product BF16x3), pairs/s, MUFU
+    fraction and the error on 256 sampled targets against the FP64 oracle; then
+    one 100-sweep Sinkhorn solve with the BF16x3 form."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2306_13618_gb300 import inputs
+
+    W = inputs.gauss64()
+    x, y = torch.from_numpy(W.x).cuda(), torch.from_numpy(W.y).cuda()
+    a, b = torch.from_numpy(W.a).cuda(), torch.from_numpy(W.b).cuda()
+    idx = inputs.subsample_rows(inputs.rng(13), 256, W.m)
+    ref = oracle.ksum(W.x.astype(np.float64), W.a.astype(np.float64),
+                      W.y[idx].astype(np.float64), W.eps)
+    clk = float(peaks.get("sm_max_mhz", 2070.0)) * 1e6
+    peak = rates[0] * sms * clk
+    res = {"workload": f"gauss64: n=m={W.n}, d={W.d}, eps={W.eps}"}
+    for method, reps in (("direct_bf16x3", 5), ("direct_bf16", 5), ("direct", 1)):
+        try:
+            uotk.kernel_sum(x, a, y, W.eps, method=method, ctx=ctx)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                out = uotk.kernel_sum(x, a, y, W.eps, method=method, ctx=ctx)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            o = out.cpu().numpy()[idx].astype(np.float64)
+            pairs = W.n * W.m / (ms / 1e3)
+            res[method] = {"ms_per_sum": ms, "pairs_per_s": pairs, "ex2_frac_of_peak": pairs / peak,
+                           "rel_err_max": float(np.max(np.abs(o - ref) / ref))}
+        except uotk.UotkError as e:
+            res[method] = {"error": str(e)}
+    try:
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, _, sweeps, _, _ = uotk.uot_sinkhorn(x, a, y, b, W.eps, W.rho, max_sweeps=W.sweeps,
+                                                method="direct_bf16x3", ctx=ctx)
+        e1.record(stream)
+        e1.synchronize()
+        res["sinkhorn_bf16x3"] = {"sweeps": sweeps,
+                                  "sweeps_per_s": sweeps / (e0.elapsed_time(e1) / 1e3)}
+    except uotk.UotkError as e:
+        res["sinkhorn_bf16x3"] = {"error": str(e)}
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -373,7 +429,8 @@ def main():
     peaks, peak_kind = load_peaks()
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     plan = uotk.nfft_plan(y, x, W.eps, ctx=ctx).as_dict() if args.method == "nfft" else None
-    roofs = stage_rooflines(prof, W, sms, peaks, plan)
+    rates = uotk.measure_unit_rates(ctx)
+    roofs = stage_rooflines(prof, W, sms, peaks, plan, rates)
     dom = max(roofs.values(), key=lambda r: r["ms_total"]) if roofs else {}
     roof = {k: v for k, v in dom.items() if k != "ms_total"}
     roof["traffic"] = recorded_traffic(roof.get("kernel"))
@@ -426,6 +483,7 @@ def main():
             except uotk.UotkError as e:
                 extras[meth] = {"error": str(e)}
         extras["gradients"] = gradient_extras(uotk, ctx, stream, W, x, a, y, b, args.method)
+        extras["gauss64"] = high_dim_extras(uotk, ctx, stream, rates, sms, peaks)
     if "nfft" in extras and "direct" in extras and "ms_per_matvec" in extras.get("direct", {}) \
             and "ms_per_matvec" in extras.get("nfft", {}):
         extras["nfft_speedup_vs_direct"] = extras["direct"]["ms_per_matvec"] / extras["nfft"]["ms_per_matvec"]
@@ -449,6 +507,7 @@ def main():
         "e2e": {"value": world * W.sweeps / (e2e_ms / 1e3), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk,
+        "unit_rates_per_clk_sm": {"ex2": rates[0], "ffma": rates[1]},
         "stages_ms_per_step": {k: v[1] / args.steps for k, v in prof.items()},
         "stage_rooflines": {k: {kk: vv for kk, vv in v.items() if kk != "ms_total"}
                             for k, v in roofs.items()},

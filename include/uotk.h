@@ -119,6 +119,15 @@ uotk_status uotk_set_profiling(uotk_ctx* ctx, int enable);
 int uotk_profile_read(uotk_ctx* ctx, char* names, int cap, int64_t* counts, double* ms, int max);
 void uotk_profile_reset(uotk_ctx* ctx);
 
+/* Unit throughputs of this GPU (instrumentation for roofline denominators; the
+ * paper has no counterpart).  Runs one CTA of 1024 threads per SM, each
+ * thread 16 independent chains of 4096 ex2.approx.ftz.f32 (then of FP32 FMA),
+ * and divides the operations of each CTA by its clock64() cycles:
+ * *ex2_per_clk and *ffma_per_clk (host) receive the mean operations per clock
+ * per SM.  Synchronises `stream`; takes a few milliseconds. */
+uotk_status uotk_measure_unit_rates(uotk_ctx* ctx, void* stream, double* ex2_per_clk,
+                                    double* ffma_per_clk);
+
 /* ---- the kernel summation (Eq. fast_sum; the matrix-vector product of Alg. 1/2) --
  * out[j] = sum_i w[i] * exp(-||src_i - tgt_j||^2 / eps),  j = 0..m-1.
  *   src: device FP32 [n*d]; w: device FP32 [n], every w[i] >= 0 and finite;

@@ -22,6 +22,7 @@ uotk_status op_sinkhorn_divergence(uotk_ctx*, cudaStream_t, int, const float*, i
 uotk_status op_mmd2(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
                     const float*, int64_t, const float*, double, double*, double*,
                     const uotk_sum_opts*);
+uotk_status op_measure_unit_rates(uotk_ctx*, cudaStream_t, double*, double*);
 uotk_status op_mmd2_grad(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
                          const float*, int64_t, const float*, double, double*, double*, double*,
                          double*, double*, const uotk_sum_opts*);
@@ -261,6 +262,14 @@ int uotk_profile_read(uotk_ctx* ctx, char* names, int cap, int64_t* counts, doub
     if (ms) ms[i] = P.ms[i];
   }
   return k;
+}
+
+uotk_status uotk_measure_unit_rates(uotk_ctx* ctx, void* stream, double* ex2_per_clk,
+                                    double* ffma_per_clk) {
+  UOTK_TRY(enter(ctx));
+  if (!ex2_per_clk || !ffma_per_clk)
+    return set_error(ctx, UOTK_ERR_INVALID, "measure_unit_rates: null output");
+  return op_measure_unit_rates(ctx, (cudaStream_t)stream, ex2_per_clk, ffma_per_clk);
 }
 
 void uotk_profile_reset(uotk_ctx* ctx) {

@@ -24,16 +24,20 @@
 // (16-byte chunk g of row r stored at chunk g ^ (r mod 8)).  Blocks are
 // 16 KB, contiguous, and move global -> shared with 1-D bulk copies.
 //
-// CTA (384 threads, one per SM, all 512 tensor-memory columns):
+// CTA (640 threads, one per SM, all 512 tensor-memory columns):
 //   warp 0, one lane: producer -- the CTA's 128-target tile once, then source
 //     tiles through a ring of shared-memory stages (mbarrier transaction counts);
 //   warp 1: allocates tensor memory; one lane issues the MMAs of each source
 //     tile into one of 4 accumulator stages of 128 columns, and commits them to
 //     the stage's barriers;
-//   warps 4-11: two epilogue warpgroups taking alternate source tiles; thread
-//     (warp, lane) owns target row 32 (warp mod 4) + lane, reads its 128
-//     accumulator columns with tcgen05.ld, and adds w_j 2^{2c S + b_j + a_i}
-//     (b_j = -c |y_j|^2, a_i = -c |x_i|^2) into a compensated FP32 pair.
+//   warp 2, one lane: copies the {b_j, w_j} pairs of each source tile into a
+//     4-entry shared ring, one entry per accumulator stage;
+//   warps 4-19: four epilogue warpgroups, warpgroup g taking source tiles
+//     k = g mod 4; thread (warp, lane) owns target row 32 (warp mod 4) + lane,
+//     reads its 128 accumulator columns with tcgen05.ld, and adds
+//     w_j 2^{2c S + b_j + a_i} (b_j = -c |y_j|^2, a_i = -c |x_i|^2) into a
+//     compensated FP32 pair.  Four warps per SM sub-partition hide the
+//     tensor-memory and MUFU latencies.
 // Every wait is bounded; a timeout raises the context's TIMEOUT flag, and the
 // CTA drains its copies and MMAs before it frees tensor memory and exits.
 #include <cuda_bf16.h>
@@ -50,18 +54,32 @@ namespace {
 constexpr int TC_ROWS = 128;                 // targets per CTA (MMA M) = sources per tile (MMA N)
 constexpr int TC_BLOCK = TC_ROWS * 128;      // bytes of one 128 x 64 BF16 block
 constexpr int TC_ACC = 4;                    // accumulator stages (4 x 128 columns)
-constexpr int TC_THREADS = 384;
-constexpr int TC_MISC = 2048;                // barriers, flags, hand-over buffer
+constexpr int TC_EPI_GROUPS = 4;            // epilogue warpgroups
+constexpr int TC_THREADS = 128 + 128 * TC_EPI_GROUPS;
+constexpr int TC_MISC = 12288;               // barriers, flags, weight ring, hand-over buffer
 constexpr int TC_MIN_SMEM = 120 * 1024;      // forces one CTA per SM
 
 __host__ __device__ constexpr int tc_ka(bool split, int dc) { return split ? 2 * dc : dc; }
-__host__ __device__ constexpr int tc_stages(bool split, int dc) {
-  return (200 * 1024 - tc_ka(split, dc) * TC_BLOCK) / (tc_ka(split, dc) * TC_BLOCK) > 4
-             ? 4
-             : (200 * 1024 - tc_ka(split, dc) * TC_BLOCK) / (tc_ka(split, dc) * TC_BLOCK);
+// Source ring: slots of T = 1 or 2 source tiles (T = 2: one MMA of N = 256
+// covers both, reading the target tile from shared memory half as often), as
+// many slots as fit next to the target tile in ~200 KB, at most 8 (a deep ring
+// hides the latency of streaming source tiles from L2).
+__host__ __device__ constexpr int tc_tiles_per_slot(bool pair) { return pair ? 2 : 1; }
+__host__ __device__ constexpr int tc_stages(bool split, int dc, bool pair) {
+  return (200 * 1024 - tc_ka(split, dc) * TC_BLOCK) /
+                     (tc_tiles_per_slot(pair) * tc_ka(split, dc) * TC_BLOCK) > 8
+             ? 8
+             : (200 * 1024 - tc_ka(split, dc) * TC_BLOCK) /
+                   (tc_tiles_per_slot(pair) * tc_ka(split, dc) * TC_BLOCK);
 }
-__host__ __device__ constexpr size_t tc_smem_bytes(bool split, int dc) {
-  return (size_t)tc_ka(split, dc) * TC_BLOCK * (1 + tc_stages(split, dc)) + TC_MISC + 1024;
+__host__ __device__ constexpr size_t tc_smem_bytes(bool split, int dc, bool pair) {
+  return (size_t)tc_ka(split, dc) * TC_BLOCK *
+             (1 + (size_t)tc_tiles_per_slot(pair) * tc_stages(split, dc, pair)) +
+         TC_MISC + 1024;
+}
+// Pairing needs at least two slots.
+__host__ __device__ constexpr bool tc_can_pair(bool split, int dc) {
+  return tc_stages(split, dc, true) >= 2;
 }
 
 // ---- tcgen05 helpers (inline PTX) ----
@@ -76,17 +94,17 @@ __device__ __forceinline__ unsigned long long tc_desc(unsigned saddr) {
   d |= 2ull << 61;                 // 128-byte swizzle
   return d;
 }
-// Instruction descriptor: D FP32, A and B BF16, both K-major, M = N = 128.
-__host__ __device__ constexpr unsigned tc_idesc() {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(TC_ROWS >> 3) << 17) |
+// Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
+__host__ __device__ constexpr unsigned tc_idesc(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) |
          ((unsigned)(TC_ROWS >> 4) << 24);
 }
 __device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long ad,
-                                       unsigned long long bd, unsigned acc) {
+                                       unsigned long long bd, unsigned idesc, unsigned acc) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(tc_idesc()), "r"(acc)
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
       : "memory");
 }
 __device__ __forceinline__ void tc_commit(unsigned long long* bar) {
@@ -132,61 +150,106 @@ __device__ __forceinline__ void tc_neumaier(float& hi, float& lo, float v) {
   hi = t;
 }
 
-// Weighted exponential sum of 16 accumulator columns of one row.
-__device__ __forceinline__ float tc_chunk(const unsigned (&v)[16], const float4* __restrict__ bw,
-                                          float two_c, float aa) {
-  float s0 = 0.f, s1 = 0.f;
+// Packed two-wide FP32 arithmetic (one instruction for two lanes of values).
+__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void f2_unpack(unsigned long long r, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+}
+__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
+                                                     unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+// Weighted exponential sum of 16 accumulator columns of one row:
+//   sum_j w_j 2^{2c S_j + b_j + aa}   (FAST: without aa, applied to the row sum).
+// Columns go in pairs through packed FP32 instructions; bw holds, per pair of
+// columns, {b_j, b_j+1, w_j, w_j+1}.
+template <bool FAST>
+__device__ __forceinline__ float tc_chunk(const unsigned (&v)[16], const ulonglong2* bw,
+                                          unsigned long long two_c2, unsigned long long aa2) {
+  unsigned long long acc = 0ull;
 #pragma unroll
   for (int j = 0; j < 16; j += 2) {
-    const float4 q = __ldg(bw + (j >> 1));  // {b_j, w_j, b_j+1, w_j+1}, same for the whole warp
-    s0 = fmaf(q.y, ex2_approx(fmaf(__uint_as_float(v[j]), two_c, q.x) + aa), s0);
-    s1 = fmaf(q.w, ex2_approx(fmaf(__uint_as_float(v[j + 1]), two_c, q.z) + aa), s1);
+    const ulonglong2 q = bw[j >> 1];  // shared-memory broadcast
+    unsigned long long e =
+        f2_fma(f2_pack(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), two_c2, q.x);
+    if (!FAST) e = f2_add(e, aa2);
+    float e0, e1;
+    f2_unpack(e, e0, e1);
+    acc = f2_fma(q.y, f2_pack(ex2_approx(e0), ex2_approx(e1)), acc);
   }
+  float s0, s1;
+  f2_unpack(acc, s0, s1);
   return s0 + s1;
 }
 
 // One CTA: 128 targets (blockIdx.x) against the source tiles of split
 // blockIdx.y.  tiles: [tile][2*DC blocks][16 KB], block 2c = hi, 2c+1 = lo of
-// coordinate chunk c.  bw: per source {-c |y|^2, w}, zero past the last source.
+// coordinate chunk c.  bw: per pair of sources {b_j, b_j+1, w_j, w_j+1} with
+// b = -c |y|^2, zero past the last source.
 // out: [splits][m] (split partial sums) or [m].
-template <bool SPLIT, int DC>
+// FAST: the row factor 2^{-c |x|^2} is applied to the finished row sum instead
+// of to every term (one FP32 add less per pair).  The host selects it only when
+// c R^2 <= 64, R the largest centred norm, so that no term 2^{c(|x|^2 - ||x-y||^2)}
+// can overflow.
+template <bool SPLIT, int DC, bool FAST, bool PAIR>
 __global__ void __launch_bounds__(TC_THREADS, 1)
-    k_direct_tc(const unsigned char* __restrict__ src_tiles, const float2* __restrict__ src_bw,
+    k_direct_tc(const unsigned char* __restrict__ src_tiles, const float* __restrict__ src_bw,
                 long long src_tiles_total, int tiles_per_split,
                 const unsigned char* __restrict__ tgt_tiles, const float* __restrict__ tgt_n2,
                 long long m, float two_c, float neg_c, float* __restrict__ out,
                 long long* __restrict__ flags) {
   constexpr int KBT = 2 * DC;               // blocks per tile in global memory
   constexpr int KA = tc_ka(SPLIT, DC);      // blocks per tile in shared memory
-  constexpr int S = tc_stages(SPLIT, DC);   // source-tile stages
-  constexpr unsigned STAGE_BYTES = (unsigned)KA * TC_BLOCK;
-  static_assert(S >= 2, "at least two source stages");
+  constexpr int T = tc_tiles_per_slot(PAIR);        // source tiles per ring slot
+  constexpr int S = tc_stages(SPLIT, DC, PAIR);     // ring slots
+  constexpr unsigned STAGE_BYTES = (unsigned)KA * TC_BLOCK;  // one tile, all blocks
+  constexpr unsigned SLOT_BYTES = (unsigned)T * STAGE_BYTES;
+  static_assert(S >= 2, "at least two source slots");
 
   extern __shared__ unsigned char tc_raw[];
   const unsigned raw = smem_addr(tc_raw);
   unsigned char* sA = tc_raw + ((1024u - (raw & 1023u)) & 1023u);
   unsigned char* sB = sA + STAGE_BYTES;
-  unsigned char* misc = sB + (size_t)S * STAGE_BYTES;
+  unsigned char* misc = sB + (size_t)S * SLOT_BYTES;
   unsigned long long* a_full = reinterpret_cast<unsigned long long*>(misc);
   unsigned long long* b_full = a_full + 1;
   unsigned long long* b_empty = b_full + S;
   unsigned long long* t_full = b_empty + S;
   unsigned long long* t_empty = t_full + TC_ACC;
   unsigned long long* done = t_empty + TC_ACC;
+  unsigned long long* w_full = done + 1;                  // [TC_ACC] weight ring entries landed
   unsigned* tmem_slot = reinterpret_cast<unsigned*>(misc + 256);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(misc + 260);
-  float* hand = reinterpret_cast<float*>(misc + 512);  // [2][128] partial sums of warpgroup 1
+  // Weight ring: the {b_j, w_j} pairs of the source tile in accumulator stage a
+  // (1 KB each), filled by warp 2 once the epilogue has released stage a.
+  float* wring = reinterpret_cast<float*>(misc + 1024);  // [TC_ACC][2 * TC_ROWS]
+  // [groups - 1][2][128] compensated row sums handed to warpgroup 0
+  float* hand = reinterpret_cast<float*>(misc + 1024 + TC_ACC * TC_ROWS * sizeof(float2));
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long t_begin = (long long)blockIdx.y * tiles_per_split;
   const long long t_end = min(t_begin + (long long)tiles_per_split, src_tiles_total);
   const int count = t_end > t_begin ? (int)(t_end - t_begin) : 0;
+  const int groups = (count + T - 1) / T;  // ring fills; group r holds tiles rT .. rT + T - 1
 
   if (threadIdx.x == 0) {
     mbar_init(a_full, 1);
     for (int s = 0; s < S; ++s) { mbar_init(&b_full[s], 1); mbar_init(&b_empty[s], 1); }
     for (int a = 0; a < TC_ACC; ++a) { mbar_init(&t_full[a], 1); mbar_init(&t_empty[a], 128); }
     mbar_init(done, 1);
+    for (int a = 0; a < TC_ACC; ++a) mbar_init(&w_full[a], 1);
     *abort_flag = 0;
     mbar_fence_init();
   }
@@ -208,26 +271,32 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     int fills[S];
 #pragma unroll
     for (int s = 0; s < S; ++s) fills[s] = 0;
+    static_assert(S <= 8, "barrier region holds at most 8 stages");
     mbar_expect(a_full, STAGE_BYTES);
     for (int b = 0; b < KA; ++b) {
       const int kb = SPLIT ? b : 2 * b;
       bulk_copy(sA + (size_t)b * TC_BLOCK,
                 tgt_tiles + ((size_t)blockIdx.x * KBT + kb) * TC_BLOCK, TC_BLOCK, a_full);
     }
-    for (int k = 0; k < count; ++k) {
-      const int s = k % S, u = k / S;
+    for (int r = 0; r < groups; ++r) {
+      const int s = r % S, u = r / S;
       if (u > 0 && !mbar_wait(&b_empty[s], (unsigned)(u - 1) & 1u)) {
         *abort_flag = 1;
         flag_add(&flags[FLAG_TIMEOUT], 1LL);
         break;
       }
       if (*abort_flag) break;
-      mbar_expect(&b_full[s], STAGE_BYTES);
-      const size_t tile = (size_t)(t_begin + k);
-      for (int b = 0; b < KA; ++b) {
-        const int kb = SPLIT ? b : 2 * b;
-        bulk_copy(sB + (size_t)s * STAGE_BYTES + (size_t)b * TC_BLOCK,
-                  src_tiles + (tile * KBT + kb) * TC_BLOCK, TC_BLOCK, &b_full[s]);
+      const int nt = min(T, count - r * T);
+      mbar_expect(&b_full[s], (unsigned)nt * STAGE_BYTES);
+      // slot layout: block b of tile t at b*T*16K + t*16K, so that the T tiles
+      // of one block form T*128 consecutive rows
+      for (int t = 0; t < nt; ++t) {
+        const size_t tile = (size_t)(t_begin + r * T + t);
+        for (int b = 0; b < KA; ++b) {
+          const int kb = SPLIT ? b : 2 * b;
+          bulk_copy(sB + (size_t)s * SLOT_BYTES + ((size_t)b * T + t) * TC_BLOCK,
+                    src_tiles + (tile * KBT + kb) * TC_BLOCK, TC_BLOCK, &b_full[s]);
+        }
       }
       fills[s]++;
     }
@@ -242,19 +311,26 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     bool ok = mbar_wait(a_full, 0u);
     if (!ok) { *abort_flag = 1; flag_add(&flags[FLAG_TIMEOUT], 1LL); }
     const unsigned a0 = smem_addr(sA);
-    for (int k = 0; ok && k < count; ++k) {
-      const int s = k % S, a = k % TC_ACC;
-      const int us = k / S, ua = k / TC_ACC;
-      if (!mbar_wait(&b_full[s], (unsigned)us & 1u) ||
-          (ua > 0 && !mbar_wait(&t_empty[a], (unsigned)(ua - 1) & 1u))) {
+    for (int r = 0; ok && r < groups; ++r) {
+      const int s = r % S, us = r / S;
+      const int nt = min(T, count - r * T);
+      bool got = mbar_wait(&b_full[s], (unsigned)us & 1u);
+      for (int t = 0; got && t < nt; ++t) {
+        const int k = r * T + t, ua = k / TC_ACC;
+        if (ua > 0) got = mbar_wait(&t_empty[k % TC_ACC], (unsigned)(ua - 1) & 1u);
+      }
+      if (!got) {
         *abort_flag = 1;
         flag_add(&flags[FLAG_TIMEOUT], 1LL);
         break;
       }
       if (*abort_flag) break;
       tc_fence_after();
-      const unsigned d_tmem = tmem + (unsigned)(a * TC_ROWS);
-      const unsigned b0 = smem_addr(sB + (size_t)s * STAGE_BYTES);
+      // the group's tiles land in consecutive accumulator stages (T = 2: stages
+      // 0,1 or 2,3, i.e. 256 consecutive columns)
+      const unsigned d_tmem = tmem + (unsigned)(((r * T) % TC_ACC) * TC_ROWS);
+      const unsigned idesc = tc_idesc(nt * TC_ROWS);
+      const unsigned b0 = smem_addr(sB + (size_t)s * SLOT_BYTES);
       unsigned q = 0;
 #pragma unroll
       for (int c = 0; c < DC; ++c) {
@@ -266,11 +342,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks, ++q)
             tc_mma(d_tmem, tc_desc(a0 + (unsigned)(ba * TC_BLOCK + ks * 32)),
-                   tc_desc(b0 + (unsigned)(bb * TC_BLOCK + ks * 32)), q > 0 ? 1u : 0u);
+                   tc_desc(b0 + (unsigned)(bb * T * TC_BLOCK + ks * 32)), idesc,
+                   q > 0 ? 1u : 0u);
         }
       }
       tc_commit(&b_empty[s]);
-      tc_commit(&t_full[a]);
+      for (int t = 0; t < nt; ++t) tc_commit(&t_full[(r * T + t) % TC_ACC]);
       issued++;
     }
     // Drain: no MMA may still be running when tensor memory is freed.
@@ -278,16 +355,36 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
       tc_commit(done);
       mbar_wait(done, 0u);
     }
+  } else if (warp == 2 && lane == 0) {
+    // ---- weight producer ----
+    int fills[TC_ACC] = {0, 0, 0, 0};
+    for (int k = 0; k < count; ++k) {
+      const int a = k % TC_ACC, ua = k / TC_ACC;
+      if (ua > 0 && !mbar_wait(&t_empty[a], (unsigned)(ua - 1) & 1u)) {
+        *abort_flag = 1;
+        flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        break;
+      }
+      if (*abort_flag) break;
+      mbar_expect(&w_full[a], 2 * TC_ROWS * sizeof(float));
+      bulk_copy(wring + a * 2 * TC_ROWS, src_bw + (t_begin + k) * 2 * TC_ROWS, TC_ROWS * sizeof(float2),
+                &w_full[a]);
+      fills[a]++;
+    }
+#pragma unroll
+    for (int a = 0; a < TC_ACC; ++a)
+      if (fills[a]) mbar_wait(&w_full[a], (unsigned)(fills[a] - 1) & 1u);
   } else if (warp >= 4) {
     // ---- epilogue ----
-    const int g = (warp - 4) >> 2;  // warpgroup: source tiles k = g, g + 2, ...
+    const int g = (warp - 4) >> 2;  // warpgroup: source tiles k = g, g + groups, ...
     const int quad = warp & 3;      // tensor-memory lanes 32 quad .. 32 quad + 31
     const int row = quad * 32 + lane;
     const long long i = (long long)blockIdx.x * TC_ROWS + row;
     const float aa = i < m ? neg_c * tgt_n2[i] : 0.f;
-    for (int k = g; k < count; k += 2) {
+    const unsigned long long aa2 = f2_pack(aa, aa), two_c2 = f2_pack(two_c, two_c);
+    for (int k = g; k < count; k += TC_EPI_GROUPS) {
       const int a = k % TC_ACC, ua = k / TC_ACC;
-      bool ok = mbar_wait(&t_full[a], (unsigned)ua & 1u);
+      bool ok = mbar_wait(&t_full[a], (unsigned)ua & 1u) && mbar_wait(&w_full[a], (unsigned)ua & 1u);
       ok = __all_sync(0xffffffffu, ok) && !__any_sync(0xffffffffu, *abort_flag != 0);
       if (!ok) {
         if (lane == 0) {
@@ -297,7 +394,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
         break;
       }
       tc_fence_after();
-      const float4* bw = reinterpret_cast<const float4*>(src_bw + (t_begin + k) * TC_ROWS);
+      const ulonglong2* bw = reinterpret_cast<const ulonglong2*>(wring + a * 2 * TC_ROWS);
       const unsigned tb = tmem + ((unsigned)(quad * 32) << 16) + (unsigned)(a * TC_ROWS);
       // columns in chunks of 16, the load of the next chunk in flight while
       // the current one is summed
@@ -307,29 +404,41 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int c0 = 0; c0 < TC_ROWS; c0 += 32) {
         tc_ld16(tb + (unsigned)(c0 + 16), v1);
-        tc_neumaier(hi, lo, tc_chunk(v0, bw + (c0 >> 1), two_c, aa));
+        tc_neumaier(hi, lo, tc_chunk<FAST>(v0, bw + (c0 >> 1), two_c2, aa2));
         tc_wait16(v1);
         if (c0 + 32 < TC_ROWS) tc_ld16(tb + (unsigned)(c0 + 32), v0);
-        tc_neumaier(hi, lo, tc_chunk(v1, bw + ((c0 + 16) >> 1), two_c, aa));
+        tc_neumaier(hi, lo, tc_chunk<FAST>(v1, bw + ((c0 + 16) >> 1), two_c2, aa2));
         if (c0 + 32 < TC_ROWS) tc_wait16(v0);
       }
       tc_fence_before();
       mbar_arrive(&t_empty[a]);
     }
-    if (g == 1) {
-      hand[row] = hi;
-      hand[TC_ROWS + row] = lo;
+    if (g > 0) {
+      hand[(g - 1) * 2 * TC_ROWS + row] = hi;
+      hand[(g - 1) * 2 * TC_ROWS + TC_ROWS + row] = lo;
     }
   }
   tc_fence_before();
   __syncthreads();
   if (warp >= 4 && warp < 8) {
-    // warpgroup 0 adds warpgroup 1's pair for the same row and writes the sum
+    // warpgroup 0 adds the other warpgroups' pairs for the same row
     const int row = (warp & 3) * 32 + lane;
     const long long i = (long long)blockIdx.x * TC_ROWS + row;
-    tc_neumaier(hi, lo, hand[row]);
-    tc_neumaier(hi, lo, hand[TC_ROWS + row]);
-    if (i < m) out[(long long)blockIdx.y * m + i] = hi + lo;
+#pragma unroll
+    for (int q = 0; q < TC_EPI_GROUPS - 1; ++q) {
+      tc_neumaier(hi, lo, hand[q * 2 * TC_ROWS + row]);
+      tc_neumaier(hi, lo, hand[q * 2 * TC_ROWS + TC_ROWS + row]);
+    }
+    if (i < m) {
+      float v = hi + lo;
+      if (FAST) {
+        // v * 2^{aa}, aa = -c |x_i|^2 <= 0, without flushing a small result
+        const float aa = neg_c * tgt_n2[i];
+        const float k = floorf(aa);
+        v = ldexpf(v * exp2f(aa - k), (int)k);
+      }
+      out[(long long)blockIdx.y * m + i] = v;
+    }
   }
   if (warp == 1) {
     __syncwarp();
@@ -366,10 +475,25 @@ __global__ void k_tc_minmax(const float* __restrict__ p, long long count, int d,
   }
 }
 
-__global__ void k_tc_center(const long long* __restrict__ slots, int d, float* __restrict__ center) {
+// Box centre per coordinate, and in r2[0] the squared distance from the centre
+// to the farthest corner (an upper bound of |p - centre|^2).  One block.
+__global__ void k_tc_center(const long long* __restrict__ slots, int d, float* __restrict__ center,
+                            double* __restrict__ r2) {
+  __shared__ double part[128];
+  double acc = 0.0;
   for (int c = threadIdx.x; c < d; c += blockDim.x) {
     const double hi = ordered_to_dbl(slots[c]), lo = -ordered_to_dbl(slots[d + c]);
-    center[c] = isfinite(hi) && isfinite(lo) ? (float)(0.5 * (hi + lo)) : 0.f;
+    const bool ok = isfinite(hi) && isfinite(lo);
+    center[c] = ok ? (float)(0.5 * (hi + lo)) : 0.f;
+    const double hw = ok ? 0.5 * (hi - lo) : 0.0;
+    acc += hw * hw;
+  }
+  part[threadIdx.x] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int k = 0; k < (int)blockDim.x; ++k) t += part[k];
+    r2[0] = t;
   }
 }
 
@@ -412,11 +536,12 @@ __global__ void k_tc_pack(const float* __restrict__ pts, long long n, long long 
   }
 }
 
-// Squared norms of the centred FP32 points (0 past n), the per-source pairs
-// {-c |p|^2, w} (w = 0 past n), and validation counters of the weights.
+// Squared norms of the centred FP32 points (0 past n), the source entries
+// {b_j, b_j+1, w_j, w_j+1} per pair of points (b = -c |p|^2; b = w = 0 past n),
+// and validation counters of the weights.
 __global__ void k_tc_norms(const float* __restrict__ pts, const float* __restrict__ w, long long n,
                            long long n_pad, int d, const float* __restrict__ center, float neg_c,
-                           float* __restrict__ n2, float2* __restrict__ bw,
+                           float* __restrict__ n2, float* __restrict__ bw,
                            long long* __restrict__ flags) {
   const long long stride = (long long)gridDim.x * blockDim.x;
   const long long start = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -440,7 +565,8 @@ __global__ void k_tc_norms(const float* __restrict__ pts, const float* __restric
         }
       }
       n2[i] = (float)s;
-      bw[i] = make_float2(neg_c * (float)s, wi);
+      bw[(i >> 1) * 4 + (i & 1)] = neg_c * (float)s;  // per source pair {b, b', w, w'}
+      bw[(i >> 1) * 4 + 2 + (i & 1)] = wi;
     }
     const unsigned bn = __ballot_sync(0xffffffffu, neg);
     const unsigned bf = __ballot_sync(0xffffffffu, bad);
@@ -452,7 +578,7 @@ __global__ void k_tc_norms(const float* __restrict__ pts, const float* __restric
 }
 
 // w_j = base_j * exp(lam*pot_j - shift) (pot NULL: base_j; base NULL: 1).
-__global__ void k_tc_set_weights(float2* __restrict__ bw, long long n, const float* __restrict__ base,
+__global__ void k_tc_set_weights(float* __restrict__ bw, long long n, const float* __restrict__ base,
                                  const double* __restrict__ pot, double lam,
                                  const long long* __restrict__ shift_slot) {
   const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
@@ -460,7 +586,7 @@ __global__ void k_tc_set_weights(float2* __restrict__ bw, long long n, const flo
        i += (long long)gridDim.x * blockDim.x) {
     float v = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
     if (base) v *= base[i];
-    bw[i].y = v;
+    bw[(i >> 1) * 4 + 2 + (i & 1)] = v;
   }
 }
 
@@ -479,7 +605,7 @@ struct TcCloud {
   int64_t n = 0, tiles = 0;
   unsigned char* tile_data = nullptr;  // [tiles][2 dc][16 KB]
   float* n2 = nullptr;                 // [tiles * 128]
-  float2* bw = nullptr;                // [tiles * 128]
+  float* bw = nullptr;                 // [tiles * 64][4]: per source pair {b, b', w, w'}
 };
 
 int64_t tc_tiles(int64_t n) { return (n + TC_ROWS - 1) / TC_ROWS; }
@@ -490,7 +616,7 @@ void tc_carve_cloud(Carver& cv, int dc, int64_t n, TcCloud& C) {
   const int64_t t = C.tiles > 0 ? C.tiles : 1;
   C.tile_data = cv.take<unsigned char>((size_t)t * 2 * dc * TC_BLOCK);
   C.n2 = cv.take<float>((size_t)t * TC_ROWS);
-  C.bw = cv.take<float2>((size_t)t * TC_ROWS);
+  C.bw = cv.take<float>((size_t)t * 2 * TC_ROWS);
 }
 
 // Source splits for a (sources -> targets) pair: enough CTAs for about two
@@ -510,15 +636,16 @@ TcSplit tc_split(const uotk_ctx* ctx, int64_t src_tiles, int64_t tgt_tiles) {
   return L;
 }
 
-template <bool SPLIT, int DC>
+template <bool SPLIT, int DC, bool FAST>
 uotk_status tc_launch(uotk_ctx* ctx, cudaStream_t s, const TcCloud& src, const TcCloud& tgt,
                       const TcSplit& L, double eps, float* dst) {
-  constexpr size_t smem0 = tc_smem_bytes(SPLIT, DC);
+  constexpr bool PAIR = tc_can_pair(SPLIT, DC);
+  constexpr size_t smem0 = tc_smem_bytes(SPLIT, DC, PAIR);
   constexpr size_t smem = smem0 > (size_t)TC_MIN_SMEM ? smem0 : (size_t)TC_MIN_SMEM;
-  UOTK_CUDA(ctx, smem_attr(s, k_direct_tc<SPLIT, DC>, smem));
+  UOTK_CUDA(ctx, smem_attr(s, k_direct_tc<SPLIT, DC, FAST, PAIR>, smem));
   const double c = 1.4426950408889634 / eps;
   const dim3 grid((unsigned)tgt.tiles, (unsigned)L.splits);
-  k_direct_tc<SPLIT, DC><<<grid, TC_THREADS, smem, s>>>(
+  k_direct_tc<SPLIT, DC, FAST, PAIR><<<grid, TC_THREADS, smem, s>>>(
       src.tile_data, src.bw, src.tiles, L.tiles_per_split, tgt.tile_data, tgt.n2, tgt.n,
       (float)(2.0 * c), (float)(-c), dst, ctx->dflags);
   UOTK_LAUNCHED(ctx);
@@ -526,8 +653,8 @@ uotk_status tc_launch(uotk_ctx* ctx, cudaStream_t s, const TcCloud& src, const T
 }
 
 // out[i] = sum_j w_j exp(-||tgt_i - src_j||^2/eps), w in src.bw.
-uotk_status tc_run(uotk_ctx* ctx, cudaStream_t s, bool split, int dc, const TcCloud& src,
-                   const TcCloud& tgt, double eps, float* part, float* out) {
+uotk_status tc_run(uotk_ctx* ctx, cudaStream_t s, bool split, int dc, bool fast,
+                   const TcCloud& src, const TcCloud& tgt, double eps, float* part, float* out) {
   if (tgt.n == 0) return UOTK_OK;
   if (src.n == 0) {
     UOTK_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(float) * tgt.n, s));
@@ -538,12 +665,13 @@ uotk_status tc_run(uotk_ctx* ctx, cudaStream_t s, bool split, int dc, const TcCl
   {
     UOTK_PROF(ctx, s, "direct_tc");
     uotk_status st;
-    if (split)
-      st = dc == 1 ? tc_launch<true, 1>(ctx, s, src, tgt, L, eps, dst)
-                   : tc_launch<true, 2>(ctx, s, src, tgt, L, eps, dst);
-    else
-      st = dc == 1 ? tc_launch<false, 1>(ctx, s, src, tgt, L, eps, dst)
-                   : tc_launch<false, 2>(ctx, s, src, tgt, L, eps, dst);
+#define UOTK_TC_CASE(SP, DCC, FA) \
+  if (split == SP && dc == DCC && fast == FA) st = tc_launch<SP, DCC, FA>(ctx, s, src, tgt, L, eps, dst);
+    st = UOTK_ERR_INTERNAL;
+    UOTK_TC_CASE(true, 1, true) UOTK_TC_CASE(true, 1, false) UOTK_TC_CASE(true, 2, true)
+    UOTK_TC_CASE(true, 2, false) UOTK_TC_CASE(false, 1, true) UOTK_TC_CASE(false, 1, false)
+    UOTK_TC_CASE(false, 2, true) UOTK_TC_CASE(false, 2, false)
+#undef UOTK_TC_CASE
     UOTK_TRY(st);
   }
   if (L.splits > 1) {
@@ -562,6 +690,7 @@ struct TcEngine : Engine {
   uotk_ctx* ctx = nullptr;
   int d = 0, dc = 1;
   bool split = true;
+  bool fast = false;  // c R^2 <= 64: row factor applied after the sum
   int64_t n = 0, m = 0;
   const float* a = nullptr;
   const float* b = nullptr;
@@ -570,6 +699,7 @@ struct TcEngine : Engine {
   float* part = nullptr;
   float* center = nullptr;
   long long* slots = nullptr;
+  double* r2 = nullptr;
 
   static void carve(const uotk_ctx* ctx, const EngineSpec& sp, Carver& cv, TcEngine* e) {
     const int dc = (sp.d + 63) / 64;
@@ -590,7 +720,9 @@ struct TcEngine : Engine {
     float* pp = cv.take<float>(part);
     float* ctr = cv.take<float>(128);
     long long* sl = cv.take<long long>(256);
+    double* r2 = cv.take<double>(1);
     if (e) {
+      e->r2 = r2;
       e->dc = dc;
       e->X = X;
       e->Y = Y;
@@ -615,12 +747,12 @@ struct TcEngine : Engine {
     TcCloud& src = side == 0 ? Y : X;
     const TcCloud& tgt = side == 0 ? X : Y;
     UOTK_TRY(set_weights(s, src, base, pot, lam, shift_slot));
-    return tc_run(ctx, s, split, dc, src, tgt, eps, part, out);
+    return tc_run(ctx, s, split, dc, fast, src, tgt, eps, part, out);
   }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
     TcCloud& S = src == 0 ? X : Y;
     UOTK_TRY(set_weights(s, S, w, nullptr, 0.0, nullptr));
-    return tc_run(ctx, s, split, dc, S, tgt == 0 ? X : Y, eps, part, out);
+    return tc_run(ctx, s, split, dc, fast, S, tgt == 0 ? X : Y, eps, part, out);
   }
   const int* perm(int) const override { return nullptr; }
   const float* weights(int side) const override { return side == 0 ? a : b; }
@@ -695,8 +827,12 @@ uotk_status tc_engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp
     UOTK_LAUNCHED(ctx);
     UOTK_TRY(tc_minmax(ctx, s, sp.x, sp.n, sp.d, e->slots));
     UOTK_TRY(tc_minmax(ctx, s, sp.y, sp.m, sp.d, e->slots));
-    k_tc_center<<<1, 128, 0, s>>>(e->slots, sp.d, e->center);
+    k_tc_center<<<1, 128, 0, s>>>(e->slots, sp.d, e->center, e->r2);
     UOTK_LAUNCHED(ctx);
+    UOTK_CUDA(ctx, cudaMemcpyAsync(ctx->host + 24, e->r2, sizeof(double), cudaMemcpyDeviceToHost, s));
+    UOTK_CUDA(ctx, cudaStreamSynchronize(s));
+    const double r2 = ctx->host[24] * 1.0001;  // margin for the FP32 rounding of the centre
+    e->fast = r2 * 1.4426950408889634 / sp.eps <= 64.0;
     UOTK_TRY(tc_pack(ctx, s, sp.x, sp.a, sp.d, e->dc, e->center, sp.eps, e->X));
     UOTK_TRY(tc_pack(ctx, s, sp.y, sp.b, sp.d, e->dc, e->center, sp.eps, e->Y));
   }

@@ -91,6 +91,7 @@ def lib():
                                                ctypes.POINTER(_D), opts]
         L.uotk_mmd2.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                 ctypes.POINTER(_D), ctypes.POINTER(_D), opts]
+        L.uotk_measure_unit_rates.argtypes = [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]
         L.uotk_mmd2_grad.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                      ctypes.POINTER(_D), _P, _P, _P, _P, opts]
         L.uotk_sinkhorn_divergence_grad.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64,
@@ -104,7 +105,7 @@ def lib():
         L.uotk_nfft_gather.argtypes = [_P, _P, plan, _P, _P, _I64, _P]
         for name in ("uotk_create", "uotk_kernel_sum", "uotk_uot_sinkhorn",
                      "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
-                     "uotk_sinkhorn_divergence_grad", "uotk_nfft_plan",
+                     "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates", "uotk_nfft_plan",
                      "uotk_nfft_cells", "uotk_nfft_spread", "uotk_nfft_convolve",
                      "uotk_nfft_gather"):
             getattr(L, name).restype = ctypes.c_int
@@ -282,6 +283,15 @@ def mmd2(x, a, y, b, ell, method="direct", ctx=None, **nfft):
     return v.value, list(parts)
 
 
+def measure_unit_rates(ctx=None):
+    """(ex2 ops, FP32 FMA ops) per clock per SM of this GPU (uotk_measure_unit_rates)."""
+    ctx = ctx or default_context()
+    e, f = _D(0.0), _D(0.0)
+    ctx.check(lib().uotk_measure_unit_rates(ctx.handle, _stream(), ctypes.byref(e),
+                                            ctypes.byref(f)))
+    return e.value, f.value
+
+
 def _grad_outputs(x, y, need):
     """FP64 device gradient buffers (a, x, b, y); None where not needed."""
     n, d = x.shape
@@ -425,5 +435,6 @@ EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_strin
             "uotk_launch_count", "uotk_set_profiling", "uotk_profile_read", "uotk_profile_reset",
             "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
-            "uotk_sinkhorn_divergence_grad", "uotk_nfft_plan", "uotk_nfft_cells",
+            "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates", "uotk_nfft_plan",
+            "uotk_nfft_cells",
             "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]

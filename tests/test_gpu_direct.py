@@ -203,3 +203,12 @@ def test_graph_replay_matches_eager(uotk):
     b2, g2, s2, v2, _ = uotk.uot_sinkhorn(*args, max_sweeps=37)
     assert s1 == s2 == 37 and v1 == v2
     assert torch.equal(b1, b2) and torch.equal(g1, g2)
+
+
+def test_measure_unit_rates(uotk):
+    """The roofline denominators measured on this GPU: exp2 and FP32 FMA per
+    clock per SM within the range of any recent NVIDIA SM (16 or 32 exp2,
+    128 FMA lanes)."""
+    ex2, ffma = uotk.measure_unit_rates()
+    assert 8.0 <= ex2 <= 40.0, ex2
+    assert 64.0 <= ffma <= 140.0, ffma

@@ -58,18 +58,38 @@ def bound(method, R, eps):
 
 
 @pytest.mark.parametrize("method", ["direct_bf16x3", "direct_bf16"])
-@pytest.mark.parametrize("d,n,m", [(64, 1000, 777), (3, 300, 129), (17, 128, 128),
-                                   (100, 513, 250), (128, 129, 1), (1, 1, 300)])
-def test_kernel_sum_tc_parity(uotk, method, d, n, m):
+@pytest.mark.parametrize("d,n,m,eps", [(64, 1000, 777, 0.5), (3, 300, 129, 0.5),
+                                       (17, 128, 128, 0.5), (100, 513, 250, 0.5),
+                                       (128, 129, 1, 0.5), (1, 1, 300, 0.5),
+                                       (64, 700, 300, 0.05)])
+def test_kernel_sum_tc_parity(uotk, method, d, n, m, eps):
+    """eps = 0.5 takes the epilogue that scales each row sum once (c R^2 <= 64);
+    eps = 0.05 takes the per-term one."""
     g = inputs.rng(400 + d)
     src = (g.standard_normal((n, d)) / np.sqrt(d)).astype(np.float32)
     tgt = (g.standard_normal((m, d)) / np.sqrt(d) + 0.05).astype(np.float32)
     w = g.uniform(0.1, 2.0, n).astype(np.float32)
-    eps = 0.5
     got = uotk.kernel_sum(dev(src), dev(w), dev(tgt), eps, method=method).cpu().numpy()
     ref = oracle.ksum(f64(src), f64(w), f64(tgt), eps)
     err = rel_err(got, ref)
     assert err <= bound(method, radius(src, tgt), eps), (err, bound(method, radius(src, tgt), eps))
+
+
+@pytest.mark.parametrize("method", ["direct_bf16x3", "direct_bf16"])
+def test_kernel_sum_tc_narrow_kernel(uotk, method):
+    """eps = 0.01 on dense uniform clouds in [-1/2, 1/2]^3 (c R^2 ~ 108: the
+    per-term epilogue).  Every target has sources within a few hundredths, so
+    the sums stay inside the FP32 range (a sum below ~1e-38 would flush to 0 in
+    any FP32 form)."""
+    g = inputs.rng(460)
+    src = g.uniform(-0.5, 0.5, (4000, 3)).astype(np.float32)
+    tgt = g.uniform(-0.5, 0.5, (700, 3)).astype(np.float32)
+    w = g.uniform(0.1, 2.0, 4000).astype(np.float32)
+    got = uotk.kernel_sum(dev(src), dev(w), dev(tgt), 0.01, method=method).cpu().numpy()
+    ref = oracle.ksum(f64(src), f64(w), f64(tgt), 0.01)
+    assert np.min(ref) > 1e-30
+    err = rel_err(got, ref)
+    assert err <= bound(method, radius(src, tgt), 0.01), (err, bound(method, radius(src, tgt), 0.01))
 
 
 def test_kernel_sum_tc_edges(uotk):
