@@ -39,9 +39,14 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="uotk", choices=["uotk", "reference"])
-    p.add_argument("--method", default="nfft", choices=["nfft", "direct"])
+    p.add_argument("--workload", default="gmm3", choices=["gmm3", "gauss64"],
+                   help="gmm3: n=m=2^20, d=3 mixture (the headline); gauss64: n=m=262144, d=64")
+    p.add_argument("--method", default=None,
+                   choices=["nfft", "direct", "direct_bf16", "direct_bf16x3"],
+                   help="summation form (default: nfft for gmm3, direct_bf16x3 for gauss64)")
     p.add_argument("--sweeps", type=int, default=0, help="sweeps per solve (0: the workload's)")
-    p.add_argument("--n", type=int, default=1 << 20)
+    p.add_argument("--n", type=int, default=0,
+                   help="points per cloud (0: the workload's, 2^20 for gmm3, 262144 for gauss64)")
     p.add_argument("--no-extras", action="store_true", help="skip direct/oracle side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
     return p.parse_args()
@@ -353,11 +358,17 @@ def main():
     args = parse()
     rank, world, local = dist_env()
     from paper_2306_13618_gb300 import inputs
-    W = inputs.gmm3(seed=2000, n=args.n, m=args.n)
+    if args.workload == "gauss64":
+        W = inputs.gauss64(n=args.n, m=args.n) if args.n else inputs.gauss64()
+        args.method = args.method or "direct_bf16x3"
+    else:
+        n = args.n or (1 << 20)
+        W = inputs.gmm3(seed=2000, n=n, m=n)
+        args.method = args.method or "nfft"
     if args.sweeps:
         W.sweeps = args.sweeps
     elif args.method == "direct":
-        W.sweeps = 2  # 200 exact sweeps at 2^20 would take ~100 s; see matvecs
+        W.sweeps = 2  # 200 exact FP32 sweeps at this size would take minutes; see matvecs
     if args.impl == "reference":
         return reference_arm(args, W, rank, world)
 
@@ -458,7 +469,7 @@ def main():
     d2h = sum(t.numel() * t.element_size() for t in (hbeta, hgamma))
 
     extras = {}
-    if not args.no_extras:
+    if not args.no_extras and args.workload == "gmm3":
         import oracle
         idx = inputs.subsample_rows(inputs.rng(11), 256, W.n)
         X, Y, Bw = W.x.astype(np.float64), W.y.astype(np.float64), W.b.astype(np.float64)
@@ -494,11 +505,14 @@ def main():
                      f"sweeps/s extrapolated as pairs/s / (2 n m)"}
 
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "metric": METRIC if args.workload == "gmm3" else
+        f"UOT Sinkhorn sweeps/s, gauss64 n=m={W.n} d={W.d} ({args.method})", "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": f"gmm3: n=m={W.n}, d=3, 5-component Gaussian mixture, eps={W.eps}, "
-                               f"rho={W.rho}", "method": args.method,
+        "config": {"workload": (f"gmm3: n=m={W.n}, d=3, 5-component Gaussian mixture, "
+                                f"eps={W.eps}, rho={W.rho}" if args.workload == "gmm3" else
+                                f"gauss64: n=m={W.n}, d={W.d}, N(0, I/64) vs N(0.1 e1, I/64), "
+                                f"eps={W.eps}, rho={W.rho}"), "method": args.method,
                    "sweeps_per_solve": W.sweeps, "step": "one full unbalanced Sinkhorn solve",
                    "l2": "flushed (512 MB write) before every timed step",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
