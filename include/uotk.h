@@ -184,6 +184,14 @@ uotk_status uotk_kernel_sum_noalloc(void* stream, int d, const float* src, int64
  *   ref = COUNTING the coupling term has no reference-mass constant).
  *   Synchronises `stream` before returning. */
 #define UOTK_WARM_START 1u
+/* flags & UOTK_LOG_DOMAIN: every half-step as a per-row log-sum-exp,
+ *   log t_i = max_j a_ij + log sum_j exp(a_ij - max_j a_ij),
+ *   a_ij = log w_j - ||x_i - y_j||^2/eps, w_j = nu_j e^{lambda gamma_j} (ref 0),
+ * so that neither the weights nor the kernel values need to be representable
+ * in FP32 (very small eps); the direct FP32 form only (UNSUPPORTED otherwise).
+ * The exponents a_ij are FP32: the relative accuracy of each term is that of
+ * an FP32 number of the size of |log w_j - M|, M = max_j lambda gamma_j. */
+#define UOTK_LOG_DOMAIN 2u
 uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d,
                               const float* x, int64_t n, const float* a,
                               const float* y, int64_t m, const float* b,

@@ -153,8 +153,9 @@ double orc_dual_value(int d, const double* x, int64_t n, const double* mu,
   for (int64_t i = 0; i < n; ++i) {
     nsum r = {0, 0};
     for (int64_t j = 0; j < m; ++j) {
-      double kij = exp(-lambda * sqdist(d, x + i * d, y + j * d));
-      double v = exp(lambda * (beta[i] + gamma[j])) * kij;
+      /* e^{lambda beta_i} k_ij e^{lambda gamma_j} as one exponential, which
+         stays finite where the factors alone would overflow or underflow */
+      double v = exp(lambda * (beta[i] + gamma[j]) - lambda * sqdist(d, x + i * d, y + j * d));
       nsum_add(&r, ref == 0 ? mu[i] * v * nu[j] : v);
     }
     row[i] = nsum_get(&r);
@@ -380,12 +381,12 @@ static void dual_grad_side(int d, const double* x, int64_t n, const double* mu,
     nsum t = {0, 0};
     nsum* g = (nsum*)calloc((size_t)d, sizeof(nsum));
     for (int64_t j = 0; j < m; ++j) {
-      double k = exp(-lambda * sqdist(d, x + i * d, y + j * d));
-      double e = exp(lambda * (beta[i] + gamma[j]));
-      nsum_add(&t, e * k * nu[j]);
+      /* ek = e^{lambda (beta_i + gamma_j)} k_ij as one exponential */
+      double ek = exp(lambda * (beta[i] + gamma[j]) - lambda * sqdist(d, x + i * d, y + j * d));
+      nsum_add(&t, ek * nu[j]);
       for (int c = 0; c < d; ++c) {
-        double dk = -2.0 * lambda * (x[i * d + c] - y[j * d + c]) * k;
-        nsum_add(&g[c], -(1.0 / lambda) * mu[i] * nu[j] * e * dk);
+        double dk = -2.0 * lambda * (x[i * d + c] - y[j * d + c]);  /* d/dx_ic k_ij / k_ij */
+        nsum_add(&g[c], -(1.0 / lambda) * mu[i] * nu[j] * ek * dk);
       }
     }
     if (gw) gw[i] = -eta * exp(-beta[i] / eta) + eta - (nsum_get(&t) - mass) / lambda;

@@ -316,6 +316,8 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x
   if (ref != UOTK_REF_PRODUCT && ref != UOTK_REF_COUNTING)
     return set_error(ctx, UOTK_ERR_INVALID, "unknown reference measure %d", ref);
   if (!(tol >= 0.0) && !(tol <= 0.0)) return set_error(ctx, UOTK_ERR_INVALID, "tol is NaN");
+  if (flags & ~(UOTK_WARM_START | UOTK_LOG_DOMAIN))
+    return set_error(ctx, UOTK_ERR_INVALID, "unknown flags 0x%x", flags);
   return op_uot_sinkhorn(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2,
                          max_sweeps, tol, ref, flags, beta, gamma, sweeps_done, value, opts);
 }

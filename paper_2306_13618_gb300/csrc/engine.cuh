@@ -17,6 +17,16 @@ struct Engine {
   // All arrays are in internal order.
   virtual uotk_status half(cudaStream_t s, int side, const float* base, const double* pot,
                            double lam, const long long* shift_slot, float* out) = 0;
+  // Log-domain half step (the direct FP32 form only): out[i] = {M_i, S_i} with
+  //   log t_i = ln2 (M_i + log2 S_i) + shift,
+  // t_i the sum of half() (same base, pot, lam and shift slot), evaluated as a
+  // per-row log-sum-exp so that no weight or kernel value has to be
+  // representable in FP32.
+  virtual uotk_status half_log(cudaStream_t s, int side, const float* base, const double* pot,
+                               double lam, const long long* shift_slot, float2* out) {
+    (void)s; (void)side; (void)base; (void)pot; (void)lam; (void)shift_slot; (void)out;
+    return UOTK_ERR_UNSUPPORTED;
+  }
   // Plain kernel sum with given internal-order weights w of the source side
   // (w = weights(src) for the caller's weights; any sign, n + 4 entries with
   // the last 4 zero): t = K(src -> tgt) w.

@@ -211,16 +211,190 @@ __global__ void k_pack(const float* __restrict__ pts, const float* __restrict__ 
   }
 }
 
-__global__ void k_set_weights(void* __restrict__ packed, long long n, int small, int dp,
-                              const float* __restrict__ base, const double* __restrict__ pot,
-                              double lam, const long long* __restrict__ shift_slot) {
+// Source weights of the packed points i < n_pad (padding rows: weight 0):
+//   LOG = false: w_i = base_i * exp(lam*pot_i - shift)    (FP32)
+//   LOG = true : w_i = log2(base_i) + (lam*pot_i - shift) log2(e)  (padding -inf)
+// shift from the ordered slot (pot NULL: no potential; base NULL: 1).
+template <bool LOG>
+__global__ void k_set_weights(void* __restrict__ packed, long long n, long long n_pad, int small,
+                              int dp, const float* __restrict__ base,
+                              const double* __restrict__ pot, double lam,
+                              const long long* __restrict__ shift_slot) {
   const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
        i += (long long)gridDim.x * blockDim.x) {
-    float v = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
-    if (base) v *= base[i];
+    float v;
+    if (i >= n) {
+      v = LOG ? -INFINITY : 0.f;
+    } else if (LOG) {
+      double lw = pot ? (lam * pot[i] - shift) * 1.4426950408889634 : 0.0;
+      if (base) lw += log2((double)base[i]);
+      v = (float)lw;
+    } else {
+      v = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
+      if (base) v *= base[i];
+    }
     if (small) reinterpret_cast<float4*>(packed)[i].w = v;
     else reinterpret_cast<float*>(packed)[i * dp + dp - 1] = v;
+  }
+}
+
+// ---- per-row log-sum-exp form (log domain) ----
+// out[j] = {M_j, S_j} with log2 sum_i 2^{lw_i - c ||s_i - t_j||^2} = M_j + log2 S_j:
+// M_j the largest exponent seen, S_j >= 1 the sum scaled by 2^{-M_j} (M = -inf,
+// S = 0 when no source contributes).  Sources carry lw = log2 of their weight
+// in the weight slot.  Exponents of a chunk of 16 sources are formed first, the
+// running sum is rescaled once per chunk when its maximum grows.
+template <int R>
+__device__ __forceinline__ void lse_fold(float (&a)[R][16], float (&M)[R], float (&hi)[R],
+                                         float (&lo)[R]) {
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    float cm = a[r][0];
+#pragma unroll
+    for (int j = 1; j < 16; ++j) cm = fmaxf(cm, a[r][j]);
+    const float mn = fmaxf(M[r], cm);
+    if (mn == -INFINITY) continue;
+    if (mn > M[r]) {
+      const float f = ex2_approx(M[r] - mn);  // 0 while M = -inf
+      hi[r] *= f;
+      lo[r] *= f;
+      M[r] = mn;
+    }
+    float acc = 0.f;
+#pragma unroll
+    for (int j = 0; j < 16; ++j) acc += ex2_approx(a[r][j] - mn);
+    neumaier(hi[r], lo[r], acc);
+  }
+}
+
+template <int D, int R>
+__global__ void __launch_bounds__(DIRECT_THREADS)
+    k_direct_lse(const float4* __restrict__ src, long long tiles, int tiles_per_split,
+                 const float4* __restrict__ tgt, long long m, float neg_c,
+                 float2* __restrict__ out, long long* __restrict__ flags) {
+  __shared__ __align__(128) float4 sm[STAGES][DIRECT_TILE];
+  __shared__ __align__(8) unsigned long long bar[STAGES];
+  const int tid = threadIdx.x;
+  const long long tb = (long long)blockIdx.x * (DIRECT_THREADS * R) + tid;
+
+  float tx[R], ty[R], tz[R], M[R], hi[R], lo[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long j = tb + (long long)r * DIRECT_THREADS;
+    const float4 p = j < m ? tgt[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    tx[r] = p.x; ty[r] = p.y; tz[r] = p.z;
+    M[r] = -INFINITY; hi[r] = 0.f; lo[r] = 0.f;
+  }
+
+  const long long t_begin = (long long)blockIdx.y * tiles_per_split;
+  const long long t_end = min(t_begin + (long long)tiles_per_split, tiles);
+  const int count = t_end > t_begin ? (int)(t_end - t_begin) : 0;
+  constexpr unsigned BYTES = DIRECT_TILE * sizeof(float4);
+
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < STAGES && s < count; ++s)
+      { mbar_expect(&bar[s], BYTES); bulk_copy(sm[s], src + (t_begin + s) * DIRECT_TILE, BYTES, &bar[s]); }
+  }
+
+  for (int k = 0; k < count; ++k) {
+    const int s = k % STAGES;
+    const bool ok = mbar_wait(&bar[s], (unsigned)(k / STAGES) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        for (int q = k; q < count && q < k + STAGES; ++q)
+          mbar_wait(&bar[q % STAGES], (unsigned)(q / STAGES) & 1u);
+      }
+      return;
+    }
+    const float4* T = sm[s];
+#pragma unroll 1
+    for (int j0 = 0; j0 < DIRECT_TILE; j0 += 16) {
+      float a[R][16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float4 q = T[j0 + j];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float dx = tx[r] - q.x;
+          float r2 = dx * dx;
+          if (D > 1) { const float dy = ty[r] - q.y; r2 = fmaf(dy, dy, r2); }
+          if (D > 2) { const float dz = tz[r] - q.z; r2 = fmaf(dz, dz, r2); }
+          a[r][j] = fmaf(r2, neg_c, q.w);
+        }
+      }
+      lse_fold<R>(a, M, hi, lo);
+    }
+    __syncthreads();
+    if (tid == 0 && k + STAGES < count)
+      { mbar_expect(&bar[s], BYTES); bulk_copy(sm[s], src + (t_begin + k + STAGES) * DIRECT_TILE, BYTES, &bar[s]); }
+  }
+
+  float2* o = out + (long long)blockIdx.y * m;
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long j = tb + (long long)r * DIRECT_THREADS;
+    if (j < m) o[j] = make_float2(M[r], hi[r] + lo[r]);
+  }
+}
+
+// General dimension, log domain (packed points of dp floats, log-weight last).
+template <int DMAX>
+__global__ void __launch_bounds__(DIRECT_THREADS)
+    k_direct_general_lse(const float* __restrict__ src, long long tiles, int tiles_per_split,
+                         const float* __restrict__ tgt, long long m, int d, int dp, float neg_c,
+                         float2* __restrict__ out) {
+  extern __shared__ float gs[];  // [GEN_TILE][dp]
+  const int tid = threadIdx.x;
+  const long long j = (long long)blockIdx.x * DIRECT_THREADS + tid;
+  float tc[DMAX];
+#pragma unroll
+  for (int t = 0; t < DMAX; ++t) tc[t] = (j < m && t < d) ? tgt[j * dp + t] : 0.f;
+  const long long t_begin = (long long)blockIdx.y * tiles_per_split;
+  const long long t_end = min(t_begin + (long long)tiles_per_split, tiles);
+  float M[1] = {-INFINITY}, hi[1] = {0.f}, lo[1] = {0.f};
+  for (long long tile = t_begin; tile < t_end; ++tile) {
+    __syncthreads();
+    const float* g = src + tile * GEN_TILE * dp;
+    for (int q = tid; q < GEN_TILE * dp; q += DIRECT_THREADS) gs[q] = g[q];
+    __syncthreads();
+    for (int i0 = 0; i0 < GEN_TILE; i0 += 16) {
+      float a[1][16];
+      for (int i = 0; i < 16; ++i) {
+        const float* p = gs + (i0 + i) * dp;
+        float r2 = 0.f;
+#pragma unroll
+        for (int t = 0; t < DMAX; ++t)
+          if (t < d) { const float u = tc[t] - p[t]; r2 = fmaf(u, u, r2); }
+        a[0][i] = fmaf(r2, neg_c, p[dp - 1]);
+      }
+      lse_fold<1>(a, M, hi, lo);
+    }
+  }
+  if (j < m) out[(long long)blockIdx.y * m + j] = make_float2(M[0], hi[0] + lo[0]);
+}
+
+// Split partials {M_k, S_k} -> {M, S}: M = max M_k, S = sum S_k 2^{M_k - M} (FP64).
+__global__ void k_reduce_splits_lse(const float2* __restrict__ part, int splits, long long m,
+                                    float2* __restrict__ out) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < m;
+       j += (long long)gridDim.x * blockDim.x) {
+    float mx = -INFINITY;
+    for (int k = 0; k < splits; ++k) mx = fmaxf(mx, part[(long long)k * m + j].x);
+    double s = 0.0;
+    if (mx > -INFINITY)
+      for (int k = 0; k < splits; ++k) {
+        const float2 v = part[(long long)k * m + j];
+        if (v.x > -INFINITY) s += (double)v.y * exp2((double)v.x - (double)mx);
+      }
+    out[j] = make_float2(mx, (float)s);
   }
 }
 
@@ -292,11 +466,16 @@ uotk_status direct_pack_targets(uotk_ctx* ctx, cudaStream_t s, const DirectLayou
 
 uotk_status direct_set_weights(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
                                void* packed, const float* base, const double* pot, double lam,
-                               const long long* shift_slot) {
+                               const long long* shift_slot, bool log2_weights) {
   if (L.n == 0) return UOTK_OK;
   UOTK_PROF(ctx, s, "weights");
-  k_set_weights<<<grid_for(ctx, L.n, 256), 256, 0, s>>>(packed, L.n, L.d <= 3, L.dp, base, pot,
-                                                        lam, shift_slot);
+  const int64_t n_pad = L.tiles * (L.d <= 3 ? DIRECT_TILE : GEN_TILE);
+  if (log2_weights)
+    k_set_weights<true><<<grid_for(ctx, n_pad, 256), 256, 0, s>>>(
+        packed, L.n, n_pad, L.d <= 3, L.dp, base, pot, lam, shift_slot);
+  else
+    k_set_weights<false><<<grid_for(ctx, n_pad, 256), 256, 0, s>>>(
+        packed, L.n, n_pad, L.d <= 3, L.dp, base, pot, lam, shift_slot);
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -348,6 +527,50 @@ uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, con
   if (L.splits > 1) {
     UOTK_PROF(ctx, s, "split_reduce");
     k_reduce_splits<<<grid_for(ctx, L.m, 256), 256, 0, s>>>(b.part, L.splits, L.m, out);
+    UOTK_LAUNCHED(ctx);
+  }
+  return UOTK_OK;
+}
+
+uotk_status direct_run_lse(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                           const DirectBufs& b, double eps, float2* out) {
+  if (L.m == 0) return UOTK_OK;
+  if (L.n == 0) return set_error(ctx, UOTK_ERR_INVALID, "log-domain sum with no sources");
+  const float neg_c = (float)(-1.4426950408889634 / eps);
+  float2* part = reinterpret_cast<float2*>(b.part);
+  float2* dst = L.splits > 1 ? part : out;
+  const dim3 grid(L.blocks_x, L.splits);
+  {
+    UOTK_PROF(ctx, s, "direct_lse");
+    if (L.d <= 3) {
+      const float4* src = reinterpret_cast<const float4*>(b.src);
+      const float4* tgt = reinterpret_cast<const float4*>(b.tgt);
+#define UOTK_LSE_CASE(DD, RR)                                                             \
+  if (L.d == DD && L.reg_targets == RR)                                                   \
+    k_direct_lse<DD, RR><<<grid, DIRECT_THREADS, 0, s>>>(src, L.tiles, L.tiles_per_split,  \
+                                                         tgt, L.m, neg_c, dst, ctx->dflags);
+      UOTK_LSE_CASE(1, 1) UOTK_LSE_CASE(1, 4) UOTK_LSE_CASE(2, 1)
+      UOTK_LSE_CASE(2, 4) UOTK_LSE_CASE(3, 1) UOTK_LSE_CASE(3, 4)
+#undef UOTK_LSE_CASE
+    } else {
+      const float* src = reinterpret_cast<const float*>(b.src);
+      const float* tgt = reinterpret_cast<const float*>(b.tgt);
+      const size_t smem = (size_t)GEN_TILE * L.dp * sizeof(float);
+#define UOTK_LSE_GEN(DM)                                                                      \
+  k_direct_general_lse<DM><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, \
+                                                               tgt, L.m, L.d, L.dp, neg_c, dst);
+      if (L.d <= 8) { UOTK_LSE_GEN(8) }
+      else if (L.d <= 16) { UOTK_LSE_GEN(16) }
+      else if (L.d <= 32) { UOTK_LSE_GEN(32) }
+      else if (L.d <= 64) { UOTK_LSE_GEN(64) }
+      else { UOTK_LSE_GEN(128) }
+#undef UOTK_LSE_GEN
+    }
+  }
+  UOTK_LAUNCHED(ctx);
+  if (L.splits > 1) {
+    UOTK_PROF(ctx, s, "split_reduce");
+    k_reduce_splits_lse<<<grid_for(ctx, L.m, 256), 256, 0, s>>>(part, L.splits, L.m, out);
     UOTK_LAUNCHED(ctx);
   }
   return UOTK_OK;

@@ -57,7 +57,8 @@ struct DirectEngine : Engine {
     size_t by = yx.src_bytes > xy.tgt_bytes ? yx.src_bytes : xy.tgt_bytes;
     void* px = cv.take<char>(bx > 0 ? bx : 16);
     void* py = cv.take<char>(by > 0 ? by : 16);
-    float* pp = part ? cv.take<float>(part / sizeof(float)) : nullptr;
+    // split partials: FP32 sums, or {M, S} pairs of the log-domain form
+    float* pp = part ? cv.take<float>(2 * part / sizeof(float)) : nullptr;
     if (e) {
       e->Lyx = yx; e->Lxy = xy; e->Lxx = xx; e->Lyy = yy;
       e->Px = px; e->Py = py; e->part = pp;
@@ -80,6 +81,15 @@ struct DirectEngine : Engine {
     UOTK_TRY(direct_set_weights(ctx, s, L, P, w, nullptr, 0.0, nullptr));
     DirectBufs bufs{P, tgt == 0 ? Px : Py, part};
     return direct_run(ctx, s, L, bufs, eps, out);
+  }
+  uotk_status half_log(cudaStream_t s, int side, const float* base, const double* pot, double lam,
+                       const long long* shift_slot, float2* out) override {
+    const DirectLayout& L = side == 0 ? Lyx : Lxy;
+    void* src = side == 0 ? Py : Px;
+    void* tgt = side == 0 ? Px : Py;
+    UOTK_TRY(direct_set_weights(ctx, s, L, src, base, pot, lam, shift_slot, true));
+    DirectBufs bufs{src, tgt, part};
+    return direct_run_lse(ctx, s, L, bufs, eps, out);
   }
   const int* perm(int) const override { return nullptr; }
   const float* weights(int side) const override { return side == 0 ? a : b; }
@@ -117,8 +127,11 @@ __device__ __forceinline__ double block_max(double v, double* sh) {
   return v;
 }
 
-// pot_i <- dual update from t_i; max of lam*pot -> *max_out; optional max |lam*change|.
-__global__ void k_dual_update(const float* __restrict__ t, const float* __restrict__ base,
+// pot_i <- dual update from the half-step sums; max of lam*pot -> *max_out;
+// optional max |lam*change|.  LOG = false: t is FP32 t_i (log t_i = log t + shift);
+// LOG = true: t is {M_i, S_i} of the log-domain form (log t_i = ln2 (M + log2 S) + shift).
+template <bool LOG>
+__global__ void k_dual_update(const void* __restrict__ t, const float* __restrict__ base,
                               long long count, double q, double lam, int ref,
                               long long* __restrict__ flags, int shift_in, int max_out,
                               int reset_slot, int delta_out, int reset_delta,
@@ -133,8 +146,16 @@ __global__ void k_dual_update(const float* __restrict__ t, const float* __restri
   long long bad = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
-    const float ti = t[i];
-    const double lt = (ti > 0.f && isfinite(ti) ? log_f32(ti) : log((double)ti)) + shift;
+    double lt;
+    if (LOG) {
+      const float2 v = reinterpret_cast<const float2*>(t)[i];
+      lt = (v.y > 0.f && isfinite(v.x) && isfinite(v.y))
+               ? ((double)v.x + log2((double)v.y)) * 0.6931471805599453 + shift
+               : (double)NAN;
+    } else {
+      const float ti = reinterpret_cast<const float*>(t)[i];
+      lt = (ti > 0.f && isfinite(ti) ? log_f32(ti) : log((double)ti)) + shift;
+    }
     const double v = ref == 0 ? -q * lt : q * (log_f32(base[i]) - lt);
     if (delta_out >= 0) dl = fmax(dl, fabs(lam * (v - pot[i])));
     pot[i] = v;
@@ -172,7 +193,7 @@ __global__ void k_sum_partials(SumTerms terms, const long long* __restrict__ fla
   __shared__ double sh[32];
   for (int q = 0; q < terms.count; ++q) {
     const SumTerm T = terms.k[q];
-    const double shift = T.kind == 3 ? ordered_to_dbl(flags[T.shift_slot]) : 0.0;
+    const double shift = T.kind >= 3 ? ordered_to_dbl(flags[T.shift_slot]) : 0.0;
     double acc = 0.0;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < T.len;
          i += (long long)gridDim.x * blockDim.x) {
@@ -181,7 +202,13 @@ __global__ void k_sum_partials(SumTerms terms, const long long* __restrict__ fla
       if (T.kind == 0) v = bi * exp(-T.pot[i] / T.eta);
       else if (T.kind == 1) v = bi;
       else if (T.kind == 2) v = bi * (double)T.t[i];
-      else v = bi * exp(T.lam * T.pot[i] + shift) * (double)T.t[i];
+      else if (T.kind == 3) v = bi * exp(T.lam * T.pot[i] + shift) * (double)T.t[i];
+      else {
+        const float2 ms = T.ms[i];
+        v = ms.y > 0.f ? bi * exp(T.lam * T.pot[i] + shift +
+                                  ((double)ms.x + log2((double)ms.y)) * 0.6931471805599453)
+                       : 0.0;
+      }
       acc += v;
     }
     acc = warp_sum(acc);
@@ -233,9 +260,14 @@ void carve_reducer(uotk_ctx* ctx, Carver& cv, Reducer& R) {
   R.out = cv.take<double>(5);
 }
 
-void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& B) {
+void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& B,
+                 bool log_domain) {
   B.tx = cv.take<float>(n > 0 ? n : 1);
   B.ty = cv.take<float>(m > 0 ? m : 1);
+  if (log_domain) {
+    B.lx = cv.take<float2>(n > 0 ? n : 1);
+    B.ly = cv.take<float2>(m > 0 ? m : 1);
+  }
   if (need_copies) {
     B.beta = cv.take<double>(n > 0 ? n : 1);
     B.gamma = cv.take<double>(m > 0 ? m : 1);
@@ -245,7 +277,7 @@ void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& 
 // Alg. 1 / Alg. 2 for up to max_sweeps sweeps on an engine, then D(beta, gamma).
 uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m, double eps,
                   double eta1, double eta2, int max_sweeps, double tol, int ref, bool warm,
-                  const SolveBufs& B, const Reducer& R, SolveResult* res) {
+                  const SolveBufs& B, const Reducer& R, SolveResult* res, bool log_domain) {
   const double lam = 1.0 / eps;
   const double q1 = eta1 / (1.0 + eta1 * lam), q2 = eta2 / (1.0 + eta2 * lam);
   const float* a = E->weights(0);
@@ -261,21 +293,29 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
   // alternate with the sweep's parity (see k_dual_update).
   auto sweep = [&](int sw) -> uotk_status {
     const int cur = sw & 1, nxt = cur ^ 1;
-    UOTK_TRY(E->half(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.tx));
+    if (log_domain)
+      UOTK_TRY(E->half_log(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.lx));
+    else
+      UOTK_TRY(E->half(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.tx));
     {
       UOTK_PROF(ctx, s, "dual_update");
-      k_dual_update<<<gu, 256, 0, s>>>(B.tx, a, n, q1, lam, ref, F, FLAG_MAX_G0 + cur,
-                                       FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt,
-                                       track ? FLAG_DELTA0 + cur : -1,
-                                       track ? FLAG_DELTA0 + nxt : -1, B.beta);
+      auto upd = log_domain ? k_dual_update<true> : k_dual_update<false>;
+      upd<<<gu, 256, 0, s>>>(log_domain ? (const void*)B.lx : (const void*)B.tx, a, n, q1, lam,
+                             ref, F, FLAG_MAX_G0 + cur, FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt,
+                             track ? FLAG_DELTA0 + cur : -1, track ? FLAG_DELTA0 + nxt : -1,
+                             B.beta);
     }
     UOTK_LAUNCHED(ctx);
-    UOTK_TRY(E->half(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ty));
+    if (log_domain)
+      UOTK_TRY(E->half_log(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ly));
+    else
+      UOTK_TRY(E->half(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ty));
     {
       UOTK_PROF(ctx, s, "dual_update");
-      k_dual_update<<<gu, 256, 0, s>>>(B.ty, b, m, q2, lam, ref, F, FLAG_MAX_B0 + cur,
-                                       FLAG_MAX_G0 + nxt, FLAG_MAX_B0 + nxt,
-                                       track ? FLAG_DELTA0 + cur : -1, -1, B.gamma);
+      auto upd = log_domain ? k_dual_update<true> : k_dual_update<false>;
+      upd<<<gu, 256, 0, s>>>(log_domain ? (const void*)B.ly : (const void*)B.ty, b, m, q2, lam,
+                             ref, F, FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt, FLAG_MAX_B0 + nxt,
+                             track ? FLAG_DELTA0 + cur : -1, -1, B.gamma);
     }
     UOTK_LAUNCHED(ctx);
     return UOTK_OK;
@@ -354,7 +394,8 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
   T.k[1] = SumTerm{0, m, b, B.gamma, nullptr, eta2, lam, 0};
   T.k[2] = SumTerm{1, n, a, nullptr, nullptr, 1.0, lam, 0};
   T.k[3] = SumTerm{1, m, b, nullptr, nullptr, 1.0, lam, 0};
-  T.k[4] = SumTerm{3, m, ref == 0 ? b : nullptr, B.gamma, B.ty, 1.0, lam, FLAG_MAX_B0 + last};
+  T.k[4] = SumTerm{log_domain ? 4 : 3, m, ref == 0 ? b : nullptr, B.gamma, B.ty, 1.0, lam,
+                   FLAG_MAX_B0 + last, B.ly};
   UOTK_TRY(run_sums(ctx, s, R, T, ctx->host + 8));
   UOTK_TRY(flags_check(ctx, s, "uot_sinkhorn"));
   const double* h = ctx->host + 8;
@@ -459,11 +500,15 @@ uotk_status op_uot_sinkhorn(uotk_ctx* ctx, cudaStream_t s, int d, const float* x
                             double* value, const uotk_sum_opts* opts) {
   EngineSpec sp{opts ? opts->method : UOTK_DIRECT, d, x, n, a, y, m, b, eps, opts};
   const bool copies = sp.method == UOTK_NFFT;
+  const bool logd = (flags & UOTK_LOG_DOMAIN) != 0;
+  if (logd && sp.method != UOTK_DIRECT)
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED,
+                     "uot_sinkhorn: the log domain is implemented for the direct FP32 form only");
   Carver size(nullptr);
   size.off = engine_bytes(ctx, sp);
   SolveBufs B;
   Reducer R;
-  carve_solve(size, n, m, copies, B);
+  carve_solve(size, n, m, copies, B, logd);
   carve_reducer(ctx, size, R);
   UOTK_TRY(ws_reserve(ctx, size.off));
   UOTK_TRY(flags_reset(ctx, s));
@@ -472,13 +517,14 @@ uotk_status op_uot_sinkhorn(uotk_ctx* ctx, cudaStream_t s, int d, const float* x
   UOTK_TRY(engine_create(ctx, s, sp, cv, &raw));
   std::unique_ptr<Engine> E(raw);
   cv.off = engine_bytes(ctx, sp);
-  carve_solve(cv, n, m, copies, B);
+  carve_solve(cv, n, m, copies, B, logd);
   carve_reducer(ctx, cv, R);
   if (!copies) { B.beta = beta; B.gamma = gamma; }
   const bool warm = (flags & UOTK_WARM_START) != 0;
   if (copies && warm) UOTK_TRY(E->from_caller(s, 1, gamma, B.gamma));
   SolveResult res;
-  UOTK_TRY(solve(ctx, s, E.get(), n, m, eps, rho1, rho2, max_sweeps, tol, ref, warm, B, R, &res));
+  UOTK_TRY(solve(ctx, s, E.get(), n, m, eps, rho1, rho2, max_sweeps, tol, ref, warm, B, R, &res,
+                 logd));
   if (copies) {
     UOTK_TRY(E->to_caller(s, 0, B.beta, beta));
     UOTK_TRY(E->to_caller(s, 1, B.gamma, gamma));

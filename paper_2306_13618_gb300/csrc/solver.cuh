@@ -11,6 +11,8 @@ namespace uotk {
 //   kind 1: sum base_i
 //   kind 2: sum base_i * t_i                     (t FP32)
 //   kind 3: sum (base_i or 1) * exp(lam*pot_i + shift) * t_i
+//   kind 4: sum (base_i or 1) * exp(lam*pot_i + shift + ln2 (M_i + log2 S_i)),
+//           {M, S} = ms_i of the log-domain form
 struct SumTerm {
   int kind;
   long long len;
@@ -19,6 +21,7 @@ struct SumTerm {
   const float* t;
   double eta, lam;
   int shift_slot;
+  const float2* ms = nullptr;
 };
 struct SumTerms {
   SumTerm k[5];
@@ -43,8 +46,11 @@ struct SolveBufs {
   double* gamma = nullptr;
   float* tx = nullptr;
   float* ty = nullptr;
+  float2* lx = nullptr;     // log-domain half-step outputs {M, S}
+  float2* ly = nullptr;
 };
-void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& B);
+void carve_solve(Carver& cv, int64_t n, int64_t m, bool need_copies, SolveBufs& B,
+                 bool log_domain = false);
 
 struct SolveResult {
   int sweeps = 0;
@@ -59,8 +65,11 @@ struct SolveResult {
 //   (ref 0; without a_i for ref 1), M_beta = max lambda*beta in flag slot
 //   FLAG_MAX_B0 + ((sweeps - 1) & 1), and M_gamma = max lambda*gamma at the
 //   final gamma in FLAG_MAX_G0 + (sweeps & 1).
+// log_domain: every half-step through Engine::half_log (per-row log-sum-exp;
+// the direct FP32 form), the dual value's coupling term from its {M, S}.
 uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m, double eps,
                   double eta1, double eta2, int max_sweeps, double tol, int ref, bool warm,
-                  const SolveBufs& B, const Reducer& R, SolveResult* res);
+                  const SolveBufs& B, const Reducer& R, SolveResult* res,
+                  bool log_domain = false);
 
 }  // namespace uotk

@@ -268,12 +268,19 @@ uotk_status direct_pack_targets(uotk_ctx* ctx, cudaStream_t s, const DirectLayou
 // Rewrite only the weights of packed sources: w_i = base_i * exp(lam*pot_i - shift),
 // shift read from the ordered-int64 slot *shift_slot (base may be NULL for 1);
 // with pot == NULL, w_i = base_i.
+// log2_weights: store log2(w_i) instead (the log-domain form; padding -inf).
 uotk_status direct_set_weights(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
                                void* packed, const float* base, const double* pot,
-                               double lam, const long long* shift_slot);
+                               double lam, const long long* shift_slot,
+                               bool log2_weights = false);
 // out[j] = sum_i w_i exp(-||s_i - t_j||^2 / eps) from packed buffers.
 uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
                        const DirectBufs& b, double eps, float* out);
+// Log domain (sources packed with log2 weights): out[j] = {M_j, S_j} with
+// log2 sum_i w_i exp(-||s_i - t_j||^2 / eps) = M_j + log2 S_j.  b.part must
+// hold splits * m float2 when L.splits > 1.
+uotk_status direct_run_lse(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
+                           const DirectBufs& b, double eps, float2* out);
 
 int grid_for(const uotk_ctx* ctx, int64_t work, int threads, int per_sm = 8);
 

@@ -21,6 +21,7 @@ UOTK_ERR_NOT_CONVERGED = 6
 DIRECT, NFFT, DIRECT_BF16, DIRECT_BF16X3 = 0, 1, 2, 3
 REF_PRODUCT, REF_COUNTING = 0, 1
 WARM_START = 1
+LOG_DOMAIN = 2
 
 _lib = None
 _lock = threading.Lock()
@@ -225,9 +226,11 @@ def kernel_sum_noalloc(src, w, tgt, eps, out):
 
 
 def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref="product",
-                 gamma0=None, method="direct", ctx=None, beta=None, gamma=None, **nfft):
+                 gamma0=None, method="direct", ctx=None, beta=None, gamma=None,
+                 log_domain=False, **nfft):
     """KL-penalised entropic UOT by Sinkhorn (uotk_uot_sinkhorn).
 
+    log_domain: per-row log-sum-exp half-steps (UOTK_LOG_DOMAIN; direct form).
     Returns (beta, gamma, sweeps_done, value, converged)."""
     x, y = _pts(x, "x"), _pts(y, "y")
     a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
@@ -241,6 +244,8 @@ def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref=
         flags |= WARM_START
     elif gamma is None:
         gamma = torch.empty(y.shape[0], device=dev, dtype=torch.float64)
+    if log_domain:
+        flags |= LOG_DOMAIN
     refc = {"product": REF_PRODUCT, "counting": REF_COUNTING}.get(ref, ref)
     sweeps = ctypes.c_int(0)
     value = _D(0.0)

@@ -212,3 +212,60 @@ def test_measure_unit_rates(uotk):
     ex2, ffma = uotk.measure_unit_rates()
     assert 8.0 <= ex2 <= 40.0, ex2
     assert 64.0 <= ffma <= 140.0, ffma
+
+
+def test_sinkhorn_log_domain_matches_oracle(uotk):
+    """UOTK_LOG_DOMAIN on the uniform box (both domains representable): the
+    same residual bar as the direct form."""
+    W = inputs.uniform_box(n=900, m=700)
+    beta, gamma, sweeps, value, _ = uotk.uot_sinkhorn(
+        dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho, max_sweeps=W.sweeps,
+        log_domain=True)
+    X, Y, A, B = f64(W.x), f64(W.y), f64(W.a), f64(W.b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=W.sweeps, logdomain=True)
+    assert residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg) <= 1e-6
+    v = oracle.dual_value(X, A, Y, B, W.eps, W.rho, W.rho, rb, rg)
+    assert abs(value - v) <= 1e-6 * abs(v)
+
+
+def test_sinkhorn_log_domain_tiny_eps(uotk):
+    """eps = 1e-4 on half-overlapping clouds: some targets see no source closer
+    than exp(-368), and the weights e^{lambda gamma - M} span e^{-460}, so the
+    FP32 form underflows (NONFINITE) while the log domain follows the FP64
+    oracle.  Bound: each half-step's log t carries the FP32 rounding of its
+    largest exponent A (in log2 units), delta = 2^-22 A ln2, amplified by at
+    most q per half-step and accumulated over the sweeps (q lambda < 1)."""
+    g = inputs.rng(77)
+    n = m = 500
+    x = g.uniform(0, 0.25, (n, 2)).astype(np.float32)
+    y = g.uniform(0.125, 0.375, (m, 2)).astype(np.float32)
+    a = np.full(n, 1.0 / n, np.float32)
+    b = np.full(m, 1.3 / m, np.float32)
+    eps, rho, S = 1e-4, 1.0, 20
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.uot_sinkhorn(dev(x), dev(a), dev(y), dev(b), eps, rho, max_sweeps=S)
+    assert e.value.status == 5
+    beta, gamma, _, value, _ = uotk.uot_sinkhorn(dev(x), dev(a), dev(y), dev(b), eps, rho,
+                                                 max_sweeps=S, log_domain=True)
+    X, Y, A, B = f64(x), f64(y), f64(a), f64(b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, eps, rho, sweeps=S, logdomain=True)
+    lam, c = 1.0 / eps, 1.4426950408889634 / eps
+    d2 = ((X[:, None, :] - Y[None, :, :]) ** 2).sum(-1)
+    spread = max(np.ptp(lam * rb), np.ptp(lam * rg)) * 1.4426950408889634
+    big = max(np.max(np.min(c * d2, 1)), np.max(np.min(c * d2, 0))) + spread
+    q = rho / (1 + rho * lam)
+    delta = 2.0 ** -22 * big * np.log(2)
+    bound = 4 * S * q * delta
+    assert np.max(np.abs(beta.cpu().numpy() - rb)) <= bound
+    assert np.max(np.abs(gamma.cpu().numpy() - rg)) <= bound
+    v = oracle.dual_value(X, A, Y, B, eps, rho, rho, rb, rg)
+    assert np.isfinite(value) and abs(value - v) <= 1e-4 * abs(v)
+
+
+def test_log_domain_rejected_off_direct(uotk):
+    W = inputs.uniform_box(n=100, m=100)
+    for method in ("nfft", "direct_bf16x3"):
+        with pytest.raises(uotk.UotkError) as e:
+            uotk.uot_sinkhorn(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho,
+                              max_sweeps=3, log_domain=True, method=method)
+        assert e.value.status == 4
