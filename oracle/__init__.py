@@ -71,6 +71,11 @@ def _load():
     lib.orc_sinkhorn_divergence.restype = ctypes.c_double
     lib.orc_balanced_sinkhorn.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
                                           ctypes.c_double, ctypes.c_int, _D, _D]
+    lib.orc_ksum_kernel.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _I64, _D,
+                                    _D, _I64, _D]
+    lib.orc_mmd2_kernel.argtypes = [ctypes.c_int, ctypes.c_double, ctypes.c_int, _D, _I64, _D,
+                                    _D, _I64, _D, _D]
+    lib.orc_mmd2_kernel.restype = ctypes.c_double
     lib.orc_mmd2_grad.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D, ctypes.c_double,
                                   _D, _D, _D, _D]
     lib.orc_mmd2_grad_rows.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
@@ -238,3 +243,25 @@ def sinkhorn_divergence_grad(x, mu, y, nu, eps, eta, sweeps=100):
                                              y.shape[0], _p(nu), 1.0 / eps, float(eta),
                                              int(sweeps), _p(ga), _p(gx), _p(gb), _p(gy))
     return v, ga, gx, gb, gy
+
+
+KERNELS = {"gauss": 0, "laplace": 1, "imq": 2, "energy": 3}
+
+
+def ksum_kernel(kind, p, src, w, tgt):
+    """out_j = sum_i w_i k(src_i, tgt_j), k one of the kernels of Table tab:0:
+    gauss exp(-r^2/p^2), laplace exp(-r/p), imq 1/sqrt(r^2 + p^2), energy -r."""
+    src, tgt, w = _pts(src), _pts(tgt), _vec(w)
+    out = np.empty(tgt.shape[0])
+    _load().orc_ksum_kernel(KERNELS[kind], float(p), src.shape[1], _p(src), src.shape[0], _p(w),
+                            _p(tgt), tgt.shape[0], _p(out))
+    return out
+
+
+def mmd2_kernel(kind, p, x, mu, y, nu, return_parts=False):
+    """MMD^2 of Eq. (1205) with a kernel of Table tab:0 (see ksum_kernel)."""
+    x, y, mu, nu = _pts(x), _pts(y), _vec(mu), _vec(nu)
+    parts = np.empty(3)
+    v = _load().orc_mmd2_kernel(KERNELS[kind], float(p), x.shape[1], _p(x), x.shape[0], _p(mu),
+                                _p(y), y.shape[0], _p(nu), _p(parts))
+    return (v, parts) if return_parts else v

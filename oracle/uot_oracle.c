@@ -456,3 +456,48 @@ double orc_sinkhorn_divergence_grad(int d, const double* x, int64_t n, const dou
   for (int64_t j = 0; j < m; ++j) gnu[j] -= dm / lambda;
   return v[0] - 0.5 * v[1] - 0.5 * v[2] + dm * dm / (2.0 * lambda);
 }
+
+/* ------------------- the other kernels of Table tab:0 -----------------------
+ * kind 0 Gauss   k = exp(-r^2 / p^2)
+ * kind 1 Laplace k = exp(-r / p)
+ * kind 2 IMQ     k = 1 / sqrt(r^2 + p^2)       (p = the constant c of the table)
+ * kind 3 energy  k = -r
+ * with r = ||x - x~||. */
+static inline double kern(int kind, double r2, double p) {
+  switch (kind) {
+    case 0: return exp(-r2 / (p * p));
+    case 1: return exp(-sqrt(r2) / p);
+    case 2: return 1.0 / sqrt(r2 + p * p);
+    default: return -sqrt(r2);
+  }
+}
+
+/* out_j = sum_i w_i k(src_i, tgt_j) for the kernel `kind` with parameter p. */
+void orc_ksum_kernel(int kind, double p, int d, const double* src, int64_t n, const double* w,
+                     const double* tgt, int64_t m, double* out) {
+#pragma omp parallel for schedule(static)
+  for (int64_t j = 0; j < m; ++j) {
+    nsum acc = {0.0, 0.0};
+    for (int64_t i = 0; i < n; ++i)
+      nsum_add(&acc, w[i] * kern(kind, sqdist(d, src + i * d, tgt + j * d), p));
+    out[j] = nsum_get(&acc);
+  }
+}
+
+/* MMD^2 of Eq. (1205) with the kernel `kind` (parameter p); parts as orc_mmd2. */
+double orc_mmd2_kernel(int kind, double p, int d, const double* x, int64_t n, const double* mu,
+                       const double* y, int64_t m, const double* nu, double* parts) {
+  double* kx = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+  double* ky = (double*)malloc(sizeof(double) * (size_t)(m > 0 ? m : 1));
+  nsum A = {0, 0}, B = {0, 0}, C = {0, 0};
+  orc_ksum_kernel(kind, p, d, x, n, mu, x, n, kx);
+  for (int64_t i = 0; i < n; ++i) nsum_add(&A, mu[i] * kx[i]);
+  orc_ksum_kernel(kind, p, d, y, m, nu, x, n, kx);
+  for (int64_t i = 0; i < n; ++i) nsum_add(&B, mu[i] * kx[i]);
+  orc_ksum_kernel(kind, p, d, y, m, nu, y, m, ky);
+  for (int64_t j = 0; j < m; ++j) nsum_add(&C, nu[j] * ky[j]);
+  free(kx);
+  free(ky);
+  if (parts) { parts[0] = nsum_get(&A); parts[1] = nsum_get(&B); parts[2] = nsum_get(&C); }
+  return nsum_get(&A) - 2.0 * nsum_get(&B) + nsum_get(&C);
+}
