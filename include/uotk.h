@@ -71,6 +71,22 @@ typedef enum {
  * q = rho/(1 + rho*lambda) in both. */
 typedef enum { UOTK_REF_PRODUCT = 0, UOTK_REF_COUNTING = 1 } uotk_ref;
 
+/* Kernels of Table tab:0, r = ||x - x~||, parameter p:
+ *   GAUSS   exp(-r^2/eps)       (the Gibbs kernel of Alg. 1/2; p^2 = eps)
+ *   LAPLACE exp(-r/p)
+ *   IMQ     1/sqrt(r^2 + p^2)   (p = the constant c of the table)
+ *   ENERGY  -r                  (p unused; any positive value)
+ * The non-Gaussian kernels are available in uotk_kernel_sum (eps = p) and
+ * uotk_mmd2 (ell = p), direct FP32 form only; every other combination returns
+ * UOTK_ERR_UNSUPPORTED (their NFFT form needs the boundary regularisation of
+ * Sec. 4, not built). */
+typedef enum {
+  UOTK_KERNEL_GAUSS = 0,
+  UOTK_KERNEL_LAPLACE = 1,
+  UOTK_KERNEL_IMQ = 2,
+  UOTK_KERNEL_ENERGY = 3
+} uotk_kernel;
+
 /* Options of one kernel summation.  A NULL pointer means all defaults. */
 typedef struct {
   int32_t method;      /* uotk_method; default UOTK_DIRECT */
@@ -79,6 +95,8 @@ typedef struct {
   int32_t cutoff;      /* NFFT: window cut-off m in [2, 8]; 0 = smallest of 6, 7, 8 meeting target_err */
   double period;       /* NFFT: torus period h; 0 = chosen from the data and eps */
   double target_err;   /* NFFT: accuracy goal, max error relative to sum|w|; 0 = 1e-6 */
+  int32_t kernel;      /* uotk_kernel; default UOTK_KERNEL_GAUSS */
+  int32_t reserved;    /* 0 */
 } uotk_sum_opts;
 
 /* Parameters of an NFFT fast summation as chosen by uotk_nfft_plan (Sec. 4).

@@ -127,6 +127,19 @@ uotk_status check_cloud(uotk_ctx* ctx, const char* what, const float* p, int64_t
   return UOTK_OK;
 }
 
+// Kernels other than the Gaussian: only in kernel_sum and mmd2, direct FP32 form.
+uotk_status check_kernel(uotk_ctx* ctx, const uotk_sum_opts* opts, bool allowed) {
+  const int kernel = opts ? opts->kernel : UOTK_KERNEL_GAUSS;
+  if (kernel < UOTK_KERNEL_GAUSS || kernel > UOTK_KERNEL_ENERGY)
+    return set_error(ctx, UOTK_ERR_INVALID, "unknown kernel %d", kernel);
+  if (kernel == UOTK_KERNEL_GAUSS) return UOTK_OK;
+  const int method = opts->method;
+  if (!allowed || method != UOTK_DIRECT)
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED,
+                     "kernel %d: only kernel_sum and mmd2 with the direct FP32 form", kernel);
+  return UOTK_OK;
+}
+
 uotk_status check_common(uotk_ctx* ctx, int d, const uotk_sum_opts* opts) {
   if (d < 1) return set_error(ctx, UOTK_ERR_INVALID, "dimension d = %d < 1", d);
   const int method = opts ? opts->method : UOTK_DIRECT;
@@ -284,6 +297,7 @@ uotk_status uotk_kernel_sum(uotk_ctx* ctx, void* stream, int d, const float* src
                             const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_kernel(ctx, opts, true));
   UOTK_TRY(check_cloud(ctx, "src", src, n, d));
   UOTK_TRY(check_cloud(ctx, "w", w, n, 1));
   UOTK_TRY(check_cloud(ctx, "tgt", tgt, m, d));
@@ -301,6 +315,7 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x
                               int* sweeps_done, double* value, const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_kernel(ctx, opts, false));
   UOTK_TRY(check_cloud(ctx, "x", x, n, d));
   UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
   UOTK_TRY(check_cloud(ctx, "y", y, m, d));
@@ -329,6 +344,7 @@ uotk_status uotk_sinkhorn_divergence(uotk_ctx* ctx, void* stream, int d, const f
                                      const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_kernel(ctx, opts, false));
   UOTK_TRY(check_cloud(ctx, "x", x, n, d));
   UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
   UOTK_TRY(check_cloud(ctx, "y", y, m, d));
@@ -348,6 +364,7 @@ uotk_status uotk_mmd2(uotk_ctx* ctx, void* stream, int d, const float* x, int64_
                       double* mmd2, double* parts, const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_kernel(ctx, opts, true));
   UOTK_TRY(check_cloud(ctx, "x", x, n, d));
   UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
   UOTK_TRY(check_cloud(ctx, "y", y, m, d));
@@ -378,6 +395,7 @@ uotk_status uotk_mmd2_grad(uotk_ctx* ctx, void* stream, int d, const float* x, i
                            double* grad_y, const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_kernel(ctx, opts, false));
   UOTK_TRY(check_cloud(ctx, "x", x, n, d));
   UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
   UOTK_TRY(check_cloud(ctx, "y", y, m, d));
@@ -398,6 +416,7 @@ uotk_status uotk_sinkhorn_divergence_grad(uotk_ctx* ctx, void* stream, int d, co
                                           const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_kernel(ctx, opts, false));
   UOTK_TRY(check_cloud(ctx, "x", x, n, d));
   UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
   UOTK_TRY(check_cloud(ctx, "y", y, m, d));

@@ -27,17 +27,40 @@ namespace {
 constexpr int STAGES = 3;
 constexpr int GEN_TILE = 64;  // sources per tile on the general-d path
 
+// Kernel value of a pair from its squared distance r2 (Table tab:0):
+//   KIND 0 Gauss   2^{c0 r2}            c0 = -log2(e)/eps
+//   KIND 1 Laplace 2^{c0 sqrt(r2)}      c0 = -log2(e)/ell
+//   KIND 2 IMQ     1/sqrt(r2 + c1)      c1 = c^2
+//   KIND 3 energy  -sqrt(r2)
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float y;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float y;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+template <int KIND>
+__device__ __forceinline__ float kpair(float r2, float c0, float c1) {
+  if (KIND == 0) return ex2_approx(r2 * c0);
+  if (KIND == 1) return ex2_approx(sqrt_approx(r2) * c0);
+  if (KIND == 2) return rsqrt_approx(r2 + c1);
+  return -sqrt_approx(r2);
+}
+
 __device__ __forceinline__ void neumaier(float& hi, float& lo, float v) {
   const float t = hi + v;
   lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
   hi = t;
 }
 
-template <int D, int R>
+template <int D, int R, int KIND = 0>
 __global__ void __launch_bounds__(DIRECT_THREADS)
     k_direct_small(const float4* __restrict__ src, long long tiles, int tiles_per_split,
                    const float4* __restrict__ tgt, long long m, float neg_c,
-                   float* __restrict__ out, long long* __restrict__ flags) {
+                   float* __restrict__ out, long long* __restrict__ flags, float c1 = 0.f) {
   __shared__ __align__(128) float4 sm[STAGES][DIRECT_TILE];
   __shared__ __align__(8) unsigned long long bar[STAGES];
   const int tid = threadIdx.x;
@@ -96,7 +119,7 @@ __global__ void __launch_bounds__(DIRECT_THREADS)
           float r2 = dx * dx;
           if (D > 1) { const float dy = ty[r] - q.y; r2 = fmaf(dy, dy, r2); }
           if (D > 2) { const float dz = tz[r] - q.z; r2 = fmaf(dz, dz, r2); }
-          acc[r] = fmaf(q.w, ex2_approx(r2 * neg_c), acc[r]);
+          acc[r] = fmaf(q.w, kpair<KIND>(r2, neg_c, c1), acc[r]);
         }
       }
 #pragma unroll
@@ -116,11 +139,11 @@ __global__ void __launch_bounds__(DIRECT_THREADS)
 }
 
 // General dimension: packed points of dp floats (coordinates, zeros, weight last).
-template <int DMAX>
+template <int DMAX, int KIND = 0>
 __global__ void __launch_bounds__(DIRECT_THREADS)
     k_direct_general(const float* __restrict__ src, long long tiles, int tiles_per_split,
                      const float* __restrict__ tgt, long long m, int d, int dp, float neg_c,
-                     float* __restrict__ out) {
+                     float* __restrict__ out, float c1 = 0.f) {
   extern __shared__ float gs[];  // [GEN_TILE][dp]
   const int tid = threadIdx.x;
   const long long j = (long long)blockIdx.x * DIRECT_THREADS + tid;
@@ -143,7 +166,7 @@ __global__ void __launch_bounds__(DIRECT_THREADS)
 #pragma unroll
         for (int t = 0; t < DMAX; ++t)
           if (t < d) { const float u = tc[t] - p[t]; r2 = fmaf(u, u, r2); }
-        acc = fmaf(p[dp - 1], ex2_approx(r2 * neg_c), acc);
+        acc = fmaf(p[dp - 1], kpair<KIND>(r2, neg_c, c1), acc);
       }
       neumaier(hi, lo, acc);
     }
@@ -480,25 +503,17 @@ uotk_status direct_set_weights(uotk_ctx* ctx, cudaStream_t s, const DirectLayout
   return UOTK_OK;
 }
 
-uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, const DirectBufs& b,
-                       double eps, float* out) {
-  if (L.m == 0) return UOTK_OK;
-  if (L.n == 0) {
-    UOTK_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(float) * L.m, s));
-    return UOTK_OK;
-  }
-  const float neg_c = (float)(-1.4426950408889634 / eps);
-  float* dst = L.splits > 1 ? b.part : out;
+template <int KIND>
+void direct_launch(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, const DirectBufs& b,
+                   float c0, float c1, float* dst) {
   const dim3 grid(L.blocks_x, L.splits);
-  {
-  UOTK_PROF(ctx, s, "direct");
   if (L.d <= 3) {
     const float4* src = reinterpret_cast<const float4*>(b.src);
     const float4* tgt = reinterpret_cast<const float4*>(b.tgt);
 #define UOTK_DIRECT_CASE(DD, RR)                                                          \
   if (L.d == DD && L.reg_targets == RR)                                                   \
-    k_direct_small<DD, RR><<<grid, DIRECT_THREADS, 0, s>>>(src, L.tiles, L.tiles_per_split, \
-                                                           tgt, L.m, neg_c, dst, ctx->dflags);
+    k_direct_small<DD, RR, KIND><<<grid, DIRECT_THREADS, 0, s>>>(                         \
+        src, L.tiles, L.tiles_per_split, tgt, L.m, c0, dst, ctx->dflags, c1);
     UOTK_DIRECT_CASE(1, 1) UOTK_DIRECT_CASE(1, 4) UOTK_DIRECT_CASE(2, 1)
     UOTK_DIRECT_CASE(2, 4) UOTK_DIRECT_CASE(3, 1) UOTK_DIRECT_CASE(3, 4)
 #undef UOTK_DIRECT_CASE
@@ -506,22 +521,37 @@ uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, con
     const float* src = reinterpret_cast<const float*>(b.src);
     const float* tgt = reinterpret_cast<const float*>(b.tgt);
     const size_t smem = (size_t)GEN_TILE * L.dp * sizeof(float);
-    if (L.d <= 8)
-      k_direct_general<8><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
-                                                             L.m, L.d, L.dp, neg_c, dst);
-    else if (L.d <= 16)
-      k_direct_general<16><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
-                                                              L.m, L.d, L.dp, neg_c, dst);
-    else if (L.d <= 32)
-      k_direct_general<32><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
-                                                              L.m, L.d, L.dp, neg_c, dst);
-    else if (L.d <= 64)
-      k_direct_general<64><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, tgt,
-                                                              L.m, L.d, L.dp, neg_c, dst);
-    else
-      k_direct_general<128><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split,
-                                                               tgt, L.m, L.d, L.dp, neg_c, dst);
+#define UOTK_DIRECT_GEN(DM)                                                                   \
+  k_direct_general<DM, KIND><<<grid, DIRECT_THREADS, smem, s>>>(src, L.tiles, L.tiles_per_split, \
+                                                                 tgt, L.m, L.d, L.dp, c0, dst, c1);
+    if (L.d <= 8) { UOTK_DIRECT_GEN(8) }
+    else if (L.d <= 16) { UOTK_DIRECT_GEN(16) }
+    else if (L.d <= 32) { UOTK_DIRECT_GEN(32) }
+    else if (L.d <= 64) { UOTK_DIRECT_GEN(64) }
+    else { UOTK_DIRECT_GEN(128) }
+#undef UOTK_DIRECT_GEN
   }
+}
+
+uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, const DirectBufs& b,
+                       double eps, float* out, int kernel) {
+  if (L.m == 0) return UOTK_OK;
+  if (L.n == 0) {
+    UOTK_CUDA(ctx, cudaMemsetAsync(out, 0, sizeof(float) * L.m, s));
+    return UOTK_OK;
+  }
+  // eps: the Gaussian width, or the parameter p of the other kernels
+  const float c0 = (float)(-1.4426950408889634 / eps);
+  const float c1 = (float)(eps * eps);
+  float* dst = L.splits > 1 ? b.part : out;
+  {
+    UOTK_PROF(ctx, s, "direct");
+    switch (kernel) {
+      case UOTK_KERNEL_LAPLACE: direct_launch<1>(ctx, s, L, b, c0, c1, dst); break;
+      case UOTK_KERNEL_IMQ: direct_launch<2>(ctx, s, L, b, c0, c1, dst); break;
+      case UOTK_KERNEL_ENERGY: direct_launch<3>(ctx, s, L, b, c0, c1, dst); break;
+      default: direct_launch<0>(ctx, s, L, b, c0, c1, dst); break;
+    }
   }
   UOTK_LAUNCHED(ctx);
   if (L.splits > 1) {

@@ -34,7 +34,8 @@ struct DirectEngine : Engine {
   int64_t n = 0, m = 0;
   const float* a = nullptr;
   const float* b = nullptr;
-  double eps = 1.0;
+  double eps = 1.0;   // Gaussian width, or the parameter p of another kernel
+  int kernel = UOTK_KERNEL_GAUSS;
   DirectLayout Lyx, Lxy, Lxx, Lyy;  // src -> tgt
   void* Px = nullptr;  // X packed as sources (weights a), also read as targets
   void* Py = nullptr;
@@ -80,7 +81,7 @@ struct DirectEngine : Engine {
     // the packed sources carry their current weights; rewrite them from w
     UOTK_TRY(direct_set_weights(ctx, s, L, P, w, nullptr, 0.0, nullptr));
     DirectBufs bufs{P, tgt == 0 ? Px : Py, part};
-    return direct_run(ctx, s, L, bufs, eps, out);
+    return direct_run(ctx, s, L, bufs, eps, out, kernel);
   }
   uotk_status half_log(cudaStream_t s, int side, const float* base, const double* pot, double lam,
                        const long long* shift_slot, float2* out) override {
@@ -428,6 +429,7 @@ uotk_status engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, C
   std::unique_ptr<DirectEngine> e(new DirectEngine());
   e->ctx = ctx; e->d = sp.d; e->n = sp.n; e->m = sp.m; e->a = sp.a; e->b = sp.b;
   e->eps = sp.eps;
+  e->kernel = sp.opts ? sp.opts->kernel : UOTK_KERNEL_GAUSS;
   DirectEngine::carve(ctx, sp, cv, e.get());
   UOTK_TRY(direct_pack_sources(ctx, s, e->Lxy, sp.x, sp.a, e->Px));
   UOTK_TRY(direct_pack_sources(ctx, s, e->Lyx, sp.y, sp.b, e->Py));
@@ -597,7 +599,10 @@ uotk_status op_sinkhorn_divergence(uotk_ctx* ctx, cudaStream_t s, int d, const f
 uotk_status op_mmd2(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
                     const float* a, const float* y, int64_t m, const float* b, double ell,
                     double* mmd2, double* parts, const uotk_sum_opts* opts) {
-  EngineSpec sp{opts ? opts->method : UOTK_DIRECT, d, x, n, a, y, m, b, ell * ell, opts};
+  // the Gaussian of Eq. (1205) has width eps = ell^2; the other kernels take ell as p
+  const int kernel = opts ? opts->kernel : UOTK_KERNEL_GAUSS;
+  EngineSpec sp{opts ? opts->method : UOTK_DIRECT, d, x, n, a, y, m, b,
+                kernel == UOTK_KERNEL_GAUSS ? ell * ell : ell, opts};
   Carver size(nullptr);
   size.off = engine_bytes(ctx, sp);
   size.take<float>(2 * (n > 0 ? n : 1) + (m > 0 ? m : 1));

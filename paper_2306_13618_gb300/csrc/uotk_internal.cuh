@@ -274,8 +274,9 @@ uotk_status direct_set_weights(uotk_ctx* ctx, cudaStream_t s, const DirectLayout
                                double lam, const long long* shift_slot,
                                bool log2_weights = false);
 // out[j] = sum_i w_i exp(-||s_i - t_j||^2 / eps) from packed buffers.
+// kernel: uotk_kernel (Table tab:0); eps is then the kernel's parameter p.
 uotk_status direct_run(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
-                       const DirectBufs& b, double eps, float* out);
+                       const DirectBufs& b, double eps, float* out, int kernel = 0);
 // Log domain (sources packed with log2 weights): out[j] = {M_j, S_j} with
 // log2 sum_i w_i exp(-||s_i - t_j||^2 / eps) = M_j + log2 S_j.  b.part must
 // hold splits * m float2 when L.splits > 1.

@@ -36,7 +36,11 @@ class UotkError(RuntimeError):
 class SumOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("bandwidth", ctypes.c_int32), ("cutoff", ctypes.c_int32),
-                ("period", ctypes.c_double), ("target_err", ctypes.c_double)]
+                ("period", ctypes.c_double), ("target_err", ctypes.c_double),
+                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+KERNELS = {"gauss": 0, "laplace": 1, "imq": 2, "energy": 3}
 
 
 class NfftPlan(ctypes.Structure):
@@ -192,10 +196,14 @@ def _pts(t, name):
     return t
 
 
-def _opts(method="direct", grid=0, bandwidth=0, cutoff=0, period=0.0, target_err=0.0):
+def _opts(method="direct", grid=0, bandwidth=0, cutoff=0, period=0.0, target_err=0.0,
+          kernel="gauss"):
+    """uotk_sum_opts; kernel is one of Table tab:0 (gauss, laplace, imq, energy)."""
     m = {"direct": DIRECT, "nfft": NFFT, "direct_bf16": DIRECT_BF16,
          "direct_bf16x3": DIRECT_BF16X3}.get(method, method)
-    return SumOpts(int(m), int(grid), int(bandwidth), int(cutoff), float(period), float(target_err))
+    k = KERNELS.get(kernel, kernel)
+    return SumOpts(int(m), int(grid), int(bandwidth), int(cutoff), float(period),
+                   float(target_err), int(k), 0)
 
 
 def _ptr(t):
@@ -203,7 +211,8 @@ def _ptr(t):
 
 
 def kernel_sum(src, w, tgt, eps, method="direct", out=None, ctx=None, **nfft):
-    """out_j = sum_i w_i exp(-||src_i - tgt_j||^2/eps) (uotk_kernel_sum)."""
+    """out_j = sum_i w_i exp(-||src_i - tgt_j||^2/eps) (uotk_kernel_sum); with
+    kernel="laplace" / "imq" / "energy" the kernel of Table tab:0 with p = eps."""
     src, tgt, w = _pts(src, "src"), _pts(tgt, "tgt"), _f32(w, "w").reshape(-1)
     ctx = ctx or default_context()
     if out is None:
@@ -275,7 +284,9 @@ def sinkhorn_divergence(x, a, y, b, eps, rho, max_sweeps=100, tol=0.0, method="d
 
 
 def mmd2(x, a, y, b, ell, method="direct", ctx=None, **nfft):
-    """MMD^2 of Eq. (1205), Gaussian kernel exp(-d^2/ell^2); returns (value, [A, B, C])."""
+    """MMD^2 of Eq. (1205), Gaussian kernel exp(-d^2/ell^2), or with kernel=
+    "laplace" / "imq" / "energy" the kernel of Table tab:0 with p = ell;
+    returns (value, [A, B, C])."""
     x, y = _pts(x, "x"), _pts(y, "y")
     a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
     ctx = ctx or default_context()
