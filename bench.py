@@ -354,6 +354,37 @@ def high_dim_extras(uotk, ctx, stream, rates, sms, peaks):
     return res
 
 
+def other_kernel_extras(uotk, ctx, stream, W, x, b, y):
+    """The other kernels of Table tab:0 (direct FP32 form) on the same 2^20-point
+    clouds: one kernel sum each, pairs/s and the error on 256 sampled targets."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2306_13618_gb300 import inputs
+
+    idx = inputs.subsample_rows(inputs.rng(14), 256, W.n)
+    Y, B, X = W.y.astype(np.float64), W.b.astype(np.float64), W.x[idx].astype(np.float64)
+    res = {}
+    for kind, p in (("laplace", 0.2), ("imq", 0.2), ("energy", 1.0)):
+        try:
+            uotk.kernel_sum(y, b, x[:1024], p, kernel=kind, ctx=ctx)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = uotk.kernel_sum(y, b, x, p, kernel=kind, ctx=ctx)
+            e1.record(stream)
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            ref = oracle.ksum_kernel(kind, p, Y, B, X)
+            o = out.cpu().numpy()[idx].astype(np.float64)
+            res[kind] = {"p": p, "ms_per_sum": ms, "pairs_per_s": W.n * W.m / (ms / 1e3),
+                         "rel_err_max": float(np.max(np.abs(o - ref) / np.abs(ref)))}
+        except uotk.UotkError as e:
+            res[kind] = {"error": str(e)}
+    return res
+
+
 def main():
     args = parse()
     rank, world, local = dist_env()
@@ -495,6 +526,7 @@ def main():
                 extras[meth] = {"error": str(e)}
         extras["gradients"] = gradient_extras(uotk, ctx, stream, W, x, a, y, b, args.method)
         extras["gauss64"] = high_dim_extras(uotk, ctx, stream, rates, sms, peaks)
+        extras["other_kernels"] = other_kernel_extras(uotk, ctx, stream, W, x, b, y)
     if "nfft" in extras and "direct" in extras and "ms_per_matvec" in extras.get("direct", {}) \
             and "ms_per_matvec" in extras.get("nfft", {}):
         extras["nfft_speedup_vs_direct"] = extras["direct"]["ms_per_matvec"] / extras["nfft"]["ms_per_matvec"]
