@@ -218,6 +218,31 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d,
                               double* beta, double* gamma, int* sweeps_done,
                               double* value, const uotk_sum_opts* opts);
 
+/* ---- many independent problems at once (batched Alg. 1, direct form) -------------
+ * npairs problems (x^p, a^p; y^p, b^p) of uneven sizes, each with its own eps_p,
+ * rho1_p, rho2_p, all solved by Alg. 1 together: every half-step of every pair is
+ * one grouped launch, two sweeps are replayed from one CUDA graph, and pairs that
+ * meet tol (tested every 10 sweeps, as in uotk_uot_sinkhorn) are retired while
+ * the others continue.
+ *   x_off, y_off: host int64 [npairs + 1], nondecreasing; pair p owns points
+ *     x_off[p] .. x_off[p+1]-1 of x (device FP32 [.*d], row-major) and of a,
+ *     and likewise y, b; every pair needs at least one point on each side.
+ *   eps, rho1, rho2: host double [npairs], finite and > 0.
+ *   beta, gamma: device FP64, indexed like a and b (gamma^0 = 0; output the
+ *     final duals of each pair).
+ *   sweeps_done (host int [npairs], may be NULL): sweeps run per pair;
+ *   values (host double [npairs], may be NULL): D(beta, gamma) per pair.
+ *   d in 1..3; opts (may be NULL) must select the direct form.
+ *   Returns UOTK_ERR_NOT_CONVERGED if tol > 0 and some pair did not reach it
+ *   (outputs valid).  Synchronises `stream`. */
+uotk_status uotk_uot_sinkhorn_batch(uotk_ctx* ctx, void* stream, int d, int npairs,
+                                    const int64_t* x_off, const float* x, const float* a,
+                                    const int64_t* y_off, const float* y, const float* b,
+                                    const double* eps, const double* rho1, const double* rho2,
+                                    int max_sweeps, double tol, int ref, double* beta,
+                                    double* gamma, int* sweeps_done, double* values,
+                                    const uotk_sum_opts* opts);
+
 /* ---- unbalanced Sinkhorn divergence, Eq. (586) ---------------------------------------
  * sd = UOT(mu,nu) - UOT(mu,mu)/2 - UOT(nu,nu)/2 + (mu(X) - nu(X))^2 * eps/2,
  * each UOT value being D(beta, gamma) after max_sweeps sweeps (or tol, as

@@ -23,6 +23,10 @@ uotk_status op_mmd2(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const f
                     const float*, int64_t, const float*, double, double*, double*,
                     const uotk_sum_opts*);
 uotk_status op_measure_unit_rates(uotk_ctx*, cudaStream_t, double*, double*);
+uotk_status op_uot_sinkhorn_batch(uotk_ctx*, cudaStream_t, int, int, const int64_t*,
+                                  const float*, const float*, const int64_t*, const float*,
+                                  const float*, const double*, const double*, const double*, int,
+                                  double, int, double*, double*, int*, double*);
 uotk_status op_mmd2_grad(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
                          const float*, int64_t, const float*, double, double*, double*, double*,
                          double*, double*, const uotk_sum_opts*);
@@ -335,6 +339,50 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x
     return set_error(ctx, UOTK_ERR_INVALID, "unknown flags 0x%x", flags);
   return op_uot_sinkhorn(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2,
                          max_sweeps, tol, ref, flags, beta, gamma, sweeps_done, value, opts);
+}
+
+uotk_status uotk_uot_sinkhorn_batch(uotk_ctx* ctx, void* stream, int d, int npairs,
+                                    const int64_t* x_off, const float* x, const float* a,
+                                    const int64_t* y_off, const float* y, const float* b,
+                                    const double* eps, const double* rho1, const double* rho2,
+                                    int max_sweeps, double tol, int ref, double* beta,
+                                    double* gamma, int* sweeps_done, double* values,
+                                    const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_common(ctx, d, opts));
+  UOTK_TRY(check_kernel(ctx, opts, false));
+  if ((opts ? opts->method : UOTK_DIRECT) != UOTK_DIRECT)
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED, "uot_sinkhorn_batch: direct FP32 form only");
+  if (d > 3) return set_error(ctx, UOTK_ERR_UNSUPPORTED, "uot_sinkhorn_batch: d = %d > 3", d);
+  if (npairs < 1 || npairs > (1 << 20))
+    return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn_batch: npairs %d outside [1, 2^20]",
+                     npairs);
+  if (!x_off || !y_off || !eps || !rho1 || !rho2)
+    return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn_batch: null host array");
+  if (x_off[0] < 0 || y_off[0] < 0)
+    return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn_batch: negative offset");
+  for (int p = 0; p < npairs; ++p) {
+    if (x_off[p + 1] <= x_off[p] || y_off[p + 1] <= y_off[p])
+      return set_error(ctx, UOTK_ERR_INVALID,
+                       "uot_sinkhorn_batch: pair %d has an empty side or decreasing offsets", p);
+    if (!(eps[p] > 0.0) || !isfinite(eps[p]) || !(rho1[p] > 0.0) || !isfinite(rho1[p]) ||
+        !(rho2[p] > 0.0) || !isfinite(rho2[p]))
+      return set_error(ctx, UOTK_ERR_INVALID,
+                       "uot_sinkhorn_batch: pair %d: eps and rho must be finite and > 0", p);
+  }
+  UOTK_TRY(check_cloud(ctx, "x", x, x_off[npairs], d));
+  UOTK_TRY(check_cloud(ctx, "a", a, x_off[npairs], 1));
+  UOTK_TRY(check_cloud(ctx, "y", y, y_off[npairs], d));
+  UOTK_TRY(check_cloud(ctx, "b", b, y_off[npairs], 1));
+  if (!beta || !gamma || !aligned(beta, 8) || !aligned(gamma, 8))
+    return set_error(ctx, UOTK_ERR_INVALID, "beta/gamma null or not 8-byte aligned");
+  if (max_sweeps < 1) return set_error(ctx, UOTK_ERR_INVALID, "max_sweeps must be >= 1");
+  if (ref != UOTK_REF_PRODUCT && ref != UOTK_REF_COUNTING)
+    return set_error(ctx, UOTK_ERR_INVALID, "unknown reference measure %d", ref);
+  if (!(tol >= 0.0) && !(tol <= 0.0)) return set_error(ctx, UOTK_ERR_INVALID, "tol is NaN");
+  return op_uot_sinkhorn_batch(ctx, (cudaStream_t)stream, d, npairs, x_off, x, a, y_off, y, b,
+                               eps, rho1, rho2, max_sweeps, tol, ref, beta, gamma, sweeps_done,
+                               values);
 }
 
 uotk_status uotk_sinkhorn_divergence(uotk_ctx* ctx, void* stream, int d, const float* x,

@@ -20,6 +20,11 @@ Workloads (shapes and distributions of the measured configurations):
   an independent draw of N(0.1 e_1, I/64) (the same cloud shifted by 0.1 along
   the first axis); uniform weights with masses 1.0 and 1.2; eps = 1, rho = 2.
   The high-dimensional case of the direct form.
+* ``pair_batch`` -- many independent problems of uneven sizes: per pair, n and
+  m log-uniform in [1024, 65536], both clouds uniform in one ball of radius 0.2
+  whose centre is uniform in [-1, 1]^3, weights uniform in [0.5, 1.5]
+  normalised to masses uniform in [0.5, 2], eps in {0.01, 0.05} and rho in
+  {0.1, 1, 10} drawn per pair.
 * ``paper_uniform`` -- the paper's own synthetic measures (Sec. 5.1.1): points and
   weights i.i.d. uniform on [0, 1] (unnormalised).
 """
@@ -100,6 +105,59 @@ def gauss64(seed: int = 3000, n: int = 262144, m: int = 262144, d: int = 64) -> 
     a = np.full(n, 1.0 / n, dtype=np.float32)
     b = np.full(m, 1.2 / m, dtype=np.float32)
     return Workload("gauss64", x, a, y, b, eps=1.0, rho=2.0, sweeps=100, ell=1.0)
+
+
+@dataclass
+class PairBatch:
+    x: np.ndarray          # (sum n_p, d) float32, pairs concatenated
+    a: np.ndarray
+    x_off: np.ndarray      # (npairs + 1,) int64
+    y: np.ndarray
+    b: np.ndarray
+    y_off: np.ndarray
+    eps: np.ndarray        # (npairs,) float64
+    rho: np.ndarray        # (npairs,) float64
+
+    @property
+    def npairs(self):
+        return self.x_off.size - 1
+
+    def pair(self, p):
+        """(x, a, y, b, eps, rho) of pair p."""
+        xs = slice(self.x_off[p], self.x_off[p + 1])
+        ys = slice(self.y_off[p], self.y_off[p + 1])
+        return self.x[xs], self.a[xs], self.y[ys], self.b[ys], self.eps[p], self.rho[p]
+
+
+def _ball(g: np.random.Generator, count: int, centre: np.ndarray, radius: float) -> np.ndarray:
+    d = centre.size
+    v = g.standard_normal((count, d))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    r = radius * g.uniform(0.0, 1.0, count) ** (1.0 / d)
+    return (centre + v * r[:, None]).astype(np.float32)
+
+
+def pair_batch(seed: int = 4000, npairs: int = 512, nmin: int = 1024, nmax: int = 65536,
+               d: int = 3, eps_choices=(0.01, 0.05), rho_choices=(0.1, 1.0, 10.0)) -> PairBatch:
+    g = rng(seed)
+    xs, as_, ys, bs = [], [], [], []
+    x_off, y_off = [0], [0]
+    eps = np.empty(npairs)
+    rho = np.empty(npairs)
+    for p in range(npairs):
+        n, m = (int(round(np.exp(g.uniform(np.log(nmin), np.log(nmax))))) for _ in range(2))
+        centre = g.uniform(-1.0, 1.0, d)
+        xs.append(_ball(g, n, centre, 0.2))
+        ys.append(_ball(g, m, centre, 0.2))
+        as_.append(_normalise(g.uniform(0.5, 1.5, n), g.uniform(0.5, 2.0)))
+        bs.append(_normalise(g.uniform(0.5, 1.5, m), g.uniform(0.5, 2.0)))
+        x_off.append(x_off[-1] + n)
+        y_off.append(y_off[-1] + m)
+        eps[p] = eps_choices[g.integers(0, len(eps_choices))]
+        rho[p] = rho_choices[g.integers(0, len(rho_choices))]
+    return PairBatch(np.concatenate(xs), np.concatenate(as_), np.asarray(x_off, np.int64),
+                     np.concatenate(ys), np.concatenate(bs), np.asarray(y_off, np.int64),
+                     eps, rho)
 
 
 def paper_uniform(seed: int = 3000, n: int = 1000, d: int = 3, eps: float = 0.05,

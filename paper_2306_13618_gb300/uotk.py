@@ -96,6 +96,9 @@ def lib():
                                                ctypes.POINTER(_D), opts]
         L.uotk_mmd2.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                 ctypes.POINTER(_D), ctypes.POINTER(_D), opts]
+        L.uotk_uot_sinkhorn_batch.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
+                                              _P, _P, _P, _P, _P, _P, ctypes.c_int, _D,
+                                              ctypes.c_int, _P, _P, _P, _P, opts]
         L.uotk_measure_unit_rates.argtypes = [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]
         L.uotk_mmd2_grad.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                      ctypes.POINTER(_D), _P, _P, _P, _P, opts]
@@ -110,7 +113,8 @@ def lib():
         L.uotk_nfft_gather.argtypes = [_P, _P, plan, _P, _P, _I64, _P]
         for name in ("uotk_create", "uotk_kernel_sum", "uotk_uot_sinkhorn",
                      "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
-                     "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates", "uotk_nfft_plan",
+                     "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
+                     "uotk_uot_sinkhorn_batch", "uotk_nfft_plan",
                      "uotk_nfft_cells", "uotk_nfft_spread", "uotk_nfft_convolve",
                      "uotk_nfft_gather"):
             getattr(L, name).restype = ctypes.c_int
@@ -265,6 +269,38 @@ def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref=
         flags, _ptr(beta), _ptr(gamma), ctypes.byref(sweeps), ctypes.byref(value),
         ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
     return beta, gamma, sweeps.value, value.value, st == UOTK_OK
+
+
+def uot_sinkhorn_batch(x, a, x_off, y, b, y_off, eps, rho1, rho2=None, max_sweeps=100, tol=0.0,
+                       ref="product", ctx=None):
+    """Many independent problems at once (uotk_uot_sinkhorn_batch).
+
+    x, a, y, b: concatenated CUDA tensors; x_off, y_off: host sequences of
+    npairs + 1 offsets; eps, rho1, rho2: per-pair sequences (or scalars).
+    Returns (beta, gamma, sweeps_done[npairs], values[npairs], converged)."""
+    import numpy as np
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    ctx = ctx or default_context()
+    xo = np.ascontiguousarray(np.asarray(x_off, dtype=np.int64))
+    yo = np.ascontiguousarray(np.asarray(y_off, dtype=np.int64))
+    npairs = xo.size - 1
+    def per_pair(v):
+        return np.ascontiguousarray(np.broadcast_to(np.asarray(v, dtype=np.float64), (npairs,)))
+    e, r1 = per_pair(eps), per_pair(rho1)
+    r2 = per_pair(rho1 if rho2 is None else rho2)
+    beta = torch.empty(x.shape[0], device=x.device, dtype=torch.float64)
+    gamma = torch.empty(y.shape[0], device=x.device, dtype=torch.float64)
+    sweeps = np.zeros(npairs, dtype=np.int32)
+    values = np.zeros(npairs, dtype=np.float64)
+    refc = {"product": REF_PRODUCT, "counting": REF_COUNTING}.get(ref, ref)
+    o = _opts("direct")
+    st = ctx.check(lib().uotk_uot_sinkhorn_batch(
+        ctx.handle, _stream(), x.shape[1], npairs, xo.ctypes.data, _ptr(x), _ptr(a),
+        yo.ctypes.data, _ptr(y), _ptr(b), e.ctypes.data, r1.ctypes.data, r2.ctypes.data,
+        int(max_sweeps), float(tol), int(refc), _ptr(beta), _ptr(gamma), sweeps.ctypes.data,
+        values.ctypes.data, ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
+    return beta, gamma, sweeps, values, st == UOTK_OK
 
 
 def sinkhorn_divergence(x, a, y, b, eps, rho, max_sweeps=100, tol=0.0, method="direct",
@@ -451,6 +487,6 @@ EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_strin
             "uotk_launch_count", "uotk_set_profiling", "uotk_profile_read", "uotk_profile_reset",
             "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
-            "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates", "uotk_nfft_plan",
-            "uotk_nfft_cells",
+            "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
+            "uotk_uot_sinkhorn_batch", "uotk_nfft_plan", "uotk_nfft_cells",
             "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]

@@ -1,0 +1,106 @@
+"""GPU parity of the batched solver (uotk_uot_sinkhorn_batch) against the FP64
+oracle, pair by pair, through the C ABI.
+
+Every pair runs the same Alg. 1 as uotk_uot_sinkhorn with the direct form, so
+each is held to the direct form's bar: the paper's dual residual <= 1e-6
+(Table Tab:Accuracy_analysis2) after the same number of sweeps, and the dual
+value to 1e-6 relative."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2306_13618_gb300 import inputs
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def uotk():
+    from paper_2306_13618_gb300 import build, uotk
+    build.build()
+    return uotk
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def f64(a):
+    return np.asarray(a, dtype=np.float64)
+
+
+def residual(b, g, rb, rg):
+    return (np.linalg.norm(b - rb) / np.linalg.norm(rb)
+            + np.linalg.norm(g - rg) / np.linalg.norm(rg))
+
+
+def run(uotk, B, **kw):
+    return uotk.uot_sinkhorn_batch(dev(B.x), dev(B.a), B.x_off, dev(B.y), dev(B.b), B.y_off,
+                                   B.eps, B.rho, **kw)
+
+
+def check_pairs(B, beta, gamma, sweeps, values, pairs):
+    beta, gamma = beta.cpu().numpy(), gamma.cpu().numpy()
+    for p in pairs:
+        x, a, y, b, eps, rho = B.pair(p)
+        X, A, Y, Bw = f64(x), f64(a), f64(y), f64(b)
+        rb, rg = oracle.uot_sinkhorn(X, A, Y, Bw, eps, rho, sweeps=int(sweeps[p]))
+        gb = beta[B.x_off[p]:B.x_off[p + 1]]
+        gg = gamma[B.y_off[p]:B.y_off[p + 1]]
+        res = residual(gb, gg, rb, rg)
+        assert res <= 1e-6, (p, res, eps, rho)
+        v = oracle.dual_value(X, A, Y, Bw, eps, rho, rho, rb, rg)
+        assert abs(values[p] - v) <= 1e-6 * abs(v) + 1e-12, (p, values[p], v)
+
+
+def test_batch_fixed_sweeps_matches_oracle(uotk):
+    """32 pairs, n and m log-uniform in [64, 2048] (ragged, some below one
+    source tile), eps and rho drawn per pair, 30 sweeps each."""
+    B = inputs.pair_batch(seed=4001, npairs=32, nmin=64, nmax=2048)
+    beta, gamma, sweeps, values, conv = run(uotk, B, max_sweeps=30)
+    assert np.all(sweeps == 30)
+    check_pairs(B, beta, gamma, sweeps, values, range(B.npairs))
+
+
+def test_batch_tolerance_retires_pairs(uotk):
+    """tol = 1e-6: pairs with fast contraction (small eta lambda) retire after
+    a few tens of sweeps, the others keep going; each pair's duals equal the
+    oracle's after exactly its own sweep count."""
+    B = inputs.pair_batch(seed=4002, npairs=16, nmin=64, nmax=1024, eps_choices=(0.05,),
+                          rho_choices=(0.1, 1.0))
+    beta, gamma, sweeps, values, conv = run(uotk, B, max_sweeps=400, tol=1e-6)
+    assert conv
+    assert len(set(sweeps.tolist())) > 1          # not all at the same count
+    assert np.all(sweeps % 10 == 0)
+    check_pairs(B, beta, gamma, sweeps, values, range(B.npairs))
+
+
+def test_batch_single_pair_equals_single_solver(uotk):
+    """One pair through the batch equals uotk_uot_sinkhorn on that pair bit for
+    bit in the duals' arithmetic: same kernels, same order of sums."""
+    W = inputs.uniform_box(n=700, m=500, d=3)
+    beta, gamma, sweeps, values, _ = uotk.uot_sinkhorn_batch(
+        dev(W.x), dev(W.a), [0, 700], dev(W.y), dev(W.b), [0, 500], [W.eps], [W.rho],
+        max_sweeps=25)
+    b1, g1, s1, v1, _ = uotk.uot_sinkhorn(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho,
+                                          max_sweeps=25)
+    rb, rg = oracle.uot_sinkhorn(f64(W.x), f64(W.a), f64(W.y), f64(W.b), W.eps, W.rho, sweeps=25)
+    assert residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg) <= 1e-6
+    assert residual(b1.cpu().numpy(), g1.cpu().numpy(), rb, rg) <= 1e-6
+    assert abs(values[0] - v1) <= 1e-6 * abs(v1)
+
+
+def test_batch_validation(uotk):
+    B = inputs.pair_batch(seed=4003, npairs=3, nmin=16, nmax=64)
+    bad_off = B.x_off.copy()
+    bad_off[1] = bad_off[0]  # empty first pair
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.uot_sinkhorn_batch(dev(B.x), dev(B.a), bad_off, dev(B.y), dev(B.b), B.y_off,
+                                B.eps, B.rho)
+    assert e.value.status == 1
+    eps = B.eps.copy()
+    eps[2] = -1.0
+    with pytest.raises(uotk.UotkError) as e:
+        run(uotk, inputs.PairBatch(B.x, B.a, B.x_off, B.y, B.b, B.y_off, eps, B.rho))
+    assert e.value.status == 1
