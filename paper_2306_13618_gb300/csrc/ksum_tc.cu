@@ -46,6 +46,7 @@
 #include <memory>
 
 #include "engine.cuh"
+#include "tcgen05.cuh"
 
 namespace uotk {
 
@@ -82,68 +83,12 @@ __host__ __device__ constexpr bool tc_can_pair(bool split, int dc) {
   return tc_stages(split, dc, true) >= 2;
 }
 
-// ---- tcgen05 helpers (inline PTX) ----
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), start address advanced within the
-// swizzle atom for each K step of 16 elements.
-__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr) {
-  unsigned long long d = (unsigned long long)((saddr & 0x3FFFFu) >> 4);
-  d |= 1ull << 16;                 // leading byte offset (unused for swizzled K-major)
-  d |= (1024ull >> 4) << 32;       // stride byte offset
-  d |= 1ull << 46;                 // descriptor version
-  d |= 2ull << 61;                 // 128-byte swizzle
-  return d;
-}
+// ---- tcgen05 instruction descriptor of this kernel ----
 // Instruction descriptor: D FP32, A and B BF16, both K-major, M = 128, N = n.
 __host__ __device__ constexpr unsigned tc_idesc(int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) |
          ((unsigned)(TC_ROWS >> 4) << 24);
 }
-__device__ __forceinline__ void tc_mma(unsigned tmem_d, unsigned long long ad,
-                                       unsigned long long bd, unsigned idesc, unsigned acc) {
-  asm volatile(
-      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
-  asm volatile(
-      "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          smem_addr(bar))
-      : "memory");
-}
-__device__ __forceinline__ void tc_fence_before() {
-  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-}
-__device__ __forceinline__ void tc_fence_after() {
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-// tcgen05.ld is asynchronous: its registers are valid only after
-// tcgen05.wait::ld.  tc_wait16 names them as in/out operands, so no use of them
-// can be scheduled before the wait.
-__device__ __forceinline__ void tc_ld16(unsigned taddr, unsigned (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, "
-      "%11, %12, %13, %14, %15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-        "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr)
-      : "memory");
-}
-__device__ __forceinline__ void tc_wait16(unsigned (&r)[16]) {
-  asm volatile("tcgen05.wait::ld.sync.aligned;"
-               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
-               :
-               : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
-}
-
 __device__ __forceinline__ void tc_neumaier(float& hi, float& lo, float v) {
   const float t = hi + v;
   lo += (fabsf(hi) >= fabsf(v)) ? ((hi - t) + v) : ((v - t) + hi);
@@ -255,10 +200,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   }
   if (warp == 1) {
     __syncwarp();
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(
-                     smem_addr(tmem_slot))
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    tc_alloc(tmem_slot, 512);
   }
   tc_fence_before();
   __syncthreads();
@@ -443,7 +385,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   if (warp == 1) {
     __syncwarp();
     tc_fence_after();
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
+    tc_dealloc(tmem, 512);
   }
 }
 
