@@ -631,11 +631,17 @@ __global__ void __launch_bounds__(256)
         }
 #pragma unroll
         for (int it = 0; it < NIT; ++it) {
-          float s = 0.f;
+          // z-contraction of the column in packed pairs (z even, z odd)
+          unsigned long long s2 = 0ull;
 #pragma unroll
-          for (int kk = 0; kk < W2; ++kk) s = fmaf(fz[kk], hc[CACHE ? it * W2 + kk : 0], s);
+          for (int kk = 0; kk < W2; kk += 2)
+            s2 = f2_fma(f2_pack(fz[kk], fz[kk + 1]),
+                        f2_pack(hc[CACHE ? it * W2 + kk : 0], hc[CACHE ? it * W2 + kk + 1 : 0]),
+                        s2);
+          float se, so;
+          f2_unpack(s2, se, so);
           const float pxy = off[it] >= 0 ? wq[kxs[it]] * wq[kys[it]] : 0.f;
-          acc = fmaf(pxy, s, acc);
+          acc = fmaf(pxy, se + so, acc);
         }
       } else {
 #pragma unroll
