@@ -218,6 +218,25 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d,
                               double* beta, double* gamma, int* sweeps_done,
                               double* value, const uotk_sum_opts* opts);
 
+/* ---- lambda-scaling (Sec. 5.1.2, "deformed iteration") --------------------------------
+ * Alg. 1/2 solved for eps_schedule[0], eps_schedule[1], ... (lambda = 1/eps
+ * increasing), each stage started from the previous stage's final gamma
+ * (the first from gamma^0 = 0) and run until tol (or max_sweeps_per_stage).
+ *   eps_schedule: host double [stages], finite, > 0.
+ *   sweeps_per_stage (host int [stages], may be NULL): sweeps run per stage.
+ *   beta, gamma, value: as uotk_uot_sinkhorn, for the last stage.
+ *   Other arguments as uotk_uot_sinkhorn (flags: UOTK_LOG_DOMAIN only).
+ *   Returns UOTK_ERR_NOT_CONVERGED when tol > 0 and the last stage did not
+ *   reach it (outputs valid). */
+uotk_status uotk_uot_sinkhorn_scaled(uotk_ctx* ctx, void* stream, int d,
+                                     const float* x, int64_t n, const float* a,
+                                     const float* y, int64_t m, const float* b,
+                                     const double* eps_schedule, int stages, double rho1,
+                                     double rho2, int max_sweeps_per_stage, double tol, int ref,
+                                     unsigned flags, double* beta, double* gamma,
+                                     int* sweeps_per_stage, double* value,
+                                     const uotk_sum_opts* opts);
+
 /* ---- many independent problems at once (batched Alg. 1, direct form) -------------
  * npairs problems (x^p, a^p; y^p, b^p) of uneven sizes, each with its own eps_p,
  * rho1_p, rho2_p, all solved by Alg. 1 together: every half-step of every pair is

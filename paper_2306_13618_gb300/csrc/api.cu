@@ -341,6 +341,35 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x
                          max_sweeps, tol, ref, flags, beta, gamma, sweeps_done, value, opts);
 }
 
+uotk_status uotk_uot_sinkhorn_scaled(uotk_ctx* ctx, void* stream, int d, const float* x,
+                                     int64_t n, const float* a, const float* y, int64_t m,
+                                     const float* b, const double* eps_schedule, int stages,
+                                     double rho1, double rho2, int max_sweeps_per_stage,
+                                     double tol, int ref, unsigned flags, double* beta,
+                                     double* gamma, int* sweeps_per_stage, double* value,
+                                     const uotk_sum_opts* opts) {
+  UOTK_TRY(enter(ctx));
+  if (stages < 1 || !eps_schedule)
+    return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn_scaled: empty schedule");
+  if (flags & ~UOTK_LOG_DOMAIN)
+    return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn_scaled: flags 0x%x", flags);
+  for (int k = 0; k < stages; ++k)
+    if (!(eps_schedule[k] > 0.0) || !isfinite(eps_schedule[k]))
+      return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn_scaled: eps[%d] not finite > 0", k);
+  uotk_status st = UOTK_OK;
+  for (int k = 0; k < stages; ++k) {
+    int sw = 0;
+    // stage k > 0 starts from the previous stage's gamma
+    st = uotk_uot_sinkhorn(ctx, stream, d, x, n, a, y, m, b, eps_schedule[k], rho1, rho2,
+                           max_sweeps_per_stage, tol, ref,
+                           flags | (k > 0 ? UOTK_WARM_START : 0u), beta, gamma, &sw,
+                           k == stages - 1 ? value : nullptr, opts);
+    if (sweeps_per_stage) sweeps_per_stage[k] = sw;
+    if (st != UOTK_OK && st != UOTK_ERR_NOT_CONVERGED) return st;
+  }
+  return st;
+}
+
 uotk_status uotk_uot_sinkhorn_batch(uotk_ctx* ctx, void* stream, int d, int npairs,
                                     const int64_t* x_off, const float* x, const float* a,
                                     const int64_t* y_off, const float* y, const float* b,

@@ -95,27 +95,6 @@ __device__ __forceinline__ void tc_neumaier(float& hi, float& lo, float v) {
   hi = t;
 }
 
-// Packed two-wide FP32 arithmetic (one instruction for two lanes of values).
-__device__ __forceinline__ unsigned long long f2_pack(float a, float b) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void f2_unpack(unsigned long long r, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
-}
-__device__ __forceinline__ unsigned long long f2_fma(unsigned long long a, unsigned long long b,
-                                                     unsigned long long c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-__device__ __forceinline__ unsigned long long f2_add(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-
 // Weighted exponential sum of 16 accumulator columns of one row:
 //   sum_j w_j 2^{2c S_j + b_j + aa}   (FAST: without aa, applied to the row sum).
 // Columns go in pairs through packed FP32 instructions; bw holds, per pair of

@@ -96,6 +96,10 @@ def lib():
                                                ctypes.POINTER(_D), opts]
         L.uotk_mmd2.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                 ctypes.POINTER(_D), ctypes.POINTER(_D), opts]
+        L.uotk_uot_sinkhorn_scaled.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
+                                               _P, ctypes.c_int, _D, _D, ctypes.c_int, _D,
+                                               ctypes.c_int, ctypes.c_uint, _P, _P, _P,
+                                               ctypes.POINTER(_D), opts]
         L.uotk_uot_sinkhorn_batch.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                               _P, _P, _P, _P, _P, _P, ctypes.c_int, _D,
                                               ctypes.c_int, _P, _P, _P, _P, opts]
@@ -114,7 +118,7 @@ def lib():
         for name in ("uotk_create", "uotk_kernel_sum", "uotk_uot_sinkhorn",
                      "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
                      "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
-                     "uotk_uot_sinkhorn_batch", "uotk_nfft_plan",
+                     "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_nfft_plan",
                      "uotk_nfft_cells", "uotk_nfft_spread", "uotk_nfft_convolve",
                      "uotk_nfft_gather"):
             getattr(L, name).restype = ctypes.c_int
@@ -269,6 +273,32 @@ def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref=
         flags, _ptr(beta), _ptr(gamma), ctypes.byref(sweeps), ctypes.byref(value),
         ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
     return beta, gamma, sweeps.value, value.value, st == UOTK_OK
+
+
+def uot_sinkhorn_scaled(x, a, y, b, eps_schedule, rho1, rho2=None, max_sweeps=1000, tol=1e-6,
+                        ref="product", method="direct", log_domain=False, ctx=None, **nfft):
+    """lambda-scaling (uotk_uot_sinkhorn_scaled): stages eps_schedule[0], ... each
+    warm-started from the previous gamma.  Returns (beta, gamma, sweeps per stage,
+    value of the last stage, converged)."""
+    import numpy as np
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    rho2 = rho1 if rho2 is None else rho2
+    ctx = ctx or default_context()
+    sched = np.ascontiguousarray(np.asarray(eps_schedule, dtype=np.float64))
+    beta = torch.empty(x.shape[0], device=x.device, dtype=torch.float64)
+    gamma = torch.empty(y.shape[0], device=x.device, dtype=torch.float64)
+    sweeps = np.zeros(sched.size, dtype=np.int32)
+    value = _D(0.0)
+    refc = {"product": REF_PRODUCT, "counting": REF_COUNTING}.get(ref, ref)
+    o = _opts(method, **nfft)
+    st = ctx.check(lib().uotk_uot_sinkhorn_scaled(
+        ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0], _ptr(a), _ptr(y), y.shape[0],
+        _ptr(b), sched.ctypes.data, sched.size, float(rho1), float(rho2), int(max_sweeps),
+        float(tol), int(refc), LOG_DOMAIN if log_domain else 0, _ptr(beta), _ptr(gamma),
+        sweeps.ctypes.data, ctypes.byref(value), ctypes.byref(o)),
+        ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
+    return beta, gamma, sweeps, value.value, st == UOTK_OK
 
 
 def uot_sinkhorn_batch(x, a, x_off, y, b, y_off, eps, rho1, rho2=None, max_sweeps=100, tol=0.0,
@@ -488,5 +518,6 @@ EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_strin
             "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
             "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
-            "uotk_uot_sinkhorn_batch", "uotk_nfft_plan", "uotk_nfft_cells",
+            "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_nfft_plan",
+            "uotk_nfft_cells",
             "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]

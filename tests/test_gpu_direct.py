@@ -269,3 +269,47 @@ def test_log_domain_rejected_off_direct(uotk):
             uotk.uot_sinkhorn(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho,
                               max_sweeps=3, log_domain=True, method=method)
         assert e.value.status == 4
+
+
+def test_lambda_scaling_matches_oracle_schedule(uotk):
+    """uotk_uot_sinkhorn_scaled against the oracle run of the same stages (the
+    oracle replays the GPU's per-stage sweep counts, warm-started the same
+    way): the direct form's residual bar on the last stage's duals."""
+    W = inputs.uniform_box(n=600, m=500)
+    sched = [1.0, 0.2, 0.05]
+    # tol above the FP32 noise of the half-step sums (lambda * |change| ~ 1e-7)
+    beta, gamma, sweeps, value, conv = uotk.uot_sinkhorn_scaled(
+        dev(W.x), dev(W.a), dev(W.y), dev(W.b), sched, 2.0, max_sweeps=3000, tol=1e-5)
+    assert conv and np.all(sweeps > 0)
+    X, Y, A, B = f64(W.x), f64(W.y), f64(W.a), f64(W.b)
+    g = None
+    for eps, s in zip(sched, sweeps):
+        rb, g = oracle.uot_sinkhorn(X, A, Y, B, eps, 2.0, sweeps=int(s), gamma0=g)
+    assert residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, g) <= 1e-6
+    v = oracle.dual_value(X, A, Y, B, sched[-1], 2.0, 2.0, rb, g)
+    assert abs(value - v) <= 1e-6 * abs(v)
+
+
+def test_lambda_scaling_reaches_the_cold_fixed_point(uotk):
+    """The setting of the paper's lambda-scaling experiment (probability
+    measures, eta1 = eta2 = 25, lambda in {1, 20, 100}): the staged solve and a
+    cold solve at lambda = 100, both stopped at tol, agree on the duals.  Each
+    is within tol / (1 - (q lambda)^2) (in lambda * dual units) of the unique
+    fixed point, q lambda = eta lambda / (1 + eta lambda) per half-step."""
+    g = inputs.rng(61)
+    x = g.uniform(0.0, 1.0, (800, 2)).astype(np.float32)
+    y = (g.uniform(0.0, 1.0, (700, 2)) ** 2).astype(np.float32)
+    a = np.full(800, 1.0 / 800, np.float32)
+    b = np.full(700, 1.0 / 700, np.float32)
+    args = (dev(x), dev(a), dev(y), dev(b))
+    tol, lam, eta = 1e-6, 100.0, 25.0
+    bs, gs, sweeps, vs, conv = uotk.uot_sinkhorn_scaled(*args, [1.0, 1 / 20, 1 / 100], eta,
+                                                        max_sweeps=30000, tol=tol)
+    bc, gc, cold, vc, conv_cold = uotk.uot_sinkhorn(*args, 1 / lam, eta, max_sweeps=30000,
+                                                    tol=tol)
+    assert conv and conv_cold
+    rate = (eta * lam / (1 + eta * lam)) ** 2
+    bound = 2 * tol / (1 - rate) / lam
+    assert torch.max(torch.abs(bs - bc)).item() <= bound
+    assert torch.max(torch.abs(gs - gc)).item() <= bound
+    assert abs(vs - vc) <= 1e-4 * abs(vc)

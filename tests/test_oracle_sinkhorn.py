@@ -223,3 +223,20 @@ def test_eta_to_zero_limit(oracle_lib):
         dist.append(np.abs(oracle.plan(x, mu, y, nu, 1 / lam, b, gm) - lim).sum())
     assert dist[0] > dist[1] > dist[2]
     assert 5 < dist[0] / dist[1] < 20 and 5 < dist[1] / dist[2] < 20
+
+
+def test_lambda_scaling_reaches_the_fixed_point_of_the_last_lambda():
+    """lambda-scaling (Sec. 5.1.2): stages at increasing lambda, each started
+    from the previous gamma, converge to the same duals as a cold start at the
+    last lambda (the fixed point of Alg. 1 is unique)."""
+    g = np.random.default_rng(12)
+    x = g.uniform(-0.25, 0.25, (9, 2))
+    y = g.uniform(-0.25, 0.25, (7, 2))
+    a = np.full(9, 1.0 / 9)
+    b = np.full(7, 1.0 / 7)
+    eta = 25.0
+    gam = None
+    for eps in (1.0, 0.05, 0.01):
+        be, gam = oracle.uot_sinkhorn(x, a, y, b, eps, eta, sweeps=60000, gamma0=gam)
+    rb, rg = oracle.uot_sinkhorn(x, a, y, b, 0.01, eta, sweeps=60000)
+    assert np.max(np.abs(be - rb)) <= 1e-12 and np.max(np.abs(gam - rg)) <= 1e-12
