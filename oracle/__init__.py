@@ -87,6 +87,8 @@ def _load():
                                                  ctypes.c_double, ctypes.c_double, ctypes.c_int,
                                                  _D, _D, _D, _D]
     lib.orc_sinkhorn_divergence_grad.restype = ctypes.c_double
+    lib.orc_mean_cost.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D, ctypes.c_double]
+    lib.orc_mean_cost.restype = ctypes.c_double
     lib.orc_num_threads.restype = ctypes.c_int
     lib.orc_set_num_threads.argtypes = [ctypes.c_int]
     _lib = lib
@@ -265,3 +267,33 @@ def mmd2_kernel(kind, p, x, mu, y, nu, return_parts=False):
     v = _load().orc_mmd2_kernel(KERNELS[kind], float(p), x.shape[1], _p(x), x.shape[0], _p(mu),
                                 _p(y), y.shape[0], _p(nu), _p(parts))
     return (v, parts) if return_parts else v
+
+
+def mean_cost(x, mu, y, nu, r=2):
+    """<mu (x) nu | d^r> = sum_ij mu_i nu_j ||x_i - y_j||^r, the double sum."""
+    x, y, mu, nu = _pts(x), _pts(y), _vec(mu), _vec(nu)
+    return _load().orc_mean_cost(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0],
+                                 _p(nu), float(r))
+
+
+def independent_objective(c, cost, m1, m2, eps, eta1, eta2):
+    """Objective of Eq. (W4) at the plan c mu (x) nu, lambda = 1/eps:
+        c <mu (x) nu|d^2> + (1/lambda) m1 m2 (c log c - c + 1)
+        + eta1 m1 (c m2 log(c m2) - c m2 + 1) + eta2 m2 (c m1 log(c m1) - c m1 + 1),
+    the marginals of c mu (x) nu being c m2 mu and c m1 nu (m1 = mu(X), m2 = nu(X))."""
+    return (c * cost + eps * m1 * m2 * (c * np.log(c) - c + 1.0)
+            + eta1 * m1 * (c * m2 * np.log(c * m2) - c * m2 + 1.0)
+            + eta2 * m2 * (c * m1 * np.log(c * m1) - c * m1 + 1.0))
+
+
+def cstar(x, mu, y, nu, eps, eta1, eta2):
+    """c*_{2;eta;lambda} of Eq. (561) (Prop. prop:536), lambda = 1/eps:
+        c* = exp(-<mu (x) nu|d^2> / (m1 m2 (eta1 + eta2 + 1/lambda)))
+             m1^{-eta2/(eta1+eta2+1/lambda)} m2^{-eta1/(eta1+eta2+1/lambda)}.
+    Returns (c*, objective of Eq. (W4) at c* mu (x) nu, <mu (x) nu|d^2>)."""
+    mu, nu = _vec(mu), _vec(nu)
+    m1, m2 = float(np.sum(mu)), float(np.sum(nu))
+    cost = mean_cost(x, mu, y, nu, 2)
+    den = eta1 + eta2 + eps
+    c = np.exp(-cost / (m1 * m2 * den)) * m1 ** (-eta2 / den) * m2 ** (-eta1 / den)
+    return c, independent_objective(c, cost, m1, m2, eps, eta1, eta2), cost

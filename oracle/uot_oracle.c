@@ -501,3 +501,17 @@ double orc_mmd2_kernel(int kind, double p, int d, const double* x, int64_t n, co
   if (parts) { parts[0] = nsum_get(&A); parts[1] = nsum_get(&B); parts[2] = nsum_get(&C); }
   return nsum_get(&A) - 2.0 * nsum_get(&B) + nsum_get(&C);
 }
+
+/* <mu (x) nu | d^r> = sum_i sum_j mu_i nu_j ||x_i - y_j||^r, the plain double sum
+ * (r = 2: the mean-cost numerator of Eq. (561); r = 1: the inner product of the
+ * complexity paragraph of Sec. 4.4, d = -k_e). */
+double orc_mean_cost(int d, const double* x, int64_t n, const double* mu, const double* y,
+                     int64_t m, const double* nu, double r) {
+  nsum acc = {0.0, 0.0};
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t j = 0; j < m; ++j) {
+      double s = sqdist(d, x + i * d, y + j * d);
+      nsum_add(&acc, mu[i] * nu[j] * (r == 2.0 ? s : pow(sqrt(s), r)));
+    }
+  return nsum_get(&acc);
+}
