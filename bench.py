@@ -58,6 +58,23 @@ def dist_env():
             int(os.environ.get("LOCAL_RANK", "0")))
 
 
+def max_over_ranks(values, world, device):
+    """Element-wise maximum over all ranks of a list of times (the job takes as
+    long as its slowest replica); the values themselves when world == 1."""
+    if world == 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.tolist()
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units of all `world` replicas / the job's time."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 class ClockSampler:
     """nvidia-smi samples (SM clock, throttle reasons) during the timed region."""
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
@@ -467,14 +484,6 @@ def batch_main(args, rank, world, local):
     launches = ctx.launch_count() - launches0
     clk = clocks.stop()
     ms = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
     n = np.diff(P.x_off)
     m = np.diff(P.y_off)
     # end to end: points and weights from pinned host memory, duals back
@@ -489,8 +498,12 @@ def batch_main(args, rank, world, local):
     e1.record(stream)
     e1.synchronize()
     e2e_ms = e0.elapsed_time(e1)
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], world, dev)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
     line = {
-        "metric": "batched UOT sweeps/s (all pairs)", "value": world * total_sweeps / (ms / 1e3),
+        "metric": "batched UOT sweeps/s (all pairs)", "value": job_rate(total_sweeps, world, ms),
         "unit": "sweeps/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
@@ -502,7 +515,7 @@ def batch_main(args, rank, world, local):
                    "pair_evaluations_per_half_step_all_active": int(np.sum(n * m)),
                    "l2": "inputs (245 MB) larger than L2",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "e2e": {"value": world * int(sweeps.sum()) / (e2e_ms / 1e3), "unit": "sweeps/s",
+        "e2e": {"value": job_rate(int(sweeps.sum()), world, e2e_ms), "unit": "sweeps/s",
                 "h2d_bytes_per_step": sum(t.numel() * t.element_size() for t in (hx, hy, ha, hb)),
                 "d2h_bytes_per_step": hbeta.numel() * 8 + hgamma.numel() * 8},
         "gpu_launches": launches, "clocks": clk,
@@ -549,11 +562,10 @@ def main():
     beta = torch.empty(W.n, device=dev, dtype=torch.float64)
     gamma = torch.empty(W.m, device=dev, dtype=torch.float64)
     flush = torch.empty(L2_FLUSH_BYTES // 4, device=dev, dtype=torch.float32)
-    nfft_kw = {} if args.method == "direct" else {}
 
     def step():
         return uotk.uot_sinkhorn(x, a, y, b, W.eps, W.rho, max_sweeps=W.sweeps,
-                                 method=args.method, ctx=ctx, beta=beta, gamma=gamma, **nfft_kw)
+                                 method=args.method, ctx=ctx, beta=beta, gamma=gamma)
 
     for _ in range(args.warmup):
         step()
@@ -584,27 +596,6 @@ def main():
     ctx.set_profiling(False)
     clk = clocks.stop()
     ms = sum(times) / len(times)
-    if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        dist.barrier()
-    value = world * W.sweeps / (ms / 1e3)
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-
-    # --- roofline of every stage; the dominant one (largest device time) is reported ---
-    peaks, peak_kind = load_peaks()
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    plan = uotk.nfft_plan(y, x, W.eps, ctx=ctx).as_dict() if args.method == "nfft" else None
-    rates = uotk.measure_unit_rates(ctx)
-    roofs = stage_rooflines(prof, W, sms, peaks, plan, rates)
-    dom = max(roofs.values(), key=lambda r: r["ms_total"]) if roofs else {}
-    roof = {k: v for k, v in dom.items() if k != "ms_total"}
-    roof["traffic"] = recorded_traffic(roof.get("kernel"))
 
     # --- end to end through the C ABI from pinned host buffers ---
     hx, hy = torch.from_numpy(W.x).pin_memory(), torch.from_numpy(W.y).pin_memory()
@@ -627,6 +618,21 @@ def main():
     e2e_ms = sum(e2e_times) / len(e2e_times)
     h2d = sum(t.numel() * t.element_size() for t in (hx, hy, ha, hb))
     d2h = sum(t.numel() * t.element_size() for t in (hbeta, hgamma))
+    ms, e2e_ms = max_over_ranks([ms, e2e_ms], world, dev)
+    value = job_rate(W.sweeps, world, ms)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+
+    # --- roofline of every stage; the dominant one (largest device time) is reported ---
+    peaks, peak_kind = load_peaks()
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    plan = uotk.nfft_plan(y, x, W.eps, ctx=ctx).as_dict() if args.method == "nfft" else None
+    rates = uotk.measure_unit_rates(ctx)
+    roofs = stage_rooflines(prof, W, sms, peaks, plan, rates)
+    dom = max(roofs.values(), key=lambda r: r["ms_total"]) if roofs else {}
+    roof = {k: v for k, v in dom.items() if k != "ms_total"}
+    roof["traffic"] = recorded_traffic(roof.get("kernel"))
 
     extras = {}
     if not args.no_extras and args.workload == "gmm3":
@@ -679,7 +685,7 @@ def main():
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof, "peaks": peak_kind,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * W.sweeps / (e2e_ms / 1e3), "unit": UNIT,
+        "e2e": {"value": job_rate(W.sweeps, world, e2e_ms), "unit": UNIT,
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": launches, "clocks": clk,
         "unit_rates_per_clk_sm": {"ex2": rates[0], "ffma": rates[1]},

@@ -335,10 +335,46 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x
   if (ref != UOTK_REF_PRODUCT && ref != UOTK_REF_COUNTING)
     return set_error(ctx, UOTK_ERR_INVALID, "unknown reference measure %d", ref);
   if (!(tol >= 0.0) && !(tol <= 0.0)) return set_error(ctx, UOTK_ERR_INVALID, "tol is NaN");
-  if (flags & ~(UOTK_WARM_START | UOTK_LOG_DOMAIN))
+  if (flags & ~(UOTK_WARM_START | UOTK_LOG_DOMAIN | UOTK_CSTAR_INIT))
     return set_error(ctx, UOTK_ERR_INVALID, "unknown flags 0x%x", flags);
+  if ((flags & UOTK_CSTAR_INIT) && ((flags & UOTK_WARM_START) || ref != UOTK_REF_PRODUCT))
+    return set_error(ctx, UOTK_ERR_INVALID,
+                     "UOTK_CSTAR_INIT needs ref = PRODUCT and no UOTK_WARM_START");
   return op_uot_sinkhorn(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2,
                          max_sweeps, tol, ref, flags, beta, gamma, sweeps_done, value, opts);
+}
+
+static uotk_status check_pair(uotk_ctx* ctx, int d, const float* x, int64_t n, const float* a,
+                              const float* y, int64_t m, const float* b) {
+  UOTK_TRY(check_common(ctx, d, nullptr));
+  UOTK_TRY(check_cloud(ctx, "x", x, n, d));
+  UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
+  UOTK_TRY(check_cloud(ctx, "y", y, m, d));
+  UOTK_TRY(check_cloud(ctx, "b", b, m, 1));
+  if (n < 1 || m < 1) return set_error(ctx, UOTK_ERR_INVALID, "needs n >= 1 and m >= 1");
+  return UOTK_OK;
+}
+
+uotk_status uotk_mean_cost(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
+                           const float* a, const float* y, int64_t m, const float* b, int r,
+                           double* out) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_pair(ctx, d, x, n, a, y, m, b));
+  if (r != 1 && r != 2) return set_error(ctx, UOTK_ERR_INVALID, "mean_cost: r = %d not 1 or 2", r);
+  if (!out) return set_error(ctx, UOTK_ERR_INVALID, "mean_cost: null output");
+  return op_mean_cost(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, r, out);
+}
+
+uotk_status uotk_cstar(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
+                       const float* a, const float* y, int64_t m, const float* b, double eps,
+                       double rho1, double rho2, double* out) {
+  UOTK_TRY(enter(ctx));
+  UOTK_TRY(check_pair(ctx, d, x, n, a, y, m, b));
+  if (!(eps > 0.0) || !isfinite(eps) || !(rho1 > 0.0) || !(rho2 > 0.0) || !isfinite(rho1) ||
+      !isfinite(rho2))
+    return set_error(ctx, UOTK_ERR_INVALID, "eps, rho1, rho2 must be finite and > 0");
+  if (!out) return set_error(ctx, UOTK_ERR_INVALID, "cstar: null output");
+  return op_cstar(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2, out);
 }
 
 uotk_status uotk_uot_sinkhorn_scaled(uotk_ctx* ctx, void* stream, int d, const float* x,

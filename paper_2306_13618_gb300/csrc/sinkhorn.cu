@@ -506,6 +506,11 @@ uotk_status op_uot_sinkhorn(uotk_ctx* ctx, cudaStream_t s, int d, const float* x
   if (logd && sp.method != UOTK_DIRECT)
     return set_error(ctx, UOTK_ERR_UNSUPPORTED,
                      "uot_sinkhorn: the log domain is implemented for the direct FP32 form only");
+  // gamma^0 = c* 1 (Remark on the initialisation; c* of Eq. 561), computed
+  // before the solve's workspace is carved.
+  const bool cstar_init = (flags & UOTK_CSTAR_INIT) != 0;
+  double cst[3] = {0.0, 0.0, 0.0};
+  if (cstar_init) UOTK_TRY(op_cstar(ctx, s, d, x, n, a, y, m, b, eps, rho1, rho2, cst));
   Carver size(nullptr);
   size.off = engine_bytes(ctx, sp);
   SolveBufs B;
@@ -522,8 +527,9 @@ uotk_status op_uot_sinkhorn(uotk_ctx* ctx, cudaStream_t s, int d, const float* x
   carve_solve(cv, n, m, copies, B, logd);
   carve_reducer(ctx, cv, R);
   if (!copies) { B.beta = beta; B.gamma = gamma; }
-  const bool warm = (flags & UOTK_WARM_START) != 0;
-  if (copies && warm) UOTK_TRY(E->from_caller(s, 1, gamma, B.gamma));
+  const bool warm = (flags & (UOTK_WARM_START | UOTK_CSTAR_INIT)) != 0;
+  if (cstar_init) UOTK_TRY(fill_f64(ctx, s, B.gamma, m, cst[0]));
+  else if (copies && warm) UOTK_TRY(E->from_caller(s, 1, gamma, B.gamma));
   SolveResult res;
   UOTK_TRY(solve(ctx, s, E.get(), n, m, eps, rho1, rho2, max_sweeps, tol, ref, warm, B, R, &res,
                  logd));

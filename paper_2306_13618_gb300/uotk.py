@@ -22,6 +22,7 @@ DIRECT, NFFT, DIRECT_BF16, DIRECT_BF16X3 = 0, 1, 2, 3
 REF_PRODUCT, REF_COUNTING = 0, 1
 WARM_START = 1
 LOG_DOMAIN = 2
+CSTAR_INIT = 4
 
 _lib = None
 _lock = threading.Lock()
@@ -103,6 +104,10 @@ def lib():
         L.uotk_uot_sinkhorn_batch.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                               _P, _P, _P, _P, _P, _P, ctypes.c_int, _D,
                                               ctypes.c_int, _P, _P, _P, _P, opts]
+        L.uotk_mean_cost.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
+                                     ctypes.c_int, ctypes.POINTER(_D)]
+        L.uotk_cstar.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, _D, _D,
+                                 ctypes.POINTER(_D)]
         L.uotk_measure_unit_rates.argtypes = [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]
         L.uotk_mmd2_grad.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                      ctypes.POINTER(_D), _P, _P, _P, _P, opts]
@@ -118,7 +123,8 @@ def lib():
         for name in ("uotk_create", "uotk_kernel_sum", "uotk_uot_sinkhorn",
                      "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
                      "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
-                     "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_nfft_plan",
+                     "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_mean_cost",
+                     "uotk_cstar", "uotk_nfft_plan",
                      "uotk_nfft_cells", "uotk_nfft_spread", "uotk_nfft_convolve",
                      "uotk_nfft_gather"):
             getattr(L, name).restype = ctypes.c_int
@@ -244,10 +250,11 @@ def kernel_sum_noalloc(src, w, tgt, eps, out):
 
 def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref="product",
                  gamma0=None, method="direct", ctx=None, beta=None, gamma=None,
-                 log_domain=False, **nfft):
+                 log_domain=False, cstar_init=False, **nfft):
     """KL-penalised entropic UOT by Sinkhorn (uotk_uot_sinkhorn).
 
     log_domain: per-row log-sum-exp half-steps (UOTK_LOG_DOMAIN; direct form).
+    cstar_init: gamma^0 = c* 1, c* of Eq. (561) (UOTK_CSTAR_INIT).
     Returns (beta, gamma, sweeps_done, value, converged)."""
     x, y = _pts(x, "x"), _pts(y, "y")
     a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
@@ -263,6 +270,8 @@ def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref=
         gamma = torch.empty(y.shape[0], device=dev, dtype=torch.float64)
     if log_domain:
         flags |= LOG_DOMAIN
+    if cstar_init:
+        flags |= CSTAR_INIT
     refc = {"product": REF_PRODUCT, "counting": REF_COUNTING}.get(ref, ref)
     sweeps = ctypes.c_int(0)
     value = _D(0.0)
@@ -273,6 +282,32 @@ def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref=
         flags, _ptr(beta), _ptr(gamma), ctypes.byref(sweeps), ctypes.byref(value),
         ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
     return beta, gamma, sweeps.value, value.value, st == UOTK_OK
+
+
+def mean_cost(x, a, y, b, r=2, ctx=None):
+    """<mu (x) nu|d^r> for r = 2 (moments) or r = 1 (energy kernel) with the
+    masses (uotk_mean_cost): returns (cost, mu(X), nu(X))."""
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    ctx = ctx or default_context()
+    out = (_D * 3)()
+    ctx.check(lib().uotk_mean_cost(ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0],
+                                   _ptr(a), _ptr(y), y.shape[0], _ptr(b), int(r), out))
+    return tuple(out)
+
+
+def cstar(x, a, y, b, eps, rho1, rho2=None, ctx=None):
+    """c* of Eq. (561) (uotk_cstar): returns (c*, Eq. (W4) objective at
+    c* mu (x) nu, <mu (x) nu|d^2>)."""
+    x, y = _pts(x, "x"), _pts(y, "y")
+    a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
+    rho2 = rho1 if rho2 is None else rho2
+    ctx = ctx or default_context()
+    out = (_D * 3)()
+    ctx.check(lib().uotk_cstar(ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0], _ptr(a),
+                               _ptr(y), y.shape[0], _ptr(b), float(eps), float(rho1),
+                               float(rho2), out))
+    return tuple(out)
 
 
 def uot_sinkhorn_scaled(x, a, y, b, eps_schedule, rho1, rho2=None, max_sweeps=1000, tol=1e-6,
@@ -518,6 +553,6 @@ EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_strin
             "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
             "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
-            "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_nfft_plan",
-            "uotk_nfft_cells",
+            "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_mean_cost",
+            "uotk_cstar", "uotk_nfft_plan", "uotk_nfft_cells",
             "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]
