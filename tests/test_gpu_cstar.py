@@ -91,23 +91,48 @@ def test_cstar_init_matches_oracle(uotk, method, tol):
     assert abs(value - v) <= tol * abs(v), (value, v)
 
 
-def test_cstar_init_reaches_the_same_fixed_point(uotk):
-    """Started from c* or from 0 and stopped at tol, the solve lands within
-    tol / (1 - (q lambda)^2) (in lambda * dual units) of the unique maximiser,
-    so the two runs agree to twice that.  Also records both sweep counts."""
-    W = inputs.uniform_box(n=900, m=700, d=3)
-    args = (dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho)
+def _workload(name):
+    if name == "uniform_box":
+        W = inputs.uniform_box(n=900, m=700, d=3)
+        return W.x, W.a, W.y, W.b, W.eps, W.rho
+    if name == "gmm3":
+        W = inputs.gmm3(seed=2103, n=4096, m=4096)
+        return W.x, W.a, W.y, W.b, W.eps, W.rho
+    # the probability measures of the lambda-scaling experiment, lambda = 100, eta = 25
+    g = inputs.rng(61)
+    x = g.uniform(0.0, 1.0, (800, 2)).astype(np.float32)
+    y = (g.uniform(0.0, 1.0, (700, 2)) ** 2).astype(np.float32)
+    return (x, np.full(800, 1.0 / 800, np.float32), y, np.full(700, 1.0 / 700, np.float32),
+            0.01, 25.0)
+
+
+@pytest.mark.parametrize("name", ["uniform_box", "gmm3", "probability"])
+def test_cstar_init_reaches_the_same_fixed_point(uotk, name):
+    """Started from 0, from c* (the Remark read literally) or from the gamma of
+    the constant-cost optimum at the mean cost, gamma_j = -eta log(c* mu(X)),
+    and stopped at tol, each solve lands within tol / (1 - (q lambda)^2) (in
+    lambda * dual units) of the unique maximiser, so any two agree to twice
+    that.  Prints the three sweep counts."""
+    x, a, y, b, eps, rho = _workload(name)
+    args = (dev(x), dev(a), dev(y), dev(b), eps, rho)
     tol = 1e-6
-    b0, g0, s0, v0, c0 = uotk.uot_sinkhorn(*args, max_sweeps=20000, tol=tol)
-    b1, g1, s1, v1, c1 = uotk.uot_sinkhorn(*args, max_sweeps=20000, tol=tol, cstar_init=True)
-    assert c0 and c1
-    lam = 1.0 / W.eps
-    rate = (W.rho * lam / (1 + W.rho * lam)) ** 2
+    c = uotk.cstar(*args)[0]
+    m1 = float(np.sum(a, dtype=np.float64))
+    g_dual = torch.full((y.shape[0],), -rho * np.log(c * m1), dtype=torch.float64)
+    runs = {"0": uotk.uot_sinkhorn(*args, max_sweeps=30000, tol=tol),
+            "c*": uotk.uot_sinkhorn(*args, max_sweeps=30000, tol=tol, cstar_init=True),
+            "dual of c*": uotk.uot_sinkhorn(*args, max_sweeps=30000, tol=tol, gamma0=g_dual)}
+    lam = 1.0 / eps
+    rate = (rho * lam / (1 + rho * lam)) ** 2
     bound = 2 * tol / (1 - rate) / lam
-    assert torch.max(torch.abs(b1 - b0)).item() <= bound
-    assert torch.max(torch.abs(g1 - g0)).item() <= bound
-    assert abs(v1 - v0) <= 1e-6 * abs(v0)
-    print(f"sweeps to tol {tol}: gamma0 = 0: {s0}, gamma0 = c*: {s1}")
+    b0, g0, _, v0, _ = runs["0"]
+    for key, (b1, g1, s1, v1, conv) in runs.items():
+        assert conv, key
+        assert torch.max(torch.abs(b1 - b0)).item() <= bound, key
+        assert torch.max(torch.abs(g1 - g0)).item() <= bound, key
+        assert abs(v1 - v0) <= 1e-5 * abs(v0), key
+    print(f"{name}: sweeps to tol {tol}: "
+          + ", ".join(f"gamma0 = {k}: {r[2]}" for k, r in runs.items()))
 
 
 def test_validation(uotk):
