@@ -77,9 +77,19 @@ typedef enum { UOTK_REF_PRODUCT = 0, UOTK_REF_COUNTING = 1 } uotk_ref;
  *   IMQ     1/sqrt(r^2 + p^2)   (p = the constant c of the table)
  *   ENERGY  -r                  (p unused; any positive value)
  * The non-Gaussian kernels are available in uotk_kernel_sum (eps = p) and
- * uotk_mmd2 (ell = p), direct FP32 form only; every other combination returns
- * UOTK_ERR_UNSUPPORTED (their NFFT form needs the boundary regularisation of
- * Sec. 4, not built). */
+ * uotk_mmd2 (ell = p), in the direct FP32 form and the NFFT form (d <= 3);
+ * every other combination returns UOTK_ERR_UNSUPPORTED.  Their NFFT form is the
+ * regularised fast summation of Sec. 4.2: on the torus (period h, units
+ * rbar = r/h) the kernel is replaced by K_R, equal to K for
+ * eps_I <= rbar <= 1/2 - eps_B and by two-point Taylor polynomials of degree
+ * 2p - 1 (p = reg_degree, matching K's derivatives of order < p) below eps_I and
+ * up to 1/2, constant beyond; b_k is the DFT of K_R sampled on I_N^d, and the
+ * near field |x - y| < eps_I h adds w (K - K_R) directly.  eps_I = eps_B = p/N;
+ * h = (Euclidean diameter of the joint bounding box) / (1/2 - eps_B), so that
+ * K_R = K wherever no near-field correction is made.  Defaults grid 256,
+ * N = 128, p = 4 (max error about 1e-6 of sum|w| max|K| on uniform clouds);
+ * the near field costs (number of pairs closer than eps_I h) kernel
+ * evaluations, so the form pays when that is a small fraction of n m. */
 typedef enum {
   UOTK_KERNEL_GAUSS = 0,
   UOTK_KERNEL_LAPLACE = 1,
@@ -90,13 +100,13 @@ typedef enum {
 /* Options of one kernel summation.  A NULL pointer means all defaults. */
 typedef struct {
   int32_t method;      /* uotk_method; default UOTK_DIRECT */
-  int32_t grid;        /* NFFT: oversampled grid size n per dimension, power of two in [16, 256]; 0 = 128 */
+  int32_t grid;        /* NFFT: oversampled grid size n per dimension, power of two in [16, 256]; 0 = 128 (256 for the non-Gaussian kernels) */
   int32_t bandwidth;   /* NFFT: bandwidth N, even, 4 <= N <= grid; 0 = grid/2 (oversampling sigma = 2) */
   int32_t cutoff;      /* NFFT: window cut-off m in [2, 8]; 0 = smallest of 6, 7, 8 meeting target_err */
-  double period;       /* NFFT: torus period h; 0 = chosen from the data and eps */
+  double period;       /* NFFT: torus period h; 0 = chosen from the data and eps (non-Gaussian kernels: must be >= the automatic choice) */
   double target_err;   /* NFFT: accuracy goal, max error relative to sum|w|; 0 = 1e-6 */
   int32_t kernel;      /* uotk_kernel; default UOTK_KERNEL_GAUSS */
-  int32_t reserved;    /* 0 */
+  int32_t reg_degree;  /* NFFT, non-Gaussian kernels: regularisation degree p in [2, 12]; 0 = 4 */
 } uotk_sum_opts;
 
 /* Parameters of an NFFT fast summation as chosen by uotk_nfft_plan (Sec. 4).

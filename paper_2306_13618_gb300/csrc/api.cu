@@ -138,9 +138,10 @@ uotk_status check_kernel(uotk_ctx* ctx, const uotk_sum_opts* opts, bool allowed)
     return set_error(ctx, UOTK_ERR_INVALID, "unknown kernel %d", kernel);
   if (kernel == UOTK_KERNEL_GAUSS) return UOTK_OK;
   const int method = opts->method;
-  if (!allowed || method != UOTK_DIRECT)
+  if (!allowed || (method != UOTK_DIRECT && method != UOTK_NFFT))
     return set_error(ctx, UOTK_ERR_UNSUPPORTED,
-                     "kernel %d: only kernel_sum and mmd2 with the direct FP32 form", kernel);
+                     "kernel %d: only kernel_sum and mmd2, in the direct FP32 or the NFFT form",
+                     kernel);
   return UOTK_OK;
 }
 

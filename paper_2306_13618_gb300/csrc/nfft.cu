@@ -137,9 +137,14 @@ struct NfftEngine : Engine {
   }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
     SpreadWeights sw{w, nullptr, 0.0, nullptr};
-    UOTK_TRY(nfft_spread(ctx, s, P, src == 0 ? X : Y, sw, W, W.grid));
+    const NfftPoints& S = src == 0 ? X : Y;
+    const NfftPoints& T = tgt == 0 ? X : Y;
+    UOTK_TRY(nfft_spread(ctx, s, P, S, sw, W, W.grid));
     UOTK_TRY(nfft_convolve(ctx, s, P, W, W.grid, W.grid));
-    return nfft_gather(ctx, s, P, tgt == 0 ? X : Y, W.grid, out);
+    UOTK_TRY(nfft_gather(ctx, s, P, T, W.grid, out));
+    // non-smooth kernels: the Fourier part sums K_R; add w (K - K_R) of the near field
+    if (P.kernel != UOTK_KERNEL_GAUSS) UOTK_TRY(nfft_near(ctx, s, P, S, w, T, out));
+    return UOTK_OK;
   }
   const float* weights(int side) const override { return side == 0 ? as : bs; }
   const int* perm(int side) const override { return side == 0 ? X.perm : Y.perm; }
@@ -211,7 +216,10 @@ uotk_status nfft_engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& 
   UOTK_TRY(nfft_points_build(ctx, s, e->P, sp.y, sp.m, e->Y));
   UOTK_TRY(sorted_weights(ctx, s, e->X, sp.a, e->as));
   UOTK_TRY(sorted_weights(ctx, s, e->Y, sp.b, e->bs));
-  UOTK_TRY(upload_scale(ctx, s, e->P, e->W.scale));
+  if (e->P.kernel != UOTK_KERNEL_GAUSS)
+    UOTK_TRY(nfft_reg_table(ctx, s, e->P, e->W));
+  else
+    UOTK_TRY(upload_scale(ctx, s, e->P, e->W.scale));
   *out = e.release();
   return UOTK_OK;
 }

@@ -46,6 +46,12 @@ struct NfftParams {
   float b = 0.f;       // Kaiser-Bessel shape pi (2 - 1/sigma)
   int tiles1 = 16;     // tiles per dimension = n / NFFT_TILE
   int E = 19;          // smem block edge = NFFT_TILE + 2m - 1
+  // Non-smooth kernels (Sec. 4.2): uotk_kernel, regularisation degree p (the
+  // pieces match p derivatives) and eps_I = eps_B (torus units); eps above is
+  // then the kernel's parameter.  kernel == UOTK_KERNEL_GAUSS: unused.
+  int kernel = 0;
+  int reg_p = 0;
+  double eps_i = 0.0;
 };
 
 // Host: choose h, m; fill params (bounding box given).
@@ -54,6 +60,9 @@ uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const floa
 // Host: 1-D factors g(k) of scale_k = prod_t g_t(k_t), k in {-N/2..N/2-1}
 // (FP64 -> FP32 table of 3*N floats, one row per dimension).
 void nfft_scale_table(const NfftParams& P, float* host_table /* 3*N */);
+// Host: the deconvolution rows 1/(n phihat(k))^2 (FP64, 3*N; an embedded
+// dimension keeps k = 0 only).
+void nfft_deconv_rows(const NfftParams& P, double* rows /* 3*N */);
 
 // A point set sorted by grid cell, cells ordered tile by tile (tile-major,
 // then z, y, x inside the tile): points of one cell are contiguous.
@@ -87,6 +96,7 @@ struct NfftWork {
   float* grid = nullptr;   // [n^3] real grid
   float2* cgrid = nullptr; // [n^3] complex work grid
   float* scale = nullptr;  // [3*N] device table
+  float* full = nullptr;   // [N^3] non-separable table [kz'][ky'][kx'] (non-smooth kernels)
 };
 size_t nfft_work_bytes(const NfftParams& P, int64_t max_points);
 void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWork& W);
@@ -106,6 +116,14 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
                           const float* grid_in, float* grid_out);
 uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
                         const float* grid, float* out_sorted);
+
+// Non-smooth kernels (nfft_reg.cu): fill W.full with b_k / prod_t (n phihat(k_t))^2,
+// b_k the DFT of the regularised kernel K_R sampled on I_N^d (FP64 on the
+// device, W.cgrid as scratch); and add the near-field correction
+// sum_{|x_i - y_j| < eps_I h} w_j (K - K_R) to out (target order).
+uotk_status nfft_reg_table(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W);
+uotk_status nfft_near(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& src,
+                      const float* w, const NfftPoints& tgt, float* out);
 
 // Bounding box of point clouds on the device -> host (synchronises).
 uotk_status nfft_bbox(uotk_ctx* ctx, cudaStream_t s, int d, const float* a, int64_t na,

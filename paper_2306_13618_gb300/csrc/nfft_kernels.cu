@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(32 * WF_WARPS)
 template <int R>
 __global__ void __launch_bounds__(32 * WF_WARPS)
     k_wfft_lines(const float2* __restrict__ in, float2* __restrict__ out, int N, int mode,
-                 const float* __restrict__ scale) {
+                 const float* __restrict__ scale, const float* __restrict__ full) {
   constexpr int n = 32 * R;
   extern __shared__ __align__(16) float2 wsh[];
   float2* tw = wsh;
@@ -435,13 +435,16 @@ __global__ void __launch_bounds__(32 * WF_WARPS)
     warp_fft<R>(v, tw, mode == 1 ? +1 : -1);
     if (mode == 2) {
       // keep I_N, multiply by scale_k, back to natural frequency order, inverse
+      // (scale_k separable, or the full table [kz'][ky'][kx'] of a non-smooth kernel)
       const int kyp = (int)outer, kxp = kx0 + l;
-      const float fxy = scale[kxp] * scale[N + kyp];
+      const float fxy = full ? 0.f : scale[kxp] * scale[N + kyp];
 #pragma unroll
       for (int k1 = 0; k1 < R; ++k1) {
         const int f = k1 + R * br;
         const int kp = kept_pos(f, N, n);
-        const float fz = kp >= 0 ? fxy * scale[2 * N + kp] : 0.f;
+        const float fz = kp < 0 ? 0.f
+                         : full ? full[((size_t)kp * N + kyp) * N + kxp]
+                                : fxy * scale[2 * N + kp];
         tout[f * WF_PITCH + l] = make_float2(v[k1].x * fz, v[k1].y * fz);
       }
       __syncwarp();
@@ -471,17 +474,18 @@ __global__ void __launch_bounds__(32 * WF_WARPS)
 
 template <int R>
 uotk_status wfft_convolve(uotk_ctx* ctx, cudaStream_t s, int N, const float* scale,
-                          const float* grid_in, float2* A1, float2* A2, float* grid_out) {
+                          const float* full, const float* grid_in, float2* A1, float2* A2,
+                          float* grid_out) {
   constexpr int n = 32 * R;
   const size_t lsmem = sizeof(float2) * (n + 2 * n * WF_PITCH);
   UOTK_CUDA(ctx, smem_attr(s, k_wfft_lines<R>, lsmem));
   k_wfft_x_fwd<R><<<n * n / WF_WARPS, 32 * WF_WARPS, 0, s>>>(grid_in, A1, N);
   UOTK_LAUNCHED(ctx);
-  k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A1, A2, N, 0, scale);
+  k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A1, A2, N, 0, scale, full);
   UOTK_LAUNCHED(ctx);
-  k_wfft_lines<R><<<N * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A2, A2, N, 2, scale);
+  k_wfft_lines<R><<<N * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A2, A2, N, 2, scale, full);
   UOTK_LAUNCHED(ctx);
-  k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A2, A1, N, 1, scale);
+  k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A2, A1, N, 1, scale, full);
   UOTK_LAUNCHED(ctx);
   k_wfft_x_inv<R><<<n * n / WF_WARPS, 32 * WF_WARPS, 0, s>>>(A1, grid_out, N);
   UOTK_LAUNCHED(ctx);
@@ -502,7 +506,8 @@ __device__ __forceinline__ long long line_addr(int axis, int n, long long L, int
 __global__ void __launch_bounds__(FFT_THREADS)
     k_fft_pass(const float* __restrict__ rin, const float2* __restrict__ cin,
                float* __restrict__ rout, float2* __restrict__ cout, int n, int logn, int axis,
-               int mode, int dir, const float* __restrict__ scale, int N) {
+               int mode, int dir, const float* __restrict__ scale, int N,
+               const float* __restrict__ full) {
   extern __shared__ __align__(16) float2 fsh[];
   float2* tw = fsh;
   float2* buf = fsh + n / 2;
@@ -526,7 +531,8 @@ __global__ void __launch_bounds__(FFT_THREADS)
       const int kx = x < n / 2 ? x : x - n, ky = y < n / 2 ? y : y - n, kz = e < n / 2 ? e : e - n;
       float f = 0.f;
       if (kx >= -N / 2 && kx < N / 2 && ky >= -N / 2 && ky < N / 2 && kz >= -N / 2 && kz < N / 2)
-        f = scale[kx + N / 2] * scale[N + ky + N / 2] * scale[2 * N + kz + N / 2];
+        f = full ? full[((size_t)(kz + N / 2) * N + ky + N / 2) * N + kx + N / 2]
+                 : scale[kx + N / 2] * scale[N + ky + N / 2] * scale[2 * N + kz + N / 2];
       const float2 v = buf[i];
       buf[i] = make_float2(v.x * f, v.y * f);
     }
@@ -744,6 +750,7 @@ uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
 uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W,
                           const float* grid_in, float* grid_out) {
   const int n = P.n, N = P.N;
+  const float* full = P.kernel != UOTK_KERNEL_GAUSS ? W.full : nullptr;
   int logn = 0;
   while ((1 << logn) < n) ++logn;
   UOTK_PROF(ctx, s, "fft");
@@ -752,10 +759,10 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
     float2* A1 = W.cgrid;
     float2* A2 = W.cgrid + (size_t)n * n * N;
     switch (n) {
-      case 32: return wfft_convolve<1>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
-      case 64: return wfft_convolve<2>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
-      case 128: return wfft_convolve<4>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
-      case 256: return wfft_convolve<8>(ctx, s, N, W.scale, grid_in, A1, A2, grid_out);
+      case 32: return wfft_convolve<1>(ctx, s, N, W.scale, full, grid_in, A1, A2, grid_out);
+      case 64: return wfft_convolve<2>(ctx, s, N, W.scale, full, grid_in, A1, A2, grid_out);
+      case 128: return wfft_convolve<4>(ctx, s, N, W.scale, full, grid_in, A1, A2, grid_out);
+      case 256: return wfft_convolve<8>(ctx, s, N, W.scale, full, grid_in, A1, A2, grid_out);
       default: break;
     }
   }
@@ -763,19 +770,19 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
   const size_t smem = sizeof(float2) * (n / 2 + FFT_LINES * n);
   // forward x (real -> complex), forward y, z (forward, scale, inverse), inverse y, inverse x
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(grid_in, nullptr, nullptr, W.cgrid, n, logn, 0, 0,
-                                               -1, nullptr, N);
+                                               -1, nullptr, N, nullptr);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 1, 1,
-                                               -1, nullptr, N);
+                                               -1, nullptr, N, nullptr);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 2, 3,
-                                               -1, W.scale, N);
+                                               -1, W.scale, N, full);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, nullptr, W.cgrid, n, logn, 1, 1,
-                                               +1, nullptr, N);
+                                               +1, nullptr, N, nullptr);
   UOTK_LAUNCHED(ctx);
   k_fft_pass<<<blocks, FFT_THREADS, smem, s>>>(nullptr, W.cgrid, grid_out, nullptr, n, logn, 0, 2,
-                                               +1, nullptr, N);
+                                               +1, nullptr, N, nullptr);
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -803,6 +810,7 @@ void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWo
   const size_t pr = (size_t)P.n * P.n * P.N + (size_t)P.n * P.N * P.N;
   W.cgrid = cv.take<float2>(pr > n3 ? pr : n3);
   W.scale = cv.take<float>(3 * P.N);
+  W.full = P.kernel != UOTK_KERNEL_GAUSS ? cv.take<float>((size_t)P.N * P.N * P.N) : nullptr;
 }
 
 }  // namespace uotk

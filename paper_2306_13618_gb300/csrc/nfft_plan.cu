@@ -300,23 +300,52 @@ int nfft_max_units(const NfftParams& P, int64_t n) {
 uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const float hi[3],
                              double eps, const uotk_sum_opts* opts, NfftParams* P) {
   P->d = d;
-  P->n = (opts && opts->grid) ? opts->grid : 128;
+  P->kernel = opts ? opts->kernel : UOTK_KERNEL_GAUSS;
+  const bool reg = P->kernel != UOTK_KERNEL_GAUSS;
+  P->n = (opts && opts->grid) ? opts->grid : (reg ? 256 : 128);
   P->N = (opts && opts->bandwidth) ? opts->bandwidth : P->n / 2;
   P->eps = eps;
   const double sigma = (double)P->n / P->N;
   P->b = (float)(M_PI * (2.0 - 1.0 / sigma));
-  double L = 0.0;
+  double L = 0.0, D2 = 0.0;
   for (int t = 0; t < 3; ++t) {
     if (t < d) {
       P->c[t] = (float)(0.5 * ((double)lo[t] + (double)hi[t]));
       L = fmax(L, (double)hi[t] - (double)lo[t]);
+      D2 += ((double)hi[t] - (double)lo[t]) * ((double)hi[t] - (double)lo[t]);
     } else {
       P->c[t] = 0.f;
     }
   }
   if (!isfinite(L)) return set_error(ctx, UOTK_ERR_NONFINITE, "NFFT plan: non-finite coordinates");
   const double target = (opts && opts->target_err > 0) ? opts->target_err : 1e-6;
-  if (opts && opts->period > 0) {
+  if (reg) {
+    // Sec. 4.2: every difference must stay where K_R = K or the near field
+    // corrects it, |x - y| <= (1/2 - eps_B) h; eps_I = eps_B = p/N.
+    if (P->n < 2 * P->N)
+      return set_error(ctx, UOTK_ERR_INVALID,
+                       "NFFT: the non-Gaussian kernels need oversampling grid >= 2 bandwidth");
+    P->reg_p = (opts && opts->reg_degree) ? opts->reg_degree : 4;
+    if (P->reg_p < 2 || P->reg_p > 12)
+      return set_error(ctx, UOTK_ERR_INVALID, "NFFT: regularisation degree %d not in [2, 12]",
+                       P->reg_p);
+    P->eps_i = (double)P->reg_p / P->N;
+    if (P->eps_i > 0.125)
+      return set_error(ctx, UOTK_ERR_INVALID,
+                       "NFFT: regularisation width p/N = %d/%d above 1/8; raise the bandwidth",
+                       P->reg_p, P->N);
+    const double diam = sqrt(D2);
+    const double hmin = diam / (0.5 - P->eps_i);
+    if (opts && opts->period > 0) {
+      P->h = opts->period;
+      if (P->h < hmin * (1.0 + 1e-6))
+        return set_error(ctx, UOTK_ERR_INVALID,
+                         "NFFT: period %g below %g = diameter / (1/2 - eps_B) of the points",
+                         P->h, hmin);
+    } else {
+      P->h = hmin > 0.0 ? hmin * (1.0 + 1e-6) : 1.0;
+    }
+  } else if (opts && opts->period > 0) {
     P->h = opts->period;
   } else {
     // Balance the periodisation error exp(-(h-L)^2/eps) against the Fourier
@@ -344,6 +373,19 @@ uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const floa
   P->tiles1 = P->n / NFFT_TILE;
   P->E = NFFT_TILE + 2 * P->m - 1;
   return UOTK_OK;
+}
+
+void nfft_deconv_rows(const NfftParams& P, double* rows) {
+  const double b = M_PI * (2.0 - (double)P.N / P.n);
+  const double m = P.m;
+  const double sh = sinh(b * m);
+  for (int t = 0; t < 3; ++t)
+    for (int i = 0; i < P.N; ++i) {
+      const double k = i - P.N / 2;
+      const double arg = b * b - pow(2.0 * M_PI * k / P.n, 2);
+      const double nph = bessel_i0(m * sqrt(arg > 0 ? arg : 0.0)) * M_PI * m / sh;
+      rows[t * P.N + i] = (t < P.d || i == P.N / 2) ? 1.0 / (nph * nph) : 0.0;
+    }
 }
 
 void nfft_scale_table(const NfftParams& P, float* table) {

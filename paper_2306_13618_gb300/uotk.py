@@ -38,7 +38,7 @@ class SumOpts(ctypes.Structure):
     _fields_ = [("method", ctypes.c_int32), ("grid", ctypes.c_int32),
                 ("bandwidth", ctypes.c_int32), ("cutoff", ctypes.c_int32),
                 ("period", ctypes.c_double), ("target_err", ctypes.c_double),
-                ("kernel", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("kernel", ctypes.c_int32), ("reg_degree", ctypes.c_int32)]
 
 
 KERNELS = {"gauss": 0, "laplace": 1, "imq": 2, "energy": 3}
@@ -211,13 +211,14 @@ def _pts(t, name):
 
 
 def _opts(method="direct", grid=0, bandwidth=0, cutoff=0, period=0.0, target_err=0.0,
-          kernel="gauss"):
-    """uotk_sum_opts; kernel is one of Table tab:0 (gauss, laplace, imq, energy)."""
+          kernel="gauss", reg_degree=0):
+    """uotk_sum_opts; kernel is one of Table tab:0 (gauss, laplace, imq, energy);
+    reg_degree: the NFFT regularisation degree p of the non-Gaussian kernels."""
     m = {"direct": DIRECT, "nfft": NFFT, "direct_bf16": DIRECT_BF16,
          "direct_bf16x3": DIRECT_BF16X3}.get(method, method)
     k = KERNELS.get(kernel, kernel)
     return SumOpts(int(m), int(grid), int(bandwidth), int(cutoff), float(period),
-                   float(target_err), int(k), 0)
+                   float(target_err), int(k), int(reg_degree))
 
 
 def _ptr(t):

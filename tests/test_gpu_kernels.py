@@ -67,7 +67,7 @@ def test_other_kernels_unsupported_paths(uotk):
     W = inputs.uniform_box(n=200, m=200)
     args = (dev(W.x), dev(W.a), dev(W.y), dev(W.b))
     with pytest.raises(uotk.UotkError) as e:
-        uotk.mmd2(*args, 0.2, method="nfft", kernel="laplace")
+        uotk.mmd2(*args, 0.2, method="direct_bf16", kernel="laplace")
     assert e.value.status == 4
     with pytest.raises(uotk.UotkError) as e:
         uotk.uot_sinkhorn(*args, W.eps, W.rho, max_sweeps=3, kernel="imq")
