@@ -247,36 +247,44 @@ __device__ __forceinline__ float near_kernel(float r2, float c1, float c2) {
   return -c1 * sqrtf(r2);
 }
 
-// One CTA per target tile (persistent over tiles): each thread holds two
+// One CTA per target tile (persistent over tiles): each thread holds NEAR_TPT
 // targets; the sources of the (2R+1)^3 neighbouring tiles, contiguous per
-// (z, y) row of tiles in sorted order, are staged through shared memory.
-template <int KIND>
+// (z, y) row of tiles in sorted order, are staged through shared memory.  T_I
+// has P coefficients held in registers (P = 12 serves any p <= 12, the unused
+// coefficients being zero).
+constexpr int NEAR_TPT = 4;
+template <int KIND, int P>
 __global__ void __launch_bounds__(NEAR_THREADS)
     k_near(const int4* __restrict__ tcell, const int* __restrict__ ttile,
            const int4* __restrict__ scell, const int* __restrict__ stile,
            const float* __restrict__ w, NearArgs a, float* __restrict__ out) {
   __shared__ float4 sh[NEAR_THREADS];
-  const int T = a.tiles1;
+  float e[P];
+#pragma unroll
+  for (int q = 0; q < P; ++q) e[q] = a.e[q];
+  const float r2i = a.r2i, inv_r2i = a.inv_r2i, c1 = a.c1, c2 = a.c2;
+  const int T = a.tiles1, R = a.R;
   const int tiles = T * T * T;
   for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int tb = ttile[tile], te = ttile[tile + 1];
     if (tb == te) continue;
     const int tx = tile % T, ty = (tile / T) % T, tz = tile / (T * T);
-    for (int t0 = tb; t0 < te; t0 += 2 * NEAR_THREADS) {
-      float px[2], py[2], pz[2], acc[2] = {0.f, 0.f};
+    for (int t0 = tb; t0 < te; t0 += NEAR_TPT * NEAR_THREADS) {
+      float px[NEAR_TPT], py[NEAR_TPT], pz[NEAR_TPT], acc[NEAR_TPT];
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < NEAR_TPT; ++q) {
         const int i = t0 + threadIdx.x + q * NEAR_THREADS;
-        px[q] = py[q] = pz[q] = 1e30f;   // far from every source
+        px[q] = py[q] = pz[q] = 1e18f;   // far from every source
+        acc[q] = 0.f;
         if (i < te) grid_pos(tcell[i], px[q], py[q], pz[q]);
       }
-      for (int dz = -a.R; dz <= a.R; ++dz) {
+      for (int dz = -R; dz <= R; ++dz) {
         const int z = tz + dz;
         if (z < 0 || z >= T) continue;
-        for (int dy = -a.R; dy <= a.R; ++dy) {
+        for (int dy = -R; dy <= R; ++dy) {
           const int y = ty + dy;
           if (y < 0 || y >= T) continue;
-          const int x0 = max(tx - a.R, 0), x1 = min(tx + a.R, T - 1);
+          const int x0 = max(tx - R, 0), x1 = min(tx + R, T - 1);
           const int row = (z * T + y) * T;
           const int sb = stile[row + x0], se = stile[row + x1 + 1];
           for (int s0 = sb; s0 < se; s0 += NEAR_THREADS) {
@@ -292,14 +300,15 @@ __global__ void __launch_bounds__(NEAR_THREADS)
             for (int k = 0; k < cnt; ++k) {
               const float4 s = sh[k];
 #pragma unroll
-              for (int q = 0; q < 2; ++q) {
+              for (int q = 0; q < NEAR_TPT; ++q) {
                 const float dx = px[q] - s.x, dy2 = py[q] - s.y, dz2 = pz[q] - s.z;
                 const float r2 = fmaf(dx, dx, fmaf(dy2, dy2, dz2 * dz2));
-                if (r2 < a.r2i) {
-                  const float u = r2 * a.inv_r2i;
-                  float ti = a.e[a.P - 1];
-                  for (int e = a.P - 2; e >= 0; --e) ti = fmaf(ti, u, a.e[e]);
-                  acc[q] = fmaf(s.w, near_kernel<KIND>(r2, a.c1, a.c2) - ti, acc[q]);
+                if (r2 < r2i) {
+                  const float u = r2 * inv_r2i;
+                  float ti = e[P - 1];
+#pragma unroll
+                  for (int j2 = P - 2; j2 >= 0; --j2) ti = fmaf(ti, u, e[j2]);
+                  acc[q] = fmaf(s.w, near_kernel<KIND>(r2, c1, c2) - ti, acc[q]);
                 }
               }
             }
@@ -307,11 +316,34 @@ __global__ void __launch_bounds__(NEAR_THREADS)
         }
       }
 #pragma unroll
-      for (int q = 0; q < 2; ++q) {
+      for (int q = 0; q < NEAR_TPT; ++q) {
         const int i = t0 + threadIdx.x + q * NEAR_THREADS;
         if (i < te) out[i] += acc[q];
       }
     }
+  }
+}
+
+template <int KIND>
+void launch_near(int P, int blocks, cudaStream_t s, const NfftPoints& src, const float* w,
+                 const NfftPoints& tgt, const NearArgs& a, float* out) {
+  switch (P) {
+    case 4:
+      k_near<KIND, 4><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
+                                                      src.tile_start, w, a, out);
+      break;
+    case 6:
+      k_near<KIND, 6><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
+                                                      src.tile_start, w, a, out);
+      break;
+    case 8:
+      k_near<KIND, 8><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
+                                                      src.tile_start, w, a, out);
+      break;
+    default:
+      k_near<KIND, REG_MAXP><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
+                                                             src.tile_start, w, a, out);
+      break;
   }
 }
 
@@ -380,18 +412,13 @@ uotk_status nfft_near(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const 
   UOTK_PROF(ctx, s, "near");
   switch (P.kernel) {
     case UOTK_KERNEL_LAPLACE:
-      k_near<UOTK_KERNEL_LAPLACE><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start,
-                                                                   src.cell, src.tile_start, w, a,
-                                                                   out);
+      launch_near<UOTK_KERNEL_LAPLACE>(a.P, blocks, s, src, w, tgt, a, out);
       break;
     case UOTK_KERNEL_IMQ:
-      k_near<UOTK_KERNEL_IMQ><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
-                                                               src.tile_start, w, a, out);
+      launch_near<UOTK_KERNEL_IMQ>(a.P, blocks, s, src, w, tgt, a, out);
       break;
     default:
-      k_near<UOTK_KERNEL_ENERGY><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start,
-                                                                  src.cell, src.tile_start, w, a,
-                                                                  out);
+      launch_near<UOTK_KERNEL_ENERGY>(a.P, blocks, s, src, w, tgt, a, out);
       break;
   }
   UOTK_LAUNCHED(ctx);
