@@ -403,6 +403,57 @@ def other_kernel_extras(uotk, ctx, stream, W, x, b, y):
     return res
 
 
+def other_kernel_nfft_extras(uotk, ctx, stream):
+    """The regularised NFFT form of the Laplace, IMQ and energy kernels (Sec. 4.2)
+    against their direct FP32 form on the paper's empirical measures (Sec. 5.1.1:
+    points and weights U[0, 1]) at n = m = 2^20, d = 3, with the kernel
+    parameters of Table Tab:Accuracy_analysis3 (ell = 1/2, c = 1): one kernel sum
+    each, the error on 256 sampled targets, and the near field's share."""
+    import numpy as np
+    import torch
+
+    import oracle
+    from paper_2306_13618_gb300 import inputs
+
+    g = inputs.rng(741)
+    n = 1 << 20
+    src = g.uniform(0, 1, (n, 3)).astype(np.float32)
+    w = g.uniform(0, 1, n).astype(np.float32)
+    tgt = g.uniform(0, 1, (n, 3)).astype(np.float32)
+    ds, dw, dt = (torch.from_numpy(a).cuda() for a in (src, w, tgt))
+    idx = inputs.subsample_rows(inputs.rng(5), 256, n)
+    S, Wt, T = src.astype(np.float64), w.astype(np.float64), tgt[idx].astype(np.float64)
+    res = {"workload": "uniform [0,1]^3, n = m = 2^20, weights U[0,1]"}
+    for kind, p in (("laplace", 0.5), ("imq", 1.0), ("energy", 1.0)):
+        ref = oracle.ksum_kernel(kind, p, S, Wt, T)
+        row = {"p": p}
+        for meth in ("nfft", "direct"):
+            try:
+                uotk.kernel_sum(ds, dw, dt, p, method=meth, kernel=kind, ctx=ctx)
+                torch.cuda.synchronize()
+                ctx.profile_reset()
+                ctx.set_profiling(True)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                out = uotk.kernel_sum(ds, dw, dt, p, method=meth, kernel=kind, ctx=ctx)
+                e1.record(stream)
+                e1.synchronize()
+                ctx.set_profiling(False)
+                prof = ctx.profile()
+                ms = e0.elapsed_time(e1)
+                o = out.cpu().numpy()[idx].astype(np.float64)
+                row[meth] = {"ms_per_sum": ms,
+                             "rel_err_max": float(np.max(np.abs(o - ref)) / np.max(np.abs(ref)))}
+                if meth == "nfft":
+                    row[meth]["near_ms"] = prof.get("near", (0, 0.0))[1]
+            except uotk.UotkError as e:
+                row[meth] = {"error": str(e)}
+        if "ms_per_sum" in row.get("nfft", {}) and "ms_per_sum" in row.get("direct", {}):
+            row["speedup"] = row["direct"]["ms_per_sum"] / row["nfft"]["ms_per_sum"]
+        res[kind] = row
+    return res
+
+
 def batch_main(args, rank, world, local):
     """512 independent problems of uneven sizes solved together by
     uotk_uot_sinkhorn_batch (tol 1e-6, a sweep cap); value = sweeps of all pairs
@@ -662,6 +713,7 @@ def main():
         extras["gradients"] = gradient_extras(uotk, ctx, stream, W, x, a, y, b, args.method)
         extras["gauss64"] = high_dim_extras(uotk, ctx, stream, rates, sms, peaks)
         extras["other_kernels"] = other_kernel_extras(uotk, ctx, stream, W, x, b, y)
+        extras["other_kernels_nfft"] = other_kernel_nfft_extras(uotk, ctx, stream)
     if "nfft" in extras and "direct" in extras and "ms_per_matvec" in extras.get("direct", {}) \
             and "ms_per_matvec" in extras.get("nfft", {}):
         extras["nfft_speedup_vs_direct"] = extras["direct"]["ms_per_matvec"] / extras["nfft"]["ms_per_matvec"]
