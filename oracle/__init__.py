@@ -54,20 +54,23 @@ def _load():
     lib.orc_ksum.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, ctypes.c_double, _D]
     lib.orc_uot_sinkhorn.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
                                      ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D]
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, _D, _D,
+                                     ctypes.c_double]
     lib.orc_dual_value.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
                                    ctypes.c_double, ctypes.c_double, ctypes.c_double,
-                                   _D, _D, ctypes.c_int]
+                                   _D, _D, ctypes.c_int, ctypes.c_double]
     lib.orc_dual_value.restype = ctypes.c_double
     lib.orc_primal_value.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
-                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D]
+                                     ctypes.c_double, ctypes.c_double, ctypes.c_double, _D, _D,
+                                     ctypes.c_double]
     lib.orc_primal_value.restype = ctypes.c_double
     lib.orc_plan.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D, ctypes.c_double,
-                             _D, _D, ctypes.c_int, _D]
+                             _D, _D, ctypes.c_int, _D, ctypes.c_double]
     lib.orc_mmd2.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D, ctypes.c_double, _D]
     lib.orc_mmd2.restype = ctypes.c_double
     lib.orc_sinkhorn_divergence.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
-                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, _D]
+                                            ctypes.c_double, ctypes.c_double, ctypes.c_int, _D,
+                                            ctypes.c_double]
     lib.orc_sinkhorn_divergence.restype = ctypes.c_double
     lib.orc_balanced_sinkhorn.argtypes = [ctypes.c_int, _D, _I64, _D, _D, _I64, _D,
                                           ctypes.c_double, ctypes.c_int, _D, _D]
@@ -129,10 +132,11 @@ def ksum(src, w, tgt, eps):
 
 
 def uot_sinkhorn(x, mu, y, nu, eps, eta1, eta2=None, sweeps=100, ref=0,
-                 logdomain=False, gamma0=None):
+                 logdomain=False, gamma0=None, r=2):
     """Alg. 1 for `sweeps` sweeps (beta then gamma) from gamma0 (default 0).
 
     lambda = 1/eps.  ref 0: product reference (paper); ref 1: counting reference.
+    r: the cost |x - y|^r (2: Gaussian Gibbs kernel, 1: Laplacian).
     Returns (beta, gamma) as float64 arrays."""
     x, y, mu, nu = _pts(x), _pts(y), _vec(mu), _vec(nu)
     eta2 = eta1 if eta2 is None else eta2
@@ -140,32 +144,32 @@ def uot_sinkhorn(x, mu, y, nu, eps, eta1, eta2=None, sweeps=100, ref=0,
     gamma = np.zeros(y.shape[0]) if gamma0 is None else _vec(gamma0).copy()
     _load().orc_uot_sinkhorn(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0], _p(nu),
                              1.0 / eps, float(eta1), float(eta2), int(sweeps), int(ref),
-                             int(bool(logdomain)), _p(beta), _p(gamma))
+                             int(bool(logdomain)), _p(beta), _p(gamma), float(r))
     return beta, gamma
 
 
-def dual_value(x, mu, y, nu, eps, eta1, eta2, beta, gamma, ref=0):
-    """D(beta, gamma) of Eq. (dual_euot)."""
+def dual_value(x, mu, y, nu, eps, eta1, eta2, beta, gamma, ref=0, r=2):
+    """D(beta, gamma) of Eq. (dual_euot) with the cost |x - y|^r."""
     x, y, mu, nu, beta, gamma = _pts(x), _pts(y), _vec(mu), _vec(nu), _vec(beta), _vec(gamma)
     return _load().orc_dual_value(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0],
                                   _p(nu), 1.0 / eps, float(eta1), float(eta2),
-                                  _p(beta), _p(gamma), int(ref))
+                                  _p(beta), _p(gamma), int(ref), float(r))
 
 
-def primal_value(x, mu, y, nu, eps, eta1, eta2, beta, gamma):
+def primal_value(x, mu, y, nu, eps, eta1, eta2, beta, gamma, r=2):
     """Discrete primal objective of Eq. (W4) at the plan of the duals (product reference)."""
     x, y, mu, nu, beta, gamma = _pts(x), _pts(y), _vec(mu), _vec(nu), _vec(beta), _vec(gamma)
     return _load().orc_primal_value(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0],
                                     _p(nu), 1.0 / eps, float(eta1), float(eta2),
-                                    _p(beta), _p(gamma))
+                                    _p(beta), _p(gamma), float(r))
 
 
-def plan(x, mu, y, nu, eps, beta, gamma, ref=0):
+def plan(x, mu, y, nu, eps, beta, gamma, ref=0, r=2):
     """pi_ij = mu_i nu_j e^{lambda(beta_i+gamma_j)} k_ij (ref 0), n x m dense."""
     x, y, mu, nu, beta, gamma = _pts(x), _pts(y), _vec(mu), _vec(nu), _vec(beta), _vec(gamma)
     pi = np.empty((x.shape[0], y.shape[0]))
     _load().orc_plan(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y), y.shape[0], _p(nu),
-                     1.0 / eps, _p(beta), _p(gamma), int(ref), _p(pi))
+                     1.0 / eps, _p(beta), _p(gamma), int(ref), _p(pi), float(r))
     return pi
 
 
@@ -178,13 +182,13 @@ def mmd2(x, mu, y, nu, ell, return_parts=False):
     return (v, parts) if return_parts else v
 
 
-def sinkhorn_divergence(x, mu, y, nu, eps, eta, sweeps=100, return_parts=False):
-    """Unbalanced Sinkhorn divergence of Eq. (586) (product reference)."""
+def sinkhorn_divergence(x, mu, y, nu, eps, eta, sweeps=100, return_parts=False, r=2):
+    """Unbalanced Sinkhorn divergence of Eq. (586) (product reference), cost |x - y|^r."""
     x, y, mu, nu = _pts(x), _pts(y), _vec(mu), _vec(nu)
     parts = np.empty(3)
     v = _load().orc_sinkhorn_divergence(x.shape[1], _p(x), x.shape[0], _p(mu), _p(y),
                                         y.shape[0], _p(nu), 1.0 / eps, float(eta),
-                                        int(sweeps), _p(parts))
+                                        int(sweeps), _p(parts), float(r))
     return (v, parts) if return_parts else v
 
 

@@ -41,6 +41,14 @@ static inline double sqdist(int d, const double* a, const double* b) {
   return r;
 }
 
+/* The cost d(x, y)^r of Eq. (W4): r = 2 the squared Euclidean distance (the
+ * Gaussian Gibbs kernel), r = 1 the distance itself (the Laplacian kernel
+ * e^{-lambda |x - y|} of the complexity paragraph of Sec. 4.4). */
+static inline double cost_r(int d, const double* a, const double* b, double r) {
+  const double s = sqdist(d, a, b);
+  return r == 2.0 ? s : (r == 1.0 ? sqrt(s) : pow(sqrt(s), r));
+}
+
 int orc_num_threads(void) {
 #ifdef _OPENMP
   return omp_get_max_threads();
@@ -82,7 +90,7 @@ void orc_ksum(int d, const double* src, int64_t n, const double* w,
 static void half_step(int d, const double* x, int64_t n, const double* mu,
                       const double* y, int64_t m, const double* nu,
                       double lambda, double eta, int ref, int logdomain,
-                      const double* gamma, double* beta) {
+                      const double* gamma, double* beta, double r) {
   const double q = eta / (1.0 + eta * lambda);
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
@@ -90,7 +98,7 @@ static void half_step(int d, const double* x, int64_t n, const double* mu,
     if (!logdomain) {
       nsum acc = {0.0, 0.0};
       for (int64_t j = 0; j < m; ++j) {
-        double kij = exp(-lambda * sqdist(d, x + i * d, y + j * d));
+        double kij = exp(-lambda * cost_r(d, x + i * d, y + j * d, r));
         double wj = exp(lambda * gamma[j]) * (ref == 0 ? nu[j] : 1.0);
         nsum_add(&acc, kij * wj);
       }
@@ -98,13 +106,13 @@ static void half_step(int d, const double* x, int64_t n, const double* mu,
     } else {
       double mx = -INFINITY;
       for (int64_t j = 0; j < m; ++j) {
-        double a = -lambda * sqdist(d, x + i * d, y + j * d) + lambda * gamma[j] +
+        double a = -lambda * cost_r(d, x + i * d, y + j * d, r) + lambda * gamma[j] +
                    (ref == 0 ? log(nu[j]) : 0.0);
         if (a > mx) mx = a;
       }
       nsum acc = {0.0, 0.0};
       for (int64_t j = 0; j < m; ++j) {
-        double a = -lambda * sqdist(d, x + i * d, y + j * d) + lambda * gamma[j] +
+        double a = -lambda * cost_r(d, x + i * d, y + j * d, r) + lambda * gamma[j] +
                    (ref == 0 ? log(nu[j]) : 0.0);
         nsum_add(&acc, exp(a - mx));
       }
@@ -121,10 +129,10 @@ static void half_step(int d, const double* x, int64_t n, const double* mu,
 void orc_uot_sinkhorn(int d, const double* x, int64_t n, const double* mu,
                       const double* y, int64_t m, const double* nu,
                       double lambda, double eta1, double eta2, int sweeps,
-                      int ref, int logdomain, double* beta, double* gamma) {
+                      int ref, int logdomain, double* beta, double* gamma, double r) {
   for (int s = 0; s < sweeps; ++s) {
-    half_step(d, x, n, mu, y, m, nu, lambda, eta1, ref, logdomain, gamma, beta);
-    half_step(d, y, m, nu, x, n, mu, lambda, eta2, ref, logdomain, beta, gamma);
+    half_step(d, x, n, mu, y, m, nu, lambda, eta1, ref, logdomain, gamma, beta, r);
+    half_step(d, y, m, nu, x, n, mu, lambda, eta2, ref, logdomain, beta, gamma, r);
   }
 }
 
@@ -138,7 +146,7 @@ void orc_uot_sinkhorn(int d, const double* x, int64_t n, const double* mu,
 double orc_dual_value(int d, const double* x, int64_t n, const double* mu,
                       const double* y, int64_t m, const double* nu,
                       double lambda, double eta1, double eta2,
-                      const double* beta, const double* gamma, int ref) {
+                      const double* beta, const double* gamma, int ref, double r) {
   nsum a = {0, 0}, b = {0, 0}, sm = {0, 0}, sn = {0, 0};
   for (int64_t i = 0; i < n; ++i) {
     nsum_add(&a, mu[i] * exp(-beta[i] / eta1));
@@ -151,14 +159,14 @@ double orc_dual_value(int d, const double* x, int64_t n, const double* mu,
   double* row = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
 #pragma omp parallel for schedule(static)
   for (int64_t i = 0; i < n; ++i) {
-    nsum r = {0, 0};
+    nsum rs = {0, 0};
     for (int64_t j = 0; j < m; ++j) {
       /* e^{lambda beta_i} k_ij e^{lambda gamma_j} as one exponential, which
          stays finite where the factors alone would overflow or underflow */
-      double v = exp(lambda * (beta[i] + gamma[j]) - lambda * sqdist(d, x + i * d, y + j * d));
-      nsum_add(&r, ref == 0 ? mu[i] * v * nu[j] : v);
+      double v = exp(lambda * (beta[i] + gamma[j]) - lambda * cost_r(d, x + i * d, y + j * d, r));
+      nsum_add(&rs, ref == 0 ? mu[i] * v * nu[j] : v);
     }
-    row[i] = nsum_get(&r);
+    row[i] = nsum_get(&rs);
   }
   nsum c = {0, 0};
   for (int64_t i = 0; i < n; ++i) nsum_add(&c, row[i]);
@@ -174,11 +182,11 @@ double orc_dual_value(int d, const double* x, int64_t n, const double* mu,
  *   pi_ij =           e^{lambda beta_i} k_ij e^{lambda gamma_j}   (ref 1). */
 void orc_plan(int d, const double* x, int64_t n, const double* mu,
               const double* y, int64_t m, const double* nu, double lambda,
-              const double* beta, const double* gamma, int ref, double* pi) {
+              const double* beta, const double* gamma, int ref, double* pi, double r) {
   for (int64_t i = 0; i < n; ++i)
     for (int64_t j = 0; j < m; ++j) {
       double v = exp(lambda * (beta[i] + gamma[j]) -
-                     lambda * sqdist(d, x + i * d, y + j * d));
+                     lambda * cost_r(d, x + i * d, y + j * d, r));
       pi[i * m + j] = ref == 0 ? mu[i] * nu[j] * v : v;
     }
 }
@@ -191,14 +199,14 @@ void orc_plan(int d, const double* x, int64_t n, const double* mu,
 double orc_primal_value(int d, const double* x, int64_t n, const double* mu,
                         const double* y, int64_t m, const double* nu,
                         double lambda, double eta1, double eta2,
-                        const double* beta, const double* gamma) {
+                        const double* beta, const double* gamma, double r) {
   nsum cost = {0, 0}, ent = {0, 0}, tot = {0, 0}, sm = {0, 0}, sn = {0, 0};
   double* col = (double*)calloc((size_t)(m > 0 ? m : 1), sizeof(double));
   nsum marg1 = {0, 0}, marg2 = {0, 0};
   for (int64_t i = 0; i < n; ++i) {
-    nsum r = {0, 0};
+    nsum rs = {0, 0};
     for (int64_t j = 0; j < m; ++j) {
-      double dij = sqdist(d, x + i * d, y + j * d);
+      double dij = cost_r(d, x + i * d, y + j * d, r);
       double lv = lambda * (beta[i] + gamma[j]) - lambda * dij; /* log(pi/(mu nu)) */
       double p = mu[i] * nu[j] * exp(lv);
       nsum_add(&cost, dij * p);
@@ -206,10 +214,10 @@ double orc_primal_value(int d, const double* x, int64_t n, const double* mu,
       nsum_add(&ent, mu[i] * nu[j]);
       nsum_add(&ent, -p);
       nsum_add(&tot, p);
-      nsum_add(&r, p);
+      nsum_add(&rs, p);
       col[j] += p;
     }
-    double ri = nsum_get(&r);
+    double ri = nsum_get(&rs);
     if (ri > 0) nsum_add(&marg1, ri * log(ri / mu[i]));
     nsum_add(&sm, mu[i]);
   }
@@ -254,20 +262,20 @@ double orc_mmd2(int d, const double* x, int64_t n, const double* mu,
  * parts (may be NULL) receives the three UOT values. */
 double orc_sinkhorn_divergence(int d, const double* x, int64_t n, const double* mu,
                                const double* y, int64_t m, const double* nu,
-                               double lambda, double eta, int sweeps, double* parts) {
+                               double lambda, double eta, int sweeps, double* parts, double r) {
   int64_t nmax = n > m ? n : m;
   double* b = (double*)malloc(sizeof(double) * (size_t)(nmax > 0 ? nmax : 1));
   double* g = (double*)malloc(sizeof(double) * (size_t)(nmax > 0 ? nmax : 1));
   double v[3];
   memset(g, 0, sizeof(double) * (size_t)m);
-  orc_uot_sinkhorn(d, x, n, mu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g);
-  v[0] = orc_dual_value(d, x, n, mu, y, m, nu, lambda, eta, eta, b, g, 0);
+  orc_uot_sinkhorn(d, x, n, mu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g, r);
+  v[0] = orc_dual_value(d, x, n, mu, y, m, nu, lambda, eta, eta, b, g, 0, r);
   memset(g, 0, sizeof(double) * (size_t)n);
-  orc_uot_sinkhorn(d, x, n, mu, x, n, mu, lambda, eta, eta, sweeps, 0, 0, b, g);
-  v[1] = orc_dual_value(d, x, n, mu, x, n, mu, lambda, eta, eta, b, g, 0);
+  orc_uot_sinkhorn(d, x, n, mu, x, n, mu, lambda, eta, eta, sweeps, 0, 0, b, g, r);
+  v[1] = orc_dual_value(d, x, n, mu, x, n, mu, lambda, eta, eta, b, g, 0, r);
   memset(g, 0, sizeof(double) * (size_t)m);
-  orc_uot_sinkhorn(d, y, m, nu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g);
-  v[2] = orc_dual_value(d, y, m, nu, y, m, nu, lambda, eta, eta, b, g, 0);
+  orc_uot_sinkhorn(d, y, m, nu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g, r);
+  v[2] = orc_dual_value(d, y, m, nu, y, m, nu, lambda, eta, eta, b, g, 0, r);
   free(b);
   free(g);
   nsum sm = {0, 0}, sn = {0, 0};
@@ -426,13 +434,13 @@ double orc_sinkhorn_divergence_grad(int d, const double* x, int64_t n, const dou
   double v[3];
   /* UOT(mu, nu) */
   memset(g, 0, sizeof(double) * (size_t)m);
-  orc_uot_sinkhorn(d, x, n, mu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g);
-  v[0] = orc_dual_value(d, x, n, mu, y, m, nu, lambda, eta, eta, b, g, 0);
+  orc_uot_sinkhorn(d, x, n, mu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g, 2.0);
+  v[0] = orc_dual_value(d, x, n, mu, y, m, nu, lambda, eta, eta, b, g, 0, 2.0);
   orc_dual_grad(d, x, n, mu, y, m, nu, lambda, eta, eta, b, g, gmu, gx, gnu, gy);
   /* UOT(mu, mu) */
   memset(g, 0, sizeof(double) * (size_t)n);
-  orc_uot_sinkhorn(d, x, n, mu, x, n, mu, lambda, eta, eta, sweeps, 0, 0, b, g);
-  v[1] = orc_dual_value(d, x, n, mu, x, n, mu, lambda, eta, eta, b, g, 0);
+  orc_uot_sinkhorn(d, x, n, mu, x, n, mu, lambda, eta, eta, sweeps, 0, 0, b, g, 2.0);
+  v[1] = orc_dual_value(d, x, n, mu, x, n, mu, lambda, eta, eta, b, g, 0, 2.0);
   orc_dual_grad(d, x, n, mu, x, n, mu, lambda, eta, eta, b, g, w1, p1, w2, p2);
   for (int64_t i = 0; i < n; ++i) {
     gmu[i] -= 0.5 * (w1[i] + w2[i]);
@@ -440,8 +448,8 @@ double orc_sinkhorn_divergence_grad(int d, const double* x, int64_t n, const dou
   }
   /* UOT(nu, nu) */
   memset(g, 0, sizeof(double) * (size_t)m);
-  orc_uot_sinkhorn(d, y, m, nu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g);
-  v[2] = orc_dual_value(d, y, m, nu, y, m, nu, lambda, eta, eta, b, g, 0);
+  orc_uot_sinkhorn(d, y, m, nu, y, m, nu, lambda, eta, eta, sweeps, 0, 0, b, g, 2.0);
+  v[2] = orc_dual_value(d, y, m, nu, y, m, nu, lambda, eta, eta, b, g, 0, 2.0);
   orc_dual_grad(d, y, m, nu, y, m, nu, lambda, eta, eta, b, g, w1, p1, w2, p2);
   for (int64_t j = 0; j < m; ++j) {
     gnu[j] -= 0.5 * (w1[j] + w2[j]);

@@ -240,3 +240,55 @@ def test_lambda_scaling_reaches_the_fixed_point_of_the_last_lambda():
         be, gam = oracle.uot_sinkhorn(x, a, y, b, eps, eta, sweeps=60000, gamma0=gam)
     rb, rg = oracle.uot_sinkhorn(x, a, y, b, 0.01, eta, sweeps=60000)
     assert np.max(np.abs(be - rb)) <= 1e-12 and np.max(np.abs(gam - rg)) <= 1e-12
+
+
+@pytest.mark.parametrize("eta1,eta2,lam", [(1.0, 1.0, 20.0), (0.5, 2.0, 5.0)])
+def test_constant_cost_closed_form_r1(oracle_lib, eta1, eta2, lam):
+    """The cost |x - y| (r = 1): with every pair at distance D the optimum is again
+    c* mu (x) nu of Eq. (561), now with D the distance, not its square."""
+    g = np.random.default_rng(11)
+    n, m = 5, 6
+    x = np.tile([0.1, -0.2, 0.05], (n, 1))
+    y = np.tile([-0.15, 0.1, 0.2], (m, 1))
+    mu = g.uniform(0.5, 1.5, n)
+    nu = g.uniform(0.5, 1.5, m) * 0.6
+    D = float(np.linalg.norm(np.array([0.25, -0.3, -0.15])))
+    c, bstar, gstar, val = _closed_form_constant_cost(D, mu.sum(), nu.sum(), lam, eta1, eta2)
+    beta, gamma = oracle.uot_sinkhorn(x, mu, y, nu, 1.0 / lam, eta1, eta2, sweeps=3000, r=1)
+    assert np.allclose(beta, bstar, rtol=0, atol=1e-12)
+    assert np.allclose(gamma, gstar, rtol=0, atol=1e-12)
+    dv = oracle.dual_value(x, mu, y, nu, 1.0 / lam, eta1, eta2, beta, gamma, r=1)
+    pv = oracle.primal_value(x, mu, y, nu, 1.0 / lam, eta1, eta2, beta, gamma, r=1)
+    assert abs(dv - val) <= 1e-12 * abs(val) and abs(pv - val) <= 1e-12 * abs(val)
+    pi = oracle.plan(x, mu, y, nu, 1.0 / lam, beta, gamma, r=1)
+    assert np.allclose(pi, c * np.outer(mu, nu), rtol=1e-11, atol=0)
+
+
+def test_strong_duality_r1(oracle_lib):
+    g = np.random.default_rng(12)
+    x, y = g.uniform(0, 1, (30, 2)), g.uniform(0, 1, (25, 2))
+    mu, nu = g.uniform(0.2, 1.0, 30), g.uniform(0.2, 1.0, 25)
+    beta, gamma = oracle.uot_sinkhorn(x, mu, y, nu, 0.1, 0.7, 1.3, sweeps=2000, r=1)
+    dv = oracle.dual_value(x, mu, y, nu, 0.1, 0.7, 1.3, beta, gamma, r=1)
+    pv = oracle.primal_value(x, mu, y, nu, 0.1, 0.7, 1.3, beta, gamma, r=1)
+    assert abs(pv - dv) <= 1e-10 * abs(dv)
+    # and the r = 1 solve differs from the r = 2 one (the cost is used)
+    b2, _ = oracle.uot_sinkhorn(x, mu, y, nu, 0.1, 0.7, 1.3, sweeps=2000)
+    assert np.max(np.abs(b2 - beta)) > 1e-3
+
+
+@pytest.mark.parametrize("lam", [1e-2, 1e-3])
+def test_cor477_divergence_tends_to_the_energy_distance(oracle_lib, lam):
+    """Cor. cor:477 (with Lemma lem:inter_ot_mmd): for probability measures the
+    debiased UOT with cost |x - y| tends, as eta -> infinity and then lambda -> 0,
+    to the energy distance; in the squared-RKHS convention of Eq. (1205) the
+    limit is MMD^2_{k_e} / 2 = E|X-Y| - E|X-X'|/2 - E|Y-Y'|/2 (the paper's setting:
+    uniform samples on [0, 1]).  The gap shrinks like lambda."""
+    g = np.random.default_rng(3)
+    x, y = g.uniform(0, 1, (120, 1)), g.uniform(0, 1, (100, 1))
+    P, Q = np.full(120, 1 / 120), np.full(100, 1 / 100)
+    half_e = 0.5 * oracle.mmd2_kernel("energy", 1.0, x, P, y, Q)
+    eta = 1e5
+    sweeps = int(min(20000, 40 * (1 + eta * lam)))
+    sd = oracle.sinkhorn_divergence(x, P, y, Q, 1.0 / lam, eta, sweeps=sweeps, r=1)
+    assert abs(sd - half_e) <= 0.5 * lam * half_e, (sd, half_e)
