@@ -223,7 +223,13 @@ uotk_status uotk_kernel_sum_noalloc(void* stream, int d, const float* src, int64
 /* flags & UOTK_CSTAR_INIT: gamma^0 = c* 1 with c* of Eq. (561) as computed by
  * uotk_cstar (the Remark on the initialisation of Sinkhorn's algorithm read
  * literally: the potential set to the number c*).  ref = PRODUCT only; not
- * together with UOTK_WARM_START (INVALID). */
+ * together with UOTK_WARM_START (INVALID).
+ * The cost: opts->kernel = GAUSS (default) solves Eq. (W4) with d^2 (r = 2, the
+ * Gibbs kernel exp(-||x - y||^2/eps)); opts->kernel = LAPLACE solves it with the
+ * cost ||x - y|| (r = 1, Gibbs kernel exp(-||x - y||/eps), the Laplace kernel of
+ * Table tab:0 with p = eps), in the direct FP32 form or the regularised NFFT
+ * (d <= 3; its accuracy needs eps above a few h/N, h the torus period).  Not
+ * with UOTK_LOG_DOMAIN (UNSUPPORTED); the same for uotk_sinkhorn_divergence. */
 #define UOTK_CSTAR_INIT 4u
 uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d,
                               const float* x, int64_t n, const float* a,
@@ -238,26 +244,31 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d,
  *   r = 2: from the first and second moments of both clouds about x_0 in FP64,
  *          O((n + m) d), no kernel summation;
  *   r = 1: d = -k_e, the energy kernel of Table tab:0 (Sec. 4.4, complexity of
- *          the upper bounds): one direct FP32 kernel summation with k_e, then
- *          an FP64 dot product with a.
+ *          the upper bounds): one kernel summation with k_e in the form
+ *          opts->method (DIRECT, or NFFT for d <= 3: the regularised fast
+ *          summation, O(n log n) plus its near field), then an FP64 dot
+ *          product with a.
  *   x, a, y, b: as uotk_uot_sinkhorn (n, m >= 1, weights >= 0, d <= 128).
- *   out (host double [3]): {<mu (x) nu|d^r>, mu(X), nu(X)}.
- * uotk_cstar: c*_{2;eta;lambda} of Eq. (561), lambda = 1/eps, eta_i = rho_i:
- *   log c* = -(<mu (x) nu|d^2> / (mu(X) nu(X)) + rho1 log nu(X) + rho2 log mu(X))
+ *   out (host double [3]): {<mu (x) nu|d^r>, mu(X), nu(X)}.  opts may be NULL.
+ * uotk_cstar: c*_{r;eta;lambda} of Eq. (561), lambda = 1/eps, eta_i = rho_i:
+ *   log c* = -(<mu (x) nu|d^r> / (mu(X) nu(X)) + rho1 log nu(X) + rho2 log mu(X))
  *            / (rho1 + rho2 + eps),
  *   the constant c for which c mu (x) nu minimises Eq. (W4) among such plans.
  *   out (host double [3]): {c*, the Eq. (W4) objective at c* mu (x) nu (an
  *   upper bound of the regularised UOT value, Remark on upper bounds),
- *   <mu (x) nu|d^2>}.
+ *   <mu (x) nu|d^r>}.
  * Both synchronise `stream`; NONFINITE / INVALID for non-finite inputs or
- * negative weights, INVALID if a measure has zero mass (uotk_cstar). */
+ * negative weights, INVALID if a measure has zero mass (uotk_cstar) or r is
+ * not 1 or 2. */
 uotk_status uotk_mean_cost(uotk_ctx* ctx, void* stream, int d,
                            const float* x, int64_t n, const float* a,
-                           const float* y, int64_t m, const float* b, int r, double* out);
+                           const float* y, int64_t m, const float* b, int r, double* out,
+                           const uotk_sum_opts* opts);
 uotk_status uotk_cstar(uotk_ctx* ctx, void* stream, int d,
                        const float* x, int64_t n, const float* a,
                        const float* y, int64_t m, const float* b,
-                       double eps, double rho1, double rho2, double* out);
+                       double eps, double rho1, double rho2, int r, double* out,
+                       const uotk_sum_opts* opts);
 
 /* ---- lambda-scaling (Sec. 5.1.2, "deformed iteration") --------------------------------
  * Alg. 1/2 solved for eps_schedule[0], eps_schedule[1], ... (lambda = 1/eps

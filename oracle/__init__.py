@@ -290,14 +290,14 @@ def independent_objective(c, cost, m1, m2, eps, eta1, eta2):
             + eta2 * m2 * (c * m1 * np.log(c * m1) - c * m1 + 1.0))
 
 
-def cstar(x, mu, y, nu, eps, eta1, eta2):
-    """c*_{2;eta;lambda} of Eq. (561) (Prop. prop:536), lambda = 1/eps:
-        c* = exp(-<mu (x) nu|d^2> / (m1 m2 (eta1 + eta2 + 1/lambda)))
+def cstar(x, mu, y, nu, eps, eta1, eta2, r=2):
+    """c*_{r;eta;lambda} of Eq. (561) (Prop. prop:536), lambda = 1/eps:
+        c* = exp(-<mu (x) nu|d^r> / (m1 m2 (eta1 + eta2 + 1/lambda)))
              m1^{-eta2/(eta1+eta2+1/lambda)} m2^{-eta1/(eta1+eta2+1/lambda)}.
-    Returns (c*, objective of Eq. (W4) at c* mu (x) nu, <mu (x) nu|d^2>)."""
+    Returns (c*, objective of Eq. (W4) at c* mu (x) nu, <mu (x) nu|d^r>)."""
     mu, nu = _vec(mu), _vec(nu)
     m1, m2 = float(np.sum(mu)), float(np.sum(nu))
-    cost = mean_cost(x, mu, y, nu, 2)
+    cost = mean_cost(x, mu, y, nu, r)
     den = eta1 + eta2 + eps
     c = np.exp(-cost / (m1 * m2 * den)) * m1 ** (-eta2 / den) * m2 ** (-eta1 / den)
     return c, independent_objective(c, cost, m1, m2, eps, eta1, eta2), cost

@@ -131,16 +131,21 @@ uotk_status check_cloud(uotk_ctx* ctx, const char* what, const float* p, int64_t
   return UOTK_OK;
 }
 
-// Kernels other than the Gaussian: only in kernel_sum and mmd2, direct FP32 form.
-uotk_status check_kernel(uotk_ctx* ctx, const uotk_sum_opts* opts, bool allowed) {
+// Kernels other than the Gaussian: in kernel_sum and mmd2 (allowed), and the
+// Laplace kernel as the Gibbs kernel of the cost |x - y| in the Sinkhorn solves
+// (cost_r1); direct FP32 or NFFT form only.
+uotk_status check_kernel(uotk_ctx* ctx, const uotk_sum_opts* opts, bool allowed,
+                         bool cost_r1 = false) {
   const int kernel = opts ? opts->kernel : UOTK_KERNEL_GAUSS;
   if (kernel < UOTK_KERNEL_GAUSS || kernel > UOTK_KERNEL_ENERGY)
     return set_error(ctx, UOTK_ERR_INVALID, "unknown kernel %d", kernel);
   if (kernel == UOTK_KERNEL_GAUSS) return UOTK_OK;
   const int method = opts->method;
-  if (!allowed || (method != UOTK_DIRECT && method != UOTK_NFFT))
+  const bool ok = allowed || (cost_r1 && kernel == UOTK_KERNEL_LAPLACE);
+  if (!ok || (method != UOTK_DIRECT && method != UOTK_NFFT))
     return set_error(ctx, UOTK_ERR_UNSUPPORTED,
-                     "kernel %d: only kernel_sum and mmd2, in the direct FP32 or the NFFT form",
+                     "kernel %d: only kernel_sum and mmd2 (and the Laplace kernel, cost |x - y|, "
+                     "in the Sinkhorn solves), in the direct FP32 or the NFFT form",
                      kernel);
   return UOTK_OK;
 }
@@ -320,7 +325,7 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x
                               int* sweeps_done, double* value, const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
-  UOTK_TRY(check_kernel(ctx, opts, false));
+  UOTK_TRY(check_kernel(ctx, opts, false, true));
   UOTK_TRY(check_cloud(ctx, "x", x, n, d));
   UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
   UOTK_TRY(check_cloud(ctx, "y", y, m, d));
@@ -356,26 +361,43 @@ static uotk_status check_pair(uotk_ctx* ctx, int d, const float* x, int64_t n, c
   return UOTK_OK;
 }
 
+static uotk_status check_cost(uotk_ctx* ctx, int d, int r, const uotk_sum_opts* opts) {
+  if (r != 1 && r != 2) return set_error(ctx, UOTK_ERR_INVALID, "cost exponent r = %d not 1 or 2", r);
+  const int method = opts ? opts->method : UOTK_DIRECT;
+  if (method != UOTK_DIRECT && method != UOTK_NFFT)
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED, "mean cost: direct or NFFT form only");
+  if (r == 1) {
+    uotk_sum_opts o = opts ? *opts : uotk_sum_opts{};
+    o.kernel = UOTK_KERNEL_ENERGY;
+    UOTK_TRY(check_common(ctx, d, &o));
+  }
+  return UOTK_OK;
+}
+
 uotk_status uotk_mean_cost(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
                            const float* a, const float* y, int64_t m, const float* b, int r,
-                           double* out) {
+                           double* out, const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_pair(ctx, d, x, n, a, y, m, b));
-  if (r != 1 && r != 2) return set_error(ctx, UOTK_ERR_INVALID, "mean_cost: r = %d not 1 or 2", r);
+  UOTK_TRY(check_cost(ctx, d, r, opts));
   if (!out) return set_error(ctx, UOTK_ERR_INVALID, "mean_cost: null output");
-  return op_mean_cost(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, r, out);
+  return op_mean_cost(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, r,
+                      opts ? opts->method : UOTK_DIRECT, out);
 }
 
 uotk_status uotk_cstar(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
                        const float* a, const float* y, int64_t m, const float* b, double eps,
-                       double rho1, double rho2, double* out) {
+                       double rho1, double rho2, int r, double* out,
+                       const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_pair(ctx, d, x, n, a, y, m, b));
+  UOTK_TRY(check_cost(ctx, d, r, opts));
   if (!(eps > 0.0) || !isfinite(eps) || !(rho1 > 0.0) || !(rho2 > 0.0) || !isfinite(rho1) ||
       !isfinite(rho2))
     return set_error(ctx, UOTK_ERR_INVALID, "eps, rho1, rho2 must be finite and > 0");
   if (!out) return set_error(ctx, UOTK_ERR_INVALID, "cstar: null output");
-  return op_cstar(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2, out);
+  return op_cstar(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2, r,
+                  opts ? opts->method : UOTK_DIRECT, out);
 }
 
 uotk_status uotk_uot_sinkhorn_scaled(uotk_ctx* ctx, void* stream, int d, const float* x,
@@ -458,7 +480,7 @@ uotk_status uotk_sinkhorn_divergence(uotk_ctx* ctx, void* stream, int d, const f
                                      const uotk_sum_opts* opts) {
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
-  UOTK_TRY(check_kernel(ctx, opts, false));
+  UOTK_TRY(check_kernel(ctx, opts, false, true));
   UOTK_TRY(check_cloud(ctx, "x", x, n, d));
   UOTK_TRY(check_cloud(ctx, "a", a, n, 1));
   UOTK_TRY(check_cloud(ctx, "y", y, m, d));

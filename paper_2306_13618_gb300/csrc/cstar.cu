@@ -154,11 +154,12 @@ uotk_status cost2(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t 
 
 // -<mu (x) nu|d>, mu(X), nu(X) into host[0..3) (r = 1, energy kernel).
 uotk_status cost1(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
-                  const float* a, const float* y, int64_t m, const float* b, double* host) {
+                  const float* a, const float* y, int64_t m, const float* b, int method,
+                  double* host) {
   uotk_sum_opts o{};
-  o.method = UOTK_DIRECT;
+  o.method = method;
   o.kernel = UOTK_KERNEL_ENERGY;
-  EngineSpec sp{UOTK_DIRECT, d, x, n, a, y, m, b, 1.0, &o};
+  EngineSpec sp{method, d, x, n, a, y, m, b, 1.0, &o};
   Carver size(nullptr);
   size.off = engine_bytes(ctx, sp);
   size.take<float>(n + 4);
@@ -187,12 +188,12 @@ uotk_status cost1(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t 
 
 uotk_status op_mean_cost(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
                          const float* a, const float* y, int64_t m, const float* b, int r,
-                         double* out) {
+                         int method, double* out) {
   double* h = ctx->host + 72;
   if (r == 2) {
     UOTK_TRY(cost2(ctx, s, d, x, n, a, y, m, b, h));
   } else {
-    UOTK_TRY(cost1(ctx, s, d, x, n, a, y, m, b, h));
+    UOTK_TRY(cost1(ctx, s, d, x, n, a, y, m, b, method, h));
     h[0] = -h[0];
   }
   out[0] = h[0];
@@ -201,14 +202,14 @@ uotk_status op_mean_cost(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, i
   return UOTK_OK;
 }
 
-// c* of Eq. (561) with r = 2, lambda = 1/eps, and the Eq. (W4) objective at
-// c* mu (x) nu: cost c* C + eps m1 m2 (c* log c* - c* + 1) plus the two KL
-// terms of the marginals c* m2 mu and c* m1 nu.
+// c* of Eq. (561) for the cost |x - y|^r (r = 1, 2), lambda = 1/eps, and the
+// Eq. (W4) objective at c* mu (x) nu: cost c* C + eps m1 m2 (c* log c* - c* + 1)
+// plus the two KL terms of the marginals c* m2 mu and c* m1 nu.
 uotk_status op_cstar(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
                      const float* a, const float* y, int64_t m, const float* b, double eps,
-                     double rho1, double rho2, double* out) {
+                     double rho1, double rho2, int r, int method, double* out) {
   double mc[3];
-  UOTK_TRY(op_mean_cost(ctx, s, d, x, n, a, y, m, b, 2, mc));
+  UOTK_TRY(op_mean_cost(ctx, s, d, x, n, a, y, m, b, r, method, mc));
   const double C = mc[0], m1 = mc[1], m2 = mc[2];
   if (!(m1 > 0.0) || !(m2 > 0.0))
     return set_error(ctx, UOTK_ERR_INVALID, "cstar: a measure has zero mass");

@@ -133,7 +133,11 @@ struct NfftEngine : Engine {
     SpreadWeights w{base, pot, lam, shift_slot};
     UOTK_TRY(nfft_spread(ctx, s, P, src, w, W, W.grid));
     UOTK_TRY(nfft_convolve(ctx, s, P, W, W.grid, W.grid));
-    return nfft_gather(ctx, s, P, tgt, W.grid, out);
+    UOTK_TRY(nfft_gather(ctx, s, P, tgt, W.grid, out));
+    // cost |x - y| (Laplace kernel): the near field with the spread's weights
+    if (P.kernel != UOTK_KERNEL_GAUSS)
+      UOTK_TRY(nfft_near(ctx, s, P, src, pot ? W.wts : base, tgt, out));
+    return UOTK_OK;
   }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
     SpreadWeights sw{w, nullptr, 0.0, nullptr};

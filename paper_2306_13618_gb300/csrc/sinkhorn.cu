@@ -73,7 +73,8 @@ struct DirectEngine : Engine {
     void* tgt = side == 0 ? Px : Py;
     UOTK_TRY(direct_set_weights(ctx, s, L, src, base, pot, lam, shift_slot));
     DirectBufs bufs{src, tgt, part};
-    return direct_run(ctx, s, L, bufs, eps, out);
+    // kernel LAPLACE: the Gibbs kernel of the cost |x - y| (r = 1), e^{-|x-y|/eps}
+    return direct_run(ctx, s, L, bufs, eps, out, kernel);
   }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
     const DirectLayout& L = src == 0 ? (tgt == 0 ? Lxx : Lxy) : (tgt == 0 ? Lyx : Lyy);
@@ -503,14 +504,18 @@ uotk_status op_uot_sinkhorn(uotk_ctx* ctx, cudaStream_t s, int d, const float* x
   EngineSpec sp{opts ? opts->method : UOTK_DIRECT, d, x, n, a, y, m, b, eps, opts};
   const bool copies = sp.method == UOTK_NFFT;
   const bool logd = (flags & UOTK_LOG_DOMAIN) != 0;
-  if (logd && sp.method != UOTK_DIRECT)
+  const int kernel = opts ? opts->kernel : UOTK_KERNEL_GAUSS;
+  if (logd && (sp.method != UOTK_DIRECT || kernel != UOTK_KERNEL_GAUSS))
     return set_error(ctx, UOTK_ERR_UNSUPPORTED,
-                     "uot_sinkhorn: the log domain is implemented for the direct FP32 form only");
+                     "uot_sinkhorn: the log domain is implemented for the direct FP32 form of "
+                     "the squared-distance cost only");
   // gamma^0 = c* 1 (Remark on the initialisation; c* of Eq. 561), computed
   // before the solve's workspace is carved.
   const bool cstar_init = (flags & UOTK_CSTAR_INIT) != 0;
   double cst[3] = {0.0, 0.0, 0.0};
-  if (cstar_init) UOTK_TRY(op_cstar(ctx, s, d, x, n, a, y, m, b, eps, rho1, rho2, cst));
+  if (cstar_init)
+    UOTK_TRY(op_cstar(ctx, s, d, x, n, a, y, m, b, eps, rho1, rho2,
+                      kernel == UOTK_KERNEL_LAPLACE ? 1 : 2, sp.method, cst));
   Carver size(nullptr);
   size.off = engine_bytes(ctx, sp);
   SolveBufs B;

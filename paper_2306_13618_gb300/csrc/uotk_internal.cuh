@@ -306,15 +306,16 @@ uotk_status direct_run_lse(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
 
 int grid_for(const uotk_ctx* ctx, int64_t work, int threads, int per_sm = 8);
 
-// cstar.cu: <mu (x) nu|d^r> (r = 1, 2) with mu(X), nu(X) into out[0..3); c* of
-// Eq. (561) (r = 2), the Eq. (W4) objective at c* mu (x) nu and the mean-cost
-// numerator into out[0..3); v[0..count) = value.
+// cstar.cu: <mu (x) nu|d^r> (r = 1, 2; r = 1 through the energy kernel in the
+// form `method`) with mu(X), nu(X) into out[0..3); c* of Eq. (561), the
+// Eq. (W4) objective at c* mu (x) nu and the mean-cost numerator into
+// out[0..3); v[0..count) = value.
 uotk_status op_mean_cost(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
                          const float* a, const float* y, int64_t m, const float* b, int r,
-                         double* out);
+                         int method, double* out);
 uotk_status op_cstar(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, int64_t n,
                      const float* a, const float* y, int64_t m, const float* b, double eps,
-                     double rho1, double rho2, double* out);
+                     double rho1, double rho2, int r, int method, double* out);
 uotk_status fill_f64(uotk_ctx* ctx, cudaStream_t s, double* v, int64_t count, double value);
 
 }  // namespace uotk

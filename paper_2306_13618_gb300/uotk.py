@@ -105,9 +105,9 @@ def lib():
                                               _P, _P, _P, _P, _P, _P, ctypes.c_int, _D,
                                               ctypes.c_int, _P, _P, _P, _P, opts]
         L.uotk_mean_cost.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
-                                     ctypes.c_int, ctypes.POINTER(_D)]
+                                     ctypes.c_int, ctypes.POINTER(_D), opts]
         L.uotk_cstar.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, _D, _D,
-                                 ctypes.POINTER(_D)]
+                                 ctypes.c_int, ctypes.POINTER(_D), opts]
         L.uotk_measure_unit_rates.argtypes = [_P, _P, ctypes.POINTER(_D), ctypes.POINTER(_D)]
         L.uotk_mmd2_grad.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D,
                                      ctypes.POINTER(_D), _P, _P, _P, _P, opts]
@@ -285,29 +285,32 @@ def uot_sinkhorn(x, a, y, b, eps, rho1, rho2=None, max_sweeps=100, tol=0.0, ref=
     return beta, gamma, sweeps.value, value.value, st == UOTK_OK
 
 
-def mean_cost(x, a, y, b, r=2, ctx=None):
-    """<mu (x) nu|d^r> for r = 2 (moments) or r = 1 (energy kernel) with the
-    masses (uotk_mean_cost): returns (cost, mu(X), nu(X))."""
+def mean_cost(x, a, y, b, r=2, method="direct", ctx=None, **nfft):
+    """<mu (x) nu|d^r> for r = 2 (moments) or r = 1 (energy kernel, direct or
+    NFFT) with the masses (uotk_mean_cost): returns (cost, mu(X), nu(X))."""
     x, y = _pts(x, "x"), _pts(y, "y")
     a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
     ctx = ctx or default_context()
     out = (_D * 3)()
+    o = _opts(method, **nfft)
     ctx.check(lib().uotk_mean_cost(ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0],
-                                   _ptr(a), _ptr(y), y.shape[0], _ptr(b), int(r), out))
+                                   _ptr(a), _ptr(y), y.shape[0], _ptr(b), int(r), out,
+                                   ctypes.byref(o)))
     return tuple(out)
 
 
-def cstar(x, a, y, b, eps, rho1, rho2=None, ctx=None):
-    """c* of Eq. (561) (uotk_cstar): returns (c*, Eq. (W4) objective at
-    c* mu (x) nu, <mu (x) nu|d^2>)."""
+def cstar(x, a, y, b, eps, rho1, rho2=None, r=2, method="direct", ctx=None, **nfft):
+    """c* of Eq. (561) for the cost |x - y|^r (uotk_cstar): returns (c*, Eq. (W4)
+    objective at c* mu (x) nu, <mu (x) nu|d^r>)."""
     x, y = _pts(x, "x"), _pts(y, "y")
     a, b = _f32(a, "a").reshape(-1), _f32(b, "b").reshape(-1)
     rho2 = rho1 if rho2 is None else rho2
     ctx = ctx or default_context()
     out = (_D * 3)()
+    o = _opts(method, **nfft)
     ctx.check(lib().uotk_cstar(ctx.handle, _stream(), x.shape[1], _ptr(x), x.shape[0], _ptr(a),
                                _ptr(y), y.shape[0], _ptr(b), float(eps), float(rho1),
-                               float(rho2), out))
+                               float(rho2), int(r), out, ctypes.byref(o)))
     return tuple(out)
 
 
