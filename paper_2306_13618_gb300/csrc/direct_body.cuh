@@ -91,18 +91,56 @@ __device__ __forceinline__ void direct_body(const float4* __restrict__ src, long
 #pragma unroll 1
     for (int j0 = 0; j0 < DIRECT_TILE; j0 += 32) {
       float acc[R];
+      if constexpr (KIND == 0 && R % 2 == 0) {
+        // Gaussian with an even number of targets per thread: the same IEEE
+        // operations on target pairs in packed FP32x2 (half the issue slots)
+        constexpr int R2 = R / 2;
+        unsigned long long px[R2], py[R2], pz[R2], a2[R2];
+        const unsigned long long c2 = f2_pack(neg_c, neg_c);
 #pragma unroll
-      for (int r = 0; r < R; ++r) acc[r] = 0.f;
+        for (int h = 0; h < R2; ++h) {
+          px[h] = f2_pack(tx[2 * h], tx[2 * h + 1]);
+          py[h] = f2_pack(ty[2 * h], ty[2 * h + 1]);
+          pz[h] = f2_pack(tz[2 * h], tz[2 * h + 1]);
+          a2[h] = 0ull;
+        }
 #pragma unroll 8
-      for (int j = j0; j < j0 + 32; ++j) {
-        const float4 q = T[j];
+        for (int j = j0; j < j0 + 32; ++j) {
+          const float4 q = T[j];
+          const unsigned long long qx = f2_pack(q.x, q.x), qw = f2_pack(q.w, q.w);
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-          const float dx = tx[r] - q.x;
-          float r2 = dx * dx;
-          if (D > 1) { const float dy = ty[r] - q.y; r2 = fmaf(dy, dy, r2); }
-          if (D > 2) { const float dz = tz[r] - q.z; r2 = fmaf(dz, dz, r2); }
-          acc[r] = fmaf(q.w, kpair<KIND>(r2, neg_c, c1), acc[r]);
+          for (int h = 0; h < R2; ++h) {
+            const unsigned long long dx = f2_sub(px[h], qx);
+            unsigned long long r2 = f2_mul(dx, dx);
+            if (D > 1) {
+              const unsigned long long dy = f2_sub(py[h], f2_pack(q.y, q.y));
+              r2 = f2_fma(dy, dy, r2);
+            }
+            if (D > 2) {
+              const unsigned long long dz = f2_sub(pz[h], f2_pack(q.z, q.z));
+              r2 = f2_fma(dz, dz, r2);
+            }
+            float e0, e1;
+            f2_unpack(f2_mul(r2, c2), e0, e1);
+            a2[h] = f2_fma(qw, f2_pack(ex2_approx(e0), ex2_approx(e1)), a2[h]);
+          }
+        }
+#pragma unroll
+        for (int h = 0; h < R2; ++h) f2_unpack(a2[h], acc[2 * h], acc[2 * h + 1]);
+      } else {
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] = 0.f;
+#pragma unroll 8
+        for (int j = j0; j < j0 + 32; ++j) {
+          const float4 q = T[j];
+#pragma unroll
+          for (int r = 0; r < R; ++r) {
+            const float dx = tx[r] - q.x;
+            float r2 = dx * dx;
+            if (D > 1) { const float dy = ty[r] - q.y; r2 = fmaf(dy, dy, r2); }
+            if (D > 2) { const float dz = tz[r] - q.z; r2 = fmaf(dz, dz, r2); }
+            acc[r] = fmaf(q.w, kpair<KIND>(r2, neg_c, c1), acc[r]);
+          }
         }
       }
 #pragma unroll
