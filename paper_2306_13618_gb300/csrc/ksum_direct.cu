@@ -337,7 +337,10 @@ DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m) {
   L.m = m;
   const bool small = d <= 3;
   const int tile = small ? DIRECT_TILE : GEN_TILE;
-  L.reg_targets = (small && m >= 4 * DIRECT_THREADS * (int64_t)ctx->num_sms) ? 4 : 1;
+  // targets per thread: enough CTAs to fill the GPU with the most reuse of each
+  // staged source (2 and 4 take the packed FP32x2 path of the Gaussian)
+  const int64_t per_wave = (int64_t)DIRECT_THREADS * ctx->num_sms;
+  L.reg_targets = !small ? 1 : (m >= 4 * per_wave ? 4 : (m >= 2 * per_wave ? 2 : 1));
   L.blocks_x = (int)((m + (int64_t)DIRECT_THREADS * L.reg_targets - 1) /
                      ((int64_t)DIRECT_THREADS * L.reg_targets));
   if (L.blocks_x < 1) L.blocks_x = 1;
@@ -415,8 +418,9 @@ void direct_launch(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L, const D
   if (L.d == DD && L.reg_targets == RR)                                                   \
     k_direct_small<DD, RR, KIND><<<grid, DIRECT_THREADS, 0, s>>>(                         \
         src, L.tiles, L.tiles_per_split, tgt, L.m, c0, dst, ctx->dflags, c1);
-    UOTK_DIRECT_CASE(1, 1) UOTK_DIRECT_CASE(1, 4) UOTK_DIRECT_CASE(2, 1)
-    UOTK_DIRECT_CASE(2, 4) UOTK_DIRECT_CASE(3, 1) UOTK_DIRECT_CASE(3, 4)
+    UOTK_DIRECT_CASE(1, 1) UOTK_DIRECT_CASE(1, 2) UOTK_DIRECT_CASE(1, 4)
+    UOTK_DIRECT_CASE(2, 1) UOTK_DIRECT_CASE(2, 2) UOTK_DIRECT_CASE(2, 4)
+    UOTK_DIRECT_CASE(3, 1) UOTK_DIRECT_CASE(3, 2) UOTK_DIRECT_CASE(3, 4)
 #undef UOTK_DIRECT_CASE
   } else {
     const float* src = reinterpret_cast<const float*>(b.src);
@@ -480,8 +484,9 @@ uotk_status direct_run_lse(uotk_ctx* ctx, cudaStream_t s, const DirectLayout& L,
   if (L.d == DD && L.reg_targets == RR)                                                   \
     k_direct_lse<DD, RR><<<grid, DIRECT_THREADS, 0, s>>>(src, L.tiles, L.tiles_per_split,  \
                                                          tgt, L.m, neg_c, dst, ctx->dflags);
-      UOTK_LSE_CASE(1, 1) UOTK_LSE_CASE(1, 4) UOTK_LSE_CASE(2, 1)
-      UOTK_LSE_CASE(2, 4) UOTK_LSE_CASE(3, 1) UOTK_LSE_CASE(3, 4)
+      UOTK_LSE_CASE(1, 1) UOTK_LSE_CASE(1, 2) UOTK_LSE_CASE(1, 4)
+      UOTK_LSE_CASE(2, 1) UOTK_LSE_CASE(2, 2) UOTK_LSE_CASE(2, 4)
+      UOTK_LSE_CASE(3, 1) UOTK_LSE_CASE(3, 2) UOTK_LSE_CASE(3, 4)
 #undef UOTK_LSE_CASE
     } else {
       const float* src = reinterpret_cast<const float*>(b.src);

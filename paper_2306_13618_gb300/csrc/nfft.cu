@@ -136,7 +136,7 @@ struct NfftEngine : Engine {
     UOTK_TRY(nfft_gather(ctx, s, P, tgt, W.grid, out));
     // cost |x - y| (Laplace kernel): the near field with the spread's weights
     if (P.kernel != UOTK_KERNEL_GAUSS)
-      UOTK_TRY(nfft_near(ctx, s, P, src, pot ? W.wts : base, tgt, out));
+      UOTK_TRY(nfft_near(ctx, s, P, src, pot ? W.wts : base, tgt, W, out));
     return UOTK_OK;
   }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
@@ -147,7 +147,7 @@ struct NfftEngine : Engine {
     UOTK_TRY(nfft_convolve(ctx, s, P, W, W.grid, W.grid));
     UOTK_TRY(nfft_gather(ctx, s, P, T, W.grid, out));
     // non-smooth kernels: the Fourier part sums K_R; add w (K - K_R) of the near field
-    if (P.kernel != UOTK_KERNEL_GAUSS) UOTK_TRY(nfft_near(ctx, s, P, S, w, T, out));
+    if (P.kernel != UOTK_KERNEL_GAUSS) UOTK_TRY(nfft_near(ctx, s, P, S, w, T, W, out));
     return UOTK_OK;
   }
   const float* weights(int side) const override { return side == 0 ? as : bs; }

@@ -17,6 +17,7 @@ constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit gr
 constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
 constexpr int NFFT_MAX_M = 8;
 constexpr int NFFT_CHUNK = 64;          // points per bulk-copied staging chunk
+constexpr int NFFT_NEAR_CHUNK = 1024;   // targets per near-field work item
 // Window table row of one point (floats): phi_x split in two halves of m
 // values, then phi_y (2m), then phi_z (2m); every block padded to a 16-byte
 // multiple, so that every chunk of the table is a legal bulk-copy source and
@@ -97,6 +98,8 @@ struct NfftWork {
   float2* cgrid = nullptr; // [n^3] complex work grid
   float* scale = nullptr;  // [3*N] device table
   float* full = nullptr;   // [N^3] non-separable table [kz'][ky'][kx'] (non-smooth kernels)
+  int2* near_items = nullptr;  // near-field work items (target tile, first target)
+  int* near_ctr = nullptr;     // [2] item count, next item to take
 };
 size_t nfft_work_bytes(const NfftParams& P, int64_t max_points);
 void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWork& W);
@@ -123,7 +126,7 @@ uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
 // sum_{|x_i - y_j| < eps_I h} w_j (K - K_R) to out (target order).
 uotk_status nfft_reg_table(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W);
 uotk_status nfft_near(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& src,
-                      const float* w, const NfftPoints& tgt, float* out);
+                      const float* w, const NfftPoints& tgt, NfftWork& W, float* out);
 
 // Bounding box of point clouds on the device -> host (synchronises).
 uotk_status nfft_bbox(uotk_ctx* ctx, cudaStream_t s, int d, const float* a, int64_t na,

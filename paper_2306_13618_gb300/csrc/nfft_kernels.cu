@@ -811,6 +811,16 @@ void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWo
   W.cgrid = cv.take<float2>(pr > n3 ? pr : n3);
   W.scale = cv.take<float>(3 * P.N);
   W.full = P.kernel != UOTK_KERNEL_GAUSS ? cv.take<float>((size_t)P.N * P.N * P.N) : nullptr;
+  if (P.kernel != UOTK_KERNEL_GAUSS) {
+    // one item per (tile, chunk of NFFT_NEAR_CHUNK targets)
+    const size_t tiles = (size_t)P.tiles1 * P.tiles1 * P.tiles1;
+    W.near_items = cv.take<int2>(tiles + (size_t)(max_points > 0 ? max_points : 0) /
+                                              NFFT_NEAR_CHUNK + 1);
+    W.near_ctr = cv.take<int>(2);
+  } else {
+    W.near_items = nullptr;
+    W.near_ctr = nullptr;
+  }
 }
 
 }  // namespace uotk

@@ -247,29 +247,52 @@ __device__ __forceinline__ float near_kernel(float r2, float c1, float c2) {
   return -c1 * sqrtf(r2);
 }
 
-// One CTA per target tile (persistent over tiles): each thread holds NEAR_TPT
-// targets; the sources of the (2R+1)^3 neighbouring tiles, contiguous per
-// (z, y) row of tiles in sorted order, are staged through shared memory.  T_I
-// has P coefficients held in registers (P = 12 serves any p <= 12, the unused
-// coefficients being zero).
+// Work items of the near field: (target tile, first target) for every chunk of
+// NFFT_NEAR_CHUNK targets of a non-empty tile, in any order.
+__global__ void k_near_items(const int* __restrict__ ttile, int tiles, int2* __restrict__ items,
+                             int* __restrict__ ctr) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
+    const int b = ttile[t], e = ttile[t + 1];
+    if (b == e) continue;
+    const int k = (e - b + NFFT_NEAR_CHUNK - 1) / NFFT_NEAR_CHUNK;
+    const int base = atomicAdd(&ctr[0], k);
+    for (int i = 0; i < k; ++i) items[base + i] = make_int2(t, b + i * NFFT_NEAR_CHUNK);
+  }
+}
+
+// Persistent CTAs take work items from a counter: each item is up to
+// NFFT_NEAR_CHUNK targets of one tile, NEAR_TPT per thread; the sources of the
+// (2R+1)^3 neighbouring tiles, contiguous per (z, y) row of tiles in sorted
+// order, are staged through shared memory.  T_I has P coefficients held in
+// registers (P = 12 serves any p <= 12, the unused coefficients being zero).
 constexpr int NEAR_TPT = 4;
+static_assert(NEAR_TPT * NEAR_THREADS == NFFT_NEAR_CHUNK, "one pass per work item");
 template <int KIND, int P>
 __global__ void __launch_bounds__(NEAR_THREADS)
     k_near(const int4* __restrict__ tcell, const int* __restrict__ ttile,
            const int4* __restrict__ scell, const int* __restrict__ stile,
-           const float* __restrict__ w, NearArgs a, float* __restrict__ out) {
+           const float* __restrict__ w, const int2* __restrict__ items,
+           int* __restrict__ ctr, NearArgs a, float* __restrict__ out) {
   __shared__ float4 sh[NEAR_THREADS];
+  __shared__ int item;
   float e[P];
 #pragma unroll
   for (int q = 0; q < P; ++q) e[q] = a.e[q];
   const float r2i = a.r2i, inv_r2i = a.inv_r2i, c1 = a.c1, c2 = a.c2;
   const int T = a.tiles1, R = a.R;
-  const int tiles = T * T * T;
-  for (int tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-    const int tb = ttile[tile], te = ttile[tile + 1];
-    if (tb == te) continue;
+  const int nitems = ctr[0];
+  for (;;) {
+    if (threadIdx.x == 0) item = atomicAdd(&ctr[1], 1);
+    __syncthreads();
+    const int li = item;
+    __syncthreads();
+    if (li >= nitems) break;
+    const int2 it = items[li];
+    const int tile = it.x;
+    const int te = min(it.y + NFFT_NEAR_CHUNK, ttile[tile + 1]);
     const int tx = tile % T, ty = (tile / T) % T, tz = tile / (T * T);
-    for (int t0 = tb; t0 < te; t0 += NEAR_TPT * NEAR_THREADS) {
+    {
+      const int t0 = it.y;
       float px[NEAR_TPT], py[NEAR_TPT], pz[NEAR_TPT], acc[NEAR_TPT];
 #pragma unroll
       for (int q = 0; q < NEAR_TPT; ++q) {
@@ -326,25 +349,16 @@ __global__ void __launch_bounds__(NEAR_THREADS)
 
 template <int KIND>
 void launch_near(int P, int blocks, cudaStream_t s, const NfftPoints& src, const float* w,
-                 const NfftPoints& tgt, const NearArgs& a, float* out) {
+                 const NfftPoints& tgt, const NfftWork& W, const NearArgs& a, float* out) {
+#define UOTK_NEAR_ARGS tgt.cell, tgt.tile_start, src.cell, src.tile_start, w, W.near_items, \
+                       W.near_ctr, a, out
   switch (P) {
-    case 4:
-      k_near<KIND, 4><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
-                                                      src.tile_start, w, a, out);
-      break;
-    case 6:
-      k_near<KIND, 6><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
-                                                      src.tile_start, w, a, out);
-      break;
-    case 8:
-      k_near<KIND, 8><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
-                                                      src.tile_start, w, a, out);
-      break;
-    default:
-      k_near<KIND, REG_MAXP><<<blocks, NEAR_THREADS, 0, s>>>(tgt.cell, tgt.tile_start, src.cell,
-                                                             src.tile_start, w, a, out);
-      break;
+    case 4: k_near<KIND, 4><<<blocks, NEAR_THREADS, 0, s>>>(UOTK_NEAR_ARGS); break;
+    case 6: k_near<KIND, 6><<<blocks, NEAR_THREADS, 0, s>>>(UOTK_NEAR_ARGS); break;
+    case 8: k_near<KIND, 8><<<blocks, NEAR_THREADS, 0, s>>>(UOTK_NEAR_ARGS); break;
+    default: k_near<KIND, REG_MAXP><<<blocks, NEAR_THREADS, 0, s>>>(UOTK_NEAR_ARGS); break;
   }
+#undef UOTK_NEAR_ARGS
 }
 
 }  // namespace
@@ -387,7 +401,7 @@ uotk_status nfft_reg_table(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, N
 }
 
 uotk_status nfft_near(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& src,
-                      const float* w, const NfftPoints& tgt, float* out) {
+                      const float* w, const NfftPoints& tgt, NfftWork& W, float* out) {
   if (src.n == 0 || tgt.n == 0) return UOTK_OK;
   const RegPoly R = make_reg_poly(P);
   NearArgs a{};
@@ -408,17 +422,21 @@ uotk_status nfft_near(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const 
   a.tiles1 = P.tiles1;
   a.R = (int)ceil(rad / NFFT_TILE);
   const int tiles = P.tiles1 * P.tiles1 * P.tiles1;
-  const int blocks = tiles < 8 * ctx->num_sms ? tiles : 8 * ctx->num_sms;
+  const int blocks = 5 * ctx->num_sms;   // resident CTAs (43 registers x 256 threads)
   UOTK_PROF(ctx, s, "near");
+  UOTK_CUDA(ctx, cudaMemsetAsync(W.near_ctr, 0, 2 * sizeof(int), s));
+  k_near_items<<<grid_for(ctx, tiles, 256), 256, 0, s>>>(tgt.tile_start, tiles, W.near_items,
+                                                         W.near_ctr);
+  UOTK_LAUNCHED(ctx);
   switch (P.kernel) {
     case UOTK_KERNEL_LAPLACE:
-      launch_near<UOTK_KERNEL_LAPLACE>(a.P, blocks, s, src, w, tgt, a, out);
+      launch_near<UOTK_KERNEL_LAPLACE>(a.P, blocks, s, src, w, tgt, W, a, out);
       break;
     case UOTK_KERNEL_IMQ:
-      launch_near<UOTK_KERNEL_IMQ>(a.P, blocks, s, src, w, tgt, a, out);
+      launch_near<UOTK_KERNEL_IMQ>(a.P, blocks, s, src, w, tgt, W, a, out);
       break;
     default:
-      launch_near<UOTK_KERNEL_ENERGY>(a.P, blocks, s, src, w, tgt, a, out);
+      launch_near<UOTK_KERNEL_ENERGY>(a.P, blocks, s, src, w, tgt, W, a, out);
       break;
   }
   UOTK_LAUNCHED(ctx);
