@@ -32,6 +32,23 @@ struct Engine {
   // the last 4 zero): t = K(src -> tgt) w.
   // src/tgt: 0 = X, 1 = Y.
   virtual uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) = 0;
+  // nrhs sums over the same pairs src -> tgt (0 = X, 1 = Y): out[k] = the sum
+  // of plain() with weights base[k] (pot == NULL), or of half() with weights
+  // base[k]_j exp(lam pot_j - shift) (pot != NULL; then src != tgt).  The
+  // default issues them one by one; an engine may share the kernel values.
+  virtual uotk_status sums_multi(cudaStream_t s, int src, int tgt, int nrhs,
+                                 const float* const* base, const double* pot, double lam,
+                                 const long long* shift_slot, float* const* out) {
+    for (int k = 0; k < nrhs; ++k) {
+      if (pot) {
+        if (src == tgt) return UOTK_ERR_INTERNAL;
+        UOTK_TRY(half(s, tgt == 0 ? 0 : 1, base[k], pot, lam, shift_slot, out[k]));
+      } else {
+        UOTK_TRY(plain(s, src, tgt, base[k], out[k]));
+      }
+    }
+    return UOTK_OK;
+  }
   // Internal position -> caller index of `side` (NULL: identity).
   virtual const int* perm(int side) const = 0;
   // Internal-order copies of the caller's weights (may alias the inputs).

@@ -140,12 +140,15 @@ uotk_status op_mmd2_grad(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, i
   const bool px = grad_x != nullptr, py = grad_y != nullptr;
   const bool coords = px || py;
   const int64_t n1 = at_least1(n), m1 = at_least1(m);
+  // d <= 3: every coordinate's weights at once, so that each (source, target)
+  // pair of clouds takes one multi-sum of 1 + d right-hand sides
+  const bool fused = coords && d <= 3;
   auto carve = [&](Carver& cv, float** t, float** sx, float** sy, float** wbuf, Reducer& R) {
     for (int k = 0; k < 2; ++k) t[k] = cv.take<float>(n1);
     for (int k = 2; k < 4; ++k) t[k] = cv.take<float>(m1);
     for (int k = 0; k < 2; ++k) sx[k] = cv.take<float>(coords ? (size_t)d * n1 : 1);
     for (int k = 0; k < 2; ++k) sy[k] = cv.take<float>(coords ? (size_t)d * m1 : 1);
-    *wbuf = cv.take<float>((n > m ? n : m) + 4);
+    *wbuf = cv.take<float>((size_t)(fused ? 2 * d : 1) * ((n > m ? n : m) + 4));
     carve_reducer(ctx, cv, R);
   };
   float *t[4], *sx[2], *sy[2], *wbuf;
@@ -164,11 +167,35 @@ uotk_status op_mmd2_grad(uotk_ctx* ctx, cudaStream_t s, int d, const float* x, i
   carve(cv, t, sx, sy, &wbuf, R);
   const float* ai = E->weights(0);
   const float* bi = E->weights(1);
-  UOTK_TRY(E->plain(s, 0, 0, ai, t[0]));  // (K_xx a)_i
-  UOTK_TRY(E->plain(s, 1, 0, bi, t[1]));  // (K_xy b)_i
-  UOTK_TRY(E->plain(s, 1, 1, bi, t[2]));  // (K_yy b)_j
-  UOTK_TRY(E->plain(s, 0, 1, ai, t[3]));  // (K_yx a)_j
-  if (coords) {
+  if (fused) {
+    // right-hand sides {w, w (p_1 - o_1), .., w (p_d - o_d)} of each cloud
+    const size_t stride = (size_t)((n > m ? n : m) + 4);
+    const float* W[2][4] = {{ai}, {bi}};
+    for (int c = 0; c < d; ++c) {
+      float* wx = wbuf + (size_t)c * stride;
+      float* wy = wbuf + (size_t)(d + c) * stride;
+      UOTK_TRY(coord_weights(ctx, s, E.get(), 0, x, n, d, c, x, ai, wx));
+      UOTK_TRY(coord_weights(ctx, s, E.get(), 1, y, m, d, c, x, bi, wy));
+      W[0][1 + c] = wx;
+      W[1][1 + c] = wy;
+    }
+    // (src, tgt, t output, coordinate-sum output): K_xx a, K_xy b, K_yy b, K_yx a
+    struct Job { int src, tgt; float* t; float* sc; int64_t len; bool want; };
+    const Job jobs[4] = {{0, 0, t[0], sx[0], n1, px}, {1, 0, t[1], sx[1], n1, px},
+                         {1, 1, t[2], sy[0], m1, py}, {0, 1, t[3], sy[1], m1, py}};
+    for (const Job& j : jobs) {
+      float* outs[4] = {j.t};
+      for (int c = 0; c < d; ++c) outs[1 + c] = j.sc + c * j.len;
+      UOTK_TRY(E->sums_multi(s, j.src, j.tgt, j.want ? 1 + d : 1, W[j.src], nullptr, 0.0,
+                             nullptr, outs));
+    }
+  } else {
+    UOTK_TRY(E->plain(s, 0, 0, ai, t[0]));  // (K_xx a)_i
+    UOTK_TRY(E->plain(s, 1, 0, bi, t[1]));  // (K_xy b)_i
+    UOTK_TRY(E->plain(s, 1, 1, bi, t[2]));  // (K_yy b)_j
+    UOTK_TRY(E->plain(s, 0, 1, ai, t[3]));  // (K_yx a)_j
+  }
+  if (coords && !fused) {
     for (int c = 0; c < d; ++c) {
       UOTK_TRY(coord_weights(ctx, s, E.get(), 0, x, n, d, c, x, ai, wbuf));
       if (px) UOTK_TRY(E->plain(s, 0, 0, wbuf, sx[0] + c * n1));
@@ -220,6 +247,8 @@ uotk_status op_sinkhorn_divergence_grad(uotk_ctx* ctx, cudaStream_t s, int d, co
   double* gp[3][2] = {{grad_x, grad_y}, {grad_x, grad_x}, {grad_y, grad_y}};
   const double coef[3] = {1.0, -0.5, -0.5};
   const double lam = 1.0 / eps;
+  // d <= 3: all coordinate weights of a role at once (one multi-sum per role)
+  const bool fused = d <= 3;
   auto carve = [&](Carver& cv, const EngineSpec& sp, SolveBufs& B, Reducer& R, float** tx,
                    float** sxy, float** wbuf) {
     carve_solve(cv, sp.n, sp.m, true, B);
@@ -227,7 +256,7 @@ uotk_status op_sinkhorn_divergence_grad(uotk_ctx* ctx, cudaStream_t s, int d, co
     *tx = cv.take<float>(at_least1(sp.n));
     sxy[0] = cv.take<float>((size_t)d * at_least1(sp.n));
     sxy[1] = cv.take<float>((size_t)d * at_least1(sp.m));
-    *wbuf = cv.take<float>((sp.n > sp.m ? sp.n : sp.m) + 4);
+    *wbuf = cv.take<float>((size_t)(fused ? d : 1) * ((sp.n > sp.m ? sp.n : sp.m) + 4));
   };
   size_t need = 0;
   for (const EngineSpec& sp : specs) {
@@ -276,19 +305,47 @@ uotk_status op_sinkhorn_divergence_grad(uotk_ctx* ctx, cudaStream_t s, int d, co
     const float* wy = E->weights(1);
     // Role 0 (first cloud, potential beta): T_i at the final gamma, and the
     // coordinate sums over the second cloud with the final-gamma weights.
-    if (any_role[0]) UOTK_TRY(E->half(s, 0, wy, B.gamma, lam, shift_g, tx));
-    if (pts_role[0]) {
-      for (int c = 0; c < d; ++c) {
-        UOTK_TRY(coord_weights(ctx, s, E.get(), 1, sp.y, sp.m, d, c, x, wy, wbuf));
-        UOTK_TRY(E->half(s, 0, wbuf, B.gamma, lam, shift_g, sxy[0] + c * at_least1(sp.n)));
+    const size_t stride = (size_t)((sp.n > sp.m ? sp.n : sp.m) + 4);
+    if (fused) {
+      // one multi-sum per role: {T_i, s_i1, .., s_id} over the other cloud
+      const float* W[4] = {wy};
+      float* outs[4] = {tx};
+      if (any_role[0]) {
+        const int K = pts_role[0] ? 1 + d : 1;
+        for (int c = 0; pts_role[0] && c < d; ++c) {
+          UOTK_TRY(coord_weights(ctx, s, E.get(), 1, sp.y, sp.m, d, c, x, wy,
+                                 wbuf + (size_t)c * stride));
+          W[1 + c] = wbuf + (size_t)c * stride;
+          outs[1 + c] = sxy[0] + c * at_least1(sp.n);
+        }
+        UOTK_TRY(E->sums_multi(s, 1, 0, K, W, B.gamma, lam, shift_g, outs));
       }
-    }
-    // Role 1 (second cloud, potential gamma): B.ty already holds the sum at the
-    // final beta (the last half-step); coordinate sums over the first cloud.
-    if (pts_role[1]) {
-      for (int c = 0; c < d; ++c) {
-        UOTK_TRY(coord_weights(ctx, s, E.get(), 0, sp.x, sp.n, d, c, x, wx, wbuf));
-        UOTK_TRY(E->half(s, 1, wbuf, B.beta, lam, shift_b, sxy[1] + c * at_least1(sp.m)));
+      // Role 1 (second cloud, potential gamma): B.ty already holds the sum at
+      // the final beta (the last half-step); coordinate sums over the first cloud.
+      if (pts_role[1]) {
+        for (int c = 0; c < d; ++c) {
+          UOTK_TRY(coord_weights(ctx, s, E.get(), 0, sp.x, sp.n, d, c, x, wx,
+                                 wbuf + (size_t)c * stride));
+          W[c] = wbuf + (size_t)c * stride;
+          outs[c] = sxy[1] + c * at_least1(sp.m);
+        }
+        UOTK_TRY(E->sums_multi(s, 0, 1, d, W, B.beta, lam, shift_b, outs));
+      }
+    } else {
+      if (any_role[0]) UOTK_TRY(E->half(s, 0, wy, B.gamma, lam, shift_g, tx));
+      if (pts_role[0]) {
+        for (int c = 0; c < d; ++c) {
+          UOTK_TRY(coord_weights(ctx, s, E.get(), 1, sp.y, sp.m, d, c, x, wy, wbuf));
+          UOTK_TRY(E->half(s, 0, wbuf, B.gamma, lam, shift_g, sxy[0] + c * at_least1(sp.n)));
+        }
+      }
+      // Role 1 (second cloud, potential gamma): B.ty already holds the sum at the
+      // final beta (the last half-step); coordinate sums over the first cloud.
+      if (pts_role[1]) {
+        for (int c = 0; c < d; ++c) {
+          UOTK_TRY(coord_weights(ctx, s, E.get(), 0, sp.x, sp.n, d, c, x, wx, wbuf));
+          UOTK_TRY(E->half(s, 1, wbuf, B.beta, lam, shift_b, sxy[1] + c * at_least1(sp.m)));
+        }
       }
     }
     if (any_role[0]) {

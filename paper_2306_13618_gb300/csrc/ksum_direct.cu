@@ -330,7 +330,7 @@ int grid_for(const uotk_ctx* ctx, int64_t work, int threads, int per_sm) {
   return (int)(want < 1 ? 1 : (want < cap ? want : cap));
 }
 
-DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m) {
+DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m, int force_r) {
   DirectLayout L;
   L.d = d;
   L.n = n;
@@ -341,6 +341,7 @@ DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m) {
   // staged source (2 and 4 take the packed FP32x2 path of the Gaussian)
   const int64_t per_wave = (int64_t)DIRECT_THREADS * ctx->num_sms;
   L.reg_targets = !small ? 1 : (m >= 4 * per_wave ? 4 : (m >= 2 * per_wave ? 2 : 1));
+  if (force_r > 0) L.reg_targets = force_r;
   L.blocks_x = (int)((m + (int64_t)DIRECT_THREADS * L.reg_targets - 1) /
                      ((int64_t)DIRECT_THREADS * L.reg_targets));
   if (L.blocks_x < 1) L.blocks_x = 1;
@@ -565,6 +566,211 @@ uotk_status noalloc_scratch_on(int dev, unsigned char** out) {
 }
 
 }  // namespace
+
+
+// ---------------------------------------------------------------------------
+// Several right-hand sides over the same pairs (the coordinate sums of the
+// gradients): out_k[j] = sum_i w_k[i] exp(-|s_i - t_j|^2/eps), k < K <= 4,
+// Gaussian, d <= 3.  The distance and the exponential of a pair are computed
+// once for all K sums: 7 + K FP32 operations per pair instead of 8 K.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int MULTI_R = 2;   // targets per thread
+
+// w4[i] = {b_0[i], .., b_3[i]} * f_i, f_i = exp(lam pot_i - shift) (pot != NULL;
+// shift from its ordered-int64 slot) or 1; zero beyond n.
+__global__ void k_pack_w4(const float* __restrict__ w0, const float* __restrict__ w1,
+                          const float* __restrict__ w2, const float* __restrict__ w3,
+                          const double* __restrict__ pot, double lam,
+                          const long long* __restrict__ shift_slot, long long n,
+                          long long n_pad, float4* __restrict__ out) {
+  const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
+       i += (long long)gridDim.x * blockDim.x) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < n) {
+      const float f = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
+      v.x = w0 ? w0[i] * f : 0.f;
+      v.y = w1 ? w1[i] * f : 0.f;
+      v.z = w2 ? w2[i] * f : 0.f;
+      v.w = w3 ? w3[i] * f : 0.f;
+    }
+    out[i] = v;
+  }
+}
+
+// Sources: positions (the packed source tiles; their weight lane is ignored)
+// and weights {w_0..w_3}, both staged per tile by bulk copies into a 3-stage
+// ring; partial sums to part[(k splits + split) m + j].
+template <int D, int K>
+__global__ void __launch_bounds__(DIRECT_THREADS)
+    k_direct_multi(const float4* __restrict__ src, const float4* __restrict__ wsrc,
+                   long long tiles, int tiles_per_split, const float4* __restrict__ tgt,
+                   long long m, float neg_c, int splits, float* __restrict__ part,
+                   long long* __restrict__ flags) {
+  constexpr int R = MULTI_R;
+  __shared__ __align__(128) float4 sp[STAGES][DIRECT_TILE];
+  __shared__ __align__(128) float4 sw[STAGES][DIRECT_TILE];
+  __shared__ __align__(8) unsigned long long bar[STAGES];
+  const int tid = threadIdx.x;
+  const long long t_begin = (long long)blockIdx.y * tiles_per_split;
+  const long long t_end = min(t_begin + (long long)tiles_per_split, tiles);
+  const int count = t_end > t_begin ? (int)(t_end - t_begin) : 0;
+  const long long tb = (long long)blockIdx.x * (DIRECT_THREADS * R) + tid;
+  float tx[R], ty[R], tz[R], hi[R][K], lo[R][K];
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long j = tb + (long long)r * DIRECT_THREADS;
+    const float4 p = j < m ? tgt[j] : make_float4(0.f, 0.f, 0.f, 0.f);
+    tx[r] = p.x; ty[r] = p.y; tz[r] = p.z;
+#pragma unroll
+    for (int k = 0; k < K; ++k) { hi[r][k] = 0.f; lo[r][k] = 0.f; }
+  }
+  constexpr unsigned BYTES = DIRECT_TILE * sizeof(float4);
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < STAGES; ++s) mbar_init(&bar[s], 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0) {
+    for (int s = 0; s < STAGES && s < count; ++s) {
+      mbar_expect(&bar[s], 2 * BYTES);
+      bulk_copy(sp[s], src + (t_begin + s) * DIRECT_TILE, BYTES, &bar[s]);
+      bulk_copy(sw[s], wsrc + (t_begin + s) * DIRECT_TILE, BYTES, &bar[s]);
+    }
+  }
+  for (int kk = 0; kk < count; ++kk) {
+    const int s = kk % STAGES;
+    const bool ok = mbar_wait(&bar[s], (unsigned)(kk / STAGES) & 1u);
+    if (__syncthreads_or(!ok)) {
+      if (tid == 0) {
+        flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        for (int q = kk; q < count && q < kk + STAGES; ++q)
+          mbar_wait(&bar[q % STAGES], (unsigned)(q / STAGES) & 1u);
+      }
+      return;
+    }
+#pragma unroll 1
+    for (int j0 = 0; j0 < DIRECT_TILE; j0 += 32) {
+      float acc[R][K];
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < K; ++k) acc[r][k] = 0.f;
+#pragma unroll 4
+      for (int j = j0; j < j0 + 32; ++j) {
+        const float4 q = sp[s][j];
+        const float4 w4 = sw[s][j];
+        const float wv[4] = {w4.x, w4.y, w4.z, w4.w};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+          const float dx = tx[r] - q.x;
+          float r2 = dx * dx;
+          if (D > 1) { const float dy = ty[r] - q.y; r2 = fmaf(dy, dy, r2); }
+          if (D > 2) { const float dz = tz[r] - q.z; r2 = fmaf(dz, dz, r2); }
+          const float e = ex2_approx(r2 * neg_c);
+#pragma unroll
+          for (int k = 0; k < K; ++k) acc[r][k] = fmaf(wv[k], e, acc[r][k]);
+        }
+      }
+#pragma unroll
+      for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int k = 0; k < K; ++k) neumaier(hi[r][k], lo[r][k], acc[r][k]);
+    }
+    __syncthreads();
+    if (tid == 0 && kk + STAGES < count) {
+      mbar_expect(&bar[s], 2 * BYTES);
+      bulk_copy(sp[s], src + (t_begin + kk + STAGES) * DIRECT_TILE, BYTES, &bar[s]);
+      bulk_copy(sw[s], wsrc + (t_begin + kk + STAGES) * DIRECT_TILE, BYTES, &bar[s]);
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r) {
+    const long long j = tb + (long long)r * DIRECT_THREADS;
+    if (j < m)
+#pragma unroll
+      for (int k = 0; k < K; ++k)
+        part[((long long)k * splits + blockIdx.y) * m + j] = hi[r][k] + lo[r][k];
+  }
+}
+
+// out_k[j] = sum over splits of part[(k splits + split) m + j], added in FP64 in split order.
+__global__ void k_reduce_multi(const float* __restrict__ part, int splits, long long m, int K,
+                               float* __restrict__ o0, float* __restrict__ o1,
+                               float* __restrict__ o2, float* __restrict__ o3) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (long long)K * m;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int k = (int)(i / m);
+    const long long j = i - (long long)k * m;
+    double acc = 0.0;
+    for (int q = 0; q < splits; ++q) acc += (double)part[((long long)k * splits + q) * m + j];
+    float* o = k == 0 ? o0 : (k == 1 ? o1 : (k == 2 ? o2 : o3));
+    o[j] = (float)acc;
+  }
+}
+
+}  // namespace
+
+size_t direct_multi_bytes(const uotk_ctx* ctx, int d, int64_t n, int64_t m) {
+  const DirectLayout L = direct_layout(ctx, d, n, m, MULTI_R);
+  const size_t w4 = (size_t)(L.tiles * DIRECT_TILE > 0 ? L.tiles * DIRECT_TILE : 1) * sizeof(float4);
+  return w4 + 256 + (size_t)4 * L.splits * (m > 0 ? m : 1) * sizeof(float) + 256;
+}
+
+uotk_status direct_run_multi(uotk_ctx* ctx, cudaStream_t s, int d, int64_t n, int64_t m,
+                             const void* src_packed, const void* tgt_packed, int K,
+                             const float* const* w, const double* pot, double lam,
+                             const long long* shift_slot, void* scratch, double eps,
+                             float* const* out) {
+  if (m == 0) return UOTK_OK;
+  if (d > 3 || K < 1 || K > 4) return set_error(ctx, UOTK_ERR_INTERNAL, "direct_run_multi: d %d K %d", d, K);
+  if (n == 0) {
+    for (int k = 0; k < K; ++k) UOTK_CUDA(ctx, cudaMemsetAsync(out[k], 0, sizeof(float) * m, s));
+    return UOTK_OK;
+  }
+  const DirectLayout L = direct_layout(ctx, d, n, m, MULTI_R);
+  const int64_t n_pad = L.tiles * DIRECT_TILE;
+  Carver cv(reinterpret_cast<char*>(scratch));
+  float4* w4 = cv.take<float4>(n_pad);
+  float* part = cv.take<float>((size_t)4 * L.splits * m);
+  const float* wk[4] = {nullptr, nullptr, nullptr, nullptr};
+  for (int k = 0; k < K; ++k) wk[k] = w[k];
+  {
+    UOTK_PROF(ctx, s, "weights");
+    k_pack_w4<<<grid_for(ctx, n_pad, 256), 256, 0, s>>>(wk[0], wk[1], wk[2], wk[3], pot, lam,
+                                                        shift_slot, n, n_pad, w4);
+    UOTK_LAUNCHED(ctx);
+  }
+  const float neg_c = (float)(-1.4426950408889634 / eps);
+  const dim3 grid(L.blocks_x, L.splits);
+  const float4* src = reinterpret_cast<const float4*>(src_packed);
+  const float4* tgt = reinterpret_cast<const float4*>(tgt_packed);
+  {
+    UOTK_PROF(ctx, s, "direct_multi");
+#define UOTK_MULTI_CASE(DD, KK)                                                              \
+  if (d == DD && K == KK)                                                                    \
+    k_direct_multi<DD, KK><<<grid, DIRECT_THREADS, 0, s>>>(src, w4, L.tiles, L.tiles_per_split, \
+                                                           tgt, m, neg_c, L.splits, part,     \
+                                                           ctx->dflags);
+    UOTK_MULTI_CASE(1, 2) UOTK_MULTI_CASE(2, 2) UOTK_MULTI_CASE(2, 3)
+    UOTK_MULTI_CASE(3, 2) UOTK_MULTI_CASE(3, 3) UOTK_MULTI_CASE(3, 4)
+    UOTK_MULTI_CASE(1, 3) UOTK_MULTI_CASE(1, 4) UOTK_MULTI_CASE(2, 4)
+    UOTK_MULTI_CASE(1, 1) UOTK_MULTI_CASE(2, 1) UOTK_MULTI_CASE(3, 1)
+#undef UOTK_MULTI_CASE
+  }
+  UOTK_LAUNCHED(ctx);
+  {
+    UOTK_PROF(ctx, s, "split_reduce");
+    k_reduce_multi<<<grid_for(ctx, (int64_t)K * m, 256), 256, 0, s>>>(
+        part, L.splits, m, K, out[0], K > 1 ? out[1] : nullptr, K > 2 ? out[2] : nullptr,
+        K > 3 ? out[3] : nullptr);
+    UOTK_LAUNCHED(ctx);
+  }
+  return UOTK_OK;
+}
 
 }  // namespace uotk
 

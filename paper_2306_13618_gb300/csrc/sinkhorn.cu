@@ -40,6 +40,7 @@ struct DirectEngine : Engine {
   void* Px = nullptr;  // X packed as sources (weights a), also read as targets
   void* Py = nullptr;
   float* part = nullptr;
+  void* multi = nullptr;  // scratch of the fused multi-sum (d <= 3)
 
   static void layouts(uotk_ctx* ctx, const EngineSpec& sp, DirectLayout& yx, DirectLayout& xy,
                       DirectLayout& xx, DirectLayout& yy) {
@@ -60,9 +61,15 @@ struct DirectEngine : Engine {
     void* py = cv.take<char>(by > 0 ? by : 16);
     // split partials: FP32 sums, or {M, S} pairs of the log-domain form
     float* pp = part ? cv.take<float>(2 * part / sizeof(float)) : nullptr;
+    size_t mb = 0;
+    if (sp.d <= 3)
+      for (size_t b : {direct_multi_bytes(ctx, sp.d, sp.m, sp.n), direct_multi_bytes(ctx, sp.d, sp.n, sp.m),
+                       direct_multi_bytes(ctx, sp.d, sp.n, sp.n), direct_multi_bytes(ctx, sp.d, sp.m, sp.m)})
+        mb = b > mb ? b : mb;
+    void* mp = mb ? cv.take<char>(mb) : nullptr;
     if (e) {
       e->Lyx = yx; e->Lxy = xy; e->Lxx = xx; e->Lyy = yy;
-      e->Px = px; e->Py = py; e->part = pp;
+      e->Px = px; e->Py = py; e->part = pp; e->multi = mp;
     }
   }
 
@@ -92,6 +99,20 @@ struct DirectEngine : Engine {
     UOTK_TRY(direct_set_weights(ctx, s, L, src, base, pot, lam, shift_slot, true));
     DirectBufs bufs{src, tgt, part};
     return direct_run_lse(ctx, s, L, bufs, eps, out);
+  }
+  uotk_status sums_multi(cudaStream_t s, int src, int tgt, int nrhs, const float* const* base,
+                         const double* pot, double lam, const long long* shift_slot,
+                         float* const* out) override {
+    if (kernel != UOTK_KERNEL_GAUSS || d > 3 || !multi)
+      return Engine::sums_multi(s, src, tgt, nrhs, base, pot, lam, shift_slot, out);
+    // the Gaussian sums share one distance and exponential per pair, 4 at a time
+    for (int k0 = 0; k0 < nrhs; k0 += 4) {
+      const int K = nrhs - k0 < 4 ? nrhs - k0 : 4;
+      UOTK_TRY(direct_run_multi(ctx, s, d, src == 0 ? n : m, tgt == 0 ? n : m,
+                                src == 0 ? Px : Py, tgt == 0 ? Px : Py, K, base + k0, pot, lam,
+                                shift_slot, multi, eps, out + k0));
+    }
+    return UOTK_OK;
   }
   const int* perm(int) const override { return nullptr; }
   const float* weights(int side) const override { return side == 0 ? a : b; }

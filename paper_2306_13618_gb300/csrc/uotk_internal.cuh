@@ -280,7 +280,20 @@ struct DirectLayout {
 constexpr int DIRECT_TILE = 256;
 constexpr int DIRECT_THREADS = 256;
 
-DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m);
+// force_r > 0 fixes the targets per thread (d <= 3 kernels).
+DirectLayout direct_layout(const uotk_ctx* ctx, int d, int64_t n, int64_t m, int force_r = 0);
+
+// K <= 4 Gaussian sums over the same pairs (d <= 3): out[k][j] = sum_i w_k[i]
+// exp(-|s_i - t_j|^2 / eps), w_k[i] = w[k][i] (pot == NULL) or
+// w[k][i] exp(lam pot_i - shift) (shift from *shift_slot), from packed source
+// positions and targets (the layouts of direct_pack_sources /
+// direct_pack_targets); scratch of direct_multi_bytes(ctx, d, n, m) bytes.
+size_t direct_multi_bytes(const uotk_ctx* ctx, int d, int64_t n, int64_t m);
+uotk_status direct_run_multi(uotk_ctx* ctx, cudaStream_t s, int d, int64_t n, int64_t m,
+                             const void* src_packed, const void* tgt_packed, int K,
+                             const float* const* w, const double* pot, double lam,
+                             const long long* shift_slot, void* scratch, double eps,
+                             float* const* out);
 
 // Buffers of one direct summation.
 struct DirectBufs {
