@@ -104,7 +104,7 @@ typedef struct {
   int32_t bandwidth;   /* NFFT: bandwidth N, even, 4 <= N <= grid; 0 = grid/2 (oversampling sigma = 2) */
   int32_t cutoff;      /* NFFT: window cut-off m in [2, 8]; 0 = smallest of 6, 7, 8 meeting target_err */
   double period;       /* NFFT: torus period h; 0 = chosen from the data and eps (non-Gaussian kernels: must be >= the automatic choice) */
-  double target_err;   /* NFFT: accuracy goal, max error relative to sum|w|; 0 = 1e-6 */
+  double target_err;   /* NFFT: accuracy goal, max error relative to sum|w|; 0 = 1e-6.  Non-Gaussian kernels: bound on the error per unit weight relative to max|K| (the plan's Fourier series against K_R, checked at plan time; UNSUPPORTED if missed); 0 = 1e-3 (sums then measure about 1e-6 of sum|w| max|K| at the defaults) */
   int32_t kernel;      /* uotk_kernel; default UOTK_KERNEL_GAUSS */
   int32_t reg_degree;  /* NFFT, non-Gaussian kernels: regularisation degree p in [2, 12]; 0 = 4 */
 } uotk_sum_opts;

@@ -53,6 +53,7 @@ struct NfftParams {
   int kernel = 0;
   int reg_p = 0;
   double eps_i = 0.0;
+  double reg_target = 1e-3;   // bound the plan's self-check enforces (error per unit weight)
 };
 
 // Host: choose h, m; fill params (bounding box given).

@@ -326,6 +326,7 @@ uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const floa
       return set_error(ctx, UOTK_ERR_INVALID,
                        "NFFT: the non-Gaussian kernels need oversampling grid >= 2 bandwidth");
     P->reg_p = (opts && opts->reg_degree) ? opts->reg_degree : 4;
+    P->reg_target = (opts && opts->target_err > 0) ? opts->target_err : 1e-3;
     if (P->reg_p < 2 || P->reg_p > 12)
       return set_error(ctx, UOTK_ERR_INVALID, "NFFT: regularisation degree %d not in [2, 12]",
                        P->reg_p);

@@ -149,7 +149,7 @@ RegPoly make_reg_poly(const NfftParams& Pm) {
   return R;
 }
 
-__device__ double reg_kernel(const RegPoly& R, double rb) {
+__host__ __device__ double reg_kernel(const RegPoly& R, double rb) {
   if (rb < R.eps_i) {
     const double u = (rb / R.eps_i) * (rb / R.eps_i);
     double v = R.ti[R.P - 1];
@@ -219,6 +219,25 @@ __global__ void k_reg_full(const double* __restrict__ B, int N, int d,
     if (d >= 3) bi += (long long)N * N * kz;
     full[i] = f == 0.0 ? 0.f : (float)(B[bi] * scale * f);
   }
+}
+
+// m[kx'] = scale * sum over the other indices of B: the coefficients of the
+// trigonometric polynomial restricted to the first axis (its values there).
+__global__ void k_reg_marginal(const double* __restrict__ B, int N, int d, double scale,
+                               double* __restrict__ out) {
+  __shared__ double sh[256];
+  long long others = 1;
+  for (int t = 1; t < d; ++t) others *= N;
+  const int kx = blockIdx.x;
+  double acc = 0.0;
+  for (long long o = threadIdx.x; o < others; o += blockDim.x) acc += B[kx + (long long)N * o];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s = 128; s > 0; s >>= 1) {
+    if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[kx] = sh[0] * scale;
 }
 
 struct NearArgs {
@@ -395,8 +414,38 @@ uotk_status nfft_reg_table(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, N
   k_reg_full<<<grid_for(ctx, (long long)N * N * N, 256), 256, 0, s>>>(cur, N, d, dec,
                                                                       1.0 / (double)nd, W.full);
   UOTK_LAUNCHED(ctx);
-  // the pageable staging vector must outlive the copy
+  // Self-check of the Fourier approximation: on the first axis the series is
+  // sum_k m_k cos(2 pi k t); it interpolates K_R at the grid points t = l/N, so
+  // compare it with K_R halfway between them, over the radii pairs can have.
+  k_reg_marginal<<<N, 256, 0, s>>>(cur, N, d, 1.0 / (double)nd, nxt);
+  UOTK_LAUNCHED(ctx);
+  std::vector<double> mk(N);
+  UOTK_CUDA(ctx, cudaMemcpyAsync(mk.data(), nxt, sizeof(double) * N, cudaMemcpyDeviceToHost, s));
+  // the pageable vectors must outlive the copies
   UOTK_CUDA(ctx, cudaStreamSynchronize(s));
+  // Error bound per unit weight, relative to max |K| over the radii pairs can
+  // have (K itself, not K_R: the near field restores K there).
+  double err = 0.0, kmax = 0.0;
+  for (int l = 0; l < N / 2; ++l) {
+    const double t = (l + 0.5) / N;
+    if (t > 0.5 - R.eps_b) break;
+    double f = 0.0;
+    for (int i = 0; i < N; ++i) f += mk[i] * cos(2.0 * M_PI * (double)(i - N / 2) * t);
+    err = fmax(err, fabs(f - reg_kernel(R, t)));
+  }
+  for (int l = 0; l <= 256; ++l) {
+    const double r = R.h * (0.5 - R.eps_b) * l / 256.0;
+    double c[1];
+    kernel_taylor(R.kind, R.par, r, 1, c);
+    kmax = fmax(kmax, fabs(c[0]));
+  }
+  const double rel = kmax > 0.0 ? err / kmax : err;
+  if (!(rel <= P.reg_target))
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED,
+                     "NFFT: the regularised kernel (p = %d, bandwidth %d, period %g, parameter %g) "
+                     "misses the accuracy goal: estimated error %.1e > %.1e; raise the grid or "
+                     "the regularisation degree, or use the direct form",
+                     P.reg_p, N, P.h, P.eps, rel, P.reg_target);
   return UOTK_OK;
 }
 

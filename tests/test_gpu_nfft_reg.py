@@ -127,3 +127,15 @@ def test_options_and_validation(uotk):
         uotk.kernel_sum(dev(np.zeros((8, 4), np.float32)), dev(np.ones(8, np.float32)),
                         dev(np.zeros((8, 4), np.float32)), 0.5, method="nfft", kernel="imq")
     assert e.value.status == 4
+    # a plan too coarse for the kernel is refused by its self-check, not run
+    # (grid 64, p = 2, ell = 0.1 on [0, 1]^3: error bound per unit weight about
+    # 3e-3 > 1e-3 on the FP64 oracle of the same construction)
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.kernel_sum(dev(src), dev(w), dev(src[:64]), 0.1, method="nfft", kernel="laplace",
+                        grid=64, reg_degree=2)
+    assert e.value.status == 4
+    # ... and runs when the caller accepts that bound
+    got = uotk.kernel_sum(dev(src), dev(w), dev(src[:64]), 0.1, method="nfft", kernel="laplace",
+                          grid=64, reg_degree=2, target_err=1e-2)
+    ref = oracle.ksum_kernel("laplace", 0.1, f64(src), f64(w), f64(src[:64]))
+    assert np.max(np.abs(got.cpu().numpy() - ref)) <= 1e-2 * np.sum(w)
