@@ -324,7 +324,8 @@ def high_dim_extras(uotk, ctx, stream, rates, sms, peaks):
     """The direct form in d = 64 (gauss64 workload, n = m = 262144): FP32 against
     the tensor-core forms (BF16 cross term, three-product BF16x3), pairs/s, MUFU
     fraction and the error on 256 sampled targets against the FP64 oracle; then
-    one 100-sweep Sinkhorn solve with the BF16x3 form."""
+    one 100-sweep Sinkhorn solve with the BF16x3 form, plain and in the log
+    domain."""
     import numpy as np
     import torch
 
@@ -357,18 +358,19 @@ def high_dim_extras(uotk, ctx, stream, rates, sms, peaks):
                            "rel_err_max": float(np.max(np.abs(o - ref) / ref))}
         except uotk.UotkError as e:
             res[method] = {"error": str(e)}
-    try:
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        _, _, sweeps, _, _ = uotk.uot_sinkhorn(x, a, y, b, W.eps, W.rho, max_sweeps=W.sweeps,
-                                                method="direct_bf16x3", ctx=ctx)
-        e1.record(stream)
-        e1.synchronize()
-        res["sinkhorn_bf16x3"] = {"sweeps": sweeps,
-                                  "sweeps_per_s": sweeps / (e0.elapsed_time(e1) / 1e3)}
-    except uotk.UotkError as e:
-        res["sinkhorn_bf16x3"] = {"error": str(e)}
+    for key, log_domain in (("sinkhorn_bf16x3", False), ("sinkhorn_bf16x3_log_domain", True)):
+        try:
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, sweeps, _, _ = uotk.uot_sinkhorn(x, a, y, b, W.eps, W.rho, max_sweeps=W.sweeps,
+                                                    method="direct_bf16x3", ctx=ctx,
+                                                    log_domain=log_domain)
+            e1.record(stream)
+            e1.synchronize()
+            res[key] = {"sweeps": sweeps, "sweeps_per_s": sweeps / (e0.elapsed_time(e1) / 1e3)}
+        except uotk.UotkError as e:
+            res[key] = {"error": str(e)}
     return res
 
 

@@ -118,6 +118,43 @@ __device__ __forceinline__ float tc_chunk(const unsigned (&v)[16], const ulonglo
   return s0 + s1;
 }
 
+// Online log-sum-exp form of tc_chunk (log domain): the terms are
+//   e_j = 2c S_j + b_j + lw_j   (log2 units; lw_j = log2 w_j in the weight lane),
+// and (M, hi + lo) is updated so that the row's running sum of 2^{e_j} equals
+// 2^M (hi + lo).  No term has to be representable as an FP32 number.
+__device__ __forceinline__ void tc_chunk_lse(const unsigned (&v)[16], const ulonglong2* bw,
+                                             unsigned long long two_c2, float& M, float& hi,
+                                             float& lo) {
+  float e[16];
+  float cm = -INFINITY;
+#pragma unroll
+  for (int j = 0; j < 16; j += 2) {
+    const ulonglong2 q = bw[j >> 1];
+    const unsigned long long t = f2_add(
+        f2_fma(f2_pack(__uint_as_float(v[j]), __uint_as_float(v[j + 1])), two_c2, q.x), q.y);
+    f2_unpack(t, e[j], e[j + 1]);
+    cm = fmaxf(cm, fmaxf(e[j], e[j + 1]));
+  }
+  if (cm == -INFINITY) return;  // every weight of the chunk is zero
+  if (cm > M) {
+    const float f = ex2_approx(M - cm);  // 0 while M is still -inf
+    hi *= f;
+    lo *= f;
+    M = cm;
+  }
+  const unsigned long long m2 = f2_pack(M, M);
+  unsigned long long acc = 0ull;
+#pragma unroll
+  for (int j = 0; j < 16; j += 2) {
+    float d0, d1;
+    f2_unpack(f2_sub(f2_pack(e[j], e[j + 1]), m2), d0, d1);
+    acc = f2_add(acc, f2_pack(ex2_approx(d0), ex2_approx(d1)));
+  }
+  float s0, s1;
+  f2_unpack(acc, s0, s1);
+  tc_neumaier(hi, lo, s0 + s1);
+}
+
 // One CTA: 128 targets (blockIdx.x) against the source tiles of split
 // blockIdx.y.  tiles: [tile][2*DC blocks][16 KB], block 2c = hi, 2c+1 = lo of
 // coordinate chunk c.  bw: per pair of sources {b_j, b_j+1, w_j, w_j+1} with
@@ -127,7 +164,10 @@ __device__ __forceinline__ float tc_chunk(const unsigned (&v)[16], const ulonglo
 // of to every term (one FP32 add less per pair).  The host selects it only when
 // c R^2 <= 64, R the largest centred norm, so that no term 2^{c(|x|^2 - ||x-y||^2)}
 // can overflow.
-template <bool SPLIT, int DC, bool FAST, bool PAIR>
+// LSE: the log-domain form; weights are log2 w_j, each row keeps a running
+// maximum M and the sum relative to it, and out holds {M + aa, S} per row
+// (float2) with log2 t_i = M + aa + log2 S.
+template <bool SPLIT, int DC, bool FAST, bool PAIR, bool LSE = false>
 __global__ void __launch_bounds__(TC_THREADS, 1)
     k_direct_tc(const unsigned char* __restrict__ src_tiles, const float* __restrict__ src_bw,
                 long long src_tiles_total, int tiles_per_split,
@@ -186,6 +226,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
   tc_fence_after();
   const unsigned tmem = *tmem_slot;
   float hi = 0.f, lo = 0.f;  // epilogue: compensated row sum
+  float M = -INFINITY;        // log domain: the row's running maximum exponent
 
   if (warp == 0 && lane == 0) {
     // ---- producer ----
@@ -325,18 +366,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
 #pragma unroll
       for (int c0 = 0; c0 < TC_ROWS; c0 += 32) {
         tc_ld16(tb + (unsigned)(c0 + 16), v1);
-        tc_neumaier(hi, lo, tc_chunk<FAST>(v0, bw + (c0 >> 1), two_c2, aa2));
+        if constexpr (LSE)
+          tc_chunk_lse(v0, bw + (c0 >> 1), two_c2, M, hi, lo);
+        else
+          tc_neumaier(hi, lo, tc_chunk<FAST>(v0, bw + (c0 >> 1), two_c2, aa2));
         tc_wait16(v1);
         if (c0 + 32 < TC_ROWS) tc_ld16(tb + (unsigned)(c0 + 32), v0);
-        tc_neumaier(hi, lo, tc_chunk<FAST>(v1, bw + ((c0 + 16) >> 1), two_c2, aa2));
+        if constexpr (LSE)
+          tc_chunk_lse(v1, bw + ((c0 + 16) >> 1), two_c2, M, hi, lo);
+        else
+          tc_neumaier(hi, lo, tc_chunk<FAST>(v1, bw + ((c0 + 16) >> 1), two_c2, aa2));
         if (c0 + 32 < TC_ROWS) tc_wait16(v0);
       }
       tc_fence_before();
       mbar_arrive(&t_empty[a]);
     }
     if (g > 0) {
-      hand[(g - 1) * 2 * TC_ROWS + row] = hi;
-      hand[(g - 1) * 2 * TC_ROWS + TC_ROWS + row] = lo;
+      // log domain: {M, S}; otherwise the compensated pair {hi, lo}
+      hand[(g - 1) * 2 * TC_ROWS + row] = LSE ? M : hi;
+      hand[(g - 1) * 2 * TC_ROWS + TC_ROWS + row] = LSE ? hi + lo : lo;
     }
   }
   tc_fence_before();
@@ -345,12 +393,31 @@ __global__ void __launch_bounds__(TC_THREADS, 1)
     // warpgroup 0 adds the other warpgroups' pairs for the same row
     const int row = (warp & 3) * 32 + lane;
     const long long i = (long long)blockIdx.x * TC_ROWS + row;
+    if constexpr (LSE) {
 #pragma unroll
-    for (int q = 0; q < TC_EPI_GROUPS - 1; ++q) {
+      for (int q = 0; q < TC_EPI_GROUPS - 1; ++q) {
+        const float Mq = hand[q * 2 * TC_ROWS + row], Sq = hand[q * 2 * TC_ROWS + TC_ROWS + row];
+        if (Mq == -INFINITY) continue;
+        if (Mq > M) {
+          const float f = ex2_approx(M - Mq);
+          hi *= f;
+          lo *= f;
+          M = Mq;
+        }
+        tc_neumaier(hi, lo, Sq * ex2_approx(Mq - M));
+      }
+      if (i < m) {
+        const float aa = neg_c * tgt_n2[i];
+        reinterpret_cast<float2*>(out)[(long long)blockIdx.y * m + i] =
+            make_float2(M == -INFINITY ? -INFINITY : M + aa, hi + lo);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < (LSE ? 0 : TC_EPI_GROUPS - 1); ++q) {
       tc_neumaier(hi, lo, hand[q * 2 * TC_ROWS + row]);
       tc_neumaier(hi, lo, hand[q * 2 * TC_ROWS + TC_ROWS + row]);
     }
-    if (i < m) {
+    if (!LSE && i < m) {
       float v = hi + lo;
       if (FAST) {
         // v * 2^{aa}, aa = -c |x_i|^2 <= 0, without flushing a small result
@@ -498,16 +565,50 @@ __global__ void k_tc_norms(const float* __restrict__ pts, const float* __restric
   }
 }
 
-// w_j = base_j * exp(lam*pot_j - shift) (pot NULL: base_j; base NULL: 1).
-__global__ void k_tc_set_weights(float* __restrict__ bw, long long n, const float* __restrict__ base,
-                                 const double* __restrict__ pot, double lam,
-                                 const long long* __restrict__ shift_slot) {
+// w_j = base_j * exp(lam*pot_j - shift) (pot NULL: base_j; base NULL: 1), 0
+// past n; LOG: log2 w_j instead (-inf past n and for zero weights), the FP64
+// exponent taken to log2 units before the one rounding to FP32.
+template <bool LOG>
+__global__ void k_tc_set_weights(float* __restrict__ bw, long long n, long long n_pad,
+                                 const float* __restrict__ base, const double* __restrict__ pot,
+                                 double lam, const long long* __restrict__ shift_slot) {
   const double shift = pot ? ordered_to_dbl(*shift_slot) : 0.0;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n_pad;
        i += (long long)gridDim.x * blockDim.x) {
-    float v = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
-    if (base) v *= base[i];
+    float v;
+    if (LOG) {
+      if (i < n) {
+        const double e = pot ? (lam * pot[i] - shift) * 1.4426950408889634 : 0.0;
+        const float bl = base ? log2f(base[i]) : 0.f;
+        v = (float)((double)bl + e);
+      } else {
+        v = -INFINITY;
+      }
+    } else {
+      v = 0.f;
+      if (i < n) {
+        v = pot ? exp_shifted(lam * pot[i] - shift) : 1.f;
+        if (base) v *= base[i];
+      }
+    }
     bw[(i >> 1) * 4 + 2 + (i & 1)] = v;
+  }
+}
+
+// Log-sum-exp of the split partials {M, S}: out = {max M, sum S 2^{M_k - max}}.
+__global__ void k_tc_reduce_lse(const float2* __restrict__ part, int splits, long long m,
+                                float2* __restrict__ out) {
+  for (long long j = blockIdx.x * (long long)blockDim.x + threadIdx.x; j < m;
+       j += (long long)gridDim.x * blockDim.x) {
+    float mx = -INFINITY;
+    for (int k = 0; k < splits; ++k) mx = fmaxf(mx, part[(long long)k * m + j].x);
+    double s = 0.0;
+    if (mx != -INFINITY)
+      for (int k = 0; k < splits; ++k) {
+        const float2 p = part[(long long)k * m + j];
+        if (p.x != -INFINITY) s += (double)p.y * (double)exp2f(p.x - mx);
+      }
+    out[j] = make_float2(mx, (float)s);
   }
 }
 
@@ -557,16 +658,16 @@ TcSplit tc_split(const uotk_ctx* ctx, int64_t src_tiles, int64_t tgt_tiles) {
   return L;
 }
 
-template <bool SPLIT, int DC, bool FAST>
+template <bool SPLIT, int DC, bool FAST, bool LSE = false>
 uotk_status tc_launch(uotk_ctx* ctx, cudaStream_t s, const TcCloud& src, const TcCloud& tgt,
                       const TcSplit& L, double eps, float* dst) {
   constexpr bool PAIR = tc_can_pair(SPLIT, DC);
   constexpr size_t smem0 = tc_smem_bytes(SPLIT, DC, PAIR);
   constexpr size_t smem = smem0 > (size_t)TC_MIN_SMEM ? smem0 : (size_t)TC_MIN_SMEM;
-  UOTK_CUDA(ctx, smem_attr(s, k_direct_tc<SPLIT, DC, FAST, PAIR>, smem));
+  UOTK_CUDA(ctx, smem_attr(s, k_direct_tc<SPLIT, DC, FAST, PAIR, LSE>, smem));
   const double c = 1.4426950408889634 / eps;
   const dim3 grid((unsigned)tgt.tiles, (unsigned)L.splits);
-  k_direct_tc<SPLIT, DC, FAST, PAIR><<<grid, TC_THREADS, smem, s>>>(
+  k_direct_tc<SPLIT, DC, FAST, PAIR, LSE><<<grid, TC_THREADS, smem, s>>>(
       src.tile_data, src.bw, src.tiles, L.tiles_per_split, tgt.tile_data, tgt.n2, tgt.n,
       (float)(2.0 * c), (float)(-c), dst, ctx->dflags);
   UOTK_LAUNCHED(ctx);
@@ -598,6 +699,32 @@ uotk_status tc_run(uotk_ctx* ctx, cudaStream_t s, bool split, int dc, bool fast,
   if (L.splits > 1) {
     UOTK_PROF(ctx, s, "split_reduce");
     k_tc_reduce<<<grid_for(ctx, tgt.n, 256), 256, 0, s>>>(part, L.splits, tgt.n, out);
+    UOTK_LAUNCHED(ctx);
+  }
+  return UOTK_OK;
+}
+
+// Log domain: out[i] = {M_i, S_i} with log2 sum_j w_j exp(-||tgt_i - src_j||^2/eps)
+// = M_i + log2 S_i, log2 w in src.bw; part holds splits * m float2.
+uotk_status tc_run_lse(uotk_ctx* ctx, cudaStream_t s, bool split, int dc, const TcCloud& src,
+                       const TcCloud& tgt, double eps, float2* part, float2* out) {
+  if (tgt.n == 0) return UOTK_OK;
+  if (src.n == 0) return set_error(ctx, UOTK_ERR_INVALID, "log-domain sum with no sources");
+  const TcSplit L = tc_split(ctx, src.tiles, tgt.tiles);
+  float* dst = reinterpret_cast<float*>(L.splits > 1 ? part : out);
+  {
+    UOTK_PROF(ctx, s, "direct_tc_lse");
+    uotk_status st = UOTK_ERR_INTERNAL;
+#define UOTK_TC_LSE_CASE(SP, DCC) \
+  if (split == SP && dc == DCC) st = tc_launch<SP, DCC, true, true>(ctx, s, src, tgt, L, eps, dst);
+    UOTK_TC_LSE_CASE(true, 1) UOTK_TC_LSE_CASE(true, 2) UOTK_TC_LSE_CASE(false, 1)
+    UOTK_TC_LSE_CASE(false, 2)
+#undef UOTK_TC_LSE_CASE
+    UOTK_TRY(st);
+  }
+  if (L.splits > 1) {
+    UOTK_PROF(ctx, s, "split_reduce");
+    k_tc_reduce_lse<<<grid_for(ctx, tgt.n, 256), 256, 0, s>>>(part, L.splits, tgt.n, out);
     UOTK_LAUNCHED(ctx);
   }
   return UOTK_OK;
@@ -638,7 +765,7 @@ struct TcEngine : Engine {
         part = need > part ? need : part;
       }
     }
-    float* pp = cv.take<float>(part);
+    float* pp = cv.take<float>(2 * part);  // FP32 sums, or {M, S} pairs of the log domain
     float* ctr = cv.take<float>(128);
     long long* sl = cv.take<long long>(256);
     double* r2 = cv.take<double>(1);
@@ -654,11 +781,16 @@ struct TcEngine : Engine {
   }
 
   uotk_status set_weights(cudaStream_t s, TcCloud& C, const float* base, const double* pot,
-                          double lam, const long long* shift_slot) {
+                          double lam, const long long* shift_slot, bool log2w = false) {
     if (C.n == 0) return UOTK_OK;
     UOTK_PROF(ctx, s, "weights");
-    k_tc_set_weights<<<grid_for(ctx, C.n, 256, 4), 256, 0, s>>>(C.bw, C.n, base, pot, lam,
-                                                                 shift_slot);
+    const long long n_pad = C.tiles * TC_ROWS;
+    if (log2w)
+      k_tc_set_weights<true><<<grid_for(ctx, n_pad, 256, 4), 256, 0, s>>>(C.bw, C.n, n_pad, base,
+                                                                          pot, lam, shift_slot);
+    else
+      k_tc_set_weights<false><<<grid_for(ctx, n_pad, 256, 4), 256, 0, s>>>(C.bw, C.n, n_pad, base,
+                                                                           pot, lam, shift_slot);
     UOTK_LAUNCHED(ctx);
     return UOTK_OK;
   }
@@ -669,6 +801,13 @@ struct TcEngine : Engine {
     const TcCloud& tgt = side == 0 ? X : Y;
     UOTK_TRY(set_weights(s, src, base, pot, lam, shift_slot));
     return tc_run(ctx, s, split, dc, fast, src, tgt, eps, part, out);
+  }
+  uotk_status half_log(cudaStream_t s, int side, const float* base, const double* pot,
+                       double lam, const long long* shift_slot, float2* out) override {
+    TcCloud& src = side == 0 ? Y : X;
+    const TcCloud& tgt = side == 0 ? X : Y;
+    UOTK_TRY(set_weights(s, src, base, pot, lam, shift_slot, true));
+    return tc_run_lse(ctx, s, split, dc, src, tgt, eps, reinterpret_cast<float2*>(part), out);
   }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
     TcCloud& S = src == 0 ? X : Y;

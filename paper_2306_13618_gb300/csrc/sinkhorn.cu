@@ -526,10 +526,10 @@ uotk_status op_uot_sinkhorn(uotk_ctx* ctx, cudaStream_t s, int d, const float* x
   const bool copies = sp.method == UOTK_NFFT;
   const bool logd = (flags & UOTK_LOG_DOMAIN) != 0;
   const int kernel = opts ? opts->kernel : UOTK_KERNEL_GAUSS;
-  if (logd && (sp.method != UOTK_DIRECT || kernel != UOTK_KERNEL_GAUSS))
+  if (logd && (sp.method == UOTK_NFFT || kernel != UOTK_KERNEL_GAUSS))
     return set_error(ctx, UOTK_ERR_UNSUPPORTED,
-                     "uot_sinkhorn: the log domain is implemented for the direct FP32 form of "
-                     "the squared-distance cost only");
+                     "uot_sinkhorn: the log domain is implemented for the direct forms (FP32, "
+                     "BF16, BF16x3) of the squared-distance cost only");
   // gamma^0 = c* 1 (Remark on the initialisation; c* of Eq. 561), computed
   // before the solve's workspace is carved.
   const bool cstar_init = (flags & UOTK_CSTAR_INIT) != 0;

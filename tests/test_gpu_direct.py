@@ -264,7 +264,7 @@ def test_sinkhorn_log_domain_tiny_eps(uotk):
 
 def test_log_domain_rejected_off_direct(uotk):
     W = inputs.uniform_box(n=100, m=100)
-    for method in ("nfft", "direct_bf16x3"):
+    for method in ("nfft",):
         with pytest.raises(uotk.UotkError) as e:
             uotk.uot_sinkhorn(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho,
                               max_sweeps=3, log_domain=True, method=method)

@@ -161,3 +161,61 @@ def test_mmd2_tc(uotk):
     v, parts = uotk.mmd2(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.ell, method="direct_bf16x3")
     assert np.allclose(parts, rp, rtol=delta, atol=0)
     assert abs(v - rv) <= delta * (rp[0] + 2 * rp[1] + rp[2])
+
+
+@pytest.mark.parametrize("method", ["direct_bf16x3", "direct_bf16"])
+def test_sinkhorn_tc_log_domain_matches_oracle(uotk, method):
+    """UOTK_LOG_DOMAIN with the tensor-core cross term (per-row log-sum-exp in
+    the epilogue) on the high-dimensional workload's subsample: the same bar as
+    the plain tensor-core solve, and the same duals as it."""
+    W = inputs.gauss64(seed=3001, n=1024, m=1024)
+    X, Y, A, B = f64(W.x), f64(W.y), f64(W.a), f64(W.b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=W.sweeps, logdomain=True)
+    args = (dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho)
+    beta, gamma, _, value, _ = uotk.uot_sinkhorn(*args, max_sweeps=W.sweeps, method=method,
+                                                 log_domain=True)
+    delta = bound(method, radius(W.x, W.y), W.eps)
+    res = residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg)
+    assert res <= delta * (1 + W.rho / W.eps), (res, delta)
+    v = oracle.dual_value(X, A, Y, B, W.eps, W.rho, W.rho, rb, rg)
+    assert abs(value - v) <= delta * abs(v) * (1 + W.rho / W.eps)
+    b2, g2, _, _, _ = uotk.uot_sinkhorn(*args, max_sweeps=W.sweeps, method=method)
+    assert residual(beta.cpu().numpy(), gamma.cpu().numpy(), b2.cpu().numpy(),
+                    g2.cpu().numpy()) <= delta * (1 + W.rho / W.eps)
+
+
+@pytest.mark.parametrize("method", ["direct_bf16x3", "direct_bf16"])
+def test_sinkhorn_tc_log_domain_tiny_eps(uotk, method):
+    """eps = 5e-4 on clouds 0.3 apart along x: the farthest targets see no
+    source within exp2(-260), so the plain form underflows (NONFINITE) while the
+    log domain follows the FP64 oracle.  Bound: per half-step the log of a sum
+    carries the tensor-core term error delta_tc (the bound of this file, in
+    relative terms of every summand) and the FP32 rounding of the exponents
+    (2^-22 A ln2, A the largest exponent in log2 units), amplified by at most q
+    per half-step over S sweeps."""
+    g = inputs.rng(78)
+    n = m = 400
+    x = np.column_stack([g.uniform(0, 0.3, n), g.uniform(0, 0.1, n)]).astype(np.float32)
+    y = np.column_stack([g.uniform(0.3, 0.6, m), g.uniform(0, 0.1, m)]).astype(np.float32)
+    a = np.full(n, 1.0 / n, np.float32)
+    b = np.full(m, 1.2 / m, np.float32)
+    eps, rho, S = 5e-4, 1.0, 20
+    args = (dev(x), dev(a), dev(y), dev(b), eps, rho)
+    with pytest.raises(uotk.UotkError) as e:
+        uotk.uot_sinkhorn(*args, max_sweeps=S, method=method)
+    assert e.value.status == 5
+    beta, gamma, _, value, _ = uotk.uot_sinkhorn(*args, max_sweeps=S, method=method,
+                                                 log_domain=True)
+    X, Y, A, B = f64(x), f64(y), f64(a), f64(b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, eps, rho, sweeps=S, logdomain=True)
+    lam, c = 1.0 / eps, 1.4426950408889634 / eps
+    R = radius(x, y)
+    spread = max(np.ptp(lam * rb), np.ptp(lam * rg)) * 1.4426950408889634
+    big = c * R * R + spread
+    q = rho / (1 + rho * lam)
+    delta = bound(method, R, eps) + 2.0 ** -22 * big * np.log(2)
+    tol = 4 * S * q * delta
+    assert np.max(np.abs(beta.cpu().numpy() - rb)) <= tol, tol
+    assert np.max(np.abs(gamma.cpu().numpy() - rg)) <= tol, tol
+    v = oracle.dual_value(X, A, Y, B, eps, rho, rho, rb, rg)
+    assert np.isfinite(value) and abs(value - v) <= max(delta, 1e-4) * abs(v)
