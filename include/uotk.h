@@ -216,9 +216,12 @@ uotk_status uotk_kernel_sum_noalloc(void* stream, int d, const float* src, int64
  *   log t_i = max_j a_ij + log sum_j exp(a_ij - max_j a_ij),
  *   a_ij = log w_j - ||x_i - y_j||^2/eps, w_j = nu_j e^{lambda gamma_j} (ref 0),
  * so that neither the weights nor the kernel values need to be representable
- * in FP32 (very small eps); the direct FP32 form only (UNSUPPORTED otherwise).
- * The exponents a_ij are FP32: the relative accuracy of each term is that of
- * an FP32 number of the size of |log w_j - M|, M = max_j lambda gamma_j. */
+ * in FP32 (very small eps).  The direct forms: FP32 (a two-pass row maximum),
+ * BF16 and BF16x3 (an online maximum per row in the tensor-core epilogue);
+ * UNSUPPORTED with NFFT or another kernel.  The exponents a_ij are FP32: the
+ * relative accuracy of each term is that of an FP32 number of the size of
+ * |log w_j - M|, M = max_j lambda gamma_j (plus the cross-term error of the
+ * BF16 forms). */
 #define UOTK_LOG_DOMAIN 2u
 /* flags & UOTK_CSTAR_INIT: gamma^0 = c* 1 with c* of Eq. (561) as computed by
  * uotk_cstar (the Remark on the initialisation of Sinkhorn's algorithm read
