@@ -382,6 +382,107 @@ __global__ void __launch_bounds__(32 * WF_WARPS)
   for (int i = L; i < n; i += 32) g[r * n + i] = rowbuf[w][i];
 }
 
+// Passes 1 + 2 fused, one CTA per z-plane (grids up to 128^3): the plane's n
+// rows are transformed along x (N of n outputs kept) into shared memory, then
+// its N columns along y (N kept), and the N x N block is written to
+// A2[z][ky'][kx'].  Shared rows are padded by one element so that a column's
+// lanes fall into different banks.
+constexpr int WP_WARPS = 16;   // warps of a plane CTA
+template <int R>
+__global__ void __launch_bounds__(32 * WP_WARPS)
+    k_wfft_xy_fwd(const float* __restrict__ g, float2* __restrict__ A2, int N) {
+  constexpr int n = 32 * R;
+  extern __shared__ __align__(16) float2 psh[];
+  float2* tw = psh;                  // [n]
+  float2* plane = tw + n;            // [n][N + 1]: rows after the x transform
+  float2* blk = plane + n * (N + 1); // [N][N]: the kept (ky', kx') block
+  const int P = N + 1;
+  full_twiddles(tw, n);
+  __syncthreads();
+  const int L = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long z = blockIdx.x;
+  const int br = (int)(__brev((unsigned)L) >> 27);
+  for (int y = w; y < n; y += WP_WARPS) {
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = make_float2(g[(z * n + y) * n + 32 * j + L], 0.f);
+    warp_fft<R>(v, tw, -1);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+      const int kp = kept_pos(k1 + R * br, N, n);
+      if (kp >= 0) plane[y * P + kp] = v[k1];
+    }
+  }
+  __syncthreads();
+  for (int kx = w; kx < N; kx += WP_WARPS) {
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) v[j] = plane[(32 * j + L) * P + kx];
+    warp_fft<R>(v, tw, -1);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) {
+      const int kp = kept_pos(k1 + R * br, N, n);
+      if (kp >= 0) blk[kp * N + kx] = v[k1];
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) A2[z * N * N + i] = blk[i];
+}
+
+// Passes 4 + 5 fused, one CTA per z-plane: the N x N block of A2[z] is
+// transformed back along y (zero outside I_N, n outputs), then every row along x,
+// and the real parts are written to the grid.
+template <int R>
+__global__ void __launch_bounds__(32 * WP_WARPS)
+    k_wfft_yx_inv(const float2* __restrict__ A2, float* __restrict__ g, int N) {
+  constexpr int n = 32 * R;
+  extern __shared__ __align__(16) float2 psh[];
+  float2* tw = psh;                  // [n]
+  float2* blk = tw + n;              // [N][N + 1]
+  float2* plane = blk + N * (N + 1); // [n][N + 1]: columns after the y transform
+  float* rowbuf = reinterpret_cast<float*>(plane + n * (N + 1));  // [WP_WARPS][n]
+  const int P = N + 1;
+  full_twiddles(tw, n);
+  const long long z = blockIdx.x;
+  for (int i = threadIdx.x; i < N * N; i += blockDim.x) blk[(i / N) * P + i % N] = A2[z * N * N + i];
+  __syncthreads();
+  const int L = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int br = (int)(__brev((unsigned)L) >> 27);
+  for (int kx = w; kx < N; kx += WP_WARPS) {
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int kp = kept_pos(32 * j + L, N, n);
+      v[j] = kp >= 0 ? blk[kp * P + kx] : make_float2(0.f, 0.f);
+    }
+    warp_fft<R>(v, tw, +1);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) plane[(k1 + R * br) * P + kx] = v[k1];
+  }
+  __syncthreads();
+  float* rb = rowbuf + w * n;
+  for (int y = w; y < n; y += WP_WARPS) {
+    float2 v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const int kp = kept_pos(32 * j + L, N, n);
+      v[j] = kp >= 0 ? plane[y * P + kp] : make_float2(0.f, 0.f);
+    }
+    warp_fft<R>(v, tw, +1);
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) rb[k1 + R * br] = v[k1].x;
+    __syncwarp();
+    for (int i = L; i < n; i += 32) g[(z * n + y) * n + i] = rb[i];
+    __syncwarp();
+  }
+}
+
+template <int R>
+constexpr size_t wfft_plane_smem(int N) {
+  return sizeof(float2) * (32 * R + (size_t)(32 * R) * (N + 1) + (size_t)N * (N + 1)) +
+         sizeof(float) * WP_WARPS * 32 * R;
+}
+
 // Passes 2 and 4 (y) and 3 (z): lines at a stride, WF_LINES adjacent lines per
 // CTA staged through shared memory so global accesses stay coalesced.
 //   mode 0 (y forward):  in A1[z][y][kx']  (n rows)  -> out A2[z][ky'][kx'] (N rows)
@@ -479,6 +580,19 @@ uotk_status wfft_convolve(uotk_ctx* ctx, cudaStream_t s, int N, const float* sca
   constexpr int n = 32 * R;
   const size_t lsmem = sizeof(float2) * (n + 2 * n * WF_PITCH);
   UOTK_CUDA(ctx, smem_attr(s, k_wfft_lines<R>, lsmem));
+  const size_t psmem = wfft_plane_smem<R>(N);
+  if (psmem <= (size_t)ctx->max_smem_optin) {
+    // three passes: x and y of each z-plane in one CTA, z, then y and x back
+    UOTK_CUDA(ctx, smem_attr(s, k_wfft_xy_fwd<R>, psmem));
+    UOTK_CUDA(ctx, smem_attr(s, k_wfft_yx_inv<R>, psmem));
+    k_wfft_xy_fwd<R><<<n, 32 * WP_WARPS, psmem, s>>>(grid_in, A2, N);
+    UOTK_LAUNCHED(ctx);
+    k_wfft_lines<R><<<N * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A2, A2, N, 2, scale, full);
+    UOTK_LAUNCHED(ctx);
+    k_wfft_yx_inv<R><<<n, 32 * WP_WARPS, psmem, s>>>(A2, grid_out, N);
+    UOTK_LAUNCHED(ctx);
+    return UOTK_OK;
+  }
   k_wfft_x_fwd<R><<<n * n / WF_WARPS, 32 * WF_WARPS, 0, s>>>(grid_in, A1, N);
   UOTK_LAUNCHED(ctx);
   k_wfft_lines<R><<<n * (N / WF_LINES), 32 * WF_WARPS, lsmem, s>>>(A1, A2, N, 0, scale, full);
