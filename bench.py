@@ -187,22 +187,39 @@ def stage_rooflines(prof, W, sms, peaks, plan, rates):
     return out
 
 
+def _span_sha(text, starts):
+    """SHA-256 of the source spans that begin at each marker in `starts` and end
+    at the first line holding only a closing brace after it (one function each),
+    or None when a marker is missing."""
+    import hashlib
+    h = hashlib.sha256()
+    for st in starts:
+        i = text.find(st)
+        if i < 0:
+            return None
+        j = text.find("\n}\n", i)
+        if j < 0:
+            return None
+        h.update(text[i:j + 3].encode())
+    return h.hexdigest()
+
+
 def recorded_traffic(stage):
     """DRAM bytes per launch of `stage` from the committed ncu capture
-    (profiles/ncu_traffic.json), or None when the kernel source has changed since
-    the capture (its SHA-256 no longer matches) or no capture exists."""
-    import hashlib
+    (profiles/ncu_traffic.json), or None when no capture exists or the kernel's
+    source (its function and the staging helpers it calls, hashed span by span)
+    has changed since the capture."""
     try:
         with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
             rec = json.load(f)
-        with open(os.path.join(ROOT, rec["source"]), "rb") as f:
-            sha = hashlib.sha256(f.read()).hexdigest()
+        with open(os.path.join(ROOT, rec["source"])) as f:
+            text = f.read()
     except (OSError, ValueError, KeyError):
         return None
-    if sha != rec.get("source_sha256"):
-        return None
     k = rec.get("kernels", {}).get(stage)
-    return k.get("bytes_per_launch") if k else None
+    if not k or _span_sha(text, k.get("spans", [])) != k.get("span_sha256"):
+        return None
+    return k.get("bytes_per_launch")
 
 
 def cpu_oracle_rate(W, seconds, rank0=True):
