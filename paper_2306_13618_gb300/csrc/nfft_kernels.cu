@@ -98,15 +98,21 @@ __device__ __forceinline__ void load_vec(const float* p, float* r) {
 }
 
 // ---------------------------------------------------------------- spread ----
-template <int M>
-__global__ void __launch_bounds__(8 * M * M)
+// Thread (kz, ky, half) of the 8m^2 threads owns one row half; with RPT rows per
+// thread (RPT | 2m), thread (kz, ky < 2m/RPT, half) of 8m^2/RPT threads owns the
+// row halves (kz, ky + k 2m/RPT), k < RPT, which share the phi_x half it loads
+// for every point.
+template <int M, int RPT = 1>
+__global__ void __launch_bounds__(8 * M * M / RPT)
     k_spread(const float* __restrict__ win, const int* __restrict__ ckey,
              const float* __restrict__ wts, const int* __restrict__ unit_tile,
              const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
              const int* __restrict__ num_units, int n, int tiles1, float* __restrict__ grid,
              long long* __restrict__ flags) {
   using G = Geo<M>;
-  constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M;
+  constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M / RPT;
+  constexpr int YR = W2 / RPT;  // rows of ky per thread group
+  static_assert(W2 % RPT == 0, "rows per thread divide 2m");
   constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
@@ -130,7 +136,7 @@ __global__ void __launch_bounds__(8 * M * M)
   int tx0, ty0, tz0;
   tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
-  const int kz = r / W2, ky = r - kz * W2;
+  const int kz = r / YR, ky = r - kz * YR;
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
@@ -160,6 +166,48 @@ __global__ void __launch_bounds__(8 * M * M)
     for (int g = 0; g < ng; ++g) {
       const int p0 = gstart[g], p1 = gstart[g + 1];
       const int key = skey[p0];
+      if constexpr (RPT > 1) {
+        float acc[RPT][M];
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+#pragma unroll
+          for (int j = 0; j < M; ++j) acc[k][j] = 0.f;
+        int q = p0;
+        for (; q + 1 < p1; q += 2) {
+          const float* w0 = sw + q * WS;
+          const float* w1 = w0 + WS;
+          const float z0 = w0[ZO + kz], z1 = w1[ZO + kz];
+          float f0[M], f1[M];
+          load_vec<M>(w0 + half * HP, f0);
+          load_vec<M>(w1 + half * HP, f1);
+#pragma unroll
+          for (int k = 0; k < RPT; ++k) {
+            const float a0 = z0 * w0[YO + ky + k * YR], a1 = z1 * w1[YO + ky + k * YR];
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc[k][j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[k][j]));
+          }
+        }
+        if (q < p1) {
+          const float* w0 = sw + q * WS;
+          const float z0 = w0[ZO + kz];
+          float f0[M];
+          load_vec<M>(w0 + half * HP, f0);
+#pragma unroll
+          for (int k = 0; k < RPT; ++k) {
+            const float a0 = z0 * w0[YO + ky + k * YR];
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc[k][j] = fmaf(a0, f0[j], acc[k][j]);
+          }
+        }
+        const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+        float* dst = blk + ((bz + kz) * E + by + ky) * E + bx + half * M;
+#pragma unroll
+        for (int k = 0; k < RPT; ++k)
+#pragma unroll
+          for (int j = 0; j < M; ++j) dst[k * YR * E + j] += acc[k][j];
+        __syncthreads();
+        continue;
+      }
       float acc[M];
 #pragma unroll
       for (int j = 0; j < M; ++j) acc[j] = 0.f;
@@ -796,10 +844,14 @@ template <int M>
 uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* wts, float* grid) {
   const size_t smem = unit_smem<M>();
-  UOTK_CUDA(ctx, smem_attr(s, k_spread<M>, smem));
-  k_spread<M><<<S.max_units, 8 * M * M, smem, s>>>(S.win, S.ckey, wts, S.unit_tile, S.unit_begin,
-                                                   S.unit_count, S.num_units, P.n, P.tiles1, grid,
-                                                   ctx->dflags);
+  // two rows per thread: 94.0 ms per 200-sweep gmm3 solve at m = 6, against
+  // 109.3 ms with one and 104.4 ms with four (72-thread CTAs hide too little)
+  constexpr int RPT = 2;
+  UOTK_CUDA(ctx, smem_attr(s, k_spread<M, RPT>, smem));
+  k_spread<M, RPT><<<S.max_units, 8 * M * M / RPT, smem, s>>>(S.win, S.ckey, wts, S.unit_tile,
+                                                              S.unit_begin, S.unit_count,
+                                                              S.num_units, P.n, P.tiles1, grid,
+                                                              ctx->dflags);
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
