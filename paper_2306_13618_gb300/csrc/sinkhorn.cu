@@ -165,6 +165,10 @@ __global__ void k_dual_update(const void* __restrict__ t, const float* __restric
     if (reset_delta >= 0) flags[reset_delta] = ORDERED_NEG_INF;
   }
   const double shift = ordered_to_dbl(flags[shift_in]);
+  // v = -q (log t + shift) = -q log t - q shift (ref 0), q (log base - log t - shift)
+  // (ref 1): the shift enters once per thread; lambda > 0 scales the maxima
+  // once per block.  FP64 operations are scarce on this GPU.
+  const double qs = q * shift;
   double mx = -INFINITY, dl = 0.0;
   long long bad = 0;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
@@ -173,23 +177,23 @@ __global__ void k_dual_update(const void* __restrict__ t, const float* __restric
     if (LOG) {
       const float2 v = reinterpret_cast<const float2*>(t)[i];
       lt = (v.y > 0.f && isfinite(v.x) && isfinite(v.y))
-               ? ((double)v.x + log2((double)v.y)) * 0.6931471805599453 + shift
+               ? ((double)v.x + log2((double)v.y)) * 0.6931471805599453
                : (double)NAN;
     } else {
       const float ti = reinterpret_cast<const float*>(t)[i];
-      lt = (ti > 0.f && isfinite(ti) ? log_f32(ti) : log((double)ti)) + shift;
+      lt = ti > 0.f && isfinite(ti) ? log_f32(ti) : log((double)ti);
     }
-    const double v = ref == 0 ? -q * lt : q * (log_f32(base[i]) - lt);
-    if (delta_out >= 0) dl = fmax(dl, fabs(lam * (v - pot[i])));
+    const double v = ref == 0 ? fma(-q, lt, -qs) : fma(q, log_f32(base[i]) - lt, -qs);
+    if (delta_out >= 0) dl = fmax(dl, fabs(v - pot[i]));
     pot[i] = v;
-    if (isfinite(v)) mx = fmax(mx, lam * v);
+    if (isfinite(v)) mx = fmax(mx, v);
     else bad++;
   }
   mx = block_max(mx, sh);
-  if (threadIdx.x == 0) atomicMax(&flags[max_out], dbl_to_ordered(mx));
+  if (threadIdx.x == 0) atomicMax(&flags[max_out], dbl_to_ordered(lam * mx));
   if (delta_out >= 0) {
     dl = block_max(dl, sh);
-    if (threadIdx.x == 0) atomicMax(&flags[delta_out], dbl_to_ordered(dl));
+    if (threadIdx.x == 0) atomicMax(&flags[delta_out], dbl_to_ordered(lam * dl));
   }
   if (bad) flag_add(&flags[FLAG_NONFINITE_DUAL], bad);
 }

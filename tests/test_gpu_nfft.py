@@ -193,3 +193,18 @@ def test_sinkhorn_divergence_nfft(uotk):
     assert np.allclose(parts, rparts, rtol=1e-4, atol=0)
     kappa = sum(abs(p) for p in rparts) / abs(rsd)
     assert abs(sd - rsd) <= 1e-4 * kappa * abs(rsd)
+
+
+def test_sinkhorn_nfft_vs_direct_at_scale(uotk):
+    """The scale workload itself (gmm3, n = m = 2^20): the NFFT solve against the
+    GPU direct solve after 10 sweeps from the same start, in the paper's dual
+    residual (Table Tab:Accuracy_analysis2), at the NFFT bar 1e-4.  (A full FP64
+    oracle at 2^20 is out of reach of host cores; the direct form is held to the
+    oracle at 1e-6 elsewhere.)"""
+    W = inputs.gmm3(seed=2000)
+    args = (dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho)
+    bn, gn, _, vn, _ = uotk.uot_sinkhorn(*args, max_sweeps=10, method="nfft")
+    bd, gd, _, vd, _ = uotk.uot_sinkhorn(*args, max_sweeps=10, method="direct")
+    res = residual(bn.cpu().numpy(), gn.cpu().numpy(), bd.cpu().numpy(), gd.cpu().numpy())
+    assert res <= 1e-4, res
+    assert abs(vn - vd) <= 1e-4 * abs(vd), (vn, vd)
