@@ -142,12 +142,14 @@ __device__ __forceinline__ float ex2_approx(float x) {
 // and |r| <= ln2/2 taken in FP64, expf(r) in FP32, scaled by 2^k.  The result
 // has FP32 relative accuracy whatever |a| (converting a itself to FP32 would
 // cost |a| ulps).  Underflows to 0 below 2^-149.
+// k is taken in FP32 (an off-by-one k next to a half-integer only widens the
+// range of r a little) and r = a - k ln2 in one FP64 FMA: ln2's FP64 rounding
+// costs |k| 2^-53 < 1e-14 for |k| <= 160, far below FP32 resolution.
 __device__ __forceinline__ float exp_shifted(double a) {
-  const double k = rint(a * 1.4426950408889634);
-  if (k < -160.0) return 0.f;
-  const double r = fma(-k, 0.6931471805599453, a);
-  const double r2 = fma(-k, 2.3190468138462996e-17, r);
-  return ldexpf(expf((float)r2), (int)k);
+  const float k = rintf((float)a * 1.44269504f);
+  if (k < -160.f) return 0.f;
+  const float r = (float)fma(-(double)k, 0.6931471805599453, a);
+  return ldexpf(expf(r), (int)k);
 }
 
 // log(t) of a positive FP32 value in FP64: t = f 2^e with f in [0.5, 1),
