@@ -17,6 +17,16 @@ struct Engine {
   // All arrays are in internal order.
   virtual uotk_status half(cudaStream_t s, int side, const float* base, const double* pot,
                            double lam, const long long* shift_slot, float* out) = 0;
+  // half() followed by the dual half-step `du` of its targets, fused into the
+  // summation's last kernel; only called when fuses_dual() is true (otherwise
+  // the solver runs half() and its own dual-update kernel).
+  virtual bool fuses_dual() const { return false; }
+  virtual uotk_status half_dual(cudaStream_t s, int side, const float* base, const double* pot,
+                                double lam, const long long* shift_slot, float* out,
+                                const DualUpdate& du) {
+    (void)s; (void)side; (void)base; (void)pot; (void)lam; (void)shift_slot; (void)out; (void)du;
+    return UOTK_ERR_UNSUPPORTED;
+  }
   // Log-domain half step (the direct FP32 form only): out[i] = {M_i, S_i} with
   //   log t_i = ln2 (M_i + log2 S_i) + shift,
   // t_i the sum of half() (same base, pot, lam and shift slot), evaluated as a

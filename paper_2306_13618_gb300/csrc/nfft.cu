@@ -139,6 +139,22 @@ struct NfftEngine : Engine {
       UOTK_TRY(nfft_near(ctx, s, P, src, pot ? W.wts : base, tgt, W, out));
     return UOTK_OK;
   }
+  // Gaussian kernel: the gather is the half-step's last kernel and takes the
+  // dual update (the non-smooth kernels add their near field after it).
+  bool fuses_dual() const override {
+    return P.kernel == UOTK_KERNEL_GAUSS && X.n > 0 && Y.n > 0;
+  }
+  uotk_status half_dual(cudaStream_t s, int side, const float* base, const double* pot,
+                        double lam, const long long* shift_slot, float* out,
+                        const DualUpdate& du) override {
+    if (!fuses_dual()) return UOTK_ERR_INTERNAL;
+    const NfftPoints& src = side == 0 ? Y : X;
+    const NfftPoints& tgt = side == 0 ? X : Y;
+    SpreadWeights w{base, pot, lam, shift_slot};
+    UOTK_TRY(nfft_spread(ctx, s, P, src, w, W, W.grid));
+    UOTK_TRY(nfft_convolve(ctx, s, P, W, W.grid, W.grid));
+    return nfft_gather(ctx, s, P, tgt, W.grid, out, &du);
+  }
   uotk_status plain(cudaStream_t s, int src, int tgt, const float* w, float* out) override {
     SpreadWeights sw{w, nullptr, 0.0, nullptr};
     const NfftPoints& S = src == 0 ? X : Y;

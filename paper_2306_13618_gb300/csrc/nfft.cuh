@@ -118,8 +118,10 @@ uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
                         const SpreadWeights& w, NfftWork& W, float* grid_out);
 uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W,
                           const float* grid_in, float* grid_out);
+// du != NULL: the dual half-step of each target follows its sum in the same
+// kernel (t still written to out_sorted).
 uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
-                        const float* grid, float* out_sorted);
+                        const float* grid, float* out_sorted, const DualUpdate* du = nullptr);
 
 // Non-smooth kernels (nfft_reg.cu): fill W.full with b_k / prod_t (n phihat(k_t))^2,
 // b_k the DFT of the regularised kernel K_R sampled on I_N^d (FP64 on the

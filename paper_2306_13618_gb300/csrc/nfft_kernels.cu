@@ -723,13 +723,15 @@ __global__ void __launch_bounds__(FFT_THREADS)
 }
 
 // ---------------------------------------------------------------- gather ----
-template <int M>
+// DUAL: the dual half-step `du` of each target follows its sum in the same
+// kernel (the arithmetic of k_dual_update<false>; t is still written to out).
+template <int M, bool DUAL>
 __global__ void __launch_bounds__(256)
     k_gather(const float* __restrict__ win, const int* __restrict__ ckey,
              const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
              const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
              int tiles1, const float* __restrict__ grid, float* __restrict__ out,
-             long long* __restrict__ flags) {
+             long long* __restrict__ flags, DualUpdate du) {
   using G = Geo<M>;
   constexpr int W2 = G::W2, E = G::E, E2 = G::E2, E3 = G::E3, WS = G::WS;
   constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
@@ -742,6 +744,10 @@ __global__ void __launch_bounds__(256)
   float* blk = smem;
   float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
+  if (DUAL && u == 0 && threadIdx.x == 0) {
+    flags[du.reset_slot] = ORDERED_NEG_INF;
+    if (du.reset_delta >= 0) flags[du.reset_delta] = ORDERED_NEG_INF;
+  }
   if (u >= *num_units) return;
   const int b0 = unit_begin[u], cnt = unit_count[u];
   const int nchunks = (cnt + CH - 1) / CH;
@@ -752,6 +758,29 @@ __global__ void __launch_bounds__(256)
       stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * CH,
                      min(CH, cnt - k * CH));
   }
+  // Dual half-step state.  A warp parks the sum of its k-th target in lane
+  // k mod 32 and updates 32 targets at once with every lane active: an FP64
+  // instruction costs the FP64 pipe a whole warp's issue whatever its mask,
+  // and FP64 throughput is scarce on this GPU.
+  const double qs = DUAL ? du.q * ordered_to_dbl(flags[du.shift_in]) : 0.0;
+  double dmx = -INFINITY, ddl = 0.0;
+  long long dbad = 0;
+  float dt = 0.f;  // parked sum of this lane
+  int di = -1;     // its target (-1: none)
+  int dn = 0;      // lane that parks the next sum (warp-uniform)
+  auto dual_flush = [&]() {
+    if (di >= 0) {
+      const double lt = dt > 0.f && isfinite(dt) ? log_f32(dt) : log((double)dt);
+      const double v = du.ref == 0 ? fma(-du.q, lt, -qs)
+                                   : fma(du.q, log_f32(du.base[di]) - lt, -qs);
+      if (du.delta_out >= 0) ddl = fmax(ddl, fabs(v - du.pot[di]));
+      du.pot[di] = v;
+      if (isfinite(v)) dmx = fmax(dmx, v);
+      else ++dbad;
+    }
+    di = -1;
+    dn = 0;
+  };
   int tx0, ty0, tz0;
   tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   for (int i = threadIdx.x; i < E3; i += blockDim.x) {
@@ -824,13 +853,42 @@ __global__ void __launch_bounds__(256)
           }
         }
       }
-      acc = warp_sum(acc);
+      acc = warp_sum(acc);  // every lane holds the sum
       if (lane == 0) out[q0 + p] = acc;
+      if (DUAL) {
+        if (lane == dn) {
+          dt = acc;
+          di = q0 + p;
+        }
+        if (++dn == 32) dual_flush();
+      }
     }
     __syncthreads();
     if (threadIdx.x == 0 && k + STAGES < nchunks)
       stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, nullptr,
                      b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
+  }
+  if (DUAL) {
+    dual_flush();
+    // block maxima and count: warp shuffles, then one slot per warp
+    dmx = warp_max(dmx);
+    ddl = warp_max(ddl);
+    dbad = warp_sum(dbad);
+    __shared__ double dsh[2][8];
+    if (lane == 0) {
+      dsh[0][warp] = dmx;
+      dsh[1][warp] = ddl;
+      if (dbad) flag_add(&flags[FLAG_NONFINITE_DUAL], dbad);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < nwarps; ++w) {
+        dmx = fmax(dmx, dsh[0][w]);
+        ddl = fmax(ddl, dsh[1][w]);
+      }
+      atomicMax(&flags[du.max_out], dbl_to_ordered(du.lam * dmx));
+      if (du.delta_out >= 0) atomicMax(&flags[du.delta_out], dbl_to_ordered(du.lam * ddl));
+    }
   }
 }
 
@@ -858,12 +916,14 @@ uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
 
 template <int M>
 uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
-                          const NfftPoints& S, const float* grid, float* out) {
+                          const NfftPoints& S, const float* grid, float* out,
+                          const DualUpdate* du) {
   const size_t smem = unit_smem<M>();
-  UOTK_CUDA(ctx, smem_attr(s, k_gather<M>, smem));
-  k_gather<M><<<S.max_units, 256, smem, s>>>(S.win, S.ckey, S.unit_tile, S.unit_begin,
-                                             S.unit_count, S.num_units, P.n, P.tiles1, grid, out,
-                                             ctx->dflags);
+  auto kern = du ? k_gather<M, true> : k_gather<M, false>;
+  UOTK_CUDA(ctx, smem_attr(s, kern, smem));
+  kern<<<S.max_units, 256, smem, s>>>(S.win, S.ckey, S.unit_tile, S.unit_begin, S.unit_count,
+                                      S.num_units, P.n, P.tiles1, grid, out, ctx->dflags,
+                                      du ? *du : DualUpdate{});
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -890,8 +950,9 @@ static uotk_status spread_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams&
 }
 
 static uotk_status gather_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
-                                const NfftPoints& S, const float* grid, float* out) {
-#define UOTK_GATHER_CALL(M) launch_gather<M>(ctx, s, P, S, grid, out)
+                                const NfftPoints& S, const float* grid, float* out,
+                                const DualUpdate* du) {
+#define UOTK_GATHER_CALL(M) launch_gather<M>(ctx, s, P, S, grid, out, du)
   UOTK_M_SWITCH(P.m, UOTK_GATHER_CALL)
 #undef UOTK_GATHER_CALL
 }
@@ -954,10 +1015,10 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
 }
 
 uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
-                        const float* grid, float* out_sorted) {
+                        const float* grid, float* out_sorted, const DualUpdate* du) {
   if (S.n == 0) return UOTK_OK;
   UOTK_PROF(ctx, s, "gather");
-  return gather_units(ctx, s, P, S, grid, out_sorted);
+  return gather_units(ctx, s, P, S, grid, out_sorted, du);
 }
 
 size_t nfft_work_bytes(const NfftParams& P, int64_t max_points) {

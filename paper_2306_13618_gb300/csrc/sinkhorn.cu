@@ -318,8 +318,21 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
   // One sweep: the beta half-step (sum over Y into X, update beta), then the
   // gamma half-step (sum over X into Y, update gamma).  The flag slots
   // alternate with the sweep's parity (see k_dual_update).
+  const bool fuse = !log_domain && E->fuses_dual();
   auto sweep = [&](int sw) -> uotk_status {
     const int cur = sw & 1, nxt = cur ^ 1;
+    if (fuse) {
+      // the same updates, slots and counters as the two k_dual_update launches below
+      const DualUpdate ub{a, B.beta, q1, lam, ref, FLAG_MAX_G0 + cur, FLAG_MAX_B0 + cur,
+                          FLAG_MAX_G0 + nxt, track ? FLAG_DELTA0 + cur : -1,
+                          track ? FLAG_DELTA0 + nxt : -1};
+      UOTK_TRY(E->half_dual(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur,
+                            B.tx, ub));
+      const DualUpdate ug{b, B.gamma, q2, lam, ref, FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt,
+                          FLAG_MAX_B0 + nxt, track ? FLAG_DELTA0 + cur : -1, -1};
+      return E->half_dual(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur,
+                          B.ty, ug);
+    }
     if (log_domain)
       UOTK_TRY(E->half_log(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.lx));
     else

@@ -62,6 +62,20 @@ enum FlagSlot {
 
 uotk_status set_error(uotk_ctx* ctx, uotk_status st, const char* fmt, ...);
 
+// One dual half-step of Alg. 1 / Alg. 2 on the targets of a kernel sum t:
+//   pot_i <- -q (log t_i + shift)                 (ref 0)
+//   pot_i <- q (log base_i - log t_i - shift)     (ref 1),
+// shift read from flags[shift_in]; max lam*pot -> flags[max_out] (ordered
+// int64); when delta_out >= 0 also max lam*|change| -> flags[delta_out]; the
+// slots reset_slot / reset_delta (>= 0) are set to -inf for the next half-step;
+// non-finite results counted in FLAG_NONFINITE_DUAL.  Internal point order.
+struct DualUpdate {
+  const float* base;  // ref 1: weights of the targets; unused for ref 0
+  double* pot;        // the targets' dual potential, read (delta) and written
+  double q, lam;
+  int ref, shift_in, max_out, reset_slot, delta_out, reset_delta;
+};
+
 // Grow the workspace to `bytes` (synchronises the device when it reallocates).
 uotk_status ws_reserve(uotk_ctx* ctx, size_t bytes);
 

@@ -175,6 +175,31 @@ def test_sinkhorn_nfft_vs_oracle(uotk):
     assert abs(value - v) <= 1e-4 * abs(v), (value, v)
 
 
+@pytest.mark.parametrize("ref", ["product", "counting"])
+def test_sinkhorn_nfft_tracking_warm_start(uotk, ref):
+    """Alg. 2 with the convergence test on, from a warm start, with either
+    reference measure: every dual update of the NFFT form (done inside its
+    gather kernel) against the FP64 Alg. 1 run for the sweeps the GPU took."""
+    W = inputs.gmm3(seed=2004, n=2000, m=1500)
+    r = 0 if ref == "product" else 1
+    g0 = inputs.rng(2005).uniform(-0.02, 0.02, W.m)
+    beta, gamma, sweeps, value, conv = uotk.uot_sinkhorn(
+        dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho, max_sweeps=1000, tol=1e-5,
+        ref=ref, gamma0=torch.from_numpy(g0), method="nfft")
+    assert conv and 10 <= sweeps < 1000 and sweeps % 10 == 0, (conv, sweeps)
+    X, Y, A, B = f64(W.x), f64(W.y), f64(W.a), f64(W.b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=sweeps, ref=r, gamma0=g0)
+    res = residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg)
+    assert res <= 1e-4, res
+    v = oracle.dual_value(X, A, Y, B, W.eps, W.rho, W.rho, rb, rg, ref=r)
+    assert abs(value - v) <= 1e-4 * abs(v), (value, v)
+    # where the GPU stopped, the oracle's last sweep changes lambda * duals by
+    # about tol as well (slack 10x for the NFFT's own error)
+    pb, pg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=sweeps - 1, ref=r, gamma0=g0)
+    change = max(np.max(np.abs(rb - pb)), np.max(np.abs(rg - pg))) / W.eps
+    assert change < 1e-4, change
+
+
 def test_mmd2_nfft(uotk):
     W = inputs.gmm3(seed=2002, n=3000, m=2500)
     v, parts = uotk.mmd2(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.ell, method="nfft")
