@@ -102,17 +102,23 @@ __device__ __forceinline__ void load_vec(const float* p, float* r) {
 // thread (RPT | 2m), thread (kz, ky < 2m/RPT, half) of 8m^2/RPT threads owns the
 // row halves (kz, ky + k 2m/RPT), k < RPT, which share the phi_x half it loads
 // for every point.
-template <int M, int RPT = 1>
+// POT: the weights are the half-step's w = base e^{lam pot - shift}, formed here
+// when a chunk lands (pw; wts unused); else they are staged from wts.
+template <int M, int RPT = 1, bool POT = false>
 __global__ void __launch_bounds__(8 * M * M / RPT)
     k_spread(const float* __restrict__ win, const int* __restrict__ ckey,
              const float* __restrict__ wts, const int* __restrict__ unit_tile,
              const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
              const int* __restrict__ num_units, int n, int tiles1, float* __restrict__ grid,
-             long long* __restrict__ flags) {
+             long long* __restrict__ flags, SpreadWeights pw) {
   using G = Geo<M>;
   constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M / RPT;
   constexpr int YR = W2 / RPT;  // rows of ky per thread group
   static_assert(W2 % RPT == 0, "rows per thread divide 2m");
+  // POT: thread WT0 + t forms the weight of point t of a chunk; warp 0 is left
+  // to list the cell runs when the CTA has a warp to spare
+  constexpr int WT0 = NT >= CH + 32 ? 32 : 0;
+  static_assert(!POT || NT >= CH + WT0, "one weight thread per chunk point");
   constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
@@ -128,8 +134,21 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
-      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, wts, b0 + k * CH,
-                     min(CH, cnt - k * CH));
+      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, POT ? nullptr : wts,
+                     b0 + k * CH, min(CH, cnt - k * CH));
+  }
+  // POT: pot and base of the next chunk's point t = threadIdx.x - WT0 are
+  // loaded a chunk ahead into registers; whole warps do the FP64 work (FP64
+  // is scarce on this GPU and a partial warp costs the pipe a whole one).
+  const int wt = (int)threadIdx.x - WT0;
+  double ppot = 0.0, shift = 0.0;
+  float pbase = 1.f;
+  if (POT) {
+    shift = ordered_to_dbl(*pw.shift_slot);
+    if (wt >= 0 && wt < min(CH, cnt)) {
+      ppot = pw.pot[b0 + wt];
+      if (pw.base) pbase = pw.base[b0 + wt];
+    }
   }
   for (int i = threadIdx.x; i < E3; i += NT) blk[i] = 0.f;
   __syncthreads();  // barriers initialised and block zeroed before anyone waits or adds
@@ -146,9 +165,23 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
     const float* swt = sw + CH * WS + CH + 4 + off;
     // Fold each point's weight into its phi_z row, and list where each cell's
     // run of points starts (points are sorted by cell).
-    for (int i = threadIdx.x; i < cn * W2; i += NT) {
-      const int q = i / W2;
-      sw[q * WS + ZO + (i - q * W2)] *= swt[q];
+    if (POT) {
+      if (wt >= 0 && wt < cn) {
+        const float w = pbase * exp_shifted(pw.lam * ppot - shift);
+        float* zr = sw + wt * WS + ZO;
+#pragma unroll
+        for (int j = 0; j < W2; ++j) zr[j] *= w;
+      }
+      const int cn1 = k + 1 < nchunks ? min(CH, cnt - (k + 1) * CH) : 0;
+      if (wt >= 0 && wt < cn1) {
+        ppot = pw.pot[q0 + CH + wt];
+        if (pw.base) pbase = pw.base[q0 + CH + wt];
+      }
+    } else {
+      for (int i = threadIdx.x; i < cn * W2; i += NT) {
+        const int q = i / W2;
+        sw[q * WS + ZO + (i - q * W2)] *= swt[q];
+      }
     }
     if (threadIdx.x < 32) {
       int base = 0;
@@ -238,8 +271,9 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
       __syncthreads();
     }
     if (threadIdx.x == 0 && k + STAGES < nchunks)
-      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, wts,
-                     b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
+      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey,
+                     POT ? nullptr : wts, b0 + (k + STAGES) * CH,
+                     min(CH, cnt - (k + STAGES) * CH));
   }
   __syncthreads();
   for (int i = threadIdx.x; i < E3; i += NT) {
@@ -809,7 +843,10 @@ __global__ void __launch_bounds__(256)
     const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), koff = q0 & 3;
     const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
     const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + koff;
-    for (int p = warp; p < cn; p += nwarps) {
+    // each warp takes a contiguous run of the chunk's targets: neighbours in
+    // cell order share a footprint more often than every nwarps-th target
+    const int per = (cn + nwarps - 1) / nwarps, pend = min(cn, (warp + 1) * per);
+    for (int p = warp * per; p < pend; ++p) {
       const int key = skey[p];
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
       const float* wq = sw + p * WS;
@@ -898,18 +935,32 @@ size_t unit_smem() {
   return sizeof(float) * (G::E3P + STAGES * G::STAGE_F);
 }
 
+// two rows per thread: 94.0 ms per 200-sweep gmm3 solve at m = 6, against
+// 109.3 ms with one and 104.4 ms with four (72-thread CTAs hide too little)
+constexpr int SPREAD_RPT = 2;
+
+// Whether the spread at cut-off m forms the half-step weights itself (one
+// weight thread per chunk point).
+constexpr bool spread_forms_weights(int m) { return 8 * m * m / SPREAD_RPT >= CH; }
+
+// pw != NULL: the weights w = base e^{lam pot - shift} are formed in the
+// kernel (requires spread_forms_weights(M)); else staged from wts.
 template <int M>
 uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
-                          const NfftPoints& S, const float* wts, float* grid) {
+                          const NfftPoints& S, const float* wts, const SpreadWeights* pw,
+                          float* grid) {
   const size_t smem = unit_smem<M>();
-  // two rows per thread: 94.0 ms per 200-sweep gmm3 solve at m = 6, against
-  // 109.3 ms with one and 104.4 ms with four (72-thread CTAs hide too little)
-  constexpr int RPT = 2;
-  UOTK_CUDA(ctx, smem_attr(s, k_spread<M, RPT>, smem));
-  k_spread<M, RPT><<<S.max_units, 8 * M * M / RPT, smem, s>>>(S.win, S.ckey, wts, S.unit_tile,
-                                                              S.unit_begin, S.unit_count,
-                                                              S.num_units, P.n, P.tiles1, grid,
-                                                              ctx->dflags);
+  constexpr int RPT = SPREAD_RPT, NT = 8 * M * M / RPT;
+  auto kern = k_spread<M, RPT, false>;
+  if constexpr (spread_forms_weights(M)) {
+    if (pw) kern = k_spread<M, RPT, true>;
+  } else {
+    if (pw) return set_error(ctx, UOTK_ERR_INTERNAL, "spread: weights not formed at m = %d", M);
+  }
+  UOTK_CUDA(ctx, smem_attr(s, kern, smem));
+  kern<<<S.max_units, NT, smem, s>>>(S.win, S.ckey, wts, S.unit_tile, S.unit_begin, S.unit_count,
+                                     S.num_units, P.n, P.tiles1, grid, ctx->dflags,
+                                     pw ? *pw : SpreadWeights{});
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -943,8 +994,9 @@ uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
   }
 
 static uotk_status spread_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
-                                const NfftPoints& S, const float* wts, float* grid) {
-#define UOTK_SPREAD_CALL(M) launch_spread<M>(ctx, s, P, S, wts, grid)
+                                const NfftPoints& S, const float* wts, const SpreadWeights* pw,
+                                float* grid) {
+#define UOTK_SPREAD_CALL(M) launch_spread<M>(ctx, s, P, S, wts, pw, grid)
   UOTK_M_SWITCH(P.m, UOTK_SPREAD_CALL)
 #undef UOTK_SPREAD_CALL
 }
@@ -963,6 +1015,12 @@ uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
   UOTK_CUDA(ctx, cudaMemsetAsync(grid_out, 0, sizeof(float) * total, s));
   if (S.n == 0) return UOTK_OK;
   const float* wts = w.base;
+  // Gaussian kernel: the spread forms the weights as its chunks land (the
+  // non-smooth kernels' near field reads them from W.wts)
+  if (w.pot && P.kernel == UOTK_KERNEL_GAUSS && spread_forms_weights(P.m)) {
+    UOTK_PROF(ctx, s, "spread");
+    return spread_units(ctx, s, P, S, nullptr, &w, grid_out);
+  }
   if (w.pot) {
     UOTK_PROF(ctx, s, "weights");
     k_point_weights<<<grid_for(ctx, S.n + 4, 256, 4), 256, 0, s>>>(w.base, w.pot, w.lam,
@@ -971,7 +1029,7 @@ uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
     wts = W.wts;
   }
   UOTK_PROF(ctx, s, "spread");
-  return spread_units(ctx, s, P, S, wts, grid_out);
+  return spread_units(ctx, s, P, S, wts, nullptr, grid_out);
 }
 
 uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W,
