@@ -16,7 +16,7 @@ namespace uotk {
 constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit granularity)
 constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
 constexpr int NFFT_MAX_M = 8;
-constexpr int NFFT_CHUNK = 64;          // points per bulk-copied staging chunk
+constexpr int NFFT_CHUNK = 64;          // default points per bulk-copied staging chunk
 constexpr int NFFT_NEAR_CHUNK = 1024;   // targets per near-field work item
 // Window table row of one point (floats): phi_x split in two halves of m
 // values, then phi_y (2m), then phi_z (2m); every block padded to a 16-byte

@@ -5,19 +5,24 @@
 // Work units.  Points are sorted by grid cell, cells tile by tile (8^3 cells
 // per tile).  A unit is (tile, up to NFFT_UNIT_POINTS points); its CTA owns the
 // E^3 block of grid nodes the tile's windows reach (E = 8 + 2m - 1).  Chunks
-// of NFFT_CHUNK points -- window table rows, packed cells, weights -- are
-// staged in shared memory by double-buffered 1-D bulk copies (TMA) completing
-// on mbarriers, so the copy of chunk k+1 overlaps the arithmetic of chunk k.
-// Spread.  Thread (row (kz, ky), half) owns the m nodes kx in [half m, half m
-// + m) of footprint row (kz, ky).  The points of one cell share the footprint:
-// their rank-1 window products w phi_z phi_y phi_x accumulate in registers and
-// are added to the shared block once per cell, a barrier separating the
-// additions of consecutive cells (no shared-memory atomics).  The finished
-// block is added into the grid with global reductions, skipping zeros.
+// of points (SPREAD_CH for the spread, GATHER_CH for the gather) -- window
+// table rows, packed cells, weights -- are staged in shared memory by
+// double-buffered 1-D bulk copies (TMA) completing on mbarriers, so the copy of
+// chunk k+1 overlaps the arithmetic of chunk k.
+// Spread.  Thread (kz, ky, half) owns the m nodes kx in [half m, half m + m)
+// of two footprint rows, (kz, ky) and (kz, ky + m).  The points of one cell
+// share the footprint: their rank-1 window products w phi_z phi_y phi_x
+// accumulate in registers (packed FP32x2 over node pairs) and are added to the
+// shared block once per cell, a barrier separating the additions of
+// consecutive cells (no shared-memory atomics).  In a Sinkhorn half-step the
+// spread forms the weights w itself.  The finished block is added into the
+// grid with global reductions, skipping zeros.
 // Gather.  The CTA stages the E^3 grid block around its tile; each warp
-// evaluates one target at a time: lanes split the (2m)^2 (y, x) pairs of the
-// footprint, each lane contracting its z-columns with phi_z; consecutive
-// targets of one cell reuse the footprint held in registers.
+// evaluates a contiguous run of a chunk's targets, one at a time: lanes split
+// the (2m)^2 (y, x) pairs of the footprint, each lane contracting its
+// z-columns with phi_z; consecutive targets of one cell reuse the footprint
+// held in registers.  In a Sinkhorn half-step the gather also runs the dual
+// update of its targets.
 #include <math.h>
 
 #include "nfft.cuh"
@@ -29,7 +34,7 @@ namespace {
 constexpr int CH = NFFT_CHUNK;
 constexpr int STAGES = 2;
 
-template <int M>
+template <int M, int C = CH>
 struct Geo {
   static constexpr int W2 = 2 * M;
   static constexpr int E = NFFT_TILE + 2 * M - 1;
@@ -37,24 +42,24 @@ struct Geo {
   static constexpr int E3 = E2 * E;
   static constexpr int E3P = (E3 + 3) & ~3;           // block floats, 16-byte multiple
   static constexpr int WS = nfft_win_stride(M);      // floats per window-table row
-  static constexpr int STAGE_F = CH * WS + 2 * (CH + 4);  // floats per staging buffer
+  static constexpr int STAGE_F = C * WS + 2 * (C + 4);  // floats per staging buffer (C points)
 };
 
 // Issue the bulk copies of chunk `k` of a unit into staging buffer `st`:
 // the window rows (16-byte aligned by construction), and the packed cells and
 // weights from the 16-byte-aligned element at or below the chunk start, whose
 // offset `off` (0..3) the consumer adds back.
-template <int M>
+template <int M, int C = CH>
 __device__ __forceinline__ void stage_chunk(float* st, unsigned long long* bar, const float* win,
                                             const int* ckey, const float* wts, int q0, int cn) {
-  using G = Geo<M>;
+  using G = Geo<M, C>;
   const int off = q0 & 3;
   const unsigned wbytes = (unsigned)(cn * G::WS * 4);
   const unsigned kbytes = (unsigned)(((cn + off + 3) & ~3) * 4);
   mbar_expect(bar, wbytes + (wts ? 2 * kbytes : kbytes));
   bulk_copy(st, win + (size_t)q0 * G::WS, wbytes, bar);
-  bulk_copy(st + CH * G::WS, ckey + (q0 - off), kbytes, bar);
-  if (wts) bulk_copy(st + CH * G::WS + CH + 4, wts + (q0 - off), kbytes, bar);
+  bulk_copy(st + C * G::WS, ckey + (q0 - off), kbytes, bar);
+  if (wts) bulk_copy(st + C * G::WS + C + 4, wts + (q0 - off), kbytes, bar);
 }
 
 // Bounded wait for a staging buffer; on time-out every thread learns it, the
@@ -104,38 +109,38 @@ __device__ __forceinline__ void load_vec(const float* p, float* r) {
 // for every point.
 // POT: the weights are the half-step's w = base e^{lam pot - shift}, formed here
 // when a chunk lands (pw; wts unused); else they are staged from wts.
-template <int M, int RPT = 1, bool POT = false>
+template <int M, int RPT = 1, bool POT = false, int C = CH>
 __global__ void __launch_bounds__(8 * M * M / RPT)
     k_spread(const float* __restrict__ win, const int* __restrict__ ckey,
              const float* __restrict__ wts, const int* __restrict__ unit_tile,
              const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
              const int* __restrict__ num_units, int n, int tiles1, float* __restrict__ grid,
              long long* __restrict__ flags, SpreadWeights pw) {
-  using G = Geo<M>;
+  using G = Geo<M, C>;
   constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M / RPT;
   constexpr int YR = W2 / RPT;  // rows of ky per thread group
   static_assert(W2 % RPT == 0, "rows per thread divide 2m");
   // POT: thread WT0 + t forms the weight of point t of a chunk; warp 0 is left
   // to list the cell runs when the CTA has a warp to spare
-  constexpr int WT0 = NT >= CH + 32 ? 32 : 0;
-  static_assert(!POT || NT >= CH + WT0, "one weight thread per chunk point");
+  constexpr int WT0 = NT >= C + 32 ? 32 : 0;
+  static_assert(!POT || NT >= C + WT0, "one weight thread per chunk point");
   constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
-  __shared__ int gstart[CH + 1];
+  __shared__ int gstart[C + 1];
   __shared__ int ngroups;
   float* blk = smem;
   float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
   if (u >= *num_units) return;
   const int b0 = unit_begin[u], cnt = unit_count[u];
-  const int nchunks = (cnt + CH - 1) / CH;
+  const int nchunks = (cnt + C - 1) / C;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
-      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, POT ? nullptr : wts,
-                     b0 + k * CH, min(CH, cnt - k * CH));
+      stage_chunk<M, C>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, POT ? nullptr : wts,
+                     b0 + k * C, min(C, cnt - k * C));
   }
   // POT: pot and base of the next chunk's point t = threadIdx.x - WT0 are
   // loaded a chunk ahead into registers; whole warps do the FP64 work (FP64
@@ -145,7 +150,7 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
   float pbase = 1.f;
   if (POT) {
     shift = ordered_to_dbl(*pw.shift_slot);
-    if (wt >= 0 && wt < min(CH, cnt)) {
+    if (wt >= 0 && wt < min(C, cnt)) {
       ppot = pw.pot[b0 + wt];
       if (pw.base) pbase = pw.base[b0 + wt];
     }
@@ -159,10 +164,10 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
   const int lane = threadIdx.x & 31;
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
-    const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), off = q0 & 3;
+    const int q0 = b0 + k * C, cn = min(C, cnt - k * C), off = q0 & 3;
     float* sw = stage0 + (k % STAGES) * G::STAGE_F;
-    const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + off;
-    const float* swt = sw + CH * WS + CH + 4 + off;
+    const int* skey = reinterpret_cast<const int*>(sw + C * WS) + off;
+    const float* swt = sw + C * WS + C + 4 + off;
     // Fold each point's weight into its phi_z row, and list where each cell's
     // run of points starts (points are sorted by cell).
     if (POT) {
@@ -172,10 +177,10 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
 #pragma unroll
         for (int j = 0; j < W2; ++j) zr[j] *= w;
       }
-      const int cn1 = k + 1 < nchunks ? min(CH, cnt - (k + 1) * CH) : 0;
+      const int cn1 = k + 1 < nchunks ? min(C, cnt - (k + 1) * C) : 0;
       if (wt >= 0 && wt < cn1) {
-        ppot = pw.pot[q0 + CH + wt];
-        if (pw.base) pbase = pw.base[q0 + CH + wt];
+        ppot = pw.pot[q0 + C + wt];
+        if (pw.base) pbase = pw.base[q0 + C + wt];
       }
     } else {
       for (int i = threadIdx.x; i < cn * W2; i += NT) {
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
     }
     if (threadIdx.x < 32) {
       int base = 0;
-      for (int h = 0; h < CH; h += 32) {
+      for (int h = 0; h < C; h += 32) {
         const int q = h + lane;
         const bool f = q < cn && (q == 0 || skey[q] != skey[q - 1]);
         const unsigned bal = __ballot_sync(0xffffffffu, f);
@@ -206,18 +211,48 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
 #pragma unroll
           for (int j = 0; j < M; ++j) acc[k][j] = 0.f;
         int q = p0;
-        for (; q + 1 < p1; q += 2) {
-          const float* w0 = sw + q * WS;
-          const float* w1 = w0 + WS;
-          const float z0 = w0[ZO + kz], z1 = w1[ZO + kz];
-          float f0[M], f1[M];
-          load_vec<M>(w0 + half * HP, f0);
-          load_vec<M>(w1 + half * HP, f1);
+        if constexpr (M % 2 == 0) {
+          // node pairs (j, j+1) in packed FP32x2 FMAs (the same IEEE FMAs)
+          unsigned long long acc2[RPT][M / 2];
 #pragma unroll
-          for (int k = 0; k < RPT; ++k) {
-            const float a0 = z0 * w0[YO + ky + k * YR], a1 = z1 * w1[YO + ky + k * YR];
+          for (int k = 0; k < RPT; ++k)
 #pragma unroll
-            for (int j = 0; j < M; ++j) acc[k][j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[k][j]));
+            for (int j = 0; j < M / 2; ++j) acc2[k][j] = 0ull;
+          for (; q + 1 < p1; q += 2) {
+            const float* w0 = sw + q * WS;
+            const float* w1 = w0 + WS;
+            const float z0 = w0[ZO + kz], z1 = w1[ZO + kz];
+            float f0[M], f1[M];
+            load_vec<M>(w0 + half * HP, f0);
+            load_vec<M>(w1 + half * HP, f1);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+              const float a0 = z0 * w0[YO + ky + k * YR], a1 = z1 * w1[YO + ky + k * YR];
+              const unsigned long long A0 = f2_pack(a0, a0), A1 = f2_pack(a1, a1);
+#pragma unroll
+              for (int j = 0; j < M / 2; ++j)
+                acc2[k][j] = f2_fma(A1, f2_pack(f1[2 * j], f1[2 * j + 1]),
+                                    f2_fma(A0, f2_pack(f0[2 * j], f0[2 * j + 1]), acc2[k][j]));
+            }
+          }
+#pragma unroll
+          for (int k = 0; k < RPT; ++k)
+#pragma unroll
+            for (int j = 0; j < M / 2; ++j) f2_unpack(acc2[k][j], acc[k][2 * j], acc[k][2 * j + 1]);
+        } else {
+          for (; q + 1 < p1; q += 2) {
+            const float* w0 = sw + q * WS;
+            const float* w1 = w0 + WS;
+            const float z0 = w0[ZO + kz], z1 = w1[ZO + kz];
+            float f0[M], f1[M];
+            load_vec<M>(w0 + half * HP, f0);
+            load_vec<M>(w1 + half * HP, f1);
+#pragma unroll
+            for (int k = 0; k < RPT; ++k) {
+              const float a0 = z0 * w0[YO + ky + k * YR], a1 = z1 * w1[YO + ky + k * YR];
+#pragma unroll
+              for (int j = 0; j < M; ++j) acc[k][j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[k][j]));
+            }
           }
         }
         if (q < p1) {
@@ -271,9 +306,9 @@ __global__ void __launch_bounds__(8 * M * M / RPT)
       __syncthreads();
     }
     if (threadIdx.x == 0 && k + STAGES < nchunks)
-      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey,
-                     POT ? nullptr : wts, b0 + (k + STAGES) * CH,
-                     min(CH, cnt - (k + STAGES) * CH));
+      stage_chunk<M, C>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey,
+                     POT ? nullptr : wts, b0 + (k + STAGES) * C,
+                     min(C, cnt - (k + STAGES) * C));
   }
   __syncthreads();
   for (int i = threadIdx.x; i < E3; i += NT) {
@@ -759,14 +794,14 @@ __global__ void __launch_bounds__(FFT_THREADS)
 // ---------------------------------------------------------------- gather ----
 // DUAL: the dual half-step `du` of each target follows its sum in the same
 // kernel (the arithmetic of k_dual_update<false>; t is still written to out).
-template <int M, bool DUAL>
+template <int M, bool DUAL, int C = CH>
 __global__ void __launch_bounds__(256)
     k_gather(const float* __restrict__ win, const int* __restrict__ ckey,
              const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
              const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
              int tiles1, const float* __restrict__ grid, float* __restrict__ out,
              long long* __restrict__ flags, DualUpdate du) {
-  using G = Geo<M>;
+  using G = Geo<M, C>;
   constexpr int W2 = G::W2, E = G::E, E2 = G::E2, E3 = G::E3, WS = G::WS;
   constexpr int YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
   constexpr int NIT = (W2 * W2 + 31) / 32;
@@ -784,13 +819,13 @@ __global__ void __launch_bounds__(256)
   }
   if (u >= *num_units) return;
   const int b0 = unit_begin[u], cnt = unit_count[u];
-  const int nchunks = (cnt + CH - 1) / CH;
+  const int nchunks = (cnt + C - 1) / C;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
-      stage_chunk<M>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * CH,
-                     min(CH, cnt - k * CH));
+      stage_chunk<M, C>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * C,
+                     min(C, cnt - k * C));
   }
   // Dual half-step state.  A warp parks the sum of its k-th target in lane
   // k mod 32 and updates 32 targets at once with every lane active: an FP64
@@ -840,9 +875,9 @@ __global__ void __launch_bounds__(256)
   int cached = -1;
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
-    const int q0 = b0 + k * CH, cn = min(CH, cnt - k * CH), koff = q0 & 3;
+    const int q0 = b0 + k * C, cn = min(C, cnt - k * C), koff = q0 & 3;
     const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
-    const int* skey = reinterpret_cast<const int*>(sw + CH * WS) + koff;
+    const int* skey = reinterpret_cast<const int*>(sw + C * WS) + koff;
     // each warp takes a contiguous run of the chunk's targets: neighbours in
     // cell order share a footprint more often than every nwarps-th target
     const int per = (cn + nwarps - 1) / nwarps, pend = min(cn, (warp + 1) * per);
@@ -902,8 +937,8 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
     if (threadIdx.x == 0 && k + STAGES < nchunks)
-      stage_chunk<M>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, nullptr,
-                     b0 + (k + STAGES) * CH, min(CH, cnt - (k + STAGES) * CH));
+      stage_chunk<M, C>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey, nullptr,
+                     b0 + (k + STAGES) * C, min(C, cnt - (k + STAGES) * C));
   }
   if (DUAL) {
     dual_flush();
@@ -929,19 +964,29 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-template <int M>
+template <int M, int C = CH>
 size_t unit_smem() {
-  using G = Geo<M>;
+  using G = Geo<M, C>;
   return sizeof(float) * (G::E3P + STAGES * G::STAGE_F);
 }
 
 // two rows per thread: 94.0 ms per 200-sweep gmm3 solve at m = 6, against
 // 109.3 ms with one and 104.4 ms with four (72-thread CTAs hide too little)
 constexpr int SPREAD_RPT = 2;
+// Points per staging chunk of the spread.  At m = 6, 32-point chunks fit five
+// CTAs per SM (38 KB each) but ran 108.1 ms per gmm3 solve against 89.8 ms
+// with 64 (four CTAs): each chunk and each cell run cut by a chunk boundary
+// costs a barrier round.  128-point chunks (three CTAs) ran 102.8 ms.
+constexpr int SPREAD_CH = 64;
+// Points per staging chunk of the gather.  Registers hold it to two CTAs per SM
+// whatever the chunk (92 KB each at 192, m = 6), and longer chunks mean fewer
+// barriers and longer runs of targets per warp: per gmm3 solve 111.2 ms with
+// 64, 103.2 with 128, 100.8 with 192.
+constexpr int GATHER_CH = 192;
 
 // Whether the spread at cut-off m forms the half-step weights itself (one
 // weight thread per chunk point).
-constexpr bool spread_forms_weights(int m) { return 8 * m * m / SPREAD_RPT >= CH; }
+constexpr bool spread_forms_weights(int m) { return 8 * m * m / SPREAD_RPT >= SPREAD_CH; }
 
 // pw != NULL: the weights w = base e^{lam pot - shift} are formed in the
 // kernel (requires spread_forms_weights(M)); else staged from wts.
@@ -949,11 +994,11 @@ template <int M>
 uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* wts, const SpreadWeights* pw,
                           float* grid) {
-  const size_t smem = unit_smem<M>();
+  const size_t smem = unit_smem<M, SPREAD_CH>();
   constexpr int RPT = SPREAD_RPT, NT = 8 * M * M / RPT;
-  auto kern = k_spread<M, RPT, false>;
+  auto kern = k_spread<M, RPT, false, SPREAD_CH>;
   if constexpr (spread_forms_weights(M)) {
-    if (pw) kern = k_spread<M, RPT, true>;
+    if (pw) kern = k_spread<M, RPT, true, SPREAD_CH>;
   } else {
     if (pw) return set_error(ctx, UOTK_ERR_INTERNAL, "spread: weights not formed at m = %d", M);
   }
@@ -969,8 +1014,8 @@ template <int M>
 uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* grid, float* out,
                           const DualUpdate* du) {
-  const size_t smem = unit_smem<M>();
-  auto kern = du ? k_gather<M, true> : k_gather<M, false>;
+  const size_t smem = unit_smem<M, GATHER_CH>();
+  auto kern = du ? k_gather<M, true, GATHER_CH> : k_gather<M, false, GATHER_CH>;
   UOTK_CUDA(ctx, smem_attr(s, kern, smem));
   kern<<<S.max_units, 256, smem, s>>>(S.win, S.ckey, S.unit_tile, S.unit_begin, S.unit_count,
                                       S.num_units, P.n, P.tiles1, grid, out, ctx->dflags,
