@@ -792,6 +792,20 @@ __global__ void __launch_bounds__(FFT_THREADS)
 }
 
 // ---------------------------------------------------------------- gather ----
+// Warp sum of four per-lane values at once: lane L returns the total of
+// v[L >> 3].  Two transposed butterfly levels (each lane keeps half of its
+// values and sends the other half) then three plain ones.
+__device__ __forceinline__ float warp_sum4(const float (&v)[4], int lane) {
+  const bool b4 = lane & 16, b3 = lane & 8;
+  const float r0 = (b4 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, b4 ? v[0] : v[2], 16);
+  const float r1 = (b4 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, b4 ? v[1] : v[3], 16);
+  float r = (b3 ? r1 : r0) + __shfl_xor_sync(0xffffffffu, b3 ? r0 : r1, 8);
+  r += __shfl_xor_sync(0xffffffffu, r, 4);
+  r += __shfl_xor_sync(0xffffffffu, r, 2);
+  r += __shfl_xor_sync(0xffffffffu, r, 1);
+  return r;
+}
+
 // DUAL: the dual half-step `du` of each target follows its sum in the same
 // kernel (the arithmetic of k_dual_update<false>; t is still written to out).
 template <int M, bool DUAL, int C = CH>
@@ -827,8 +841,8 @@ __global__ void __launch_bounds__(256)
       stage_chunk<M, C>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * C,
                      min(C, cnt - k * C));
   }
-  // Dual half-step state.  A warp parks the sum of its k-th target in lane
-  // k mod 32 and updates 32 targets at once with every lane active: an FP64
+  // Dual half-step state.  A warp parks the sums of its targets one per lane
+  // and updates 32 targets at once with every lane active: an FP64
   // instruction costs the FP64 pipe a whole warp's issue whatever its mask,
   // and FP64 throughput is scarce on this GPU.
   const double qs = DUAL ? du.q * ordered_to_dbl(flags[du.shift_in]) : 0.0;
@@ -836,7 +850,7 @@ __global__ void __launch_bounds__(256)
   long long dbad = 0;
   float dt = 0.f;  // parked sum of this lane
   int di = -1;     // its target (-1: none)
-  int dn = 0;      // lane that parks the next sum (warp-uniform)
+  int dn = 0;      // group of four targets that parks next (warp-uniform)
   auto dual_flush = [&]() {
     if (di >= 0) {
       const double lt = dt > 0.f && isfinite(dt) ? log_f32(dt) : log((double)dt);
@@ -881,7 +895,8 @@ __global__ void __launch_bounds__(256)
     // each warp takes a contiguous run of the chunk's targets: neighbours in
     // cell order share a footprint more often than every nwarps-th target
     const int per = (cn + nwarps - 1) / nwarps, pend = min(cn, (warp + 1) * per);
-    for (int p = warp * per; p < pend; ++p) {
+    // this lane's part of the sum of target p (the warp adds the 32 parts)
+    auto target_part = [&](int p) -> float {
       const int key = skey[p];
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
       const float* wq = sw + p * WS;
@@ -925,14 +940,25 @@ __global__ void __launch_bounds__(256)
           }
         }
       }
-      acc = warp_sum(acc);  // every lane holds the sum
-      if (lane == 0) out[q0 + p] = acc;
+      return acc;
+    };
+    // Targets in groups of four: each lane keeps its four parts and one
+    // transposed reduction adds them (6 shuffles for four sums instead of 20);
+    // lanes 8j..8j+7 then hold the sum of target p + j.
+    for (int p = warp * per; p < pend; p += 4) {
+      float part[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[j] = p + j < pend ? target_part(p + j) : 0.f;
+      const float tsum = warp_sum4(part, lane);
+      const int t = p + (lane >> 3);
+      if ((lane & 7) == 0 && t < pend) out[q0 + t] = tsum;
       if (DUAL) {
-        if (lane == dn) {
-          dt = acc;
-          di = q0 + p;
+        // group g of eight parks in lanes 8j + g: eight groups fill the warp
+        if ((lane & 7) == dn && t < pend) {
+          dt = tsum;
+          di = q0 + t;
         }
-        if (++dn == 32) dual_flush();
+        if (++dn == 8) dual_flush();
       }
     }
     __syncthreads();
