@@ -200,6 +200,29 @@ def test_sinkhorn_nfft_tracking_warm_start(uotk, ref):
     assert change < 1e-4, change
 
 
+@pytest.mark.parametrize("cutoff", [3, 4, 5, 7, 8])
+def test_sinkhorn_nfft_cutoffs(uotk, cutoff):
+    """Alg. 2 at every other window cut-off: the spread forms the weights with
+    the CTA's threads 0.. (m = 4), threads 32.. (m >= 5), or takes them from a
+    separate kernel (m = 3); the gather runs without its footprint cache at
+    m >= 7.  Against the FP64 Alg. 1 after 30 sweeps, both reference measures.
+    Tolerances follow the window error bound of the cut-off (R8: ~1e-4 at m = 3
+    down to below 1e-7 at m = 7)."""
+    W = inputs.gmm3(seed=2006, n=2000, m=1500)
+    ref = "counting" if cutoff in (4, 8) else "product"
+    r = 0 if ref == "product" else 1
+    beta, gamma, sweeps, value, _ = uotk.uot_sinkhorn(
+        dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho, max_sweeps=30, ref=ref,
+        method="nfft", cutoff=cutoff, target_err=1e-3)
+    X, Y, A, B = f64(W.x), f64(W.y), f64(W.a), f64(W.b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=30, ref=r)
+    res = residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg)
+    tol = 1e-2 if cutoff <= 4 else 1e-3
+    assert sweeps == 30 and res <= tol, (cutoff, res)
+    v = oracle.dual_value(X, A, Y, B, W.eps, W.rho, W.rho, rb, rg, ref=r)
+    assert abs(value - v) <= tol * abs(v), (cutoff, value, v)
+
+
 def test_mmd2_nfft(uotk):
     W = inputs.gmm3(seed=2002, n=3000, m=2500)
     v, parts = uotk.mmd2(dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.ell, method="nfft")
