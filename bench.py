@@ -7,6 +7,9 @@ Alg. 2 with the NFFT fast summation by default; --method direct runs Alg. 1's
 exact form): plan, binning, every sweep (two kernel summations and two FP64 dual
 updates each) and the dual value.  `value` = sweeps processed by all ranks /
 max-over-ranks time.  Inputs are resident in HBM; L2 is flushed between steps.
+The K timed steps run the path a caller gets (the sweep loop replayed from a
+CUDA graph); a second pass of the same K steps, with an event pair around every
+launch, gives the per-stage times and the rooflines.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--method nfft|direct]
   python bench.py --impl reference ...   # the FP64 CPU oracle on this host's cores
