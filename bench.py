@@ -148,7 +148,8 @@ def stage_rooflines(prof, W, sms, peaks, plan, rates):
     direct : MUFU ex2 bound, one ex2 per (source, target) pair;
              peak = measured ex2/clk/SM x SMs x max SM clock.
     spread, gather : FP32 FMA-pipe bound, one FMA per footprint node per point,
-             (2m)^3 nodes; peak = measured FMA/clk/SM x SMs x max SM clock.
+             (2m)^3 nodes; peak = measured FMA/clk/SM x SMs x max SM clock.  Also
+             their memory side (`hbm`): 16 B per point and the n^3 FP32 grid.
     fft    : HBM bound, algorithmic bytes = read + write of the n^3 FP32 grid.
     dual_update : HBM bound, 24 bytes per element (t, base, old and new dual).
     """
@@ -174,6 +175,10 @@ def stage_rooflines(prof, W, sms, peaks, plan, rates):
                      peak=ffma * sms * clk / 1e9,
                      peak_source=f"{ffma:.1f} FP32 FMA/clk/SM (measured) x {sms} SMs x "
                                  f"{clk/1e6:.0f} MHz; {nodes} FMAs per point (m = {plan['cutoff']})")
+            # the memory side, which does not bind: the points (16 B each) and the grid
+            byts = 16 * W.n + 4 * plan["grid"] ** 3
+            r["hbm"] = {"algorithmic_bytes": byts, "achieved_gbs": byts / t / 1e9,
+                        "frac": byts / t / 1e9 / hbm}
         elif name == "fft" and plan:
             byts = 2 * 4 * plan["grid"] ** 3
             r.update(bound="hbm", unit="GB/s", achieved=byts / t / 1e9, peak=hbm,

@@ -60,3 +60,34 @@ def test_reference_arm_two_ranks():
     lines = json_lines(r.stdout)
     assert len(lines) == 1
     check_line(lines[0], 2)
+
+
+def test_stage_rooflines_arithmetic():
+    """The per-stage roofline figures from stage times, against hand arithmetic."""
+    sys.path.insert(0, ROOT)
+    import bench
+
+    class W:
+        n = m = 1 << 20
+
+    prof = {"gather": (400, 100.0), "spread": (400, 90.0), "fft": (1200, 22.0),
+            "direct": (2, 540.0), "bin": (4, 1.0)}
+    peaks = {"hbm_gbs": 6774.0, "sm_max_mhz": 2070.0}
+    plan = {"cutoff": 6, "grid": 128}
+    r = bench.stage_rooflines(prof, W, 152, peaks, plan, (32.0, 123.0))
+    clk = 2070e6
+    t = 100.0e-3 / 400                                   # s per gather launch
+    g = r["gather"]
+    assert g["us_per_launch"] == pytest.approx(t * 1e6)
+    assert g["achieved"] == pytest.approx((1 << 20) * 1728 / t / 1e9)
+    assert g["peak"] == pytest.approx(123.0 * 152 * clk / 1e9)
+    assert g["frac"] == pytest.approx(g["achieved"] / g["peak"])
+    assert g["hbm"]["algorithmic_bytes"] == 16 * (1 << 20) + 4 * 128 ** 3
+    assert g["share"] == pytest.approx(100.0 / 753.0)
+    f = r["fft"]
+    tf = 22.0e-3 / 1200
+    assert f["bound"] == "hbm" and f["achieved"] == pytest.approx(2 * 4 * 128 ** 3 / tf / 1e9)
+    d = r["direct"]
+    assert d["achieved"] == pytest.approx((1 << 40) / (540.0e-3 / 2) / 1e9)
+    assert d["peak"] == pytest.approx(32.0 * 152 * clk / 1e9)
+    assert r["bin"]["achieved"] is None and "frac" not in r["bin"]
