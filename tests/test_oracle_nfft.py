@@ -122,3 +122,29 @@ def test_cell_index_f32_agrees_with_exact_away_from_edges():
     near = np.abs(u - np.round(u)) < 1e-4
     assert np.array_equal(cells[~near], exact[~near])
     assert near.mean() < 1e-3
+
+
+@pytest.mark.parametrize("m", [4, 6, 8])
+def test_footprint_holds_the_window_support(m):
+    """The 2m nodes floor(nu) - m + 1 .. floor(nu) + m per axis hold the whole
+    support |v| <= m/n of the window: the nodes one further out on either side
+    carry phi = 0, except node floor(nu) - m when u sits on a grid node (f = 0),
+    where v = m/n exactly and phi = b/pi, a fraction bm/sinh(bm) of phi(0)
+    (3e-11 at m = 6, sigma = 2)."""
+    n, N = 128, 64
+    g = np.random.default_rng(5)
+    u = np.concatenate([g.uniform(0, 1, 4000), np.arange(n) / n])
+    base = np.floor(n * u)
+    f = n * u - base
+    for off in (-m - 1, m + 1, m + 2):
+        assert np.all(nf.kb_phi(u - (base + off) / n, n, N, m) == 0.0)
+    edge = nf.kb_phi(u - (base - m) / n, n, N, m)
+    assert np.all(edge[f > 0] == 0.0)
+    b = nf.kb_params(n, N)
+    assert np.allclose(edge[f == 0], b / np.pi, rtol=1e-14)
+    ratio = b / np.pi / nf.kb_phi(0.0, n, N, m)
+    assert ratio == pytest.approx(b * m / np.sinh(b * m), rel=1e-12)
+    if m >= 6:
+        assert ratio < 1e-10
+    for off in range(-m + 1, m + 1):
+        assert np.all(np.abs(u - (base + off) / n) <= m / n)
