@@ -1,6 +1,7 @@
-"""bench.py's reference arm on CPU: the FP64 oracle timed through the same
-command line the driver uses, one JSON line with the contract's keys; under
-torch.distributed.run with two ranks, rank 0 alone runs and prints it."""
+"""bench.py's reference arm on CPU: the FP64 oracle timed through
+`bench.py --impl reference`, one JSON line with the benchmark line's keys;
+under torch.distributed.run with two ranks, rank 0 alone runs and prints it.
+Also the arithmetic of the per-stage rooflines."""
 import json
 import os
 import socket
