@@ -148,3 +148,21 @@ def test_footprint_holds_the_window_support(m):
         assert ratio < 1e-10
     for off in range(-m + 1, m + 1):
         assert np.all(np.abs(u - (base + off) / n) <= m / n)
+
+
+def test_gaussian_convolution_is_three_circulants():
+    """For the Gaussian, b_k / prod_t (n phihat(k_t))^2 is a product over the
+    axes, so the grid convolution of Eq. (1724) is one real circulant n x n
+    operator, C[a, i] = sum_k s(k) cos(2 pi k (a - i)/n), applied along each
+    axis: a dense restatement of the oracle's FFT pipeline.  The unpaired
+    frequency -N/2 of I_N contributes a sine part of relative size
+    exp(-pi^2 eps N^2 / (4 h^2)), e^-63 here and e^-64 for the 2^20 workload."""
+    n, N, m, eps, h = 32, 16, 4, 0.1, 1.0
+    g = np.random.default_rng(7).standard_normal((n, n, n))
+    want = nf.convolve_grid(g, N, m, eps, h)
+    k = np.arange(-N // 2, N // 2)
+    s = nf.gauss_coeffs(N, 1, eps, h) / (n * nf.kb_phihat(k, n, N, m)) ** 2
+    a = np.arange(n)
+    C = np.cos(2 * np.pi * np.subtract.outer(a, a)[:, :, None] * k / n) @ s
+    got = np.einsum("ai,bj,ck,ijk->abc", C, C, C, g, optimize=True)
+    assert np.max(np.abs(got - want)) <= 1e-12 * np.max(np.abs(want))
