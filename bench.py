@@ -13,6 +13,18 @@ launch, gives the per-stage times and the rooflines.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--method nfft|direct]
   python bench.py --impl reference ...   # the FP64 CPU oracle on this host's cores
+  python bench.py --case <case> [--n N] [--reps K]   # one library call, for timing/ncu
+
+--case runs one named call at a chosen size (one untimed call, then K timed
+calls) and prints one JSON line with the milliseconds of each:
+  direct      Gaussian kernel sum, direct FP32 form, 5-component mixture (d = 3,
+              eps = 0.02), n = m = N
+  nfft        the same with the NFFT fast summation (grid 128^3)
+  nfft_solve  a 4-sweep NFFT Sinkhorn solve of that mixture (the spread forming
+              the weights, the gather running the dual update), n = m = N
+  nfft_reg    Laplace kernel sum (ell = 1/2), regularised NFFT (grid 256^3, p = 4),
+              points and weights uniform on [0, 1] (d = 3), n = m = N
+  tc          Gaussian kernel sum, d = 64, tensor-core BF16x3 form, n = m = N
 
 Under torchrun each rank runs an independent replica (the path has no exchange
 step: "replicas only"); rank 0 prints one JSON line.
@@ -53,7 +65,55 @@ def parse():
                    help="points per cloud (0: the workload's, 2^20 for gmm3, 262144 for gauss64)")
     p.add_argument("--no-extras", action="store_true", help="skip direct/oracle side measurements")
     p.add_argument("--cpu-seconds", type=float, default=12.0)
+    p.add_argument("--case", default=None,
+                   choices=["direct", "nfft", "nfft_solve", "nfft_reg", "tc"],
+                   help="time one library call at size --n instead of the benchmark")
+    p.add_argument("--reps", type=int, default=2, help="timed calls of --case")
     return p.parse_args()
+
+
+def run_case(args):
+    """One named library call at size --n (default 2^17): one untimed call, then
+    --reps timed calls (CUDA events); one JSON line with the milliseconds."""
+    import numpy as np
+    import torch
+
+    from paper_2306_13618_gb300 import build as B
+    from paper_2306_13618_gb300 import inputs, uotk
+    B.build()
+    n = args.n or (1 << 17)
+    dev = torch.device("cuda", 0)
+    if args.case in ("direct", "nfft", "nfft_solve"):
+        W = inputs.gmm3(seed=2000, n=n, m=n)
+        src, w, tgt = (torch.from_numpy(v).to(dev) for v in (W.y, W.b, W.x))
+        if args.case == "nfft_solve":
+            a = torch.from_numpy(W.a).to(dev)
+            call = lambda: uotk.uot_sinkhorn(tgt, a, src, w, W.eps, W.rho,  # noqa: E731
+                                             max_sweeps=4, method="nfft")
+        else:
+            call = lambda: uotk.kernel_sum(src, w, tgt, W.eps, method=args.case)  # noqa: E731
+    elif args.case == "nfft_reg":
+        g = inputs.rng(741)
+        src, tgt = (torch.from_numpy(g.uniform(0, 1, (n, 3)).astype(np.float32)).to(dev)
+                    for _ in range(2))
+        w = torch.from_numpy(g.uniform(0, 1, n).astype(np.float32)).to(dev)
+        call = lambda: uotk.kernel_sum(src, w, tgt, 0.5, method="nfft",  # noqa: E731
+                                       kernel="laplace")
+    else:
+        W = inputs.gauss64(n=n, m=n)
+        src, w, tgt = (torch.from_numpy(v).to(dev) for v in (W.y, W.b, W.x))
+        call = lambda: uotk.kernel_sum(src, w, tgt, W.eps, method="direct_bf16x3")  # noqa: E731
+    call()
+    torch.cuda.synchronize()
+    ms = []
+    for _ in range(args.reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        call()
+        e1.record()
+        e1.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    print(json.dumps({"case": args.case, "n": n, "ms": ms}), flush=True)
 
 
 def dist_env():
@@ -254,6 +314,29 @@ def cpu_oracle_rate(W, seconds, rank0=True):
     oracle.ksum(Y, B, X[:want], W.eps)
     dt = time.perf_counter() - t0
     return want * W.m / dt, want, dt, oracle.num_threads()
+
+
+def cpu_oracle_rate_1t(W, seconds):
+    """The same FP64 oracle kernel sum on one host thread: all sources onto a
+    sample of targets sized for about `seconds` of work."""
+    import numpy as np
+
+    import oracle
+    oracle.build()
+    Y, B, X = W.y.astype(np.float64), W.b.astype(np.float64), W.x.astype(np.float64)
+    cores = oracle.num_threads()
+    oracle.set_num_threads(1)
+    try:
+        t0 = time.perf_counter()
+        oracle.ksum(Y, B, X[:16], W.eps)
+        per = (time.perf_counter() - t0) / 16
+        want = int(max(16, min(W.n, seconds / per)))
+        t0 = time.perf_counter()
+        oracle.ksum(Y, B, X[:want], W.eps)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_num_threads(cores)
+    return want * W.m / dt, want, dt
 
 
 def reference_arm(args, W, rank, world):
@@ -605,6 +688,8 @@ def batch_main(args, rank, world, local):
 
 def main():
     args = parse()
+    if args.case:
+        return run_case(args)
     rank, world, local = dist_env()
     if args.workload == "batch":
         return batch_main(args, rank, world, local)
@@ -759,9 +844,13 @@ def main():
         extras["nfft_speedup_vs_direct"] = extras["direct"]["ms_per_matvec"] / extras["nfft"]["ms_per_matvec"]
 
     rate, tgt, dt, cores = cpu_oracle_rate(W, args.cpu_seconds)
+    rate1, tgt1, dt1 = cpu_oracle_rate_1t(W, max(1.0, args.cpu_seconds / 3))
     cpu = {"value": rate / (2.0 * W.n * W.m), "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": f"FP64 kernel sum of all {W.m} sources onto {tgt} targets ({dt:.1f} s); "
-                     f"sweeps/s extrapolated as pairs/s / (2 n m)"}
+                     f"sweeps/s extrapolated as pairs/s / (2 n m)",
+           "single_thread": {"value": rate1 / (2.0 * W.n * W.m), "unit": UNIT, "cores": 1,
+                             "sample": f"the same sum onto {tgt1} targets on one thread "
+                                       f"({dt1:.1f} s)"}}
 
     line = {
         "metric": METRIC if args.workload == "gmm3" else

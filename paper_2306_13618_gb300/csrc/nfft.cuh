@@ -14,7 +14,13 @@
 namespace uotk {
 
 constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit granularity)
-constexpr int NFFT_UNIT_POINTS = 2048; // points per spread/gather work unit
+// Points per work unit.  Clustered clouds fill few tiles (the 2^20-point
+// mixture workload: 83 of 4096), so a tile is cut into units of at most this
+// many points: the spread's CTAs (96 threads at m = 6) take small units so that
+// every SM gets several, the gather's (256 threads) larger ones, whose warps then
+// keep long runs of targets.
+constexpr int NFFT_SPREAD_UNIT = 1024;
+constexpr int NFFT_GATHER_UNIT = 2048;
 constexpr int NFFT_MAX_M = 8;
 constexpr int NFFT_CHUNK = 64;          // default points per bulk-copied staging chunk
 constexpr int NFFT_NEAR_CHUNK = 1024;   // targets per near-field work item
@@ -34,6 +40,14 @@ __host__ __device__ constexpr int nfft_win_stride(int m) {
 __host__ __device__ constexpr int nfft_win_xoff(int m, int kx) {
   return kx < m ? kx : nfft_win_half(m) + kx - m;
 }
+// Pair window table (the spread's): sorted points 2p and 2p + 1 share row p,
+// every window value stored as the pair (value of 2p, value of 2p + 1): the two
+// halves of phi_x (m pairs each, padded to a 16-byte multiple), phi_y (2m
+// pairs), phi_z (2m pairs).  Packed FP32x2 FMAs then run over point pairs.
+__host__ __device__ constexpr int nfft_winp_half(int m) { return (2 * m + 3) & ~3; }
+__host__ __device__ constexpr int nfft_winp_yoff(int m) { return 2 * nfft_winp_half(m); }
+__host__ __device__ constexpr int nfft_winp_zoff(int m) { return nfft_winp_yoff(m) + 4 * m; }
+__host__ __device__ constexpr int nfft_winp_stride(int m) { return nfft_winp_zoff(m) + 4 * m; }
 
 struct NfftParams {
   int d = 3;
@@ -73,18 +87,35 @@ struct NfftPoints {
   int4* cell = nullptr;      // sorted: (cx | cy<<10 | cz<<20, frac x, y, z as float bits)
   float* win = nullptr;      // sorted: [n][nfft_win_stride(m)] window rows (layout above)
   int* ckey = nullptr;       // sorted: packed cell (cx | cy<<10 | cz<<20), n + 4 entries
+  float* winp = nullptr;     // [ceil(n/2)][nfft_winp_stride(m)] pair window rows (spread)
   int* perm = nullptr;       // sorted position -> caller index
   int* tile_start = nullptr; // [tiles+1] start of each tile in sorted order
+  // spread work units (at most NFFT_SPREAD_UNIT points of one tile)
   int* unit_tile = nullptr;  // [max_units] tile of each work unit
   int* unit_begin = nullptr; // [max_units] first sorted point of the unit
   int* unit_count = nullptr; // [max_units]
+  int* unit_zr = nullptr;    // [max_units] first and last local z cell (lo | hi << 8)
   int* num_units = nullptr;  // [1] device count
   int* tile_unit_start = nullptr;  // [tiles+1] first unit of each tile
   int max_units = 0;
+  // gather work units (at most NFFT_GATHER_UNIT points of one tile)
+  int* g_unit_tile = nullptr;
+  int* g_unit_begin = nullptr;
+  int* g_unit_count = nullptr;
+  int* g_num_units = nullptr;
+  int* g_tile_unit_start = nullptr;
+  int g_max_units = 0;
   int* scratch = nullptr;    // [tiles] counters
-  int* cell_count = nullptr; // [n^3] histogram, then scatter cursor
+  int* cell_count = nullptr; // [n^3] histogram
   int* cell_start = nullptr; // [n^3 + 1] exclusive scan
   int* block_sums = nullptr; // scan partials
+  // stable radix sort of the cell keys (deterministic order inside a cell)
+  int* rs_key[2] = {nullptr, nullptr};  // [n] keys, ping-pong
+  int* rs_val[2] = {nullptr, nullptr};  // [n] caller indices, ping-pong
+  int* rs_hist = nullptr;     // [256 * blocks + 1] digit counts, then their scan
+  int* rs_start = nullptr;    // [256 * blocks + 1]
+  int* rs_bsum = nullptr;     // scan partials
+  int4* tmp_cell = nullptr;   // [n] caller order: packed cell and fractions
 };
 size_t nfft_points_bytes(const NfftParams& P, int64_t n);
 void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S);
@@ -96,6 +127,7 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
 struct NfftWork {
   float* wts = nullptr;    // [max points + 4] spread weights (sorted order)
   float* grid = nullptr;   // [n^3] real grid
+  float* blocks = nullptr; // [max units][E^3 rounded to 4] spread blocks, one per work unit
   float2* cgrid = nullptr; // [n^3] complex work grid
   float* scale = nullptr;  // [3*N] device table
   float* full = nullptr;   // [N^3] non-separable table [kz'][ky'][kx'] (non-smooth kernels)
@@ -135,6 +167,6 @@ uotk_status nfft_near(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const 
 uotk_status nfft_bbox(uotk_ctx* ctx, cudaStream_t s, int d, const float* a, int64_t na,
                       const float* b, int64_t nb, float lo[3], float hi[3]);
 
-int nfft_max_units(const NfftParams& P, int64_t n);
+int nfft_max_units(const NfftParams& P, int64_t n, int unit_points = NFFT_SPREAD_UNIT);
 
 }  // namespace uotk

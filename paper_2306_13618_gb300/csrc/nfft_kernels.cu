@@ -3,26 +3,25 @@
 // inverse FFT) and gather (NFFT final step).
 //
 // Work units.  Points are sorted by grid cell, cells tile by tile (8^3 cells
-// per tile).  A unit is (tile, up to NFFT_UNIT_POINTS points); its CTA owns the
-// E^3 block of grid nodes the tile's windows reach (E = 8 + 2m - 1).  Chunks
-// of points (SPREAD_CH for the spread, GATHER_CH for the gather) -- window
-// table rows, packed cells, weights -- are staged in shared memory by
-// double-buffered 1-D bulk copies (TMA) completing on mbarriers, so the copy of
-// chunk k+1 overlaps the arithmetic of chunk k.
-// Spread.  Thread (kz, ky, half) owns the m nodes kx in [half m, half m + m)
-// of two footprint rows, (kz, ky) and (kz, ky + m).  The points of one cell
-// share the footprint: their rank-1 window products w phi_z phi_y phi_x
-// accumulate in registers (packed FP32x2 over node pairs) and are added to the
-// shared block once per cell, a barrier separating the additions of
-// consecutive cells (no shared-memory atomics).  In a Sinkhorn half-step the
-// spread forms the weights w itself.  The finished block is added into the
-// grid with global reductions, skipping zeros.
-// Gather.  The CTA stages the E^3 grid block around its tile; each warp
-// evaluates a contiguous run of a chunk's targets, one at a time: lanes split
-// the (2m)^2 (y, x) pairs of the footprint, each lane contracting its
-// z-columns with phi_z; consecutive targets of one cell reuse the footprint
-// held in registers.  In a Sinkhorn half-step the gather also runs the dual
-// update of its targets.
+// per tile), and inside a cell in caller order (a stable sort), so every sum
+// below is taken in the same order on every run.  A unit is (tile, up to
+// NFFT_SPREAD_UNIT or NFFT_GATHER_UNIT points); its CTA owns the E^3 block of
+// grid nodes the tile's windows reach (E = 8 + 2m - 1).  Window rows, cells and
+// weights arrive in shared memory by double-buffered 1-D bulk copies (TMA)
+// completing on mbarriers, so the copy of the next chunk overlaps the
+// arithmetic of the current one.
+// Spread.  The threads partition the footprint of one cell; the points of a
+// cell run accumulate their rank-1 window products w phi_z phi_y phi_x in
+// registers (packed FP32x2 over point pairs, from the pair window table) and
+// are added to the shared block once per run, a barrier separating the
+// additions of consecutive runs.  In a Sinkhorn half-step the spread forms the
+// weights itself.  Each unit writes its block to a workspace; the fold sums the
+// blocks of every grid node in a fixed order (no atomics anywhere).
+// Gather.  The CTA stages the E^3 grid block around its tile.  For even m <= 6
+// each warp stages and evaluates its own run of targets (k_gather_w); lanes
+// split the footprint, which stays in registers while consecutive targets share
+// a cell.  Odd m and m = 8 use the CTA-staged form (k_gather).  In a Sinkhorn
+// half-step the gather also runs the dual update of its targets.
 #include <math.h>
 
 #include "nfft.cuh"
@@ -103,224 +102,347 @@ __device__ __forceinline__ void load_vec(const float* p, float* r) {
 }
 
 // ---------------------------------------------------------------- spread ----
-// Thread (kz, ky, half) of the 8m^2 threads owns one row half; with RPT rows per
-// thread (RPT | 2m), thread (kz, ky < 2m/RPT, half) of 8m^2/RPT threads owns the
-// row halves (kz, ky + k 2m/RPT), k < RPT, which share the phi_x half it loads
-// for every point.
+// Thread (zg, y, xh) of the NT = ZG 2m 2 threads owns the ZB = 2m/ZG nodes
+// z in [zg ZB, zg ZB + ZB) of footprint row y, x in [xh m, xh m + m).  The
+// spread reads the pair window table: every value is the pair (point 2p, point
+// 2p + 1), so one packed FP32x2 FMA adds the contributions of two points of a
+// cell to a node, the two halves summing the even and the odd points (added
+// when the cell's run ends).  Per point pair a thread forms ZB packed products
+// w phi_z phi_y and adds each times its m phi_x pairs.  The threads partition
+// the footprint, so the per-cell additions into the shared block need no
+// atomics; a barrier separates consecutive cells.
+template <int M>
+struct SpreadMap {
+  static constexpr int W2 = 2 * M;
+  static constexpr int ZG = (M % 2 == 0) ? 4 : 2;  // z groups
+  static constexpr int ZB = W2 / ZG;               // z rows per thread
+  static constexpr int NT = ZG * W2 * 2;           // threads owning footprint nodes
+  static constexpr int NTH = NT < 32 ? 32 : NT;    // threads launched (warp 0 lists cell runs)
+};
+template <int M, int CP>
+struct SpreadGeo {
+  static constexpr int E = NFFT_TILE + 2 * M - 1;
+  static constexpr int E2 = E * E, E3 = E2 * E, E3P = (E3 + 3) & ~3;
+  static constexpr int WSP = nfft_winp_stride(M);   // floats per pair row
+  static constexpr int CPT = 2 * CP;                 // point positions per chunk
+  static constexpr int STAGE_F = CP * WSP + 2 * (CPT + 4);  // pair rows, cells, weights
+};
+constexpr int SPREAD_CP = 32;   // point pairs per staging chunk
+
+// Copies of chunk k of a unit: pair rows [pc0, pc0 + cpn), and the cells and
+// weights of points 2 pc0 .. from the 16-byte-aligned element at or below,
+// whose offset (0 or 2) the consumer adds back.
+template <int M, int CP>
+__device__ __forceinline__ void stage_pairs(float* st, unsigned long long* bar, const float* winp,
+                                            const int* ckey, const float* wts, int pc0, int cpn) {
+  using SG = SpreadGeo<M, CP>;
+  const int q0 = 2 * pc0, off = q0 & 3;
+  const unsigned wbytes = (unsigned)(cpn * SG::WSP * 4);
+  const unsigned kbytes = (unsigned)(((2 * cpn + off + 3) & ~3) * 4);
+  mbar_expect(bar, wbytes + (wts ? 2 * kbytes : kbytes));
+  bulk_copy(st, winp + (size_t)pc0 * SG::WSP, wbytes, bar);
+  bulk_copy(st + CP * SG::WSP, ckey + (q0 - off), kbytes, bar);
+  if (wts) bulk_copy(st + CP * SG::WSP + SG::CPT + 4, wts + (q0 - off), kbytes, bar);
+}
+
 // POT: the weights are the half-step's w = base e^{lam pot - shift}, formed here
-// when a chunk lands (pw; wts unused); else they are staged from wts.
-template <int M, int RPT = 1, bool POT = false, int C = CH>
-__global__ void __launch_bounds__(8 * M * M / RPT)
-    k_spread(const float* __restrict__ win, const int* __restrict__ ckey,
+// when a chunk lands (threads WT0.. hold the pot and base of the chunk's points,
+// loaded a chunk ahead; wts unused); else they are staged from wts.  Points of
+// a pair that lie outside the unit get weight 0.  The finished block's z-planes
+// that the unit's cells reach (unit_zr) go to blocks[u]; k_fold_units and
+// k_fold add the blocks into the grid.
+template <int M, bool POT, int CP>
+__global__ void __launch_bounds__(SpreadMap<M>::NTH)
+    k_spread(const float* __restrict__ winp, const int* __restrict__ ckey,
              const float* __restrict__ wts, const int* __restrict__ unit_tile,
              const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
-             const int* __restrict__ num_units, int n, int tiles1, float* __restrict__ grid,
-             long long* __restrict__ flags, SpreadWeights pw) {
-  using G = Geo<M, C>;
-  constexpr int W2 = G::W2, E = G::E, E3 = G::E3, WS = G::WS, NT = 8 * M * M / RPT;
-  constexpr int YR = W2 / RPT;  // rows of ky per thread group
-  static_assert(W2 % RPT == 0, "rows per thread divide 2m");
-  // POT: thread WT0 + t forms the weight of point t of a chunk; warp 0 is left
-  // to list the cell runs when the CTA has a warp to spare
-  constexpr int WT0 = NT >= C + 32 ? 32 : 0;
-  static_assert(!POT || NT >= C + WT0, "one weight thread per chunk point");
-  constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
+             const int* __restrict__ unit_zr, const int* __restrict__ num_units, int tiles1,
+             float* __restrict__ blocks, long long* __restrict__ flags, SpreadWeights pw) {
+  using SG = SpreadGeo<M, CP>;
+  using SM = SpreadMap<M>;
+  constexpr int W2 = 2 * M, E = SG::E, E2 = SG::E2, E3 = SG::E3, WSP = SG::WSP, CPT = SG::CPT;
+  constexpr int NT = SM::NTH, ZB = SM::ZB;
+  constexpr int HP2 = nfft_winp_half(M), YO2 = nfft_winp_yoff(M), ZO2 = nfft_winp_zoff(M);
+  // threads SM::NT.. (present when the footprint needs fewer than a warp) own
+  // no nodes; they take part in the listing, the weights and the copies
+  const bool owner = (int)threadIdx.x < SM::NT;
+  // POT: threads WT0 .. NT-1 form the weights (warp 0 lists the cell runs
+  // meanwhile when the CTA has a warp to spare), WK chunk positions each
+  constexpr int WT0 = NT >= CPT + 32 ? 32 : 0;
+  constexpr int WTN = NT - WT0;
+  constexpr int WK = (CPT + WTN - 1) / WTN;
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
-  __shared__ int gstart[C + 1];
+  __shared__ int gstart[CPT + 1];
   __shared__ int ngroups;
   float* blk = smem;
-  float* stage0 = smem + G::E3P;
+  float* stage0 = smem + SG::E3P;
   const int u = blockIdx.x;
   if (u >= *num_units) return;
-  const int b0 = unit_begin[u], cnt = unit_count[u];
-  const int nchunks = (cnt + C - 1) / C;
+  const int b0 = unit_begin[u], e0 = b0 + unit_count[u];
+  const int pb = b0 >> 1, pe = (e0 + 1) >> 1;
+  const int nchunks = (pe - pb + CP - 1) / CP;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
-      stage_chunk<M, C>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, POT ? nullptr : wts,
-                     b0 + k * C, min(C, cnt - k * C));
+      stage_pairs<M, CP>(stage0 + k * SG::STAGE_F, &bars[k], winp, ckey, POT ? nullptr : wts,
+                         pb + k * CP, min(CP, pe - pb - k * CP));
   }
-  // POT: pot and base of the next chunk's point t = threadIdx.x - WT0 are
-  // loaded a chunk ahead into registers; whole warps do the FP64 work (FP64
-  // is scarce on this GPU and a partial warp costs the pipe a whole one).
+  // POT: FP64 work by whole warps (FP64 is scarce on this GPU and a partial
+  // warp costs the pipe a whole one)
   const int wt = (int)threadIdx.x - WT0;
-  double ppot = 0.0, shift = 0.0;
-  float pbase = 1.f;
+  double ppot[WK], shift = 0.0;
+  float pbase[WK];
+  auto prefetch = [&](int pc0) {
+#pragma unroll
+    for (int j = 0; j < WK; ++j) {
+      const int q = 2 * pc0 + wt + j * WTN;
+      ppot[j] = 0.0;
+      pbase[j] = 1.f;
+      if (wt >= 0 && wt + j * WTN < CPT && q >= b0 && q < e0) {
+        ppot[j] = pw.pot[q];
+        if (pw.base) pbase[j] = pw.base[q];
+      }
+    }
+  };
   if (POT) {
     shift = ordered_to_dbl(*pw.shift_slot);
-    if (wt >= 0 && wt < min(C, cnt)) {
-      ppot = pw.pot[b0 + wt];
-      if (pw.base) pbase = pw.base[b0 + wt];
-    }
+    prefetch(pb);
   }
   for (int i = threadIdx.x; i < E3; i += NT) blk[i] = 0.f;
   __syncthreads();  // barriers initialised and block zeroed before anyone waits or adds
   int tx0, ty0, tz0;
   tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
-  const int r = threadIdx.x >> 1, half = threadIdx.x & 1;
-  const int kz = r / YR, ky = r - kz * YR;
+  const int xh = threadIdx.x & 1;
+  const int y = (threadIdx.x >> 1) % W2;
+  const int z0 = ((threadIdx.x >> 1) / W2) * ZB;
   const int lane = threadIdx.x & 31;
+  const unsigned long long keep_hi = f2_pack(0.f, 1.f), keep_lo = f2_pack(1.f, 0.f);
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags)) return;
-    const int q0 = b0 + k * C, cn = min(C, cnt - k * C), off = q0 & 3;
-    float* sw = stage0 + (k % STAGES) * G::STAGE_F;
-    const int* skey = reinterpret_cast<const int*>(sw + C * WS) + off;
-    const float* swt = sw + C * WS + C + 4 + off;
-    // Fold each point's weight into its phi_z row, and list where each cell's
-    // run of points starts (points are sorted by cell).
+    const int pc0 = pb + k * CP, cpn = min(CP, pe - pc0), P0 = 2 * pc0;
+    const int lo = max(b0, P0) - P0, hi = min(e0, P0 + 2 * cpn) - P0;  // unit positions
+    float* sw = stage0 + (k % STAGES) * SG::STAGE_F;
+    const int koff = P0 & 3;
+    const int* skey = reinterpret_cast<const int*>(sw + CP * WSP) + koff;
+    const float* swt = sw + CP * WSP + CPT + 4 + koff;
+    // Fold each point's weight into its phi_z lane (0 outside the unit), and
+    // list where each cell's run of points starts (points are sorted by cell).
     if (POT) {
-      if (wt >= 0 && wt < cn) {
-        const float w = pbase * exp_shifted(pw.lam * ppot - shift);
-        float* zr = sw + wt * WS + ZO;
+      if (wt >= 0) {
 #pragma unroll
-        for (int j = 0; j < W2; ++j) zr[j] *= w;
-      }
-      const int cn1 = k + 1 < nchunks ? min(C, cnt - (k + 1) * C) : 0;
-      if (wt >= 0 && wt < cn1) {
-        ppot = pw.pot[q0 + C + wt];
-        if (pw.base) pbase = pw.base[q0 + C + wt];
+        for (int j = 0; j < WK; ++j) {
+          const int t = wt + j * WTN;
+          if (t < 2 * cpn) {
+            const float w = (t >= lo && t < hi) ? pbase[j] * exp_shifted(pw.lam * ppot[j] - shift)
+                                                : 0.f;
+            float* zr = sw + (t >> 1) * WSP + ZO2 + (t & 1);
+#pragma unroll
+            for (int i = 0; i < W2; ++i) zr[2 * i] *= w;
+          }
+        }
+        if (k + 1 < nchunks) prefetch(pc0 + CP);
       }
     } else {
-      for (int i = threadIdx.x; i < cn * W2; i += NT) {
-        const int q = i / W2;
-        sw[q * WS + ZO + (i - q * W2)] *= swt[q];
+      for (int i = threadIdx.x; i < 2 * cpn * W2; i += NT) {
+        const int t = i / W2, z = i - t * W2;
+        const float w = (t >= lo && t < hi) ? swt[t] : 0.f;
+        sw[(t >> 1) * WSP + ZO2 + 2 * z + (t & 1)] *= w;
       }
     }
     if (threadIdx.x < 32) {
       int base = 0;
-      for (int h = 0; h < C; h += 32) {
-        const int q = h + lane;
-        const bool f = q < cn && (q == 0 || skey[q] != skey[q - 1]);
+      for (int h = 0; h < CPT; h += 32) {
+        const int t = h + lane;
+        const bool f = t >= lo && t < hi && (t == lo || skey[t] != skey[t - 1]);
         const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (f) gstart[base + __popc(bal & ((1u << lane) - 1u))] = q;
+        if (f) gstart[base + __popc(bal & ((1u << lane) - 1u))] = t;
         base += __popc(bal);
       }
-      if (lane == 0) { ngroups = base; gstart[base] = cn; }
+      if (lane == 0) { ngroups = base; gstart[base] = hi; }
     }
     __syncthreads();
     const int ng = ngroups;
     for (int g = 0; g < ng; ++g) {
-      const int p0 = gstart[g], p1 = gstart[g + 1];
-      const int key = skey[p0];
-      if constexpr (RPT > 1) {
-        float acc[RPT][M];
+      if (owner) {
+        const int t0 = gstart[g], t1 = gstart[g + 1];
+        const int key = skey[t0];
+        unsigned long long acc2[ZB][M];
 #pragma unroll
-        for (int k = 0; k < RPT; ++k)
+        for (int r = 0; r < ZB; ++r)
 #pragma unroll
-          for (int j = 0; j < M; ++j) acc[k][j] = 0.f;
-        int q = p0;
-        if constexpr (M % 2 == 0) {
-          // node pairs (j, j+1) in packed FP32x2 FMAs (the same IEEE FMAs)
-          unsigned long long acc2[RPT][M / 2];
+          for (int j = 0; j < M; ++j) acc2[r][j] = 0ull;
+        const int pp0 = t0 >> 1, pp1 = (t1 - 1) >> 1;
+        for (int pp = pp0; pp <= pp1; ++pp) {
+          const float* row = sw + pp * WSP;
+          unsigned long long fy2 = *reinterpret_cast<const unsigned long long*>(row + YO2 + 2 * y);
+          // a pair half outside the run (the neighbouring cell's point) is masked
+          if (pp == pp0 && (t0 & 1)) fy2 = f2_mul(fy2, keep_hi);
+          if (pp == pp1 && (t1 & 1)) fy2 = f2_mul(fy2, keep_lo);
+          unsigned long long fx2[M];
+          const float* xr = row + xh * HP2;
 #pragma unroll
-          for (int k = 0; k < RPT; ++k)
-#pragma unroll
-            for (int j = 0; j < M / 2; ++j) acc2[k][j] = 0ull;
-          for (; q + 1 < p1; q += 2) {
-            const float* w0 = sw + q * WS;
-            const float* w1 = w0 + WS;
-            const float z0 = w0[ZO + kz], z1 = w1[ZO + kz];
-            float f0[M], f1[M];
-            load_vec<M>(w0 + half * HP, f0);
-            load_vec<M>(w1 + half * HP, f1);
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-              const float a0 = z0 * w0[YO + ky + k * YR], a1 = z1 * w1[YO + ky + k * YR];
-              const unsigned long long A0 = f2_pack(a0, a0), A1 = f2_pack(a1, a1);
-#pragma unroll
-              for (int j = 0; j < M / 2; ++j)
-                acc2[k][j] = f2_fma(A1, f2_pack(f1[2 * j], f1[2 * j + 1]),
-                                    f2_fma(A0, f2_pack(f0[2 * j], f0[2 * j + 1]), acc2[k][j]));
-            }
+          for (int j = 0; j + 1 < M; j += 2) {
+            const float4 v = *reinterpret_cast<const float4*>(xr + 2 * j);
+            fx2[j] = f2_pack(v.x, v.y);
+            fx2[j + 1] = f2_pack(v.z, v.w);
           }
+          if (M & 1) fx2[M - 1] = *reinterpret_cast<const unsigned long long*>(xr + 2 * (M - 1));
 #pragma unroll
-          for (int k = 0; k < RPT; ++k)
+          for (int r = 0; r < ZB; ++r) {
+            const unsigned long long A2 = f2_mul(
+                *reinterpret_cast<const unsigned long long*>(row + ZO2 + 2 * (z0 + r)), fy2);
 #pragma unroll
-            for (int j = 0; j < M / 2; ++j) f2_unpack(acc2[k][j], acc[k][2 * j], acc[k][2 * j + 1]);
-        } else {
-          for (; q + 1 < p1; q += 2) {
-            const float* w0 = sw + q * WS;
-            const float* w1 = w0 + WS;
-            const float z0 = w0[ZO + kz], z1 = w1[ZO + kz];
-            float f0[M], f1[M];
-            load_vec<M>(w0 + half * HP, f0);
-            load_vec<M>(w1 + half * HP, f1);
-#pragma unroll
-            for (int k = 0; k < RPT; ++k) {
-              const float a0 = z0 * w0[YO + ky + k * YR], a1 = z1 * w1[YO + ky + k * YR];
-#pragma unroll
-              for (int j = 0; j < M; ++j) acc[k][j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[k][j]));
-            }
-          }
-        }
-        if (q < p1) {
-          const float* w0 = sw + q * WS;
-          const float z0 = w0[ZO + kz];
-          float f0[M];
-          load_vec<M>(w0 + half * HP, f0);
-#pragma unroll
-          for (int k = 0; k < RPT; ++k) {
-            const float a0 = z0 * w0[YO + ky + k * YR];
-#pragma unroll
-            for (int j = 0; j < M; ++j) acc[k][j] = fmaf(a0, f0[j], acc[k][j]);
+            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(A2, fx2[j], acc2[r][j]);
           }
         }
         const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-        float* dst = blk + ((bz + kz) * E + by + ky) * E + bx + half * M;
+        float* dst = blk + ((bz + z0) * E + by + y) * E + bx + xh * M;
 #pragma unroll
-        for (int k = 0; k < RPT; ++k)
+        for (int r = 0; r < ZB; ++r)
 #pragma unroll
-          for (int j = 0; j < M; ++j) dst[k * YR * E + j] += acc[k][j];
-        __syncthreads();
-        continue;
+          for (int j = 0; j < M; ++j) {
+            float e, o;
+            f2_unpack(acc2[r][j], e, o);
+            dst[r * E2 + j] += e + o;
+          }
       }
-      float acc[M];
-#pragma unroll
-      for (int j = 0; j < M; ++j) acc[j] = 0.f;
-      int q = p0;
-      for (; q + 1 < p1; q += 2) {
-        const float* w0 = sw + q * WS;
-        const float* w1 = w0 + WS;
-        const float a0 = w0[ZO + kz] * w0[YO + ky];
-        const float a1 = w1[ZO + kz] * w1[YO + ky];
-        float f0[M], f1[M];
-        load_vec<M>(w0 + half * HP, f0);
-        load_vec<M>(w1 + half * HP, f1);
-#pragma unroll
-        for (int j = 0; j < M; ++j) acc[j] = fmaf(a1, f1[j], fmaf(a0, f0[j], acc[j]));
-      }
-      if (q < p1) {
-        const float* w0 = sw + q * WS;
-        const float a0 = w0[ZO + kz] * w0[YO + ky];
-        float f0[M];
-        load_vec<M>(w0 + half * HP, f0);
-#pragma unroll
-        for (int j = 0; j < M; ++j) acc[j] = fmaf(a0, f0[j], acc[j]);
-      }
-      const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-      float* dst = blk + ((bz + kz) * E + by + ky) * E + bx + half * M;
-#pragma unroll
-      for (int j = 0; j < M; ++j) dst[j] += acc[j];
       __syncthreads();
     }
     if (threadIdx.x == 0 && k + STAGES < nchunks)
-      stage_chunk<M, C>(stage0 + (k % STAGES) * G::STAGE_F, &bars[k % STAGES], win, ckey,
-                     POT ? nullptr : wts, b0 + (k + STAGES) * C,
-                     min(C, cnt - (k + STAGES) * C));
+      stage_pairs<M, CP>(stage0 + (k % STAGES) * SG::STAGE_F, &bars[k % STAGES], winp, ckey,
+                         POT ? nullptr : wts, pc0 + STAGES * CP,
+                         min(CP, pe - pc0 - STAGES * CP));
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < E3; i += NT) {
-    const float v = blk[i];
-    if (v == 0.f) continue;
-    const int lz = i / G::E2, ly = (i / E) % E, lx = i % E;
-    int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
-    gz += gz < 0 ? n : 0;
-    gy += gy < 0 ? n : 0;
-    gx += gx < 0 ? n : 0;
-    atomicAdd(&grid[((long long)gz * n + gy) * n + gx], v);
+  // the z-planes the unit's cells reach: local z cells zlo .. zhi, planes
+  // zlo .. zhi + 2m - 1
+  const int zr = unit_zr[u];
+  const int i0 = (zr & 255) * E2, i1 = min(E3, ((zr >> 8) + W2) * E2);
+  float* outb = blocks + (size_t)u * SG::E3P;
+  for (int i = i0 + threadIdx.x; i < i1; i += NT) outb[i] = blk[i];
+}
+
+// Fold, step 1: the units of one tile (a tile with more than NFFT_SPREAD_UNIT
+// points has several) are summed into the block of the tile's first unit, in
+// a fixed order; a unit contributes to the z-planes it wrote (unit_zr).  The U
+// units of a tile share the work: CTA k of the tile takes the k-th of U slices
+// of the block's entries.  When a slice has fewer entries than the CTA has
+// threads, G groups of threads each sum the units g, g + G, g + 2G, .. of
+// every entry, and the G partial sums are then added in group order: a dense
+// tile costs about one block's reads per CTA and short dependency chains.
+constexpr int FOLD_THREADS = 256;
+template <int M>
+__global__ void __launch_bounds__(FOLD_THREADS)
+    k_fold_units(float* __restrict__ blocks, const int* __restrict__ unit_tile,
+                 const int* __restrict__ tile_unit_start, const int* __restrict__ unit_zr,
+                 const int* __restrict__ num_units) {
+  constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E2 = E * E, E3 = E2 * E;
+  constexpr int E3P = (E3 + 3) & ~3;
+  __shared__ float part[FOLD_THREADS];
+  const int u = blockIdx.x;
+  if (u >= *num_units) return;
+  const int t = unit_tile[u];
+  const int u0 = tile_unit_start[t], U = tile_unit_start[t + 1] - u0;
+  if (U < 2) return;
+  const int k = u - u0;
+  const int chunk = (E3 + U - 1) / U;
+  const int e0 = min(E3, k * chunk), e1 = min(E3, e0 + chunk);
+  const int ne = e1 - e0;
+  if (ne <= 0) return;
+  float* first = blocks + (size_t)u0 * E3P;
+  auto covers = [&](int v, int e) {
+    const int zr = __ldg(&unit_zr[u0 + v]);
+    const int pz = e / E2;
+    return pz >= (zr & 255) && pz < (zr >> 8) + W2;
+  };
+  if (ne >= FOLD_THREADS / 2) {
+    for (int e = e0 + threadIdx.x; e < e1; e += FOLD_THREADS) {
+      float s = 0.f;
+      for (int v = 0; v < U; ++v)
+        if (covers(v, e)) s += first[(size_t)v * E3P + e];
+      first[e] = s;
+    }
+    return;
   }
+  int G = FOLD_THREADS / ne;
+  G = G < U ? G : U;
+  const int ei = threadIdx.x % ne, g = threadIdx.x / ne;
+  float s = 0.f;
+  if (g < G)
+    for (int v = g; v < U; v += G)
+      if (covers(v, e0 + ei)) s += first[(size_t)v * E3P + e0 + ei];
+  part[threadIdx.x] = s;
+  __syncthreads();  // every group has read its units before the first block is overwritten
+  if (threadIdx.x < ne) {
+    float r = 0.f;
+    for (int q = 0; q < G; ++q) r += part[q * ne + threadIdx.x];
+    first[e0 + threadIdx.x] = r;
+  }
+}
+
+// Fold, step 2: grid node g is the sum of the tile blocks (in each tile's
+// first unit) of the up to 27 tiles whose blocks cover it, in a fixed order
+// (tile offsets dz, dy, dx = -1, 0, 1): no atomics, and every node is summed
+// in the same order on every run.  A tile's block covers nodes 8T - m + 1 ..
+// 8T + 8 + m - 2 (mod n) per axis, within one tile of T for m <= 8; on a grid
+// of two tiles per axis the offsets -1 and +1 name the same tile, whose block
+// then covers some nodes twice, as the torus requires.  A tile of one unit
+// holds only the z-planes that unit wrote.  One CTA per output tile, one
+// thread per node.
+template <int M>
+__global__ void __launch_bounds__(512)
+    k_fold(const float* __restrict__ blocks, const int* __restrict__ tile_unit_start,
+           const int* __restrict__ unit_zr, int n, int tiles1, float* __restrict__ grid) {
+  constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1;
+  constexpr int E3P = (E * E * E + 3) & ~3;
+  static_assert(M - 1 < NFFT_TILE, "a block reaches at most one tile beyond its own");
+  __shared__ int first[27], offs[27], zlo[27], zhi[27];
+  __shared__ int nlist;
+  const int t0 = blockIdx.x;
+  const int tx = t0 % tiles1, ty = (t0 / tiles1) % tiles1, tz = t0 / (tiles1 * tiles1);
+  if (threadIdx.x < 32) {
+    // the non-empty neighbour tiles, listed in offset order
+    const int c = threadIdx.x;
+    int us = -1, lo = 0, hi = E;
+    if (c < 27) {
+      const int dz = c / 9 - 1, dy = (c / 3) % 3 - 1, dx = c % 3 - 1;
+      const int T = (((tz + dz + tiles1) % tiles1) * tiles1 + (ty + dy + tiles1) % tiles1) *
+                        tiles1 + (tx + dx + tiles1) % tiles1;
+      const int a = tile_unit_start[T], b = tile_unit_start[T + 1];
+      if (b > a) {
+        us = a;
+        if (b - a == 1) {
+          const int zr = unit_zr[a];
+          lo = zr & 255;
+          hi = (zr >> 8) + W2;
+        }
+      }
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, us >= 0);
+    if (us >= 0) {
+      const int slot = __popc(bal & ((1u << c) - 1u));
+      first[slot] = us;
+      offs[slot] = c;
+      zlo[slot] = lo;
+      zhi[slot] = hi;
+    }
+    if (c == 0) nlist = __popc(bal);
+  }
+  __syncthreads();
+  const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
+  float v = 0.f;
+  const int nl = nlist;
+  for (int q = 0; q < nl; ++q) {
+    const int c = offs[q];
+    const int dz = c / 9 - 1, dy = (c / 3) % 3 - 1, dx = c % 3 - 1;
+    const int Lz = lz - NFFT_TILE * dz + M - 1, Ly = ly - NFFT_TILE * dy + M - 1,
+              Lx = lx - NFFT_TILE * dx + M - 1;
+    if (Lz < zlo[q] || Lz >= zhi[q] || Ly < 0 || Ly >= E || Lx < 0 || Lx >= E) continue;
+    v += blocks[(size_t)first[q] * E3P + (Lz * E + Ly) * E + Lx];
+  }
+  grid[((long long)(tz * NFFT_TILE + lz) * n + ty * NFFT_TILE + ly) * n + tx * NFFT_TILE + lx] = v;
 }
 
 // Spread weights in sorted order: w_q = base_q exp(lam pot_q - shift).
@@ -990,49 +1112,250 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Gather, even m <= 6 (the per-warp form).  Each warp takes a contiguous run
+// of the unit's targets and stages their window rows and cells itself
+// (double-buffered bulk copies of GW targets completing on the warp's own
+// mbarriers), so after the grid block is staged no warp waits for another.
+// Lane (zg, yg, xh) owns the BZ x BZ x m footprint nodes z in [zg BZ, +BZ),
+// y in [yg BZ, +BZ), x in [xh m, +m), BZ = m/2 (4 x 4 x 2 lanes cover the
+// (2m)^3 nodes), held in registers as x pairs while consecutive targets share
+// a cell.  Per target, lane part = sum_x phi_x sum_{z,y} (phi_z phi_y) g[z][y][x]
+// (the inner sums packed over x pairs), and the warp adds the 32 parts.
+constexpr int GW = 16;      // targets per per-warp staging buffer
+constexpr int GWARPS = 8;   // warps of a gather CTA
+template <int M>
+struct GatherGeo {
+  static constexpr int E = NFFT_TILE + 2 * M - 1;
+  static constexpr int E3P = (E * E * E + 3) & ~3;
+  static constexpr int WS = nfft_win_stride(M);
+  static constexpr int BUF_F = GW * WS + GW + 4;   // window rows, then cells (align slack)
+  static constexpr int WARP_F = 2 * BUF_F;
+  static_assert(BUF_F % 4 == 0, "16-byte aligned buffers");
+};
+
+template <int M>
+__device__ __forceinline__ void stage_warp(float* buf, unsigned long long* bar,
+                                           const float* win, const int* ckey, int q0, int cn) {
+  constexpr int WS = GatherGeo<M>::WS;
+  const int off = q0 & 3;
+  const unsigned wbytes = (unsigned)(cn * WS * 4);
+  const unsigned kbytes = (unsigned)(((cn + off + 3) & ~3) * 4);
+  mbar_expect(bar, wbytes + kbytes);
+  bulk_copy(buf, win + (size_t)q0 * WS, wbytes, bar);
+  bulk_copy(buf + GW * WS, ckey + (q0 - off), kbytes, bar);
+}
+
+template <int M, bool DUAL>
+__global__ void __launch_bounds__(32 * GWARPS, 2)
+    k_gather_w(const float* __restrict__ win, const int* __restrict__ ckey,
+               const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
+               const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
+               int tiles1, const float* __restrict__ grid, float* __restrict__ out,
+               long long* __restrict__ flags, DualUpdate du) {
+  using GG = GatherGeo<M>;
+  constexpr int E = GG::E, E2 = E * E, E3 = E2 * E, WS = GG::WS;
+  constexpr int BZ = M / 2, MP = M / 2;
+  constexpr int HP = nfft_win_half(M), YO = nfft_win_yoff(M), ZO = nfft_win_zoff(M);
+  static_assert(M % 2 == 0 && M <= 6, "per-warp gather: even m <= 6");
+  extern __shared__ __align__(16) float smem[];
+  __shared__ __align__(8) unsigned long long bars[GWARPS][2];
+  float* blk = smem;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* wbuf = smem + GG::E3P + warp * GG::WARP_F;
+  const int u = blockIdx.x;
+  if (DUAL && u == 0 && threadIdx.x == 0) {
+    flags[du.reset_slot] = ORDERED_NEG_INF;
+    if (du.reset_delta >= 0) flags[du.reset_delta] = ORDERED_NEG_INF;
+  }
+  if (u >= *num_units) return;
+  const int b0 = unit_begin[u], cnt = unit_count[u];
+  const int per = (cnt + GWARPS - 1) / GWARPS;
+  const int wb = min(cnt, warp * per), we = min(cnt, wb + per);
+  const int nch = (we - wb + GW - 1) / GW;
+  if (lane == 0) {
+    mbar_init(&bars[warp][0], 1);
+    mbar_init(&bars[warp][1], 1);
+    mbar_fence_init();
+    for (int k = 0; k < 2 && k < nch; ++k)
+      stage_warp<M>(wbuf + k * GG::BUF_F, &bars[warp][k], win, ckey, b0 + wb + k * GW,
+                    min(GW, we - wb - k * GW));
+  }
+  int tx0, ty0, tz0;
+  tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
+  for (int i = threadIdx.x; i < E3; i += blockDim.x) {
+    const int lz = i / E2, ly = (i / E) % E, lx = i % E;
+    int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
+    gz += gz < 0 ? n : 0;
+    gy += gy < 0 ? n : 0;
+    gx += gx < 0 ? n : 0;
+    blk[i] = grid[((long long)gz * n + gy) * n + gx];
+  }
+  __syncthreads();  // barriers initialised and block staged before anyone waits or reads
+  // Dual half-step state (as in k_gather): sums parked one per lane, 32 targets
+  // updated at once with every lane active.
+  const double qs = DUAL ? du.q * ordered_to_dbl(flags[du.shift_in]) : 0.0;
+  double dmx = -INFINITY, ddl = 0.0;
+  long long dbad = 0;
+  float dt = 0.f;
+  int di = -1, dn = 0;
+  auto dual_flush = [&]() {
+    if (di >= 0) {
+      const double lt = dt > 0.f && isfinite(dt) ? log_f32(dt) : log((double)dt);
+      const double v = du.ref == 0 ? fma(-du.q, lt, -qs)
+                                   : fma(du.q, log_f32(du.base[di]) - lt, -qs);
+      if (du.delta_out >= 0) ddl = fmax(ddl, fabs(v - du.pot[di]));
+      du.pot[di] = v;
+      if (isfinite(v)) dmx = fmax(dmx, v);
+      else ++dbad;
+    }
+    di = -1;
+    dn = 0;
+  };
+  const int zg = lane >> 3, yg = (lane >> 1) & 3, xh = lane & 1;
+  const int z0 = zg * BZ, y0 = yg * BZ;
+  unsigned long long hc[BZ][BZ][MP];
+  int cached = -1;
+  // this lane's part of the sum of the target with window row `row`, cell `key`
+  auto target_part = [&](const float* row, int key) -> float {
+    if (key != cached) {
+      const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+      const float* src = blk + ((bz + z0) * E + by + y0) * E + bx + xh * M;
+#pragma unroll
+      for (int z = 0; z < BZ; ++z)
+#pragma unroll
+        for (int yy = 0; yy < BZ; ++yy)
+#pragma unroll
+          for (int j = 0; j < MP; ++j)
+            hc[z][yy][j] = f2_pack(src[(z * E + yy) * E + 2 * j], src[(z * E + yy) * E + 2 * j + 1]);
+      cached = key;
+    }
+    float fz[BZ], fy[BZ], fx[M];
+#pragma unroll
+    for (int k = 0; k < BZ; ++k) {
+      fz[k] = row[ZO + z0 + k];
+      fy[k] = row[YO + y0 + k];
+    }
+    load_vec<M>(row + xh * HP, fx);
+    unsigned long long H[MP];
+#pragma unroll
+    for (int j = 0; j < MP; ++j) H[j] = 0ull;
+#pragma unroll
+    for (int z = 0; z < BZ; ++z)
+#pragma unroll
+      for (int yy = 0; yy < BZ; ++yy) {
+        const float a = fz[z] * fy[yy];
+        const unsigned long long A = f2_pack(a, a);
+#pragma unroll
+        for (int j = 0; j < MP; ++j) H[j] = f2_fma(A, hc[z][yy][j], H[j]);
+      }
+    unsigned long long r = f2_mul(f2_pack(fx[0], fx[1]), H[0]);
+#pragma unroll
+    for (int j = 1; j < MP; ++j) r = f2_fma(f2_pack(fx[2 * j], fx[2 * j + 1]), H[j], r);
+    float lo, hi;
+    f2_unpack(r, lo, hi);
+    return lo + hi;
+  };
+  for (int k = 0; k < nch; ++k) {
+    const int q0 = b0 + wb + k * GW, cn = min(GW, we - wb - k * GW);
+    float* sb = wbuf + (k & 1) * GG::BUF_F;
+    const bool ok = mbar_wait(&bars[warp][k & 1], (unsigned)(k >> 1) & 1u);
+    if (__any_sync(0xffffffffu, !ok)) {
+      // give up: record it, let this warp's copies in flight land, and stop
+      if (lane == 0) {
+        flag_add(&flags[FLAG_TIMEOUT], 1LL);
+        for (int q = k; q < nch && q < k + 2; ++q)
+          mbar_wait(&bars[warp][q & 1], (unsigned)(q >> 1) & 1u);
+      }
+      __syncwarp();
+      break;
+    }
+    const int* skey = reinterpret_cast<const int*>(sb + GW * WS) + (q0 & 3);
+    for (int p = 0; p < cn; p += 4) {
+      float part[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) part[j] = p + j < cn ? target_part(sb + (p + j) * WS, skey[p + j]) : 0.f;
+      const float tsum = warp_sum4(part, lane);
+      const int t = p + (lane >> 3);
+      if ((lane & 7) == 0 && t < cn) out[q0 + t] = tsum;
+      if (DUAL) {
+        if ((lane & 7) == dn && t < cn) {
+          dt = tsum;
+          di = q0 + t;
+        }
+        if (++dn == 8) dual_flush();
+      }
+    }
+    __syncwarp();
+    if (lane == 0 && k + 2 < nch) {
+      // the warp's reads of this buffer are done (generic proxy) before the
+      // bulk copy (async proxy) overwrites it
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      stage_warp<M>(sb, &bars[warp][k & 1], win, ckey, q0 + 2 * GW, min(GW, we - wb - (k + 2) * GW));
+    }
+  }
+  if (DUAL) {
+    dual_flush();
+    dmx = warp_max(dmx);
+    ddl = warp_max(ddl);
+    dbad = warp_sum(dbad);
+    __shared__ double dsh[2][GWARPS];
+    if (lane == 0) {
+      dsh[0][warp] = dmx;
+      dsh[1][warp] = ddl;
+      if (dbad) flag_add(&flags[FLAG_NONFINITE_DUAL], dbad);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < GWARPS; ++w) {
+        dmx = fmax(dmx, dsh[0][w]);
+        ddl = fmax(ddl, dsh[1][w]);
+      }
+      atomicMax(&flags[du.max_out], dbl_to_ordered(du.lam * dmx));
+      if (du.delta_out >= 0) atomicMax(&flags[du.delta_out], dbl_to_ordered(du.lam * ddl));
+    }
+  }
+}
+
 template <int M, int C = CH>
 size_t unit_smem() {
   using G = Geo<M, C>;
   return sizeof(float) * (G::E3P + STAGES * G::STAGE_F);
 }
 
-// two rows per thread: 94.0 ms per 200-sweep gmm3 solve at m = 6, against
-// 109.3 ms with one and 104.4 ms with four (72-thread CTAs hide too little)
-constexpr int SPREAD_RPT = 2;
-// Points per staging chunk of the spread.  At m = 6, 32-point chunks fit five
-// CTAs per SM (38 KB each) but ran 108.1 ms per gmm3 solve against 89.8 ms
-// with 64 (four CTAs): each chunk and each cell run cut by a chunk boundary
-// costs a barrier round.  128-point chunks (three CTAs) ran 102.8 ms.
-constexpr int SPREAD_CH = 64;
-// Points per staging chunk of the gather.  Registers hold it to two CTAs per SM
-// whatever the chunk (92 KB each at 192, m = 6), and longer chunks mean fewer
-// barriers and longer runs of targets per warp: per gmm3 solve 111.2 ms with
-// 64, 103.2 with 128, 100.8 with 192.
+// Points per staging chunk of the CTA-staged gather (odd m and m = 8).
+// Registers hold it to two CTAs per SM whatever the chunk, and longer chunks
+// mean fewer barriers and longer runs of targets per warp.
 constexpr int GATHER_CH = 192;
 
-// Whether the spread at cut-off m forms the half-step weights itself (one
-// weight thread per chunk point).
-constexpr bool spread_forms_weights(int m) { return 8 * m * m / SPREAD_RPT >= SPREAD_CH; }
-
 // pw != NULL: the weights w = base e^{lam pot - shift} are formed in the
-// kernel (requires spread_forms_weights(M)); else staged from wts.
+// kernel; else staged from wts.  The unit blocks go to W.blocks and the fold
+// writes the whole grid.
 template <int M>
 uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* wts, const SpreadWeights* pw,
-                          float* grid) {
-  const size_t smem = unit_smem<M, SPREAD_CH>();
-  constexpr int RPT = SPREAD_RPT, NT = 8 * M * M / RPT;
-  auto kern = k_spread<M, RPT, false, SPREAD_CH>;
-  if constexpr (spread_forms_weights(M)) {
-    if (pw) kern = k_spread<M, RPT, true, SPREAD_CH>;
-  } else {
-    if (pw) return set_error(ctx, UOTK_ERR_INTERNAL, "spread: weights not formed at m = %d", M);
+                          NfftWork& W, float* grid) {
+  using SG = SpreadGeo<M, SPREAD_CP>;
+  const size_t smem = sizeof(float) * (SG::E3P + STAGES * SG::STAGE_F);
+  constexpr int NT = SpreadMap<M>::NTH;
+  auto kern = pw ? k_spread<M, true, SPREAD_CP> : k_spread<M, false, SPREAD_CP>;
+  {
+    UOTK_PROF(ctx, s, "spread");
+    UOTK_CUDA(ctx, smem_attr(s, kern, smem));
+    kern<<<S.max_units, NT, smem, s>>>(S.winp, S.ckey, wts, S.unit_tile, S.unit_begin,
+                                       S.unit_count, S.unit_zr, S.num_units, P.tiles1, W.blocks,
+                                       ctx->dflags, pw ? *pw : SpreadWeights{});
+    UOTK_LAUNCHED(ctx);
   }
-  UOTK_CUDA(ctx, smem_attr(s, kern, smem));
-  kern<<<S.max_units, NT, smem, s>>>(S.win, S.ckey, wts, S.unit_tile, S.unit_begin, S.unit_count,
-                                     S.num_units, P.n, P.tiles1, grid, ctx->dflags,
-                                     pw ? *pw : SpreadWeights{});
-  UOTK_LAUNCHED(ctx);
+  {
+    UOTK_PROF(ctx, s, "fold");
+    k_fold_units<M><<<S.max_units, FOLD_THREADS, 0, s>>>(W.blocks, S.unit_tile,
+                                                         S.tile_unit_start, S.unit_zr,
+                                                         S.num_units);
+    UOTK_LAUNCHED(ctx);
+    k_fold<M><<<P.tiles1 * P.tiles1 * P.tiles1, 512, 0, s>>>(W.blocks, S.tile_unit_start,
+                                                             S.unit_zr, P.n, P.tiles1, grid);
+    UOTK_LAUNCHED(ctx);
+  }
   return UOTK_OK;
 }
 
@@ -1040,12 +1363,22 @@ template <int M>
 uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                           const NfftPoints& S, const float* grid, float* out,
                           const DualUpdate* du) {
-  const size_t smem = unit_smem<M, GATHER_CH>();
-  auto kern = du ? k_gather<M, true, GATHER_CH> : k_gather<M, false, GATHER_CH>;
-  UOTK_CUDA(ctx, smem_attr(s, kern, smem));
-  kern<<<S.max_units, 256, smem, s>>>(S.win, S.ckey, S.unit_tile, S.unit_begin, S.unit_count,
-                                      S.num_units, P.n, P.tiles1, grid, out, ctx->dflags,
-                                      du ? *du : DualUpdate{});
+  if constexpr (M % 2 == 0 && M <= 6) {
+    using GG = GatherGeo<M>;
+    const size_t smem = sizeof(float) * (GG::E3P + GWARPS * GG::WARP_F);
+    auto kern = du ? k_gather_w<M, true> : k_gather_w<M, false>;
+    UOTK_CUDA(ctx, smem_attr(s, kern, smem));
+    kern<<<S.g_max_units, 32 * GWARPS, smem, s>>>(S.win, S.ckey, S.g_unit_tile, S.g_unit_begin,
+                                                   S.g_unit_count, S.g_num_units, P.n, P.tiles1,
+                                                   grid, out, ctx->dflags, du ? *du : DualUpdate{});
+  } else {
+    const size_t smem = unit_smem<M, GATHER_CH>();
+    auto kern = du ? k_gather<M, true, GATHER_CH> : k_gather<M, false, GATHER_CH>;
+    UOTK_CUDA(ctx, smem_attr(s, kern, smem));
+    kern<<<S.g_max_units, 256, smem, s>>>(S.win, S.ckey, S.g_unit_tile, S.g_unit_begin,
+                                          S.g_unit_count, S.g_num_units, P.n, P.tiles1, grid, out,
+                                          ctx->dflags, du ? *du : DualUpdate{});
+  }
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
@@ -1066,8 +1399,8 @@ uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
 
 static uotk_status spread_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                                 const NfftPoints& S, const float* wts, const SpreadWeights* pw,
-                                float* grid) {
-#define UOTK_SPREAD_CALL(M) launch_spread<M>(ctx, s, P, S, wts, pw, grid)
+                                NfftWork& W, float* grid) {
+#define UOTK_SPREAD_CALL(M) launch_spread<M>(ctx, s, P, S, wts, pw, W, grid)
   UOTK_M_SWITCH(P.m, UOTK_SPREAD_CALL)
 #undef UOTK_SPREAD_CALL
 }
@@ -1082,16 +1415,16 @@ static uotk_status gather_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams&
 
 uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
                         const SpreadWeights& w, NfftWork& W, float* grid_out) {
-  const long long total = (long long)P.n * P.n * P.n;
-  UOTK_CUDA(ctx, cudaMemsetAsync(grid_out, 0, sizeof(float) * total, s));
-  if (S.n == 0) return UOTK_OK;
-  const float* wts = w.base;
+  if (S.n == 0) {
+    const long long total = (long long)P.n * P.n * P.n;
+    UOTK_CUDA(ctx, cudaMemsetAsync(grid_out, 0, sizeof(float) * total, s));
+    return UOTK_OK;
+  }
   // Gaussian kernel: the spread forms the weights as its chunks land (the
   // non-smooth kernels' near field reads them from W.wts)
-  if (w.pot && P.kernel == UOTK_KERNEL_GAUSS && spread_forms_weights(P.m)) {
-    UOTK_PROF(ctx, s, "spread");
-    return spread_units(ctx, s, P, S, nullptr, &w, grid_out);
-  }
+  if (w.pot && P.kernel == UOTK_KERNEL_GAUSS)
+    return spread_units(ctx, s, P, S, nullptr, &w, W, grid_out);
+  const float* wts = w.base;
   if (w.pot) {
     UOTK_PROF(ctx, s, "weights");
     k_point_weights<<<grid_for(ctx, S.n + 4, 256, 4), 256, 0, s>>>(w.base, w.pot, w.lam,
@@ -1099,8 +1432,7 @@ uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
     UOTK_LAUNCHED(ctx);
     wts = W.wts;
   }
-  UOTK_PROF(ctx, s, "spread");
-  return spread_units(ctx, s, P, S, wts, nullptr, grid_out);
+  return spread_units(ctx, s, P, S, wts, nullptr, W, grid_out);
 }
 
 uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, NfftWork& W,
@@ -1161,6 +1493,10 @@ void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWo
   const size_t n3 = (size_t)P.n * P.n * P.n;
   W.wts = cv.take<float>((size_t)(max_points > 0 ? max_points : 1) + 4);
   W.grid = cv.take<float>(n3);
+  // one E^3 block per spread work unit, folded into the grid in a fixed order
+  const int E = NFFT_TILE + 2 * P.m - 1;
+  W.blocks = cv.take<float>((size_t)nfft_max_units(P, max_points > 0 ? max_points : 1) *
+                            (size_t)((E * E * E + 3) & ~3));
   // complex work grid: n^3 for the unpruned passes, n^2 N + n N^2 for the
   // pruned ones (A1 and A2)
   const size_t pr = (size_t)P.n * P.n * P.N + (size_t)P.n * P.N * P.N;

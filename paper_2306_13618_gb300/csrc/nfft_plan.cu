@@ -190,70 +190,157 @@ __global__ void k_tile_counts(const int* __restrict__ cell_start, int tiles,
     count[t] = cell_start[(long long)(t + 1) * T3] - cell_start[(long long)t * T3];
 }
 
-// Single block: exclusive scans of points and of work units per tile.
-__global__ void k_bin_scan(int* __restrict__ count, int tiles, int unit_pts,
-                           int* __restrict__ tile_start, int* __restrict__ tile_unit_start,
-                           int* __restrict__ num_units) {
-  __shared__ int sp[1024], su[1024];
-  __shared__ int carry_p, carry_u;
-  if (threadIdx.x == 0) { carry_p = 0; carry_u = 0; }
+// Single block: exclusive scans of points and of the work units per tile at
+// two unit sizes (spread units of unit_a points, gather units of unit_b).
+__global__ void k_bin_scan(int* __restrict__ count, int tiles, int unit_a, int unit_b,
+                           int* __restrict__ tile_start, int* __restrict__ tus_a,
+                           int* __restrict__ num_a, int* __restrict__ tus_b,
+                           int* __restrict__ num_b) {
+  __shared__ int sp[1024], sa[1024], sb[1024];
+  __shared__ int carry_p, carry_a, carry_b;
+  if (threadIdx.x == 0) { carry_p = 0; carry_a = 0; carry_b = 0; }
   __syncthreads();
   for (int base = 0; base < tiles; base += 1024) {
     const int i = base + threadIdx.x;
     const int c = i < tiles ? count[i] : 0;
+    const int ca = (c + unit_a - 1) / unit_a, cb = (c + unit_b - 1) / unit_b;
     sp[threadIdx.x] = c;
-    su[threadIdx.x] = (c + unit_pts - 1) / unit_pts;
+    sa[threadIdx.x] = ca;
+    sb[threadIdx.x] = cb;
     __syncthreads();
     for (int o = 1; o < 1024; o <<= 1) {
-      const int a = threadIdx.x >= o ? sp[threadIdx.x - o] : 0;
-      const int b = threadIdx.x >= o ? su[threadIdx.x - o] : 0;
+      const int x = threadIdx.x >= o ? sp[threadIdx.x - o] : 0;
+      const int y = threadIdx.x >= o ? sa[threadIdx.x - o] : 0;
+      const int z = threadIdx.x >= o ? sb[threadIdx.x - o] : 0;
       __syncthreads();
-      sp[threadIdx.x] += a;
-      su[threadIdx.x] += b;
+      sp[threadIdx.x] += x;
+      sa[threadIdx.x] += y;
+      sb[threadIdx.x] += z;
       __syncthreads();
     }
     if (i < tiles) {
       tile_start[i] = carry_p + sp[threadIdx.x] - c;
-      tile_unit_start[i] = carry_u + su[threadIdx.x] - (c + unit_pts - 1) / unit_pts;
-      count[i] = 0;  // reused as the scatter cursor
+      tus_a[i] = carry_a + sa[threadIdx.x] - ca;
+      tus_b[i] = carry_b + sb[threadIdx.x] - cb;
     }
     __syncthreads();
-    if (threadIdx.x == 1023) { carry_p += sp[1023]; carry_u += su[1023]; }
+    if (threadIdx.x == 1023) {
+      carry_p += sp[1023];
+      carry_a += sa[1023];
+      carry_b += sb[1023];
+    }
     __syncthreads();
   }
   if (threadIdx.x == 0) {
     tile_start[tiles] = carry_p;
-    tile_unit_start[tiles] = carry_u;
-    *num_units = carry_u;
+    tus_a[tiles] = carry_a;
+    tus_b[tiles] = carry_b;
+    *num_a = carry_a;
+    *num_b = carry_b;
   }
 }
 
-__global__ void k_bin_scatter(const int4* __restrict__ tmp_cell, const int* __restrict__ tmp_key,
-                              long long n, const int* __restrict__ cell_start,
-                              int* __restrict__ cursor, int4* __restrict__ cell,
-                              int* __restrict__ ckey, int* __restrict__ perm) {
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int k = tmp_key[i];
-    const int pos = cell_start[k] + atomicAdd(&cursor[k], 1);
+// Stable LSD radix sort of the cell keys, 8-bit digits: the points of one cell
+// keep their caller order, so the sorted order (and every FP32 sum taken in it)
+// is the same on every run.  A CTA owns RS_TILE consecutive elements; its
+// per-digit counts go digit-major into hist[digit * blocks + cta], whose
+// exclusive scan gives each (digit, CTA) its first output position.
+constexpr int RS_THREADS = 256;
+constexpr int RS_ITEMS = 16;
+constexpr int RS_TILE = RS_THREADS * RS_ITEMS;
+
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_hist(const int* __restrict__ keys, long long n, int shift, int blocks,
+              int* __restrict__ hist) {
+  __shared__ int h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const long long b0 = (long long)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const long long i = b0 + (long long)r * RS_THREADS + threadIdx.x;
+    if (i < n) atomicAdd(&h[(keys[i] >> shift) & 255], 1);  // integer counts: order-free
+  }
+  __syncthreads();
+  hist[threadIdx.x * blocks + blockIdx.x] = h[threadIdx.x];
+}
+
+// Element i of the CTA's tile goes to start[digit][cta] + (number of earlier
+// elements of the tile with the same digit): earlier rounds (base), earlier
+// warps of this round (cnt), earlier lanes of this warp (match mask).
+__global__ void __launch_bounds__(RS_THREADS)
+    k_rs_scatter(const int* __restrict__ kin, const int* __restrict__ vin, long long n, int shift,
+                 int blocks, const int* __restrict__ start, int* __restrict__ kout,
+                 int* __restrict__ vout) {
+  constexpr int NW = RS_THREADS / 32;
+  __shared__ int base[256];
+  __shared__ int cnt[NW][256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  base[threadIdx.x] = start[threadIdx.x * blocks + blockIdx.x];
+  for (int k = threadIdx.x; k < NW * 256; k += RS_THREADS) (&cnt[0][0])[k] = 0;
+  __syncthreads();
+  const long long b0 = (long long)blockIdx.x * RS_TILE;
+  for (int r = 0; r < RS_ITEMS; ++r) {
+    const long long i = b0 + (long long)r * RS_THREADS + threadIdx.x;
+    const bool valid = i < n;
+    const int key = valid ? kin[i] : 0;
+    // lanes past the end take distinct out-of-range digits: no peers, no counts
+    const int dg = valid ? (key >> shift) & 255 : 256 + lane;
+    const unsigned peers = __match_any_sync(0xffffffffu, dg);
+    const int rank = __popc(peers & ((1u << lane) - 1u));
+    const bool leader = rank == 0;
+    if (valid && leader) cnt[w][dg] = __popc(peers);
+    __syncthreads();
+    int pos = 0;
+    if (valid) {
+      pos = base[dg] + rank;
+      for (int w2 = 0; w2 < w; ++w2) pos += cnt[w2][dg];
+    }
+    __syncthreads();
+    if (valid && leader) {
+      atomicAdd(&base[dg], __popc(peers));  // integer: order-free
+      cnt[w][dg] = 0;
+    }
+    if (valid) {
+      kout[pos] = key;
+      vout[pos] = vin ? vin[i] : (int)i;
+    }
+    __syncthreads();
+  }
+}
+
+// Sorted position -> packed cell, key and caller index.
+__global__ void k_bin_place(const int4* __restrict__ tmp_cell, const int* __restrict__ order,
+                            long long n, int4* __restrict__ cell, int* __restrict__ ckey,
+                            int* __restrict__ perm) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < n;
+       p += (long long)gridDim.x * blockDim.x) {
+    const int i = order[p];
     const int4 c = tmp_cell[i];
-    cell[pos] = c;
-    ckey[pos] = c.x;
-    perm[pos] = (int)i;
+    cell[p] = c;
+    ckey[p] = c.x;
+    perm[p] = i;
   }
 }
 
+// Units of at most unit_pts points per tile; zr (optional) gets the first and
+// last local z cell of each unit (cells are ordered z-major inside a tile).
 __global__ void k_make_units(const int* __restrict__ tile_start,
                              const int* __restrict__ tile_unit_start, int tiles, int unit_pts,
-                             int* __restrict__ unit_tile, int* __restrict__ unit_begin,
-                             int* __restrict__ unit_count) {
+                             const int* __restrict__ ckey, int* __restrict__ unit_tile,
+                             int* __restrict__ unit_begin, int* __restrict__ unit_count,
+                             int* __restrict__ zr) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
     const int b = tile_start[t], e = tile_start[t + 1];
     int u = tile_unit_start[t];
     for (int p = b; p < e; p += unit_pts, ++u) {
+      const int c = min(unit_pts, e - p);
       unit_tile[u] = t;
       unit_begin[u] = p;
-      unit_count[u] = min(unit_pts, e - p);
+      unit_count[u] = c;
+      if (zr) {
+        const int z0 = (ckey[p] >> 20) % NFFT_TILE, z1 = (ckey[p + c - 1] >> 20) % NFFT_TILE;
+        zr[u] = z0 | (z1 << 8);
+      }
     }
   }
 }
@@ -290,11 +377,41 @@ __global__ void k_windows(const int4* __restrict__ cell, long long n, int m, flo
   }
 }
 
+
+// Pair window rows: row p holds, for every window value, the pair (point 2p,
+// point 2p + 1); a missing second point (odd n) gets zeros.
+__global__ void k_windows_pair(const int4* __restrict__ cell, long long n, int m, float b,
+                               float* __restrict__ win) {
+  const int ws = nfft_winp_stride(m), hp = nfft_winp_half(m);
+  const int yo = nfft_winp_yoff(m), zo = nfft_winp_zoff(m);
+  const long long np = (n + 1) / 2;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np * ws;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long p = i / ws;
+    const int r = (int)(i - p * ws);
+    int t, k, lane;
+    if (r < yo) {
+      const int h = r / hp, rem = r - h * hp;
+      if (rem >= 2 * m) { win[i] = 0.f; continue; }
+      t = 0; k = h * m + (rem >> 1); lane = rem & 1;
+    } else if (r < zo) {
+      t = 1; k = (r - yo) >> 1; lane = (r - yo) & 1;
+    } else {
+      t = 2; k = (r - zo) >> 1; lane = (r - zo) & 1;
+    }
+    const long long q = 2 * p + lane;
+    if (q >= n) { win[i] = 0.f; continue; }
+    const int4 c = cell[q];
+    const float f = __int_as_float(t == 0 ? c.y : (t == 1 ? c.z : c.w));
+    win[i] = kb_window(f + (float)(m - 1 - k), m, b);
+  }
+}
+
 }  // namespace
 
-int nfft_max_units(const NfftParams& P, int64_t n) {
+int nfft_max_units(const NfftParams& P, int64_t n, int unit_points) {
   const int64_t tiles = (int64_t)P.tiles1 * P.tiles1 * P.tiles1;
-  return (int)((n + NFFT_UNIT_POINTS - 1) / NFFT_UNIT_POINTS + (n < tiles ? n : tiles));
+  return (int)((n + unit_points - 1) / unit_points + (n < tiles ? n : tiles));
 }
 
 uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const float hi[3],
@@ -449,25 +566,40 @@ void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S
   const int tiles = P.tiles1 * P.tiles1 * P.tiles1;
   const int64_t nn = n > 0 ? n : 1;
   S.n = n;
-  S.max_units = nfft_max_units(P, n);
+  S.max_units = nfft_max_units(P, n, NFFT_SPREAD_UNIT);
+  S.g_max_units = nfft_max_units(P, n, NFFT_GATHER_UNIT);
   S.cell = cv.take<int4>(nn);
   S.ckey = cv.take<int>(nn + 4);
   S.win = cv.take<float>((size_t)nn * nfft_win_stride(P.m));
+  S.winp = cv.take<float>((size_t)((nn + 1) / 2) * nfft_winp_stride(P.m));
   S.perm = cv.take<int>(nn);
   S.tile_start = cv.take<int>(tiles + 1);
   S.tile_unit_start = cv.take<int>(tiles + 1);
   S.unit_tile = cv.take<int>(S.max_units + 1);
   S.unit_begin = cv.take<int>(S.max_units + 1);
   S.unit_count = cv.take<int>(S.max_units + 1);
+  S.unit_zr = cv.take<int>(S.max_units + 1);
   S.num_units = cv.take<int>(1);
+  S.g_tile_unit_start = cv.take<int>(tiles + 1);
+  S.g_unit_tile = cv.take<int>(S.g_max_units + 1);
+  S.g_unit_begin = cv.take<int>(S.g_max_units + 1);
+  S.g_unit_count = cv.take<int>(S.g_max_units + 1);
+  S.g_num_units = cv.take<int>(1);
   S.scratch = cv.take<int>(tiles);
   const long long n3 = (long long)P.n * P.n * P.n;
   S.cell_count = cv.take<int>(n3);
   S.cell_start = cv.take<int>(n3 + 1);
   S.block_sums = cv.take<int>(n3 / 2048 + 2);
-  // temporaries of the build (caller order)
-  cv.take<int4>(nn);
-  cv.take<int>(nn);
+  // temporaries of the build: caller-order cells and the radix sort buffers
+  const int64_t rb = (nn + RS_TILE - 1) / RS_TILE;
+  S.tmp_cell = cv.take<int4>(nn);
+  for (int k = 0; k < 2; ++k) {
+    S.rs_key[k] = cv.take<int>(nn);
+    S.rs_val[k] = cv.take<int>(nn);
+  }
+  S.rs_hist = cv.take<int>(256 * rb + 1);
+  S.rs_start = cv.take<int>(256 * rb + 1);
+  S.rs_bsum = cv.take<int>((256 * rb) / SCAN_BLOCK + 2);
 }
 
 uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
@@ -475,18 +607,13 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
   const int tiles = P.tiles1 * P.tiles1 * P.tiles1;
   const long long n3 = (long long)P.n * P.n * P.n;
   const int nb = (int)((n3 + SCAN_BLOCK - 1) / SCAN_BLOCK);
-  // the temporaries sit right after `block_sums` (see nfft_points_carve)
-  Carver cv(reinterpret_cast<char*>(S.block_sums));
-  cv.take<int>(n3 / 2048 + 2);
-  int4* tmp_cell = cv.take<int4>(n > 0 ? n : 1);
-  int* tmp_key = cv.take<int>(n > 0 ? n : 1);
   CellRule R{{P.c[0], P.c[1], P.c[2]}, P.inv_h, P.n, P.d};
   {
     UOTK_PROF(ctx, s, "bin");
     UOTK_CUDA(ctx, cudaMemsetAsync(S.cell_count, 0, sizeof(int) * n3, s));
     if (n > 0) {
-      k_bin_count<<<grid_for(ctx, n, 256), 256, 0, s>>>(pts, n, R, P.tiles1, tmp_cell, tmp_key,
-                                                         S.cell_count);
+      k_bin_count<<<grid_for(ctx, n, 256), 256, 0, s>>>(pts, n, R, P.tiles1, S.tmp_cell,
+                                                         S.rs_key[0], S.cell_count);
       UOTK_LAUNCHED(ctx);
     }
     k_scan_local<<<nb, 1024, 0, s>>>(S.cell_count, n3, S.cell_start, S.block_sums);
@@ -497,23 +624,53 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
     UOTK_LAUNCHED(ctx);
     k_tile_counts<<<grid_for(ctx, tiles, 256), 256, 0, s>>>(S.cell_start, tiles, S.scratch);
     UOTK_LAUNCHED(ctx);
-    k_bin_scan<<<1, 1024, 0, s>>>(S.scratch, tiles, NFFT_UNIT_POINTS, S.tile_start,
-                                  S.tile_unit_start, S.num_units);
+    k_bin_scan<<<1, 1024, 0, s>>>(S.scratch, tiles, NFFT_SPREAD_UNIT, NFFT_GATHER_UNIT,
+                                  S.tile_start, S.tile_unit_start, S.num_units,
+                                  S.g_tile_unit_start, S.g_num_units);
     UOTK_LAUNCHED(ctx);
     if (n > 0) {
-      k_bin_scatter<<<grid_for(ctx, n, 256), 256, 0, s>>>(tmp_cell, tmp_key, n, S.cell_start,
-                                                           S.cell_count, S.cell, S.ckey, S.perm);
+      // stable sort by cell key: ceil(bits / 8) passes over the key's bits
+      int bits = 0;
+      while ((1LL << bits) < n3) ++bits;
+      const int rb = (int)((n + RS_TILE - 1) / RS_TILE);
+      const long long hn = 256LL * rb;
+      const int hb = (int)((hn + SCAN_BLOCK - 1) / SCAN_BLOCK);
+      int cur = 0;
+      for (int shift = 0; shift < bits; shift += 8, cur ^= 1) {
+        k_rs_hist<<<rb, RS_THREADS, 0, s>>>(S.rs_key[cur], n, shift, rb, S.rs_hist);
+        UOTK_LAUNCHED(ctx);
+        k_scan_local<<<hb, 1024, 0, s>>>(S.rs_hist, hn, S.rs_start, S.rs_bsum);
+        UOTK_LAUNCHED(ctx);
+        k_scan_top<<<1, 1024, 0, s>>>(S.rs_bsum, hb);
+        UOTK_LAUNCHED(ctx);
+        k_scan_add<<<grid_for(ctx, hn, 256), 256, 0, s>>>(S.rs_start, hn, S.rs_bsum, hb);
+        UOTK_LAUNCHED(ctx);
+        k_rs_scatter<<<rb, RS_THREADS, 0, s>>>(S.rs_key[cur], shift == 0 ? nullptr : S.rs_val[cur],
+                                               n, shift, rb, S.rs_start, S.rs_key[cur ^ 1],
+                                               S.rs_val[cur ^ 1]);
+        UOTK_LAUNCHED(ctx);
+      }
+      k_bin_place<<<grid_for(ctx, n, 256), 256, 0, s>>>(S.tmp_cell, S.rs_val[cur], n, S.cell,
+                                                         S.ckey, S.perm);
       UOTK_LAUNCHED(ctx);
     }
     k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.tile_unit_start, tiles,
-                                                          NFFT_UNIT_POINTS, S.unit_tile,
-                                                          S.unit_begin, S.unit_count);
+                                                          NFFT_SPREAD_UNIT, S.ckey, S.unit_tile,
+                                                          S.unit_begin, S.unit_count, S.unit_zr);
+    UOTK_LAUNCHED(ctx);
+    k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.g_tile_unit_start,
+                                                          tiles, NFFT_GATHER_UNIT, S.ckey,
+                                                          S.g_unit_tile, S.g_unit_begin,
+                                                          S.g_unit_count, nullptr);
     UOTK_LAUNCHED(ctx);
   }
   if (n > 0) {
     UOTK_PROF(ctx, s, "window");
     k_windows<<<grid_for(ctx, n * nfft_win_stride(P.m), 256), 256, 0, s>>>(S.cell, n, P.m, P.b,
                                                                          P.d, S.win);
+    UOTK_LAUNCHED(ctx);
+    k_windows_pair<<<grid_for(ctx, (n + 1) / 2 * nfft_winp_stride(P.m), 256), 256, 0, s>>>(
+        S.cell, n, P.m, P.b, S.winp);
     UOTK_LAUNCHED(ctx);
   }
   return UOTK_OK;

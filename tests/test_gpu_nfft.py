@@ -83,6 +83,58 @@ def test_spread_stage(uotk, d):
     assert np.max(np.abs(g - want)) <= 2e-5 * np.max(np.abs(want))
 
 
+@pytest.mark.parametrize("grid,cutoff", [(16, 6), (16, 3)])
+def test_spread_stage_small_grids(uotk, grid, cutoff):
+    """The smallest grid, two tiles per axis: the tile offsets -1 and +1 of the
+    fold name the same tile, whose block wraps onto itself and covers some nodes
+    twice (the torus case of the fixed-order fold)."""
+    src = cloud(11, 2500, 3, "gmm")
+    w = inputs.rng(12).uniform(0.2, 2.0, 2500).astype(np.float32)
+    p, P = plan_for(uotk, src, src, 0.02, grid=grid, cutoff=cutoff, period=1.0)
+    g = uotk.nfft_spread(p, dev(src), dev(w)).cpu().numpy().astype(np.float64)
+    u = torus(P, src)
+    want = onf.spread(u, f64(w), P["grid"], P["bandwidth"], P["cutoff"])
+    want = np.transpose(want, (2, 1, 0)) / onf.kb_phi(np.zeros(1), P["grid"], P["bandwidth"],
+                                                      P["cutoff"])[0] ** 3
+    assert np.max(np.abs(g - want)) <= 2e-5 * np.max(np.abs(want))
+
+
+def test_spread_and_sum_are_deterministic(uotk):
+    """The spread stage and the NFFT kernel sum give bit-identical results on
+    repeated calls, also from a second context (other workspace addresses):
+    the points of a cell keep their caller order (stable binning) and the unit
+    blocks are folded into the grid in a fixed order, without atomics."""
+    src = cloud(13, 30000, 3, "gmm")
+    tgt = cloud(14, 20001, 3, "gmm")
+    w = inputs.rng(15).lognormal(0.0, 0.5, 30000).astype(np.float32)
+    p, P = plan_for(uotk, src, tgt, 0.02)
+    g1 = uotk.nfft_spread(p, dev(src), dev(w))
+    g2 = uotk.nfft_spread(p, dev(src), dev(w))
+    assert torch.equal(g1, g2)
+    s1 = uotk.kernel_sum(dev(src), dev(w), dev(tgt), 0.02, method="nfft")
+    s2 = uotk.kernel_sum(dev(src), dev(w), dev(tgt), 0.02, method="nfft")
+    ctx2 = uotk.Context(0)
+    s3 = uotk.kernel_sum(dev(src), dev(w), dev(tgt), 0.02, method="nfft", ctx=ctx2)
+    ctx2.close()
+    assert torch.equal(s1, s2) and torch.equal(s1, s3)
+
+
+def test_sinkhorn_nfft_is_deterministic(uotk):
+    """Alg. 2 solved twice on the graph path, and once with eager launches
+    (per-stage profiling on), gives bit-identical duals and dual values."""
+    W = inputs.gmm3(seed=2007, n=40000, m=33001)
+    args = (dev(W.x), dev(W.a), dev(W.y), dev(W.b), W.eps, W.rho)
+    ctx = uotk.Context(0)
+    r1 = uotk.uot_sinkhorn(*args, max_sweeps=24, method="nfft", ctx=ctx)
+    r2 = uotk.uot_sinkhorn(*args, max_sweeps=24, method="nfft", ctx=ctx)
+    ctx.set_profiling(True)
+    r3 = uotk.uot_sinkhorn(*args, max_sweeps=24, method="nfft", ctx=ctx)
+    ctx.set_profiling(False)
+    ctx.close()
+    for r in (r2, r3):
+        assert torch.equal(r1[0], r[0]) and torch.equal(r1[1], r[1]) and r1[3] == r[3]
+
+
 def test_convolve_stage(uotk):
     src = cloud(5, 2000, 3)
     p, P = plan_for(uotk, src, src, 0.05, grid=64)
@@ -202,12 +254,13 @@ def test_sinkhorn_nfft_tracking_warm_start(uotk, ref):
 
 @pytest.mark.parametrize("cutoff", [3, 4, 5, 7, 8])
 def test_sinkhorn_nfft_cutoffs(uotk, cutoff):
-    """Alg. 2 at every other window cut-off: the spread forms the weights with
-    the CTA's threads 0.. (m = 4), threads 32.. (m >= 5), or takes them from a
-    separate kernel (m = 3); the gather runs without its footprint cache at
-    m >= 7.  Against the FP64 Alg. 1 after 30 sweeps, both reference measures.
-    Tolerances follow the window error bound of the cut-off (R8: ~1e-4 at m = 3
-    down to below 1e-7 at m = 7)."""
+    """Alg. 2 at every other window cut-off: the spread's thread boxes and
+    weight threads differ with m (several chunk points per weight thread at
+    m = 3, 5, 7), the gather is the per-warp form at m = 4 and the CTA-staged
+    form at m = 3, 5, 7, 8 (without its footprint cache at m >= 7).  Against the
+    FP64 Alg. 1 after 30 sweeps, both reference measures.  Tolerances follow the
+    Kaiser-Bessel error bound of the cut-off (about 1e-4 at m = 3, below 1e-7
+    at m = 7)."""
     W = inputs.gmm3(seed=2006, n=2000, m=1500)
     ref = "counting" if cutoff in (4, 8) else "product"
     r = 0 if ref == "product" else 1

@@ -5,12 +5,15 @@ scratch is a fixed array inside the library, shared by every call on a device.
 
 The test calls it through the C ABI twice in a row on different inputs -- the
 second call must not see anything the first left in the shared scratch -- and
-compares each result with uotk_kernel_sum, the context-based entry point, at the
-direct form's tolerance (2e-6 relative per output).  This file is collected
-last, and passes both alone in a fresh process and after the other tests."""
+compares each result with uotk_kernel_sum, the context-based entry point, and
+with the FP64 oracle's kernel sum, at the direct form's tolerance (2e-6
+relative per output).  With no sources the output must be all zeros.  This file
+is collected last, and passes both alone in a fresh process and after the
+other tests."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2306_13618_gb300 import inputs
 
 torch = pytest.importorskip("torch")
@@ -42,6 +45,19 @@ def test_noalloc_matches_kernel_sum_twice(uotk):
         torch.cuda.synchronize()
         rel = ((out.double() - ref.double()).abs() / ref.double()).max().item()
         assert rel <= 2e-6, rel
+        exact = oracle.ksum(src.cpu().double().numpy(), w.cpu().double().numpy(),
+                            tgt.cpu().double().numpy(), eps)
+        rel = np.max(np.abs(out.cpu().double().numpy() - exact) / exact)
+        assert rel <= 2e-6, rel
+
+
+def test_noalloc_no_sources_gives_zeros(uotk):
+    _, _, tgt = _case(505, 10, 333, 3)
+    src = torch.zeros((0, 3), device="cuda")
+    out = torch.full((333,), float("nan"), device="cuda")
+    assert uotk.kernel_sum_noalloc(src, torch.zeros(0, device="cuda"), tgt, 0.05, out) == 0
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
 
 
 def test_noalloc_rejects_oversize_and_bad_weights(uotk):
