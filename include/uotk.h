@@ -147,6 +147,22 @@ uotk_status uotk_set_profiling(uotk_ctx* ctx, int enable);
 int uotk_profile_read(uotk_ctx* ctx, char* names, int cap, int64_t* counts, double* ms, int max);
 void uotk_profile_reset(uotk_ctx* ctx);
 
+/* Failure-path controls (the paper has none; they let a caller, and the tests,
+ * reach the NOMEM and TIMEOUT statuses without any device fault).
+ * uotk_set_workspace_limit: the largest device workspace, in bytes, the context
+ * may hold (0: no limit, the default).  A call that needs more returns
+ * UOTK_ERR_NOMEM before it launches anything; the context stays usable.
+ * uotk_set_wait_timeout_test: with cycles > 0, the first bounded wait of each
+ * CTA of the NFFT spread and gather kernels waits on a barrier that nothing
+ * completes, for at most `cycles` clock cycles, so that it times out; 0 (the
+ * default) turns this off.  A wait that times out records it, waits (with the
+ * normal limit of about 2^31 cycles) for the CTA's bulk copies still in
+ * flight, and the CTA leaves; the call returns UOTK_ERR_TIMEOUT and its outputs
+ * are not valid.  Both return UOTK_ERR_INVALID for a NULL context or a
+ * negative value. */
+uotk_status uotk_set_workspace_limit(uotk_ctx* ctx, int64_t bytes);
+uotk_status uotk_set_wait_timeout_test(uotk_ctx* ctx, int64_t cycles);
+
 /* Unit throughputs of this GPU (instrumentation for roofline denominators; the
  * paper has no counterpart).  Runs one CTA of 1024 threads per SM, each
  * thread 16 independent chains of 4096 ex2.approx.ftz.f32 (then of FP32 FMA),

@@ -55,9 +55,19 @@ uotk_status set_error(uotk_ctx* ctx, uotk_status st, const char* fmt, ...) {
   return st;
 }
 
+uotk_status stream_fence(uotk_ctx* ctx, cudaStream_t from, cudaStream_t to, cudaEvent_t ev) {
+  UOTK_CUDA(ctx, cudaEventRecord(ev, from));
+  UOTK_CUDA(ctx, cudaStreamWaitEvent(to, ev, 0));
+  return UOTK_OK;
+}
+
 uotk_status ws_reserve(uotk_ctx* ctx, size_t bytes) {
   if (bytes <= ctx->ws_cap) return UOTK_OK;
+  if (ctx->ws_limit && bytes > ctx->ws_limit)
+    return set_error(ctx, UOTK_ERR_NOMEM, "workspace of %zu bytes needed, above the limit of %zu",
+                     bytes, ctx->ws_limit);
   size_t want = bytes + bytes / 8 + (1 << 20);
+  if (ctx->ws_limit && want > ctx->ws_limit) want = ctx->ws_limit;
   if (ctx->ws) {
     UOTK_CUDA(ctx, cudaDeviceSynchronize());
     cudaFree(ctx->ws);
@@ -215,6 +225,17 @@ uotk_status uotk_create(uotk_ctx** out, int device) {
     delete ctx;
     return UOTK_ERR_NOMEM;
   }
+  if (cudaStreamCreateWithFlags(&ctx->gs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->fence_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->fence_out, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (ctx->gs) cudaStreamDestroy(ctx->gs);
+    if (ctx->fence_in) cudaEventDestroy(ctx->fence_in);
+    cudaFree(ctx->dflags);
+    cudaFreeHost(ctx->host);
+    delete ctx;
+    return UOTK_ERR_CUDA;
+  }
   cudaMemset(ctx->dflags, 0, NUM_FLAGS * sizeof(long long));
   cudaDeviceSynchronize();
   *out = ctx;
@@ -230,8 +251,12 @@ void uotk_destroy(uotk_ctx* ctx) {
   if (ctx->host) cudaFreeHost(ctx->host);
   if (ctx->prof.created)
     for (int i = 0; i < 2 * UOTK_PROF_POOL; ++i) cudaEventDestroy(ctx->prof.ev[i]);
+  if (ctx->gs) cudaStreamDestroy(ctx->gs);
+  if (ctx->fence_in) cudaEventDestroy(ctx->fence_in);
+  if (ctx->fence_out) cudaEventDestroy(ctx->fence_out);
   delete ctx;
 }
+
 
 const char* uotk_last_error(const uotk_ctx* ctx) { return ctx ? ctx->err : "null context"; }
 
@@ -262,6 +287,21 @@ uotk_status uotk_set_profiling(uotk_ctx* ctx, int enable) {
   }
   if (!enable) prof_fold(ctx);
   P.on = enable != 0;
+  return UOTK_OK;
+}
+
+uotk_status uotk_set_workspace_limit(uotk_ctx* ctx, int64_t bytes) {
+  if (!ctx) return UOTK_ERR_INVALID;
+  if (bytes < 0) return set_error(ctx, UOTK_ERR_INVALID, "workspace limit %lld < 0", (long long)bytes);
+  ctx->ws_limit = (size_t)bytes;
+  return UOTK_OK;
+}
+
+uotk_status uotk_set_wait_timeout_test(uotk_ctx* ctx, int64_t cycles) {
+  if (!ctx) return UOTK_ERR_INVALID;
+  if (cycles < 0)
+    return set_error(ctx, UOTK_ERR_INVALID, "wait time-out test: %lld cycles < 0", (long long)cycles);
+  ctx->wait_test = (long long)cycles;
   return UOTK_OK;
 }
 

@@ -5,11 +5,15 @@
 // Every half-step of every pair is one grouped launch: a table of work items
 // (pair, target block, source split) built once per call assigns CTAs to
 // pairs, so a sweep over all pairs costs six launches whatever their number,
-// and two sweeps are replayed from one CUDA graph.  Per-pair state (shift
-// maxima, convergence deltas) lives in per-pair slots that alternate with the
-// sweep parity exactly as in the single-problem solver.  Every 10 sweeps the
-// host reads the deltas and retires the pairs that met the tolerance: their
-// CTAs return at once in later sweeps, and their duals stay as they were.
+// and the sweep loop runs on the device: one CUDA graph whose WHILE
+// conditional node repeats a body of two sweeps and a control kernel.  Per-pair
+// state (shift maxima, convergence deltas) lives in per-pair slots that
+// alternate with the sweep parity exactly as in the single-problem solver.
+// After every body the control kernel retires the pairs whose last change met
+// the tolerance (their CTAs return at once in later sweeps, and their duals stay
+// as they were) and ends the loop when none is left or the sweep cap is near:
+// no host round trip inside the loop.  With per-stage profiling on, the
+// launches stay eager and the host checks the deltas every 10 sweeps.
 #include <math.h>
 #include <string.h>
 
@@ -237,6 +241,40 @@ __global__ void k_batch_values(const PairDev* __restrict__ pairs, const float* _
     for (int k = 0; k < 5; ++k) out[(long long)p * 5 + k] = v[k];
 }
 
+// Loop control after a body of two sweeps (one CTA): state[0] = sweeps done
+// before the body, state[1] = pairs still active after it.  A pair whose
+// largest change lambda |delta| in the body's last sweep is below tol retires
+// with its sweep count; the WHILE condition drops to 0 when no pair is left or
+// another body would pass max_sweeps.
+__global__ void k_batch_control(int npairs, int* __restrict__ active, int* __restrict__ dsweeps,
+                                const long long* __restrict__ slots, int* __restrict__ state,
+                                double tol, int max_sweeps, cudaGraphConditionalHandle cond) {
+  __shared__ int rem[32];
+  const int done = state[0] + 2;
+  const int par = (done - 1) & 1;
+  int r = 0;
+  for (int p = threadIdx.x; p < npairs; p += blockDim.x) {
+    if (!active[p]) continue;
+    if (tol > 0.0 &&
+        ordered_to_dbl(slots[(long long)p * SL_COUNT + SL_DELTA0 + par]) < tol) {
+      active[p] = 0;
+      dsweeps[p] = done;
+      continue;
+    }
+    ++r;
+  }
+  r = warp_sum(r);
+  if ((threadIdx.x & 31) == 0) rem[threadIdx.x >> 5] = r;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) total += rem[w];
+    state[0] = done;
+    state[1] = total;
+    if (total == 0 || done + 2 > max_sweeps) cudaGraphSetConditional(cond, 0);
+  }
+}
+
 template <class T>
 uotk_status upload(uotk_ctx* ctx, cudaStream_t s, T* dst, const std::vector<T>& src) {
   if (src.empty()) return UOTK_OK;
@@ -301,8 +339,11 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
   // ---- workspace ----
   auto carve = [&](Carver& cv, PairDev** dp, SumItem** dsx, SumItem** dsy, ElemItem** dex,
                    ElemItem** dey, int** act, long long** slots, int** lastpar, float4** dpx,
-                   float4** dpy, float** dpartx, float** dparty, float** ty, double** vals) {
+                   float4** dpy, float** dpartx, float** dparty, float** ty, double** vals,
+                   int** dsw, int** state) {
     *dp = cv.take<PairDev>(npairs);
+    *dsw = cv.take<int>(npairs);
+    *state = cv.take<int>(2);
     *dsx = cv.take<SumItem>(sx.size() ? sx.size() : 1);
     *dsy = cv.take<SumItem>(sy.size() ? sy.size() : 1);
     *dex = cv.take<ElemItem>(ex.size() ? ex.size() : 1);
@@ -325,15 +366,16 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
   float4 *dPX, *dPY;
   float *partX, *partY, *ty;
   double* vals;
+  int *dsw, *state;
   {
     Carver size(nullptr);
     carve(size, &dP, &dSX, &dSY, &dEX, &dEY, &act, &slots, &lastpar, &dPX, &dPY, &partX, &partY,
-          &ty, &vals);
+          &ty, &vals, &dsw, &state);
     UOTK_TRY(ws_reserve(ctx, size.off));
   }
   Carver cv(ctx->ws);
   carve(cv, &dP, &dSX, &dSY, &dEX, &dEY, &act, &slots, &lastpar, &dPX, &dPY, &partX, &partY, &ty,
-        &vals);
+        &vals, &dsw, &state);
   (void)total_n;
 
   UOTK_TRY(flags_reset(ctx, s));
@@ -359,51 +401,54 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
 
   // ---- the sweep loop (shared structure with the single-problem solver) ----
   const bool track = tol > 0.0;
+  // the stream of the sweeps: the caller's, or the context's own stream while
+  // the device loop is captured and run
+  cudaStream_t cs = s;
   auto sum_x = [&]() -> uotk_status {
     if (sx.empty()) return UOTK_OK;
-    UOTK_PROF(ctx, s, "direct");
-    if (d == 1) k_batch_sum<0, 1><<<(unsigned)sx.size(), DIRECT_THREADS, 0, s>>>(dSX, dP, act, dPX, dPY, partX, ctx->dflags);
-    else if (d == 2) k_batch_sum<0, 2><<<(unsigned)sx.size(), DIRECT_THREADS, 0, s>>>(dSX, dP, act, dPX, dPY, partX, ctx->dflags);
-    else k_batch_sum<0, 3><<<(unsigned)sx.size(), DIRECT_THREADS, 0, s>>>(dSX, dP, act, dPX, dPY, partX, ctx->dflags);
+    UOTK_PROF(ctx, cs, "direct");
+    if (d == 1) k_batch_sum<0, 1><<<(unsigned)sx.size(), DIRECT_THREADS, 0, cs>>>(dSX, dP, act, dPX, dPY, partX, ctx->dflags);
+    else if (d == 2) k_batch_sum<0, 2><<<(unsigned)sx.size(), DIRECT_THREADS, 0, cs>>>(dSX, dP, act, dPX, dPY, partX, ctx->dflags);
+    else k_batch_sum<0, 3><<<(unsigned)sx.size(), DIRECT_THREADS, 0, cs>>>(dSX, dP, act, dPX, dPY, partX, ctx->dflags);
     UOTK_LAUNCHED(ctx);
     return UOTK_OK;
   };
   auto sum_y = [&]() -> uotk_status {
     if (sy.empty()) return UOTK_OK;
-    UOTK_PROF(ctx, s, "direct");
-    if (d == 1) k_batch_sum<1, 1><<<(unsigned)sy.size(), DIRECT_THREADS, 0, s>>>(dSY, dP, act, dPX, dPY, partY, ctx->dflags);
-    else if (d == 2) k_batch_sum<1, 2><<<(unsigned)sy.size(), DIRECT_THREADS, 0, s>>>(dSY, dP, act, dPX, dPY, partY, ctx->dflags);
-    else k_batch_sum<1, 3><<<(unsigned)sy.size(), DIRECT_THREADS, 0, s>>>(dSY, dP, act, dPX, dPY, partY, ctx->dflags);
+    UOTK_PROF(ctx, cs, "direct");
+    if (d == 1) k_batch_sum<1, 1><<<(unsigned)sy.size(), DIRECT_THREADS, 0, cs>>>(dSY, dP, act, dPX, dPY, partY, ctx->dflags);
+    else if (d == 2) k_batch_sum<1, 2><<<(unsigned)sy.size(), DIRECT_THREADS, 0, cs>>>(dSY, dP, act, dPX, dPY, partY, ctx->dflags);
+    else k_batch_sum<1, 3><<<(unsigned)sy.size(), DIRECT_THREADS, 0, cs>>>(dSY, dP, act, dPX, dPY, partY, ctx->dflags);
     UOTK_LAUNCHED(ctx);
     return UOTK_OK;
   };
   auto sweep = [&](int sw) -> uotk_status {
     const int cur = sw & 1, nxt = cur ^ 1;
     {
-      UOTK_PROF(ctx, s, "weights");
-      k_batch_weights<0><<<(unsigned)ey.size(), 256, 0, s>>>(dEY, dP, act, ref == 0 ? b : nullptr,
+      UOTK_PROF(ctx, cs, "weights");
+      k_batch_weights<0><<<(unsigned)ey.size(), 256, 0, cs>>>(dEY, dP, act, ref == 0 ? b : nullptr,
                                                              gamma, slots, SL_MAXG0 + cur, dPY);
     }
     UOTK_LAUNCHED(ctx);
     UOTK_TRY(sum_x());
     {
-      UOTK_PROF(ctx, s, "dual_update");
-      k_batch_update<0><<<(unsigned)ex.size(), 256, 0, s>>>(
+      UOTK_PROF(ctx, cs, "dual_update");
+      k_batch_update<0><<<(unsigned)ex.size(), 256, 0, cs>>>(
           dEX, dP, act, partX, a, ref, slots, SL_MAXG0 + cur, SL_MAXB0 + cur, SL_MAXG0 + nxt,
           track ? SL_DELTA0 + cur : -1, track ? SL_DELTA0 + nxt : -1, beta, nullptr,
           ctx->dflags);
     }
     UOTK_LAUNCHED(ctx);
     {
-      UOTK_PROF(ctx, s, "weights");
-      k_batch_weights<1><<<(unsigned)ex.size(), 256, 0, s>>>(dEX, dP, act, ref == 0 ? a : nullptr,
+      UOTK_PROF(ctx, cs, "weights");
+      k_batch_weights<1><<<(unsigned)ex.size(), 256, 0, cs>>>(dEX, dP, act, ref == 0 ? a : nullptr,
                                                              beta, slots, SL_MAXB0 + cur, dPX);
     }
     UOTK_LAUNCHED(ctx);
     UOTK_TRY(sum_y());
     {
-      UOTK_PROF(ctx, s, "dual_update");
-      k_batch_update<1><<<(unsigned)ey.size(), 256, 0, s>>>(
+      UOTK_PROF(ctx, cs, "dual_update");
+      k_batch_update<1><<<(unsigned)ey.size(), 256, 0, cs>>>(
           dEY, dP, act, partY, b, ref, slots, SL_MAXB0 + cur, SL_MAXG0 + nxt, SL_MAXB0 + nxt,
           track ? SL_DELTA0 + cur : -1, -1, gamma, ty, ctx->dflags);
     }
@@ -442,47 +487,90 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
   int done = 0;
   UOTK_TRY(sweep(0));
   done = 1;
-  cudaGraphExec_t exec = nullptr;
-  int64_t body_launches = 0;
-  if (!ctx->prof.on && max_sweeps >= 9) {
-    cudaGraph_t graph = nullptr;
-    const int64_t l0 = ctx->launches;
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      const uotk_status st1 = sweep(1);
-      const uotk_status st2 = st1 == UOTK_OK ? sweep(2) : st1;
-      const cudaError_t ec = cudaStreamEndCapture(s, &graph);
-      if (st2 == UOTK_OK && ec == cudaSuccess && graph &&
-          cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess)
-        body_launches = ctx->launches - l0;
-      else
-        exec = nullptr;
-      if (graph) cudaGraphDestroy(graph);
-    }
-    cudaGetLastError();
-    ctx->launches = l0;
-  }
-  int next_check = 10;
   uotk_status st = UOTK_OK;
-  while (done < max_sweeps && remaining > 0) {
-    if (exec && done + 2 <= max_sweeps && (done & 1) == 1) {
-      if (cudaGraphLaunch(exec, s) != cudaSuccess) {
-        st = set_error(ctx, UOTK_ERR_CUDA, "graph launch of the batched sweep loop failed");
-        break;
+  if (!ctx->prof.on && max_sweeps >= 3) {
+    // The loop on the device: WHILE (condition) { sweep; sweep; control }.
+    const int init[2] = {done, npairs};
+    int* hstate = reinterpret_cast<int*>(ctx->host);
+    memcpy(hstate, init, sizeof(init));
+    UOTK_CUDA(ctx, cudaMemcpyAsync(state, hstate, sizeof(init), cudaMemcpyHostToDevice, s));
+    UOTK_CUDA(ctx, cudaMemsetAsync(dsw, 0, sizeof(int) * npairs, s));
+    UOTK_TRY(stream_fence(ctx, s, ctx->gs, ctx->fence_in));
+    cs = ctx->gs;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle cond;
+    UOTK_CUDA(ctx, cudaGraphCreate(&graph, 0));
+    cudaError_t ce = cudaGraphConditionalHandleCreate(&cond, graph, 1, cudaGraphCondAssignDefault);
+    cudaGraphNodeParams np = {};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = cond;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if (ce == cudaSuccess) ce = cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &np);
+    const int64_t l0 = ctx->launches;
+    int64_t body_launches = 0;
+    if (ce == cudaSuccess) {
+      cudaGraph_t body = np.conditional.phGraph_out[0];
+      ce = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                         cudaStreamCaptureModeThreadLocal);
+      if (ce == cudaSuccess) {
+        uotk_status cst = sweep(1);
+        if (cst == UOTK_OK) cst = sweep(2);
+        if (cst == UOTK_OK) {
+          k_batch_control<<<1, 256, 0, cs>>>(npairs, act, dsw, slots, state, tol, max_sweeps,
+                                             cond);
+          if (cudaGetLastError() != cudaSuccess) cst = UOTK_ERR_CUDA;
+          else ctx->launches++;
+        }
+        const cudaError_t ec = cudaStreamEndCapture(cs, &body);
+        if (cst != UOTK_OK || ec != cudaSuccess) ce = cudaErrorUnknown;
       }
-      ctx->launches += body_launches;
-      done += 2;
-    } else {
+      body_launches = ctx->launches - l0;
+    }
+    ctx->launches = l0;
+    if (ce == cudaSuccess) ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce == cudaSuccess) ce = cudaGraphLaunch(exec, cs);
+    if (exec) cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      cudaGetLastError();
+      return set_error(ctx, UOTK_ERR_CUDA, "uot_sinkhorn_batch: device sweep loop failed: %s",
+                       cudaGetErrorString(ce));
+    }
+    // one read-back after the loop: sweeps done, per-pair retirement counts
+    UOTK_CUDA(ctx, cudaMemcpyAsync(hstate, state, 2 * sizeof(int), cudaMemcpyDeviceToHost, cs));
+    UOTK_CUDA(ctx, cudaMemcpyAsync(sweeps.data(), dsw, sizeof(int) * npairs,
+                                   cudaMemcpyDeviceToHost, cs));
+    UOTK_CUDA(ctx, cudaMemcpyAsync(host_act.data(), act, sizeof(int) * npairs,
+                                   cudaMemcpyDeviceToHost, cs));
+    UOTK_CUDA(ctx, cudaStreamSynchronize(cs));
+    UOTK_TRY(stream_fence(ctx, cs, s, ctx->fence_out));
+    cs = s;
+    const int bodies = (hstate[0] - done) / 2;
+    ctx->launches += (int64_t)bodies * body_launches;
+    done = hstate[0];
+    remaining = hstate[1];
+    // an odd remainder of the cap: the last sweep eagerly, then its check
+    if (remaining > 0 && done < max_sweeps) {
+      UOTK_TRY(sweep(done));
+      done += 1;
+      if (track) UOTK_TRY(check(done));
+    }
+  } else {
+    int next_check = 10;
+    while (done < max_sweeps && remaining > 0) {
       st = sweep(done);
       if (st != UOTK_OK) break;
       done += 1;
-    }
-    if (track && (done >= next_check || done == max_sweeps)) {
-      next_check = done + 10;
-      st = check(done);
-      if (st != UOTK_OK) break;
+      if (track && (done >= next_check || done == max_sweeps)) {
+        next_check = done + 10;
+        st = check(done);
+        if (st != UOTK_OK) break;
+      }
     }
   }
-  if (exec) cudaGraphExecDestroy(exec);
   UOTK_TRY(st);
   if (track && done == 1 && max_sweeps == 1) UOTK_TRY(check(done));
   for (int p = 0; p < npairs; ++p)

@@ -63,9 +63,12 @@ __device__ __forceinline__ void stage_chunk(float* st, unsigned long long* bar, 
 
 // Bounded wait for a staging buffer; on time-out every thread learns it, the
 // copies still in flight are waited for (bounded) and the CTA leaves.
+// The first wait (k = 0) goes through first_wait (the context's time-out test
+// waits on `never` there); the copies are drained with the normal limit.
 __device__ __forceinline__ bool stage_ready(unsigned long long* bars, int k, int nchunks,
-                                            long long* flags) {
-  const bool ok = mbar_wait(&bars[k % STAGES], (unsigned)(k / STAGES) & 1u);
+                                            long long* flags, unsigned long long* never) {
+  const bool ok = k == 0 ? first_wait(&bars[0], 0u, never, flags)
+                         : mbar_wait(&bars[k % STAGES], (unsigned)(k / STAGES) & 1u);
   if (__syncthreads_or(!ok)) {
     if (threadIdx.x == 0) {
       flag_add(&flags[FLAG_TIMEOUT], 1LL);
@@ -173,6 +176,7 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
   constexpr int WK = (CPT + WTN - 1) / WTN;
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
+  __shared__ __align__(8) unsigned long long never;  // nothing arrives (time-out test)
   __shared__ int gstart[CPT + 1];
   __shared__ int ngroups;
   float* blk = smem;
@@ -184,6 +188,7 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
   const int nchunks = (pe - pb + CP - 1) / CP;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    mbar_init(&never, 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
       stage_pairs<M, CP>(stage0 + k * SG::STAGE_F, &bars[k], winp, ckey, POT ? nullptr : wts,
@@ -220,7 +225,7 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
   const int lane = threadIdx.x & 31;
   const unsigned long long keep_hi = f2_pack(0.f, 1.f), keep_lo = f2_pack(1.f, 0.f);
   for (int k = 0; k < nchunks; ++k) {
-    if (!stage_ready(bars, k, nchunks, flags)) return;
+    if (!stage_ready(bars, k, nchunks, flags, &never)) return;
     const int pc0 = pb + k * CP, cpn = min(CP, pe - pc0), P0 = 2 * pc0;
     const int lo = max(b0, P0) - P0, hi = min(e0, P0 + 2 * cpn) - P0;  // unit positions
     float* sw = stage0 + (k % STAGES) * SG::STAGE_F;
@@ -946,6 +951,7 @@ __global__ void __launch_bounds__(256)
   constexpr bool CACHE = NIT * W2 <= 64;
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[STAGES];
+  __shared__ __align__(8) unsigned long long never;  // nothing arrives (time-out test)
   float* blk = smem;
   float* stage0 = smem + G::E3P;
   const int u = blockIdx.x;
@@ -958,6 +964,7 @@ __global__ void __launch_bounds__(256)
   const int nchunks = (cnt + C - 1) / C;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
+    mbar_init(&never, 1);
     mbar_fence_init();
     for (int k = 0; k < STAGES && k < nchunks; ++k)
       stage_chunk<M, C>(stage0 + k * G::STAGE_F, &bars[k], win, ckey, nullptr, b0 + k * C,
@@ -1010,7 +1017,7 @@ __global__ void __launch_bounds__(256)
   float hc[CACHE ? NIT * W2 : 1];
   int cached = -1;
   for (int k = 0; k < nchunks; ++k) {
-    if (!stage_ready(bars, k, nchunks, flags)) return;
+    if (!stage_ready(bars, k, nchunks, flags, &never)) return;
     const int q0 = b0 + k * C, cn = min(C, cnt - k * C), koff = q0 & 3;
     const float* sw = stage0 + (k % STAGES) * G::STAGE_F;
     const int* skey = reinterpret_cast<const int*>(sw + C * WS) + koff;
@@ -1159,6 +1166,7 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
   static_assert(M % 2 == 0 && M <= 6, "per-warp gather: even m <= 6");
   extern __shared__ __align__(16) float smem[];
   __shared__ __align__(8) unsigned long long bars[GWARPS][2];
+  __shared__ __align__(8) unsigned long long never;  // nothing arrives (time-out test)
   float* blk = smem;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* wbuf = smem + GG::E3P + warp * GG::WARP_F;
@@ -1175,6 +1183,7 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
   if (lane == 0) {
     mbar_init(&bars[warp][0], 1);
     mbar_init(&bars[warp][1], 1);
+    if (warp == 0) mbar_init(&never, 1);
     mbar_fence_init();
     for (int k = 0; k < 2 && k < nch; ++k)
       stage_warp<M>(wbuf + k * GG::BUF_F, &bars[warp][k], win, ckey, b0 + wb + k * GW,
@@ -1258,7 +1267,8 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
   for (int k = 0; k < nch; ++k) {
     const int q0 = b0 + wb + k * GW, cn = min(GW, we - wb - k * GW);
     float* sb = wbuf + (k & 1) * GG::BUF_F;
-    const bool ok = mbar_wait(&bars[warp][k & 1], (unsigned)(k >> 1) & 1u);
+    const bool ok = k == 0 ? first_wait(&bars[warp][0], 0u, &never, flags)
+                           : mbar_wait(&bars[warp][k & 1], (unsigned)(k >> 1) & 1u);
     if (__any_sync(0xffffffffu, !ok)) {
       // give up: record it, let this warp's copies in flight land, and stop
       if (lane == 0) {

@@ -209,10 +209,12 @@ __global__ void k_max_pot(const double* __restrict__ pot, long long count, doubl
   if (threadIdx.x == 0) atomicMax(slot, dbl_to_ordered(mx));
 }
 
-__global__ void k_flags_reset(long long* flags) {
+__global__ void k_flags_reset(long long* flags, long long wait_test) {
   const int i = threadIdx.x;
   if (i < NUM_FLAGS)
-    flags[i] = (i >= FLAG_MAX_G0 && i <= FLAG_DELTA1) ? ORDERED_NEG_INF : 0LL;
+    flags[i] = (i >= FLAG_MAX_G0 && i <= FLAG_DELTA1) ? ORDERED_NEG_INF
+               : i == FLAG_WAIT_TEST                  ? wait_test
+                                                      : 0LL;
 }
 
 __global__ void k_sum_partials(SumTerms terms, const long long* __restrict__ flags,
@@ -319,6 +321,9 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
   // gamma half-step (sum over X into Y, update gamma).  The flag slots
   // alternate with the sweep's parity (see k_dual_update).
   const bool fuse = !log_domain && E->fuses_dual();
+  // The stream the sweeps go to: the caller's, or the context's own stream
+  // while the loop is replayed from a graph (see below).
+  cudaStream_t cs = s;
   auto sweep = [&](int sw) -> uotk_status {
     const int cur = sw & 1, nxt = cur ^ 1;
     if (fuse) {
@@ -326,34 +331,34 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
       const DualUpdate ub{a, B.beta, q1, lam, ref, FLAG_MAX_G0 + cur, FLAG_MAX_B0 + cur,
                           FLAG_MAX_G0 + nxt, track ? FLAG_DELTA0 + cur : -1,
                           track ? FLAG_DELTA0 + nxt : -1};
-      UOTK_TRY(E->half_dual(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur,
+      UOTK_TRY(E->half_dual(cs, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur,
                             B.tx, ub));
       const DualUpdate ug{b, B.gamma, q2, lam, ref, FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt,
                           FLAG_MAX_B0 + nxt, track ? FLAG_DELTA0 + cur : -1, -1};
-      return E->half_dual(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur,
+      return E->half_dual(cs, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur,
                           B.ty, ug);
     }
     if (log_domain)
-      UOTK_TRY(E->half_log(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.lx));
+      UOTK_TRY(E->half_log(cs, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.lx));
     else
-      UOTK_TRY(E->half(s, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.tx));
+      UOTK_TRY(E->half(cs, 0, ref == 0 ? b : nullptr, B.gamma, lam, F + FLAG_MAX_G0 + cur, B.tx));
     {
-      UOTK_PROF(ctx, s, "dual_update");
+      UOTK_PROF(ctx, cs, "dual_update");
       auto upd = log_domain ? k_dual_update<true> : k_dual_update<false>;
-      upd<<<gu, 256, 0, s>>>(log_domain ? (const void*)B.lx : (const void*)B.tx, a, n, q1, lam,
+      upd<<<gu, 256, 0, cs>>>(log_domain ? (const void*)B.lx : (const void*)B.tx, a, n, q1, lam,
                              ref, F, FLAG_MAX_G0 + cur, FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt,
                              track ? FLAG_DELTA0 + cur : -1, track ? FLAG_DELTA0 + nxt : -1,
                              B.beta);
     }
     UOTK_LAUNCHED(ctx);
     if (log_domain)
-      UOTK_TRY(E->half_log(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ly));
+      UOTK_TRY(E->half_log(cs, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ly));
     else
-      UOTK_TRY(E->half(s, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ty));
+      UOTK_TRY(E->half(cs, 1, ref == 0 ? a : nullptr, B.beta, lam, F + FLAG_MAX_B0 + cur, B.ty));
     {
-      UOTK_PROF(ctx, s, "dual_update");
+      UOTK_PROF(ctx, cs, "dual_update");
       auto upd = log_domain ? k_dual_update<true> : k_dual_update<false>;
-      upd<<<gu, 256, 0, s>>>(log_domain ? (const void*)B.ly : (const void*)B.ty, b, m, q2, lam,
+      upd<<<gu, 256, 0, cs>>>(log_domain ? (const void*)B.ly : (const void*)B.ty, b, m, q2, lam,
                              ref, F, FLAG_MAX_B0 + cur, FLAG_MAX_G0 + nxt, FLAG_MAX_B0 + nxt,
                              track ? FLAG_DELTA0 + cur : -1, -1, B.gamma);
     }
@@ -362,8 +367,8 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
   };
   auto converged_now = [&](int done_sweeps, bool* conv) -> uotk_status {
     UOTK_CUDA(ctx, cudaMemcpyAsync(ctx->host, F + FLAG_DELTA0 + ((done_sweeps - 1) & 1),
-                                   sizeof(long long), cudaMemcpyDeviceToHost, s));
-    UOTK_CUDA(ctx, cudaStreamSynchronize(s));
+                                   sizeof(long long), cudaMemcpyDeviceToHost, cs));
+    UOTK_CUDA(ctx, cudaStreamSynchronize(cs));
     long long enc;
     memcpy(&enc, ctx->host, sizeof(long long));
     *conv = ordered_to_dbl(enc) < tol;
@@ -372,35 +377,51 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
   int done = 0;
   bool converged = false;
   int next_check = 10;
-  // Sweep 0 runs eagerly (it also sets kernel attributes); later sweeps are
-  // replayed from a CUDA graph of two sweeps (odd, even) when the loop is long
-  // enough to pay for the capture.  With profiling on, launches stay eager so
-  // that every launch is timed by its own events.
+  // Sweeps 0 and 1 run eagerly (they also set kernel attributes); later sweeps
+  // are replayed from a CUDA graph of two sweeps (even, odd) when the loop is
+  // long enough to pay for the capture, so that the convergence checks fall on
+  // multiples of 10 sweeps as in the eager loop.  With profiling on, launches
+  // stay eager so that every launch is timed by its own events.
   UOTK_TRY(sweep(0));
   done = 1;
   cudaGraphExec_t exec = nullptr;
   int64_t body_launches = 0;
-  if (!ctx->prof.on && max_sweeps >= 9) {
+  const bool graph_loop = !ctx->prof.on && max_sweeps >= 9;
+  if (graph_loop) {
+    UOTK_TRY(sweep(1));
+    done = 2;
+  }
+  if (graph_loop) {
+    // Capture two sweeps (even, odd) on the context's stream, ordered after
+    // the caller's stream; the rest of the loop runs there and the caller's
+    // stream waits for it at the end.
+    UOTK_TRY(stream_fence(ctx, s, ctx->gs, ctx->fence_in));
+    cs = ctx->gs;
     cudaGraph_t graph = nullptr;
     const int64_t l0 = ctx->launches;
-    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-      const uotk_status st1 = sweep(1);
-      const uotk_status st2 = st1 == UOTK_OK ? sweep(2) : st1;
-      const cudaError_t ec = cudaStreamEndCapture(s, &graph);
-      if (st2 == UOTK_OK && ec == cudaSuccess && graph &&
-          cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
-        body_launches = ctx->launches - l0;
-      } else {
-        exec = nullptr;
-      }
+    cudaError_t ec = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (ec == cudaSuccess) {
+      const uotk_status st1 = sweep(2);
+      const uotk_status st2 = st1 == UOTK_OK ? sweep(3) : st1;
+      ec = cudaStreamEndCapture(cs, &graph);
+      if (st2 == UOTK_OK && ec == cudaSuccess && graph)
+        ec = cudaGraphInstantiate(&exec, graph, 0);
+      else if (ec == cudaSuccess)
+        ec = cudaErrorUnknown;
       if (graph) cudaGraphDestroy(graph);
     }
-    cudaGetLastError();
+    body_launches = ctx->launches - l0;
     ctx->launches = l0;
+    if (ec != cudaSuccess) {
+      cudaGetLastError();
+      if (exec) cudaGraphExecDestroy(exec);
+      return set_error(ctx, UOTK_ERR_CUDA, "capture of the sweep loop failed: %s",
+                       cudaGetErrorString(ec));
+    }
   }
   while (done < max_sweeps) {
-    if (exec && done + 2 <= max_sweeps && (done & 1) == 1) {
-      if (cudaGraphLaunch(exec, s) != cudaSuccess) {
+    if (exec && done + 2 <= max_sweeps && (done & 1) == 0) {
+      if (cudaGraphLaunch(exec, cs) != cudaSuccess) {
         cudaGraphExecDestroy(exec);
         return set_error(ctx, UOTK_ERR_CUDA, "graph launch of the sweep loop failed");
       }
@@ -421,6 +442,8 @@ uotk_status solve(uotk_ctx* ctx, cudaStream_t s, Engine* E, int64_t n, int64_t m
     }
   }
   if (exec) cudaGraphExecDestroy(exec);
+  if (cs != s) UOTK_TRY(stream_fence(ctx, cs, s, ctx->fence_out));
+  cs = s;
   if (track && done == 1 && max_sweeps == 1) {
     UOTK_TRY(converged_now(done, &converged));
   }
@@ -477,7 +500,7 @@ uotk_status engine_create(uotk_ctx* ctx, cudaStream_t s, const EngineSpec& sp, C
 }
 
 uotk_status flags_reset(uotk_ctx* ctx, cudaStream_t s) {
-  k_flags_reset<<<1, 32, 0, s>>>(ctx->dflags);
+  k_flags_reset<<<1, 32, 0, s>>>(ctx->dflags, ctx->wait_test);
   UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }

@@ -33,12 +33,18 @@ struct uotk_ctx {
   // Device workspace: one allocation, carved per call.
   char* ws = nullptr;
   size_t ws_cap = 0;
+  size_t ws_limit = 0;        // largest workspace allowed (0: none)
+  long long wait_test = 0;    // > 0: first wait per CTA runs out after this many cycles
   // Pinned host staging for scalars read back at the end of a call.
   double* host = nullptr;   // 128 doubles
   // Device flags/counters (int64 slots), zeroed per call where used.
   long long* dflags = nullptr;  // NUM_FLAGS slots
   int64_t launches = 0;
   uotk_prof prof;
+  // The context's own stream for captured loops (a caller's legacy default
+  // stream cannot be captured), fenced to the caller's stream with events.
+  cudaStream_t gs = nullptr;
+  cudaEvent_t fence_in = nullptr, fence_out = nullptr;
 };
 
 namespace uotk {
@@ -56,6 +62,7 @@ enum FlagSlot {
   FLAG_DELTA0 = 8,         // max |lambda * change| over a sweep (two parities)
   FLAG_DELTA1 = 9,
   FLAG_NONFINITE_DUAL = 10,  // count of non-finite dual values produced
+  FLAG_WAIT_TEST = 11,     // > 0: the first wait per CTA runs out (uotk_set_wait_timeout_test)
   FLAG_BBOX = 16,          // 6 slots: max x,y,z and max of -x,-y,-z (ordered encodings)
   NUM_FLAGS = 32
 };
@@ -75,6 +82,10 @@ struct DualUpdate {
   double q, lam;
   int ref, shift_in, max_out, reset_slot, delta_out, reset_delta;
 };
+
+// Order work: everything enqueued on `from` so far runs before what is
+// enqueued on `to` next (an event recorded on `from`, waited for on `to`).
+uotk_status stream_fence(uotk_ctx* ctx, cudaStream_t from, cudaStream_t to, cudaEvent_t ev);
 
 // Grow the workspace to `bytes` (synchronises the device when it reallocates).
 uotk_status ws_reserve(uotk_ctx* ctx, size_t bytes);
@@ -231,8 +242,11 @@ __device__ __forceinline__ void bulk_copy(void* dst, const void* src, unsigned b
       "l"(src), "r"(bytes), "r"(smem_addr(bar))
       : "memory");
 }
-// Bounded wait for phase `parity` of `bar`: gives up after ~2^31 clocks (~1 s).
-__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity) {
+// Bounded wait for phase `parity` of `bar`: gives up after `limit` clocks
+// (default ~2^31, about a second).
+constexpr long long UOTK_WAIT_CYCLES = 1LL << 31;
+__device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned parity,
+                                          long long limit = UOTK_WAIT_CYCLES) {
   const unsigned a = smem_addr(bar);
   const long long t0 = clock64();
   while (true) {
@@ -243,8 +257,18 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, unsigned pari
         : "r"(a), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > (1LL << 31)) return false;
+    if (clock64() - t0 > limit) return false;
   }
+}
+// The first bounded wait of a CTA, on phase `parity` of `bar`.  With the
+// context's time-out test on (flags[FLAG_WAIT_TEST] = cycles > 0) it waits
+// instead on `never`, a barrier nothing arrives at, and runs out after that
+// many cycles.
+__device__ __forceinline__ bool first_wait(unsigned long long* bar, unsigned parity,
+                                           unsigned long long* never, const long long* flags) {
+  const long long test = flags[FLAG_WAIT_TEST];
+  if (test > 0) return mbar_wait(never, 0u, test);
+  return mbar_wait(bar, parity);
 }
 
 // Order-preserving map of doubles onto signed 64-bit integers, so that the

@@ -80,6 +80,8 @@ def lib():
         L.uotk_launch_count.restype = _I64
         L.uotk_set_profiling.argtypes = [_P, ctypes.c_int]
         L.uotk_set_profiling.restype = ctypes.c_int
+        L.uotk_set_workspace_limit.argtypes = [_P, _I64]
+        L.uotk_set_wait_timeout_test.argtypes = [_P, _I64]
         L.uotk_profile_read.argtypes = [_P, ctypes.c_char_p, ctypes.c_int,
                                         ctypes.POINTER(_I64), ctypes.POINTER(_D), ctypes.c_int]
         L.uotk_profile_read.restype = ctypes.c_int
@@ -159,6 +161,16 @@ class Context:
 
     def set_profiling(self, on: bool):
         self.check(lib().uotk_set_profiling(self.handle, int(bool(on))))
+
+    def set_workspace_limit(self, nbytes: int):
+        """Largest device workspace of this context (0: no limit)."""
+        self.check(lib().uotk_set_workspace_limit(self.handle, int(nbytes)))
+
+    def set_wait_timeout_test(self, cycles: int):
+        """cycles > 0: the first bounded device wait per CTA of the NFFT spread
+        and gather waits on a barrier nothing completes and runs out after that
+        many cycles (calls then return UOTK_ERR_TIMEOUT); 0 turns it off."""
+        self.check(lib().uotk_set_wait_timeout_test(self.handle, int(cycles)))
 
     def profile(self) -> dict:
         """{stage: (launches, total device ms)} since the last reset."""
@@ -554,6 +566,7 @@ def nfft_gather(plan, grid, pts, ctx=None):
 
 EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_string",
             "uotk_launch_count", "uotk_set_profiling", "uotk_profile_read", "uotk_profile_reset",
+            "uotk_set_workspace_limit", "uotk_set_wait_timeout_test",
             "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
             "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
