@@ -279,13 +279,14 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
 #pragma unroll
           for (int j = 0; j < M; ++j) acc2[r][j] = 0ull;
         const int pp0 = t0 >> 1, pp1 = (t1 - 1) >> 1;
-        for (int pp = pp0; pp <= pp1; ++pp) {
+        // one point pair: the masked y factor, the m phi_x pairs and the ZB
+        // products w phi_z phi_y, all loaded before any FMA of the pair
+        auto load_pair = [&](int pp, unsigned long long (&fx2)[M], unsigned long long (&A2)[ZB]) {
           const float* row = sw + pp * WSP;
           unsigned long long fy2 = *reinterpret_cast<const unsigned long long*>(row + YO2 + 2 * y);
           // a pair half outside the run (the neighbouring cell's point) is masked
           if (pp == pp0 && (t0 & 1)) fy2 = f2_mul(fy2, keep_hi);
           if (pp == pp1 && (t1 & 1)) fy2 = f2_mul(fy2, keep_lo);
-          unsigned long long fx2[M];
           const float* xr = row + xh * HP2;
 #pragma unroll
           for (int j = 0; j + 1 < M; j += 2) {
@@ -295,12 +296,28 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
           }
           if (M & 1) fx2[M - 1] = *reinterpret_cast<const unsigned long long*>(xr + 2 * (M - 1));
 #pragma unroll
-          for (int r = 0; r < ZB; ++r) {
-            const unsigned long long A2 = f2_mul(
-                *reinterpret_cast<const unsigned long long*>(row + ZO2 + 2 * (z0 + r)), fy2);
+          for (int r = 0; r < ZB; ++r)
+            A2[r] = f2_mul(*reinterpret_cast<const unsigned long long*>(row + ZO2 + 2 * (z0 + r)),
+                           fy2);
+        };
+        int pp = pp0;
+        // two pairs per iteration: the second pair's loads overlap the first's FMAs
+        for (; pp + 1 <= pp1; pp += 2) {
+          unsigned long long fa[M], fb[M], Aa[ZB], Ab[ZB];
+          load_pair(pp, fa, Aa);
+          load_pair(pp + 1, fb, Ab);
 #pragma unroll
-            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(A2, fx2[j], acc2[r][j]);
-          }
+          for (int r = 0; r < ZB; ++r)
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Ab[r], fb[j], f2_fma(Aa[r], fa[j], acc2[r][j]));
+        }
+        if (pp <= pp1) {
+          unsigned long long fa[M], Aa[ZB];
+          load_pair(pp, fa, Aa);
+#pragma unroll
+          for (int r = 0; r < ZB; ++r)
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
         }
         const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
         float* dst = blk + ((bz + z0) * E + by + y) * E + bx + xh * M;
@@ -338,6 +355,7 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
 // every entry, and the G partial sums are then added in group order: a dense
 // tile costs about one block's reads per CTA and short dependency chains.
 constexpr int FOLD_THREADS = 256;
+constexpr int FOLD_ZR_CACHE = 2048;   // unit z ranges of a tile held in shared memory
 template <int M>
 __global__ void __launch_bounds__(FOLD_THREADS)
     k_fold_units(float* __restrict__ blocks, const int* __restrict__ unit_tile,
@@ -346,6 +364,7 @@ __global__ void __launch_bounds__(FOLD_THREADS)
   constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E2 = E * E, E3 = E2 * E;
   constexpr int E3P = (E3 + 3) & ~3;
   __shared__ float part[FOLD_THREADS];
+  __shared__ short zlo[FOLD_ZR_CACHE], zhi[FOLD_ZR_CACHE];
   const int u = blockIdx.x;
   if (u >= *num_units) return;
   const int t = unit_tile[u];
@@ -356,34 +375,58 @@ __global__ void __launch_bounds__(FOLD_THREADS)
   const int e0 = min(E3, k * chunk), e1 = min(E3, e0 + chunk);
   const int ne = e1 - e0;
   if (ne <= 0) return;
-  float* first = blocks + (size_t)u0 * E3P;
-  auto covers = [&](int v, int e) {
-    const int zr = __ldg(&unit_zr[u0 + v]);
-    const int pz = e / E2;
-    return pz >= (zr & 255) && pz < (zr >> 8) + W2;
-  };
-  if (ne >= FOLD_THREADS / 2) {
-    for (int e = e0 + threadIdx.x; e < e1; e += FOLD_THREADS) {
-      float s = 0.f;
-      for (int v = 0; v < U; ++v)
-        if (covers(v, e)) s += first[(size_t)v * E3P + e];
-      first[e] = s;
-    }
-    return;
+  for (int v = threadIdx.x; v < U && v < FOLD_ZR_CACHE; v += FOLD_THREADS) {
+    const int zr = unit_zr[u0 + v];
+    zlo[v] = (short)(zr & 255);
+    zhi[v] = (short)((zr >> 8) + W2);
   }
+  __syncthreads();
+  float* first = blocks + (size_t)u0 * E3P;
+  // block entry e of unit v, or 0 where that unit wrote nothing (its z-planes)
+  auto entry = [&](int v, int e) -> float {
+    int lo, hi;
+    if (v < FOLD_ZR_CACHE) {
+      lo = zlo[v];
+      hi = zhi[v];
+    } else {
+      const int zr = unit_zr[u0 + v];
+      lo = zr & 255;
+      hi = (zr >> 8) + W2;
+    }
+    const int pz = e / E2;
+    return pz >= lo && pz < hi ? first[(size_t)v * E3P + e] : 0.f;
+  };
+  // G groups of threads per entry; group g sums the units g, g + G, ..: eight
+  // running sums (unit index mod 8 within the group) keep eight loads in
+  // flight, added in a fixed order
   int G = FOLD_THREADS / ne;
-  G = G < U ? G : U;
-  const int ei = threadIdx.x % ne, g = threadIdx.x / ne;
-  float s = 0.f;
-  if (g < G)
-    for (int v = g; v < U; v += G)
-      if (covers(v, e0 + ei)) s += first[(size_t)v * E3P + e0 + ei];
-  part[threadIdx.x] = s;
-  __syncthreads();  // every group has read its units before the first block is overwritten
-  if (threadIdx.x < ne) {
-    float r = 0.f;
-    for (int q = 0; q < G; ++q) r += part[q * ne + threadIdx.x];
-    first[e0 + threadIdx.x] = r;
+  G = G < 1 ? 1 : (G < U ? G : U);
+  const int ei = G > 1 ? threadIdx.x % ne : 0, g = G > 1 ? threadIdx.x / ne : 0;
+  for (int eb = e0 + (G > 1 ? ei : (int)threadIdx.x); eb < e1; eb += (G > 1 ? e1 : FOLD_THREADS)) {
+    float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (g < G) {
+      int v = g;
+      for (; v + 7 * G < U; v += 8 * G) {
+        float tv[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) tv[j] = entry(v + j * G, eb);
+#pragma unroll
+        for (int j = 0; j < 8; ++j) s8[j] += tv[j];
+      }
+      for (int j = 0; v < U; v += G, ++j) s8[j] += entry(v, eb);
+    }
+    const float sum = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
+    if (G == 1) {
+      first[eb] = sum;
+    } else {
+      part[threadIdx.x] = sum;
+      __syncthreads();  // every group has read its units before the first block is overwritten
+      if (threadIdx.x < ne) {
+        float r = 0.f;
+        for (int q = 0; q < G; ++q) r += part[q * ne + threadIdx.x];
+        first[e0 + threadIdx.x] = r;
+      }
+    }
   }
 }
 
@@ -437,17 +480,35 @@ __global__ void __launch_bounds__(512)
   }
   __syncthreads();
   const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
-  float v = 0.f;
   const int nl = nlist;
-  for (int q = 0; q < nl; ++q) {
-    const int c = offs[q];
-    const int dz = c / 9 - 1, dy = (c / 3) % 3 - 1, dx = c % 3 - 1;
-    const int Lz = lz - NFFT_TILE * dz + M - 1, Ly = ly - NFFT_TILE * dy + M - 1,
-              Lx = lx - NFFT_TILE * dx + M - 1;
-    if (Lz < zlo[q] || Lz >= zhi[q] || Ly < 0 || Ly >= E || Lx < 0 || Lx >= E) continue;
-    v += blocks[(size_t)first[q] * E3P + (Lz * E + Ly) * E + Lx];
+  float* dst = grid + ((long long)(tz * NFFT_TILE + lz) * n + ty * NFFT_TILE + ly) * n +
+               tx * NFFT_TILE + lx;
+  if (nl == 0) {  // no tile block reaches this output tile
+    *dst = 0.f;
+    return;
   }
-  grid[((long long)(tz * NFFT_TILE + lz) * n + ty * NFFT_TILE + ly) * n + tx * NFFT_TILE + lx] = v;
+  // in batches of four: the loads of a batch in flight together, then added
+  // in list order
+  float v = 0.f;
+  for (int q0 = 0; q0 < nl; q0 += 4) {
+    float t[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int q = q0 + j;
+      t[j] = 0.f;
+      if (q < nl) {
+        const int c = offs[q];
+        const int dz = c / 9 - 1, dy = (c / 3) % 3 - 1, dx = c % 3 - 1;
+        const int Lz = lz - NFFT_TILE * dz + M - 1, Ly = ly - NFFT_TILE * dy + M - 1,
+                  Lx = lx - NFFT_TILE * dx + M - 1;
+        if (Lz >= zlo[q] && Lz < zhi[q] && Ly >= 0 && Ly < E && Lx >= 0 && Lx < E)
+          t[j] = blocks[(size_t)first[q] * E3P + (Lz * E + Ly) * E + Lx];
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v += t[j];
+  }
+  *dst = v;
 }
 
 // Spread weights in sorted order: w_q = base_q exp(lam pot_q - shift).
@@ -815,6 +876,224 @@ __global__ void __launch_bounds__(32 * WF_WARPS)
     const int e = i / WF_LINES, l = i - e * WF_LINES;
     out[out_base + e * out_stride + l] = tout[e * WF_PITCH + l];
   }
+}
+
+// ---- separable circulant passes (Gaussian kernel) -------------------------
+// For the Gaussian the scale b_k / prod_t (n phihat(k_t))^2 is a product over
+// the axes, so the grid convolution is one real circulant operator applied
+// along each axis in turn: per line, a forward DFT, the axis's factor at every
+// kept frequency, an inverse DFT.  With the kept band taken symmetric,
+// |k| <= N/2 - 1 (the frequency -N/2 of I_N carries b_k below the plan's
+// truncation bound), the operator is real, so two real lines share one complex
+// transform: line a in the real part, line b in the imaginary part.
+//
+// 128-point transforms by 8 threads each (4 per warp), split as 128 = 16 x 8:
+// with m = 8a + b and k = c + 16d,
+//   X[c + 16d] = sum_b W8^{bd} W128^{bc} sum_a x[8a + b] W16^{ac}.
+// Thread b holds x[8a + b], a < 16, takes the 16-point DFT over a in registers
+// and applies W128^{bc}; a transpose through shared memory hands thread t the
+// values of c = 2t and 2t + 1, whose 8-point DFTs over b give X[c + 16d].  The
+// inverse runs the same steps backwards from that layout.  A CTA of 4 warps
+// takes 32 lines (16 pairs); lines along y and z are staged through shared
+// memory as an [element][line] tile so that global accesses stay coalesced.
+// The passes run in place: every CTA reads its lines before it writes them,
+// and no other CTA of the pass touches them.
+constexpr int CIRC_LINES = 32;
+constexpr int CIRC_WARPS = 4;
+// Shared-memory strides chosen so that the transposes and the tile accesses
+// of a warp take at most three (transposes) or two (tile) wavefronts: a row c
+// of an FFT's [c][b] block is 9 float2 apart, FFT blocks 147 apart, tile rows
+// 35 floats apart.
+constexpr int CIRC_RS = 9, CIRC_FS = 147, CIRC_P = 35;
+
+__device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+// a * w for w = (c, s); FWD selects the sign of the exponent (-1 forward)
+__device__ __forceinline__ float2 c_rot(float2 a, float c, float s) {
+  return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
+}
+// 4-point DFT in place, natural order in and out (forward: exponent -)
+template <bool FWD>
+__device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2& a3) {
+  const float2 t0 = c_add(a0, a2), t1 = c_sub(a0, a2), t2 = c_add(a1, a3), t3 = c_sub(a1, a3);
+  a0 = c_add(t0, t2);
+  a2 = c_sub(t0, t2);
+  // forward: X1 = t1 - i t3, X3 = t1 + i t3; inverse the other way round
+  const float2 mi = FWD ? make_float2(t3.y, -t3.x) : make_float2(-t3.y, t3.x);
+  a1 = c_add(t1, mi);
+  a3 = c_sub(t1, mi);
+}
+// 16-point DFT of v (natural order in and out) as 4 x 4.
+template <bool FWD>
+__device__ __forceinline__ void dft16(float2 (&v)[16]) {
+  constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508978f;
+  constexpr float R2 = 0.70710678118654752f;
+  const float sg = FWD ? -1.f : 1.f;
+  // inner 4-point DFTs over p of x[4p + q]
+#pragma unroll
+  for (int q = 0; q < 4; ++q) dft4<FWD>(v[q], v[4 + q], v[8 + q], v[12 + q]);
+  // twiddles W16^{q r} on element (r, q) at v[4r + q]
+  v[5] = c_rot(v[5], C1, sg * S1);      // q=1 r=1
+  v[6] = c_rot(v[6], R2, sg * R2);      // q=2 r=1
+  v[7] = c_rot(v[7], S1, sg * C1);      // q=3 r=1
+  v[9] = c_rot(v[9], R2, sg * R2);      // q=1 r=2
+  v[10] = make_float2(-sg * v[10].y, sg * v[10].x);  // q=2 r=2: W16^4 = exp(sg i pi/2)
+  v[11] = c_rot(v[11], -R2, sg * R2);   // q=3 r=2
+  v[13] = c_rot(v[13], S1, sg * C1);    // q=1 r=3
+  v[14] = c_rot(v[14], -R2, sg * R2);   // q=2 r=3
+  v[15] = c_rot(v[15], -C1, -sg * S1);  // q=3 r=3: W16^9
+  // outer 4-point DFTs over q; X[r + 4 s] lands at v[4 r + s]
+#pragma unroll
+  for (int r = 0; r < 4; ++r) dft4<FWD>(v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
+  // v[4 r + s] holds X[r + 4 s]: transpose the 4 x 4 index to natural order
+  float2 t;
+  t = v[1]; v[1] = v[4]; v[4] = t;
+  t = v[2]; v[2] = v[8]; v[8] = t;
+  t = v[3]; v[3] = v[12]; v[12] = t;
+  t = v[6]; v[6] = v[9]; v[9] = t;
+  t = v[7]; v[7] = v[13]; v[13] = t;
+  t = v[11]; v[11] = v[14]; v[14] = t;
+}
+// 8-point DFT of v (natural order in and out) as 4 x 2.
+template <bool FWD>
+__device__ __forceinline__ void dft8(float2 (&v)[8]) {
+  constexpr float R2 = 0.70710678118654752f;
+  const float sg = FWD ? -1.f : 1.f;
+  float2 e0 = v[0], e1 = v[2], e2 = v[4], e3 = v[6];
+  float2 o0 = v[1], o1 = v[3], o2 = v[5], o3 = v[7];
+  dft4<FWD>(e0, e1, e2, e3);
+  dft4<FWD>(o0, o1, o2, o3);
+  o1 = c_rot(o1, R2, sg * R2);
+  o2 = make_float2(-sg * o2.y, sg * o2.x);
+  o3 = c_rot(o3, -R2, sg * R2);
+  v[0] = c_add(e0, o0); v[4] = c_sub(e0, o0);
+  v[1] = c_add(e1, o1); v[5] = c_sub(e1, o1);
+  v[2] = c_add(e2, o2); v[6] = c_sub(e2, o2);
+  v[3] = c_add(e3, o3); v[7] = c_sub(e3, o3);
+}
+
+template <int AXIS>
+__global__ void __launch_bounds__(32 * CIRC_WARPS, 4)
+    k_circ(float* __restrict__ g, const float* __restrict__ scale, int N) {
+  constexpr int n = 128;
+  constexpr int P = CIRC_P;
+  __shared__ float2 tw[n];
+  __shared__ float fac[n];
+  __shared__ float2 buf[CIRC_WARPS * 4 * CIRC_FS];  // per FFT: [c][b] at c * CIRC_RS + b
+  __shared__ float tile[AXIS == 0 ? 1 : n * P];
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    float sn, cs;
+    sincospif(-2.0f * (float)j / (float)n, &sn, &cs);
+    tw[j] = make_float2(cs, sn);
+    // this axis's factor at frequency index j (k = j or j - n), zero outside |k| < N/2
+    const int k = j < n / 2 ? j : j - n;
+    fac[j] = (k > -N / 2 && k < N / 2) ? scale[AXIS * N + k + N / 2] : 0.f;
+  }
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int f = lane >> 3, b = lane & 7;       // FFT of the warp, thread within it
+  const int pr = w * 4 + f;                     // line pair of the CTA
+  const int la = 2 * pr, lb = la + 1;
+  const int c = blockIdx.x;
+  auto addr = [&](int e, int l) -> long long {
+    if (AXIS == 0) return ((long long)c * CIRC_LINES + l) * n + e;
+    const int x0 = (c % (n / CIRC_LINES)) * CIRC_LINES, o = c / (n / CIRC_LINES);
+    if (AXIS == 1) return ((long long)o * n + e) * n + x0 + l;
+    return ((long long)e * n + o) * n + x0 + l;
+  };
+  constexpr int PER = n * CIRC_LINES / (32 * CIRC_WARPS);
+  float2 v[16];
+  if (AXIS == 0) {
+#pragma unroll
+    for (int a = 0; a < 16; ++a) v[a] = make_float2(g[addr(8 * a + b, la)], g[addr(8 * a + b, lb)]);
+  } else {
+    float t[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = threadIdx.x + 32 * CIRC_WARPS * r;
+      t[r] = g[addr(i / CIRC_LINES, i % CIRC_LINES)];
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = threadIdx.x + 32 * CIRC_WARPS * r;
+      tile[(i / CIRC_LINES) * P + i % CIRC_LINES] = t[r];
+    }
+  }
+  __syncthreads();
+  if (AXIS != 0) {
+#pragma unroll
+    for (int a = 0; a < 16; ++a) v[a] = make_float2(tile[(8 * a + b) * P + la], tile[(8 * a + b) * P + lb]);
+  }
+  float2* B = buf + (w * 4 + f) * CIRC_FS;
+  // forward: 16-point DFT over a, twiddle W128^{b c}, transpose
+  dft16<true>(v);
+#pragma unroll
+  for (int cc = 0; cc < 16; ++cc) {
+    const float2 t = tw[(b * cc) & (n - 1)];
+    B[cc * CIRC_RS + b] = c_rot(v[cc], t.x, t.y);
+  }
+  __syncwarp();
+  float2 u0[8], u1[8];
+#pragma unroll
+  for (int bb = 0; bb < 8; ++bb) {
+    u0[bb] = B[2 * b * CIRC_RS + bb];
+    u1[bb] = B[(2 * b + 1) * CIRC_RS + bb];
+  }
+  __syncwarp();
+  dft8<true>(u0);
+  dft8<true>(u1);
+  // scale: u0[d] = X[2b + 16 d], u1[d] = X[2b + 1 + 16 d]
+#pragma unroll
+  for (int d = 0; d < 8; ++d) {
+    const float f0 = fac[2 * b + 16 * d], f1 = fac[2 * b + 1 + 16 * d];
+    u0[d] = make_float2(u0[d].x * f0, u0[d].y * f0);
+    u1[d] = make_float2(u1[d].x * f1, u1[d].y * f1);
+  }
+  // inverse: 8-point DFTs over d, twiddle W128^{-b' c}, transpose, 16-point over c
+  dft8<false>(u0);
+  dft8<false>(u1);
+#pragma unroll
+  for (int bb = 0; bb < 8; ++bb) {
+    const float2 t0 = tw[(bb * 2 * b) & (n - 1)], t1 = tw[(bb * (2 * b + 1)) & (n - 1)];
+    B[2 * b * CIRC_RS + bb] = c_rot(u0[bb], t0.x, -t0.y);
+    B[(2 * b + 1) * CIRC_RS + bb] = c_rot(u1[bb], t1.x, -t1.y);
+  }
+  __syncwarp();
+#pragma unroll
+  for (int cc = 0; cc < 16; ++cc) v[cc] = B[cc * CIRC_RS + b];
+  dft16<false>(v);
+  // v[a] = line values at element 8a + b (line a in x, line b in y)
+  if (AXIS == 0) {
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      g[addr(8 * a + b, la)] = v[a].x;
+      g[addr(8 * a + b, lb)] = v[a].y;
+    }
+  } else {
+    __syncthreads();  // every warp has read its lines of the tile
+#pragma unroll
+    for (int a = 0; a < 16; ++a) {
+      tile[(8 * a + b) * P + la] = v[a].x;
+      tile[(8 * a + b) * P + lb] = v[a].y;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+      const int i = threadIdx.x + 32 * CIRC_WARPS * r;
+      g[addr(i / CIRC_LINES, i % CIRC_LINES)] = tile[(i / CIRC_LINES) * P + i % CIRC_LINES];
+    }
+  }
+}
+
+uotk_status circ_convolve(uotk_ctx* ctx, cudaStream_t s, int N, const float* scale, float* g) {
+  constexpr int n = 128;
+  const unsigned blocks = (unsigned)((long long)n * n / CIRC_LINES);
+  k_circ<0><<<blocks, 32 * CIRC_WARPS, 0, s>>>(g, scale, N);
+  UOTK_LAUNCHED(ctx);
+  k_circ<1><<<blocks, 32 * CIRC_WARPS, 0, s>>>(g, scale, N);
+  UOTK_LAUNCHED(ctx);
+  k_circ<2><<<blocks, 32 * CIRC_WARPS, 0, s>>>(g, scale, N);
+  UOTK_LAUNCHED(ctx);
+  return UOTK_OK;
 }
 
 template <int R>
@@ -1452,6 +1731,13 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
   int logn = 0;
   while ((1 << logn) < n) ++logn;
   UOTK_PROF(ctx, s, "fft");
+  if (!full && n == 128) {
+    // Gaussian: three separable circulant passes, in place on the output grid
+    if (grid_out != grid_in)
+      UOTK_CUDA(ctx, cudaMemcpyAsync(grid_out, grid_in, sizeof(float) * (size_t)n * n * n,
+                                     cudaMemcpyDeviceToDevice, s));
+    return circ_convolve(ctx, s, N, W.scale, grid_out);
+  }
   if (n >= 32 && N % WF_LINES == 0) {
     // pruned warp-FFT passes: A1 = n x n x N, A2 = n x N x N complex inside cgrid
     float2* A1 = W.cgrid;

@@ -135,9 +135,13 @@ def test_sinkhorn_nfft_is_deterministic(uotk):
         assert torch.equal(r1[0], r[0]) and torch.equal(r1[1], r[1]) and r1[3] == r[3]
 
 
-def test_convolve_stage(uotk):
+@pytest.mark.parametrize("grid", [64, 128])
+def test_convolve_stage(uotk, grid):
+    """The grid convolution against its FP64 restatement: the pruned 3-D FFT
+    (grid 64) and the three separable circulant passes of the Gaussian
+    (grid 128), on a standard normal grid (every frequency present)."""
     src = cloud(5, 2000, 3)
-    p, P = plan_for(uotk, src, src, 0.05, grid=64)
+    p, P = plan_for(uotk, src, src, 0.05, grid=grid)
     n, N, m = P["grid"], P["bandwidth"], P["cutoff"]
     g = inputs.rng(6).standard_normal((n, n, n)).astype(np.float32)
     out = uotk.nfft_convolve(p, dev(g)).cpu().numpy().astype(np.float64)

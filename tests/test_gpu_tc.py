@@ -154,6 +154,31 @@ def test_sinkhorn_tc_vs_oracle(uotk):
     assert abs(value - v) <= delta * abs(v) * (1 + W.rho / W.eps)
 
 
+@pytest.mark.parametrize("log_domain", [False, True])
+def test_sinkhorn_tc_subsample_4096(uotk, log_domain):
+    """The high-dimensional workload's check as stated: a full 100-sweep solve
+    (eps = 1, rho = 2, BF16x3 cross term, FP64 dual updates) on a 4096-point
+    subsample of each cloud, plain and log-domain, against the FP64 oracle at
+    the tensor-core bar."""
+    W = inputs.gauss64()
+    idx = inputs.subsample_rows(inputs.rng(31), 4096, W.n)
+    x, y = W.x[idx], W.y[idx]
+    a = (W.a[idx] * (1.0 / W.a[idx].sum())).astype(np.float32)
+    b = (W.b[idx] * (1.2 / W.b[idx].sum())).astype(np.float32)
+    X, Y, A, B = f64(x), f64(y), f64(a), f64(b)
+    rb, rg = oracle.uot_sinkhorn(X, A, Y, B, W.eps, W.rho, sweeps=W.sweeps,
+                                 logdomain=log_domain)
+    beta, gamma, sweeps, value, _ = uotk.uot_sinkhorn(dev(x), dev(a), dev(y), dev(b), W.eps,
+                                                      W.rho, max_sweeps=W.sweeps,
+                                                      method="direct_bf16x3",
+                                                      log_domain=log_domain)
+    delta = bound("direct_bf16x3", radius(x, y), W.eps)
+    res = residual(beta.cpu().numpy(), gamma.cpu().numpy(), rb, rg)
+    assert sweeps == W.sweeps and res <= delta * (1 + W.rho / W.eps), (res, delta)
+    v = oracle.dual_value(X, A, Y, B, W.eps, W.rho, W.rho, rb, rg)
+    assert abs(value - v) <= delta * abs(v) * (1 + W.rho / W.eps)
+
+
 def test_mmd2_tc(uotk):
     W = inputs.gauss64(seed=3002, n=1500, m=1300)
     rv, rp = oracle.mmd2(f64(W.x), f64(W.a), f64(W.y), f64(W.b), W.ell, return_parts=True)
