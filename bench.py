@@ -836,6 +836,16 @@ def main():
                                 "err_vs_sum_w": float(np.max(np.abs(o - ref)) / scale)}
             except uotk.UotkError as e:
                 extras[meth] = {"error": str(e)}
+        # the autotuner on the full workload: free grid and cut-off at 1e-5, and
+        # the workload's own 128^3 grid at 1e-6
+        extras["autotune"] = {}
+        for key, kw in (("free_1e-5", {"target_err": 1e-5}),
+                        ("grid128_1e-6", {"target_err": 1e-6, "grid": 128})):
+            try:
+                o, r = uotk.autotune_sum(y, b, x, W.eps, ctx=ctx, **kw)
+                extras["autotune"][key] = {"chosen": o, "report": r}
+            except uotk.UotkError as e:
+                extras["autotune"][key] = {"error": str(e)}
         extras["gradients"] = gradient_extras(uotk, ctx, stream, W, x, a, y, b, args.method)
         extras["gauss64"] = high_dim_extras(uotk, ctx, stream, rates, sms, peaks)
         extras["other_kernels"] = other_kernel_extras(uotk, ctx, stream, W, x, b, y)

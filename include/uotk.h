@@ -60,7 +60,11 @@ typedef enum {
   UOTK_DIRECT = 0,
   UOTK_NFFT = 1,
   UOTK_DIRECT_BF16 = 2,
-  UOTK_DIRECT_BF16X3 = 3
+  UOTK_DIRECT_BF16X3 = 3,
+  /* the form chosen by uotk_autotune_sum for the problem at hand (cached per
+   * context); accepted by uotk_kernel_sum, uotk_uot_sinkhorn,
+   * uotk_sinkhorn_divergence, uotk_mmd2 and their gradients (Gaussian kernel) */
+  UOTK_AUTO = 4
 } uotk_method;
 
 /* Reference measure of the entropy term.
@@ -185,6 +189,28 @@ uotk_status uotk_kernel_sum(uotk_ctx* ctx, void* stream, int d,
                             const float* src, int64_t n, const float* w,
                             const float* tgt, int64_t m, float* out,
                             double eps, const uotk_sum_opts* opts);
+
+/* ---- autotuning of the summation form ---------------------------------------------
+ * The paper chooses its NFFT parameters by hand (Rem. on NFFT parameters, Sec. 4);
+ * this measures them.  For the Gaussian kernel sum src (n points, weights w) ->
+ * tgt (m points) with width eps, on this GPU: the direct FP32 form, for d > 3
+ * the tensor-core forms (BF16x3, BF16), and for d <= 3 the NFFT at grid 64 and
+ * 128 with cut-off m = 4..8 (only in->grid / in->cutoff when those are set)
+ * whose plans accept the data.  Each is timed (one full summation; the direct
+ * forms on the first 32768 targets, scaled to m) and its error
+ * max_j |s_j - s*_j| / sum_i |w_i| measured at 256 targets spread through tgt
+ * against their exact sums, taken in FP64 on the device.  *out receives the
+ * fastest form whose error is at most in->target_err (0: 1e-5); the direct
+ * FP32 form always qualifies.  report (host double[8], may be NULL): {time of
+ * the chosen form in ms, its measured error, time of the direct FP32 form in
+ * ms, forms measured, chosen grid (0: direct), chosen cut-off, targets
+ * sampled, target}.  The choice is cached in the context per (d, n, m, eps,
+ * target, in->grid, in->cutoff, bounding box of the points); a cached problem
+ * costs one bounding-box reduction.  in may be NULL; in->kernel must be GAUSS.
+ * Runs several summations; synchronises `stream`. */
+uotk_status uotk_autotune_sum(uotk_ctx* ctx, void* stream, int d, const float* src, int64_t n,
+                              const float* w, const float* tgt, int64_t m, double eps,
+                              const uotk_sum_opts* in, uotk_sum_opts* out, double* report);
 
 /* ---- the direct kernel summation without allocation ------------------------------
  * The paper has no counterpart to this entry point; it serves callers that may

@@ -164,8 +164,10 @@ uotk_status check_common(uotk_ctx* ctx, int d, const uotk_sum_opts* opts) {
   if (d < 1) return set_error(ctx, UOTK_ERR_INVALID, "dimension d = %d < 1", d);
   const int method = opts ? opts->method : UOTK_DIRECT;
   if (method != UOTK_DIRECT && method != UOTK_NFFT && method != UOTK_DIRECT_BF16 &&
-      method != UOTK_DIRECT_BF16X3)
+      method != UOTK_DIRECT_BF16X3 && method != UOTK_AUTO)
     return set_error(ctx, UOTK_ERR_INVALID, "unknown method %d", method);
+  if (method == UOTK_AUTO && opts->kernel != UOTK_KERNEL_GAUSS)
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED, "UOTK_AUTO: the Gaussian kernel only");
   if (method != UOTK_NFFT && d > 128)
     return set_error(ctx, UOTK_ERR_UNSUPPORTED, "direct form: d = %d > 128", d);
   if (method == UOTK_NFFT) {
@@ -183,6 +185,17 @@ uotk_status check_common(uotk_ctx* ctx, int d, const uotk_sum_opts* opts) {
     if (!(opts->period >= 0.0) || !(opts->target_err >= 0.0))
       return set_error(ctx, UOTK_ERR_INVALID, "NFFT period/target_err must be >= 0");
   }
+  return UOTK_OK;
+}
+
+// opts naming UOTK_AUTO: replaced by the autotuned form of the sum src -> tgt
+// (kept in *store).
+uotk_status resolve_auto(uotk_ctx* ctx, cudaStream_t s, int d, const float* src, int64_t n,
+                         const float* w, const float* tgt, int64_t m, double eps,
+                         const uotk_sum_opts*& opts, uotk_sum_opts* store) {
+  if (!opts || opts->method != UOTK_AUTO) return UOTK_OK;
+  UOTK_TRY(op_autotune_sum(ctx, s, d, src, n, w, tgt, m, eps, opts, store, nullptr));
+  opts = store;
   return UOTK_OK;
 }
 
@@ -355,7 +368,28 @@ uotk_status uotk_kernel_sum(uotk_ctx* ctx, void* stream, int d, const float* src
   if (!(eps > 0.0) || !isfinite(eps))
     return set_error(ctx, UOTK_ERR_INVALID, "eps must be finite and > 0, got %g", eps);
   if (m == 0) return UOTK_OK;
+  uotk_sum_opts chosen;
+  if (n > 0)
+    UOTK_TRY(resolve_auto(ctx, (cudaStream_t)stream, d, src, n, w, tgt, m, eps, opts, &chosen));
+  else if (opts && opts->method == UOTK_AUTO)
+    opts = nullptr;  // no sources: zeros whatever the form
   return op_kernel_sum(ctx, (cudaStream_t)stream, d, src, n, w, tgt, m, out, eps, opts);
+}
+
+uotk_status uotk_autotune_sum(uotk_ctx* ctx, void* stream, int d, const float* src, int64_t n,
+                              const float* w, const float* tgt, int64_t m, double eps,
+                              const uotk_sum_opts* in, uotk_sum_opts* out, double* report) {
+  UOTK_TRY(enter(ctx));
+  if (!out) return set_error(ctx, UOTK_ERR_INVALID, "autotune: out is null");
+  if (d < 1 || d > 128) return set_error(ctx, UOTK_ERR_INVALID, "autotune: d = %d not in [1, 128]", d);
+  UOTK_TRY(check_cloud(ctx, "src", src, n, d));
+  UOTK_TRY(check_cloud(ctx, "w", w, n, 1));
+  UOTK_TRY(check_cloud(ctx, "tgt", tgt, m, d));
+  if (!(eps > 0.0) || !isfinite(eps))
+    return set_error(ctx, UOTK_ERR_INVALID, "eps must be finite and > 0, got %g", eps);
+  if (in && !(in->target_err >= 0.0))
+    return set_error(ctx, UOTK_ERR_INVALID, "autotune: target_err must be >= 0");
+  return op_autotune_sum(ctx, (cudaStream_t)stream, d, src, n, w, tgt, m, eps, in, out, report);
 }
 
 uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x, int64_t n,
@@ -386,6 +420,9 @@ uotk_status uotk_uot_sinkhorn(uotk_ctx* ctx, void* stream, int d, const float* x
   if ((flags & UOTK_CSTAR_INIT) && ((flags & UOTK_WARM_START) || ref != UOTK_REF_PRODUCT))
     return set_error(ctx, UOTK_ERR_INVALID,
                      "UOTK_CSTAR_INIT needs ref = PRODUCT and no UOTK_WARM_START");
+  // UOTK_AUTO: the form of the beta half-step's sum y -> x with the weights b
+  uotk_sum_opts chosen;
+  UOTK_TRY(resolve_auto(ctx, (cudaStream_t)stream, d, y, m, b, x, n, eps, opts, &chosen));
   return op_uot_sinkhorn(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho1, rho2,
                          max_sweeps, tol, ref, flags, beta, gamma, sweeps_done, value, opts);
 }
@@ -531,6 +568,8 @@ uotk_status uotk_sinkhorn_divergence(uotk_ctx* ctx, void* stream, int d, const f
   if (!(eps > 0.0) || !isfinite(eps) || !(rho > 0.0) || !isfinite(rho))
     return set_error(ctx, UOTK_ERR_INVALID, "eps and rho must be finite and > 0");
   if (max_sweeps < 1) return set_error(ctx, UOTK_ERR_INVALID, "max_sweeps must be >= 1");
+  uotk_sum_opts chosen;
+  UOTK_TRY(resolve_auto(ctx, (cudaStream_t)stream, d, y, m, b, x, n, eps, opts, &chosen));
   return op_sinkhorn_divergence(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho,
                                 max_sweeps, tol, sd, parts, opts);
 }
@@ -549,6 +588,8 @@ uotk_status uotk_mmd2(uotk_ctx* ctx, void* stream, int d, const float* x, int64_
   if (!mmd2) return set_error(ctx, UOTK_ERR_INVALID, "mmd2 is null");
   if (!(ell > 0.0) || !isfinite(ell))
     return set_error(ctx, UOTK_ERR_INVALID, "ell must be finite and > 0");
+  uotk_sum_opts chosen;
+  UOTK_TRY(resolve_auto(ctx, (cudaStream_t)stream, d, y, m, b, x, n, ell * ell, opts, &chosen));
   return op_mmd2(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, ell, mmd2, parts, opts);
 }
 
@@ -580,6 +621,8 @@ uotk_status uotk_mmd2_grad(uotk_ctx* ctx, void* stream, int d, const float* x, i
   UOTK_TRY(check_grad_outputs(ctx, d, n, m, grad_a, grad_x, grad_b, grad_y));
   if (!(ell > 0.0) || !isfinite(ell))
     return set_error(ctx, UOTK_ERR_INVALID, "ell must be finite and > 0");
+  uotk_sum_opts chosen;
+  UOTK_TRY(resolve_auto(ctx, (cudaStream_t)stream, d, y, m, b, x, n, ell * ell, opts, &chosen));
   return op_mmd2_grad(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, ell, mmd2, grad_a, grad_x,
                       grad_b, grad_y, opts);
 }
@@ -604,6 +647,8 @@ uotk_status uotk_sinkhorn_divergence_grad(uotk_ctx* ctx, void* stream, int d, co
     return set_error(ctx, UOTK_ERR_INVALID, "eps and rho must be finite and > 0");
   if (max_sweeps < 1) return set_error(ctx, UOTK_ERR_INVALID, "max_sweeps must be >= 1");
   if (!(tol >= 0.0) && !(tol <= 0.0)) return set_error(ctx, UOTK_ERR_INVALID, "tol is NaN");
+  uotk_sum_opts chosen;
+  UOTK_TRY(resolve_auto(ctx, (cudaStream_t)stream, d, y, m, b, x, n, eps, opts, &chosen));
   return op_sinkhorn_divergence_grad(ctx, (cudaStream_t)stream, d, x, n, a, y, m, b, eps, rho,
                                      max_sweeps, tol, sd, parts, grad_a, grad_x, grad_b, grad_y,
                                      opts);

@@ -25,6 +25,19 @@ struct uotk_prof {
   bool created = false;
 };
 
+// One autotuned summation form (see op_autotune_sum), keyed by the problem.
+constexpr int UOTK_AUTO_CACHE = 8;
+struct AutoEntry {
+  bool valid = false;
+  int d = 0;
+  int64_t n = 0, m = 0;
+  double eps = 0.0, target = 0.0;
+  int grid_in = 0, cutoff_in = 0;
+  float box[6] = {0, 0, 0, 0, 0, 0};
+  uotk_sum_opts chosen = {};
+  double report[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+};
+
 struct uotk_ctx {
   int device = 0;
   int num_sms = 0;
@@ -45,6 +58,9 @@ struct uotk_ctx {
   // stream cannot be captured), fenced to the caller's stream with events.
   cudaStream_t gs = nullptr;
   cudaEvent_t fence_in = nullptr, fence_out = nullptr;
+  // autotuned forms, most recent first out
+  AutoEntry autos[UOTK_AUTO_CACHE];
+  int auto_next = 0;
 };
 
 namespace uotk {
@@ -68,6 +84,12 @@ enum FlagSlot {
 };
 
 uotk_status set_error(uotk_ctx* ctx, uotk_status st, const char* fmt, ...);
+
+// The fastest summation form within in->target_err for the sum src -> tgt
+// (autotune.cu; uotk_autotune_sum).
+uotk_status op_autotune_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* src, int64_t n,
+                            const float* w, const float* tgt, int64_t m, double eps,
+                            const uotk_sum_opts* in, uotk_sum_opts* out, double* report);
 
 // One dual half-step of Alg. 1 / Alg. 2 on the targets of a kernel sum t:
 //   pot_i <- -q (log t_i + shift)                 (ref 0)

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libuotk.so")
 
 UOTK_OK = 0
 UOTK_ERR_NOT_CONVERGED = 6
-DIRECT, NFFT, DIRECT_BF16, DIRECT_BF16X3 = 0, 1, 2, 3
+DIRECT, NFFT, DIRECT_BF16, DIRECT_BF16X3, AUTO = 0, 1, 2, 3, 4
 REF_PRODUCT, REF_COUNTING = 0, 1
 WARM_START = 1
 LOG_DOMAIN = 2
@@ -90,6 +90,8 @@ def lib():
         plan = ctypes.POINTER(NfftPlan)
         L.uotk_kernel_sum.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, opts]
         L.uotk_kernel_sum_noalloc.argtypes = [_P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D]
+        L.uotk_autotune_sum.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _D, opts,
+                                        opts, ctypes.POINTER(_D)]
         L.uotk_kernel_sum_noalloc.restype = ctypes.c_int
         L.uotk_uot_sinkhorn.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, _D,
                                         _D, ctypes.c_int, _D, ctypes.c_int, ctypes.c_uint, _P, _P,
@@ -227,7 +229,7 @@ def _opts(method="direct", grid=0, bandwidth=0, cutoff=0, period=0.0, target_err
     """uotk_sum_opts; kernel is one of Table tab:0 (gauss, laplace, imq, energy);
     reg_degree: the NFFT regularisation degree p of the non-Gaussian kernels."""
     m = {"direct": DIRECT, "nfft": NFFT, "direct_bf16": DIRECT_BF16,
-         "direct_bf16x3": DIRECT_BF16X3}.get(method, method)
+         "direct_bf16x3": DIRECT_BF16X3, "auto": AUTO}.get(method, method)
     k = KERNELS.get(kernel, kernel)
     return SumOpts(int(m), int(grid), int(bandwidth), int(cutoff), float(period),
                    float(target_err), int(k), int(reg_degree))
@@ -249,6 +251,30 @@ def kernel_sum(src, w, tgt, eps, method="direct", out=None, ctx=None, **nfft):
                                     _ptr(w), _ptr(tgt), tgt.shape[0], _ptr(out), float(eps),
                                     ctypes.byref(o)))
     return out
+
+
+METHOD_NAMES = {DIRECT: "direct", NFFT: "nfft", DIRECT_BF16: "direct_bf16",
+                DIRECT_BF16X3: "direct_bf16x3"}
+
+
+def autotune_sum(src, w, tgt, eps, target_err=0.0, grid=0, cutoff=0, ctx=None):
+    """uotk_autotune_sum: the fastest summation form for src -> tgt within
+    target_err (max error / sum|w|; 0: 1e-5), measured on this GPU and cached
+    in the context.  Returns (options dict, report dict)."""
+    src, tgt, w = _pts(src, "src"), _pts(tgt, "tgt"), _f32(w, "w").reshape(-1)
+    ctx = ctx or default_context()
+    o = _opts("direct", grid=grid, cutoff=cutoff, target_err=target_err)
+    chosen = SumOpts()
+    rep = (_D * 8)()
+    ctx.check(lib().uotk_autotune_sum(ctx.handle, _stream(), src.shape[1], _ptr(src),
+                                      src.shape[0], _ptr(w), _ptr(tgt), tgt.shape[0],
+                                      float(eps), ctypes.byref(o), ctypes.byref(chosen), rep))
+    opts = {"method": METHOD_NAMES.get(chosen.method, chosen.method), "grid": chosen.grid,
+            "bandwidth": chosen.bandwidth, "cutoff": chosen.cutoff,
+            "target_err": chosen.target_err}
+    report = dict(zip(["ms", "err", "direct_ms", "forms", "grid", "cutoff", "samples",
+                       "target"], list(rep)))
+    return opts, report
 
 
 def kernel_sum_noalloc(src, w, tgt, eps, out):
@@ -567,7 +593,7 @@ def nfft_gather(plan, grid, pts, ctx=None):
 EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_string",
             "uotk_launch_count", "uotk_set_profiling", "uotk_profile_read", "uotk_profile_reset",
             "uotk_set_workspace_limit", "uotk_set_wait_timeout_test",
-            "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_uot_sinkhorn",
+            "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_autotune_sum", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
             "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
             "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_mean_cost",
