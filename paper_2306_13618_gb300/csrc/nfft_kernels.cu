@@ -281,12 +281,14 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
         const int pp0 = t0 >> 1, pp1 = (t1 - 1) >> 1;
         // one point pair: the masked y factor, the m phi_x pairs and the ZB
         // products w phi_z phi_y, all loaded before any FMA of the pair
-        auto load_pair = [&](int pp, unsigned long long (&fx2)[M], unsigned long long (&A2)[ZB]) {
+        // a pair half outside the run (the neighbouring cell's point) is masked:
+        // the run's first pair keeps only its odd point when t0 is odd, its last
+        // pair only its even point when t1 is odd
+        auto load_pair = [&](int pp, unsigned long long (&fx2)[M], unsigned long long (&A2)[ZB],
+                             unsigned long long mask) {
           const float* row = sw + pp * WSP;
           unsigned long long fy2 = *reinterpret_cast<const unsigned long long*>(row + YO2 + 2 * y);
-          // a pair half outside the run (the neighbouring cell's point) is masked
-          if (pp == pp0 && (t0 & 1)) fy2 = f2_mul(fy2, keep_hi);
-          if (pp == pp1 && (t1 & 1)) fy2 = f2_mul(fy2, keep_lo);
+          if (mask) fy2 = f2_mul(fy2, mask);
           const float* xr = row + xh * HP2;
 #pragma unroll
           for (int j = 0; j + 1 < M; j += 2) {
@@ -300,20 +302,41 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
             A2[r] = f2_mul(*reinterpret_cast<const unsigned long long*>(row + ZO2 + 2 * (z0 + r)),
                            fy2);
         };
-        int pp = pp0;
+        int pp = pp0, pe1 = pp1;
+        // the boundary pairs with a masked half, then the inner pairs unmasked
+        if ((t0 & 1) || pp0 == pp1) {
+          unsigned long long m0 = (t0 & 1) ? keep_hi : f2_pack(1.f, 1.f);
+          if (pp0 == pp1 && (t1 & 1)) m0 = f2_mul(m0, keep_lo);
+          unsigned long long fa[M], Aa[ZB];
+          load_pair(pp0, fa, Aa, m0);
+#pragma unroll
+          for (int r = 0; r < ZB; ++r)
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
+          ++pp;
+        }
+        if (pp <= pp1 && (t1 & 1)) {
+          unsigned long long fa[M], Aa[ZB];
+          load_pair(pp1, fa, Aa, keep_lo);
+#pragma unroll
+          for (int r = 0; r < ZB; ++r)
+#pragma unroll
+            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
+          --pe1;
+        }
         // two pairs per iteration: the second pair's loads overlap the first's FMAs
-        for (; pp + 1 <= pp1; pp += 2) {
+        for (; pp + 1 <= pe1; pp += 2) {
           unsigned long long fa[M], fb[M], Aa[ZB], Ab[ZB];
-          load_pair(pp, fa, Aa);
-          load_pair(pp + 1, fb, Ab);
+          load_pair(pp, fa, Aa, 0ull);
+          load_pair(pp + 1, fb, Ab, 0ull);
 #pragma unroll
           for (int r = 0; r < ZB; ++r)
 #pragma unroll
             for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Ab[r], fb[j], f2_fma(Aa[r], fa[j], acc2[r][j]));
         }
-        if (pp <= pp1) {
+        if (pp <= pe1) {
           unsigned long long fa[M], Aa[ZB];
-          load_pair(pp, fa, Aa);
+          load_pair(pp, fa, Aa, 0ull);
 #pragma unroll
           for (int r = 0; r < ZB; ++r)
 #pragma unroll
