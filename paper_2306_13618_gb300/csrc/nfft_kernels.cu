@@ -1527,6 +1527,42 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
   unsigned long long hc[BZ][BZ][MP];
   int cached = -1;
   // this lane's part of the sum of the target with window row `row`, cell `key`
+  // two targets of the same cell (the footprint cached): their sums share the
+  // footprint registers and give six independent FMA chains instead of three
+  auto target_pair = [&](const float* ra, const float* rb, float& pa, float& pb) {
+    unsigned long long Ha[MP], Hb[MP];
+#pragma unroll
+    for (int j = 0; j < MP; ++j) Ha[j] = Hb[j] = 0ull;
+#pragma unroll
+    for (int z = 0; z < BZ; ++z) {
+      const float za = ra[ZO + z0 + z], zb = rb[ZO + z0 + z];
+#pragma unroll
+      for (int yy = 0; yy < BZ; ++yy) {
+        const float a = za * ra[YO + y0 + yy], b = zb * rb[YO + y0 + yy];
+        const unsigned long long A = f2_pack(a, a), B = f2_pack(b, b);
+#pragma unroll
+        for (int j = 0; j < MP; ++j) {
+          Ha[j] = f2_fma(A, hc[z][yy][j], Ha[j]);
+          Hb[j] = f2_fma(B, hc[z][yy][j], Hb[j]);
+        }
+      }
+    }
+    float fa[M], fb[M];
+    load_vec<M>(ra + xh * HP, fa);
+    load_vec<M>(rb + xh * HP, fb);
+    unsigned long long sa = f2_mul(f2_pack(fa[0], fa[1]), Ha[0]);
+    unsigned long long sb = f2_mul(f2_pack(fb[0], fb[1]), Hb[0]);
+#pragma unroll
+    for (int j = 1; j < MP; ++j) {
+      sa = f2_fma(f2_pack(fa[2 * j], fa[2 * j + 1]), Ha[j], sa);
+      sb = f2_fma(f2_pack(fb[2 * j], fb[2 * j + 1]), Hb[j], sb);
+    }
+    float lo, hi;
+    f2_unpack(sa, lo, hi);
+    pa = lo + hi;
+    f2_unpack(sb, lo, hi);
+    pb = lo + hi;
+  };
   auto target_part = [&](const float* row, int key) -> float {
     if (key != cached) {
       const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
@@ -1585,7 +1621,16 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
     for (int p = 0; p < cn; p += 4) {
       float part[4];
 #pragma unroll
-      for (int j = 0; j < 4; ++j) part[j] = p + j < cn ? target_part(sb + (p + j) * WS, skey[p + j]) : 0.f;
+      for (int j = 0; j < 4; j += 2) {
+        if (p + j + 1 < cn && skey[p + j] == skey[p + j + 1]) {
+          // the first call loads the pair's footprint if needed; then both together
+          if (skey[p + j] != cached) (void)target_part(sb + (p + j) * WS, skey[p + j]);
+          target_pair(sb + (p + j) * WS, sb + (p + j + 1) * WS, part[j], part[j + 1]);
+        } else {
+          part[j] = p + j < cn ? target_part(sb + (p + j) * WS, skey[p + j]) : 0.f;
+          part[j + 1] = p + j + 1 < cn ? target_part(sb + (p + j + 1) * WS, skey[p + j + 1]) : 0.f;
+        }
+      }
       const float tsum = warp_sum4(part, lane);
       const int t = p + (lane >> 3);
       if ((lane & 7) == 0 && t < cn) out[q0 + t] = tsum;
