@@ -19,8 +19,8 @@ constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit gr
 // many points: the spread's CTAs (96 threads at m = 6) take small units so that
 // every SM gets several, the gather's (256 threads) larger ones, whose warps then
 // keep long runs of targets.
-constexpr int NFFT_SPREAD_UNIT = 1024;
-constexpr int NFFT_GATHER_UNIT = 2048;
+constexpr int NFFT_SPREAD_UNIT = 512;
+constexpr int NFFT_GATHER_UNIT = 4096;
 constexpr int NFFT_MAX_M = 8;
 constexpr int NFFT_CHUNK = 64;          // default points per bulk-copied staging chunk
 constexpr int NFFT_NEAR_CHUNK = 1024;   // targets per near-field work item
@@ -94,7 +94,8 @@ struct NfftPoints {
   int* unit_tile = nullptr;  // [max_units] tile of each work unit
   int* unit_begin = nullptr; // [max_units] first sorted point of the unit
   int* unit_count = nullptr; // [max_units]
-  int* unit_zr = nullptr;    // [max_units] first and last local z cell (lo | hi << 8)
+  int* unit_box = nullptr;   // [max_units] box of the unit's local cells, written by the
+                             // spread: 4-bit fields zlo, zhi, ylo, yhi, xlo, xhi (bits 0..23)
   int* num_units = nullptr;  // [1] device count
   int* tile_unit_start = nullptr;  // [tiles+1] first unit of each tile
   int max_units = 0;

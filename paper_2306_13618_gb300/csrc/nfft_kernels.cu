@@ -151,15 +151,17 @@ __device__ __forceinline__ void stage_pairs(float* st, unsigned long long* bar, 
 // POT: the weights are the half-step's w = base e^{lam pot - shift}, formed here
 // when a chunk lands (threads WT0.. hold the pot and base of the chunk's points,
 // loaded a chunk ahead; wts unused); else they are staged from wts.  Points of
-// a pair that lie outside the unit get weight 0.  The finished block's z-planes
-// that the unit's cells reach (unit_zr) go to blocks[u]; k_fold_units and
-// k_fold add the blocks into the grid.
+// a pair that lie outside the unit get weight 0.  The warp that lists the cell
+// runs also takes the range of local z and y cells of the unit; the block's
+// entries that those cells reach (z-planes and y-rows, whole x-rows) go to
+// blocks[u], and the range to unit_box[u] for k_fold_units and k_fold, which
+// add the blocks into the grid.
 template <int M, bool POT, int CP>
 __global__ void __launch_bounds__(SpreadMap<M>::NTH)
     k_spread(const float* __restrict__ winp, const int* __restrict__ ckey,
              const float* __restrict__ wts, const int* __restrict__ unit_tile,
              const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
-             const int* __restrict__ unit_zr, const int* __restrict__ num_units, int tiles1,
+             int* __restrict__ unit_box, const int* __restrict__ num_units, int tiles1,
              float* __restrict__ blocks, long long* __restrict__ flags, SpreadWeights pw) {
   using SG = SpreadGeo<M, CP>;
   using SM = SpreadMap<M>;
@@ -223,6 +225,9 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
   const int y = (threadIdx.x >> 1) % W2;
   const int z0 = ((threadIdx.x >> 1) / W2) * ZB;
   const int lane = threadIdx.x & 31;
+  // range of the unit's local z and y cells (kept by the listing warp)
+  int bz_lo = NFFT_TILE, bz_hi = -1, by_lo = NFFT_TILE, by_hi = -1;
+  __shared__ int box_s;
   const unsigned long long keep_hi = f2_pack(0.f, 1.f), keep_lo = f2_pack(1.f, 0.f);
   for (int k = 0; k < nchunks; ++k) {
     if (!stage_ready(bars, k, nchunks, flags, &never)) return;
@@ -262,7 +267,15 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
         const int t = h + lane;
         const bool f = t >= lo && t < hi && (t == lo || skey[t] != skey[t - 1]);
         const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (f) gstart[base + __popc(bal & ((1u << lane) - 1u))] = t;
+        if (f) {
+          gstart[base + __popc(bal & ((1u << lane) - 1u))] = t;
+          const int key = skey[t];
+          const int cz = (key >> 20) - tz0, cy = ((key >> 10) & 1023) - ty0;
+          bz_lo = min(bz_lo, cz);
+          bz_hi = max(bz_hi, cz);
+          by_lo = min(by_lo, cy);
+          by_hi = max(by_hi, cy);
+        }
         base += __popc(bal);
       }
       if (lane == 0) { ngroups = base; gstart[base] = hi; }
@@ -360,34 +373,49 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
                          POT ? nullptr : wts, pc0 + STAGES * CP,
                          min(CP, pe - pc0 - STAGES * CP));
   }
+  if (threadIdx.x < 32) {
+    bz_lo = warp_min_i(bz_lo);
+    bz_hi = warp_max_i(bz_hi);
+    by_lo = warp_min_i(by_lo);
+    by_hi = warp_max_i(by_hi);
+    if (lane == 0) {
+      const int box = bz_lo | (bz_hi << 4) | (by_lo << 8) | (by_hi << 12);
+      box_s = box;
+      unit_box[u] = box;
+    }
+  }
   __syncthreads();
-  // the z-planes the unit's cells reach: local z cells zlo .. zhi, planes
-  // zlo .. zhi + 2m - 1
-  const int zr = unit_zr[u];
-  const int i0 = (zr & 255) * E2, i1 = min(E3, ((zr >> 8) + W2) * E2);
+  // the entries the unit's cells reach: local cells z in [zlo, zhi], y in
+  // [ylo, yhi] reach block planes zlo .. zhi + 2m - 1 and rows ylo .. yhi + 2m - 1
+  const int box = box_s;
+  const int pz0 = box & 15, pz1 = ((box >> 4) & 15) + W2;
+  const int py0 = (box >> 8) & 15, ny = ((box >> 12) & 15) + W2 - py0;
   float* outb = blocks + (size_t)u * SG::E3P;
-  for (int i = i0 + threadIdx.x; i < i1; i += NT) outb[i] = blk[i];
+  for (int pz = pz0; pz < pz1; ++pz) {
+    const int i0 = (pz * E + py0) * E;
+    for (int q = threadIdx.x; q < ny * E; q += NT) outb[i0 + q] = blk[i0 + q];
+  }
 }
 
 // Fold, step 1: the units of one tile (a tile with more than NFFT_SPREAD_UNIT
 // points has several) are summed into the block of the tile's first unit, in
-// a fixed order; a unit contributes to the z-planes it wrote (unit_zr).  The U
+// a fixed order; a unit contributes the entries it wrote (unit_box).  The U
 // units of a tile share the work: CTA k of the tile takes the k-th of U slices
 // of the block's entries.  When a slice has fewer entries than the CTA has
 // threads, G groups of threads each sum the units g, g + G, g + 2G, .. of
 // every entry, and the G partial sums are then added in group order: a dense
 // tile costs about one block's reads per CTA and short dependency chains.
 constexpr int FOLD_THREADS = 256;
-constexpr int FOLD_ZR_CACHE = 2048;   // unit z ranges of a tile held in shared memory
+constexpr int FOLD_BOX_CACHE = 2048;  // unit boxes of a tile held in shared memory
 template <int M>
 __global__ void __launch_bounds__(FOLD_THREADS)
     k_fold_units(float* __restrict__ blocks, const int* __restrict__ unit_tile,
-                 const int* __restrict__ tile_unit_start, const int* __restrict__ unit_zr,
+                 const int* __restrict__ tile_unit_start, const int* __restrict__ unit_box,
                  const int* __restrict__ num_units) {
   constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1, E2 = E * E, E3 = E2 * E;
   constexpr int E3P = (E3 + 3) & ~3;
   __shared__ float part[FOLD_THREADS];
-  __shared__ short zlo[FOLD_ZR_CACHE], zhi[FOLD_ZR_CACHE];
+  __shared__ int boxes[FOLD_BOX_CACHE];
   const int u = blockIdx.x;
   if (u >= *num_units) return;
   const int t = unit_tile[u];
@@ -398,26 +426,18 @@ __global__ void __launch_bounds__(FOLD_THREADS)
   const int e0 = min(E3, k * chunk), e1 = min(E3, e0 + chunk);
   const int ne = e1 - e0;
   if (ne <= 0) return;
-  for (int v = threadIdx.x; v < U && v < FOLD_ZR_CACHE; v += FOLD_THREADS) {
-    const int zr = unit_zr[u0 + v];
-    zlo[v] = (short)(zr & 255);
-    zhi[v] = (short)((zr >> 8) + W2);
-  }
+  for (int v = threadIdx.x; v < U && v < FOLD_BOX_CACHE; v += FOLD_THREADS)
+    boxes[v] = unit_box[u0 + v];
   __syncthreads();
   float* first = blocks + (size_t)u0 * E3P;
-  // block entry e of unit v, or 0 where that unit wrote nothing (its z-planes)
+  // block entry e of unit v, or 0 where that unit wrote nothing (outside the
+  // z-planes and y-rows of its box)
   auto entry = [&](int v, int e) -> float {
-    int lo, hi;
-    if (v < FOLD_ZR_CACHE) {
-      lo = zlo[v];
-      hi = zhi[v];
-    } else {
-      const int zr = unit_zr[u0 + v];
-      lo = zr & 255;
-      hi = (zr >> 8) + W2;
-    }
-    const int pz = e / E2;
-    return pz >= lo && pz < hi ? first[(size_t)v * E3P + e] : 0.f;
+    const int box = v < FOLD_BOX_CACHE ? boxes[v] : unit_box[u0 + v];
+    const int pz = e / E2, py = (e / E) % E;
+    const bool in = pz >= (box & 15) && pz < ((box >> 4) & 15) + W2 &&
+                    py >= ((box >> 8) & 15) && py < ((box >> 12) & 15) + W2;
+    return in ? first[(size_t)v * E3P + e] : 0.f;
   };
   // G groups of threads per entry; group g sums the units g, g + G, ..: eight
   // running sums (unit index mod 8 within the group) keep eight loads in
@@ -465,18 +485,18 @@ __global__ void __launch_bounds__(FOLD_THREADS)
 template <int M>
 __global__ void __launch_bounds__(512)
     k_fold(const float* __restrict__ blocks, const int* __restrict__ tile_unit_start,
-           const int* __restrict__ unit_zr, int n, int tiles1, float* __restrict__ grid) {
+           const int* __restrict__ unit_box, int n, int tiles1, float* __restrict__ grid) {
   constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1;
   constexpr int E3P = (E * E * E + 3) & ~3;
   static_assert(M - 1 < NFFT_TILE, "a block reaches at most one tile beyond its own");
-  __shared__ int first[27], offs[27], zlo[27], zhi[27];
+  __shared__ int first[27], offs[27], zlo[27], zhi[27], ylo[27], yhi[27];
   __shared__ int nlist;
   const int t0 = blockIdx.x;
   const int tx = t0 % tiles1, ty = (t0 / tiles1) % tiles1, tz = t0 / (tiles1 * tiles1);
   if (threadIdx.x < 32) {
     // the non-empty neighbour tiles, listed in offset order
     const int c = threadIdx.x;
-    int us = -1, lo = 0, hi = E;
+    int us = -1, lo = 0, hi = E, ylo_ = 0, yhi_ = E;
     if (c < 27) {
       const int dz = c / 9 - 1, dy = (c / 3) % 3 - 1, dx = c % 3 - 1;
       const int T = (((tz + dz + tiles1) % tiles1) * tiles1 + (ty + dy + tiles1) % tiles1) *
@@ -485,9 +505,11 @@ __global__ void __launch_bounds__(512)
       if (b > a) {
         us = a;
         if (b - a == 1) {
-          const int zr = unit_zr[a];
-          lo = zr & 255;
-          hi = (zr >> 8) + W2;
+          const int box = unit_box[a];
+          lo = box & 15;
+          hi = ((box >> 4) & 15) + W2;
+          ylo_ = (box >> 8) & 15;
+          yhi_ = ((box >> 12) & 15) + W2;
         }
       }
     }
@@ -498,6 +520,8 @@ __global__ void __launch_bounds__(512)
       offs[slot] = c;
       zlo[slot] = lo;
       zhi[slot] = hi;
+      ylo[slot] = ylo_;
+      yhi[slot] = yhi_;
     }
     if (c == 0) nlist = __popc(bal);
   }
@@ -524,7 +548,7 @@ __global__ void __launch_bounds__(512)
         const int dz = c / 9 - 1, dy = (c / 3) % 3 - 1, dx = c % 3 - 1;
         const int Lz = lz - NFFT_TILE * dz + M - 1, Ly = ly - NFFT_TILE * dy + M - 1,
                   Lx = lx - NFFT_TILE * dx + M - 1;
-        if (Lz >= zlo[q] && Lz < zhi[q] && Ly >= 0 && Ly < E && Lx >= 0 && Lx < E)
+        if (Lz >= zlo[q] && Lz < zhi[q] && Ly >= ylo[q] && Ly < yhi[q] && Lx >= 0 && Lx < E)
           t[j] = blocks[(size_t)first[q] * E3P + (Lz * E + Ly) * E + Lx];
       }
     }
@@ -1699,18 +1723,18 @@ uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
     UOTK_PROF(ctx, s, "spread");
     UOTK_CUDA(ctx, smem_attr(s, kern, smem));
     kern<<<S.max_units, NT, smem, s>>>(S.winp, S.ckey, wts, S.unit_tile, S.unit_begin,
-                                       S.unit_count, S.unit_zr, S.num_units, P.tiles1, W.blocks,
+                                       S.unit_count, S.unit_box, S.num_units, P.tiles1, W.blocks,
                                        ctx->dflags, pw ? *pw : SpreadWeights{});
     UOTK_LAUNCHED(ctx);
   }
   {
     UOTK_PROF(ctx, s, "fold");
     k_fold_units<M><<<S.max_units, FOLD_THREADS, 0, s>>>(W.blocks, S.unit_tile,
-                                                         S.tile_unit_start, S.unit_zr,
+                                                         S.tile_unit_start, S.unit_box,
                                                          S.num_units);
     UOTK_LAUNCHED(ctx);
     k_fold<M><<<P.tiles1 * P.tiles1 * P.tiles1, 512, 0, s>>>(W.blocks, S.tile_unit_start,
-                                                             S.unit_zr, P.n, P.tiles1, grid);
+                                                             S.unit_box, P.n, P.tiles1, grid);
     UOTK_LAUNCHED(ctx);
   }
   return UOTK_OK;

@@ -578,7 +578,7 @@ void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S
   S.unit_tile = cv.take<int>(S.max_units + 1);
   S.unit_begin = cv.take<int>(S.max_units + 1);
   S.unit_count = cv.take<int>(S.max_units + 1);
-  S.unit_zr = cv.take<int>(S.max_units + 1);
+  S.unit_box = cv.take<int>(S.max_units + 1);
   S.num_units = cv.take<int>(1);
   S.g_tile_unit_start = cv.take<int>(tiles + 1);
   S.g_unit_tile = cv.take<int>(S.g_max_units + 1);
@@ -656,7 +656,7 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
     }
     k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.tile_unit_start, tiles,
                                                           NFFT_SPREAD_UNIT, S.ckey, S.unit_tile,
-                                                          S.unit_begin, S.unit_count, S.unit_zr);
+                                                          S.unit_begin, S.unit_count, nullptr);
     UOTK_LAUNCHED(ctx);
     k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.g_tile_unit_start,
                                                           tiles, NFFT_GATHER_UNIT, S.ckey,
