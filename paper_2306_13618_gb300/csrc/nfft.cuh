@@ -14,13 +14,23 @@
 namespace uotk {
 
 constexpr int NFFT_TILE = 8;           // grid cells per tile edge (work-unit granularity)
-// Points per work unit.  Clustered clouds fill few tiles (the 2^20-point
-// mixture workload: 83 of 4096), so a tile is cut into units of at most this
-// many points: the spread's CTAs (96 threads at m = 6) take small units so that
-// every SM gets several, the gather's (256 threads) larger ones, whose warps then
-// keep long runs of targets.
-constexpr int NFFT_SPREAD_UNIT = 512;
-constexpr int NFFT_GATHER_UNIT = 4096;
+// Work split.  Clustered clouds fill few tiles (the 2^20-point mixture
+// workload: 83 of 4096, one of them with a quarter of the points), so work is
+// not cut by tile.  Every point costs 1, every occupied cell and every
+// occupied tile a fixed cost (a cell's run of points ends in a flush or a
+// footprint load, a tile's block is staged and written once per piece), in
+// points; the sorted points, each cell's and tile's cost before its first
+// point, are cut into chunks of equal cost Q, one chunk per CTA that the GPU
+// holds at once, and a chunk is cut further where a tile ends.  These pieces
+// are the work units: a piece lies in one tile (its CTA stages that tile's
+// block) and a CTA takes the pieces of its chunk in turn.  Q is at least the
+// minimum.
+constexpr int NFFT_SPREAD_TILE_COST = 64;
+constexpr int NFFT_GATHER_TILE_COST = 128;
+constexpr int NFFT_SPREAD_CELL_COST = 8;
+constexpr int NFFT_GATHER_CELL_COST = 8;
+constexpr int NFFT_SPREAD_MIN_CHUNK = 64;
+constexpr int NFFT_GATHER_MIN_CHUNK = 256;
 constexpr int NFFT_MAX_M = 8;
 constexpr int NFFT_CHUNK = 64;          // default points per bulk-copied staging chunk
 constexpr int NFFT_NEAR_CHUNK = 1024;   // targets per near-field work item
@@ -90,7 +100,10 @@ struct NfftPoints {
   float* winp = nullptr;     // [ceil(n/2)][nfft_winp_stride(m)] pair window rows (spread)
   int* perm = nullptr;       // sorted position -> caller index
   int* tile_start = nullptr; // [tiles+1] start of each tile in sorted order
-  // spread work units (at most NFFT_SPREAD_UNIT points of one tile)
+  int* tile_rank = nullptr;  // [tiles+1] occupied tiles before each tile
+  int* cell_rank = nullptr;  // [n^3+1] occupied cells before each cell (tile-major order)
+  long long* chunk_q = nullptr;  // [2] cost per chunk: spread, gather
+  // spread work units (pieces of the c_spread chunks, each in one tile)
   int* unit_tile = nullptr;  // [max_units] tile of each work unit
   int* unit_begin = nullptr; // [max_units] first sorted point of the unit
   int* unit_count = nullptr; // [max_units]
@@ -98,16 +111,22 @@ struct NfftPoints {
                              // spread: 4-bit fields zlo, zhi, ylo, yhi, xlo, xhi (bits 0..23)
   int* num_units = nullptr;  // [1] device count
   int* tile_unit_start = nullptr;  // [tiles+1] first unit of each tile
+  int* unit_chunk = nullptr;       // [max_units] chunk of each unit
+  int* chunk_unit_start = nullptr; // [c_spread+1] first unit of each chunk
   int max_units = 0;
-  // gather work units (at most NFFT_GATHER_UNIT points of one tile)
+  int c_spread = 0;                // chunks (CTAs of the spread)
+  // gather work units (pieces of the c_gather chunks, each in one tile)
   int* g_unit_tile = nullptr;
   int* g_unit_begin = nullptr;
   int* g_unit_count = nullptr;
   int* g_num_units = nullptr;
   int* g_tile_unit_start = nullptr;
+  int* g_unit_chunk = nullptr;
+  int* g_chunk_unit_start = nullptr;
   int g_max_units = 0;
+  int c_gather = 0;
   int* scratch = nullptr;    // [tiles] counters
-  int* cell_count = nullptr; // [n^3] histogram
+  int* cell_count = nullptr; // [n^3] histogram, then 0/1 occupied flags
   int* cell_start = nullptr; // [n^3 + 1] exclusive scan
   int* block_sums = nullptr; // scan partials
   // stable radix sort of the cell keys (deterministic order inside a cell)
@@ -168,6 +187,11 @@ uotk_status nfft_near(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const 
 uotk_status nfft_bbox(uotk_ctx* ctx, cudaStream_t s, int d, const float* a, int64_t na,
                       const float* b, int64_t nb, float lo[3], float hi[3]);
 
-int nfft_max_units(const NfftParams& P, int64_t n, int unit_points = NFFT_SPREAD_UNIT);
+// Upper bound of the work units of n points cut into `chunks` chunks.
+int nfft_max_units(const NfftParams& P, int64_t n, int chunks);
+// Chunks of the spread and of the gather at cut-off m: the CTAs of the kernel
+// that the device holds at once.
+int nfft_spread_slots(int m);
+int nfft_gather_slots(int m);
 
 }  // namespace uotk

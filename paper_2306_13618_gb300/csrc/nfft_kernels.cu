@@ -4,9 +4,12 @@
 //
 // Work units.  Points are sorted by grid cell, cells tile by tile (8^3 cells
 // per tile), and inside a cell in caller order (a stable sort), so every sum
-// below is taken in the same order on every run.  A unit is (tile, up to
-// NFFT_SPREAD_UNIT or NFFT_GATHER_UNIT points); its CTA owns the E^3 block of
-// grid nodes the tile's windows reach (E = 8 + 2m - 1).  Window rows, cells and
+// below is taken in the same order on every run.  The sorted points are cut
+// into chunks of equal cost (points, plus a fixed cost per occupied cell and
+// tile), one per CTA the device holds at once, and a chunk into units where a
+// tile ends; a CTA takes its chunk's units in turn, and for each owns the E^3
+// block of grid nodes the unit's tile reaches with its windows
+// (E = 8 + 2m - 1).  Window rows, cells and
 // weights arrive in shared memory by double-buffered 1-D bulk copies (TMA)
 // completing on mbarriers, so the copy of the next chunk overlaps the
 // arithmetic of the current one.
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
     k_spread(const float* __restrict__ winp, const int* __restrict__ ckey,
              const float* __restrict__ wts, const int* __restrict__ unit_tile,
              const int* __restrict__ unit_begin, const int* __restrict__ unit_count,
-             int* __restrict__ unit_box, const int* __restrict__ num_units, int tiles1,
+             int* __restrict__ unit_box, const int* __restrict__ chunk_unit_start, int tiles1,
              float* __restrict__ blocks, long long* __restrict__ flags, SpreadWeights pw) {
   using SG = SpreadGeo<M, CP>;
   using SM = SpreadMap<M>;
@@ -183,222 +186,231 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
   __shared__ int ngroups;
   float* blk = smem;
   float* stage0 = smem + SG::E3P;
-  const int u = blockIdx.x;
-  if (u >= *num_units) return;
-  const int b0 = unit_begin[u], e0 = b0 + unit_count[u];
-  const int pb = b0 >> 1, pe = (e0 + 1) >> 1;
-  const int nchunks = (pe - pb + CP - 1) / CP;
+  // the CTA's chunk: units ubeg .. uend - 1, taken in turn; kb counts the
+  // staging chunks of the earlier units (the barriers' phases run on)
+  const int ubeg = chunk_unit_start[blockIdx.x], uend = chunk_unit_start[blockIdx.x + 1];
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) mbar_init(&bars[s], 1);
     mbar_init(&never, 1);
     mbar_fence_init();
-    for (int k = 0; k < STAGES && k < nchunks; ++k)
-      stage_pairs<M, CP>(stage0 + k * SG::STAGE_F, &bars[k], winp, ckey, POT ? nullptr : wts,
-                         pb + k * CP, min(CP, pe - pb - k * CP));
   }
   // POT: FP64 work by whole warps (FP64 is scarce on this GPU and a partial
   // warp costs the pipe a whole one)
   const int wt = (int)threadIdx.x - WT0;
-  double ppot[WK], shift = 0.0;
-  float pbase[WK];
-  auto prefetch = [&](int pc0) {
-#pragma unroll
-    for (int j = 0; j < WK; ++j) {
-      const int q = 2 * pc0 + wt + j * WTN;
-      ppot[j] = 0.0;
-      pbase[j] = 1.f;
-      if (wt >= 0 && wt + j * WTN < CPT && q >= b0 && q < e0) {
-        ppot[j] = pw.pot[q];
-        if (pw.base) pbase[j] = pw.base[q];
-      }
-    }
-  };
-  if (POT) {
-    shift = ordered_to_dbl(*pw.shift_slot);
-    prefetch(pb);
-  }
-  for (int i = threadIdx.x; i < E3; i += NT) blk[i] = 0.f;
-  __syncthreads();  // barriers initialised and block zeroed before anyone waits or adds
-  int tx0, ty0, tz0;
-  tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   const int xh = threadIdx.x & 1;
   const int y = (threadIdx.x >> 1) % W2;
   const int z0 = ((threadIdx.x >> 1) / W2) * ZB;
   const int lane = threadIdx.x & 31;
-  // range of the unit's local z and y cells (kept by the listing warp)
-  int bz_lo = NFFT_TILE, bz_hi = -1, by_lo = NFFT_TILE, by_hi = -1;
   __shared__ int box_s;
   const unsigned long long keep_hi = f2_pack(0.f, 1.f), keep_lo = f2_pack(1.f, 0.f);
-  for (int k = 0; k < nchunks; ++k) {
-    if (!stage_ready(bars, k, nchunks, flags, &never)) return;
-    const int pc0 = pb + k * CP, cpn = min(CP, pe - pc0), P0 = 2 * pc0;
-    const int lo = max(b0, P0) - P0, hi = min(e0, P0 + 2 * cpn) - P0;  // unit positions
-    float* sw = stage0 + (k % STAGES) * SG::STAGE_F;
-    const int koff = P0 & 3;
-    const int* skey = reinterpret_cast<const int*>(sw + CP * WSP) + koff;
-    const float* swt = sw + CP * WSP + CPT + 4 + koff;
-    // Fold each point's weight into its phi_z lane (0 outside the unit), and
-    // list where each cell's run of points starts (points are sorted by cell).
-    if (POT) {
-      if (wt >= 0) {
-#pragma unroll
-        for (int j = 0; j < WK; ++j) {
-          const int t = wt + j * WTN;
-          if (t < 2 * cpn) {
-            const float w = (t >= lo && t < hi) ? pbase[j] * exp_shifted(pw.lam * ppot[j] - shift)
-                                                : 0.f;
-            float* zr = sw + (t >> 1) * WSP + ZO2 + (t & 1);
-#pragma unroll
-            for (int i = 0; i < W2; ++i) zr[2 * i] *= w;
-          }
-        }
-        if (k + 1 < nchunks) prefetch(pc0 + CP);
-      }
-    } else {
-      for (int i = threadIdx.x; i < 2 * cpn * W2; i += NT) {
-        const int t = i / W2, z = i - t * W2;
-        const float w = (t >= lo && t < hi) ? swt[t] : 0.f;
-        sw[(t >> 1) * WSP + ZO2 + 2 * z + (t & 1)] *= w;
-      }
+  double shift = 0.0;
+  if (POT) shift = ordered_to_dbl(*pw.shift_slot);
+  int kb = 0;
+  for (int u = ubeg; u < uend; ++u) {
+    const int b0 = unit_begin[u], e0 = b0 + unit_count[u];
+    const int pb = b0 >> 1, pe = (e0 + 1) >> 1;
+    const int nchunks = (pe - pb + CP - 1) / CP;
+    if (threadIdx.x == 0) {
+      // the staging buffers were last read by the generic proxy (previous unit)
+      if (u != ubeg) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int k = 0; k < STAGES && k < nchunks; ++k)
+        stage_pairs<M, CP>(stage0 + ((kb + k) % STAGES) * SG::STAGE_F, &bars[(kb + k) % STAGES],
+                           winp, ckey, POT ? nullptr : wts, pb + k * CP, min(CP, pe - pb - k * CP));
     }
-    if (threadIdx.x < 32) {
-      int base = 0;
-      for (int h = 0; h < CPT; h += 32) {
-        const int t = h + lane;
-        const bool f = t >= lo && t < hi && (t == lo || skey[t] != skey[t - 1]);
-        const unsigned bal = __ballot_sync(0xffffffffu, f);
-        if (f) {
-          gstart[base + __popc(bal & ((1u << lane) - 1u))] = t;
-          const int key = skey[t];
-          const int cz = (key >> 20) - tz0, cy = ((key >> 10) & 1023) - ty0;
-          bz_lo = min(bz_lo, cz);
-          bz_hi = max(bz_hi, cz);
-          by_lo = min(by_lo, cy);
-          by_hi = max(by_hi, cy);
+    double ppot[WK];
+    float pbase[WK];
+    auto prefetch = [&](int pc0) {
+  #pragma unroll
+      for (int j = 0; j < WK; ++j) {
+        const int q = 2 * pc0 + wt + j * WTN;
+        ppot[j] = 0.0;
+        pbase[j] = 1.f;
+        if (wt >= 0 && wt + j * WTN < CPT && q >= b0 && q < e0) {
+          ppot[j] = pw.pot[q];
+          if (pw.base) pbase[j] = pw.base[q];
         }
-        base += __popc(bal);
       }
-      if (lane == 0) { ngroups = base; gstart[base] = hi; }
-    }
-    __syncthreads();
-    const int ng = ngroups;
-    for (int g = 0; g < ng; ++g) {
-      if (owner) {
-        const int t0 = gstart[g], t1 = gstart[g + 1];
-        const int key = skey[t0];
-        unsigned long long acc2[ZB][M];
-#pragma unroll
-        for (int r = 0; r < ZB; ++r)
-#pragma unroll
-          for (int j = 0; j < M; ++j) acc2[r][j] = 0ull;
-        const int pp0 = t0 >> 1, pp1 = (t1 - 1) >> 1;
-        // one point pair: the masked y factor, the m phi_x pairs and the ZB
-        // products w phi_z phi_y, all loaded before any FMA of the pair
-        // a pair half outside the run (the neighbouring cell's point) is masked:
-        // the run's first pair keeps only its odd point when t0 is odd, its last
-        // pair only its even point when t1 is odd
-        auto load_pair = [&](int pp, unsigned long long (&fx2)[M], unsigned long long (&A2)[ZB],
-                             unsigned long long mask) {
-          const float* row = sw + pp * WSP;
-          unsigned long long fy2 = *reinterpret_cast<const unsigned long long*>(row + YO2 + 2 * y);
-          if (mask) fy2 = f2_mul(fy2, mask);
-          const float* xr = row + xh * HP2;
-#pragma unroll
-          for (int j = 0; j + 1 < M; j += 2) {
-            const float4 v = *reinterpret_cast<const float4*>(xr + 2 * j);
-            fx2[j] = f2_pack(v.x, v.y);
-            fx2[j + 1] = f2_pack(v.z, v.w);
+    };
+    if (POT) prefetch(pb);
+    for (int i = threadIdx.x; i < E3; i += NT) blk[i] = 0.f;
+    __syncthreads();  // barriers initialised and block zeroed before anyone waits or adds
+    int tx0, ty0, tz0;
+    tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
+    // range of the unit's local z and y cells (kept by the listing warp)
+    int bz_lo = NFFT_TILE, bz_hi = -1, by_lo = NFFT_TILE, by_hi = -1;
+    for (int k = 0; k < nchunks; ++k) {
+      if (!stage_ready(bars, kb + k, kb + nchunks, flags, &never)) return;
+      const int pc0 = pb + k * CP, cpn = min(CP, pe - pc0), P0 = 2 * pc0;
+      const int lo = max(b0, P0) - P0, hi = min(e0, P0 + 2 * cpn) - P0;  // unit positions
+      float* sw = stage0 + ((kb + k) % STAGES) * SG::STAGE_F;
+      const int koff = P0 & 3;
+      const int* skey = reinterpret_cast<const int*>(sw + CP * WSP) + koff;
+      const float* swt = sw + CP * WSP + CPT + 4 + koff;
+      // Fold each point's weight into its phi_z lane (0 outside the unit), and
+      // list where each cell's run of points starts (points are sorted by cell).
+      if (POT) {
+        if (wt >= 0) {
+  #pragma unroll
+          for (int j = 0; j < WK; ++j) {
+            const int t = wt + j * WTN;
+            if (t < 2 * cpn) {
+              const float w = (t >= lo && t < hi) ? pbase[j] * exp_shifted(pw.lam * ppot[j] - shift)
+                                                  : 0.f;
+              float* zr = sw + (t >> 1) * WSP + ZO2 + (t & 1);
+  #pragma unroll
+              for (int i = 0; i < W2; ++i) zr[2 * i] *= w;
+            }
           }
-          if (M & 1) fx2[M - 1] = *reinterpret_cast<const unsigned long long*>(xr + 2 * (M - 1));
-#pragma unroll
-          for (int r = 0; r < ZB; ++r)
-            A2[r] = f2_mul(*reinterpret_cast<const unsigned long long*>(row + ZO2 + 2 * (z0 + r)),
-                           fy2);
-        };
-        int pp = pp0, pe1 = pp1;
-        // the boundary pairs with a masked half, then the inner pairs unmasked
-        if ((t0 & 1) || pp0 == pp1) {
-          unsigned long long m0 = (t0 & 1) ? keep_hi : f2_pack(1.f, 1.f);
-          if (pp0 == pp1 && (t1 & 1)) m0 = f2_mul(m0, keep_lo);
-          unsigned long long fa[M], Aa[ZB];
-          load_pair(pp0, fa, Aa, m0);
-#pragma unroll
-          for (int r = 0; r < ZB; ++r)
-#pragma unroll
-            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
-          ++pp;
+          if (k + 1 < nchunks) prefetch(pc0 + CP);
         }
-        if (pp <= pp1 && (t1 & 1)) {
-          unsigned long long fa[M], Aa[ZB];
-          load_pair(pp1, fa, Aa, keep_lo);
-#pragma unroll
-          for (int r = 0; r < ZB; ++r)
-#pragma unroll
-            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
-          --pe1;
+      } else {
+        for (int i = threadIdx.x; i < 2 * cpn * W2; i += NT) {
+          const int t = i / W2, z = i - t * W2;
+          const float w = (t >= lo && t < hi) ? swt[t] : 0.f;
+          sw[(t >> 1) * WSP + ZO2 + 2 * z + (t & 1)] *= w;
         }
-        // two pairs per iteration: the second pair's loads overlap the first's FMAs
-        for (; pp + 1 <= pe1; pp += 2) {
-          unsigned long long fa[M], fb[M], Aa[ZB], Ab[ZB];
-          load_pair(pp, fa, Aa, 0ull);
-          load_pair(pp + 1, fb, Ab, 0ull);
-#pragma unroll
-          for (int r = 0; r < ZB; ++r)
-#pragma unroll
-            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Ab[r], fb[j], f2_fma(Aa[r], fa[j], acc2[r][j]));
-        }
-        if (pp <= pe1) {
-          unsigned long long fa[M], Aa[ZB];
-          load_pair(pp, fa, Aa, 0ull);
-#pragma unroll
-          for (int r = 0; r < ZB; ++r)
-#pragma unroll
-            for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
-        }
-        const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-        float* dst = blk + ((bz + z0) * E + by + y) * E + bx + xh * M;
-#pragma unroll
-        for (int r = 0; r < ZB; ++r)
-#pragma unroll
-          for (int j = 0; j < M; ++j) {
-            float e, o;
-            f2_unpack(acc2[r][j], e, o);
-            dst[r * E2 + j] += e + o;
+      }
+      if (threadIdx.x < 32) {
+        int base = 0;
+        for (int h = 0; h < CPT; h += 32) {
+          const int t = h + lane;
+          const bool f = t >= lo && t < hi && (t == lo || skey[t] != skey[t - 1]);
+          const unsigned bal = __ballot_sync(0xffffffffu, f);
+          if (f) {
+            gstart[base + __popc(bal & ((1u << lane) - 1u))] = t;
+            const int key = skey[t];
+            const int cz = (key >> 20) - tz0, cy = ((key >> 10) & 1023) - ty0;
+            bz_lo = min(bz_lo, cz);
+            bz_hi = max(bz_hi, cz);
+            by_lo = min(by_lo, cy);
+            by_hi = max(by_hi, cy);
           }
+          base += __popc(bal);
+        }
+        if (lane == 0) { ngroups = base; gstart[base] = hi; }
       }
       __syncthreads();
+      const int ng = ngroups;
+      for (int g = 0; g < ng; ++g) {
+        if (owner) {
+          const int t0 = gstart[g], t1 = gstart[g + 1];
+          const int key = skey[t0];
+          unsigned long long acc2[ZB][M];
+  #pragma unroll
+          for (int r = 0; r < ZB; ++r)
+  #pragma unroll
+            for (int j = 0; j < M; ++j) acc2[r][j] = 0ull;
+          const int pp0 = t0 >> 1, pp1 = (t1 - 1) >> 1;
+          // one point pair: the masked y factor, the m phi_x pairs and the ZB
+          // products w phi_z phi_y, all loaded before any FMA of the pair
+          // a pair half outside the run (the neighbouring cell's point) is masked:
+          // the run's first pair keeps only its odd point when t0 is odd, its last
+          // pair only its even point when t1 is odd
+          auto load_pair = [&](int pp, unsigned long long (&fx2)[M], unsigned long long (&A2)[ZB],
+                               unsigned long long mask) {
+            const float* row = sw + pp * WSP;
+            unsigned long long fy2 = *reinterpret_cast<const unsigned long long*>(row + YO2 + 2 * y);
+            if (mask) fy2 = f2_mul(fy2, mask);
+            const float* xr = row + xh * HP2;
+  #pragma unroll
+            for (int j = 0; j + 1 < M; j += 2) {
+              const float4 v = *reinterpret_cast<const float4*>(xr + 2 * j);
+              fx2[j] = f2_pack(v.x, v.y);
+              fx2[j + 1] = f2_pack(v.z, v.w);
+            }
+            if (M & 1) fx2[M - 1] = *reinterpret_cast<const unsigned long long*>(xr + 2 * (M - 1));
+  #pragma unroll
+            for (int r = 0; r < ZB; ++r)
+              A2[r] = f2_mul(*reinterpret_cast<const unsigned long long*>(row + ZO2 + 2 * (z0 + r)),
+                             fy2);
+          };
+          int pp = pp0, pe1 = pp1;
+          // the boundary pairs with a masked half, then the inner pairs unmasked
+          if ((t0 & 1) || pp0 == pp1) {
+            unsigned long long m0 = (t0 & 1) ? keep_hi : f2_pack(1.f, 1.f);
+            if (pp0 == pp1 && (t1 & 1)) m0 = f2_mul(m0, keep_lo);
+            unsigned long long fa[M], Aa[ZB];
+            load_pair(pp0, fa, Aa, m0);
+  #pragma unroll
+            for (int r = 0; r < ZB; ++r)
+  #pragma unroll
+              for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
+            ++pp;
+          }
+          if (pp <= pp1 && (t1 & 1)) {
+            unsigned long long fa[M], Aa[ZB];
+            load_pair(pp1, fa, Aa, keep_lo);
+  #pragma unroll
+            for (int r = 0; r < ZB; ++r)
+  #pragma unroll
+              for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
+            --pe1;
+          }
+          // two pairs per iteration: the second pair's loads overlap the first's FMAs
+          for (; pp + 1 <= pe1; pp += 2) {
+            unsigned long long fa[M], fb[M], Aa[ZB], Ab[ZB];
+            load_pair(pp, fa, Aa, 0ull);
+            load_pair(pp + 1, fb, Ab, 0ull);
+  #pragma unroll
+            for (int r = 0; r < ZB; ++r)
+  #pragma unroll
+              for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Ab[r], fb[j], f2_fma(Aa[r], fa[j], acc2[r][j]));
+          }
+          if (pp <= pe1) {
+            unsigned long long fa[M], Aa[ZB];
+            load_pair(pp, fa, Aa, 0ull);
+  #pragma unroll
+            for (int r = 0; r < ZB; ++r)
+  #pragma unroll
+              for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
+          }
+          const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+          float* dst = blk + ((bz + z0) * E + by + y) * E + bx + xh * M;
+  #pragma unroll
+          for (int r = 0; r < ZB; ++r)
+  #pragma unroll
+            for (int j = 0; j < M; ++j) {
+              float e, o;
+              f2_unpack(acc2[r][j], e, o);
+              dst[r * E2 + j] += e + o;
+            }
+        }
+        __syncthreads();
+      }
+      if (threadIdx.x == 0 && k + STAGES < nchunks)
+        stage_pairs<M, CP>(stage0 + ((kb + k) % STAGES) * SG::STAGE_F, &bars[(kb + k) % STAGES],
+                           winp, ckey, POT ? nullptr : wts, pc0 + STAGES * CP,
+                           min(CP, pe - pc0 - STAGES * CP));
     }
-    if (threadIdx.x == 0 && k + STAGES < nchunks)
-      stage_pairs<M, CP>(stage0 + (k % STAGES) * SG::STAGE_F, &bars[k % STAGES], winp, ckey,
-                         POT ? nullptr : wts, pc0 + STAGES * CP,
-                         min(CP, pe - pc0 - STAGES * CP));
-  }
-  if (threadIdx.x < 32) {
-    bz_lo = warp_min_i(bz_lo);
-    bz_hi = warp_max_i(bz_hi);
-    by_lo = warp_min_i(by_lo);
-    by_hi = warp_max_i(by_hi);
-    if (lane == 0) {
-      const int box = bz_lo | (bz_hi << 4) | (by_lo << 8) | (by_hi << 12);
-      box_s = box;
-      unit_box[u] = box;
+    if (threadIdx.x < 32) {
+      bz_lo = warp_min_i(bz_lo);
+      bz_hi = warp_max_i(bz_hi);
+      by_lo = warp_min_i(by_lo);
+      by_hi = warp_max_i(by_hi);
+      if (lane == 0) {
+        const int box = bz_lo | (bz_hi << 4) | (by_lo << 8) | (by_hi << 12);
+        box_s = box;
+        unit_box[u] = box;
+      }
     }
-  }
-  __syncthreads();
-  // the entries the unit's cells reach: local cells z in [zlo, zhi], y in
-  // [ylo, yhi] reach block planes zlo .. zhi + 2m - 1 and rows ylo .. yhi + 2m - 1
-  const int box = box_s;
-  const int pz0 = box & 15, pz1 = ((box >> 4) & 15) + W2;
-  const int py0 = (box >> 8) & 15, ny = ((box >> 12) & 15) + W2 - py0;
-  float* outb = blocks + (size_t)u * SG::E3P;
-  for (int pz = pz0; pz < pz1; ++pz) {
-    const int i0 = (pz * E + py0) * E;
-    for (int q = threadIdx.x; q < ny * E; q += NT) outb[i0 + q] = blk[i0 + q];
+    __syncthreads();
+    // the entries the unit's cells reach: local cells z in [zlo, zhi], y in
+    // [ylo, yhi] reach block planes zlo .. zhi + 2m - 1 and rows ylo .. yhi + 2m - 1
+    const int box = box_s;
+    const int pz0 = box & 15, pz1 = ((box >> 4) & 15) + W2;
+    const int py0 = (box >> 8) & 15, ny = ((box >> 12) & 15) + W2 - py0;
+    float* outb = blocks + (size_t)u * SG::E3P;
+    for (int pz = pz0; pz < pz1; ++pz) {
+      const int i0 = (pz * E + py0) * E;
+      for (int q = threadIdx.x; q < ny * E; q += NT) outb[i0 + q] = blk[i0 + q];
+    }
+    kb += nchunks;
+    __syncthreads();  // the block is written out before the next unit clears it
   }
 }
 
-// Fold, step 1: the units of one tile (a tile with more than NFFT_SPREAD_UNIT
-// points has several) are summed into the block of the tile's first unit, in
+// Fold, step 1: the units of one tile (a tile that meets several chunks has
+// several) are summed into the block of the tile's first unit, in
 // a fixed order; a unit contributes the entries it wrote (unit_box).  The U
 // units of a tile share the work: CTA k of the tile takes the k-th of U slices
 // of the block's entries.  When a slice has fewer entries than the CTA has
@@ -1482,8 +1494,8 @@ template <int M, bool DUAL>
 __global__ void __launch_bounds__(32 * GWARPS, 2)
     k_gather_w(const float* __restrict__ win, const int* __restrict__ ckey,
                const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
-               const int* __restrict__ unit_count, const int* __restrict__ num_units, int n,
-               int tiles1, const float* __restrict__ grid, float* __restrict__ out,
+               const int* __restrict__ unit_count, const int* __restrict__ chunk_unit_start,
+               int n, int tiles1, const float* __restrict__ grid, float* __restrict__ out,
                long long* __restrict__ flags, DualUpdate du) {
   using GG = GatherGeo<M>;
   constexpr int E = GG::E, E2 = E * E, E3 = E2 * E, WS = GG::WS;
@@ -1496,36 +1508,19 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
   float* blk = smem;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* wbuf = smem + GG::E3P + warp * GG::WARP_F;
-  const int u = blockIdx.x;
-  if (DUAL && u == 0 && threadIdx.x == 0) {
+  if (DUAL && blockIdx.x == 0 && threadIdx.x == 0) {
     flags[du.reset_slot] = ORDERED_NEG_INF;
     if (du.reset_delta >= 0) flags[du.reset_delta] = ORDERED_NEG_INF;
   }
-  if (u >= *num_units) return;
-  const int b0 = unit_begin[u], cnt = unit_count[u];
-  const int per = (cnt + GWARPS - 1) / GWARPS;
-  const int wb = min(cnt, warp * per), we = min(cnt, wb + per);
-  const int nch = (we - wb + GW - 1) / GW;
+  // the CTA's chunk: units ubeg .. uend - 1, taken in turn; kw counts the warp's
+  // staging chunks of the earlier units (the barriers' phases run on)
+  const int ubeg = chunk_unit_start[blockIdx.x], uend = chunk_unit_start[blockIdx.x + 1];
   if (lane == 0) {
     mbar_init(&bars[warp][0], 1);
     mbar_init(&bars[warp][1], 1);
     if (warp == 0) mbar_init(&never, 1);
     mbar_fence_init();
-    for (int k = 0; k < 2 && k < nch; ++k)
-      stage_warp<M>(wbuf + k * GG::BUF_F, &bars[warp][k], win, ckey, b0 + wb + k * GW,
-                    min(GW, we - wb - k * GW));
   }
-  int tx0, ty0, tz0;
-  tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
-  for (int i = threadIdx.x; i < E3; i += blockDim.x) {
-    const int lz = i / E2, ly = (i / E) % E, lx = i % E;
-    int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
-    gz += gz < 0 ? n : 0;
-    gy += gy < 0 ? n : 0;
-    gx += gx < 0 ? n : 0;
-    blk[i] = grid[((long long)gz * n + gy) * n + gx];
-  }
-  __syncthreads();  // barriers initialised and block staged before anyone waits or reads
   // Dual half-step state (as in k_gather): sums parked one per lane, 32 targets
   // updated at once with every lane active.
   const double qs = DUAL ? du.q * ordered_to_dbl(flags[du.shift_in]) : 0.0;
@@ -1549,130 +1544,161 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
   const int zg = lane >> 3, yg = (lane >> 1) & 3, xh = lane & 1;
   const int z0 = zg * BZ, y0 = yg * BZ;
   unsigned long long hc[BZ][BZ][MP];
-  int cached = -1;
-  // this lane's part of the sum of the target with window row `row`, cell `key`
-  // two targets of the same cell (the footprint cached): their sums share the
-  // footprint registers and give six independent FMA chains instead of three
-  auto target_pair = [&](const float* ra, const float* rb, float& pa, float& pb) {
-    unsigned long long Ha[MP], Hb[MP];
-#pragma unroll
-    for (int j = 0; j < MP; ++j) Ha[j] = Hb[j] = 0ull;
-#pragma unroll
-    for (int z = 0; z < BZ; ++z) {
-      const float za = ra[ZO + z0 + z], zb = rb[ZO + z0 + z];
-#pragma unroll
-      for (int yy = 0; yy < BZ; ++yy) {
-        const float a = za * ra[YO + y0 + yy], b = zb * rb[YO + y0 + yy];
-        const unsigned long long A = f2_pack(a, a), B = f2_pack(b, b);
-#pragma unroll
-        for (int j = 0; j < MP; ++j) {
-          Ha[j] = f2_fma(A, hc[z][yy][j], Ha[j]);
-          Hb[j] = f2_fma(B, hc[z][yy][j], Hb[j]);
+  int kw = 0;
+  bool dead = false;  // a wait of this warp ran out: it computes nothing more
+  for (int u = ubeg; u < uend; ++u) {
+    const int b0 = unit_begin[u], cnt = unit_count[u];
+    const int per = (cnt + GWARPS - 1) / GWARPS;
+    const int wb = min(cnt, warp * per), we = min(cnt, wb + per);
+    const int nch = dead ? 0 : (we - wb + GW - 1) / GW;
+    // every warp is done with the previous unit's block before it is replaced
+    if (u != ubeg) __syncthreads();
+    if (lane == 0) {
+      // the warp's staging buffers were last read by the generic proxy
+      if (u != ubeg) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      for (int k = 0; k < 2 && k < nch; ++k)
+        stage_warp<M>(wbuf + ((kw + k) & 1) * GG::BUF_F, &bars[warp][(kw + k) & 1], win, ckey,
+                      b0 + wb + k * GW, min(GW, we - wb - k * GW));
+    }
+    int tx0, ty0, tz0;
+    tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
+    for (int i = threadIdx.x; i < E3; i += blockDim.x) {
+      const int lz = i / E2, ly = (i / E) % E, lx = i % E;
+      int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
+      gz += gz < 0 ? n : 0;
+      gy += gy < 0 ? n : 0;
+      gx += gx < 0 ? n : 0;
+      blk[i] = grid[((long long)gz * n + gy) * n + gx];
+    }
+    __syncthreads();  // barriers initialised and block staged before anyone waits or reads
+    int cached = -1;
+    // this lane's part of the sum of the target with window row `row`, cell `key`
+    // two targets of the same cell (the footprint cached): their sums share the
+    // footprint registers and give six independent FMA chains instead of three
+    auto target_pair = [&](const float* ra, const float* rb, float& pa, float& pb) {
+      unsigned long long Ha[MP], Hb[MP];
+  #pragma unroll
+      for (int j = 0; j < MP; ++j) Ha[j] = Hb[j] = 0ull;
+  #pragma unroll
+      for (int z = 0; z < BZ; ++z) {
+        const float za = ra[ZO + z0 + z], zb = rb[ZO + z0 + z];
+  #pragma unroll
+        for (int yy = 0; yy < BZ; ++yy) {
+          const float a = za * ra[YO + y0 + yy], b = zb * rb[YO + y0 + yy];
+          const unsigned long long A = f2_pack(a, a), B = f2_pack(b, b);
+  #pragma unroll
+          for (int j = 0; j < MP; ++j) {
+            Ha[j] = f2_fma(A, hc[z][yy][j], Ha[j]);
+            Hb[j] = f2_fma(B, hc[z][yy][j], Hb[j]);
+          }
         }
       }
-    }
-    float fa[M], fb[M];
-    load_vec<M>(ra + xh * HP, fa);
-    load_vec<M>(rb + xh * HP, fb);
-    unsigned long long sa = f2_mul(f2_pack(fa[0], fa[1]), Ha[0]);
-    unsigned long long sb = f2_mul(f2_pack(fb[0], fb[1]), Hb[0]);
-#pragma unroll
-    for (int j = 1; j < MP; ++j) {
-      sa = f2_fma(f2_pack(fa[2 * j], fa[2 * j + 1]), Ha[j], sa);
-      sb = f2_fma(f2_pack(fb[2 * j], fb[2 * j + 1]), Hb[j], sb);
-    }
-    float lo, hi;
-    f2_unpack(sa, lo, hi);
-    pa = lo + hi;
-    f2_unpack(sb, lo, hi);
-    pb = lo + hi;
-  };
-  auto target_part = [&](const float* row, int key) -> float {
-    if (key != cached) {
-      const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
-      const float* src = blk + ((bz + z0) * E + by + y0) * E + bx + xh * M;
-#pragma unroll
-      for (int z = 0; z < BZ; ++z)
-#pragma unroll
-        for (int yy = 0; yy < BZ; ++yy)
-#pragma unroll
-          for (int j = 0; j < MP; ++j)
-            hc[z][yy][j] = f2_pack(src[(z * E + yy) * E + 2 * j], src[(z * E + yy) * E + 2 * j + 1]);
-      cached = key;
-    }
-    float fz[BZ], fy[BZ], fx[M];
-#pragma unroll
-    for (int k = 0; k < BZ; ++k) {
-      fz[k] = row[ZO + z0 + k];
-      fy[k] = row[YO + y0 + k];
-    }
-    load_vec<M>(row + xh * HP, fx);
-    unsigned long long H[MP];
-#pragma unroll
-    for (int j = 0; j < MP; ++j) H[j] = 0ull;
-#pragma unroll
-    for (int z = 0; z < BZ; ++z)
-#pragma unroll
-      for (int yy = 0; yy < BZ; ++yy) {
-        const float a = fz[z] * fy[yy];
-        const unsigned long long A = f2_pack(a, a);
-#pragma unroll
-        for (int j = 0; j < MP; ++j) H[j] = f2_fma(A, hc[z][yy][j], H[j]);
+      float fa[M], fb[M];
+      load_vec<M>(ra + xh * HP, fa);
+      load_vec<M>(rb + xh * HP, fb);
+      unsigned long long sa = f2_mul(f2_pack(fa[0], fa[1]), Ha[0]);
+      unsigned long long sb = f2_mul(f2_pack(fb[0], fb[1]), Hb[0]);
+  #pragma unroll
+      for (int j = 1; j < MP; ++j) {
+        sa = f2_fma(f2_pack(fa[2 * j], fa[2 * j + 1]), Ha[j], sa);
+        sb = f2_fma(f2_pack(fb[2 * j], fb[2 * j + 1]), Hb[j], sb);
       }
-    unsigned long long r = f2_mul(f2_pack(fx[0], fx[1]), H[0]);
-#pragma unroll
-    for (int j = 1; j < MP; ++j) r = f2_fma(f2_pack(fx[2 * j], fx[2 * j + 1]), H[j], r);
-    float lo, hi;
-    f2_unpack(r, lo, hi);
-    return lo + hi;
-  };
-  for (int k = 0; k < nch; ++k) {
-    const int q0 = b0 + wb + k * GW, cn = min(GW, we - wb - k * GW);
-    float* sb = wbuf + (k & 1) * GG::BUF_F;
-    const bool ok = k == 0 ? first_wait(&bars[warp][0], 0u, &never, flags)
-                           : mbar_wait(&bars[warp][k & 1], (unsigned)(k >> 1) & 1u);
-    if (__any_sync(0xffffffffu, !ok)) {
-      // give up: record it, let this warp's copies in flight land, and stop
-      if (lane == 0) {
-        flag_add(&flags[FLAG_TIMEOUT], 1LL);
-        for (int q = k; q < nch && q < k + 2; ++q)
-          mbar_wait(&bars[warp][q & 1], (unsigned)(q >> 1) & 1u);
+      float lo, hi;
+      f2_unpack(sa, lo, hi);
+      pa = lo + hi;
+      f2_unpack(sb, lo, hi);
+      pb = lo + hi;
+    };
+    auto target_part = [&](const float* row, int key) -> float {
+      if (key != cached) {
+        const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
+        const float* src = blk + ((bz + z0) * E + by + y0) * E + bx + xh * M;
+  #pragma unroll
+        for (int z = 0; z < BZ; ++z)
+  #pragma unroll
+          for (int yy = 0; yy < BZ; ++yy)
+  #pragma unroll
+            for (int j = 0; j < MP; ++j)
+              hc[z][yy][j] = f2_pack(src[(z * E + yy) * E + 2 * j], src[(z * E + yy) * E + 2 * j + 1]);
+        cached = key;
+      }
+      float fz[BZ], fy[BZ], fx[M];
+  #pragma unroll
+      for (int k = 0; k < BZ; ++k) {
+        fz[k] = row[ZO + z0 + k];
+        fy[k] = row[YO + y0 + k];
+      }
+      load_vec<M>(row + xh * HP, fx);
+      unsigned long long H[MP];
+  #pragma unroll
+      for (int j = 0; j < MP; ++j) H[j] = 0ull;
+  #pragma unroll
+      for (int z = 0; z < BZ; ++z)
+  #pragma unroll
+        for (int yy = 0; yy < BZ; ++yy) {
+          const float a = fz[z] * fy[yy];
+          const unsigned long long A = f2_pack(a, a);
+  #pragma unroll
+          for (int j = 0; j < MP; ++j) H[j] = f2_fma(A, hc[z][yy][j], H[j]);
+        }
+      unsigned long long r = f2_mul(f2_pack(fx[0], fx[1]), H[0]);
+  #pragma unroll
+      for (int j = 1; j < MP; ++j) r = f2_fma(f2_pack(fx[2 * j], fx[2 * j + 1]), H[j], r);
+      float lo, hi;
+      f2_unpack(r, lo, hi);
+      return lo + hi;
+    };
+    for (int k = 0; k < nch; ++k) {
+      const int q0 = b0 + wb + k * GW, cn = min(GW, we - wb - k * GW);
+      const int kg = kw + k;
+      float* sb = wbuf + (kg & 1) * GG::BUF_F;
+      const bool ok = kg == 0 ? first_wait(&bars[warp][0], 0u, &never, flags)
+                              : mbar_wait(&bars[warp][kg & 1], (unsigned)(kg >> 1) & 1u);
+      if (__any_sync(0xffffffffu, !ok)) {
+        // give up: record it, let this warp's copies in flight land, and stop
+        if (lane == 0) {
+          flag_add(&flags[FLAG_TIMEOUT], 1LL);
+          for (int q = kg; q < kw + nch && q < kg + 2; ++q)
+            mbar_wait(&bars[warp][q & 1], (unsigned)(q >> 1) & 1u);
+        }
+        __syncwarp();
+        dead = true;
+        break;
+      }
+      const int* skey = reinterpret_cast<const int*>(sb + GW * WS) + (q0 & 3);
+      for (int p = 0; p < cn; p += 4) {
+        float part[4];
+  #pragma unroll
+        for (int j = 0; j < 4; j += 2) {
+          if (p + j + 1 < cn && skey[p + j] == skey[p + j + 1]) {
+            // the first call loads the pair's footprint if needed; then both together
+            if (skey[p + j] != cached) (void)target_part(sb + (p + j) * WS, skey[p + j]);
+            target_pair(sb + (p + j) * WS, sb + (p + j + 1) * WS, part[j], part[j + 1]);
+          } else {
+            part[j] = p + j < cn ? target_part(sb + (p + j) * WS, skey[p + j]) : 0.f;
+            part[j + 1] = p + j + 1 < cn ? target_part(sb + (p + j + 1) * WS, skey[p + j + 1]) : 0.f;
+          }
+        }
+        const float tsum = warp_sum4(part, lane);
+        const int t = p + (lane >> 3);
+        if ((lane & 7) == 0 && t < cn) out[q0 + t] = tsum;
+        if (DUAL) {
+          if ((lane & 7) == dn && t < cn) {
+            dt = tsum;
+            di = q0 + t;
+          }
+          if (++dn == 8) dual_flush();
+        }
       }
       __syncwarp();
-      break;
-    }
-    const int* skey = reinterpret_cast<const int*>(sb + GW * WS) + (q0 & 3);
-    for (int p = 0; p < cn; p += 4) {
-      float part[4];
-#pragma unroll
-      for (int j = 0; j < 4; j += 2) {
-        if (p + j + 1 < cn && skey[p + j] == skey[p + j + 1]) {
-          // the first call loads the pair's footprint if needed; then both together
-          if (skey[p + j] != cached) (void)target_part(sb + (p + j) * WS, skey[p + j]);
-          target_pair(sb + (p + j) * WS, sb + (p + j + 1) * WS, part[j], part[j + 1]);
-        } else {
-          part[j] = p + j < cn ? target_part(sb + (p + j) * WS, skey[p + j]) : 0.f;
-          part[j + 1] = p + j + 1 < cn ? target_part(sb + (p + j + 1) * WS, skey[p + j + 1]) : 0.f;
-        }
-      }
-      const float tsum = warp_sum4(part, lane);
-      const int t = p + (lane >> 3);
-      if ((lane & 7) == 0 && t < cn) out[q0 + t] = tsum;
-      if (DUAL) {
-        if ((lane & 7) == dn && t < cn) {
-          dt = tsum;
-          di = q0 + t;
-        }
-        if (++dn == 8) dual_flush();
+      if (lane == 0 && k + 2 < nch) {
+        // the warp's reads of this buffer are done (generic proxy) before the
+        // bulk copy (async proxy) overwrites it
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        stage_warp<M>(sb, &bars[warp][kg & 1], win, ckey, q0 + 2 * GW, min(GW, we - wb - (k + 2) * GW));
       }
     }
-    __syncwarp();
-    if (lane == 0 && k + 2 < nch) {
-      // the warp's reads of this buffer are done (generic proxy) before the
-      // bulk copy (async proxy) overwrites it
-      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      stage_warp<M>(sb, &bars[warp][k & 1], win, ckey, q0 + 2 * GW, min(GW, we - wb - (k + 2) * GW));
-    }
+    kw += nch;
   }
   if (DUAL) {
     dual_flush();
@@ -1722,9 +1748,9 @@ uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
   {
     UOTK_PROF(ctx, s, "spread");
     UOTK_CUDA(ctx, smem_attr(s, kern, smem));
-    kern<<<S.max_units, NT, smem, s>>>(S.winp, S.ckey, wts, S.unit_tile, S.unit_begin,
-                                       S.unit_count, S.unit_box, S.num_units, P.tiles1, W.blocks,
-                                       ctx->dflags, pw ? *pw : SpreadWeights{});
+    kern<<<S.c_spread, NT, smem, s>>>(S.winp, S.ckey, wts, S.unit_tile, S.unit_begin,
+                                      S.unit_count, S.unit_box, S.chunk_unit_start, P.tiles1,
+                                      W.blocks, ctx->dflags, pw ? *pw : SpreadWeights{});
     UOTK_LAUNCHED(ctx);
   }
   {
@@ -1749,9 +1775,10 @@ uotk_status launch_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
     const size_t smem = sizeof(float) * (GG::E3P + GWARPS * GG::WARP_F);
     auto kern = du ? k_gather_w<M, true> : k_gather_w<M, false>;
     UOTK_CUDA(ctx, smem_attr(s, kern, smem));
-    kern<<<S.g_max_units, 32 * GWARPS, smem, s>>>(S.win, S.ckey, S.g_unit_tile, S.g_unit_begin,
-                                                   S.g_unit_count, S.g_num_units, P.n, P.tiles1,
-                                                   grid, out, ctx->dflags, du ? *du : DualUpdate{});
+    kern<<<S.c_gather, 32 * GWARPS, smem, s>>>(S.win, S.ckey, S.g_unit_tile, S.g_unit_begin,
+                                                S.g_unit_count, S.g_chunk_unit_start, P.n,
+                                                P.tiles1, grid, out, ctx->dflags,
+                                                du ? *du : DualUpdate{});
   } else {
     const size_t smem = unit_smem<M, GATHER_CH>();
     auto kern = du ? k_gather<M, true, GATHER_CH> : k_gather<M, false, GATHER_CH>;
@@ -1792,6 +1819,82 @@ static uotk_status gather_units(uotk_ctx* ctx, cudaStream_t s, const NfftParams&
 #define UOTK_GATHER_CALL(M) launch_gather<M>(ctx, s, P, S, grid, out, du)
   UOTK_M_SWITCH(P.m, UOTK_GATHER_CALL)
 #undef UOTK_GATHER_CALL
+}
+
+// CTAs of the spread / gather kernel at cut-off m that one SM holds at once.
+template <int M>
+static int spread_slots_m() {
+  using SG = SpreadGeo<M, SPREAD_CP>;
+  const size_t smem = sizeof(float) * (SG::E3P + STAGES * SG::STAGE_F);
+  auto kern = k_spread<M, true, SPREAD_CP>;
+  int per = 0;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+          cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, SpreadMap<M>::NTH, smem) !=
+          cudaSuccess)
+    per = 1;
+  return per > 0 ? per : 1;
+}
+template <int M>
+static int gather_slots_m() {
+  int per = 0;
+  if constexpr (M % 2 == 0 && M <= 6) {
+    using GG = GatherGeo<M>;
+    const size_t smem = sizeof(float) * (GG::E3P + GWARPS * GG::WARP_F);
+    auto kern = k_gather_w<M, true>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, 32 * GWARPS, smem) !=
+            cudaSuccess)
+      per = 1;
+  } else {
+    per = 2;  // one CTA per unit (k_gather): the number of chunks only sets the unit sizes
+  }
+  return per > 0 ? per : 1;
+}
+
+static int device_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      return 1;
+  }
+  return sms;
+}
+
+int nfft_spread_slots(int m) {
+  static int per[NFFT_MAX_M + 1] = {};
+  if (m < 2 || m > NFFT_MAX_M) return device_sms();
+  if (!per[m]) {
+    switch (m) {
+      case 2: per[m] = spread_slots_m<2>(); break;
+      case 3: per[m] = spread_slots_m<3>(); break;
+      case 4: per[m] = spread_slots_m<4>(); break;
+      case 5: per[m] = spread_slots_m<5>(); break;
+      case 6: per[m] = spread_slots_m<6>(); break;
+      case 7: per[m] = spread_slots_m<7>(); break;
+      default: per[m] = spread_slots_m<8>(); break;
+    }
+  }
+  return per[m] * device_sms();
+}
+
+int nfft_gather_slots(int m) {
+  static int per[NFFT_MAX_M + 1] = {};
+  if (m < 2 || m > NFFT_MAX_M) return device_sms();
+  if (!per[m]) {
+    switch (m) {
+      case 2: per[m] = gather_slots_m<2>(); break;
+      case 4: per[m] = gather_slots_m<4>(); break;
+      case 6: per[m] = gather_slots_m<6>(); break;
+      default: per[m] = gather_slots_m<3>(); break;
+    }
+  }
+  return per[m] * device_sms();
 }
 
 uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
@@ -1883,7 +1986,8 @@ void nfft_work_carve(Carver& cv, const NfftParams& P, int64_t max_points, NfftWo
   W.grid = cv.take<float>(n3);
   // one E^3 block per spread work unit, folded into the grid in a fixed order
   const int E = NFFT_TILE + 2 * P.m - 1;
-  W.blocks = cv.take<float>((size_t)nfft_max_units(P, max_points > 0 ? max_points : 1) *
+  W.blocks = cv.take<float>((size_t)nfft_max_units(P, max_points > 0 ? max_points : 1,
+                                                   nfft_spread_slots(P.m)) *
                             (size_t)((E * E * E + 3) & ~3));
   // complex work grid: n^3 for the unpruned passes, n^2 N + n N^2 for the
   // pruned ones (A1 and A2)

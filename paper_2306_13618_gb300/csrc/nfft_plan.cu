@@ -190,53 +190,110 @@ __global__ void k_tile_counts(const int* __restrict__ cell_start, int tiles,
     count[t] = cell_start[(long long)(t + 1) * T3] - cell_start[(long long)t * T3];
 }
 
-// Single block: exclusive scans of points and of the work units per tile at
-// two unit sizes (spread units of unit_a points, gather units of unit_b).
-__global__ void k_bin_scan(int* __restrict__ count, int tiles, int unit_a, int unit_b,
-                           int* __restrict__ tile_start, int* __restrict__ tus_a,
+// 1 where a cell holds points (from the scanned counts), for the cell ranks.
+__global__ void k_occ_flags(const int* __restrict__ cell_start, long long cells,
+                            int* __restrict__ flag) {
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < cells;
+       c += (long long)gridDim.x * blockDim.x)
+    flag[c] = cell_start[c + 1] > cell_start[c];
+}
+
+// Cost of sorted point p of a tile with occupied-tile rank r (see nfft.cuh):
+// p + cell_cost (occupied cells up to p's cell) + tile_cost (r + 1).
+__device__ __forceinline__ long long point_cost(int p, int cells_upto, int r, int cell_cost,
+                                                int tile_cost) {
+  return (long long)p + (long long)cell_cost * cells_upto + (long long)tile_cost * (r + 1);
+}
+
+// Single block.  Pass 1: exclusive scans of the points per tile (tile_start)
+// and of the occupied tiles (tile_rank), then the cost per chunk of the spread
+// and of the gather: Q = max(min chunk, ceil(total cost / chunks)).  Pass 2:
+// the work units per tile, one per chunk its cost range meets, scanned (tus_a,
+// tus_b, totals num_a, num_b).
+__global__ void k_bin_scan(const int* __restrict__ count, const int* __restrict__ cell_rank,
+                           int tiles, int chunks_a, int chunks_b,
+                           int* __restrict__ tile_start, int* __restrict__ tile_rank,
+                           long long* __restrict__ chunk_q, int* __restrict__ tus_a,
                            int* __restrict__ num_a, int* __restrict__ tus_b,
                            int* __restrict__ num_b) {
-  __shared__ int sp[1024], sa[1024], sb[1024];
-  __shared__ int carry_p, carry_a, carry_b;
-  if (threadIdx.x == 0) { carry_p = 0; carry_a = 0; carry_b = 0; }
+  constexpr int T3 = NFFT_TILE * NFFT_TILE * NFFT_TILE;
+  __shared__ int sa[1024], sb[1024];
+  __shared__ int carry_a, carry_b;
+  __shared__ long long qa, qb;
+  if (threadIdx.x == 0) { carry_a = 0; carry_b = 0; }
   __syncthreads();
-  for (int base = 0; base < tiles; base += 1024) {
-    const int i = base + threadIdx.x;
-    const int c = i < tiles ? count[i] : 0;
-    const int ca = (c + unit_a - 1) / unit_a, cb = (c + unit_b - 1) / unit_b;
-    sp[threadIdx.x] = c;
-    sa[threadIdx.x] = ca;
-    sb[threadIdx.x] = cb;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {
-      const int x = threadIdx.x >= o ? sp[threadIdx.x - o] : 0;
-      const int y = threadIdx.x >= o ? sa[threadIdx.x - o] : 0;
-      const int z = threadIdx.x >= o ? sb[threadIdx.x - o] : 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int base = 0; base < tiles; base += 1024) {
+      const int i = base + threadIdx.x;
+      int ca = 0, cb = 0;
+      if (i < tiles) {
+        if (pass == 0) {
+          ca = count[i];
+          cb = ca > 0;
+        } else {
+          const int b = tile_start[i], e = tile_start[i + 1];
+          if (e > b) {
+            // occupied cells up to the tile's first and last occupied cell
+            const int c0 = cell_rank[(long long)i * T3] + 1, c1 = cell_rank[(long long)(i + 1) * T3];
+            const int r = tile_rank[i];
+            ca = (int)(point_cost(e - 1, c1, r, NFFT_SPREAD_CELL_COST, NFFT_SPREAD_TILE_COST) / qa -
+                       point_cost(b, c0, r, NFFT_SPREAD_CELL_COST, NFFT_SPREAD_TILE_COST) / qa) + 1;
+            cb = (int)(point_cost(e - 1, c1, r, NFFT_GATHER_CELL_COST, NFFT_GATHER_TILE_COST) / qb -
+                       point_cost(b, c0, r, NFFT_GATHER_CELL_COST, NFFT_GATHER_TILE_COST) / qb) + 1;
+          }
+        }
+      }
+      sa[threadIdx.x] = ca;
+      sb[threadIdx.x] = cb;
       __syncthreads();
-      sp[threadIdx.x] += x;
-      sa[threadIdx.x] += y;
-      sb[threadIdx.x] += z;
+      for (int o = 1; o < 1024; o <<= 1) {
+        const int y = threadIdx.x >= o ? sa[threadIdx.x - o] : 0;
+        const int z = threadIdx.x >= o ? sb[threadIdx.x - o] : 0;
+        __syncthreads();
+        sa[threadIdx.x] += y;
+        sb[threadIdx.x] += z;
+        __syncthreads();
+      }
+      if (i < tiles) {
+        if (pass == 0) {
+          tile_start[i] = carry_a + sa[threadIdx.x] - ca;
+          tile_rank[i] = carry_b + sb[threadIdx.x] - cb;
+        } else {
+          tus_a[i] = carry_a + sa[threadIdx.x] - ca;
+          tus_b[i] = carry_b + sb[threadIdx.x] - cb;
+        }
+      }
+      __syncthreads();
+      if (threadIdx.x == 1023) {
+        carry_a += sa[1023];
+        carry_b += sb[1023];
+      }
       __syncthreads();
     }
-    if (i < tiles) {
-      tile_start[i] = carry_p + sp[threadIdx.x] - c;
-      tus_a[i] = carry_a + sa[threadIdx.x] - ca;
-      tus_b[i] = carry_b + sb[threadIdx.x] - cb;
+    if (threadIdx.x == 0) {
+      if (pass == 0) {
+        const int n = carry_a, occ = carry_b, cells = cell_rank[(long long)tiles * T3];
+        tile_start[tiles] = carry_a;
+        tile_rank[tiles] = carry_b;
+        // total cost: one past the last point's
+        const long long ta = point_cost(n, cells, occ - 1, NFFT_SPREAD_CELL_COST,
+                                        NFFT_SPREAD_TILE_COST);
+        const long long tb = point_cost(n, cells, occ - 1, NFFT_GATHER_CELL_COST,
+                                        NFFT_GATHER_TILE_COST);
+        qa = max((long long)NFFT_SPREAD_MIN_CHUNK, (ta + chunks_a - 1) / chunks_a);
+        qb = max((long long)NFFT_GATHER_MIN_CHUNK, (tb + chunks_b - 1) / chunks_b);
+        chunk_q[0] = qa;
+        chunk_q[1] = qb;
+        carry_a = 0;
+        carry_b = 0;
+      } else {
+        tus_a[tiles] = carry_a;
+        tus_b[tiles] = carry_b;
+        *num_a = carry_a;
+        *num_b = carry_b;
+      }
     }
     __syncthreads();
-    if (threadIdx.x == 1023) {
-      carry_p += sp[1023];
-      carry_a += sa[1023];
-      carry_b += sb[1023];
-    }
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) {
-    tile_start[tiles] = carry_p;
-    tus_a[tiles] = carry_a;
-    tus_b[tiles] = carry_b;
-    *num_a = carry_a;
-    *num_b = carry_b;
   }
 }
 
@@ -322,26 +379,84 @@ __global__ void k_bin_place(const int4* __restrict__ tmp_cell, const int* __rest
   }
 }
 
-// Units of at most unit_pts points per tile; zr (optional) gets the first and
-// last local z cell of each unit (cells are ordered z-major inside a tile).
+// Cost of sorted point p from its cell key (the point costs of nfft.cuh).
+__device__ __forceinline__ long long sorted_point_cost(int p, const int* __restrict__ ckey,
+                                                       const int* __restrict__ cell_rank,
+                                                       const int* __restrict__ tile_rank,
+                                                       int tiles1, int cell_cost, int tile_cost) {
+  const int k = ckey[p];
+  const int c[3] = {k & 1023, (k >> 10) & 1023, k >> 20};
+  const int cell = cell_key(c, tiles1);
+  return point_cost(p, cell_rank[cell] + 1, tile_rank[cell / (NFFT_TILE * NFFT_TILE * NFFT_TILE)],
+                    cell_cost, tile_cost);
+}
+
+// first[c] = the first sorted point whose cost reaches c q (n if none),
+// c = 0 .. chunks, by bisection (the costs increase along the sorted points).
+__global__ void k_chunk_first(const int* __restrict__ ckey, const int* __restrict__ cell_rank,
+                              const int* __restrict__ tile_rank, int n, int tiles1,
+                              const long long* __restrict__ chunk_q, int which, int cell_cost,
+                              int tile_cost, int chunks, int* __restrict__ first) {
+  const long long q = chunk_q[which];
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= chunks; c += gridDim.x * blockDim.x) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+      const int mid = lo + ((hi - lo) >> 1);
+      if (sorted_point_cost(mid, ckey, cell_rank, tile_rank, tiles1, cell_cost, tile_cost) <
+          (long long)c * q)
+        lo = mid + 1;
+      else
+        hi = mid;
+    }
+    first[c] = lo;
+  }
+}
+
+// The work units of each tile: its sorted points [b, e) cut at the first
+// points of the chunks that start inside it; chunk(b) .. chunk(e - 1) are the
+// tile's chunks (no chunk is skipped inside a tile: consecutive points differ
+// in cost by at most 1 + cell cost < q).  unit_chunk gets each unit's chunk.
 __global__ void k_make_units(const int* __restrict__ tile_start,
-                             const int* __restrict__ tile_unit_start, int tiles, int unit_pts,
-                             const int* __restrict__ ckey, int* __restrict__ unit_tile,
+                             const int* __restrict__ tile_rank, const int* __restrict__ cell_rank,
+                             const int* __restrict__ ckey, const int* __restrict__ tile_unit_start,
+                             int tiles, int tiles1, const long long* __restrict__ chunk_q,
+                             int which, int cell_cost, int tile_cost,
+                             const int* __restrict__ first, int* __restrict__ unit_tile,
                              int* __restrict__ unit_begin, int* __restrict__ unit_count,
-                             int* __restrict__ zr) {
+                             int* __restrict__ unit_chunk) {
+  const long long q = chunk_q[which];
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < tiles; t += gridDim.x * blockDim.x) {
     const int b = tile_start[t], e = tile_start[t + 1];
-    int u = tile_unit_start[t];
-    for (int p = b; p < e; p += unit_pts, ++u) {
-      const int c = min(unit_pts, e - p);
+    if (e <= b) continue;
+    const int c0 = (int)(sorted_point_cost(b, ckey, cell_rank, tile_rank, tiles1, cell_cost,
+                                           tile_cost) / q);
+    const int c1 = (int)(sorted_point_cost(e - 1, ckey, cell_rank, tile_rank, tiles1, cell_cost,
+                                           tile_cost) / q);
+    int u = tile_unit_start[t], p = b;
+    for (int c = c0; c <= c1; ++c, ++u) {
+      const int end = c < c1 ? first[c + 1] : e;
       unit_tile[u] = t;
       unit_begin[u] = p;
-      unit_count[u] = c;
-      if (zr) {
-        const int z0 = (ckey[p] >> 20) % NFFT_TILE, z1 = (ckey[p + c - 1] >> 20) % NFFT_TILE;
-        zr[u] = z0 | (z1 << 8);
-      }
+      unit_count[u] = end - p;
+      unit_chunk[u] = c;
+      p = end;
     }
+  }
+}
+
+// chunk_unit_start[c] = the first unit of chunk c or later (units are in
+// chunk order), c = 0 .. chunks; chunks past the last unit start at num.
+__global__ void k_chunk_starts(const int* __restrict__ unit_chunk, const int* __restrict__ num,
+                               int chunks, int* __restrict__ chunk_unit_start) {
+  const int nu = *num;
+  for (int c = blockIdx.x * blockDim.x + threadIdx.x; c <= chunks; c += gridDim.x * blockDim.x) {
+    int lo = 0, hi = nu;
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (unit_chunk[mid] < c) lo = mid + 1;
+      else hi = mid;
+    }
+    chunk_unit_start[c] = lo;
   }
 }
 
@@ -409,9 +524,9 @@ __global__ void k_windows_pair(const int4* __restrict__ cell, long long n, int m
 
 }  // namespace
 
-int nfft_max_units(const NfftParams& P, int64_t n, int unit_points) {
+int nfft_max_units(const NfftParams& P, int64_t n, int chunks) {
   const int64_t tiles = (int64_t)P.tiles1 * P.tiles1 * P.tiles1;
-  return (int)((n + unit_points - 1) / unit_points + (n < tiles ? n : tiles));
+  return (int)(chunks + (n < tiles ? n : tiles));
 }
 
 uotk_status nfft_make_params(uotk_ctx* ctx, int d, const float lo[3], const float hi[3],
@@ -566,21 +681,29 @@ void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S
   const int tiles = P.tiles1 * P.tiles1 * P.tiles1;
   const int64_t nn = n > 0 ? n : 1;
   S.n = n;
-  S.max_units = nfft_max_units(P, n, NFFT_SPREAD_UNIT);
-  S.g_max_units = nfft_max_units(P, n, NFFT_GATHER_UNIT);
+  S.c_spread = nfft_spread_slots(P.m);
+  S.c_gather = nfft_gather_slots(P.m);
+  S.max_units = nfft_max_units(P, n, S.c_spread);
+  S.g_max_units = nfft_max_units(P, n, S.c_gather);
   S.cell = cv.take<int4>(nn);
   S.ckey = cv.take<int>(nn + 4);
   S.win = cv.take<float>((size_t)nn * nfft_win_stride(P.m));
   S.winp = cv.take<float>((size_t)((nn + 1) / 2) * nfft_winp_stride(P.m));
   S.perm = cv.take<int>(nn);
   S.tile_start = cv.take<int>(tiles + 1);
+  S.tile_rank = cv.take<int>(tiles + 1);
+  S.chunk_q = cv.take<long long>(2);
   S.tile_unit_start = cv.take<int>(tiles + 1);
   S.unit_tile = cv.take<int>(S.max_units + 1);
   S.unit_begin = cv.take<int>(S.max_units + 1);
   S.unit_count = cv.take<int>(S.max_units + 1);
   S.unit_box = cv.take<int>(S.max_units + 1);
   S.num_units = cv.take<int>(1);
+  S.unit_chunk = cv.take<int>(S.max_units + 1);
+  S.chunk_unit_start = cv.take<int>(S.c_spread + 1);
   S.g_tile_unit_start = cv.take<int>(tiles + 1);
+  S.g_unit_chunk = cv.take<int>(S.g_max_units + 1);
+  S.g_chunk_unit_start = cv.take<int>(S.c_gather + 1);
   S.g_unit_tile = cv.take<int>(S.g_max_units + 1);
   S.g_unit_begin = cv.take<int>(S.g_max_units + 1);
   S.g_unit_count = cv.take<int>(S.g_max_units + 1);
@@ -589,6 +712,7 @@ void nfft_points_carve(Carver& cv, const NfftParams& P, int64_t n, NfftPoints& S
   const long long n3 = (long long)P.n * P.n * P.n;
   S.cell_count = cv.take<int>(n3);
   S.cell_start = cv.take<int>(n3 + 1);
+  S.cell_rank = cv.take<int>(n3 + 1);
   S.block_sums = cv.take<int>(n3 / 2048 + 2);
   // temporaries of the build: caller-order cells and the radix sort buffers
   const int64_t rb = (nn + RS_TILE - 1) / RS_TILE;
@@ -624,9 +748,18 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
     UOTK_LAUNCHED(ctx);
     k_tile_counts<<<grid_for(ctx, tiles, 256), 256, 0, s>>>(S.cell_start, tiles, S.scratch);
     UOTK_LAUNCHED(ctx);
-    k_bin_scan<<<1, 1024, 0, s>>>(S.scratch, tiles, NFFT_SPREAD_UNIT, NFFT_GATHER_UNIT,
-                                  S.tile_start, S.tile_unit_start, S.num_units,
-                                  S.g_tile_unit_start, S.g_num_units);
+    // occupied-cell ranks (the counts are not needed any more: flags in place)
+    k_occ_flags<<<grid_for(ctx, n3, 256), 256, 0, s>>>(S.cell_start, n3, S.cell_count);
+    UOTK_LAUNCHED(ctx);
+    k_scan_local<<<nb, 1024, 0, s>>>(S.cell_count, n3, S.cell_rank, S.block_sums);
+    UOTK_LAUNCHED(ctx);
+    k_scan_top<<<1, 1024, 0, s>>>(S.block_sums, nb);
+    UOTK_LAUNCHED(ctx);
+    k_scan_add<<<grid_for(ctx, n3, 256), 256, 0, s>>>(S.cell_rank, n3, S.block_sums, nb);
+    UOTK_LAUNCHED(ctx);
+    k_bin_scan<<<1, 1024, 0, s>>>(S.scratch, S.cell_rank, tiles, S.c_spread, S.c_gather,
+                                  S.tile_start, S.tile_rank, S.chunk_q, S.tile_unit_start,
+                                  S.num_units, S.g_tile_unit_start, S.g_num_units);
     UOTK_LAUNCHED(ctx);
     if (n > 0) {
       // stable sort by cell key: ceil(bits / 8) passes over the key's bits
@@ -654,14 +787,30 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
                                                          S.ckey, S.perm);
       UOTK_LAUNCHED(ctx);
     }
-    k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.tile_unit_start, tiles,
-                                                          NFFT_SPREAD_UNIT, S.ckey, S.unit_tile,
-                                                          S.unit_begin, S.unit_count, nullptr);
+    // the chunks' first points (in the unit-start arrays, overwritten below)
+    k_chunk_first<<<grid_for(ctx, S.c_spread + 1, 128), 128, 0, s>>>(
+        S.ckey, S.cell_rank, S.tile_rank, (int)n, P.tiles1, S.chunk_q, 0, NFFT_SPREAD_CELL_COST,
+        NFFT_SPREAD_TILE_COST, S.c_spread, S.chunk_unit_start);
     UOTK_LAUNCHED(ctx);
-    k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(S.tile_start, S.g_tile_unit_start,
-                                                          tiles, NFFT_GATHER_UNIT, S.ckey,
-                                                          S.g_unit_tile, S.g_unit_begin,
-                                                          S.g_unit_count, nullptr);
+    k_chunk_first<<<grid_for(ctx, S.c_gather + 1, 128), 128, 0, s>>>(
+        S.ckey, S.cell_rank, S.tile_rank, (int)n, P.tiles1, S.chunk_q, 1, NFFT_GATHER_CELL_COST,
+        NFFT_GATHER_TILE_COST, S.c_gather, S.g_chunk_unit_start);
+    UOTK_LAUNCHED(ctx);
+    k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(
+        S.tile_start, S.tile_rank, S.cell_rank, S.ckey, S.tile_unit_start, tiles, P.tiles1,
+        S.chunk_q, 0, NFFT_SPREAD_CELL_COST, NFFT_SPREAD_TILE_COST, S.chunk_unit_start,
+        S.unit_tile, S.unit_begin, S.unit_count, S.unit_chunk);
+    UOTK_LAUNCHED(ctx);
+    k_make_units<<<grid_for(ctx, tiles, 128), 128, 0, s>>>(
+        S.tile_start, S.tile_rank, S.cell_rank, S.ckey, S.g_tile_unit_start, tiles, P.tiles1,
+        S.chunk_q, 1, NFFT_GATHER_CELL_COST, NFFT_GATHER_TILE_COST, S.g_chunk_unit_start,
+        S.g_unit_tile, S.g_unit_begin, S.g_unit_count, S.g_unit_chunk);
+    UOTK_LAUNCHED(ctx);
+    k_chunk_starts<<<grid_for(ctx, S.c_spread + 1, 256), 256, 0, s>>>(
+        S.unit_chunk, S.num_units, S.c_spread, S.chunk_unit_start);
+    UOTK_LAUNCHED(ctx);
+    k_chunk_starts<<<grid_for(ctx, S.c_gather + 1, 256), 256, 0, s>>>(
+        S.g_unit_chunk, S.g_num_units, S.c_gather, S.g_chunk_unit_start);
     UOTK_LAUNCHED(ctx);
   }
   if (n > 0) {
