@@ -492,10 +492,11 @@ __global__ void __launch_bounds__(FOLD_THREADS)
 // 8T + 8 + m - 2 (mod n) per axis, within one tile of T for m <= 8; on a grid
 // of two tiles per axis the offsets -1 and +1 name the same tile, whose block
 // then covers some nodes twice, as the torus requires.  A tile of one unit
-// holds only the z-planes that unit wrote.  One CTA per output tile, one
-// thread per node.
+// holds only the entries of that unit's box.  One CTA per output tile, each
+// thread four consecutive x nodes (one 16-byte store).
+constexpr int FOLD2_THREADS = NFFT_TILE * NFFT_TILE * NFFT_TILE / 4;
 template <int M>
-__global__ void __launch_bounds__(512)
+__global__ void __launch_bounds__(FOLD2_THREADS)
     k_fold(const float* __restrict__ blocks, const int* __restrict__ tile_unit_start,
            const int* __restrict__ unit_box, int n, int tiles1, float* __restrict__ grid) {
   constexpr int W2 = 2 * M, E = NFFT_TILE + 2 * M - 1;
@@ -538,36 +539,39 @@ __global__ void __launch_bounds__(512)
     if (c == 0) nlist = __popc(bal);
   }
   __syncthreads();
-  const int lx = threadIdx.x & 7, ly = (threadIdx.x >> 3) & 7, lz = threadIdx.x >> 6;
+  const int lx = (threadIdx.x & 1) * 4, ly = (threadIdx.x >> 1) & 7, lz = threadIdx.x >> 4;
   const int nl = nlist;
-  float* dst = grid + ((long long)(tz * NFFT_TILE + lz) * n + ty * NFFT_TILE + ly) * n +
-               tx * NFFT_TILE + lx;
-  if (nl == 0) {  // no tile block reaches this output tile
-    *dst = 0.f;
-    return;
-  }
-  // in batches of four: the loads of a batch in flight together, then added
-  // in list order
-  float v = 0.f;
+  float4* dst = reinterpret_cast<float4*>(
+      grid + ((long long)(tz * NFFT_TILE + lz) * n + ty * NFFT_TILE + ly) * n + tx * NFFT_TILE + lx);
+  float v[4] = {0.f, 0.f, 0.f, 0.f};
+  // in batches of four neighbours: the 16 loads of a batch in flight together,
+  // then added in list order
   for (int q0 = 0; q0 < nl; q0 += 4) {
-    float t[4];
+    float t[4][4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       const int q = q0 + j;
-      t[j] = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) t[j][i] = 0.f;
       if (q < nl) {
         const int c = offs[q];
         const int dz = c / 9 - 1, dy = (c / 3) % 3 - 1, dx = c % 3 - 1;
         const int Lz = lz - NFFT_TILE * dz + M - 1, Ly = ly - NFFT_TILE * dy + M - 1,
                   Lx = lx - NFFT_TILE * dx + M - 1;
-        if (Lz >= zlo[q] && Lz < zhi[q] && Ly >= ylo[q] && Ly < yhi[q] && Lx >= 0 && Lx < E)
-          t[j] = blocks[(size_t)first[q] * E3P + (Lz * E + Ly) * E + Lx];
+        if (Lz >= zlo[q] && Lz < zhi[q] && Ly >= ylo[q] && Ly < yhi[q]) {
+          const float* row = blocks + (size_t)first[q] * E3P + (Lz * E + Ly) * E;
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+            if (Lx + i >= 0 && Lx + i < E) t[j][i] = row[Lx + i];
+        }
       }
     }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) v += t[j];
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int i = 0; i < 4; ++i) v[i] += t[j][i];
   }
-  *dst = v;
+  *dst = make_float4(v[0], v[1], v[2], v[3]);
 }
 
 // Spread weights in sorted order: w_q = base_q exp(lam pot_q - shift).
@@ -1734,6 +1738,20 @@ size_t unit_smem() {
 // mean fewer barriers and longer runs of targets per warp.
 constexpr int GATHER_CH = 192;
 
+// SMs of the current device (queried once).
+int device_sms() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
+      sms = v;
+    else
+      return 1;
+  }
+  return sms;
+}
+
 // pw != NULL: the weights w = base e^{lam pot - shift} are formed in the
 // kernel; else staged from wts.  The unit blocks go to W.blocks and the fold
 // writes the whole grid.
@@ -1759,8 +1777,8 @@ uotk_status launch_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
                                                          S.tile_unit_start, S.unit_box,
                                                          S.num_units);
     UOTK_LAUNCHED(ctx);
-    k_fold<M><<<P.tiles1 * P.tiles1 * P.tiles1, 512, 0, s>>>(W.blocks, S.tile_unit_start,
-                                                             S.unit_box, P.n, P.tiles1, grid);
+    k_fold<M><<<P.tiles1 * P.tiles1 * P.tiles1, FOLD2_THREADS, 0, s>>>(
+        W.blocks, S.tile_unit_start, S.unit_box, P.n, P.tiles1, grid);
     UOTK_LAUNCHED(ctx);
   }
   return UOTK_OK;
@@ -1851,19 +1869,6 @@ static int gather_slots_m() {
     per = 2;  // one CTA per unit (k_gather): the number of chunks only sets the unit sizes
   }
   return per > 0 ? per : 1;
-}
-
-static int device_sms() {
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0, v = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess &&
-        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess && v > 0)
-      sms = v;
-    else
-      return 1;
-  }
-  return sms;
 }
 
 int nfft_spread_slots(int m) {
