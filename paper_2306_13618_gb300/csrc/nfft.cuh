@@ -98,6 +98,9 @@ struct NfftPoints {
   float* win = nullptr;      // sorted: [n][nfft_win_stride(m)] window rows (layout above)
   int* ckey = nullptr;       // sorted: packed cell (cx | cy<<10 | cz<<20), n + 4 entries
   float* winp = nullptr;     // [ceil(n/2)][nfft_winp_stride(m)] pair window rows (spread)
+  // the window tables are built on first use (nfft_points_windows): a cloud that
+  // is only spread, or only gathered at, never builds the other one
+  mutable bool win_ready = false, winp_ready = false;
   int* perm = nullptr;       // sorted position -> caller index
   int* tile_start = nullptr; // [tiles+1] start of each tile in sorted order
   int* tile_rank = nullptr;  // [tiles+1] occupied tiles before each tile
@@ -189,6 +192,10 @@ uotk_status nfft_bbox(uotk_ctx* ctx, cudaStream_t s, int d, const float* a, int6
 
 // Upper bound of the work units of n points cut into `chunks` chunks.
 int nfft_max_units(const NfftParams& P, int64_t n, int chunks);
+// Build the gather's window table (pair = false) or the spread's pair table
+// (pair = true) of a binned cloud unless it is built already.
+uotk_status nfft_points_windows(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                                const NfftPoints& S, bool pair);
 // Chunks of the spread and of the gather at cut-off m: the CTAs of the kernel
 // that the device holds at once.
 int nfft_spread_slots(int m);

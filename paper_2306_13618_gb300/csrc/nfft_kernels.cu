@@ -1909,6 +1909,7 @@ uotk_status nfft_spread(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, cons
     UOTK_CUDA(ctx, cudaMemsetAsync(grid_out, 0, sizeof(float) * total, s));
     return UOTK_OK;
   }
+  UOTK_TRY(nfft_points_windows(ctx, s, P, S, true));
   // Gaussian kernel: the spread forms the weights as its chunks land (the
   // non-smooth kernels' near field reads them from W.wts)
   if (w.pot && P.kernel == UOTK_KERNEL_GAUSS)
@@ -1974,6 +1975,7 @@ uotk_status nfft_convolve(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, Nf
 uotk_status nfft_gather(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P, const NfftPoints& S,
                         const float* grid, float* out_sorted, const DualUpdate* du) {
   if (S.n == 0) return UOTK_OK;
+  UOTK_TRY(nfft_points_windows(ctx, s, P, S, false));
   UOTK_PROF(ctx, s, "gather");
   return gather_units(ctx, s, P, S, grid, out_sorted, du);
 }

@@ -116,39 +116,58 @@ __global__ void k_bin_count(const float* __restrict__ pts, long long n, CellRule
   }
 }
 
-// Exclusive scan of the n^3 cell counts: blocks of 2048 (two per thread),
+// Exclusive scan of the n^3 cell counts: blocks of 2048 (eight per thread),
 // block sums scanned by one block, then added back.  Counts are zeroed as they
 // are read (they become the scatter cursors).
 constexpr int SCAN_BLOCK = 2048;
 
-__global__ void __launch_bounds__(1024) k_scan_local(int* __restrict__ count, long long total,
-                                                     int* __restrict__ start,
-                                                     int* __restrict__ block_sums) {
-  __shared__ int sh[SCAN_BLOCK];
-  const long long base = (long long)blockIdx.x * SCAN_BLOCK;
-  for (int k = threadIdx.x; k < SCAN_BLOCK; k += blockDim.x) {
+__global__ void __launch_bounds__(256) k_scan_local(int* __restrict__ count, long long total,
+                                                    int* __restrict__ start,
+                                                    int* __restrict__ block_sums) {
+  // 256 threads x 8 consecutive entries: serial sums per thread, a shuffle scan
+  // of the thread totals per warp, then of the eight warp totals
+  constexpr int PER = SCAN_BLOCK / 256;
+  __shared__ int wsum[8];
+  const long long base = (long long)blockIdx.x * SCAN_BLOCK + (long long)threadIdx.x * PER;
+  int v[PER];
+  int run = 0;
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
     const long long i = base + k;
-    int v = 0;
-    if (i < total) { v = count[i]; count[i] = 0; }
-    sh[k] = v;
+    v[k] = 0;
+    if (i < total) {
+      v[k] = count[i];
+      count[i] = 0;
+    }
+    run += v[k];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int inc = run;  // inclusive scan of the thread totals in the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += t;
+  }
+  if (lane == 31) wsum[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < 8 ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 8; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += t;
+    }
+    if (lane < 8) wsum[lane] = w;  // inclusive warp prefix
   }
   __syncthreads();
-  // Hillis-Steele inclusive scan over 2048 entries (each thread owns two)
-  for (int o = 1; o < SCAN_BLOCK; o <<= 1) {
-    int a0 = 0, a1 = 0;
-    const int k0 = threadIdx.x, k1 = threadIdx.x + 1024;
-    if (k0 >= o) a0 = sh[k0 - o];
-    if (k1 >= o) a1 = sh[k1 - o];
-    __syncthreads();
-    sh[k0] += a0;
-    sh[k1] += a1;
-    __syncthreads();
-  }
-  for (int k = threadIdx.x; k < SCAN_BLOCK; k += blockDim.x) {
+  int off = inc - run + (warp ? wsum[warp - 1] : 0);  // exclusive prefix of this thread
+#pragma unroll
+  for (int k = 0; k < PER; ++k) {
     const long long i = base + k;
-    if (i < total) start[i] = k ? sh[k - 1] : 0;
+    if (i < total) start[i] = off;
+    off += v[k];
   }
-  if (threadIdx.x == 0) block_sums[blockIdx.x] = sh[SCAN_BLOCK - 1];
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = wsum[7];
 }
 
 __global__ void __launch_bounds__(1024) k_scan_top(int* __restrict__ block_sums, int nb) {
@@ -471,54 +490,70 @@ __device__ __forceinline__ float kb_window(float v, int m, float b) {
   return mf * expf(b * (s - mf)) * (-expm1f(-2.f * b * s)) / (s * den);
 }
 
-__global__ void k_windows(const int4* __restrict__ cell, long long n, int m, float b,
-                          int d, float* __restrict__ win) {
-  const int w2 = 2 * m, ws = nfft_win_stride(m), hp = nfft_win_half(m);
+// Window tables.  A CTA takes WIN_PTS consecutive sorted points, thread (q, t)
+// evaluates the 2m values of point q along axis t into a shared-memory copy
+// of the CTA's rows (with their padding), and the CTA then writes its rows,
+// which are contiguous in the table, with 16-byte stores.
+constexpr int WIN_PTS = 64;
+constexpr int WIN_SMEM_F = WIN_PTS * 48;  // rows of the largest stride (m = 8): 48 floats a point
+
+// Gather layout (nfft.cuh): point q's row, phi_x halves, phi_y, phi_z.
+__global__ void __launch_bounds__(3 * WIN_PTS)
+    k_windows(const int4* __restrict__ cell, long long n, int m, float b,
+              float* __restrict__ win) {
+  __shared__ __align__(16) float buf[WIN_SMEM_F];
+  const int ws = nfft_win_stride(m), hp = nfft_win_half(m);
   const int yo = nfft_win_yoff(m), zo = nfft_win_zoff(m);
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n * ws;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long q = i / ws;
-    const int r = (int)(i - q * ws);
-    int t, k;
-    if (r < m) { t = 0; k = r; }
-    else if (r >= hp && r < hp + m) { t = 0; k = r - hp + m; }
-    else if (r >= yo && r < yo + w2) { t = 1; k = r - yo; }
-    else if (r >= zo && r < zo + w2) { t = 2; k = r - zo; }
-    else { win[i] = 0.f; continue; }
-    const int4 c = cell[q];
-    const float f = __int_as_float(t == 0 ? c.y : (t == 1 ? c.z : c.w));
-    const float v = f + (float)(m - 1 - k);
-    win[i] = kb_window(v, m, b);
+  for (long long q0 = (long long)blockIdx.x * WIN_PTS; q0 < n; q0 += (long long)gridDim.x * WIN_PTS) {
+    const int np = (int)min((long long)WIN_PTS, n - q0);
+    for (int i = threadIdx.x; i < np * ws; i += blockDim.x) buf[i] = 0.f;
+    __syncthreads();
+    const int qi = threadIdx.x / 3, t = threadIdx.x - 3 * qi;
+    if (qi < np) {
+      const int4 c = cell[q0 + qi];
+      const float f = __int_as_float(t == 0 ? c.y : (t == 1 ? c.z : c.w));
+      float* row = buf + qi * ws;
+      for (int k = 0; k < 2 * m; ++k) {
+        const int r = t == 0 ? (k < m ? k : hp + k - m) : (t == 1 ? yo : zo) + k;
+        row[r] = kb_window(f + (float)(m - 1 - k), m, b);
+      }
+    }
+    __syncthreads();
+    float4* dst = reinterpret_cast<float4*>(win + q0 * ws);
+    const float4* src = reinterpret_cast<const float4*>(buf);
+    for (int i = threadIdx.x; i < np * ws / 4; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
   }
 }
 
-
-// Pair window rows: row p holds, for every window value, the pair (point 2p,
-// point 2p + 1); a missing second point (odd n) gets zeros.
-__global__ void k_windows_pair(const int4* __restrict__ cell, long long n, int m, float b,
-                               float* __restrict__ win) {
+// Pair layout (nfft.cuh): row p holds, for every window value, the pair
+// (point 2p, point 2p + 1); a missing second point (odd n) gets zeros.
+__global__ void __launch_bounds__(3 * WIN_PTS)
+    k_windows_pair(const int4* __restrict__ cell, long long n, int m, float b,
+                   float* __restrict__ win) {
+  __shared__ __align__(16) float buf[WIN_SMEM_F];
   const int ws = nfft_winp_stride(m), hp = nfft_winp_half(m);
   const int yo = nfft_winp_yoff(m), zo = nfft_winp_zoff(m);
-  const long long np = (n + 1) / 2;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < np * ws;
-       i += (long long)gridDim.x * blockDim.x) {
-    const long long p = i / ws;
-    const int r = (int)(i - p * ws);
-    int t, k, lane;
-    if (r < yo) {
-      const int h = r / hp, rem = r - h * hp;
-      if (rem >= 2 * m) { win[i] = 0.f; continue; }
-      t = 0; k = h * m + (rem >> 1); lane = rem & 1;
-    } else if (r < zo) {
-      t = 1; k = (r - yo) >> 1; lane = (r - yo) & 1;
-    } else {
-      t = 2; k = (r - zo) >> 1; lane = (r - zo) & 1;
+  const long long n2 = (n + 1) & ~1LL;
+  for (long long q0 = (long long)blockIdx.x * WIN_PTS; q0 < n2; q0 += (long long)gridDim.x * WIN_PTS) {
+    const int np = (int)min((long long)WIN_PTS, n2 - q0);  // even
+    for (int i = threadIdx.x; i < np / 2 * ws; i += blockDim.x) buf[i] = 0.f;
+    __syncthreads();
+    const int qi = threadIdx.x / 3, t = threadIdx.x - 3 * qi;
+    if (qi < np && q0 + qi < n) {
+      const int4 c = cell[q0 + qi];
+      const float f = __int_as_float(t == 0 ? c.y : (t == 1 ? c.z : c.w));
+      float* row = buf + (qi >> 1) * ws + (qi & 1);
+      for (int k = 0; k < 2 * m; ++k) {
+        const int r = t == 0 ? (k / m) * hp + 2 * (k % m) : (t == 1 ? yo : zo) + 2 * k;
+        row[r] = kb_window(f + (float)(m - 1 - k), m, b);
+      }
     }
-    const long long q = 2 * p + lane;
-    if (q >= n) { win[i] = 0.f; continue; }
-    const int4 c = cell[q];
-    const float f = __int_as_float(t == 0 ? c.y : (t == 1 ? c.z : c.w));
-    win[i] = kb_window(f + (float)(m - 1 - k), m, b);
+    __syncthreads();
+    float4* dst = reinterpret_cast<float4*>(win + (q0 >> 1) * ws);
+    const float4* src = reinterpret_cast<const float4*>(buf);
+    for (int i = threadIdx.x; i < np / 2 * ws / 4; i += blockDim.x) dst[i] = src[i];
+    __syncthreads();
   }
 }
 
@@ -740,7 +775,7 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
                                                          S.rs_key[0], S.cell_count);
       UOTK_LAUNCHED(ctx);
     }
-    k_scan_local<<<nb, 1024, 0, s>>>(S.cell_count, n3, S.cell_start, S.block_sums);
+    k_scan_local<<<nb, 256, 0, s>>>(S.cell_count, n3, S.cell_start, S.block_sums);
     UOTK_LAUNCHED(ctx);
     k_scan_top<<<1, 1024, 0, s>>>(S.block_sums, nb);
     UOTK_LAUNCHED(ctx);
@@ -751,7 +786,7 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
     // occupied-cell ranks (the counts are not needed any more: flags in place)
     k_occ_flags<<<grid_for(ctx, n3, 256), 256, 0, s>>>(S.cell_start, n3, S.cell_count);
     UOTK_LAUNCHED(ctx);
-    k_scan_local<<<nb, 1024, 0, s>>>(S.cell_count, n3, S.cell_rank, S.block_sums);
+    k_scan_local<<<nb, 256, 0, s>>>(S.cell_count, n3, S.cell_rank, S.block_sums);
     UOTK_LAUNCHED(ctx);
     k_scan_top<<<1, 1024, 0, s>>>(S.block_sums, nb);
     UOTK_LAUNCHED(ctx);
@@ -772,7 +807,7 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
       for (int shift = 0; shift < bits; shift += 8, cur ^= 1) {
         k_rs_hist<<<rb, RS_THREADS, 0, s>>>(S.rs_key[cur], n, shift, rb, S.rs_hist);
         UOTK_LAUNCHED(ctx);
-        k_scan_local<<<hb, 1024, 0, s>>>(S.rs_hist, hn, S.rs_start, S.rs_bsum);
+        k_scan_local<<<hb, 256, 0, s>>>(S.rs_hist, hn, S.rs_start, S.rs_bsum);
         UOTK_LAUNCHED(ctx);
         k_scan_top<<<1, 1024, 0, s>>>(S.rs_bsum, hb);
         UOTK_LAUNCHED(ctx);
@@ -813,15 +848,26 @@ uotk_status nfft_points_build(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P
         S.g_unit_chunk, S.g_num_units, S.c_gather, S.g_chunk_unit_start);
     UOTK_LAUNCHED(ctx);
   }
-  if (n > 0) {
-    UOTK_PROF(ctx, s, "window");
-    k_windows<<<grid_for(ctx, n * nfft_win_stride(P.m), 256), 256, 0, s>>>(S.cell, n, P.m, P.b,
-                                                                         P.d, S.win);
-    UOTK_LAUNCHED(ctx);
-    k_windows_pair<<<grid_for(ctx, (n + 1) / 2 * nfft_winp_stride(P.m), 256), 256, 0, s>>>(
+  S.win_ready = false;
+  S.winp_ready = false;
+  return UOTK_OK;
+}
+
+uotk_status nfft_points_windows(uotk_ctx* ctx, cudaStream_t s, const NfftParams& P,
+                                const NfftPoints& S, bool pair) {
+  const int64_t n = S.n;
+  if (n == 0 || (pair ? S.winp_ready : S.win_ready)) return UOTK_OK;
+  UOTK_PROF(ctx, s, "window");
+  if (pair) {
+    k_windows_pair<<<grid_for(ctx, (n + 1) / 2 * 6, 3 * WIN_PTS), 3 * WIN_PTS, 0, s>>>(
         S.cell, n, P.m, P.b, S.winp);
-    UOTK_LAUNCHED(ctx);
+    S.winp_ready = true;
+  } else {
+    k_windows<<<grid_for(ctx, 3 * n, 3 * WIN_PTS), 3 * WIN_PTS, 0, s>>>(S.cell, n, P.m, P.b,
+                                                                        S.win);
+    S.win_ready = true;
   }
+  UOTK_LAUNCHED(ctx);
   return UOTK_OK;
 }
 
