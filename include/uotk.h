@@ -337,9 +337,13 @@ uotk_status uotk_uot_sinkhorn_scaled(uotk_ctx* ctx, void* stream, int d,
 /* ---- many independent problems at once (batched Alg. 1, direct form) -------------
  * npairs problems (x^p, a^p; y^p, b^p) of uneven sizes, each with its own eps_p,
  * rho1_p, rho2_p, all solved by Alg. 1 together: every half-step of every pair is
- * one grouped launch, two sweeps are replayed from one CUDA graph, and pairs that
- * meet tol (tested every 10 sweeps, as in uotk_uot_sinkhorn) are retired while
- * the others continue.
+ * one grouped launch, and the sweep loop runs on the device (a CUDA graph whose
+ * WHILE node repeats two sweeps and a control kernel, captured on the context's
+ * own stream).  After every two sweeps the control kernel retires the pairs whose
+ * last change met tol, while the others continue, and ends the loop when none is
+ * left or max_sweeps would be passed; the host reads the outcome once at the end.
+ * With per-stage profiling on, the launches stay eager and the host tests the
+ * pairs every 10 sweeps.
  *   x_off, y_off: host int64 [npairs + 1], nondecreasing; pair p owns points
  *     x_off[p] .. x_off[p+1]-1 of x (device FP32 [.*d], row-major) and of a,
  *     and likewise y, b; every pair needs at least one point on each side.
@@ -435,7 +439,11 @@ uotk_status uotk_sinkhorn_divergence_grad(uotk_ctx* ctx, void* stream, int d,
  *   into grid (device FP32 [grid^3], overwritten).
  * uotk_nfft_convolve: grid_out = IFFT( scale_k * FFT(grid_in) ), with
  *   scale_k = b_k / prod_t (n phihat(k_t))^2 on {-N/2..N/2-1}^3 and 0 elsewhere;
- *   forward and inverse FFT unnormalised.  grid_in and grid_out may alias.
+ *   forward and inverse FFT unnormalised.  For the Gaussian at grid 128 the
+ *   convolution runs as three real circulant passes, one per axis, over the
+ *   symmetric band |k_t| <= N/2 - 1 (the k_t = -N/2 planes, whose coefficients
+ *   are at the truncation error the plan balances, are left out).  grid_in and
+ *   grid_out may alias.
  * uotk_nfft_gather: out_j = sum_l grid_l prod_t phi(u_jt - l_t/n), out = device FP32 [m]. */
 uotk_status uotk_nfft_plan(uotk_ctx* ctx, void* stream, int d,
                            const float* src, int64_t n, const float* tgt, int64_t m,
