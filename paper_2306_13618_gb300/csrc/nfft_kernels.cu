@@ -417,6 +417,8 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
 // threads, G groups of threads each sum the units g, g + G, g + 2G, .. of
 // every entry, and the G partial sums are then added in group order: a dense
 // tile costs about one block's reads per CTA and short dependency chains.
+// Longer slices (tiles of few units) give each thread four entries at once,
+// loaded four units per round.
 constexpr int FOLD_THREADS = 256;
 constexpr int FOLD_BOX_CACHE = 2048;  // unit boxes of a tile held in shared memory
 template <int M>
@@ -456,8 +458,34 @@ __global__ void __launch_bounds__(FOLD_THREADS)
   // flight, added in a fixed order
   int G = FOLD_THREADS / ne;
   G = G < 1 ? 1 : (G < U ? G : U);
-  const int ei = G > 1 ? threadIdx.x % ne : 0, g = G > 1 ? threadIdx.x / ne : 0;
-  for (int eb = e0 + (G > 1 ? ei : (int)threadIdx.x); eb < e1; eb += (G > 1 ? e1 : FOLD_THREADS)) {
+  if (G == 1) {
+    // long slices (tiles of few units): four entries per thread at once, each
+    // summed over the units in order, four units per round: 16 loads in flight
+    constexpr int EPT = 4, UPR = 4;
+    for (int eb0 = e0 + (int)threadIdx.x; eb0 < e1; eb0 += EPT * FOLD_THREADS) {
+      float acc[EPT] = {0.f, 0.f, 0.f, 0.f};
+      for (int v0 = 0; v0 < U; v0 += UPR) {
+        float tv[UPR][EPT];
+#pragma unroll
+        for (int j = 0; j < UPR; ++j)
+#pragma unroll
+          for (int i = 0; i < EPT; ++i) {
+            const int eb = eb0 + i * FOLD_THREADS;
+            tv[j][i] = (v0 + j < U && eb < e1) ? entry(v0 + j, eb) : 0.f;
+          }
+#pragma unroll
+        for (int j = 0; j < UPR; ++j)
+#pragma unroll
+          for (int i = 0; i < EPT; ++i) acc[i] += tv[j][i];
+      }
+#pragma unroll
+      for (int i = 0; i < EPT; ++i)
+        if (eb0 + i * FOLD_THREADS < e1) first[eb0 + i * FOLD_THREADS] = acc[i];
+    }
+    return;
+  }
+  const int ei = threadIdx.x % ne, g = threadIdx.x / ne;
+  for (int eb = e0 + ei; eb < e1; eb += e1) {
     float s8[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (g < G) {
       int v = g;
@@ -471,16 +499,12 @@ __global__ void __launch_bounds__(FOLD_THREADS)
       for (int j = 0; v < U; v += G, ++j) s8[j] += entry(v, eb);
     }
     const float sum = ((s8[0] + s8[1]) + (s8[2] + s8[3])) + ((s8[4] + s8[5]) + (s8[6] + s8[7]));
-    if (G == 1) {
-      first[eb] = sum;
-    } else {
-      part[threadIdx.x] = sum;
-      __syncthreads();  // every group has read its units before the first block is overwritten
-      if (threadIdx.x < ne) {
-        float r = 0.f;
-        for (int q = 0; q < G; ++q) r += part[q * ne + threadIdx.x];
-        first[e0 + threadIdx.x] = r;
-      }
+    part[threadIdx.x] = sum;
+    __syncthreads();  // every group has read its units before the first block is overwritten
+    if (threadIdx.x < ne) {
+      float r = 0.f;
+      for (int q = 0; q < G; ++q) r += part[q * ne + threadIdx.x];
+      first[e0 + threadIdx.x] = r;
     }
   }
 }
