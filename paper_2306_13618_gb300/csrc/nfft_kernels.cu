@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
     double ppot[WK];
     float pbase[WK];
     auto prefetch = [&](int pc0) {
-  #pragma unroll
+#pragma unroll
       for (int j = 0; j < WK; ++j) {
         const int q = 2 * pc0 + wt + j * WTN;
         ppot[j] = 0.0;
@@ -250,14 +250,14 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
       // list where each cell's run of points starts (points are sorted by cell).
       if (POT) {
         if (wt >= 0) {
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < WK; ++j) {
             const int t = wt + j * WTN;
             if (t < 2 * cpn) {
               const float w = (t >= lo && t < hi) ? pbase[j] * exp_shifted(pw.lam * ppot[j] - shift)
                                                   : 0.f;
               float* zr = sw + (t >> 1) * WSP + ZO2 + (t & 1);
-  #pragma unroll
+#pragma unroll
               for (int i = 0; i < W2; ++i) zr[2 * i] *= w;
             }
           }
@@ -296,9 +296,9 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
           const int t0 = gstart[g], t1 = gstart[g + 1];
           const int key = skey[t0];
           unsigned long long acc2[ZB][M];
-  #pragma unroll
+#pragma unroll
           for (int r = 0; r < ZB; ++r)
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < M; ++j) acc2[r][j] = 0ull;
           const int pp0 = t0 >> 1, pp1 = (t1 - 1) >> 1;
           // one point pair: the masked y factor, the m phi_x pairs and the ZB
@@ -312,14 +312,14 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
             unsigned long long fy2 = *reinterpret_cast<const unsigned long long*>(row + YO2 + 2 * y);
             if (mask) fy2 = f2_mul(fy2, mask);
             const float* xr = row + xh * HP2;
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j + 1 < M; j += 2) {
               const float4 v = *reinterpret_cast<const float4*>(xr + 2 * j);
               fx2[j] = f2_pack(v.x, v.y);
               fx2[j + 1] = f2_pack(v.z, v.w);
             }
             if (M & 1) fx2[M - 1] = *reinterpret_cast<const unsigned long long*>(xr + 2 * (M - 1));
-  #pragma unroll
+#pragma unroll
             for (int r = 0; r < ZB; ++r)
               A2[r] = f2_mul(*reinterpret_cast<const unsigned long long*>(row + ZO2 + 2 * (z0 + r)),
                              fy2);
@@ -331,18 +331,18 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
             if (pp0 == pp1 && (t1 & 1)) m0 = f2_mul(m0, keep_lo);
             unsigned long long fa[M], Aa[ZB];
             load_pair(pp0, fa, Aa, m0);
-  #pragma unroll
+#pragma unroll
             for (int r = 0; r < ZB; ++r)
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
             ++pp;
           }
           if (pp <= pp1 && (t1 & 1)) {
             unsigned long long fa[M], Aa[ZB];
             load_pair(pp1, fa, Aa, keep_lo);
-  #pragma unroll
+#pragma unroll
             for (int r = 0; r < ZB; ++r)
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
             --pe1;
           }
@@ -351,24 +351,24 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
             unsigned long long fa[M], fb[M], Aa[ZB], Ab[ZB];
             load_pair(pp, fa, Aa, 0ull);
             load_pair(pp + 1, fb, Ab, 0ull);
-  #pragma unroll
+#pragma unroll
             for (int r = 0; r < ZB; ++r)
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Ab[r], fb[j], f2_fma(Aa[r], fa[j], acc2[r][j]));
           }
           if (pp <= pe1) {
             unsigned long long fa[M], Aa[ZB];
             load_pair(pp, fa, Aa, 0ull);
-  #pragma unroll
+#pragma unroll
             for (int r = 0; r < ZB; ++r)
-  #pragma unroll
+#pragma unroll
               for (int j = 0; j < M; ++j) acc2[r][j] = f2_fma(Aa[r], fa[j], acc2[r][j]);
           }
           const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
           float* dst = blk + ((bz + z0) * E + by + y) * E + bx + xh * M;
-  #pragma unroll
+#pragma unroll
           for (int r = 0; r < ZB; ++r)
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < M; ++j) {
               float e, o;
               f2_unpack(acc2[r][j], e, o);
@@ -1605,16 +1605,16 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
     // footprint registers and give six independent FMA chains instead of three
     auto target_pair = [&](const float* ra, const float* rb, float& pa, float& pb) {
       unsigned long long Ha[MP], Hb[MP];
-  #pragma unroll
+#pragma unroll
       for (int j = 0; j < MP; ++j) Ha[j] = Hb[j] = 0ull;
-  #pragma unroll
+#pragma unroll
       for (int z = 0; z < BZ; ++z) {
         const float za = ra[ZO + z0 + z], zb = rb[ZO + z0 + z];
-  #pragma unroll
+#pragma unroll
         for (int yy = 0; yy < BZ; ++yy) {
           const float a = za * ra[YO + y0 + yy], b = zb * rb[YO + y0 + yy];
           const unsigned long long A = f2_pack(a, a), B = f2_pack(b, b);
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < MP; ++j) {
             Ha[j] = f2_fma(A, hc[z][yy][j], Ha[j]);
             Hb[j] = f2_fma(B, hc[z][yy][j], Hb[j]);
@@ -1626,7 +1626,7 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
       load_vec<M>(rb + xh * HP, fb);
       unsigned long long sa = f2_mul(f2_pack(fa[0], fa[1]), Ha[0]);
       unsigned long long sb = f2_mul(f2_pack(fb[0], fb[1]), Hb[0]);
-  #pragma unroll
+#pragma unroll
       for (int j = 1; j < MP; ++j) {
         sa = f2_fma(f2_pack(fa[2 * j], fa[2 * j + 1]), Ha[j], sa);
         sb = f2_fma(f2_pack(fb[2 * j], fb[2 * j + 1]), Hb[j], sb);
@@ -1641,36 +1641,36 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
       if (key != cached) {
         const int bx = (key & 1023) - tx0, by = ((key >> 10) & 1023) - ty0, bz = (key >> 20) - tz0;
         const float* src = blk + ((bz + z0) * E + by + y0) * E + bx + xh * M;
-  #pragma unroll
+#pragma unroll
         for (int z = 0; z < BZ; ++z)
-  #pragma unroll
+#pragma unroll
           for (int yy = 0; yy < BZ; ++yy)
-  #pragma unroll
+#pragma unroll
             for (int j = 0; j < MP; ++j)
               hc[z][yy][j] = f2_pack(src[(z * E + yy) * E + 2 * j], src[(z * E + yy) * E + 2 * j + 1]);
         cached = key;
       }
       float fz[BZ], fy[BZ], fx[M];
-  #pragma unroll
+#pragma unroll
       for (int k = 0; k < BZ; ++k) {
         fz[k] = row[ZO + z0 + k];
         fy[k] = row[YO + y0 + k];
       }
       load_vec<M>(row + xh * HP, fx);
       unsigned long long H[MP];
-  #pragma unroll
+#pragma unroll
       for (int j = 0; j < MP; ++j) H[j] = 0ull;
-  #pragma unroll
+#pragma unroll
       for (int z = 0; z < BZ; ++z)
-  #pragma unroll
+#pragma unroll
         for (int yy = 0; yy < BZ; ++yy) {
           const float a = fz[z] * fy[yy];
           const unsigned long long A = f2_pack(a, a);
-  #pragma unroll
+#pragma unroll
           for (int j = 0; j < MP; ++j) H[j] = f2_fma(A, hc[z][yy][j], H[j]);
         }
       unsigned long long r = f2_mul(f2_pack(fx[0], fx[1]), H[0]);
-  #pragma unroll
+#pragma unroll
       for (int j = 1; j < MP; ++j) r = f2_fma(f2_pack(fx[2 * j], fx[2 * j + 1]), H[j], r);
       float lo, hi;
       f2_unpack(r, lo, hi);
@@ -1696,7 +1696,7 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
       const int* skey = reinterpret_cast<const int*>(sb + GW * WS) + (q0 & 3);
       for (int p = 0; p < cn; p += 4) {
         float part[4];
-  #pragma unroll
+#pragma unroll
         for (int j = 0; j < 4; j += 2) {
           if (p + j + 1 < cn && skey[p + j] == skey[p + j + 1]) {
             // the first call loads the pair's footprint if needed; then both together
