@@ -83,6 +83,12 @@ __device__ __forceinline__ bool stage_ready(unsigned long long* bars, int k, int
   return true;
 }
 
+// Grid node index v mod n for v in [-n, 2n): a tile's block reaches at most
+// m - 1 nodes below its tile and m - 2 above it, and n >= 16 > m.
+__device__ __forceinline__ int wrap_node(int v, int n) {
+  return v < 0 ? v + n : (v >= n ? v - n : v);
+}
+
 __device__ __forceinline__ void tile_origin(int tile, int tiles1, int& x, int& y, int& z) {
   x = (tile % tiles1) * NFFT_TILE;
   y = ((tile / tiles1) % tiles1) * NFFT_TILE;
@@ -1363,10 +1369,8 @@ __global__ void __launch_bounds__(256)
   tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
   for (int i = threadIdx.x; i < E3; i += blockDim.x) {
     const int lz = i / E2, ly = (i / E) % E, lx = i % E;
-    int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
-    gz += gz < 0 ? n : 0;
-    gy += gy < 0 ? n : 0;
-    gx += gx < 0 ? n : 0;
+    const int gz = wrap_node(tz0 - M + 1 + lz, n), gy = wrap_node(ty0 - M + 1 + ly, n),
+              gx = wrap_node(tx0 - M + 1 + lx, n);
     blk[i] = grid[((long long)gz * n + gy) * n + gx];
   }
   __syncthreads();  // barriers initialised and block staged before anyone waits or reads
@@ -1592,10 +1596,8 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
     tile_origin(unit_tile[u], tiles1, tx0, ty0, tz0);
     for (int i = threadIdx.x; i < E3; i += blockDim.x) {
       const int lz = i / E2, ly = (i / E) % E, lx = i % E;
-      int gz = (tz0 - M + 1 + lz) % n, gy = (ty0 - M + 1 + ly) % n, gx = (tx0 - M + 1 + lx) % n;
-      gz += gz < 0 ? n : 0;
-      gy += gy < 0 ? n : 0;
-      gx += gx < 0 ? n : 0;
+      const int gz = wrap_node(tz0 - M + 1 + lz, n), gy = wrap_node(ty0 - M + 1 + ly, n),
+                gx = wrap_node(tx0 - M + 1 + lx, n);
       blk[i] = grid[((long long)gz * n + gy) * n + gx];
     }
     __syncthreads();  // barriers initialised and block staged before anyone waits or reads
