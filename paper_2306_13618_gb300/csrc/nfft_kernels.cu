@@ -1498,7 +1498,7 @@ __global__ void __launch_bounds__(256)
 // (2m)^3 nodes), held in registers as x pairs while consecutive targets share
 // a cell.  Per target, lane part = sum_x phi_x sum_{z,y} (phi_z phi_y) g[z][y][x]
 // (the inner sums packed over x pairs), and the warp adds the 32 parts.
-constexpr int GW = 16;      // targets per per-warp staging buffer
+constexpr int GW = 32;      // targets per per-warp staging buffer (two buffers of 32 rows: two CTAs per SM)
 constexpr int GWARPS = 8;   // warps of a gather CTA
 template <int M>
 struct GatherGeo {
