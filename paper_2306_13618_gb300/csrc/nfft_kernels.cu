@@ -89,6 +89,18 @@ __device__ __forceinline__ int wrap_node(int v, int n) {
   return v < 0 ? v + n : (v >= n ? v - n : v);
 }
 
+// NFFT half-steps take the weights and the logarithms of the sums in FP32 from
+// the FP64 exponent: w = base e^{lam pot - shift} with the difference in FP64 and
+// the exponential in FP32.  A weight e^a then carries a relative error of about
+// |a| 2^-24, an absolute error below e^-1 2^-24 of the largest weight, far below
+// the window sums' own error of about 1e-5 of the total weight; likewise log t
+// in FP32 (about 4e-6 absolute at the extreme |log t| = 88) against the sums'
+// relative error.  This leaves one FP64 FMA and one conversion per point, on a
+// GPU where an FP64 warp instruction holds the FP64 unit for about 64 cycles.
+__device__ __forceinline__ float nfft_weight(float base, double lam, double pot, double shift) {
+  return base * expf((float)fma(lam, pot, -shift));
+}
+
 __device__ __forceinline__ void tile_origin(int tile, int tiles1, int& x, int& y, int& z) {
   x = (tile % tiles1) * NFFT_TILE;
   y = ((tile / tiles1) % tiles1) * NFFT_TILE;
@@ -260,7 +272,7 @@ __global__ void __launch_bounds__(SpreadMap<M>::NTH)
           for (int j = 0; j < WK; ++j) {
             const int t = wt + j * WTN;
             if (t < 2 * cpn) {
-              const float w = (t >= lo && t < hi) ? pbase[j] * exp_shifted(pw.lam * ppot[j] - shift)
+              const float w = (t >= lo && t < hi) ? nfft_weight(pbase[j], pw.lam, ppot[j], shift)
                                                   : 0.f;
               float* zr = sw + (t >> 1) * WSP + ZO2 + (t & 1);
 #pragma unroll
@@ -1354,9 +1366,9 @@ __global__ void __launch_bounds__(256)
   int dn = 0;      // group of four targets that parks next (warp-uniform)
   auto dual_flush = [&]() {
     if (di >= 0) {
-      const double lt = dt > 0.f && isfinite(dt) ? log_f32(dt) : log((double)dt);
-      const double v = du.ref == 0 ? fma(-du.q, lt, -qs)
-                                   : fma(du.q, log_f32(du.base[di]) - lt, -qs);
+      const float lt = logf(dt);  // -inf for 0, nan for negatives: flagged below
+      const double v = du.ref == 0 ? fma(-du.q, (double)lt, -qs)
+                                   : fma(du.q, (double)(logf(du.base[di]) - lt), -qs);
       if (du.delta_out >= 0) ddl = fmax(ddl, fabs(v - du.pot[di]));
       du.pot[di] = v;
       if (isfinite(v)) dmx = fmax(dmx, v);
@@ -1562,9 +1574,9 @@ __global__ void __launch_bounds__(32 * GWARPS, 2)
   int di = -1, dn = 0;
   auto dual_flush = [&]() {
     if (di >= 0) {
-      const double lt = dt > 0.f && isfinite(dt) ? log_f32(dt) : log((double)dt);
-      const double v = du.ref == 0 ? fma(-du.q, lt, -qs)
-                                   : fma(du.q, log_f32(du.base[di]) - lt, -qs);
+      const float lt = logf(dt);  // -inf for 0, nan for negatives: flagged below
+      const double v = du.ref == 0 ? fma(-du.q, (double)lt, -qs)
+                                   : fma(du.q, (double)(logf(du.base[di]) - lt), -qs);
       if (du.delta_out >= 0) ddl = fmax(ddl, fabs(v - du.pot[di]));
       du.pot[di] = v;
       if (isfinite(v)) dmx = fmax(dmx, v);
