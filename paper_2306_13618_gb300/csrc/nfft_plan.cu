@@ -341,8 +341,9 @@ __global__ void __launch_bounds__(RS_THREADS)
 }
 
 // Element i of the CTA's tile goes to start[digit][cta] + (number of earlier
-// elements of the tile with the same digit): earlier rounds (base), earlier
-// warps of this round (cnt), earlier lanes of this warp (match mask).
+// elements of the tile with the same digit): earlier iterations of the tile
+// loop (base), earlier warps of this iteration (cnt), earlier lanes of this
+// warp (match mask).
 __global__ void __launch_bounds__(RS_THREADS)
     k_rs_scatter(const int* __restrict__ kin, const int* __restrict__ vin, long long n, int shift,
                  int blocks, const int* __restrict__ start, int* __restrict__ kout,
