@@ -334,7 +334,7 @@ uotk_status uotk_uot_sinkhorn_scaled(uotk_ctx* ctx, void* stream, int d,
                                      int* sweeps_per_stage, double* value,
                                      const uotk_sum_opts* opts);
 
-/* ---- many independent problems at once (batched Alg. 1, direct form) -------------
+/* ---- many independent problems at once (batched Alg. 1 / Alg. 2) -----------------
  * npairs problems (x^p, a^p; y^p, b^p) of uneven sizes, each with its own eps_p,
  * rho1_p, rho2_p, all solved by Alg. 1 together: every half-step of every pair is
  * one grouped launch, and the sweep loop runs on the device (a CUDA graph whose
@@ -352,7 +352,15 @@ uotk_status uotk_uot_sinkhorn_scaled(uotk_ctx* ctx, void* stream, int d,
  *     final duals of each pair).
  *   sweeps_done (host int [npairs], may be NULL): sweeps run per pair;
  *   values (host double [npairs], may be NULL): D(beta, gamma) per pair.
- *   d in 1..3; opts (may be NULL) must select the direct form.
+ *   d in 1..3; opts (may be NULL) selects the direct form (UOTK_DIRECT) or
+ *   UOTK_AUTO: every pair with at least 16384 points on both sides then has
+ *   its form measured on its own data by the autotuner (as uotk_autotune_sum,
+ *   within opts->target_err, default 1e-5, with opts->grid / cutoff fixed if
+ *   given), each form timed as one sum on an already built plan, since a solve
+ *   builds its plan once.  Pairs whose fastest form is the NFFT (Alg. 2) are
+ *   solved one after another by the NFFT solver, the rest together as above;
+ *   start, stopping rule, cap and outputs per pair are the same.
+ *   uotk_batch_forms reports the form each pair used.
  *   Returns UOTK_ERR_NOT_CONVERGED if tol > 0 and some pair did not reach it
  *   (outputs valid).  Synchronises `stream`. */
 uotk_status uotk_uot_sinkhorn_batch(uotk_ctx* ctx, void* stream, int d, int npairs,
@@ -362,6 +370,11 @@ uotk_status uotk_uot_sinkhorn_batch(uotk_ctx* ctx, void* stream, int d, int npai
                                     int max_sweeps, double tol, int ref, double* beta,
                                     double* gamma, int* sweeps_done, double* values,
                                     const uotk_sum_opts* opts);
+/* uotk_batch_forms: forms (host int32 [npairs]) receives the uotk_method each
+ * pair of the last uotk_uot_sinkhorn_batch call on ctx was solved with
+ * (UOTK_DIRECT or UOTK_NFFT); npairs must be that call's.  Not part of the
+ * paper: a report of the per-pair choice of UOTK_AUTO. */
+uotk_status uotk_batch_forms(uotk_ctx* ctx, int npairs, int32_t* forms);
 
 /* ---- unbalanced Sinkhorn divergence, Eq. (586) ---------------------------------------
  * sd = UOT(mu,nu) - UOT(mu,mu)/2 - UOT(nu,nu)/2 + (mu(X) - nu(X))^2 * eps/2,

@@ -26,7 +26,7 @@ uotk_status op_measure_unit_rates(uotk_ctx*, cudaStream_t, double*, double*);
 uotk_status op_uot_sinkhorn_batch(uotk_ctx*, cudaStream_t, int, int, const int64_t*,
                                   const float*, const float*, const int64_t*, const float*,
                                   const float*, const double*, const double*, const double*, int,
-                                  double, int, double*, double*, int*, double*);
+                                  double, int, double*, double*, int*, double*, const int*, int);
 uotk_status op_mmd2_grad(uotk_ctx*, cudaStream_t, int, const float*, int64_t, const float*,
                          const float*, int64_t, const float*, double, double*, double*, double*,
                          double*, double*, const uotk_sum_opts*);
@@ -516,8 +516,10 @@ uotk_status uotk_uot_sinkhorn_batch(uotk_ctx* ctx, void* stream, int d, int npai
   UOTK_TRY(enter(ctx));
   UOTK_TRY(check_common(ctx, d, opts));
   UOTK_TRY(check_kernel(ctx, opts, false));
-  if ((opts ? opts->method : UOTK_DIRECT) != UOTK_DIRECT)
-    return set_error(ctx, UOTK_ERR_UNSUPPORTED, "uot_sinkhorn_batch: direct FP32 form only");
+  const int method = opts ? opts->method : UOTK_DIRECT;
+  if (method != UOTK_DIRECT && method != UOTK_AUTO)
+    return set_error(ctx, UOTK_ERR_UNSUPPORTED,
+                     "uot_sinkhorn_batch: the direct FP32 form or UOTK_AUTO only");
   if (d > 3) return set_error(ctx, UOTK_ERR_UNSUPPORTED, "uot_sinkhorn_batch: d = %d > 3", d);
   if (npairs < 1 || npairs > (1 << 20))
     return set_error(ctx, UOTK_ERR_INVALID, "uot_sinkhorn_batch: npairs %d outside [1, 2^20]",
@@ -545,9 +547,76 @@ uotk_status uotk_uot_sinkhorn_batch(uotk_ctx* ctx, void* stream, int d, int npai
   if (ref != UOTK_REF_PRODUCT && ref != UOTK_REF_COUNTING)
     return set_error(ctx, UOTK_ERR_INVALID, "unknown reference measure %d", ref);
   if (!(tol >= 0.0) && !(tol <= 0.0)) return set_error(ctx, UOTK_ERR_INVALID, "tol is NaN");
-  return op_uot_sinkhorn_batch(ctx, (cudaStream_t)stream, d, npairs, x_off, x, a, y_off, y, b,
-                               eps, rho1, rho2, max_sweeps, tol, ref, beta, gamma, sweeps_done,
-                               values);
+  cudaStream_t s = (cudaStream_t)stream;
+  ctx->batch_forms.assign(npairs, UOTK_DIRECT);
+  if (method == UOTK_DIRECT)
+    return op_uot_sinkhorn_batch(ctx, s, d, npairs, x_off, x, a, y_off, y, b, eps, rho1, rho2,
+                                 max_sweeps, tol, ref, beta, gamma, sweeps_done, values, nullptr, 0);
+  // UOTK_AUTO.  Every pair with at least BATCH_AUTO_MIN points on both sides has
+  // its form measured by the autotuner, per sum on a built engine (the plan is
+  // paid once per solve): the beta half-step's sum y -> x within
+  // opts->target_err.  Pairs whose fastest form is the NFFT are solved one by
+  // one by the NFFT solver; the others together by the grouped direct batch,
+  // first (it clears gamma of its pairs only).  Start, stopping rule, cap and
+  // outputs per pair are those of the batch.
+  constexpr int64_t BATCH_AUTO_MIN = 16384;
+  uotk_sum_opts base = *opts;
+  base.method = UOTK_DIRECT;
+  std::vector<int> direct_pairs, nfft_pairs;
+  std::vector<uotk_sum_opts> form(npairs);
+  for (int p = 0; p < npairs; ++p) {
+    const int64_t np_ = x_off[p + 1] - x_off[p], mp = y_off[p + 1] - y_off[p];
+    if (np_ >= BATCH_AUTO_MIN && mp >= BATCH_AUTO_MIN) {
+      uotk_sum_opts chosen{};
+      UOTK_TRY(op_autotune_sum(ctx, s, d, y + y_off[p] * d, mp, b + y_off[p], x + x_off[p] * d,
+                               np_, eps[p], &base, &chosen, nullptr, true));
+      if (chosen.method == UOTK_NFFT) {
+        form[p] = chosen;
+        nfft_pairs.push_back(p);
+        ctx->batch_forms[p] = UOTK_NFFT;
+        continue;
+      }
+    }
+    direct_pairs.push_back(p);
+  }
+  uotk_status st_direct = UOTK_OK;
+  if (!direct_pairs.empty()) {
+    st_direct = op_uot_sinkhorn_batch(ctx, s, d, npairs, x_off, x, a, y_off, y, b, eps, rho1,
+                                      rho2, max_sweeps, tol, ref, beta, gamma, sweeps_done,
+                                      values, direct_pairs.data(), (int)direct_pairs.size());
+    if (st_direct != UOTK_OK && st_direct != UOTK_ERR_NOT_CONVERGED) return st_direct;
+  }
+  int nfft_open = 0;
+  for (int p : nfft_pairs) {
+    const int64_t np_ = x_off[p + 1] - x_off[p], mp = y_off[p + 1] - y_off[p];
+    int sw = 0;
+    double val = 0.0;
+    const uotk_status st = op_uot_sinkhorn(ctx, s, d, x + x_off[p] * d, np_, a + x_off[p],
+                                           y + y_off[p] * d, mp, b + y_off[p], eps[p], rho1[p],
+                                           rho2[p], max_sweeps, tol, ref, 0u, beta + x_off[p],
+                                           gamma + y_off[p], &sw, &val, &form[p]);
+    if (st == UOTK_ERR_NOT_CONVERGED) ++nfft_open;
+    else if (st != UOTK_OK) return st;
+    if (sweeps_done) sweeps_done[p] = sw;
+    if (values) values[p] = val;
+  }
+  if (st_direct == UOTK_ERR_NOT_CONVERGED || nfft_open > 0)
+    return set_error(ctx, UOTK_ERR_NOT_CONVERGED,
+                     "uot_sinkhorn_batch: pairs did not reach tol %g in %d sweeps (%d of %zu "
+                     "NFFT-form pairs; direct-form pairs: %s)",
+                     tol, max_sweeps, nfft_open, nfft_pairs.size(),
+                     st_direct == UOTK_ERR_NOT_CONVERGED ? "some" : "none");
+  return UOTK_OK;
+}
+
+uotk_status uotk_batch_forms(uotk_ctx* ctx, int npairs, int32_t* forms) {
+  UOTK_TRY(enter(ctx));
+  if (!forms || npairs != (int)ctx->batch_forms.size())
+    return set_error(ctx, UOTK_ERR_INVALID,
+                     "batch_forms: forms null or npairs %d != the last batch's %zu", npairs,
+                     ctx->batch_forms.size());
+  for (int p = 0; p < npairs; ++p) forms[p] = ctx->batch_forms[p];
+  return UOTK_OK;
 }
 
 uotk_status uotk_sinkhorn_divergence(uotk_ctx* ctx, void* stream, int d, const float* x,

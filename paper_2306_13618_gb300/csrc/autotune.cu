@@ -6,14 +6,18 @@
 //   * error: max_j |s_j - s*_j| / sum |w| over 256 targets spread through the
 //     target array, s* their exact sums taken in FP64 by k_ref64;
 // and the fastest form whose error meets the target is kept, per (d, n, m,
-// eps, target, fixed grid/cut-off, bounding box of the points), in a small
-// cache of the context.  Candidates: the direct FP32 form (always accepted: it
+// eps, target, fixed grid/cut-off, bounding box of the points, timing mode),
+// in a small cache of the context.  With per_sum, each form is timed as one
+// sum on an engine already built (the NFFT plan and binning, or the direct
+// form's packing, excluded): the cost per sum of a solve that builds its
+// engine once and sums hundreds of times.  Candidates: the direct FP32 form (always accepted: it
 // is the exact sum up to FP32 rounding), the tensor-core forms for d > 3, and
 // for d <= 3 the NFFT at grid 64 and 128 (or the caller's grid) with cut-off
 // m = 4..8 (or the caller's), where the plan accepts them.
 #include <math.h>
 #include <string.h>
 
+#include <memory>
 #include <vector>
 
 #include "nfft.cuh"
@@ -89,7 +93,7 @@ __global__ void k_abs_sum(const float* __restrict__ w, long long n, double* __re
 bool same_key(const AutoEntry& e, const AutoEntry& k) {
   return e.valid && e.d == k.d && e.n == k.n && e.m == k.m && e.eps == k.eps &&
          e.target == k.target && e.grid_in == k.grid_in && e.cutoff_in == k.cutoff_in &&
-         memcmp(e.box, k.box, sizeof(e.box)) == 0;
+         e.per_sum == k.per_sum && memcmp(e.box, k.box, sizeof(e.box)) == 0;
 }
 
 // Scratch of one autotuning run, owned by it (the context's workspace is
@@ -105,7 +109,8 @@ struct AtScratch {
 
 uotk_status op_autotune_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* src, int64_t n,
                             const float* w, const float* tgt, int64_t m, double eps,
-                            const uotk_sum_opts* in, uotk_sum_opts* out, double* report) {
+                            const uotk_sum_opts* in, uotk_sum_opts* out, double* report,
+                            bool per_sum) {
   const uotk_sum_opts base = in ? *in : uotk_sum_opts{};
   if (base.kernel != UOTK_KERNEL_GAUSS)
     return set_error(ctx, UOTK_ERR_UNSUPPORTED, "autotune: the Gaussian kernel only");
@@ -121,6 +126,7 @@ uotk_status op_autotune_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* s
   key.target = target;
   key.grid_in = base.grid;
   key.cutoff_in = base.cutoff;
+  key.per_sum = per_sum;
   if (d <= 3) {
     float lo[3], hi[3];
     UOTK_TRY(nfft_bbox(ctx, s, d, src, n, tgt, m, lo, hi));
@@ -225,6 +231,46 @@ uotk_status op_autotune_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* s
     *msec = f;
     return true;
   };
+  // per_sum: one sum on an engine already built, after an untimed one
+  auto timed_sum = [&](const uotk_sum_opts& o, const float* t, int64_t mt,
+                       double* msec) -> bool {
+    EngineSpec sp{o.method, d, t, mt, nullptr, src, n, w, eps, &o};
+    Carver size(nullptr);
+    const size_t eb = engine_bytes(ctx, sp);
+    size.off = eb;
+    size.take<float>(mt > 0 ? mt : 1);
+    uotk_status st = ws_reserve(ctx, size.off);
+    if (st == UOTK_OK) st = flags_reset(ctx, s);
+    Engine* raw = nullptr;
+    if (st == UOTK_OK) {
+      Carver cv(ctx->ws);
+      st = engine_create(ctx, s, sp, cv, &raw);
+    }
+    std::unique_ptr<Engine> E(raw);
+    if (st == UOTK_ERR_UNSUPPORTED || st == UOTK_ERR_INVALID) return false;
+    if (st != UOTK_OK) {
+      bad = st;
+      return false;
+    }
+    Carver cv(ctx->ws);
+    cv.off = eb;
+    float* tmp = cv.take<float>(mt > 0 ? mt : 1);
+    st = E->plain(s, 1, 0, E->weights(1), tmp);
+    if (st == UOTK_OK && cudaEventRecord(e0, s) != cudaSuccess) st = UOTK_ERR_CUDA;
+    if (st == UOTK_OK) st = E->plain(s, 1, 0, E->weights(1), tmp);
+    float f = 0.f;
+    if (st == UOTK_OK &&
+        (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+         cudaEventElapsedTime(&f, e0, e1) != cudaSuccess))
+      st = UOTK_ERR_CUDA;
+    if (st == UOTK_OK) st = flags_check(ctx, s, "autotune");
+    if (st != UOTK_OK) {
+      bad = st;
+      return false;
+    }
+    *msec = f;
+    return true;
+  };
   // the direct forms: timed on a prefix of the targets, error on the samples
   std::vector<int> direct_forms = {UOTK_DIRECT};
   if (d > 3) {
@@ -237,7 +283,7 @@ uotk_status op_autotune_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* s
     uotk_sum_opts o = base;
     o.method = meth;
     double t_ms;
-    if (!timed(o, tgt, mt, d_full, &t_ms)) continue;
+    if (!(per_sum ? timed_sum(o, tgt, mt, &t_ms) : timed(o, tgt, mt, d_full, &t_ms))) continue;
     if (op_kernel_sum(ctx, s, d, src, n, w, d_tgt, ms, d_samp, eps, &o) != UOTK_OK) continue;
     meas.push_back({o, t_ms * (double)m / (double)mt, sample_err()});
   }
@@ -256,7 +302,16 @@ uotk_status op_autotune_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* s
         o.cutoff = c;
         o.target_err = target;
         double t_ms;
-        if (!timed(o, tgt, m, d_full, &t_ms)) continue;
+        if (per_sum) {
+          if (!timed_sum(o, tgt, m, &t_ms)) continue;
+          const uotk_status st = op_kernel_sum(ctx, s, d, src, n, w, tgt, m, d_full, eps, &o);
+          if (st != UOTK_OK) {
+            if (st != UOTK_ERR_UNSUPPORTED && st != UOTK_ERR_INVALID) bad = st;
+            continue;
+          }
+        } else if (!timed(o, tgt, m, d_full, &t_ms)) {
+          continue;
+        }
         k_take<<<grid_for(ctx, ms, 256, 1), 256, 0, s>>>(d_full, d_idx, ms, d_samp);
         UOTK_LAUNCHED(ctx);
         meas.push_back({o, t_ms, sample_err()});

@@ -285,12 +285,26 @@ uotk_status upload(uotk_ctx* ctx, cudaStream_t s, T* dst, const std::vector<T>& 
 
 }  // namespace
 
-uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npairs,
+uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npairs_all,
                                   const int64_t* x_off, const float* x, const float* a,
                                   const int64_t* y_off, const float* y, const float* b,
-                                  const double* eps, const double* rho1, const double* rho2,
-                                  int max_sweeps, double tol, int ref, double* beta,
-                                  double* gamma, int* sweeps_done, double* values) {
+                                  const double* eps_all, const double* rho1_all,
+                                  const double* rho2_all, int max_sweeps, double tol, int ref,
+                                  double* beta, double* gamma, int* sweeps_done_all,
+                                  double* values_all, const int* subset, int nsub) {
+  // With `subset`, only the pairs subset[0 .. nsub-1] of the caller's npairs_all
+  // are solved (each keeps its own point ranges and outputs); pair k below is
+  // the caller's pair orig[k].
+  const int npairs = subset ? nsub : npairs_all;
+  std::vector<int> orig(npairs);
+  for (int k = 0; k < npairs; ++k) orig[k] = subset ? subset[k] : k;
+  std::vector<double> eps(npairs), rho1(npairs), rho2(npairs);
+  for (int k = 0; k < npairs; ++k) {
+    eps[k] = eps_all[orig[k]];
+    rho1[k] = rho1_all[orig[k]];
+    rho2[k] = rho2_all[orig[k]];
+  }
+  if (npairs == 0) return UOTK_OK;
   // ---- per-pair layout and work-item tables (host) ----
   std::vector<PairDev> P(npairs);
   std::vector<SumItem> sx, sy;
@@ -299,10 +313,11 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
   const long long tile = DIRECT_TILE;
   for (int p = 0; p < npairs; ++p) {
     PairDev& q = P[p];
-    q.x_off = x_off[p];
-    q.y_off = y_off[p];
-    q.n = x_off[p + 1] - x_off[p];
-    q.m = y_off[p + 1] - y_off[p];
+    const int o = orig[p];
+    q.x_off = x_off[o];
+    q.y_off = y_off[o];
+    q.n = x_off[o + 1] - x_off[o];
+    q.m = y_off[o + 1] - y_off[o];
     q.tiles_x = (int)((q.n + tile - 1) / tile);
     q.tiles_y = (int)((q.m + tile - 1) / tile);
     q.px_off = px;
@@ -334,7 +349,7 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
   }
   if (sx.size() > 0x7fffffff || sy.size() > 0x7fffffff)
     return set_error(ctx, UOTK_ERR_UNSUPPORTED, "uot_sinkhorn_batch: too many work items");
-  const long long total_n = x_off[npairs] - x_off[0], total_m = y_off[npairs] - y_off[0];
+  const long long total_n = x_off[npairs_all] - x_off[0], total_m = y_off[npairs_all] - y_off[0];
 
   // ---- workspace ----
   auto carve = [&](Carver& cv, PairDev** dp, SumItem** dsx, SumItem** dsy, ElemItem** dex,
@@ -386,7 +401,12 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
   UOTK_TRY(upload(ctx, s, dEY, ey));
   UOTK_CUDA(ctx, cudaMemsetAsync(dPX, 0, sizeof(float4) * (px > 0 ? px : 1), s));
   UOTK_CUDA(ctx, cudaMemsetAsync(dPY, 0, sizeof(float4) * (py > 0 ? py : 1), s));
-  UOTK_CUDA(ctx, cudaMemsetAsync(gamma + y_off[0], 0, sizeof(double) * total_m, s));
+  if (!subset) {
+    UOTK_CUDA(ctx, cudaMemsetAsync(gamma + y_off[0], 0, sizeof(double) * total_m, s));
+  } else {
+    for (int p = 0; p < npairs; ++p)
+      UOTK_CUDA(ctx, cudaMemsetAsync(gamma + P[p].y_off, 0, sizeof(double) * P[p].m, s));
+  }
   k_batch_init<<<grid_for(ctx, npairs, 256), 256, 0, s>>>(dP, npairs, slots, act);
   UOTK_LAUNCHED(ctx);
   if (!ex.empty()) {
@@ -590,10 +610,10 @@ uotk_status op_uot_sinkhorn_batch(uotk_ctx* ctx, cudaStream_t s, int d, int npai
     const double* h = &hv[(size_t)p * 5];
     double coupling = h[4];
     if (ref == 0) coupling -= h[2] * h[3];
-    if (values)
-      values[p] = -P[p].eta1 * h[0] - P[p].eta2 * h[1] + P[p].eta1 * h[2] + P[p].eta2 * h[3] -
-                  coupling / P[p].lam;
-    if (sweeps_done) sweeps_done[p] = sweeps[p];
+    if (values_all)
+      values_all[orig[p]] = -P[p].eta1 * h[0] - P[p].eta2 * h[1] + P[p].eta1 * h[2] +
+                            P[p].eta2 * h[3] - coupling / P[p].lam;
+    if (sweeps_done_all) sweeps_done_all[orig[p]] = sweeps[p];
   }
   if (track && remaining > 0)
     return set_error(ctx, UOTK_ERR_NOT_CONVERGED,

@@ -6,6 +6,8 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <vector>
+
 #include "../../include/uotk.h"
 
 // ---------------------------------------------------------------------------
@@ -33,6 +35,7 @@ struct AutoEntry {
   int64_t n = 0, m = 0;
   double eps = 0.0, target = 0.0;
   int grid_in = 0, cutoff_in = 0;
+  bool per_sum = false;  // timed per sum on a built plan (see op_autotune_sum)
   float box[6] = {0, 0, 0, 0, 0, 0};
   uotk_sum_opts chosen = {};
   double report[8] = {0, 0, 0, 0, 0, 0, 0, 0};
@@ -61,6 +64,7 @@ struct uotk_ctx {
   // autotuned forms, most recent first out
   AutoEntry autos[UOTK_AUTO_CACHE];
   int auto_next = 0;
+  std::vector<int> batch_forms;  // form of every pair of the last batched solve (uotk_method)
 };
 
 namespace uotk {
@@ -89,7 +93,8 @@ uotk_status set_error(uotk_ctx* ctx, uotk_status st, const char* fmt, ...);
 // (autotune.cu; uotk_autotune_sum).
 uotk_status op_autotune_sum(uotk_ctx* ctx, cudaStream_t s, int d, const float* src, int64_t n,
                             const float* w, const float* tgt, int64_t m, double eps,
-                            const uotk_sum_opts* in, uotk_sum_opts* out, double* report);
+                            const uotk_sum_opts* in, uotk_sum_opts* out, double* report,
+                            bool per_sum = false);
 
 // One dual half-step of Alg. 1 / Alg. 2 on the targets of a kernel sum t:
 //   pot_i <- -q (log t_i + shift)                 (ref 0)

@@ -108,6 +108,7 @@ def lib():
         L.uotk_uot_sinkhorn_batch.argtypes = [_P, _P, ctypes.c_int, ctypes.c_int, _P, _P, _P,
                                               _P, _P, _P, _P, _P, _P, ctypes.c_int, _D,
                                               ctypes.c_int, _P, _P, _P, _P, opts]
+        L.uotk_batch_forms.argtypes = [_P, ctypes.c_int, _P]
         L.uotk_mean_cost.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P,
                                      ctypes.c_int, ctypes.POINTER(_D), opts]
         L.uotk_cstar.argtypes = [_P, _P, ctypes.c_int, _P, _I64, _P, _P, _I64, _P, _D, _D, _D,
@@ -127,7 +128,8 @@ def lib():
         for name in ("uotk_create", "uotk_kernel_sum", "uotk_uot_sinkhorn",
                      "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
                      "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
-                     "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_mean_cost",
+                     "uotk_uot_sinkhorn_batch", "uotk_batch_forms", "uotk_uot_sinkhorn_scaled",
+            "uotk_mean_cost",
                      "uotk_cstar", "uotk_nfft_plan",
                      "uotk_nfft_cells", "uotk_nfft_spread", "uotk_nfft_convolve",
                      "uotk_nfft_gather"):
@@ -379,11 +381,13 @@ def uot_sinkhorn_scaled(x, a, y, b, eps_schedule, rho1, rho2=None, max_sweeps=10
 
 
 def uot_sinkhorn_batch(x, a, x_off, y, b, y_off, eps, rho1, rho2=None, max_sweeps=100, tol=0.0,
-                       ref="product", ctx=None):
+                       ref="product", method="direct", target_err=0.0, ctx=None):
     """Many independent problems at once (uotk_uot_sinkhorn_batch).
 
     x, a, y, b: concatenated CUDA tensors; x_off, y_off: host sequences of
     npairs + 1 offsets; eps, rho1, rho2: per-pair sequences (or scalars).
+    method "direct" (all pairs in the grouped direct batch) or "auto" (each
+    large pair's form measured; see batch_forms).
     Returns (beta, gamma, sweeps_done[npairs], values[npairs], converged)."""
     import numpy as np
     x, y = _pts(x, "x"), _pts(y, "y")
@@ -401,13 +405,23 @@ def uot_sinkhorn_batch(x, a, x_off, y, b, y_off, eps, rho1, rho2=None, max_sweep
     sweeps = np.zeros(npairs, dtype=np.int32)
     values = np.zeros(npairs, dtype=np.float64)
     refc = {"product": REF_PRODUCT, "counting": REF_COUNTING}.get(ref, ref)
-    o = _opts("direct")
+    o = _opts(method, target_err=target_err)
     st = ctx.check(lib().uotk_uot_sinkhorn_batch(
         ctx.handle, _stream(), x.shape[1], npairs, xo.ctypes.data, _ptr(x), _ptr(a),
         yo.ctypes.data, _ptr(y), _ptr(b), e.ctypes.data, r1.ctypes.data, r2.ctypes.data,
         int(max_sweeps), float(tol), int(refc), _ptr(beta), _ptr(gamma), sweeps.ctypes.data,
         values.ctypes.data, ctypes.byref(o)), ok=(UOTK_OK, UOTK_ERR_NOT_CONVERGED))
     return beta, gamma, sweeps, values, st == UOTK_OK
+
+
+def batch_forms(npairs, ctx=None):
+    """The form (DIRECT or NFFT) each pair of the last uot_sinkhorn_batch call on
+    ctx was solved with (uotk_batch_forms)."""
+    import numpy as np
+    ctx = ctx or default_context()
+    forms = np.zeros(npairs, dtype=np.int32)
+    ctx.check(lib().uotk_batch_forms(ctx.handle, int(npairs), forms.ctypes.data))
+    return forms
 
 
 def sinkhorn_divergence(x, a, y, b, eps, rho, max_sweeps=100, tol=0.0, method="direct",
@@ -596,6 +610,7 @@ EXPORTED = ["uotk_create", "uotk_destroy", "uotk_last_error", "uotk_status_strin
             "uotk_kernel_sum", "uotk_kernel_sum_noalloc", "uotk_autotune_sum", "uotk_uot_sinkhorn",
             "uotk_sinkhorn_divergence", "uotk_mmd2", "uotk_mmd2_grad",
             "uotk_sinkhorn_divergence_grad", "uotk_measure_unit_rates",
-            "uotk_uot_sinkhorn_batch", "uotk_uot_sinkhorn_scaled", "uotk_mean_cost",
+            "uotk_uot_sinkhorn_batch", "uotk_batch_forms", "uotk_uot_sinkhorn_scaled",
+            "uotk_mean_cost",
             "uotk_cstar", "uotk_nfft_plan", "uotk_nfft_cells",
             "uotk_nfft_spread", "uotk_nfft_convolve", "uotk_nfft_gather"]

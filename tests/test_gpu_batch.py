@@ -132,3 +132,43 @@ def test_batch_validation(uotk):
     with pytest.raises(uotk.UotkError) as e:
         run(uotk, inputs.PairBatch(B.x, B.a, B.x_off, B.y, B.b, B.y_off, eps, B.rho))
     assert e.value.status == 1
+
+
+def test_batch_auto_takes_nfft_for_large_clustered_pairs(uotk):
+    """UOTK_AUTO: pairs with at least 16384 points on both sides have their form
+    measured (per sum on a built plan); on clustered clouds of about 2e4 points
+    the NFFT wins and those pairs are solved by Alg. 2, while the small pairs
+    stay in the grouped direct batch.  Every pair against the FP64 Alg. 1 after
+    10 sweeps: direct-form pairs at the direct bar (1e-6), NFFT-form pairs at
+    the NFFT bar (1e-4, residual and value)."""
+    g = inputs.rng(4200)
+    sizes = [(2000, 3000), (20000, 18000), (4000, 2500), (19000, 21000), (3000, 3500)]
+    eps = [0.02, 0.02, 0.05, 0.02, 0.05]
+    rho = [0.5, 0.5, 1.0, 0.5, 1.0]
+    xs, ys, As, Bs = [], [], [], []
+    for n, m in sizes:
+        means = g.uniform(-0.2, 0.2, (5, 3))
+        xs.append(inputs.gmm_points(g, n, means, 0.03))
+        ys.append(inputs.gmm_points(g, m, means, 0.03))
+        As.append((g.uniform(0.5, 1.5, n) / n).astype(np.float32))
+        Bs.append((g.uniform(0.5, 1.5, m) / m).astype(np.float32))
+    x_off = np.cumsum([0] + [n for n, _ in sizes])
+    y_off = np.cumsum([0] + [m for _, m in sizes])
+    X, Y = np.concatenate(xs), np.concatenate(ys)
+    A, B = np.concatenate(As), np.concatenate(Bs)
+    beta, gamma, sw, vals, _ = uotk.uot_sinkhorn_batch(dev(X), dev(A), x_off, dev(Y), dev(B),
+                                                       y_off, eps, rho, max_sweeps=10,
+                                                       method="auto")
+    forms = uotk.batch_forms(len(sizes))
+    assert [int(f) for f in forms] == [uotk.DIRECT, uotk.NFFT, uotk.DIRECT, uotk.NFFT,
+                                       uotk.DIRECT], forms
+    beta, gamma = beta.cpu().numpy(), gamma.cpu().numpy()
+    for p in range(len(sizes)):
+        rb, rg = oracle.uot_sinkhorn(f64(xs[p]), f64(As[p]), f64(ys[p]), f64(Bs[p]), eps[p],
+                                     rho[p], sweeps=10)
+        res = residual(beta[x_off[p]:x_off[p + 1]], gamma[y_off[p]:y_off[p + 1]], rb, rg)
+        bar = 1e-4 if forms[p] == uotk.NFFT else 1e-6
+        assert sw[p] == 10 and res <= bar, (p, res)
+        v = oracle.dual_value(f64(xs[p]), f64(As[p]), f64(ys[p]), f64(Bs[p]), eps[p], rho[p],
+                              rho[p], rb, rg)
+        assert abs(vals[p] - v) <= bar * abs(v) + 1e-12, (p, vals[p], v)
