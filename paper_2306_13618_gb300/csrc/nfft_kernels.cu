@@ -1510,8 +1510,8 @@ __global__ void __launch_bounds__(256)
 // (2m)^3 nodes), held in registers as x pairs while consecutive targets share
 // a cell.  Per target, lane part = sum_x phi_x sum_{z,y} (phi_z phi_y) g[z][y][x]
 // (the inner sums packed over x pairs), and the warp adds the 32 parts.
-constexpr int GW = 32;      // targets per per-warp staging buffer (two buffers of 32 rows: two CTAs per SM)
-constexpr int GWARPS = 8;   // warps of a gather CTA
+constexpr int GW = 32;      // targets per per-warp staging buffer (two per warp)
+constexpr int GWARPS = 16;  // warps of a gather CTA (one CTA per SM: all 64K registers at 128 a thread)
 template <int M>
 struct GatherGeo {
   static constexpr int E = NFFT_TILE + 2 * M - 1;
@@ -1535,7 +1535,7 @@ __device__ __forceinline__ void stage_warp(float* buf, unsigned long long* bar,
 }
 
 template <int M, bool DUAL>
-__global__ void __launch_bounds__(32 * GWARPS, 2)
+__global__ void __launch_bounds__(32 * GWARPS, 1)
     k_gather_w(const float* __restrict__ win, const int* __restrict__ ckey,
                const int* __restrict__ unit_tile, const int* __restrict__ unit_begin,
                const int* __restrict__ unit_count, const int* __restrict__ chunk_unit_start,
