@@ -992,24 +992,27 @@ __global__ void __launch_bounds__(32 * WF_WARPS)
 // truncation bound), the operator is real, so two real lines share one complex
 // transform: line a in the real part, line b in the imaginary part.
 //
-// 128-point transforms by 8 threads each (4 per warp), split as 128 = 16 x 8:
-// with m = 8a + b and k = c + 16d,
-//   X[c + 16d] = sum_b W8^{bd} W128^{bc} sum_a x[8a + b] W16^{ac}.
-// Thread b holds x[8a + b], a < 16, takes the 16-point DFT over a in registers
-// and applies W128^{bc}; a transpose through shared memory hands thread t the
-// values of c = 2t and 2t + 1, whose 8-point DFTs over b give X[c + 16d].  The
-// inverse runs the same steps backwards from that layout.  A CTA of 4 warps
-// takes 32 lines (16 pairs); lines along y and z are staged through shared
-// memory as an [element][line] tile so that global accesses stay coalesced.
-// The passes run in place: every CTA reads its lines before it writes them,
-// and no other CTA of the pass touches them.
+// 128-point transforms by 16 threads each (2 per warp), split as 128 = 8 x 16:
+// with m = 16a + b and k = c + 8d,
+//   X[c + 8d] = sum_b W16^{bd} W128^{bc} sum_a x[16a + b] W8^{ac}.
+// Thread b holds x[16a + b], a < 8, takes the 8-point DFT over a in registers
+// and applies W128^{bc}.  A transpose through shared memory hands thread
+// t = 2c' + b0 the values of column c' at b = 2 b1 + b0, b1 < 8; their
+// 8-point DFT over b1, the twiddle W16^{b0 d1} and a 2-point DFT with the
+// partner thread t ^ 1 (a shuffle) give X[c' + 8 d1 + 64 b0] (the 16-point
+// DFT over b split as 8 x 2).  The inverse runs the same steps backwards.  A
+// CTA of 8 warps takes 32 lines (16 pairs): transform f of warp w holds line
+// 4w + f in the real part and line 4w + f + 2 in the imaginary part, so the
+// two transforms of a warp read neighbouring columns of the y and z passes'
+// [element][line] tile, which keeps global accesses coalesced.  The passes run
+// in place: every CTA reads its lines before it writes them, and no other CTA
+// of the pass touches them.
 constexpr int CIRC_LINES = 32;
-constexpr int CIRC_WARPS = 4;
-// Shared-memory strides chosen so that the transposes and the tile accesses
-// of a warp take at most three (transposes) or two (tile) wavefronts: a row c
-// of an FFT's [c][b] block is 9 float2 apart, FFT blocks 147 apart, tile rows
-// 35 floats apart.
-constexpr int CIRC_RS = 9, CIRC_FS = 147, CIRC_P = 35;
+constexpr int CIRC_WARPS = 8;
+// Shared-memory strides that make every transpose, twiddle-table and tile
+// access of a transform (16 threads) one wavefront: rows c of a transform's
+// [c][b] block 18 float2 apart, tile rows 34 floats apart.
+constexpr int CIRC_RS = 18, CIRC_FS = 8 * CIRC_RS, CIRC_P = 34;
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -1027,37 +1030,6 @@ __device__ __forceinline__ void dft4(float2& a0, float2& a1, float2& a2, float2&
   const float2 mi = FWD ? make_float2(t3.y, -t3.x) : make_float2(-t3.y, t3.x);
   a1 = c_add(t1, mi);
   a3 = c_sub(t1, mi);
-}
-// 16-point DFT of v (natural order in and out) as 4 x 4.
-template <bool FWD>
-__device__ __forceinline__ void dft16(float2 (&v)[16]) {
-  constexpr float C1 = 0.92387953251128674f, S1 = 0.38268343236508978f;
-  constexpr float R2 = 0.70710678118654752f;
-  const float sg = FWD ? -1.f : 1.f;
-  // inner 4-point DFTs over p of x[4p + q]
-#pragma unroll
-  for (int q = 0; q < 4; ++q) dft4<FWD>(v[q], v[4 + q], v[8 + q], v[12 + q]);
-  // twiddles W16^{q r} on element (r, q) at v[4r + q]
-  v[5] = c_rot(v[5], C1, sg * S1);      // q=1 r=1
-  v[6] = c_rot(v[6], R2, sg * R2);      // q=2 r=1
-  v[7] = c_rot(v[7], S1, sg * C1);      // q=3 r=1
-  v[9] = c_rot(v[9], R2, sg * R2);      // q=1 r=2
-  v[10] = make_float2(-sg * v[10].y, sg * v[10].x);  // q=2 r=2: W16^4 = exp(sg i pi/2)
-  v[11] = c_rot(v[11], -R2, sg * R2);   // q=3 r=2
-  v[13] = c_rot(v[13], S1, sg * C1);    // q=1 r=3
-  v[14] = c_rot(v[14], -R2, sg * R2);   // q=2 r=3
-  v[15] = c_rot(v[15], -C1, -sg * S1);  // q=3 r=3: W16^9
-  // outer 4-point DFTs over q; X[r + 4 s] lands at v[4 r + s]
-#pragma unroll
-  for (int r = 0; r < 4; ++r) dft4<FWD>(v[4 * r], v[4 * r + 1], v[4 * r + 2], v[4 * r + 3]);
-  // v[4 r + s] holds X[r + 4 s]: transpose the 4 x 4 index to natural order
-  float2 t;
-  t = v[1]; v[1] = v[4]; v[4] = t;
-  t = v[2]; v[2] = v[8]; v[8] = t;
-  t = v[3]; v[3] = v[12]; v[12] = t;
-  t = v[6]; v[6] = v[9]; v[9] = t;
-  t = v[7]; v[7] = v[13]; v[13] = t;
-  t = v[11]; v[11] = v[14]; v[14] = t;
 }
 // 8-point DFT of v (natural order in and out) as 4 x 2.
 template <bool FWD>
@@ -1078,26 +1050,34 @@ __device__ __forceinline__ void dft8(float2 (&v)[8]) {
 }
 
 template <int AXIS>
-__global__ void __launch_bounds__(32 * CIRC_WARPS, 4)
+__global__ void __launch_bounds__(32 * CIRC_WARPS)
     k_circ(float* __restrict__ g, const float* __restrict__ scale, int N) {
   constexpr int n = 128;
   constexpr int P = CIRC_P;
-  __shared__ float2 tw[n];
+  constexpr float R2 = 0.70710678118654752f, C1 = 0.92387953251128674f,
+                  S1 = 0.38268343236508978f;
+  // W16^{d}, d < 8 (cos, -sin)
+  constexpr float W16C[8] = {1.f, C1, R2, S1, 0.f, -S1, -R2, -C1};
+  constexpr float W16S[8] = {0.f, -S1, -R2, -C1, -1.f, -C1, -R2, -S1};
+  __shared__ float2 tw[CIRC_FS];  // W128^{b c} at c * CIRC_RS + b, c < 8, b < 16
   __shared__ float fac[n];
-  __shared__ float2 buf[CIRC_WARPS * 4 * CIRC_FS];  // per FFT: [c][b] at c * CIRC_RS + b
+  __shared__ float2 buf[CIRC_WARPS * 2 * CIRC_FS];  // per transform: [c][b] at c * CIRC_RS + b
   __shared__ float tile[AXIS == 0 ? 1 : n * P];
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    float sn, cs;
-    sincospif(-2.0f * (float)j / (float)n, &sn, &cs);
-    tw[j] = make_float2(cs, sn);
+    const int cj = j >> 4, bj = j & 15;
+    if (cj < 8) {
+      float sn, cs;
+      sincospif(-2.0f * (float)(bj * cj) / (float)n, &sn, &cs);
+      tw[cj * CIRC_RS + bj] = make_float2(cs, sn);
+    }
     // this axis's factor at frequency index j (k = j or j - n), zero outside |k| < N/2
     const int k = j < n / 2 ? j : j - n;
     fac[j] = (k > -N / 2 && k < N / 2) ? scale[AXIS * N + k + N / 2] : 0.f;
   }
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int f = lane >> 3, b = lane & 7;       // FFT of the warp, thread within it
-  const int pr = w * 4 + f;                     // line pair of the CTA
-  const int la = 2 * pr, lb = la + 1;
+  const int f = lane >> 4, b = lane & 15;      // transform of the warp, thread within it
+  const int la = 4 * w + f, lb = la + 2;       // its real and imaginary line
+  const int cq = b >> 1, b0 = b & 1;           // column and half of the second stage
   const int c = blockIdx.x;
   auto addr = [&](int e, int l) -> long long {
     if (AXIS == 0) return ((long long)c * CIRC_LINES + l) * n + e;
@@ -1106,10 +1086,10 @@ __global__ void __launch_bounds__(32 * CIRC_WARPS, 4)
     return ((long long)e * n + o) * n + x0 + l;
   };
   constexpr int PER = n * CIRC_LINES / (32 * CIRC_WARPS);
-  float2 v[16];
+  float2 v[8];
   if (AXIS == 0) {
 #pragma unroll
-    for (int a = 0; a < 16; ++a) v[a] = make_float2(g[addr(8 * a + b, la)], g[addr(8 * a + b, lb)]);
+    for (int a = 0; a < 8; ++a) v[a] = make_float2(g[addr(16 * a + b, la)], g[addr(16 * a + b, lb)]);
   } else {
     float t[PER];
 #pragma unroll
@@ -1126,59 +1106,67 @@ __global__ void __launch_bounds__(32 * CIRC_WARPS, 4)
   __syncthreads();
   if (AXIS != 0) {
 #pragma unroll
-    for (int a = 0; a < 16; ++a) v[a] = make_float2(tile[(8 * a + b) * P + la], tile[(8 * a + b) * P + lb]);
+    for (int a = 0; a < 8; ++a) v[a] = make_float2(tile[(16 * a + b) * P + la], tile[(16 * a + b) * P + lb]);
   }
-  float2* B = buf + (w * 4 + f) * CIRC_FS;
-  // forward: 16-point DFT over a, twiddle W128^{b c}, transpose
-  dft16<true>(v);
+  float2* B = buf + (w * 2 + f) * CIRC_FS;
+  // forward: 8-point DFT over a, twiddle W128^{b c}, transpose
+  dft8<true>(v);
 #pragma unroll
-  for (int cc = 0; cc < 16; ++cc) {
-    const float2 t = tw[(b * cc) & (n - 1)];
+  for (int cc = 0; cc < 8; ++cc) {
+    const float2 t = tw[cc * CIRC_RS + b];
     B[cc * CIRC_RS + b] = c_rot(v[cc], t.x, t.y);
   }
   __syncwarp();
-  float2 u0[8], u1[8];
 #pragma unroll
-  for (int bb = 0; bb < 8; ++bb) {
-    u0[bb] = B[2 * b * CIRC_RS + bb];
-    u1[bb] = B[(2 * b + 1) * CIRC_RS + bb];
+  for (int b1 = 0; b1 < 8; ++b1) v[b1] = B[cq * CIRC_RS + 2 * b1 + b0];
+  __syncwarp();
+  // 8-point DFT over b1, twiddle W16^{b0 d1}, 2-point DFT over b0 with the partner
+  dft8<true>(v);
+#pragma unroll
+  for (int d1 = 0; d1 < 8; ++d1) {
+    const float wc = b0 ? W16C[d1] : 1.f, ws = b0 ? W16S[d1] : 0.f;
+    const float2 z = c_rot(v[d1], wc, ws);
+    const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, z.x, 1),
+                                 __shfl_xor_sync(0xffffffffu, z.y, 1));
+    v[d1] = b0 ? c_sub(p, z) : c_add(z, p);
+  }
+  // v[d1] = X[cq + 8 d1 + 64 b0]: scale, then the inverse 2-point DFT over d0
+  // with the partner, twiddle W16^{-b0 d1}, 8-point DFT over d1
+#pragma unroll
+  for (int d1 = 0; d1 < 8; ++d1) {
+    const float s = fac[cq + 8 * d1 + 64 * b0];
+    const float2 z = make_float2(v[d1].x * s, v[d1].y * s);
+    const float2 p = make_float2(__shfl_xor_sync(0xffffffffu, z.x, 1),
+                                 __shfl_xor_sync(0xffffffffu, z.y, 1));
+    const float2 u = b0 ? c_sub(p, z) : c_add(z, p);
+    const float wc = b0 ? W16C[d1] : 1.f, ws = b0 ? W16S[d1] : 0.f;
+    v[d1] = c_rot(u, wc, -ws);
+  }
+  dft8<false>(v);
+  // v[b1] = value at b = 2 b1 + b0 of column cq: twiddle W128^{-b cq}, transpose
+#pragma unroll
+  for (int b1 = 0; b1 < 8; ++b1) {
+    const int bb = 2 * b1 + b0;
+    const float2 t = tw[cq * CIRC_RS + bb];
+    B[cq * CIRC_RS + bb] = c_rot(v[b1], t.x, -t.y);
   }
   __syncwarp();
-  dft8<true>(u0);
-  dft8<true>(u1);
-  // scale: u0[d] = X[2b + 16 d], u1[d] = X[2b + 1 + 16 d]
 #pragma unroll
-  for (int d = 0; d < 8; ++d) {
-    const float f0 = fac[2 * b + 16 * d], f1 = fac[2 * b + 1 + 16 * d];
-    u0[d] = make_float2(u0[d].x * f0, u0[d].y * f0);
-    u1[d] = make_float2(u1[d].x * f1, u1[d].y * f1);
-  }
-  // inverse: 8-point DFTs over d, twiddle W128^{-b' c}, transpose, 16-point over c
-  dft8<false>(u0);
-  dft8<false>(u1);
-#pragma unroll
-  for (int bb = 0; bb < 8; ++bb) {
-    const float2 t0 = tw[(bb * 2 * b) & (n - 1)], t1 = tw[(bb * (2 * b + 1)) & (n - 1)];
-    B[2 * b * CIRC_RS + bb] = c_rot(u0[bb], t0.x, -t0.y);
-    B[(2 * b + 1) * CIRC_RS + bb] = c_rot(u1[bb], t1.x, -t1.y);
-  }
-  __syncwarp();
-#pragma unroll
-  for (int cc = 0; cc < 16; ++cc) v[cc] = B[cc * CIRC_RS + b];
-  dft16<false>(v);
-  // v[a] = line values at element 8a + b (line a in x, line b in y)
+  for (int cc = 0; cc < 8; ++cc) v[cc] = B[cc * CIRC_RS + b];
+  dft8<false>(v);
+  // v[a] = line values at element 16a + b (line la in x, line lb in y)
   if (AXIS == 0) {
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {
-      g[addr(8 * a + b, la)] = v[a].x;
-      g[addr(8 * a + b, lb)] = v[a].y;
+    for (int a = 0; a < 8; ++a) {
+      g[addr(16 * a + b, la)] = v[a].x;
+      g[addr(16 * a + b, lb)] = v[a].y;
     }
   } else {
     __syncthreads();  // every warp has read its lines of the tile
 #pragma unroll
-    for (int a = 0; a < 16; ++a) {
-      tile[(8 * a + b) * P + la] = v[a].x;
-      tile[(8 * a + b) * P + lb] = v[a].y;
+    for (int a = 0; a < 8; ++a) {
+      tile[(16 * a + b) * P + la] = v[a].x;
+      tile[(16 * a + b) * P + lb] = v[a].y;
     }
     __syncthreads();
 #pragma unroll
