@@ -1016,7 +1016,7 @@ constexpr int CIRC_RS = 18, CIRC_FS = 8 * CIRC_RS, CIRC_P = 34;
 
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-// a * w for w = (c, s); FWD selects the sign of the exponent (-1 forward)
+// a * w for the complex w = c + i s
 __device__ __forceinline__ float2 c_rot(float2 a, float c, float s) {
   return make_float2(a.x * c - a.y * s, a.x * s + a.y * c);
 }
